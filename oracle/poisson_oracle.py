@@ -1,0 +1,346 @@
+"""Plain FP64 CPU oracle for the direct FFT pressure solve.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import or call this
+module: only the tests, the smoke check of ``__graft_entry__`` and the CPU
+baseline / reference arm of ``bench.py`` use it.  It shares no code with the
+CUDA path.
+
+What it computes (Brown, "A comparison of techniques for solving the Poisson
+equation in CFD", Section 2.1): a forward Fourier transform over the periodic
+x/y plane at every level, an independent vertical tridiagonal solve per
+(kx, ky) column, and a backward transform that gives the pressure.  The paper
+names a "Poisson-like elliptic equation" (Section 2) and nabla^2 x = b
+(Section 2.2) but prints no discretisation, so this module fixes one reading,
+listed in the design notes:
+
+  * cell-centred finite-volume 7-point operator, periodic in x and y with
+    uniform dx, dy; cell thicknesses dz[k]; reference density rho0[k] at cell
+    centres, faces by arithmetic mean; homogeneous Neumann (zero flux) at the
+    bottom and top faces;
+        (L p) = (p[i+1]-2p[i]+p[i-1])/dx^2 + (p[j+1]-2p[j]+p[j-1])/dy^2
+                + a_k (p[k-1]-p[k]) + c_k (p[k+1]-p[k]),
+        W_k = rho_k dz_k,  a_k = rho_{k-1/2}/(W_k h_{k-1/2}),
+        c_k = rho_{k+1/2}/(W_k h_{k+1/2}),  h_{k+1/2} = (dz_k+dz_{k+1})/2;
+  * compatibility: the source is projected, Q_W S = S - mu_W with mu_W the
+    W-weighted mean of S over all cells;
+  * the solution is the unique p with L p = Q_W S and plain mean zero.
+
+The solve is exact ("provides the exact solution every time", Section 3), so
+the oracle is that definition written out: a naive O(n^2) DFT per line built
+from exactly index-reduced twiddles (matrix products are the library step), the
+textbook Thomas recurrence per column, a dense bordered solve for the singular
+(0,0) column, and the naive inverse DFT.  No blocking, fusion or reordering.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "vertical_coefficients", "horizontal_eigenvalues", "weighted_mean", "project_compatible",
+    "apply_L", "residual", "dft_x", "dft_y", "idft_y", "idft_x", "thomas",
+    "column_matrix", "singular_column_solve", "solve", "adjoint", "rho0_gradient",
+    "relative_l2",
+]
+
+
+def _f64(x):
+    return np.asarray(x, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Operator pieces (Section 2: the elliptic pressure equation, read as above)
+# ---------------------------------------------------------------------------
+
+def vertical_coefficients(dz, rho0):
+    """Return (W, a, c) of the density-weighted vertical operator.
+
+    W_k = rho_k dz_k; a_k couples level k to k-1 (a_0 = 0), c_k couples k to k+1
+    (c_{nz-1} = 0): zero flux through the bottom and top faces.
+    """
+    dz = _f64(dz)
+    rho0 = _f64(rho0)
+    nz = dz.size
+    W = rho0 * dz
+    h = 0.5 * (dz[:-1] + dz[1:])              # centre-to-centre spacing at face k+1/2
+    rho_face = 0.5 * (rho0[:-1] + rho0[1:])   # density at face k+1/2
+    conductance = rho_face / h
+    a = np.zeros(nz)
+    c = np.zeros(nz)
+    c[:-1] = conductance / W[:-1]
+    a[1:] = conductance / W[1:]
+    return W, a, c
+
+
+def horizontal_eigenvalues(n, d, count=None):
+    """Eigenvalues of the periodic second difference on n points of spacing d.
+
+    For wavenumber m the eigenvector exp(2 pi i m j / n) gives
+    (e^{-i t} - 2 + e^{i t})/d^2 = -(4/d^2) sin^2(pi m / n); the sin^2 form
+    avoids the cancellation of 2cos(t)-2 at small m.
+    """
+    if count is None:
+        count = n
+    m = np.arange(count, dtype=np.float64)
+    return -(4.0 / (d * d)) * np.sin(np.pi * m / n) ** 2
+
+
+def weighted_mean(S, W):
+    """mu_W = sum_{ijk} W_k S_ijk / (nx ny sum_k W_k)."""
+    S = _f64(S)
+    nz, ny, nx = S.shape
+    level_sums = S.reshape(nz, -1).sum(axis=1)
+    return float(np.dot(W, level_sums) / (nx * ny * W.sum()))
+
+
+def project_compatible(S, W):
+    """Q_W S = S - mu_W: the part of S in the range of L (sum W_k (Q_W S)_ijk = 0)."""
+    return _f64(S) - weighted_mean(S, W)
+
+
+def apply_L(p, dx, dy, a, c):
+    """Matrix-free 7-point operator L p (periodic x/y, zero-flux z)."""
+    p = _f64(p)
+    Lx = (np.roll(p, -1, axis=2) - 2.0 * p + np.roll(p, 1, axis=2)) / (dx * dx)
+    Ly = (np.roll(p, -1, axis=1) - 2.0 * p + np.roll(p, 1, axis=1)) / (dy * dy)
+    Lz = np.zeros_like(p)
+    Lz[1:] += a[1:, None, None] * (p[:-1] - p[1:])
+    Lz[:-1] += c[:-1, None, None] * (p[1:] - p[:-1])
+    return Lx + Ly + Lz
+
+
+def residual(S, p, dx, dy, dz, rho0):
+    """r = Q_W S - L p (the quantity the relative-residual measure of Section 2.2 uses)."""
+    W, a, c = vertical_coefficients(dz, rho0)
+    return project_compatible(S, W) - apply_L(p, dx, dy, a, c)
+
+
+# ---------------------------------------------------------------------------
+# Naive discrete Fourier transforms (Section 2.1: one dimension at a time)
+# ---------------------------------------------------------------------------
+
+def _twiddles(n, count, sign):
+    """Matrix E[m, k] = exp(sign * 2 pi i ((m k) mod n) / n), m < n, k < count."""
+    m = np.arange(n, dtype=np.int64)[:, None]
+    k = np.arange(count, dtype=np.int64)[None, :]
+    r = (m * k) % n
+    t = 2.0 * np.pi * r.astype(np.float64) / n
+    return np.cos(t), sign * np.sin(t)
+
+
+def dft_x(S):
+    """Real forward DFT along x: X[..., kx] = sum_i S[..., i] e^{-2 pi i kx i/nx}, kx = 0..nx//2."""
+    S = _f64(S)
+    nx = S.shape[-1]
+    C, Sn = _twiddles(nx, nx // 2 + 1, -1.0)
+    return (S @ C) + 1j * (S @ Sn)
+
+
+def dft_y(X):
+    """Complex forward DFT along y (axis -2): Y[.., ky, kx] = sum_j e^{-2 pi i ky j/ny} X[.., j, kx]."""
+    ny = X.shape[-2]
+    C, Sn = _twiddles(ny, ny, -1.0)
+    F = C + 1j * Sn                    # symmetric: F[j, ky] = F[ky, j]
+    return np.matmul(F, X)
+
+
+def idft_y(Y):
+    """Complex inverse DFT along y with the 1/ny factor."""
+    ny = Y.shape[-2]
+    C, Sn = _twiddles(ny, ny, +1.0)
+    F = C + 1j * Sn
+    return np.matmul(F, Y) / ny
+
+
+def idft_x(X, nx):
+    """Real inverse DFT along x from the half spectrum kx = 0..nx//2, with 1/nx.
+
+    p[i] = (1/nx) sum_kx w_kx Re(X_kx e^{+2 pi i kx i/nx}); w = 1 for the
+    self-conjugate bins kx = 0 and (nx even) kx = nx/2, 2 for all others.
+    This is the full inverse DFT of the Hermitian extension of X, real part.
+    """
+    nh = nx // 2 + 1
+    assert X.shape[-1] == nh
+    w = np.full(nh, 2.0)
+    w[0] = 1.0
+    if nx % 2 == 0:
+        w[-1] = 1.0
+    C, Sn = _twiddles(nx, nh, +1.0)    # (nx, nh): [i, kx]
+    return (X.real @ (C * w).T - X.imag @ (Sn * w).T) / nx
+
+
+# ---------------------------------------------------------------------------
+# Column solves (Section 2.1: tridiagonal solve up and down each column)
+# ---------------------------------------------------------------------------
+
+def thomas(sub, diag, sup, rhs):
+    """Textbook Thomas recurrence, vectorised over independent columns.
+
+    Row k reads  sub[k] x[k-1] + diag[k] x[k] + sup[k] x[k+1] = rhs[k];
+    all arrays have the level index first and broadcast over the rest.
+    """
+    n = rhs.shape[0]
+    shape = np.broadcast_shapes(np.shape(diag[0]), np.shape(rhs[0]))
+    cp = np.empty((n,) + shape, dtype=np.result_type(diag, sup))
+    dp = np.empty((n,) + shape, dtype=np.result_type(diag, rhs))
+    beta = diag[0] * np.ones(shape)
+    cp[0] = sup[0] / beta
+    dp[0] = rhs[0] / beta
+    for k in range(1, n):
+        beta = diag[k] - sub[k] * cp[k - 1]
+        cp[k] = sup[k] / beta
+        dp[k] = (rhs[k] - sub[k] * dp[k - 1]) / beta
+    x = np.empty_like(dp)
+    x[n - 1] = dp[n - 1]
+    for k in range(n - 2, -1, -1):
+        x[k] = dp[k] - cp[k] * x[k + 1]
+    return x
+
+
+def column_matrix(a, c, lam):
+    """Dense T = L_z + lam I for one column (a, c from vertical_coefficients)."""
+    nz = a.size
+    T = np.zeros((nz, nz))
+    for k in range(nz):
+        T[k, k] = -(a[k] + c[k]) + lam
+        if k > 0:
+            T[k, k - 1] = a[k]
+        if k < nz - 1:
+            T[k, k + 1] = c[k]
+    return T
+
+
+def singular_column_solve(a, c, rhs, transpose=False):
+    """Unique zero-sum solution of T x = rhs for the singular (0,0) column.
+
+    T = L_z has null vector 1 (T^T has null vector W); the bordered matrix
+    [[T, 1], [1^T, 0]] is nonsingular and, for a compatible right-hand side,
+    its solution is the zero-sum x with multiplier 0.  Dense library solve.
+    """
+    nz = a.size
+    T = column_matrix(a, c, 0.0)
+    if transpose:
+        T = T.T
+    B = np.zeros((nz + 1, nz + 1))
+    B[:nz, :nz] = T
+    B[:nz, nz] = 1.0
+    B[nz, :nz] = 1.0
+    r = np.zeros(nz + 1, dtype=np.result_type(rhs, np.float64))
+    r[:nz] = rhs
+    return np.linalg.solve(B, r)[:nz]
+
+
+def _spectral_diag(a, c, dx, dy, nx, ny):
+    lx = horizontal_eigenvalues(nx, dx, nx // 2 + 1)     # (nxh,)
+    ly = horizontal_eigenvalues(ny, dy, ny)              # (ny,)
+    lam = ly[:, None] + lx[None, :]                      # (ny, nxh)
+    diag = -(a + c)[:, None, None] + lam[None, :, :]
+    # the (0,0) column is singular; it is solved separately, so give the
+    # textbook recurrence a diagonally dominant stand-in there and discard it
+    diag[:, 0, 0] = -(a + c) - 1.0
+    return diag
+
+
+def solve(S, dx, dy, dz, rho0, return_info=False):
+    """p = the zero-mean solution of L p = Q_W S (Section 2.1 structure).
+
+    Forward DFT in x then y at every level, textbook Thomas per (kx, ky)
+    column with T = L_z + (lambda_x + lambda_y) I, bordered solve for the
+    (0,0) column, inverse DFT in y then x.
+    """
+    S = _f64(S)
+    nz, ny, nx = S.shape
+    W, a, c = vertical_coefficients(dz, rho0)
+    mu_W = weighted_mean(S, W)
+    Shat = dft_y(dft_x(S - mu_W))                          # (nz, ny, nxh)
+    diag = _spectral_diag(a, c, dx, dy, nx, ny)
+    sub = a[:, None, None]
+    sup = c[:, None, None]
+    phat = thomas(sub, diag, sup, Shat)
+    phat[:, 0, 0] = singular_column_solve(a, c, Shat[:, 0, 0])
+    p = idft_x(idft_y(phat), nx)
+    if return_info:
+        return p, {"removed_weighted_mean": mu_W}
+    return p
+
+
+def adjoint(wgt, dx, dy, dz, rho0):
+    """g = G^T wgt where G: S -> p is the map computed by solve().
+
+    G = P_1 L^+ Q_W with P_1 the plain-mean projection.  The 2-D DFT matrix is
+    symmetric and each column matrix is the same for +k and -k, so
+    G^T = Q_W^T F^{-1} T_k^{-T} F P_1: forward DFT, transposed column solve,
+    inverse DFT.  In the (0,0) column P_1 removes the plain mean of the
+    transformed weights, the transposed singular column (null vector W) is
+    solved by the bordered system, and Q_W^T v = v - W (sum v)/(nx ny sum W)
+    removes the W direction.
+    """
+    wgt = _f64(wgt)
+    nz, ny, nx = wgt.shape
+    W, a, c = vertical_coefficients(dz, rho0)
+    What = dft_y(dft_x(wgt))
+    What[:, 0, 0] -= What[:, 0, 0].mean()                  # P_1
+    diag = _spectral_diag(a, c, dx, dy, nx, ny)
+    # T^T: row k has T[k-1,k] = c_{k-1} below the diagonal and T[k+1,k] = a_{k+1} above
+    sub_t = np.zeros(nz)
+    sup_t = np.zeros(nz)
+    sub_t[1:] = c[:-1]
+    sup_t[:-1] = a[1:]
+    mhat = thomas(sub_t[:, None, None], diag, sup_t[:, None, None], What)
+    mhat[:, 0, 0] = singular_column_solve(a, c, What[:, 0, 0], transpose=True)
+    m = idft_x(idft_y(mhat), nx)
+    m -= W[:, None, None] * (m.sum() / (nx * ny * W.sum()))  # Q_W^T
+    return m
+
+
+def rho0_gradient(wgt, S, dx, dy, dz, rho0, p=None, g=None):
+    """d(sum wgt*p)/d rho0_m for p = solve(S; rho0).
+
+    Differentiating L p = Q_W S with 1^T p = 0 gives
+        dl/drho_m = g^T (dQ_W/drho_m S - dL/drho_m p),  g = G^T wgt.
+    dL/drho_m only touches the vertical coefficients a_k, c_k of rows m-1, m,
+    m+1 (through W_m and the face densities at m-1/2, m+1/2).
+    """
+    dz = _f64(dz)
+    rho0 = _f64(rho0)
+    S = _f64(S)
+    nz, ny, nx = S.shape
+    W, a, c = vertical_coefficients(dz, rho0)
+    if p is None:
+        p = solve(S, dx, dy, dz, rho0)
+    if g is None:
+        g = adjoint(wgt, dx, dy, dz, rho0)
+    h = 0.5 * (dz[:-1] + dz[1:])
+    # per-level contractions  Ma_k = sum_ij g_k (p_{k-1}-p_k),  Mc_k = sum_ij g_k (p_{k+1}-p_k)
+    Ma = np.zeros(nz)
+    Mc = np.zeros(nz)
+    Ma[1:] = np.einsum("kji,kji->k", g[1:], p[:-1] - p[1:])
+    Mc[:-1] = np.einsum("kji,kji->k", g[:-1], p[1:] - p[:-1])
+    level_S = S.reshape(nz, -1).sum(axis=1)
+    level_g = g.reshape(nz, -1).sum(axis=1)
+    sumW = W.sum()
+    mu_W = np.dot(W, level_S) / (nx * ny * sumW)
+    grad = np.zeros(nz)
+    for m in range(nz):
+        da = np.zeros(nz)
+        dc = np.zeros(nz)
+        for k in range(nz):
+            dW = dz[k] if k == m else 0.0
+            if k > 0:   # a_k = rho_face[k-1] / (W_k h[k-1])
+                dnum = 0.5 if m in (k - 1, k) else 0.0
+                da[k] = dnum / (W[k] * h[k - 1]) - a[k] * dW / W[k]
+            if k < nz - 1:   # c_k = rho_face[k] / (W_k h[k])
+                dnum = 0.5 if m in (k, k + 1) else 0.0
+                dc[k] = dnum / (W[k] * h[k]) - c[k] * dW / W[k]
+        dL_term = np.dot(da, Ma) + np.dot(dc, Mc)
+        # Q_W S = S - mu_W 1:  d/drho_m (-mu_W) contracted with g
+        dmu = dz[m] * (level_S[m] - nx * ny * mu_W) / (nx * ny * sumW)
+        dQ_term = -dmu * level_g.sum()
+        grad[m] = dQ_term - dL_term
+    return grad
+
+
+def relative_l2(x, ref):
+    """||x - ref||_2 / ||ref||_2 over all cells."""
+    x = _f64(x)
+    ref = _f64(ref)
+    return float(np.linalg.norm((x - ref).ravel()) / np.linalg.norm(ref.ravel()))
