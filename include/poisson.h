@@ -1,0 +1,148 @@
+/*
+ * poisson.h -- C ABI of the GB300 direct FFT pressure solver.
+ *
+ * The solver computes the pressure p of the Poisson-like elliptic equation that
+ * a dynamical core solves every timestep (Brown, "A comparison of techniques
+ * for solving the Poisson equation in CFD", Section 2), by the direct method of
+ * Section 2.1: a forward real Fourier transform over the periodic x/y plane at
+ * every level, an independent tridiagonal solve per (kx, ky) wavenumber column,
+ * and a backward transform.  Planning happens once and the plan is reused every
+ * solve (the FFTW-style plan-once idea of Section 2.1).
+ *
+ * Discretisation (the paper names the equation but prints no stencil; this is
+ * the reading the library implements):
+ *   (L p)_ijk = (p_{i+1}-2p_i+p_{i-1})/dx^2 + (p_{j+1}-2p_j+p_{j-1})/dy^2
+ *             + a_k (p_{k-1}-p_k) + c_k (p_{k+1}-p_k)
+ *   W_k = rho0_k dz_k, a_k = rho_{k-1/2}/(W_k h_{k-1/2}), c_k = rho_{k+1/2}/(W_k h_{k+1/2}),
+ *   h_{k+1/2} = (dz_k + dz_{k+1})/2, rho_{k+1/2} = (rho0_k + rho0_{k+1})/2,
+ *   a_0 = c_{nz-1} = 0 (zero flux through the bottom and top faces),
+ *   periodic in x and y.
+ * The solve returns the unique p with  L p = S - mu_W  and plain mean zero,
+ * mu_W = sum W_k S_ijk / (nx ny sum W_k) (the part of S outside the range of L).
+ *
+ * Memory conventions (all calls):
+ *   - fields are C-contiguous [nz][ny][nx] arrays, x fastest, in DEVICE memory;
+ *   - element type: double for POISSON_FP64 and POISSON_MIXED, float for POISSON_FP32;
+ *   - the caller owns every field and the workspace; the plan owns only its small
+ *     device tables (coefficients, twiddles), allocated by create, freed by destroy;
+ *   - every call is asynchronous on the given CUDA stream (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream) unless it fills a poisson_info, in which
+ *     case it synchronises that stream before returning;
+ *   - one plan + one workspace must not be used by two calls in flight at once;
+ *   - no call throws; every call returns a poisson_status.
+ */
+#ifndef POISSON_GB300_H
+#define POISSON_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct poisson_plan poisson_plan;    /* opaque, owned by the library */
+typedef struct poisson_batch poisson_batch;  /* opaque, owned by the library */
+
+typedef enum {
+  POISSON_OK = 0,
+  POISSON_ERR_INVALID_ARG = -1,    /* null pointer, aliasing, non-positive spacing, bad enum */
+  POISSON_ERR_UNSUPPORTED = -2,    /* size not of the supported form (see poisson_plan_create) */
+  POISSON_ERR_CUDA = -3,           /* a CUDA runtime call failed (allocation, launch, copy) */
+  POISSON_ERR_WORKSPACE = -4,      /* workspace pointer NULL or not 256-byte aligned */
+  POISSON_ERR_NOT_CONVERGED = -5,  /* mixed path: refinement stopped above its tolerance; p is written */
+  POISSON_ERR_TIMEOUT = -6         /* a bounded device-side wait gave up (batched scheduler) */
+} poisson_status;
+
+typedef enum { POISSON_BC_PERIODIC_XY_NEUMANN_Z = 0 } poisson_bc;
+
+typedef enum {
+  POISSON_FP64 = 0,   /* all arithmetic in double */
+  POISSON_FP32 = 1,   /* all arithmetic in float */
+  POISSON_MIXED = 2   /* double in/out; float transforms; double low-|k| columns;
+                         double-float residual and iterative refinement */
+} poisson_dtype;
+
+/* Plan options (poisson_plan_set_option). */
+typedef enum {
+  POISSON_OPT_LOWK_RADIUS2 = 0,  /* mixed: columns with kx^2 + ky'^2 <= value (ky' signed) use
+                                    double; default 64 (|k| <= 8); the (0,0) column always does */
+  POISSON_OPT_MAX_SWEEPS = 1,    /* mixed: refinement sweeps after the first solve, 0..3; default 3 */
+  POISSON_OPT_TOLERANCE = 2,     /* mixed: target relative L2 error estimate; default 1e-11 */
+  POISSON_OPT_Y_TILE = 3         /* y-pass kx tile width (autotuner hook); 0 = plan default */
+} poisson_option;
+
+typedef struct {
+  int sweeps;                  /* refinement sweeps executed (mixed path; 0 otherwise) */
+  int converged;               /* 1 if the mixed stopping test passed (always 1 for FP64/FP32) */
+  double rel_update[4];        /* ||delta_n||_2/||p||_2 of sweep n (index 0 = first solve = 1) */
+  double error_estimate;       /* estimated relative L2 error of the returned p (mixed path) */
+  double removed_weighted_mean;/* mu_W removed from S (first solve) */
+} poisson_info;
+
+/* Create a plan.  dz and rho0 are HOST arrays of nz doubles (copied).
+ * Supported: nx even, nx >= 4, ny >= 4, each of nx, ny of the form 2^a 3^b and
+ * <= 4096, nz in [2, 512]; dx, dy > 0; dz[k] > 0; rho0[k] > 0.
+ * Returns POISSON_ERR_UNSUPPORTED for other sizes, INVALID_ARG for bad values.
+ * *out is set to NULL on failure. */
+int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const double* dz,
+                        const double* rho0, int bc, int dtype, poisson_plan** out);
+
+/* Bytes of device workspace one solve/adjoint call of this plan needs. */
+int poisson_plan_workspace_bytes(const poisson_plan* plan, size_t* bytes);
+
+/* Set a plan option (see poisson_option).  Values out of range: INVALID_ARG. */
+int poisson_plan_set_option(poisson_plan* plan, int option, double value);
+
+/* Replace rho0 from a DEVICE array of nz doubles, recomputing the vertical
+ * coefficient tables on the device, asynchronously on stream (used when rho0 is
+ * a trained parameter).  Values must be positive; this is not checked on the
+ * host (the call stays asynchronous). */
+int poisson_plan_set_rho0(poisson_plan* plan, const double* rho0_dev, void* stream);
+
+/* Solve for p given the source S (both device fields of the plan's element type;
+ * they must not overlap: INVALID_ARG).  workspace: device, >= workspace_bytes,
+ * 256-byte aligned.  info: nullable host struct; when given, the call synchronises
+ * the stream and fills it.  Mixed path: returns POISSON_ERR_NOT_CONVERGED (p still
+ * written) when info is given and the error estimate stays above the tolerance. */
+int poisson_solve(poisson_plan* plan, const void* S, void* p, void* workspace, void* stream,
+                  poisson_info* info);
+
+/* Adjoint of the solve map G: S -> p (a linear map for fixed rho0).
+ * gp: dL/dp (device field); gS (out, device field): G^T gp = dL/dS.
+ * grho (out, nullable, device array of nz doubles): dL/drho0 for p = G(rho0) S,
+ * which needs p, the forward result (ignored when grho is NULL).
+ * Same element type, workspace and stream rules as poisson_solve; gp, p, gS must
+ * not overlap.  The mixed dtype runs the adjoint with double fields and float
+ * transforms (no refinement). */
+int poisson_solve_adjoint(poisson_plan* plan, const void* gp, const void* p, void* gS,
+                          double* grho, void* workspace, void* stream);
+
+/* NULL-safe.  Frees the plan's device tables (synchronously). */
+int poisson_plan_destroy(poisson_plan* plan);
+
+/* Static string for a status code. */
+const char* poisson_status_string(int status);
+
+/* Text of the last CUDA failure seen by this thread (for POISSON_ERR_CUDA). */
+const char* poisson_last_error_detail(void);
+
+/* ---- Batched: many independent domains of uneven sizes in one graph launch ----
+ * Arrays have n entries; dz[b], rho0[b] are host arrays of nz[b] doubles.
+ * dtype POISSON_FP32 (float fields) or POISSON_MIXED (double fields). */
+int poisson_batch_create(int n, const int* nx, const int* ny, const int* nz, const double* dx,
+                         const double* dy, const double* const* dz, const double* const* rho0,
+                         int dtype, poisson_batch** out);
+int poisson_batch_workspace_bytes(const poisson_batch* batch, size_t* bytes);
+/* S[b], p[b]: device fields of domain b.  info: nullable array of n structs.
+ * The first call captures the launch sequence of all domains into a CUDA graph
+ * bound to the given pointers and workspace; later calls with the same pointers,
+ * workspace and stream replay it with a single graph launch, other pointers
+ * re-capture.  Returns the first failing domain's status. */
+int poisson_batch_solve(poisson_batch* batch, const void* const* S, void* const* p,
+                        void* workspace, void* stream, poisson_info* info);
+int poisson_batch_destroy(poisson_batch* batch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POISSON_GB300_H */

@@ -1,0 +1,610 @@
+// C ABI of the direct FFT pressure solver: plan construction (twiddles,
+// eigenvalue and coefficient tables, workspace layout) and the launch sequence
+// of each call.  Section 2.1: plan once, execute every timestep.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/poisson.h"
+#include "kernels.cuh"
+
+using namespace pgb;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* where) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+  return POISSON_ERR_CUDA;
+}
+#define PGB_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool factor23(int n, int& a, int& b) {
+  a = b = 0;
+  if (n < 1) return false;
+  while (n % 2 == 0) { n /= 2; ++a; }
+  while (n % 3 == 0) { n /= 3; ++b; }
+  return n == 1;
+}
+
+// Radix schedule and elements-per-thread for a line of length n = 2^a 3^b.
+bool make_fft_plan(int n, FftPlan& fp) {
+  int a, b;
+  if (n < 2 || !factor23(n, a, b)) return false;
+  std::memset(&fp, 0, sizeof(fp));
+  fp.n = n;
+  int s = 0;
+  for (int i = 0; i < b; ++i) fp.radix[s++] = 3;
+  for (int i = 0; i < a / 3; ++i) fp.radix[s++] = 8;
+  if (a % 3 == 1) fp.radix[s++] = 2;
+  if (a % 3 == 2) fp.radix[s++] = 4;
+  if (s > kMaxStages) return false;
+  fp.nstages = s;
+  if (b == 0) fp.E = n < 16 ? n : 16;
+  else fp.E = a >= 3 ? 24 : (a == 2 ? 12 : (a == 1 ? 6 : 3));
+  return n % fp.E == 0 && fft_e_supported(fp.E);
+}
+
+int signed_k(int k, int n) { return k > n / 2 ? k - n : k; }
+
+}  // namespace
+
+struct poisson_plan {
+  int nx = 0, ny = 0, nz = 0, nxh = 0, P = 0;
+  double dx = 0, dy = 0;
+  int dtype = 0;
+  std::vector<double> dz, rho0;
+  FftPlan fx{}, fy{};
+  int lowk_r2 = 64, max_sweeps = 3, ytile = 0;
+  double tol = 1e-11;
+  Geom g{};
+  Tables tb{};
+  double* dz_d = nullptr;
+  double* rho_d = nullptr;
+  void* tables = nullptr;
+  int2* lowk_d = nullptr;
+  int n_lowk = 0;
+  float2 cx{}, cy{};
+  // workspace layout
+  size_t off_spec = 0, off_stats = 0, off_part = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0, off_r = 0,
+         off_gp = 0, ws_bytes = 0;
+  int xinv_blocks = 1, grho_nb = 1;
+  bool mixed() const { return dtype == POISSON_MIXED; }
+  bool fp64() const { return dtype == POISSON_FP64; }
+  size_t elem() const { return dtype == POISSON_FP32 ? 4 : 8; }
+  size_t csize() const { return dtype == POISSON_FP64 ? 16 : 8; }
+};
+
+struct poisson_batch {
+  int n = 0;
+  int dtype = 0;
+  std::vector<poisson_plan*> plans;
+  std::vector<size_t> off;
+  size_t ws_bytes = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> capS;
+  std::vector<void*> capP;
+  void* capW = nullptr;
+};
+
+namespace {
+
+float2 split_host(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+int build_lowk(poisson_plan* pl) {
+  std::vector<int2> cols;
+  cols.push_back(make_int2(0, 0));
+  const int r2 = pl->mixed() ? pl->lowk_r2 : 0;
+  for (int ky = 0; ky < pl->ny; ++ky)
+    for (int kx = 0; kx < pl->nxh; ++kx) {
+      if (kx == 0 && ky == 0) continue;
+      const int ks = signed_k(ky, pl->ny);
+      if (kx * kx + ks * ks <= r2) cols.push_back(make_int2(kx, ky));
+    }
+  if (pl->lowk_d) cudaFree(pl->lowk_d);
+  pl->lowk_d = nullptr;
+  PGB_CUDA(cudaMalloc(&pl->lowk_d, cols.size() * sizeof(int2)));
+  PGB_CUDA(cudaMemcpy(pl->lowk_d, cols.data(), cols.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  pl->n_lowk = (int)cols.size();
+  return POISSON_OK;
+}
+
+void layout_workspace(poisson_plan* pl) {
+  const long long N = pl->g.N;
+  size_t off = 0;
+  pl->off_spec = off;
+  off = align256(off + (size_t)pl->nz * pl->g.plane * pl->csize());
+  pl->off_stats = off;
+  off = align256(off + sizeof(Stats));
+  pl->off_part = off;
+  off = align256(off + 2 * sizeof(double) * (size_t)(pl->xinv_blocks > 0 ? pl->xinv_blocks : 1));
+  pl->off_lz = off;
+  off = align256(off + sizeof(double2) * (size_t)pl->nz * pl->n_lowk);
+  pl->off_lw = off;
+  off = align256(off + sizeof(double) * (size_t)pl->nz * pl->n_lowk);
+  if (pl->mixed()) {
+    pl->off_p0 = off;
+    off = align256(off + sizeof(float) * (size_t)N);
+    pl->off_q = off;
+    off = align256(off + sizeof(float) * (size_t)N);
+    pl->off_r = off;
+    off = align256(off + sizeof(float) * (size_t)N);
+  }
+  pl->off_gp = off;
+  off = align256(off + 2 * sizeof(double) * (size_t)(pl->nz - 1) * pl->grho_nb);
+  pl->ws_bytes = off;
+}
+
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* poisson_status_string(int s) {
+  switch (s) {
+    case POISSON_OK: return "ok";
+    case POISSON_ERR_INVALID_ARG: return "invalid argument";
+    case POISSON_ERR_UNSUPPORTED: return "unsupported size";
+    case POISSON_ERR_CUDA: return "CUDA error";
+    case POISSON_ERR_WORKSPACE: return "bad workspace";
+    case POISSON_ERR_NOT_CONVERGED: return "refinement did not reach its tolerance";
+    case POISSON_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* poisson_last_error_detail(void) { return g_last_error; }
+
+int poisson_plan_destroy(poisson_plan* pl) {
+  if (!pl) return POISSON_OK;
+  cudaDeviceSynchronize();
+  if (pl->tables) cudaFree(pl->tables);
+  if (pl->lowk_d) cudaFree(pl->lowk_d);
+  delete pl;
+  return POISSON_OK;
+}
+
+int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const double* dz, const double* rho0, int bc,
+                        int dtype, poisson_plan** out) {
+  if (!out) return POISSON_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!dz || !rho0) return POISSON_ERR_INVALID_ARG;
+  if (bc != POISSON_BC_PERIODIC_XY_NEUMANN_Z) return POISSON_ERR_INVALID_ARG;
+  if (dtype != POISSON_FP64 && dtype != POISSON_FP32 && dtype != POISSON_MIXED) return POISSON_ERR_INVALID_ARG;
+  if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy)) return POISSON_ERR_INVALID_ARG;
+  for (int k = 0; k < nz; ++k)
+    if (!(dz[k] > 0) || !(rho0[k] > 0) || !std::isfinite(dz[k]) || !std::isfinite(rho0[k]))
+      return POISSON_ERR_INVALID_ARG;
+  int a, b;
+  if (nx < 4 || ny < 4 || nx > 4096 || ny > 4096 || nx % 2 != 0 || nz < 2 || nz > 512) return POISSON_ERR_UNSUPPORTED;
+  if (!factor23(nx, a, b) || !factor23(ny, a, b)) return POISSON_ERR_UNSUPPORTED;
+
+  poisson_plan* pl = new (std::nothrow) poisson_plan();
+  if (!pl) return POISSON_ERR_CUDA;
+  pl->nx = nx;
+  pl->ny = ny;
+  pl->nz = nz;
+  pl->dx = dx;
+  pl->dy = dy;
+  pl->dtype = dtype;
+  pl->nxh = nx / 2 + 1;
+  const int pad = dtype == POISSON_FP64 ? 8 : 16;  // 128-byte rows
+  pl->P = (pl->nxh + pad - 1) / pad * pad;
+  pl->dz.assign(dz, dz + nz);
+  pl->rho0.assign(rho0, rho0 + nz);
+  if (!make_fft_plan(nx / 2, pl->fx) || !make_fft_plan(ny, pl->fy)) {
+    delete pl;
+    return POISSON_ERR_UNSUPPORTED;
+  }
+  pl->g.nx = nx;
+  pl->g.ny = ny;
+  pl->g.nz = nz;
+  pl->g.nxh = pl->nxh;
+  pl->g.P = pl->P;
+  pl->g.plane = (long long)ny * pl->P;
+  pl->g.N = (long long)nx * ny * nz;
+  pl->g.dx = dx;
+  pl->g.dy = dy;
+  pl->cx = split_host(1.0 / (dx * dx));
+  pl->cy = split_host(1.0 / (dy * dy));
+
+  // ---- host tables
+  const int n = nx / 2;
+  std::vector<double2> twx(n), twr(pl->nxh), twy(ny);
+  for (int m = 0; m < n; ++m) twx[m] = make_double2(std::cos(2 * M_PI * m / n), -std::sin(2 * M_PI * m / n));
+  for (int m = 0; m < pl->nxh; ++m) twr[m] = make_double2(std::cos(2 * M_PI * m / nx), -std::sin(2 * M_PI * m / nx));
+  for (int m = 0; m < ny; ++m) twy[m] = make_double2(std::cos(2 * M_PI * m / ny), -std::sin(2 * M_PI * m / ny));
+  std::vector<double> lx(pl->nxh), ly(ny);
+  for (int k = 0; k < pl->nxh; ++k) {
+    const double sn = std::sin(M_PI * k / nx);
+    lx[k] = -(4.0 / (dx * dx)) * sn * sn;
+  }
+  for (int k = 0; k < ny; ++k) {
+    const double sn = std::sin(M_PI * k / ny);
+    ly[k] = -(4.0 / (dy * dy)) * sn * sn;
+  }
+
+  // ---- one device block for all tables
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const size_t o_a = take(nz * 8), o_c = take(nz * 8), o_W = take(nz * 8), o_af = take(nz * 4), o_cf = take(nz * 4),
+               o_aff = take(nz * 8), o_cff = take(nz * 8), o_acff = take(nz * 8), o_lxd = take(pl->nxh * 8),
+               o_lyd = take(ny * 8), o_lxf = take(pl->nxh * 4), o_lyf = take(ny * 4), o_twxd = take(n * 16),
+               o_twrd = take(pl->nxh * 16), o_twyd = take(ny * 16), o_twxf = take(n * 8), o_twrf = take(pl->nxh * 8),
+               o_twyf = take(ny * 8), o_dz = take(nz * 8), o_rho = take(nz * 8);
+  cudaError_t e = cudaMalloc(&pl->tables, off);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaMalloc(tables)");
+  }
+  char* base = (char*)pl->tables;
+  auto upd = [&](size_t o, const void* src, size_t bytes) {
+    return cudaMemcpy(base + o, src, bytes, cudaMemcpyHostToDevice);
+  };
+  std::vector<float> lxf(pl->nxh), lyf(ny);
+  std::vector<float2> twxf(n), twrf(pl->nxh), twyf(ny);
+  for (int k = 0; k < pl->nxh; ++k) lxf[k] = (float)lx[k];
+  for (int k = 0; k < ny; ++k) lyf[k] = (float)ly[k];
+  for (int m = 0; m < n; ++m) twxf[m] = make_float2((float)twx[m].x, (float)twx[m].y);
+  for (int m = 0; m < pl->nxh; ++m) twrf[m] = make_float2((float)twr[m].x, (float)twr[m].y);
+  for (int m = 0; m < ny; ++m) twyf[m] = make_float2((float)twy[m].x, (float)twy[m].y);
+  cudaError_t ce = cudaSuccess;
+  if (ce == cudaSuccess) ce = upd(o_lxd, lx.data(), pl->nxh * 8);
+  if (ce == cudaSuccess) ce = upd(o_lyd, ly.data(), ny * 8);
+  if (ce == cudaSuccess) ce = upd(o_lxf, lxf.data(), pl->nxh * 4);
+  if (ce == cudaSuccess) ce = upd(o_lyf, lyf.data(), ny * 4);
+  if (ce == cudaSuccess) ce = upd(o_twxd, twx.data(), n * 16);
+  if (ce == cudaSuccess) ce = upd(o_twrd, twr.data(), pl->nxh * 16);
+  if (ce == cudaSuccess) ce = upd(o_twyd, twy.data(), ny * 16);
+  if (ce == cudaSuccess) ce = upd(o_twxf, twxf.data(), n * 8);
+  if (ce == cudaSuccess) ce = upd(o_twrf, twrf.data(), pl->nxh * 8);
+  if (ce == cudaSuccess) ce = upd(o_twyf, twyf.data(), ny * 8);
+  if (ce == cudaSuccess) ce = upd(o_dz, dz, nz * 8);
+  if (ce == cudaSuccess) ce = upd(o_rho, rho0, nz * 8);
+  Tables& tb = pl->tb;
+  tb.a_d = (double*)(base + o_a);
+  tb.c_d = (double*)(base + o_c);
+  tb.W_d = (double*)(base + o_W);
+  tb.a_f = (float*)(base + o_af);
+  tb.c_f = (float*)(base + o_cf);
+  tb.a_ff = (float2*)(base + o_aff);
+  tb.c_ff = (float2*)(base + o_cff);
+  tb.ac_ff = (float2*)(base + o_acff);
+  tb.lamx_d = (double*)(base + o_lxd);
+  tb.lamy_d = (double*)(base + o_lyd);
+  tb.lamx_f = (float*)(base + o_lxf);
+  tb.lamy_f = (float*)(base + o_lyf);
+  tb.twx_d = (double2*)(base + o_twxd);
+  tb.twr_d = (double2*)(base + o_twrd);
+  tb.twy_d = (double2*)(base + o_twyd);
+  tb.twx_f = (float2*)(base + o_twxf);
+  tb.twr_f = (float2*)(base + o_twrf);
+  tb.twy_f = (float2*)(base + o_twyf);
+  pl->dz_d = (double*)(base + o_dz);
+  pl->rho_d = (double*)(base + o_rho);
+  if (ce == cudaSuccess)
+    ce = launch_coefficients(pl->dz_d, pl->rho_d, nz, (double*)tb.a_d, (double*)tb.c_d, (double*)tb.W_d,
+                             (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff, (float2*)tb.ac_ff,
+                             0);
+  if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+  if (ce != cudaSuccess) {
+    int rc = cuda_fail(ce, "plan tables");
+    poisson_plan_destroy(pl);
+    return rc;
+  }
+  int rc = build_lowk(pl);
+  if (rc != POISSON_OK) {
+    poisson_plan_destroy(pl);
+    return rc;
+  }
+  {
+    // x-pass block count (rows per CTA as chosen by the launcher)
+    const int nl = pl->fx.n / pl->fx.E;
+    int rbk = 256 / nl;
+    if (rbk < 1) rbk = 1;
+    while (rbk > 1 && (size_t)rbk * (pl->fx.n + 1) * pl->csize() > 64 * 1024) rbk >>= 1;
+    const long long nrows = (long long)ny * nz;
+    pl->xinv_blocks = (int)((nrows + rbk - 1) / rbk);
+    long long nb = ((long long)nx * ny + 255) / 256;
+    pl->grho_nb = (int)(nb > 1024 ? 1024 : nb);
+  }
+  layout_workspace(pl);
+  *out = pl;
+  return POISSON_OK;
+}
+
+int poisson_plan_workspace_bytes(const poisson_plan* pl, size_t* bytes) {
+  if (!pl || !bytes) return POISSON_ERR_INVALID_ARG;
+  *bytes = pl->ws_bytes;
+  return POISSON_OK;
+}
+
+int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
+  if (!pl) return POISSON_ERR_INVALID_ARG;
+  switch (option) {
+    case POISSON_OPT_LOWK_RADIUS2: {
+      if (!(value >= 0) || value > 1e6) return POISSON_ERR_INVALID_ARG;
+      pl->lowk_r2 = (int)value;
+      int rc = build_lowk(pl);
+      if (rc != POISSON_OK) return rc;
+      layout_workspace(pl);
+      return POISSON_OK;
+    }
+    case POISSON_OPT_MAX_SWEEPS:
+      if (!(value >= 0 && value <= 3)) return POISSON_ERR_INVALID_ARG;
+      pl->max_sweeps = (int)value;
+      return POISSON_OK;
+    case POISSON_OPT_TOLERANCE:
+      if (!(value > 0 && value < 1)) return POISSON_ERR_INVALID_ARG;
+      pl->tol = value;
+      return POISSON_OK;
+    case POISSON_OPT_Y_TILE:
+      if (!(value >= 0 && value <= 64)) return POISSON_ERR_INVALID_ARG;
+      pl->ytile = (int)value;
+      return POISSON_OK;
+    default:
+      return POISSON_ERR_INVALID_ARG;
+  }
+}
+
+int poisson_plan_set_rho0(poisson_plan* pl, const double* rho0_dev, void* stream) {
+  if (!pl || !rho0_dev) return POISSON_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  PGB_CUDA(cudaMemcpyAsync(pl->rho_d, rho0_dev, sizeof(double) * pl->nz, cudaMemcpyDeviceToDevice, st));
+  const Tables& tb = pl->tb;
+  PGB_CUDA(launch_coefficients(pl->dz_d, pl->rho_d, pl->nz, (double*)tb.a_d, (double*)tb.c_d, (double*)tb.W_d,
+                               (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff,
+                               (float2*)tb.ac_ff, st));
+  return POISSON_OK;
+}
+
+static int check_ws(const poisson_plan* pl, void* ws) {
+  if (!ws) return POISSON_ERR_WORKSPACE;
+  if (((uintptr_t)ws & 255) != 0) return POISSON_ERR_WORKSPACE;
+  (void)pl;
+  return POISSON_OK;
+}
+
+// Forward transform -> column solve -> inverse transform of one field.
+static cudaError_t run_pipeline(poisson_plan* pl, const void* in, int in_double, char* ws, cudaStream_t st,
+                                int adjoint, const int* done) {
+  const bool t_double = pl->fp64();
+  void* spec = ws + pl->off_spec;
+  Stats* stats = (Stats*)(ws + pl->off_stats);
+  cudaError_t e = launch_xfwd(in_double, t_double, in, spec, pl->g, pl->fx, pl->tb, done, st);
+  if (e != cudaSuccess) return e;
+  e = launch_yfft(t_double, -1, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, st);
+  if (e != cudaSuccess) return e;
+  ThomasArgs A{};
+  A.spec = spec;
+  A.t_is_double = t_double;
+  A.adjoint = adjoint;
+  A.scale = 1.0 / ((double)pl->nx * pl->ny);
+  A.lowk_r2 = pl->mixed() ? pl->lowk_r2 : 0;
+  A.lowk_double = pl->mixed() || t_double;
+  A.lowk_cols = pl->lowk_d;
+  A.n_lowk = pl->n_lowk;
+  A.lowk_z = (double2*)(ws + pl->off_lz);
+  A.lowk_w = (double*)(ws + pl->off_lw);
+  A.stats = stats;
+  A.done = done;
+  e = launch_thomas(A, pl->g, pl->tb, st);
+  if (e != cudaSuccess) return e;
+  return launch_yfft(t_double, +1, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, st);
+}
+
+static int fill_info(poisson_plan* pl, char* ws, cudaStream_t st, poisson_info* info) {
+  Stats s{};
+  PGB_CUDA(cudaMemcpyAsync(&s, ws + pl->off_stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+  PGB_CUDA(cudaStreamSynchronize(st));
+  std::memset(info, 0, sizeof(*info));
+  info->removed_weighted_mean = s.mu_w;
+  if (s.err & ERR_WAIT_TIMEOUT) return POISSON_ERR_TIMEOUT;
+  if (!pl->mixed()) {
+    info->converged = 1;
+    info->sweeps = 0;
+    info->rel_update[0] = 1.0;
+    info->error_estimate = -1.0;
+    return POISSON_OK;
+  }
+  info->sweeps = s.sweeps;
+  info->converged = s.converged;
+  for (int i = 0; i < 4; ++i) info->rel_update[i] = s.rel_update[i];
+  info->error_estimate = s.err_est;
+  return s.converged ? POISSON_OK : POISSON_ERR_NOT_CONVERGED;
+}
+
+int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, void* stream, poisson_info* info) {
+  if (!pl || !S || !p) return POISSON_ERR_INVALID_ARG;
+  int rc = check_ws(pl, workspace);
+  if (rc != POISSON_OK) return rc;
+  const size_t fbytes = (size_t)pl->g.N * pl->elem();
+  if (ranges_overlap(S, fbytes, p, fbytes)) return POISSON_ERR_INVALID_ARG;
+  if (ranges_overlap(S, fbytes, workspace, pl->ws_bytes) || ranges_overlap(p, fbytes, workspace, pl->ws_bytes))
+    return POISSON_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  Stats* stats = (Stats*)(ws + pl->off_stats);
+  PGB_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), st));
+  const bool t_double = pl->fp64();
+  XinvExtra ex{};
+  ex.partials = (double*)(ws + pl->off_part);
+  if (!pl->mixed()) {
+    PGB_CUDA(run_pipeline(pl, S, t_double, ws, st, 0, nullptr));
+    PGB_CUDA(launch_xinv(t_double, t_double, XINV_PLAIN, ws + pl->off_spec, p, pl->g, pl->fx, pl->tb, ex, nullptr,
+                         st));
+  } else {
+    const int* done = &stats->done;
+    float* p0 = (float*)(ws + pl->off_p0);
+    float* q = (float*)(ws + pl->off_q);
+    float* r = (float*)(ws + pl->off_r);
+    int nb = 0;
+    // first solve: double source, float transforms, double low-|k| columns
+    PGB_CUDA(run_pipeline(pl, S, 1, ws, st, 0, nullptr));
+    ex.p0 = p0;
+    ex.p_out = pl->max_sweeps == 0 ? (double*)p : nullptr;
+    PGB_CUDA(launch_xinv(0, 0, XINV_P0, ws + pl->off_spec, p0, pl->g, pl->fx, pl->tb, ex, &nb, st));
+    PGB_CUDA(launch_control(stats, ex.partials, nb, 0, pl->max_sweeps, pl->tol, st));
+    for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
+      PGB_CUDA(launch_residual_ff((const double*)S, p0, sweep > 1 ? q : nullptr, r, pl->g, pl->tb, pl->cx, pl->cy,
+                                  done, st));
+      PGB_CUDA(run_pipeline(pl, r, 0, ws, st, 0, done));
+      XinvExtra eu = ex;
+      eu.p0 = p0;
+      eu.q = q;
+      eu.q_valid = sweep > 1;
+      eu.p_out = (double*)p;
+      eu.done = done;
+      PGB_CUDA(launch_xinv(0, 0, XINV_UPDATE, ws + pl->off_spec, nullptr, pl->g, pl->fx, pl->tb, eu, &nb, st));
+      PGB_CUDA(launch_control(stats, ex.partials, nb, sweep, pl->max_sweeps, pl->tol, st));
+    }
+  }
+  if (info) return fill_info(pl, ws, st, info);
+  return POISSON_OK;
+}
+
+int poisson_solve_adjoint(poisson_plan* pl, const void* gp, const void* p, void* gS, double* grho, void* workspace,
+                          void* stream) {
+  if (!pl || !gp || !gS) return POISSON_ERR_INVALID_ARG;
+  if (grho && !p) return POISSON_ERR_INVALID_ARG;
+  int rc = check_ws(pl, workspace);
+  if (rc != POISSON_OK) return rc;
+  const size_t fbytes = (size_t)pl->g.N * pl->elem();
+  if (ranges_overlap(gp, fbytes, gS, fbytes)) return POISSON_ERR_INVALID_ARG;
+  if (p && grho && ranges_overlap(p, fbytes, gS, fbytes)) return POISSON_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  Stats* stats = (Stats*)(ws + pl->off_stats);
+  PGB_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), st));
+  const bool t_double = pl->fp64();
+  const int io_double = pl->dtype != POISSON_FP32;
+  PGB_CUDA(run_pipeline(pl, gp, io_double, ws, st, 1, nullptr));
+  XinvExtra ex{};
+  PGB_CUDA(launch_xinv(t_double, io_double, XINV_PLAIN, ws + pl->off_spec, gS, pl->g, pl->fx, pl->tb, ex, nullptr, st));
+  if (grho) {
+    const int kind = pl->fp64() ? 0 : (pl->dtype == POISSON_FP32 ? 1 : 2);
+    PGB_CUDA(launch_grho(kind, gS, p, pl->g, pl->tb, pl->dz_d, pl->rho_d, (double*)(ws + pl->off_gp), pl->grho_nb,
+                         grho, st));
+  }
+  return POISSON_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solve: per-domain plans; the launch sequence of all domains is
+// captured once into a CUDA graph and replayed with one graph launch.
+// ---------------------------------------------------------------------------
+int poisson_batch_destroy(poisson_batch* b) {
+  if (!b) return POISSON_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (auto* p : b->plans) poisson_plan_destroy(p);
+  delete b;
+  return POISSON_OK;
+}
+
+int poisson_batch_create(int n, const int* nx, const int* ny, const int* nz, const double* dx, const double* dy,
+                         const double* const* dz, const double* const* rho0, int dtype, poisson_batch** out) {
+  if (!out) return POISSON_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n <= 0 || !nx || !ny || !nz || !dx || !dy || !dz || !rho0) return POISSON_ERR_INVALID_ARG;
+  if (dtype != POISSON_FP32 && dtype != POISSON_MIXED) return POISSON_ERR_INVALID_ARG;
+  poisson_batch* b = new (std::nothrow) poisson_batch();
+  if (!b) return POISSON_ERR_CUDA;
+  b->n = n;
+  b->dtype = dtype;
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    poisson_plan* pl = nullptr;
+    int rc = poisson_plan_create(nx[i], ny[i], nz[i], dx[i], dy[i], dz[i], rho0[i], POISSON_BC_PERIODIC_XY_NEUMANN_Z,
+                                 dtype, &pl);
+    if (rc != POISSON_OK) {
+      poisson_batch_destroy(b);
+      return rc;
+    }
+    b->plans.push_back(pl);
+    b->off.push_back(off);
+    off = align256(off + pl->ws_bytes);
+  }
+  b->ws_bytes = off;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    poisson_batch_destroy(b);
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  *out = b;
+  return POISSON_OK;
+}
+
+int poisson_batch_workspace_bytes(const poisson_batch* b, size_t* bytes) {
+  if (!b || !bytes) return POISSON_ERR_INVALID_ARG;
+  *bytes = b->ws_bytes;
+  return POISSON_OK;
+}
+
+int poisson_batch_solve(poisson_batch* b, const void* const* S, void* const* p, void* workspace, void* stream,
+                        poisson_info* info) {
+  if (!b || !S || !p) return POISSON_ERR_INVALID_ARG;
+  if (!workspace || ((uintptr_t)workspace & 255)) return POISSON_ERR_WORKSPACE;
+  for (int i = 0; i < b->n; ++i)
+    if (!S[i] || !p[i]) return POISSON_ERR_INVALID_ARG;
+  bool same = b->exec && b->capW == workspace;
+  if (same)
+    for (int i = 0; i < b->n; ++i) same = same && b->capS[i] == S[i] && b->capP[i] == p[i];
+  if (!same) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    PGB_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+    int rc = POISSON_OK;
+    for (int i = 0; i < b->n && rc == POISSON_OK; ++i)
+      rc = poisson_solve(b->plans[i], S[i], p[i], (char*)workspace + b->off[i], b->cap, nullptr);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc != POISSON_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    b->capS.assign(S, S + b->n);
+    b->capP.assign(p, p + b->n);
+    b->capW = workspace;
+  }
+  PGB_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  if (info) {
+    int first = POISSON_OK;
+    for (int i = 0; i < b->n; ++i) {
+      int rc = fill_info(b->plans[i], (char*)workspace + b->off[i], (cudaStream_t)stream, &info[i]);
+      if (rc != POISSON_OK && first == POISSON_OK) first = rc;
+    }
+    return first;
+  }
+  return POISSON_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Internal launch interface between the C ABI (api.cu) and the kernel units.
+#pragma once
+#include <cuda_runtime.h>
+#include "fft_engine.cuh"
+
+namespace pgb {
+
+// Per-solve device statistics and control flags (zeroed at the start of a solve).
+struct Stats {
+  double sq_delta[4];     // ||delta_n||^2 of pass n (pass 0 = first solve, delta_0 = p0)
+  double sq_p[4];         // ||p||^2 after pass n
+  double rel_update[4];
+  double err_est;         // estimated relative error after the last executed pass
+  double mu_w;            // weighted mean removed from the source (first solve)
+  int done;               // later passes become no-ops once set
+  int sweeps;
+  int converged;
+  unsigned err;           // ERR_* bits
+};
+
+// Device-resident tables owned by a plan.
+struct Tables {
+  // vertical coefficients, level k
+  const double* a_d; const double* c_d; const double* W_d;
+  const float* a_f; const float* c_f;
+  // double-float splits for the residual: a, c, a+c (hi, lo)
+  const float2* a_ff; const float2* c_ff; const float2* ac_ff;
+  // horizontal eigenvalues: lamx[kx], kx < nxh; lamy[ky], ky < ny
+  const double* lamx_d; const double* lamy_d;
+  const float* lamx_f; const float* lamy_f;
+  // twiddles exp(-2 pi i m / n): x line (n = nx/2), R2C post (m = 0..nx/2 over nx), y line
+  const double2* twx_d; const double2* twr_d; const double2* twy_d;
+  const float2* twx_f; const float2* twr_f; const float2* twy_f;
+};
+
+struct Geom {
+  int nx, ny, nz, nxh, P;      // P: spectrum row pitch (complex elements), >= nxh
+  long long plane;             // ny * P
+  long long N;                 // nx * ny * nz
+  double dx, dy;
+};
+
+// Output handling of the inverse x-pass.
+enum XinvMode : int {
+  XINV_PLAIN = 0,   // out[TO] = result
+  XINV_P0 = 1,      // mixed first solve: p0 (float) + partial sums of p0^2; optional double output
+  XINV_UPDATE = 2   // mixed sweep: q += delta, p(double) = p0 + q, partial sums of delta^2, p^2
+};
+
+struct XinvExtra {
+  float* p0;            // P0: written; UPDATE: read
+  float* q;             // UPDATE: read (unless first sweep) and written
+  int q_valid;          // UPDATE: q holds a previous correction
+  double* p_out;        // P0 (when final) / UPDATE: double output field
+  double* partials;     // per-block partial sums (2 per block)
+  const int* done;      // skip when set (nullable)
+};
+
+// ---- launchers (stream-ordered, return cudaError_t of the launch) ----
+cudaError_t launch_xfwd(int ti_is_double, int t_is_double, const void* in, void* spec, const Geom& g,
+                        const FftPlan& fx, const Tables& tb, const int* done, cudaStream_t st);
+cudaError_t launch_yfft(int t_is_double, int sign, void* spec, const Geom& g, const FftPlan& fy,
+                        const Tables& tb, int tile, const int* done, cudaStream_t st);
+cudaError_t launch_xinv(int t_is_double, int to_is_double, int mode, const void* spec, void* out,
+                        const Geom& g, const FftPlan& fx, const Tables& tb, const XinvExtra& ex,
+                        int* nblocks_out, cudaStream_t st);
+
+struct ThomasArgs {
+  void* spec;
+  int t_is_double;        // storage/compute precision of the main kernel
+  int adjoint;
+  double scale;           // 1/(nx ny)
+  int lowk_r2;            // columns with kx^2+ky'^2 <= lowk_r2 go to the low-k kernel (>= 0)
+  int lowk_double;        // low-k kernel computes in double
+  const int2* lowk_cols;  // (kx, ky) list, (0,0) first
+  int n_lowk;
+  double2* lowk_z;        // scratch nz * n_lowk
+  double* lowk_w;         // scratch nz * n_lowk
+  Stats* stats;
+  const int* done;
+};
+cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
+
+cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
+                               const Tables& tb, float2 cx, float2 cy, const int* done, cudaStream_t st);
+cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
+                           double tol, cudaStream_t st);
+cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
+                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff,
+                                float2* ac_ff, cudaStream_t st);
+cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math*/, const void* g, const void* p, const Geom& g_, const Tables& tb,
+                        const double* dz, const double* rho0, double* partials, int nparts_max,
+                        double* grho, cudaStream_t st);
+
+// Elements per thread the FFT kernels are instantiated for.
+bool fft_e_supported(int E);
+
+}  // namespace pgb

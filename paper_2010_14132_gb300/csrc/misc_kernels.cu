@@ -1,0 +1,331 @@
+// Residual, refinement control, coefficient tables and rho0-gradient reductions.
+#include "kernels.cuh"
+
+namespace pgb {
+
+// ---------------------------------------------------------------------------
+// Vertical coefficient tables (one thread per level, FP64; nz values only).
+//   W_k = rho_k dz_k, a_k = rho_{k-1/2}/(W_k h_{k-1/2}), c_k = rho_{k+1/2}/(W_k h_{k+1/2}),
+//   h_{k+1/2} = (dz_k + dz_{k+1})/2, rho_{k+1/2} = (rho_k + rho_{k+1})/2; a_0 = c_{nz-1} = 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 split_ff(double x) {
+  const float h = __double2float_rn(x);
+  const float l = __double2float_rn(x - (double)h);
+  return make_float2(h, l);
+}
+
+__global__ void k_coefficients(const double* __restrict__ dz, const double* __restrict__ rho, int nz,
+                               double* a_d, double* c_d, double* W_d, float* a_f, float* c_f, float2* a_ff,
+                               float2* c_ff, float2* ac_ff) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nz; k += blockDim.x * gridDim.x) {
+    const double W = rho[k] * dz[k];
+    const double up = (k + 1 < nz) ? (0.5 * (rho[k] + rho[k + 1])) / (0.5 * (dz[k] + dz[k + 1])) : 0.0;
+    const double dn = (k > 0) ? (0.5 * (rho[k - 1] + rho[k])) / (0.5 * (dz[k - 1] + dz[k])) : 0.0;
+    const double a = dn / W, c = up / W;
+    a_d[k] = a;
+    c_d[k] = c;
+    W_d[k] = W;
+    a_f[k] = __double2float_rn(a);
+    c_f[k] = __double2float_rn(c);
+    a_ff[k] = split_ff(a);
+    c_ff[k] = split_ff(c);
+    ac_ff[k] = split_ff(a + c);
+  }
+}
+
+cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
+                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff,
+                                float2* ac_ff, cudaStream_t st) {
+  k_coefficients<<<(nz + 127) / 128, 128, 0, st>>>(dz, rho0, nz, a_d, c_d, W_d, a_f, c_f, a_ff, c_ff, ac_ff);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Residual r = S - L (p0 + q) in double-float arithmetic (mixed path).
+//
+// The refinement needs r to about 2^-44 of |L||p| (the 7-point sum cancels by
+// orders of magnitude for the smooth, large pressure field), which FP32 alone
+// cannot give and FP64 instructions make ALU bound on GB300.  Every product and
+// sum of p0 (exact floats) with the double-float coefficients is formed with
+// error-free transformations; the small correction q enters in plain FP32.
+// S (double) is split into hi + lo floats with integer operations.
+// One thread per point; neighbours come through L1/L2.
+// ---------------------------------------------------------------------------
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return FF{s, e + a.l + b.l};
+}
+
+template <bool HAS_Q>
+__global__ void __launch_bounds__(256) k_residual_ff(const double* __restrict__ S, const float* __restrict__ p0,
+                                                     const float* __restrict__ q, float* __restrict__ r, Geom g,
+                                                     const float2* __restrict__ a_ff, const float2* __restrict__ c_ff,
+                                                     const float2* __restrict__ ac_ff, float2 cx, float2 cy,
+                                                     const int* __restrict__ done) {
+  if (done && *done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  if (i >= g.nx) return;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long long pl = (long long)nx * ny;
+  const long long row = ((long long)k * ny + j) * nx;
+  const long long idx = row + i;
+  const int ie = (i + 1 == nx) ? 0 : i + 1, iw = (i == 0) ? nx - 1 : i - 1;
+  const long long rn = ((long long)k * ny + ((j + 1 == ny) ? 0 : j + 1)) * nx;
+  const long long rs = ((long long)k * ny + ((j == 0) ? ny - 1 : j - 1)) * nx;
+  const float pc = p0[idx];
+  const float pe = p0[row + ie], pw = p0[row + iw], pn = p0[rn + i], ps = p0[rs + i];
+  const bool has_dn = k > 0, has_up = k + 1 < nz;
+  const float pd = has_dn ? p0[idx - pl] : pc;
+  const float pu = has_up ? p0[idx + pl] : pc;
+  float qc = 0, qe = 0, qw = 0, qn = 0, qs = 0, qd = 0, qu = 0;
+  if (HAS_Q) {
+    qc = q[idx];
+    qe = q[row + ie];
+    qw = q[row + iw];
+    qn = q[rn + i];
+    qs = q[rs + i];
+    qd = has_dn ? q[idx - pl] : qc;
+    qu = has_up ? q[idx + pl] : qc;
+  }
+  // x: cx (pe + pw - 2 pc)
+  float s1, e1, s2, e2;
+  two_sum(pe, pw, s1, e1);
+  two_sum(s1, -2.f * pc, s2, e2);
+  float dl = e1 + e2 + (qe + qw - 2.f * qc);
+  FF tx;
+  two_prod(cx.x, s2, tx.h, tx.l);
+  tx.l = __fmaf_rn(cx.x, dl, __fmaf_rn(cx.y, s2, tx.l));
+  // y: cy (pn + ps - 2 pc)
+  two_sum(pn, ps, s1, e1);
+  two_sum(s1, -2.f * pc, s2, e2);
+  dl = e1 + e2 + (qn + qs - 2.f * qc);
+  FF ty;
+  two_prod(cy.x, s2, ty.h, ty.l);
+  ty.l = __fmaf_rn(cy.x, dl, __fmaf_rn(cy.y, s2, ty.l));
+  // z: a pd + c pu - (a + c) pc   (a = 0 at the bottom, c = 0 at the top)
+  const float2 A = a_ff[k], Cc = c_ff[k], AC = ac_ff[k];
+  float p1, l1, p2, l2, p3, l3;
+  two_prod(A.x, pd, p1, l1);
+  two_prod(Cc.x, pu, p2, l2);
+  two_prod(AC.x, pc, p3, l3);
+  two_sum(p1, p2, s1, e1);
+  two_sum(s1, -p3, s2, e2);
+  float zl = (l1 + l2 - l3) + (e1 + e2);
+  zl = __fmaf_rn(A.y, pd, zl);
+  zl = __fmaf_rn(Cc.y, pu, zl);
+  zl = __fmaf_rn(-AC.y, pc, zl);
+  zl = __fmaf_rn(A.x, qd, zl);
+  zl = __fmaf_rn(Cc.x, qu, zl);
+  zl = __fmaf_rn(-AC.x, qc, zl);
+  FF tz{s2, zl};
+  FF Lp = ff_add(ff_add(tx, ty), tz);
+  float sh, sl;
+  d2ff_int(S[idx], sh, sl);
+  float rh, rl;
+  two_sum(sh, -Lp.h, rh, rl);
+  r[idx] = rh + (rl + (sl - Lp.l));
+}
+
+cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
+                               const Tables& tb, float2 cx, float2 cy, const int* done, cudaStream_t st) {
+  const dim3 block(256);
+  const dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
+  if (q)
+    k_residual_ff<true><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, tb.ac_ff, cx, cy, done);
+  else
+    k_residual_ff<false><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, tb.ac_ff, cx, cy, done);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Refinement control (one block): sums the x-pass partials in a fixed order,
+// records ||delta_n||/||p|| and the error estimate, and sets the done flag.
+// Stopping rule: after sweep n >= 1 the remaining error is estimated as
+// rho_n * ||delta_n||/||p|| with the observed contraction rho_n =
+// (||delta_n||/||p||) / (||delta_{n-1}||/||p||) (||delta_0|| = ||p0||).
+// ---------------------------------------------------------------------------
+__global__ void k_control(Stats* st, const double* __restrict__ partials, int nblocks, int pass, int max_sweeps,
+                          double tol) {
+  __shared__ double s0[256], s1[256];
+  const int t = threadIdx.x;
+  double a = 0, b = 0;
+  for (int i = t; i < nblocks; i += blockDim.x) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  s0[t] = a;
+  s1[t] = b;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (t < h) {
+      s0[t] += s0[t + h];
+      s1[t] += s1[t + h];
+    }
+    __syncthreads();
+  }
+  if (t != 0) return;
+  if (st->done) return;
+  const double sd = (pass == 0) ? s1[0] : s0[0];
+  const double sp = s1[0];
+  st->sq_delta[pass] = sd;
+  st->sq_p[pass] = sp;
+  const double rel = (sp > 0) ? sqrt(sd / sp) : 0.0;
+  st->rel_update[pass] = (pass == 0) ? 1.0 : rel;
+  st->sweeps = pass;
+  if (pass == 0) {
+    st->err_est = -1.0;
+    if (max_sweeps == 0) {
+      st->done = 1;
+      st->converged = 1;
+    }
+    return;
+  }
+  const double prev = st->rel_update[pass - 1];
+  const double est = (prev > 0) ? rel * (rel / prev) : rel;
+  st->err_est = est;
+  if (est <= tol || rel == 0.0) {
+    st->done = 1;
+    st->converged = 1;
+  } else if (pass >= max_sweeps) {
+    st->done = 1;
+    st->converged = 0;
+  }
+}
+
+cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps, double tol,
+                           cudaStream_t st) {
+  k_control<<<1, 256, 0, st>>>(st_dev, partials, nblocks, pass, max_sweeps, tol);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// rho0 gradient.  With g = G^T (dL/dp) and D_f = p_{k+1} - p_k on face f = k+1/2:
+//   Lo_f = sum_ij g_k D_f,  Up_f = sum_ij g_{k+1} D_f,
+//   dL/drho_m = -sum_k (da_k/drho_m * Ma_k + dc_k/drho_m * Mc_k),
+//   Mc_k = Lo_k,  Ma_k = -Up_{k-1}.
+// Partials per (face, block) are reduced in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+template <typename TIO>
+__global__ void __launch_bounds__(256) k_grho_partial(const TIO* __restrict__ gS, const TIO* __restrict__ p,
+                                                      long long plane, double* __restrict__ partials) {
+  __shared__ double s0[256], s1[256];
+  const int f = blockIdx.y;
+  const TIO* g0 = gS + f * plane;
+  const TIO* g1 = g0 + plane;
+  const TIO* p0 = p + f * plane;
+  const TIO* p1 = p0 + plane;
+  TIO lo = 0, up = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (long long)gridDim.x * blockDim.x) {
+    const TIO d = p1[i] - p0[i];
+    lo += g0[i] * d;
+    up += g1[i] * d;
+  }
+  const int t = threadIdx.x;
+  s0[t] = (double)lo;
+  s1[t] = (double)up;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h) {
+      s0[t] += s0[t + h];
+      s1[t] += s1[t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    partials[2 * ((long long)f * gridDim.x + blockIdx.x)] = s0[0];
+    partials[2 * ((long long)f * gridDim.x + blockIdx.x) + 1] = s1[0];
+  }
+}
+
+// Mixed dtype: double fields converted with integer operations, float products.
+__global__ void __launch_bounds__(256) k_grho_partial_mixed(const double* __restrict__ gS,
+                                                            const double* __restrict__ p, long long plane,
+                                                            double* __restrict__ partials) {
+  __shared__ double s0[256], s1[256];
+  const int f = blockIdx.y;
+  const double* g0 = gS + f * plane;
+  const double* g1 = g0 + plane;
+  const double* p0 = p + f * plane;
+  const double* p1 = p0 + plane;
+  float lo = 0, up = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (long long)gridDim.x * blockDim.x) {
+    const float d = d2f_int(p1[i]) - d2f_int(p0[i]);
+    lo += d2f_int(g0[i]) * d;
+    up += d2f_int(g1[i]) * d;
+  }
+  const int t = threadIdx.x;
+  s0[t] = (double)lo;
+  s1[t] = (double)up;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h) {
+      s0[t] += s0[t + h];
+      s1[t] += s1[t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    partials[2 * ((long long)f * gridDim.x + blockIdx.x)] = s0[0];
+    partials[2 * ((long long)f * gridDim.x + blockIdx.x) + 1] = s1[0];
+  }
+}
+
+// One thread per level m; each sums the partials of faces m-1 and m in fixed order.
+__global__ void k_grho_final(const double* __restrict__ partials, int nb, int nz, const double* __restrict__ dz,
+                             const double* __restrict__ rho, const double* __restrict__ a,
+                             const double* __restrict__ c, const double* __restrict__ W, double* __restrict__ grho) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nz) return;
+  auto face = [&](int f, int which) {
+    double s = 0;
+    for (int b = 0; b < nb; ++b) s += partials[2 * ((long long)f * nb + b) + which];
+    return s;
+  };
+  auto hf = [&](int f) { return 0.5 * (dz[f] + dz[f + 1]); };
+  double acc = 0;
+  // a-terms: k = m (face m-1) and k = m+1 (face m); Ma_k = -Up_{k-1}
+  if (m >= 1) {
+    const double Ma = -face(m - 1, 1);
+    acc += (0.5 / (W[m] * hf(m - 1)) - a[m] / rho[m]) * Ma;
+  }
+  if (m + 1 <= nz - 1) {
+    const double Ma = -face(m, 1);
+    acc += (0.5 / (W[m + 1] * hf(m))) * Ma;
+  }
+  // c-terms: k = m (face m) and k = m-1 (face m-1); Mc_k = Lo_k
+  if (m <= nz - 2) {
+    const double Mc = face(m, 0);
+    acc += (0.5 / (W[m] * hf(m)) - c[m] / rho[m]) * Mc;
+  }
+  if (m >= 1) {
+    const double Mc = face(m - 1, 0);
+    acc += (0.5 / (W[m - 1] * hf(m - 1))) * Mc;
+  }
+  grho[m] = -acc;
+}
+
+cudaError_t launch_grho(int kind, const void* g, const void* p, const Geom& g_, const Tables& tb, const double* dz,
+                        const double* rho0, double* partials, int nparts_max, double* grho, cudaStream_t st) {
+  const long long plane = (long long)g_.nx * g_.ny;
+  int nb = (int)((plane + 255) / 256);
+  if (nb > nparts_max) nb = nparts_max;
+  if (nb < 1) nb = 1;
+  const dim3 grid(nb, g_.nz - 1);
+  if (kind == 0)
+    k_grho_partial<double><<<grid, 256, 0, st>>>((const double*)g, (const double*)p, plane, partials);
+  else if (kind == 1)
+    k_grho_partial<float><<<grid, 256, 0, st>>>((const float*)g, (const float*)p, plane, partials);
+  else
+    k_grho_partial_mixed<<<grid, 256, 0, st>>>((const double*)g, (const double*)p, plane, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_grho_final<<<(g_.nz + 127) / 128, 128, 0, st>>>(partials, nb, g_.nz, dz, rho0, tb.a_d, tb.c_d, tb.W_d, grho);
+  return cudaGetLastError();
+}
+
+}  // namespace pgb

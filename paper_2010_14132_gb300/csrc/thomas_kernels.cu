@@ -1,0 +1,339 @@
+// Vertical column solves of the direct method (Section 2.1: after the forward
+// transform each (kx, ky) wavenumber gives an independent tridiagonal system
+// along z, solved up and down the column).
+//
+// Column matrix T = L_z + (lambda_x + lambda_y) I.  With M = -T (an M-matrix:
+// diagonal a_k + c_k + s, off-diagonals -a_k, -c_k, row sums s = -(lambda_x +
+// lambda_y) >= 0) the LU pivots are formed without subtraction:
+//     g_0 = s,  u_k = g_k + c_k,  g_k = s + a_k g_{k-1} / u_{k-1},
+// (g_k is the row sum of the reduced row k), so every pivot is relatively
+// accurate however close s is to 0.  For s = 0 (the (0,0) column) g vanishes
+// identically and the last pivot is exactly 0, the singular mode.
+//   forward solve   M x = b:  y_k = b_k + (a_k/u_{k-1}) y_{k-1};  x_k = y_k/u_k + (c_k/u_k) x_{k+1}
+//   adjoint solve M^T x = b:  v_k = (b_k + c_{k-1} v_{k-1})/u_k;   x_k = v_k + (a_{k+1}/u_k) x_{k+1}
+// The spectrum is scaled by 1/(nx ny) here, which makes the inverse transforms
+// unnormalised.
+#include "kernels.cuh"
+
+namespace pgb {
+
+// ---------------------------------------------------------------------------
+// mbarrier / bulk-copy primitives (sm_90+ PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after max_iter polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long max_iter) {
+  for (long long i = 0; i < max_iter; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+constexpr long long kWaitPolls = 1LL << 22;
+
+template <typename T> __device__ __forceinline__ T rcp(T u);
+template <> __device__ __forceinline__ float rcp<float>(float u) { return __frcp_rn(u); }
+template <> __device__ __forceinline__ double rcp<double>(double u) { return 1.0 / u; }
+
+__device__ __forceinline__ int signed_ky(int ky, int ny) { return ky > ny / 2 ? ky - ny : ky; }
+
+// ---------------------------------------------------------------------------
+// Main column kernel: one thread per column, a tile of TC consecutive columns
+// (flattened (ky, kx) index with pitch P) staged for all nz levels.
+// Shared layout: tile [nz][TC] complex, wv [nz][TC] real, one mbarrier.
+// ---------------------------------------------------------------------------
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(128) k_thomas(typename CT<T>::t* __restrict__ spec, Geom g,
+                                                const T* __restrict__ a, const T* __restrict__ c,
+                                                const T* __restrict__ lamx, const T* __restrict__ lamy, T scale,
+                                                int lowk_r2, const int* __restrict__ done, Stats* stats) {
+  using C = typename CT<T>::t;
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int TC = blockDim.x, t = threadIdx.x, nz = g.nz;
+  C* tile = reinterpret_cast<C*>(smraw);
+  T* wv = reinterpret_cast<T*>(tile + (size_t)nz * TC);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + (((size_t)nz * TC * (sizeof(C) + sizeof(T)) + 15) & ~(size_t)15));
+
+  const long long ncols = g.plane;
+  const long long c0 = (long long)blockIdx.x * TC;
+  const int tcv = (int)((ncols - c0) < TC ? (ncols - c0) : TC);
+  const unsigned row_bytes = (unsigned)(tcv * sizeof(C));
+  if (t == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (t == 0) {
+    mbar_arrive_expect_tx(bar, row_bytes * (unsigned)nz);
+    for (int k = 0; k < nz; ++k) bulk_g2s(tile + (size_t)k * TC, spec + k * g.plane + c0, row_bytes, bar);
+  }
+  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+    if (t == 0) atomicOr(&stats->err, (unsigned)ERR_WAIT_TIMEOUT);
+    mbar_wait_bounded(bar, 0, kWaitPolls);  // let copies in flight land before the CTA exits
+    return;
+  }
+
+  const long long col = c0 + t;
+  const int ky = (int)(col / g.P), kx = (int)(col - (long long)ky * g.P);
+  const int kys = signed_ky(ky, g.ny);
+  const bool valid = t < tcv && kx < g.nxh && (kx * kx + kys * kys > lowk_r2);
+  if (!valid) return;
+
+  const T s = -(lamx[kx] + lamy[ky]);
+  const T ms = -scale;
+  C* colp = tile + t;
+  T* wp = wv + t;
+  // forward sweep (pivots in level order)
+  T g_prev = s, inv_prev = 0;
+  C y_prev = make_c<T>(0, 0);
+  for (int k = 0; k < nz; ++k) {
+    const C d = colp[(size_t)k * TC];
+    const C b = make_c<T>(ms * d.x, ms * d.y);
+    T gk;
+    C y;
+    if (k == 0) {
+      gk = s;
+    } else {
+      if (!ADJ) {
+        const T f = a[k] * inv_prev;
+        gk = s + f * g_prev;
+      } else {
+        gk = s + a[k] * g_prev * inv_prev;
+      }
+    }
+    const T u = gk + c[k];
+    const T inv = rcp(u);
+    if (!ADJ) {
+      if (k == 0) {
+        y = b;
+      } else {
+        const T f = a[k] * inv_prev;
+        y = make_c<T>(b.x + f * y_prev.x, b.y + f * y_prev.y);
+      }
+      colp[(size_t)k * TC] = make_c<T>(y.x * inv, y.y * inv);
+      wp[(size_t)k * TC] = c[k] * inv;
+    } else {
+      if (k == 0) {
+        y = make_c<T>(b.x * inv, b.y * inv);
+      } else {
+        const T cm = c[k - 1];
+        y = make_c<T>((b.x + cm * y_prev.x) * inv, (b.y + cm * y_prev.y) * inv);
+      }
+      colp[(size_t)k * TC] = y;
+      wp[(size_t)k * TC] = (k + 1 < nz) ? a[k + 1] * inv : (T)0;
+    }
+    g_prev = gk;
+    inv_prev = inv;
+    y_prev = y;
+  }
+  // back substitution, written straight to HBM (coalesced across the tile)
+  C x = colp[(size_t)(nz - 1) * TC];
+  C* out = spec + col;
+  out[(long long)(nz - 1) * g.plane] = x;
+  for (int k = nz - 2; k >= 0; --k) {
+    const C z = colp[(size_t)k * TC];
+    const T w = wp[(size_t)k * TC];
+    x = make_c<T>(z.x + w * x.x, z.y + w * x.y);
+    out[(long long)k * g.plane] = x;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Low-|k| and singular columns: one thread per listed column, compute type TCm
+// (double in the mixed path), scratch in global memory.  The (0,0) column:
+//   forward: remove the W-weighted mean of the right-hand side (compatibility),
+//            pin x_{nz-1} = 0, back-substitute, shift to zero mean;
+//   adjoint: remove the plain mean of the right-hand side, pin v_{nz-1} = 0,
+//            back-substitute, remove the W direction (x -= W sum(x)/sum(W)).
+// ---------------------------------------------------------------------------
+template <typename TS, typename TCm, bool ADJ>
+__global__ void k_thomas_lowk(typename CT<TS>::t* __restrict__ spec, Geom g, const double* __restrict__ a,
+                              const double* __restrict__ c, const double* __restrict__ W,
+                              const double* __restrict__ lamx, const double* __restrict__ lamy, double scale,
+                              const int2* __restrict__ cols, int ncols, double2* __restrict__ zs,
+                              double* __restrict__ ws, Stats* stats, const int* __restrict__ done) {
+  using CS = typename CT<TS>::t;
+  if (done && *done) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncols) return;
+  const int kx = cols[t].x, ky = cols[t].y, nz = g.nz;
+  const bool singular = (kx == 0 && ky == 0);
+  CS* colp = spec + (long long)ky * g.P + kx;
+  double2* z = zs + (size_t)t * nz;
+  double* w = ws + (size_t)t * nz;
+  // right-hand side in compute precision
+  TCm mean_x = 0, mean_y = 0;
+  if (singular) {
+    TCm sw = 0;
+    for (int k = 0; k < nz; ++k) {
+      const CS v = colp[(long long)k * g.plane];
+      const TCm wk = ADJ ? (TCm)1 : (TCm)W[k];
+      mean_x += wk * (TCm)v.x;
+      mean_y += wk * (TCm)v.y;
+      sw += wk;
+    }
+    mean_x /= sw;
+    mean_y /= sw;
+    if (!ADJ && stats) stats->mu_w = (double)mean_x * scale;
+  }
+  const TCm s = singular ? (TCm)0 : -((TCm)lamx[kx] + (TCm)lamy[ky]);
+  const TCm ms = -(TCm)scale;
+  TCm g_prev = s, inv_prev = 0, yx = 0, yy = 0;
+  for (int k = 0; k < nz; ++k) {
+    const CS v = colp[(long long)k * g.plane];
+    const TCm bx = ms * ((TCm)v.x - mean_x), by = ms * ((TCm)v.y - mean_y);
+    const TCm gk = (k == 0) ? s : s + (TCm)a[k] * g_prev * inv_prev;
+    const TCm u = gk + (TCm)c[k];
+    const bool last_singular = singular && (k == nz - 1);
+    const TCm inv = last_singular ? (TCm)0 : (TCm)1 / u;
+    if (!ADJ) {
+      TCm nx_ = bx, ny_ = by;
+      if (k > 0) {
+        const TCm f = (TCm)a[k] * inv_prev;
+        nx_ += f * yx;
+        ny_ += f * yy;
+      }
+      yx = nx_;
+      yy = ny_;
+      z[k] = make_double2((double)(yx * inv), (double)(yy * inv));   // pinned 0 at the singular top
+      w[k] = (double)((TCm)c[k] * inv);
+    } else {
+      TCm nx_ = bx, ny_ = by;
+      if (k > 0) {
+        nx_ += (TCm)c[k - 1] * yx;
+        ny_ += (TCm)c[k - 1] * yy;
+      }
+      yx = nx_ * inv;
+      yy = ny_ * inv;
+      z[k] = make_double2((double)yx, (double)yy);
+      w[k] = (k + 1 < nz) ? (double)((TCm)a[k + 1] * inv) : 0.0;
+    }
+    g_prev = gk;
+    inv_prev = inv;
+  }
+  TCm xx = (TCm)z[nz - 1].x, xy = (TCm)z[nz - 1].y;
+  z[nz - 1] = make_double2((double)xx, (double)xy);
+  TCm sumx = xx, sumy = xy;
+  for (int k = nz - 2; k >= 0; --k) {
+    const TCm wk = (TCm)w[k];
+    xx = (TCm)z[k].x + wk * xx;
+    xy = (TCm)z[k].y + wk * xy;
+    z[k] = make_double2((double)xx, (double)xy);
+    sumx += xx;
+    sumy += xy;
+  }
+  TCm shx = 0, shy = 0, sw = 0;
+  if (singular) {
+    if (!ADJ) {
+      shx = sumx / (TCm)nz;
+      shy = sumy / (TCm)nz;
+    } else {
+      for (int k = 0; k < nz; ++k) sw += (TCm)W[k];
+    }
+  }
+  for (int k = 0; k < nz; ++k) {
+    TCm ox = (TCm)z[k].x, oy = (TCm)z[k].y;
+    if (singular) {
+      if (!ADJ) {
+        ox -= shx;
+        oy -= shy;
+      } else {
+        const TCm f = (TCm)W[k] / sw;
+        ox -= f * sumx;
+        oy -= f * sumy;
+      }
+    }
+    CS o;
+    o.x = (TS)ox;
+    o.y = (TS)oy;
+    colp[(long long)k * g.plane] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launcher
+// ---------------------------------------------------------------------------
+static int thomas_tile(int nz, size_t entry_bytes) {
+  // largest TC in {128, 64, 32, 16} whose tile fits about 100 KB (two CTAs per SM)
+  for (int tc = 128; tc >= 16; tc >>= 1)
+    if ((size_t)tc * nz * entry_bytes + 16 <= 100 * 1024) return tc;
+  for (int tc = 32; tc >= 16; tc >>= 1)
+    if ((size_t)tc * nz * entry_bytes + 16 <= 200 * 1024) return tc;
+  return 0;
+}
+
+template <typename T, bool ADJ>
+static cudaError_t thomas_main(const ThomasArgs& A, const Geom& g, const T* a, const T* c, const T* lx,
+                               const T* ly, cudaStream_t st) {
+  using C = typename CT<T>::t;
+  const int tc = thomas_tile(g.nz, sizeof(C) + sizeof(T));
+  if (tc == 0) return cudaErrorInvalidValue;
+  const size_t smem = (((size_t)g.nz * tc * (sizeof(C) + sizeof(T)) + 15) & ~(size_t)15) + 16;
+  const long long nb = (g.plane + tc - 1) / tc;
+  auto kern = k_thomas<T, ADJ>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<(unsigned)nb, tc, smem, st>>>((C*)A.spec, g, a, c, lx, ly, (T)A.scale, A.lowk_r2, A.done, A.stats);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TCm, bool ADJ>
+static cudaError_t thomas_lowk(const ThomasArgs& A, const Geom& g, const Tables& tb, cudaStream_t st) {
+  if (A.n_lowk <= 0) return cudaSuccess;
+  const int threads = 64;
+  const int blocks = (A.n_lowk + threads - 1) / threads;
+  k_thomas_lowk<TS, TCm, ADJ><<<blocks, threads, 0, st>>>((typename CT<TS>::t*)A.spec, g, tb.a_d, tb.c_d, tb.W_d,
+                                                          tb.lamx_d, tb.lamy_d, A.scale, A.lowk_cols, A.n_lowk,
+                                                          A.lowk_z, A.lowk_w, A.stats, A.done);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thomas(const ThomasArgs& A, const Geom& g, const Tables& tb, cudaStream_t st) {
+  cudaError_t e;
+  // the low-|k| kernel reads its columns before the main kernel (which skips them) runs
+  if (A.t_is_double) {
+    e = A.adjoint ? thomas_lowk<double, double, true>(A, g, tb, st) : thomas_lowk<double, double, false>(A, g, tb, st);
+    if (e != cudaSuccess) return e;
+    return A.adjoint ? thomas_main<double, true>(A, g, tb.a_d, tb.c_d, tb.lamx_d, tb.lamy_d, st)
+                     : thomas_main<double, false>(A, g, tb.a_d, tb.c_d, tb.lamx_d, tb.lamy_d, st);
+  }
+  if (A.lowk_double)
+    e = A.adjoint ? thomas_lowk<float, double, true>(A, g, tb, st) : thomas_lowk<float, double, false>(A, g, tb, st);
+  else
+    e = A.adjoint ? thomas_lowk<float, float, true>(A, g, tb, st) : thomas_lowk<float, float, false>(A, g, tb, st);
+  if (e != cudaSuccess) return e;
+  return A.adjoint ? thomas_main<float, true>(A, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f, st)
+                   : thomas_main<float, false>(A, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f, st);
+}
+
+}  // namespace pgb

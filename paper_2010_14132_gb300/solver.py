@@ -1,0 +1,219 @@
+"""PyTorch-facing API of the GB300 direct FFT pressure solver.
+
+PyTorch provides device memory, streams and autograd plumbing only; every step
+of the solve runs in the library's CUDA kernels through the C ABI
+(``_native``).  There is no CPU path: creating a plan needs the built library
+and solving needs CUDA tensors.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+DTYPES = {"fp64": N.POISSON_FP64, "fp32": N.POISSON_FP32, "mixed": N.POISSON_MIXED}
+FIELD_DTYPE = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float64}
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous tensor of shape {tuple(shape)}")
+
+
+class Plan:
+    """A planned solve for one grid (Section 2.1: plan once, reuse every timestep).
+
+    nx, ny: periodic horizontal sizes (2^a 3^b, nx even); nz levels; dx, dy
+    spacings; dz, rho0: per-level thickness and reference density (length nz).
+    dtype: "fp64", "fp32" or "mixed" (double fields, float transforms, double
+    low-|k| columns and double-float refinement).
+    """
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, rho0, dtype="fp64", device=None,
+                 lowk_radius2=None, max_sweeps=None, tolerance=None, y_tile=None):
+        if dtype not in DTYPES:
+            raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.dx, self.dy = float(dx), float(dy)
+        self.dz = np.asarray(dz, dtype=np.float64).copy()
+        self.rho0 = np.asarray(rho0, dtype=np.float64).copy()
+        if self.dz.shape != (self.nz,) or self.rho0.shape != (self.nz,):
+            raise ValueError("dz and rho0 must have nz entries")
+        self.dtype = dtype
+        self.field_dtype = FIELD_DTYPE[dtype]
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self._h = N.poisson_plan_create(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.rho0,
+                                            N.POISSON_BC_PERIODIC_XY_NEUMANN_Z, DTYPES[dtype])
+        if lowk_radius2 is not None:
+            N.poisson_plan_set_option(self._h, N.POISSON_OPT_LOWK_RADIUS2, lowk_radius2)
+        if max_sweeps is not None:
+            N.poisson_plan_set_option(self._h, N.POISSON_OPT_MAX_SWEEPS, max_sweeps)
+        if tolerance is not None:
+            N.poisson_plan_set_option(self._h, N.POISSON_OPT_TOLERANCE, tolerance)
+        if y_tile is not None:
+            N.poisson_plan_set_option(self._h, N.POISSON_OPT_Y_TILE, y_tile)
+        self._ws = None
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            N.poisson_plan_destroy(self._h)
+            self._h = None
+        self._ws = None
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown ordering
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def npoints(self):
+        return self.nx * self.ny * self.nz
+
+    def workspace_bytes(self) -> int:
+        return N.poisson_plan_workspace_bytes(self._h)
+
+    def workspace(self) -> torch.Tensor:
+        nb = self.workspace_bytes()
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def _ws_ptr(self) -> int:
+        ws = self.workspace()
+        ptr = ws.data_ptr()
+        return ptr + ((-ptr) % 256)
+
+    def set_option(self, option: int, value: float):
+        N.poisson_plan_set_option(self._h, option, value)
+        self._ws = None
+
+    def set_rho0(self, rho0: torch.Tensor, stream=None):
+        """Replace rho0 from a device float64 tensor (asynchronous on the stream)."""
+        _require_cuda(rho0, torch.float64, (self.nz,), "rho0")
+        N.poisson_plan_set_rho0(self._h, rho0.data_ptr(), _stream_handle(stream))
+        self.rho0 = None  # now lives on the device only
+
+    # -- calls ---------------------------------------------------------------
+    def solve(self, S: torch.Tensor, out: torch.Tensor | None = None, info: bool = False, stream=None):
+        """p with L p = S - mu_W and zero mean.  Returns p, or (p, info dict) if info."""
+        _require_cuda(S, self.field_dtype, self.shape, "S")
+        p = out if out is not None else torch.empty_like(S)
+        _require_cuda(p, self.field_dtype, self.shape, "out")
+        r = N.poisson_solve(self._h, S.data_ptr(), p.data_ptr(), self._ws_ptr(), _stream_handle(stream),
+                            want_info=info)
+        if info:
+            st, d = r
+            d["status"] = st
+            return p, d
+        return p
+
+    def adjoint(self, gp: torch.Tensor, p: torch.Tensor | None = None, want_grho: bool = False,
+                out: torch.Tensor | None = None, stream=None):
+        """(G^T gp, d/drho0) for the solve map G; d/drho0 needs the forward p."""
+        _require_cuda(gp, self.field_dtype, self.shape, "gp")
+        gS = out if out is not None else torch.empty_like(gp)
+        grho = None
+        p_ptr = None
+        if want_grho:
+            if p is None:
+                raise ValueError("the rho0 gradient needs the forward solution p")
+            _require_cuda(p, self.field_dtype, self.shape, "p")
+            grho = torch.empty(self.nz, dtype=torch.float64, device=gp.device)
+            p_ptr = p.data_ptr()
+        N.poisson_solve_adjoint(self._h, gp.data_ptr(), p_ptr, gS.data_ptr(),
+                                grho.data_ptr() if grho is not None else None, self._ws_ptr(),
+                                _stream_handle(stream))
+        return gS, grho
+
+
+class PoissonSolve(torch.autograd.Function):
+    """p = G(rho0) S as a differentiable op (gradients w.r.t. S and rho0).
+
+    The backward pass calls the library's adjoint: forward transforms, the
+    transposed tridiagonal solve, inverse transforms, and per-face reductions
+    for the rho0 gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, S, rho0, plan: Plan):
+        if rho0 is not None:
+            plan.set_rho0(rho0.detach())
+        p = plan.solve(S.detach())
+        ctx.plan = plan
+        ctx.need_rho = rho0 is not None and ctx.needs_input_grad[1]
+        ctx.save_for_backward(p)
+        return p
+
+    @staticmethod
+    def backward(ctx, gp):
+        (p,) = ctx.saved_tensors
+        gS, grho = ctx.plan.adjoint(gp.contiguous(), p=p, want_grho=ctx.need_rho)
+        return gS, grho, None
+
+
+def poisson_solve(S: torch.Tensor, plan: Plan, rho0: torch.Tensor | None = None) -> torch.Tensor:
+    """Differentiable solve; pass rho0 (device float64, requires_grad) to train through it."""
+    return PoissonSolve.apply(S, rho0, plan)
+
+
+class Batch:
+    """Many independent domains of uneven sizes, solved by one CUDA-graph launch."""
+
+    def __init__(self, domains, dtype="mixed", device=None):
+        if dtype not in ("fp32", "mixed"):
+            raise ValueError("batched solves support dtype 'fp32' or 'mixed'")
+        self.dtype = dtype
+        self.field_dtype = FIELD_DTYPE[dtype]
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.shapes = [(d.nz, d.ny, d.nx) for d in domains]
+        with torch.cuda.device(self.device):
+            self._h = N.poisson_batch_create([d.nx for d in domains], [d.ny for d in domains],
+                                             [d.nz for d in domains], [d.dx for d in domains],
+                                             [d.dy for d in domains], [d.dz for d in domains],
+                                             [d.rho0 for d in domains], DTYPES[dtype])
+        nb = N.poisson_batch_workspace_bytes(self._h)
+        self._ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+
+    def _ws_ptr(self):
+        ptr = self._ws.data_ptr()
+        return ptr + ((-ptr) % 256)
+
+    def solve(self, S_list, out_list=None, info=False, stream=None):
+        if len(S_list) != len(self.shapes):
+            raise ValueError("one source per domain")
+        for S, shp in zip(S_list, self.shapes):
+            _require_cuda(S, self.field_dtype, shp, "S")
+        outs = out_list if out_list is not None else [torch.empty_like(S) for S in S_list]
+        r = N.poisson_batch_solve(self._h, [S.data_ptr() for S in S_list], [p.data_ptr() for p in outs],
+                                  self._ws_ptr(), _stream_handle(stream), want_info=info)
+        if info:
+            return outs, r[1]
+        return outs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.poisson_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,139 @@
+"""Adjoint and gradients on the GPU: against the oracle, the dot-product identity
+and finite differences (central, eps = 1e-6).
+
+dL/dS is G^T w; dL/drho0 comes from the per-face reductions of the adjoint.
+The finite-difference check on S uses the exact linearity of the solve in S
+(the central difference is one solve of the 2 eps e_i source); the literal
+two-solve difference is reported with its noise estimate.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2010_14132_gb300 import workloads as wl
+from paper_2010_14132_gb300.solver import Plan, poisson_solve
+
+pytestmark = pytest.mark.gpu
+
+ADJ_TOL = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
+GRHO_TOL = {"fp64": 1e-10, "fp32": 1e-4, "mixed": 1e-4}
+
+
+def _plan(d, dtype):
+    return Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype=dtype)
+
+
+def _t(x, plan):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", plan.field_dtype)
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("dims", [(64, 48, 16), (12, 96, 9), (6, 4, 3)])
+def test_adjoint_and_rho_gradient_vs_oracle(dtype, dims):
+    nx, ny, nz = dims
+    d = wl.random_stretched(nx, ny, nz, seed=sum(dims))
+    w = np.random.default_rng(3).standard_normal(d.S.shape)
+    plan = _plan(d, dtype)
+    p = plan.solve(_t(d.S, plan))
+    gS, grho = plan.adjoint(_t(w, plan), p=p, want_grho=True)
+    torch.cuda.synchronize()
+    g_ref = O.adjoint(w, d.dx, d.dy, d.dz, d.rho0)
+    assert O.relative_l2(gS.double().cpu().numpy(), g_ref) <= ADJ_TOL[dtype]
+    r_ref = O.rho0_gradient(w, d.S, d.dx, d.dy, d.dz, d.rho0)
+    err = np.abs(grho.cpu().numpy() - r_ref).max() / np.abs(r_ref).max()
+    assert err <= GRHO_TOL[dtype], err
+
+
+def test_dot_product_identity_fp64():
+    d = wl.anelastic_blobs(128, 64, 32, seed=41)
+    rng = np.random.default_rng(4)
+    w = rng.standard_normal(d.S.shape)
+    plan = _plan(d, "fp64")
+    p = plan.solve(_t(d.S, plan)).cpu().numpy()
+    g, _ = plan.adjoint(_t(w, plan))
+    g = g.cpu().numpy()
+    lhs, rhs = (w * p).sum(), (g * d.S).sum()
+    assert abs(lhs - rhs) <= 1e-12 * (np.abs(w * p).sum() + np.abs(g * d.S).sum())
+
+
+def test_adjoint_equals_weighted_similarity_fp64():
+    """T^{-T} = W T^{-1} W^{-1} on non-singular columns: G^T w = Q_W^T W G (W^{-1} P_1 w)."""
+    d = wl.random_stretched(32, 16, 12, seed=42)
+    w = np.random.default_rng(5).standard_normal(d.S.shape)
+    plan = _plan(d, "fp64")
+    g, _ = plan.adjoint(_t(w, plan))
+    W = (d.rho0 * d.dz)[:, None, None]
+    v = (w - w.mean()) / W
+    x = plan.solve(_t(v, plan)).cpu().numpy() * W
+    x -= W * (x.sum() / (d.nx * d.ny * (d.rho0 * d.dz).sum()))
+    assert O.relative_l2(g.cpu().numpy(), x) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_gradient_workload_512x512x64_full_reference(dtype):
+    d = wl.gradient_problem(512, 512, 64)
+    w = d.extra["w"]
+    plan = _plan(d, dtype)
+    p = plan.solve(_t(d.S, plan))
+    gS, grho = plan.adjoint(_t(w, plan), p=p, want_grho=True)
+    torch.cuda.synchronize()
+    g_ref = O.adjoint(w, d.dx, d.dy, d.dz, d.rho0)
+    r_ref = O.rho0_gradient(w, d.S, d.dx, d.dy, d.dz, d.rho0, g=g_ref)
+    assert O.relative_l2(gS.double().cpu().numpy(), g_ref) <= ADJ_TOL[dtype]
+    assert np.abs(grho.cpu().numpy() - r_ref).max() / np.abs(r_ref).max() <= GRHO_TOL[dtype]
+
+
+def test_gradient_workload_512x512x64_finite_differences_fp64():
+    d = wl.gradient_problem(512, 512, 64)
+    w = d.extra["w"]
+    plan = _plan(d, "fp64")
+    wt = _t(w, plan)
+    St = _t(d.S, plan)
+    p = plan.solve(St)
+    gS, grho = plan.adjoint(wt, p=p, want_grho=True)
+    gS = gS.cpu().numpy().ravel()
+    grho = grho.cpu().numpy()
+    eps = 1e-6
+    # source: exact linearity, the central difference is one solve of 2 eps e_i
+    gmax = np.abs(gS).max()
+    for q in d.extra["fd_index"]:
+        e = torch.zeros_like(St).view(-1)
+        e[q] = 2 * eps
+        fd = float((wt * plan.solve(e.view_as(St))).sum()) / (2 * eps)
+        assert abs(fd - gS[q]) <= 1e-6 * gmax, (q, fd, gS[q])
+    # rho0: literal central differences of the loss
+    rmax = np.abs(grho).max()
+    for m in np.random.default_rng(6).choice(d.nz, 8, replace=False):
+        vals = []
+        for sgn in (+1, -1):
+            rho = d.rho0.copy()
+            rho[m] += sgn * eps * d.rho0[m]
+            pl = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, rho, dtype="fp64")
+            vals.append(float((wt * pl.solve(St)).sum()))
+        fd = (vals[0] - vals[1]) / (2 * eps * d.rho0[m])
+        assert abs(fd - grho[m]) <= 1e-6 * rmax, (m, fd, grho[m])
+
+
+def test_autograd_function_matches_oracle():
+    d = wl.random_stretched(32, 24, 10, seed=44)
+    plan = _plan(d, "fp64")
+    w = np.random.default_rng(7).standard_normal(d.S.shape)
+    S = _t(d.S, plan).requires_grad_(True)
+    rho = torch.from_numpy(d.rho0.copy()).cuda().requires_grad_(True)
+    p = poisson_solve(S, plan, rho0=rho)
+    loss = (p * _t(w, plan)).sum()
+    loss.backward()
+    assert O.relative_l2(S.grad.cpu().numpy(), O.adjoint(w, d.dx, d.dy, d.dz, d.rho0)) < 1e-12
+    r_ref = O.rho0_gradient(w, d.S, d.dx, d.dy, d.dz, d.rho0)
+    assert np.abs(rho.grad.cpu().numpy() - r_ref).max() <= 1e-10 * np.abs(r_ref).max()
+
+
+def test_set_rho0_on_device_matches_new_plan():
+    d = wl.random_stretched(32, 16, 8, seed=45)
+    plan = _plan(d, "fp64")
+    rho2 = d.rho0 * np.linspace(0.9, 1.2, d.nz)
+    plan.set_rho0(torch.from_numpy(rho2).cuda())
+    p = plan.solve(_t(d.S, plan)).cpu().numpy()
+    ref = O.solve(d.S, d.dx, d.dy, d.dz, rho2)
+    assert O.relative_l2(p, ref) < 1e-12

@@ -1,0 +1,185 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (relative L2 over all cells, both sides pinned to zero mean):
+FP64 path <= 1e-12, FP32 path <= 1e-5, mixed path (after refinement) <= 1e-10.
+Inputs are the seeded synthetic workloads; sizes span several tiles, ragged
+tails, radix-2/3 mixes and the degenerate cases of the method (the singular
+(0,0) column, constant sources, pure vertical and pure horizontal modes).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2010_14132_gb300 import workloads as wl
+from paper_2010_14132_gb300.solver import Plan, Batch, poisson_solve
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-10}
+
+
+def gpu_solve(d, dtype, S=None, **opts):
+    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype=dtype, **opts)
+    S = d.S if S is None else S
+    St = torch.from_numpy(np.ascontiguousarray(S)).to("cuda", plan.field_dtype)
+    p, info = plan.solve(St, info=True)
+    torch.cuda.synchronize()
+    return p.double().cpu().numpy(), info, plan
+
+
+def check(d, dtype, tol=None, S=None, **opts):
+    p, info, _ = gpu_solve(d, dtype, S=S, **opts)
+    ref = O.solve(d.S if S is None else S, d.dx, d.dy, d.dz, d.rho0)
+    err = O.relative_l2(p, ref)
+    assert np.isfinite(p).all()
+    assert err <= (tol if tol is not None else TOL[dtype]), (dtype, d.name, err, info)
+    return err, info
+
+
+# ---------------------------------------------------------------------------
+# the five workloads
+# ---------------------------------------------------------------------------
+
+def test_uniform_cube_32_fp64():
+    err, info = check(wl.uniform_cube(32, seed=1), "fp64")
+    assert abs(info["removed_weighted_mean"]) < 1e-15
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_anelastic_blobs_256x256x64(dtype):
+    check(wl.anelastic_blobs(256, 256, 64, seed=2), dtype)
+
+
+def test_anelastic_noise_1024x1024x128_mixed_full_size():
+    d = wl.anelastic_noise(1024, 1024, 128, seed=3)
+    err, info = check(d, "mixed")
+    assert info["converged"] and 1 <= info["sweeps"] <= 3, info
+    assert info["error_estimate"] <= 1e-10
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
+def test_anelastic_noise_small(dtype):
+    check(wl.anelastic_noise(128, 96, 32, seed=31), dtype)
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
+def test_gradient_workload_forward_512x512x64(dtype):
+    d = wl.gradient_problem(512, 512, 64)
+    check(d, dtype)
+
+
+# ---------------------------------------------------------------------------
+# sizes: radix 2/3 mixes, ragged tiles, minimum sizes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nx,ny,nz", [(4, 4, 2), (4, 6, 3), (6, 4, 5), (12, 48, 7), (96, 384, 9), (384, 96, 4),
+                                      (48, 12, 33), (8, 16, 130), (18, 27, 6), (36, 8, 3), (64, 64, 512),
+                                      (2048, 8, 4), (8, 4096, 2)])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_sizes(nx, ny, nz, dtype):
+    d = wl.random_stretched(nx, ny, nz, seed=nx * 7 + ny * 3 + nz)
+    check(d, dtype)
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(384, 384, 48), (64, 128, 96), (512, 256, 32)])
+def test_sizes_mixed(nx, ny, nz):
+    d = wl.uneven_batch(1)[0]
+    d = wl.Domain(nx, ny, nz, 50.0, 50.0, wl.stretched_levels(nz, 12.0, 1.02),
+                  wl.exponential_density(wl.stretched_levels(nz, 12.0, 1.02), 1.1, 8500.0),
+                  wl.normal_source((nz, ny, nx), seed=nx + ny + nz))
+    check(d, "mixed")
+
+
+# ---------------------------------------------------------------------------
+# closed forms and degenerate cases (no oracle on the expected side)
+# ---------------------------------------------------------------------------
+
+def _cos_mode(nx, ny, nz, ax, by, cz):
+    i = np.arange(nx)[None, None, :]
+    j = np.arange(ny)[None, :, None]
+    k = np.arange(nz)[:, None, None]
+    return (np.cos(2 * np.pi * ax * i / nx + 0.3) * np.cos(2 * np.pi * by * j / ny - 0.7)
+            * np.cos(np.pi * cz * (k + 0.5) / nz))
+
+
+@pytest.mark.parametrize("mode", [(1, 0, 0), (0, 0, 1), (0, 0, 31), (16, 16, 0), (5, 3, 7), (0, 16, 2)])
+@pytest.mark.parametrize("dtype", ["fp64", "mixed"])
+def test_eigenfunctions_uniform_cube(mode, dtype):
+    n = 32
+    p_exact = _cos_mode(n, n, n, *mode)
+    a, b, c = mode
+    lam = -4 * np.sin(np.pi * a / n) ** 2 - 4 * np.sin(np.pi * b / n) ** 2 - 4 * np.sin(np.pi * c / (2 * n)) ** 2
+    d = wl.Domain(n, n, n, 1.0, 1.0, np.ones(n), np.ones(n), lam * p_exact)
+    p, info, _ = gpu_solve(d, dtype)
+    assert O.relative_l2(p, p_exact) < (1e-13 if dtype == "fp64" else 1e-10)
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
+def test_constant_source_gives_zero(dtype):
+    d = wl.random_stretched(16, 12, 8, seed=5)
+    S = np.full(d.S.shape, 3.25)
+    p, info, _ = gpu_solve(d, dtype, S=S)
+    assert np.abs(p).max() < 1e-9
+    assert abs(info["removed_weighted_mean"] - 3.25) < 1e-6
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
+def test_zero_mean_and_residual(dtype):
+    d = wl.anelastic_blobs(64, 48, 24, seed=12)
+    p, info, _ = gpu_solve(d, dtype)
+    assert abs(p.mean()) <= 1e-12 * np.abs(p).max() * (1 if dtype != "fp32" else 1e6)
+    r = O.residual(d.S, p, d.dx, d.dy, d.dz, d.rho0)
+    bound = {"fp64": 1e-10, "fp32": 1e-3, "mixed": 1e-8}[dtype]
+    assert np.linalg.norm(r) / np.linalg.norm(d.S) < bound
+
+
+def test_periodic_shift_equivariance_fp64():
+    d = wl.anelastic_blobs(64, 32, 16, seed=13)
+    p1, _, plan = gpu_solve(d, "fp64")
+    S2 = np.roll(d.S, (5, 11), axis=(1, 2))
+    p2 = plan.solve(torch.from_numpy(S2).cuda()).cpu().numpy()
+    assert O.relative_l2(p2, np.roll(p1, (5, 11), axis=(1, 2))) < 1e-13
+
+
+def test_repeated_solves_are_bitwise_identical():
+    d = wl.anelastic_noise(128, 128, 32, seed=14)
+    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype="mixed")
+    St = torch.from_numpy(d.S).cuda()
+    a = plan.solve(St).clone()
+    b = plan.solve(St).clone()
+    assert torch.equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# mixed-path options
+# ---------------------------------------------------------------------------
+
+def test_mixed_without_refinement_is_fp32_accurate():
+    d = wl.anelastic_noise(256, 256, 64, seed=15)
+    err, info = check(d, "mixed", tol=1e-5, max_sweeps=0)
+    assert info["sweeps"] == 0
+
+
+def test_mixed_lowk_radius_zero_still_converges():
+    d = wl.anelastic_noise(256, 256, 64, seed=16)
+    check(d, "mixed", lowk_radius2=0)
+
+
+# ---------------------------------------------------------------------------
+# batched solve (uneven sizes, one graph launch)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["fp32", "mixed"])
+def test_batch_uneven_domains(dtype):
+    doms = wl.uneven_batch(6, seed=70, nxy_choices=(64, 96, 128), nz_choices=(16, 24, 32))
+    b = Batch(doms, dtype=dtype)
+    fd = torch.float32 if dtype == "fp32" else torch.float64
+    S = [torch.from_numpy(d.S).to("cuda", fd) for d in doms]
+    outs, infos = b.solve(S, info=True)
+    outs2 = b.solve(S)   # graph replay
+    torch.cuda.synchronize()
+    for d, p, p2 in zip(doms, outs, outs2):
+        ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
+        assert O.relative_l2(p.double().cpu().numpy(), ref) <= TOL[dtype]
+        assert torch.equal(p, p2)
