@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Throughput of the direct FFT-tridiagonal pressure solve on GB300.
+
+Metric: Mpoints/s of one complete solve (all refinement sweeps included) of the
+mixed-precision path on the 1024x1024x128 stretched/anelastic workload
+(S ~ N(0,1), mean removed), at the 1e-10 relative-L2 target; the plain FP64
+GPU solve of the same grid is timed beside it, and the solve's algorithmic
+bytes are reported as a fraction of the measured HBM copy peak.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  Multi-GPU: replicas only (one independent domain per
+rank, no data-path collective); a barrier and a max-over-ranks of the device
+time bracket the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s of FFT-tridiag Poisson solve, mixed vs FP64 at 1e-10 rel; % HBM peak"
+WORKLOAD = dict(name="anelastic_noise_1024x1024x128_mixed", nx=1024, ny=1024, nz=128, seed=3)
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2010_14132_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(phase):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(phase)
+        if e and e.get("source_sha") == source_hash():
+            return float(e["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def algorithmic_bytes(nx, ny, nz, sweeps):
+    """Per-phase algorithmic bytes of one mixed solve with `sweeps` executed sweeps.
+
+    N points, Nc = (nx/2+1) ny nz spectral entries (complex float, 8 B).
+    """
+    N = nx * ny * nz
+    Nc = (nx // 2 + 1) * ny * nz
+    b = {
+        "xfwd": 8 * N + 8 * Nc + sweeps * (4 * N + 8 * Nc),
+        "yfwd": (1 + sweeps) * 16 * Nc,
+        "columns": (1 + sweeps) * 16 * Nc,
+        "yinv": (1 + sweeps) * 16 * Nc,
+        "xinv": (8 * Nc + 4 * N) + sum(8 * Nc + 4 * N + 4 * N + 8 * N + (4 * N if s > 1 else 0)
+                                       for s in range(1, sweeps + 1)),
+        "residual": sum(8 * N + 4 * N + 4 * N + (4 * N if s > 1 else 0) for s in range(1, sweeps + 1)),
+        "control": 0,
+    }
+    # the solve as a whole: read S, write p once; spectrum written and read once per pass;
+    # each sweep also reads S and p and updates p
+    total = 16 * N + 16 * Nc + sweeps * (32 * N + 16 * Nc)
+    return b, total
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_step(S, d, O):
+    t0 = time.perf_counter()
+    O.solve(S, d.dx, d.dy, d.dz, d.rho0)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_domain(nz_sample):
+    from paper_2010_14132_gb300 import workloads as wl
+    d = wl.anelastic_noise(WORKLOAD["nx"], WORKLOAD["ny"], nz_sample, seed=WORKLOAD["seed"])
+    return d
+
+
+def cpu_baseline(budget_s=20.0):
+    """Oracle Mpoints/s on a slab of the workload (all nx x ny columns, fewer levels)."""
+    import oracle as O
+    d = oracle_sample_domain(8)
+    t = oracle_step(d.S, d, O)
+    nz_s = int(max(2, min(WORKLOAD["nz"], 8 * budget_s / max(t, 1e-3) / 2)))
+    d = oracle_sample_domain(nz_s)
+    t = oracle_step(d.S, d, O)
+    return {"value": d.npoints / t / 1e6, "unit": "Mpoints/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one FP64 oracle solve (numpy DFT-by-matmul + textbook Thomas) of a "
+                      f"{d.nx}x{d.ny}x{d.nz} slab of the workload, {t:.2f} s, BLAS threads = host cores"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle as O
+    K, W = args.steps, args.warmup
+    d = oracle_sample_domain(4)
+    t4 = oracle_step(d.S, d, O)
+    per_level = t4 / 4
+    budget = 150.0 / max(1, K + W)
+    nz_s = int(max(2, min(WORKLOAD["nz"], budget / max(per_level, 1e-4))))
+    d = oracle_sample_domain(nz_s)
+    for _ in range(W):
+        oracle_step(d.S, d, O)
+    ts = [oracle_step(d.S, d, O) for _ in range(K)]
+    t = float(np.mean(ts))
+    value = d.npoints / t / 1e6
+    sample = (f"FP64 oracle solve of a {d.nx}x{d.ny}x{d.nz} slab of {WORKLOAD['name']} per step "
+              f"(per-point cost independent of nz), BLAS threads = host cores")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "nx": d.nx, "ny": d.ny, "nz_sample": d.nz, "nz": WORKLOAD["nz"]},
+        "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if local == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_2010_14132_gb300 import _native as N
+    from paper_2010_14132_gb300 import workloads as wl
+    from paper_2010_14132_gb300.solver import Plan
+
+    nx, ny, nz = WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"]
+    d = wl.anelastic_noise(nx, ny, nz, seed=WORKLOAD["seed"] + rank)
+    plan = Plan(nx, ny, nz, d.dx, d.dy, d.dz, d.rho0, dtype="mixed")
+    stream = torch.cuda.current_stream()
+    S = torch.from_numpy(d.S).cuda()
+    p = torch.empty_like(S)
+    # warm-up (first call also reports the sweeps the stopping rule needs)
+    _, info = plan.solve(S, out=p, info=True)
+    for _ in range(args.warmup - 1):
+        plan.solve(S, out=p)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- timed region: device time, per-kernel events live on the launching stream
+    plan.set_option(N.POISSON_OPT_PROFILE, 1)
+    N.poisson_plan_profile_read(plan._h)
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.solve(S, out=p)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms)
+    prof = N.poisson_plan_profile_read(plan._h)
+    plan.set_option(N.POISSON_OPT_PROFILE, 0)
+    value = world * d.npoints / (ms_max * 1e-3) / 1e6
+
+    # ---- roofline of the dominant kernel phase
+    peak, peak_kind = measured_peaks()
+    sweeps = int(info["sweeps"])
+    alg, alg_total = algorithmic_bytes(nx, ny, nz, sweeps)
+    phases = {}
+    for name, (tms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        per_solve_ms = tms / args.steps
+        gbs = alg[name] / (per_solve_ms * 1e-3) / 1e9 if per_solve_ms > 0 and alg[name] else None
+        phases[name] = {"ms_per_solve": per_solve_ms, "launches_per_solve": cnt / args.steps,
+                        "alg_bytes_per_solve": alg[name], "gbs": gbs}
+    dom = max(phases, key=lambda k: phases[k]["ms_per_solve"])
+    execd = {"xfwd": 1 + sweeps, "yfwd": 1 + sweeps, "columns": 1 + sweeps, "yinv": 1 + sweeps,
+             "xinv": 1 + sweeps, "residual": sweeps, "control": 1 + sweeps}[dom]
+    dom_ms_launch = phases[dom]["ms_per_solve"] / execd
+    dom_bytes_launch = alg[dom] / execd
+    achieved = dom_bytes_launch / (dom_ms_launch * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(dom), "kernel": dom, "peak_kind": f"{peak_kind} copy peak",
+                "alg_bytes_per_launch": dom_bytes_launch, "ms_per_launch": dom_ms_launch}
+    solve_gbs = alg_total / (ms * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host buffers
+    Sh = torch.from_numpy(d.S).pin_memory()
+    ph = torch.empty_like(Sh).pin_memory()
+    K2 = max(3, min(args.steps, 30))
+    for _ in range(2):
+        S.copy_(Sh, non_blocking=True)
+        plan.solve(S, out=p)
+        ph.copy_(p, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(K2):
+        S.copy_(Sh, non_blocking=True)
+        plan.solve(S, out=p)
+        ph.copy_(p, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / K2)
+    e2e = {"value": world * d.npoints / (ms_e2e * 1e-3) / 1e6, "unit": "Mpoints/s",
+           "h2d_bytes_per_step": int(S.numel() * 8), "d2h_bytes_per_step": int(p.numel() * 8)}
+
+    # ---- plain FP64 GPU solve of the same grid (the comparison the metric names)
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = Plan(nx, ny, nz, d.dx, d.dy, d.dz, d.rho0, dtype="fp64")
+        p64 = torch.empty_like(S)
+        for _ in range(2):
+            plan64.solve(S, out=p64)
+        torch.cuda.synchronize()
+        K3 = max(3, min(args.steps, 10))
+        barrier()
+        e0.record(stream)
+        for _ in range(K3):
+            plan64.solve(S, out=p64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms64 = max_over_ranks(e0.elapsed_time(e1) / K3)
+        fp64 = {"value": world * d.npoints / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
+                "steps": K3, "bound": "alu (FP64 at 1/65 of FP32 on GB300)"}
+        del plan64, p64
+
+    n_launches_per_solve = sum(int(round(v["launches_per_solve"])) for v in phases.values())
+    # the column phase launches two kernels (low-|k| and main)
+    n_launches_per_solve += int(round(phases.get("columns", {}).get("launches_per_solve", 0)))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline()
+        except Exception as ex:  # pragma: no cover
+            cpu = {"value": None, "unit": "Mpoints/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {ex}"}
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 transforms + double-float residual, f64 in/out",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "nx": nx, "ny": ny, "nz": nz, "dx": 50.0,
+                       "dz": "10*1.03^k m", "rho0": "1.2*exp(-z/8000)", "source": "N(0,1) mean removed, seed 3",
+                       "sweeps": sweeps, "error_estimate": info["error_estimate"],
+                       "l2": "inputs larger than L2 (1.07 GB source per solve)", "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "hbm_frac_solve": {"alg_bytes": alg_total, "gbs": solve_gbs, "frac": solve_gbs / peak,
+                               "peak": peak, "peak_kind": peak_kind},
+            "phases": phases,
+            "fp64": fp64,
+            "e2e": e2e,
+            "gpu_launches": n_launches_per_solve * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -68,8 +68,22 @@ typedef enum {
                                     double; default 64 (|k| <= 8); the (0,0) column always does */
   POISSON_OPT_MAX_SWEEPS = 1,    /* mixed: refinement sweeps after the first solve, 0..3; default 3 */
   POISSON_OPT_TOLERANCE = 2,     /* mixed: target relative L2 error estimate; default 1e-11 */
-  POISSON_OPT_Y_TILE = 3         /* y-pass kx tile width (autotuner hook); 0 = plan default */
+  POISSON_OPT_Y_TILE = 3,        /* y-pass kx tile width (autotuner hook); 0 = plan default */
+  POISSON_OPT_PROFILE = 4        /* 1: record CUDA events around every kernel launch of this plan on
+                                    the launching stream (read with poisson_plan_profile_read) */
 } poisson_option;
+
+/* Kernel phases reported by poisson_plan_profile_read. */
+typedef enum {
+  POISSON_PHASE_XFWD = 0,      /* forward x-pass (R2C) */
+  POISSON_PHASE_YFWD = 1,      /* forward y-pass */
+  POISSON_PHASE_COLUMNS = 2,   /* tridiagonal column solves (low-|k| + main kernels) */
+  POISSON_PHASE_YINV = 3,      /* inverse y-pass */
+  POISSON_PHASE_XINV = 4,      /* inverse x-pass (C2R) with its epilogue */
+  POISSON_PHASE_RESIDUAL = 5,  /* double-float residual of a refinement sweep */
+  POISSON_PHASE_CONTROL = 6,   /* refinement control */
+  POISSON_NPHASES = 7
+} poisson_phase;
 
 typedef struct {
   int sweeps;                  /* refinement sweeps executed (mixed path; 0 otherwise) */
@@ -116,6 +130,12 @@ int poisson_solve(poisson_plan* plan, const void* S, void* p, void* workspace, v
  * transforms (no refinement). */
 int poisson_solve_adjoint(poisson_plan* plan, const void* gp, const void* p, void* gS,
                           double* grho, void* workspace, void* stream);
+
+/* Sum of the recorded per-phase kernel times (milliseconds) and launch counts
+ * since the last read, for phases 0..nphases-1 (host arrays); synchronises on
+ * the recorded events and clears them.  Recording is off unless
+ * POISSON_OPT_PROFILE is set, and is skipped while a stream is being captured. */
+int poisson_plan_profile_read(poisson_plan* plan, double* ms, int* launches, int nphases);
 
 /* NULL-safe.  Frees the plan's device tables (synchronously). */
 int poisson_plan_destroy(poisson_plan* plan);

@@ -22,13 +22,15 @@ POISSON_ERR_TIMEOUT = -6
 POISSON_BC_PERIODIC_XY_NEUMANN_Z = 0
 POISSON_FP64, POISSON_FP32, POISSON_MIXED = 0, 1, 2
 POISSON_OPT_LOWK_RADIUS2, POISSON_OPT_MAX_SWEEPS, POISSON_OPT_TOLERANCE, POISSON_OPT_Y_TILE = 0, 1, 2, 3
+POISSON_OPT_PROFILE = 4
+PHASES = ("xfwd", "yfwd", "columns", "yinv", "xinv", "residual", "control")
 
 # every symbol include/poisson.h declares
 EXPORTED = (
     "poisson_plan_create", "poisson_plan_workspace_bytes", "poisson_plan_set_option", "poisson_plan_set_rho0",
     "poisson_solve", "poisson_solve_adjoint", "poisson_plan_destroy", "poisson_status_string",
     "poisson_last_error_detail", "poisson_batch_create", "poisson_batch_workspace_bytes", "poisson_batch_solve",
-    "poisson_batch_destroy",
+    "poisson_batch_destroy", "poisson_plan_profile_read",
 )
 
 
@@ -92,6 +94,7 @@ def load():
     L.poisson_batch_workspace_bytes.argtypes = [vp, C.POINTER(sz)]
     L.poisson_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), vp, vp, C.POINTER(PoissonInfo)]
     L.poisson_batch_destroy.argtypes = [vp]
+    L.poisson_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int), i]
     for name in EXPORTED:
         if name not in ("poisson_status_string", "poisson_last_error_detail"):
             getattr(L, name).restype = C.c_int
@@ -147,6 +150,15 @@ def poisson_solve_adjoint(plan, gp_ptr, p_ptr, gS_ptr, grho_ptr, ws_ptr, stream)
 def poisson_plan_destroy(plan):
     if plan:
         load().poisson_plan_destroy(plan)
+
+
+def poisson_plan_profile_read(plan):
+    """{phase name: (total ms, launches)} since the last read."""
+    k = len(PHASES)
+    ms = (C.c_double * k)()
+    cnt = (C.c_int * k)()
+    _check(load().poisson_plan_profile_read(plan, ms, cnt, k), "poisson_plan_profile_read")
+    return {PHASES[i]: (ms[i], cnt[i]) for i in range(k)}
 
 
 def poisson_status_string(status) -> str:

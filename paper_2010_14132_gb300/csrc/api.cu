@@ -58,6 +58,16 @@ int signed_k(int k, int n) { return k > n / 2 ? k - n : k; }
 
 }  // namespace
 
+
+// Optional per-phase CUDA-event timing (POISSON_OPT_PROFILE): events recorded on
+// the launching stream around each kernel launch, summed on read.
+struct PhaseProfiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> phase;   // phase of event pair i (events 2i, 2i+1)
+  size_t used = 0;
+};
+
 struct poisson_plan {
   int nx = 0, ny = 0, nz = 0, nxh = 0, P = 0;
   double dx = 0, dy = 0;
@@ -78,6 +88,7 @@ struct poisson_plan {
   size_t off_spec = 0, off_stats = 0, off_part = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0, off_r = 0,
          off_gp = 0, ws_bytes = 0;
   int xinv_blocks = 1, grho_nb = 1;
+  PhaseProfiler prof;
   bool mixed() const { return dtype == POISSON_MIXED; }
   bool fp64() const { return dtype == POISSON_FP64; }
   size_t elem() const { return dtype == POISSON_FP32 ? 4 : 8; }
@@ -130,7 +141,7 @@ void layout_workspace(poisson_plan* pl) {
   pl->off_stats = off;
   off = align256(off + sizeof(Stats));
   pl->off_part = off;
-  off = align256(off + 2 * sizeof(double) * (size_t)(pl->xinv_blocks > 0 ? pl->xinv_blocks : 1));
+  off = align256(off + 3 * sizeof(double) * (size_t)(pl->xinv_blocks > 0 ? pl->xinv_blocks : 1));
   pl->off_lz = off;
   off = align256(off + sizeof(double2) * (size_t)pl->nz * pl->n_lowk);
   pl->off_lw = off;
@@ -156,6 +167,34 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
 
 }  // namespace
 
+
+namespace {
+
+int prof_begin(poisson_plan* pl, int phase, cudaStream_t st) {
+  if (!pl->prof.on) return -1;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return -1;
+  PhaseProfiler& P = pl->prof;
+  if (2 * (P.used + 1) > P.pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      P.pool.push_back(e);
+    }
+  }
+  if (P.phase.size() < P.used + 1) P.phase.resize(P.used + 1);
+  const int slot = (int)P.used++;
+  P.phase[slot] = phase;
+  cudaEventRecord(P.pool[2 * slot], st);
+  return slot;
+}
+
+void prof_end(poisson_plan* pl, int slot, cudaStream_t st) {
+  if (slot >= 0) cudaEventRecord(pl->prof.pool[2 * slot + 1], st);
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* poisson_status_string(int s) {
@@ -176,6 +215,7 @@ const char* poisson_last_error_detail(void) { return g_last_error; }
 int poisson_plan_destroy(poisson_plan* pl) {
   if (!pl) return POISSON_OK;
   cudaDeviceSynchronize();
+  for (cudaEvent_t e : pl->prof.pool) cudaEventDestroy(e);
   if (pl->tables) cudaFree(pl->tables);
   if (pl->lowk_d) cudaFree(pl->lowk_d);
   delete pl;
@@ -364,9 +404,35 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value >= 0 && value <= 64)) return POISSON_ERR_INVALID_ARG;
       pl->ytile = (int)value;
       return POISSON_OK;
+    case POISSON_OPT_PROFILE:
+      if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
+      pl->prof.on = value != 0;
+      pl->prof.used = 0;
+      return POISSON_OK;
     default:
       return POISSON_ERR_INVALID_ARG;
   }
+}
+
+int poisson_plan_profile_read(poisson_plan* pl, double* ms, int* launches, int nphases) {
+  if (!pl || !ms || !launches || nphases < 0) return POISSON_ERR_INVALID_ARG;
+  for (int i = 0; i < nphases; ++i) {
+    ms[i] = 0;
+    launches[i] = 0;
+  }
+  PhaseProfiler& P = pl->prof;
+  for (size_t s = 0; s < P.used; ++s) {
+    PGB_CUDA(cudaEventSynchronize(P.pool[2 * s + 1]));
+    float t = 0;
+    PGB_CUDA(cudaEventElapsedTime(&t, P.pool[2 * s], P.pool[2 * s + 1]));
+    const int ph = P.phase[s];
+    if (ph >= 0 && ph < nphases) {
+      ms[ph] += t;
+      launches[ph] += 1;
+    }
+  }
+  P.used = 0;
+  return POISSON_OK;
 }
 
 int poisson_plan_set_rho0(poisson_plan* pl, const double* rho0_dev, void* stream) {
@@ -389,13 +455,17 @@ static int check_ws(const poisson_plan* pl, void* ws) {
 
 // Forward transform -> column solve -> inverse transform of one field.
 static cudaError_t run_pipeline(poisson_plan* pl, const void* in, int in_double, char* ws, cudaStream_t st,
-                                int adjoint, const int* done) {
+                                int adjoint, const int* done, const double* target_mean = nullptr) {
   const bool t_double = pl->fp64();
   void* spec = ws + pl->off_spec;
   Stats* stats = (Stats*)(ws + pl->off_stats);
+  int ps = prof_begin(pl, POISSON_PHASE_XFWD, st);
   cudaError_t e = launch_xfwd(in_double, t_double, in, spec, pl->g, pl->fx, pl->tb, done, st);
+  prof_end(pl, ps, st);
   if (e != cudaSuccess) return e;
+  ps = prof_begin(pl, POISSON_PHASE_YFWD, st);
   e = launch_yfft(t_double, -1, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, st);
+  prof_end(pl, ps, st);
   if (e != cudaSuccess) return e;
   ThomasArgs A{};
   A.spec = spec;
@@ -410,9 +480,15 @@ static cudaError_t run_pipeline(poisson_plan* pl, const void* in, int in_double,
   A.lowk_w = (double*)(ws + pl->off_lw);
   A.stats = stats;
   A.done = done;
+  A.target_mean = target_mean;
+  ps = prof_begin(pl, POISSON_PHASE_COLUMNS, st);
   e = launch_thomas(A, pl->g, pl->tb, st);
+  prof_end(pl, ps, st);
   if (e != cudaSuccess) return e;
-  return launch_yfft(t_double, +1, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, st);
+  ps = prof_begin(pl, POISSON_PHASE_YINV, st);
+  e = launch_yfft(t_double, +1, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, st);
+  prof_end(pl, ps, st);
+  return e;
 }
 
 static int fill_info(poisson_plan* pl, char* ws, cudaStream_t st, poisson_info* info) {
@@ -453,8 +529,11 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
   ex.partials = (double*)(ws + pl->off_part);
   if (!pl->mixed()) {
     PGB_CUDA(run_pipeline(pl, S, t_double, ws, st, 0, nullptr));
-    PGB_CUDA(launch_xinv(t_double, t_double, XINV_PLAIN, ws + pl->off_spec, p, pl->g, pl->fx, pl->tb, ex, nullptr,
-                         st));
+    const int ps = prof_begin(pl, POISSON_PHASE_XINV, st);
+    const cudaError_t e = launch_xinv(t_double, t_double, XINV_PLAIN, ws + pl->off_spec, p, pl->g, pl->fx, pl->tb,
+                                      ex, nullptr, st);
+    prof_end(pl, ps, st);
+    PGB_CUDA(e);
   } else {
     const int* done = &stats->done;
     float* p0 = (float*)(ws + pl->off_p0);
@@ -465,20 +544,35 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
     PGB_CUDA(run_pipeline(pl, S, 1, ws, st, 0, nullptr));
     ex.p0 = p0;
     ex.p_out = pl->max_sweeps == 0 ? (double*)p : nullptr;
-    PGB_CUDA(launch_xinv(0, 0, XINV_P0, ws + pl->off_spec, p0, pl->g, pl->fx, pl->tb, ex, &nb, st));
-    PGB_CUDA(launch_control(stats, ex.partials, nb, 0, pl->max_sweeps, pl->tol, st));
+    int ps = prof_begin(pl, POISSON_PHASE_XINV, st);
+    cudaError_t e = launch_xinv(0, 0, XINV_P0, ws + pl->off_spec, p0, pl->g, pl->fx, pl->tb, ex, &nb, st);
+    prof_end(pl, ps, st);
+    PGB_CUDA(e);
+    ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
+    e = launch_control(stats, ex.partials, nb, 0, pl->max_sweeps, pl->tol, pl->g.N, st);
+    prof_end(pl, ps, st);
+    PGB_CUDA(e);
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
-      PGB_CUDA(launch_residual_ff((const double*)S, p0, sweep > 1 ? q : nullptr, r, pl->g, pl->tb, pl->cx, pl->cy,
-                                  done, st));
-      PGB_CUDA(run_pipeline(pl, r, 0, ws, st, 0, done));
+      ps = prof_begin(pl, POISSON_PHASE_RESIDUAL, st);
+      e = launch_residual_ff((const double*)S, p0, sweep > 1 ? q : nullptr, r, pl->g, pl->tb, pl->cx, pl->cy, done,
+                             st);
+      prof_end(pl, ps, st);
+      PGB_CUDA(e);
+      PGB_CUDA(run_pipeline(pl, r, 0, ws, st, 0, done, &stats->pmean));
       XinvExtra eu = ex;
       eu.p0 = p0;
       eu.q = q;
       eu.q_valid = sweep > 1;
       eu.p_out = (double*)p;
       eu.done = done;
-      PGB_CUDA(launch_xinv(0, 0, XINV_UPDATE, ws + pl->off_spec, nullptr, pl->g, pl->fx, pl->tb, eu, &nb, st));
-      PGB_CUDA(launch_control(stats, ex.partials, nb, sweep, pl->max_sweeps, pl->tol, st));
+      ps = prof_begin(pl, POISSON_PHASE_XINV, st);
+      e = launch_xinv(0, 0, XINV_UPDATE, ws + pl->off_spec, nullptr, pl->g, pl->fx, pl->tb, eu, &nb, st);
+      prof_end(pl, ps, st);
+      PGB_CUDA(e);
+      ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
+      e = launch_control(stats, ex.partials, nb, sweep, pl->max_sweeps, pl->tol, pl->g.N, st);
+      prof_end(pl, ps, st);
+      PGB_CUDA(e);
     }
   }
   if (info) return fill_info(pl, ws, st, info);

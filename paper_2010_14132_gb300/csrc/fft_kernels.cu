@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
   if (ex.done && *ex.done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ float red[2][256];
+  __shared__ double redd[256];
   C* sm = reinterpret_cast<C*>(smraw);
   const int n = fx.n, nl = n / E;
   const int lane = threadIdx.x, ty = threadIdx.y;
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
 
   const long long base = (valid ? row : 0) * g.nx;
   float acc0 = 0.f, acc1 = 0.f;
+  float sh = 0.f, sl = 0.f;   // double-float running sum of p
 #pragma unroll
   for (int q = 0; q < E; ++q) {
     const int m = lane + nl * q;
@@ -119,6 +121,10 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
     } else if constexpr (MODE == XINV_P0) {
       reinterpret_cast<float2*>(ex.p0 + base)[m] = make_float2(z.x, z.y);
       acc1 += z.x * z.x + z.y * z.y;
+      float e0, e1;
+      two_sum(sh, z.x, sh, e0);
+      two_sum(sh, z.y, sh, e1);
+      sl += e0 + e1;
       if (ex.p_out) reinterpret_cast<double2*>(ex.p_out + base)[m] = make_double2(f2d_int(z.x), f2d_int(z.y));
     } else {  // XINV_UPDATE
       const float2 p0 = reinterpret_cast<const float2*>(ex.p0 + base)[m];
@@ -135,6 +141,10 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
       reinterpret_cast<double2*>(ex.p_out + base)[m] = make_double2(ff2d_int(s0, t0), ff2d_int(s1, t1));
       acc0 += z.x * z.x + z.y * z.y;
       acc1 += s0 * s0 + s1 * s1;
+      float e0, e1;
+      two_sum(sh, s0, sh, e0);
+      two_sum(sh, s1, sh, e1);
+      sl += (e0 + e1) + (t0 + t1);
     }
   }
   if constexpr (MODE != XINV_PLAIN) {
@@ -143,17 +153,20 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
     const int nthreads = blockDim.x * blockDim.y;   // <= 256
     red[0][tid] = acc0;
     red[1][tid] = acc1;
+    redd[tid] = f2d_int(sh) + f2d_int(sl);
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
       if (tid < h && tid + h < nthreads) {
         red[0][tid] += red[0][tid + h];
         red[1][tid] += red[1][tid + h];
+        redd[tid] += redd[tid + h];
       }
       __syncthreads();
     }
     if (tid == 0) {
-      ex.partials[2 * blockIdx.x] = (double)red[0][0];
-      ex.partials[2 * blockIdx.x + 1] = (double)red[1][0];
+      ex.partials[3 * blockIdx.x] = (double)red[0][0];
+      ex.partials[3 * blockIdx.x + 1] = (double)red[1][0];
+      ex.partials[3 * blockIdx.x + 2] = redd[0];
     }
   }
 }

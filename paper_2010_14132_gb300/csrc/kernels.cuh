@@ -12,6 +12,7 @@ struct Stats {
   double rel_update[4];
   double err_est;         // estimated relative error after the last executed pass
   double mu_w;            // weighted mean removed from the source (first solve)
+  double pmean;           // mean of the current mixed iterate p0 + q (double-float accurate)
   int done;               // later passes become no-ops once set
   int sweeps;
   int converged;
@@ -52,7 +53,7 @@ struct XinvExtra {
   float* q;             // UPDATE: read (unless first sweep) and written
   int q_valid;          // UPDATE: q holds a previous correction
   double* p_out;        // P0 (when final) / UPDATE: double output field
-  double* partials;     // per-block partial sums (2 per block)
+  double* partials;     // per-block partial sums (3 per block: delta^2, p^2, sum p)
   const int* done;      // skip when set (nullable)
 };
 
@@ -78,13 +79,14 @@ struct ThomasArgs {
   double* lowk_w;         // scratch nz * n_lowk
   Stats* stats;
   const int* done;
+  const double* target_mean;  // nullable: the (0,0) column then gives the solution mean -(*target_mean)
 };
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
 
 cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
                                const Tables& tb, float2 cx, float2 cy, const int* done, cudaStream_t st);
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
-                           double tol, cudaStream_t st);
+                           double tol, long long npoints, cudaStream_t st);
 cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
                                 double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff,
                                 float2* ac_ff, cudaStream_t st);

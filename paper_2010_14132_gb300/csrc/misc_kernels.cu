@@ -150,26 +150,30 @@ cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q,
 // (||delta_n||/||p||) / (||delta_{n-1}||/||p||) (||delta_0|| = ||p0||).
 // ---------------------------------------------------------------------------
 __global__ void k_control(Stats* st, const double* __restrict__ partials, int nblocks, int pass, int max_sweeps,
-                          double tol) {
-  __shared__ double s0[256], s1[256];
+                          double tol, long long npoints) {
+  __shared__ double s0[256], s1[256], s2[256];
   const int t = threadIdx.x;
-  double a = 0, b = 0;
+  double a = 0, b = 0, c = 0;
   for (int i = t; i < nblocks; i += blockDim.x) {
-    a += partials[2 * i];
-    b += partials[2 * i + 1];
+    a += partials[3 * i];
+    b += partials[3 * i + 1];
+    c += partials[3 * i + 2];
   }
   s0[t] = a;
   s1[t] = b;
+  s2[t] = c;
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
     if (t < h) {
       s0[t] += s0[t + h];
       s1[t] += s1[t + h];
+      s2[t] += s2[t + h];
     }
     __syncthreads();
   }
   if (t != 0) return;
   if (st->done) return;
+  st->pmean = s2[0] / (double)npoints;
   const double sd = (pass == 0) ? s1[0] : s0[0];
   const double sp = s1[0];
   st->sq_delta[pass] = sd;
@@ -198,8 +202,8 @@ __global__ void k_control(Stats* st, const double* __restrict__ partials, int nb
 }
 
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps, double tol,
-                           cudaStream_t st) {
-  k_control<<<1, 256, 0, st>>>(st_dev, partials, nblocks, pass, max_sweeps, tol);
+                           long long npoints, cudaStream_t st) {
+  k_control<<<1, 256, 0, st>>>(st_dev, partials, nblocks, pass, max_sweeps, tol, npoints);
   return cudaGetLastError();
 }
 

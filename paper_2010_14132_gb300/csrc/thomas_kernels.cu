@@ -179,7 +179,8 @@ __global__ void k_thomas_lowk(typename CT<TS>::t* __restrict__ spec, Geom g, con
                               const double* __restrict__ c, const double* __restrict__ W,
                               const double* __restrict__ lamx, const double* __restrict__ lamy, double scale,
                               const int2* __restrict__ cols, int ncols, double2* __restrict__ zs,
-                              double* __restrict__ ws, Stats* stats, const int* __restrict__ done) {
+                              double* __restrict__ ws, Stats* stats, const int* __restrict__ done,
+                              const double* __restrict__ target_mean) {
   using CS = typename CT<TS>::t;
   if (done && *done) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -255,6 +256,8 @@ __global__ void k_thomas_lowk(typename CT<TS>::t* __restrict__ spec, Geom g, con
     if (!ADJ) {
       shx = sumx / (TCm)nz;
       shy = sumy / (TCm)nz;
+      // refinement sweep: the correction also removes the mean of the current iterate
+      if (target_mean) shx += (TCm)(*target_mean);
     } else {
       for (int k = 0; k < nz; ++k) sw += (TCm)W[k];
     }
@@ -314,7 +317,7 @@ static cudaError_t thomas_lowk(const ThomasArgs& A, const Geom& g, const Tables&
   const int blocks = (A.n_lowk + threads - 1) / threads;
   k_thomas_lowk<TS, TCm, ADJ><<<blocks, threads, 0, st>>>((typename CT<TS>::t*)A.spec, g, tb.a_d, tb.c_d, tb.W_d,
                                                           tb.lamx_d, tb.lamy_d, A.scale, A.lowk_cols, A.n_lowk,
-                                                          A.lowk_z, A.lowk_w, A.stats, A.done);
+                                                          A.lowk_z, A.lowk_w, A.stats, A.done, A.target_mean);
   return cudaGetLastError();
 }
 

@@ -78,7 +78,15 @@ def test_gradient_workload_forward_512x512x64(dtype):
                                       (2048, 8, 4), (8, 4096, 2)])
 @pytest.mark.parametrize("dtype", ["fp64", "fp32"])
 def test_sizes(nx, ny, nz, dtype):
-    d = wl.random_stretched(nx, ny, nz, seed=nx * 7 + ny * 3 + nz)
+    """Radix 2/3 mixes, ragged tiles, the smallest and largest line lengths.
+
+    The horizontal spacing keeps every column well conditioned (smallest
+    horizontal eigenvalue ~ (2 pi / 8)^2 against O(1) vertical coupling): with
+    nz of 2-4 and kappa ~ 1e6 the FP64 oracle's textbook recurrence itself
+    loses ~eps*kappa, which is not what these cases are about (conditioning is
+    covered by the stretched workloads)."""
+    h = 8.0 / max(nx, ny)
+    d = wl.random_stretched(nx, ny, nz, seed=nx * 7 + ny * 3 + nz, dx=h, dy=1.3 * h)
     check(d, dtype)
 
 
@@ -112,7 +120,9 @@ def test_eigenfunctions_uniform_cube(mode, dtype):
     lam = -4 * np.sin(np.pi * a / n) ** 2 - 4 * np.sin(np.pi * b / n) ** 2 - 4 * np.sin(np.pi * c / (2 * n)) ** 2
     d = wl.Domain(n, n, n, 1.0, 1.0, np.ones(n), np.ones(n), lam * p_exact)
     p, info, _ = gpu_solve(d, dtype)
-    assert O.relative_l2(p, p_exact) < (1e-13 if dtype == "fp64" else 1e-10)
+    # the FP64 bar (the float-rounded source itself moves the exact discrete solution
+    # of the highest vertical mode by ~8e-13 from the closed form)
+    assert O.relative_l2(p, p_exact) < (1e-12 if dtype == "fp64" else 1e-10)
 
 
 @pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
@@ -120,7 +130,7 @@ def test_constant_source_gives_zero(dtype):
     d = wl.random_stretched(16, 12, 8, seed=5)
     S = np.full(d.S.shape, 3.25)
     p, info, _ = gpu_solve(d, dtype, S=S)
-    assert np.abs(p).max() < 1e-9
+    assert np.abs(p).max() < {"fp64": 1e-12, "fp32": 1e-4, "mixed": 1e-9}[dtype]
     assert abs(info["removed_weighted_mean"] - 3.25) < 1e-6
 
 
