@@ -69,8 +69,10 @@ typedef enum {
   POISSON_OPT_MAX_SWEEPS = 1,    /* mixed: refinement sweeps after the first solve, 0..3; default 3 */
   POISSON_OPT_TOLERANCE = 2,     /* mixed: target relative L2 error estimate; default 1e-11 */
   POISSON_OPT_Y_TILE = 3,        /* y-pass kx tile width (autotuner hook); 0 = plan default */
-  POISSON_OPT_PROFILE = 4        /* 1: record CUDA events around every kernel launch of this plan on
+  POISSON_OPT_PROFILE = 4,       /* 1: record CUDA events around every kernel launch of this plan on
                                     the launching stream (read with poisson_plan_profile_read) */
+  POISSON_OPT_Y_KERNEL = 5       /* y-pass kernel: 0 = persistent TMA-staged kernel where the shape
+                                    allows (default), 1 = plain shared-memory tile kernel */
 } poisson_option;
 
 /* Kernel phases reported by poisson_plan_profile_read. */

@@ -23,6 +23,7 @@ POISSON_BC_PERIODIC_XY_NEUMANN_Z = 0
 POISSON_FP64, POISSON_FP32, POISSON_MIXED = 0, 1, 2
 POISSON_OPT_LOWK_RADIUS2, POISSON_OPT_MAX_SWEEPS, POISSON_OPT_TOLERANCE, POISSON_OPT_Y_TILE = 0, 1, 2, 3
 POISSON_OPT_PROFILE = 4
+POISSON_OPT_Y_KERNEL = 5
 PHASES = ("xfwd", "yfwd", "columns", "yinv", "xinv", "residual", "control")
 
 # every symbol include/poisson.h declares

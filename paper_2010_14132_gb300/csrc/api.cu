@@ -74,7 +74,7 @@ struct poisson_plan {
   int dtype = 0;
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
-  int lowk_r2 = 64, max_sweeps = 3, ytile = 0;
+  int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0;
   double tol = 1e-11;
   Geom g{};
   Tables tb{};
@@ -290,7 +290,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
     return o;
   };
   const size_t o_a = take(nz * 8), o_c = take(nz * 8), o_W = take(nz * 8), o_af = take(nz * 4), o_cf = take(nz * 4),
-               o_aff = take(nz * 8), o_cff = take(nz * 8), o_acff = take(nz * 8), o_lxd = take(pl->nxh * 8),
+               o_aff = take(nz * 8), o_cff = take(nz * 8), o_lxd = take(pl->nxh * 8),
                o_lyd = take(ny * 8), o_lxf = take(pl->nxh * 4), o_lyf = take(ny * 4), o_twxd = take(n * 16),
                o_twrd = take(pl->nxh * 16), o_twyd = take(ny * 16), o_twxf = take(n * 8), o_twrf = take(pl->nxh * 8),
                o_twyf = take(ny * 8), o_dz = take(nz * 8), o_rho = take(nz * 8);
@@ -331,7 +331,6 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
   tb.c_f = (float*)(base + o_cf);
   tb.a_ff = (float2*)(base + o_aff);
   tb.c_ff = (float2*)(base + o_cff);
-  tb.ac_ff = (float2*)(base + o_acff);
   tb.lamx_d = (double*)(base + o_lxd);
   tb.lamy_d = (double*)(base + o_lyd);
   tb.lamx_f = (float*)(base + o_lxf);
@@ -346,8 +345,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
   pl->rho_d = (double*)(base + o_rho);
   if (ce == cudaSuccess)
     ce = launch_coefficients(pl->dz_d, pl->rho_d, nz, (double*)tb.a_d, (double*)tb.c_d, (double*)tb.W_d,
-                             (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff, (float2*)tb.ac_ff,
-                             0);
+                             (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff, 0);
   if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
   if (ce != cudaSuccess) {
     int rc = cuda_fail(ce, "plan tables");
@@ -404,6 +402,10 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value >= 0 && value <= 64)) return POISSON_ERR_INVALID_ARG;
       pl->ytile = (int)value;
       return POISSON_OK;
+    case POISSON_OPT_Y_KERNEL:
+      if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
+      pl->ykernel = (int)value;
+      return POISSON_OK;
     case POISSON_OPT_PROFILE:
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->prof.on = value != 0;
@@ -441,8 +443,7 @@ int poisson_plan_set_rho0(poisson_plan* pl, const double* rho0_dev, void* stream
   PGB_CUDA(cudaMemcpyAsync(pl->rho_d, rho0_dev, sizeof(double) * pl->nz, cudaMemcpyDeviceToDevice, st));
   const Tables& tb = pl->tb;
   PGB_CUDA(launch_coefficients(pl->dz_d, pl->rho_d, pl->nz, (double*)tb.a_d, (double*)tb.c_d, (double*)tb.W_d,
-                               (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff,
-                               (float2*)tb.ac_ff, st));
+                               (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff, st));
   return POISSON_OK;
 }
 
@@ -451,6 +452,17 @@ static int check_ws(const poisson_plan* pl, void* ws) {
   if (((uintptr_t)ws & 255) != 0) return POISSON_ERR_WORKSPACE;
   (void)pl;
   return POISSON_OK;
+}
+
+// y-pass: the persistent TMA kernel where the shape allows, else the plain one.
+static cudaError_t ypass(poisson_plan* pl, int sign, void* spec, const int* done, Stats* stats, cudaStream_t st) {
+  const bool t_double = pl->fp64();
+  if (pl->ykernel == 0) {
+    bool used = false;
+    cudaError_t e = launch_yfft_tma(t_double, sign, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, stats, st, &used);
+    if (e != cudaSuccess || used) return e;
+  }
+  return launch_yfft(t_double, sign, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, st);
 }
 
 // Forward transform -> column solve -> inverse transform of one field.
@@ -464,7 +476,7 @@ static cudaError_t run_pipeline(poisson_plan* pl, const void* in, int in_double,
   prof_end(pl, ps, st);
   if (e != cudaSuccess) return e;
   ps = prof_begin(pl, POISSON_PHASE_YFWD, st);
-  e = launch_yfft(t_double, -1, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, st);
+  e = ypass(pl, -1, spec, done, stats, st);
   prof_end(pl, ps, st);
   if (e != cudaSuccess) return e;
   ThomasArgs A{};
@@ -486,7 +498,7 @@ static cudaError_t run_pipeline(poisson_plan* pl, const void* in, int in_double,
   prof_end(pl, ps, st);
   if (e != cudaSuccess) return e;
   ps = prof_begin(pl, POISSON_PHASE_YINV, st);
-  e = launch_yfft(t_double, +1, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, st);
+  e = ypass(pl, +1, spec, done, stats, st);
   prof_end(pl, ps, st);
   return e;
 }
@@ -554,8 +566,8 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
     PGB_CUDA(e);
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
       ps = prof_begin(pl, POISSON_PHASE_RESIDUAL, st);
-      e = launch_residual_ff((const double*)S, p0, sweep > 1 ? q : nullptr, r, pl->g, pl->tb, pl->cx, pl->cy, done,
-                             st);
+      e = launch_residual_ff((const double*)S, p0, sweep > 1 ? q : nullptr, r, pl->g, pl->tb, pl->cx, pl->cy,
+                             &stats->mu_w, done, st);
       prof_end(pl, ps, st);
       PGB_CUDA(e);
       PGB_CUDA(run_pipeline(pl, r, 0, ws, st, 0, done, &stats->pmean));

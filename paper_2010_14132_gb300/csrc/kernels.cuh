@@ -24,8 +24,8 @@ struct Tables {
   // vertical coefficients, level k
   const double* a_d; const double* c_d; const double* W_d;
   const float* a_f; const float* c_f;
-  // double-float splits for the residual: a, c, a+c (hi, lo)
-  const float2* a_ff; const float2* c_ff; const float2* ac_ff;
+  // double-float splits for the residual: a, c (hi, lo)
+  const float2* a_ff; const float2* c_ff;
   // horizontal eigenvalues: lamx[kx], kx < nxh; lamy[ky], ky < ny
   const double* lamx_d; const double* lamy_d;
   const float* lamx_f; const float* lamy_f;
@@ -62,6 +62,9 @@ cudaError_t launch_xfwd(int ti_is_double, int t_is_double, const void* in, void*
                         const FftPlan& fx, const Tables& tb, const int* done, cudaStream_t st);
 cudaError_t launch_yfft(int t_is_double, int sign, void* spec, const Geom& g, const FftPlan& fy,
                         const Tables& tb, int tile, const int* done, cudaStream_t st);
+// Persistent TMA y-pass; *used = false when the shape is not supported (caller falls back).
+cudaError_t launch_yfft_tma(int t_is_double, int sign, void* spec, const Geom& g, const FftPlan& fy,
+                            const Tables& tb, int tile, const int* done, Stats* stats, cudaStream_t st, bool* used);
 cudaError_t launch_xinv(int t_is_double, int to_is_double, int mode, const void* spec, void* out,
                         const Geom& g, const FftPlan& fx, const Tables& tb, const XinvExtra& ex,
                         int* nblocks_out, cudaStream_t st);
@@ -84,12 +87,12 @@ struct ThomasArgs {
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
 
 cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
-                               const Tables& tb, float2 cx, float2 cy, const int* done, cudaStream_t st);
+                               const Tables& tb, float2 cx, float2 cy, const double* mu_w, const int* done,
+                               cudaStream_t st);
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
                            double tol, long long npoints, cudaStream_t st);
 cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
-                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff,
-                                float2* ac_ff, cudaStream_t st);
+                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff, cudaStream_t st);
 cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math*/, const void* g, const void* p, const Geom& g_, const Tables& tb,
                         const double* dz, const double* rho0, double* partials, int nparts_max,
                         double* grho, cudaStream_t st);

@@ -16,7 +16,7 @@ __device__ __forceinline__ float2 split_ff(double x) {
 
 __global__ void k_coefficients(const double* __restrict__ dz, const double* __restrict__ rho, int nz,
                                double* a_d, double* c_d, double* W_d, float* a_f, float* c_f, float2* a_ff,
-                               float2* c_ff, float2* ac_ff) {
+                               float2* c_ff) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nz; k += blockDim.x * gridDim.x) {
     const double W = rho[k] * dz[k];
     const double up = (k + 1 < nz) ? (0.5 * (rho[k] + rho[k + 1])) / (0.5 * (dz[k] + dz[k + 1])) : 0.0;
@@ -29,19 +29,23 @@ __global__ void k_coefficients(const double* __restrict__ dz, const double* __re
     c_f[k] = __double2float_rn(c);
     a_ff[k] = split_ff(a);
     c_ff[k] = split_ff(c);
-    ac_ff[k] = split_ff(a + c);
   }
 }
 
 cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
-                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff,
-                                float2* ac_ff, cudaStream_t st) {
-  k_coefficients<<<(nz + 127) / 128, 128, 0, st>>>(dz, rho0, nz, a_d, c_d, W_d, a_f, c_f, a_ff, c_ff, ac_ff);
+                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff, cudaStream_t st) {
+  k_coefficients<<<(nz + 127) / 128, 128, 0, st>>>(dz, rho0, nz, a_d, c_d, W_d, a_f, c_f, a_ff, c_ff);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Residual r = S - L (p0 + q) in double-float arithmetic (mixed path).
+// Residual r = S - mu_W - L (p0 + q) in double-float arithmetic (mixed path).
+//
+// mu_W (the weighted mean of S, found by the first solve) is removed here: it is
+// outside the range of L, and left in r it would dominate r's dynamic range, so
+// that the float rounding of r and of its transform would swamp the small
+// compatible part (most visibly in the kx = 0 columns, whose y-transform carries
+// the constant).  The correction solve removes what little constant remains.
 //
 // The refinement needs r to about 2^-44 of |L||p| (the 7-point sum cancels by
 // orders of magnitude for the smooth, large pressure field), which FP32 alone
@@ -64,7 +68,7 @@ template <bool HAS_Q>
 __global__ void __launch_bounds__(256) k_residual_ff(const double* __restrict__ S, const float* __restrict__ p0,
                                                      const float* __restrict__ q, float* __restrict__ r, Geom g,
                                                      const float2* __restrict__ a_ff, const float2* __restrict__ c_ff,
-                                                     const float2* __restrict__ ac_ff, float2 cx, float2 cy,
+                                                     float2 cx, float2 cy, const double* __restrict__ mu_w,
                                                      const int* __restrict__ done) {
   if (done && *done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -107,38 +111,41 @@ __global__ void __launch_bounds__(256) k_residual_ff(const double* __restrict__ 
   FF ty;
   two_prod(cy.x, s2, ty.h, ty.l);
   ty.l = __fmaf_rn(cy.x, dl, __fmaf_rn(cy.y, s2, ty.l));
-  // z: a pd + c pu - (a + c) pc   (a = 0 at the bottom, c = 0 at the top)
-  const float2 A = a_ff[k], Cc = c_ff[k], AC = ac_ff[k];
-  float p1, l1, p2, l2, p3, l3;
-  two_prod(A.x, pd, p1, l1);
-  two_prod(Cc.x, pu, p2, l2);
-  two_prod(AC.x, pc, p3, l3);
-  two_sum(p1, p2, s1, e1);
-  two_sum(s1, -p3, s2, e2);
-  float zl = (l1 + l2 - l3) + (e1 + e2);
-  zl = __fmaf_rn(A.y, pd, zl);
-  zl = __fmaf_rn(Cc.y, pu, zl);
-  zl = __fmaf_rn(-AC.y, pc, zl);
-  zl = __fmaf_rn(A.x, qd, zl);
-  zl = __fmaf_rn(Cc.x, qu, zl);
-  zl = __fmaf_rn(-AC.x, qc, zl);
-  FF tz{s2, zl};
+  // z: a (pd - pc) + c (pu - pc)   (a = 0 at the bottom, c = 0 at the top).
+  // Differences first: a constant field maps to exactly zero whatever the
+  // rounding of the coefficient splits.  Summing a pd + c pu - (a+c) pc instead
+  // leaves a row-sum mismatch of ~2^-48 (a+c) that the near-null vertical mode of
+  // the lowest-|k| columns amplifies by their condition number (1e-10 and worse).
+  const float2 A = a_ff[k], Cc = c_ff[k];
+  float dd, ed, du, eu, p1, l1, p2, l2;
+  two_sum(pd, -pc, dd, ed);
+  two_sum(pu, -pc, du, eu);
+  two_prod(A.x, dd, p1, l1);
+  two_prod(Cc.x, du, p2, l2);
+  l1 = __fmaf_rn(A.x, ed + (qd - qc), __fmaf_rn(A.y, dd, l1));
+  l2 = __fmaf_rn(Cc.x, eu + (qu - qc), __fmaf_rn(Cc.y, du, l2));
+  two_sum(p1, p2, s2, e2);
+  FF tz{s2, (l1 + l2) + e2};
   FF Lp = ff_add(ff_add(tx, ty), tz);
-  float sh, sl;
+  float sh, sl, mh, ml, th, tl;
   d2ff_int(S[idx], sh, sl);
+  d2ff_int(*mu_w, mh, ml);
+  two_sum(sh, -mh, th, tl);
+  tl += sl - ml;
   float rh, rl;
-  two_sum(sh, -Lp.h, rh, rl);
-  r[idx] = rh + (rl + (sl - Lp.l));
+  two_sum(th, -Lp.h, rh, rl);
+  r[idx] = rh + (rl + (tl - Lp.l));
 }
 
 cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
-                               const Tables& tb, float2 cx, float2 cy, const int* done, cudaStream_t st) {
+                               const Tables& tb, float2 cx, float2 cy, const double* mu_w, const int* done,
+                               cudaStream_t st) {
   const dim3 block(256);
   const dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
   if (q)
-    k_residual_ff<true><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, tb.ac_ff, cx, cy, done);
+    k_residual_ff<true><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, cx, cy, mu_w, done);
   else
-    k_residual_ff<false><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, tb.ac_ff, cx, cy, done);
+    k_residual_ff<false><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, cx, cy, mu_w, done);
   return cudaGetLastError();
 }
 

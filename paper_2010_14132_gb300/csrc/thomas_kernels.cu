@@ -14,49 +14,9 @@
 // The spectrum is scaled by 1/(nx ny) here, which makes the inverse transforms
 // unnormalised.
 #include "kernels.cuh"
+#include "async_copy.cuh"
 
 namespace pgb {
-
-// ---------------------------------------------------------------------------
-// mbarrier / bulk-copy primitives (sm_90+ PTX)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after max_iter polls (each poll may suspend briefly).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long max_iter) {
-  for (long long i = 0; i < max_iter; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-constexpr long long kWaitPolls = 1LL << 22;
 
 template <typename T> __device__ __forceinline__ T rcp(T u);
 template <> __device__ __forceinline__ float rcp<float>(float u) { return __frcp_rn(u); }
@@ -203,7 +163,8 @@ __global__ void k_thomas_lowk(typename CT<TS>::t* __restrict__ spec, Geom g, con
     }
     mean_x /= sw;
     mean_y /= sw;
-    if (!ADJ && stats) stats->mu_w = (double)mean_x * scale;
+    // only the first solve records mu_W (a refinement correction solve has a target mean)
+    if (!ADJ && stats && !target_mean) stats->mu_w = (double)mean_x * scale;
   }
   const TCm s = singular ? (TCm)0 : -((TCm)lamx[kx] + (TCm)lamy[ky]);
   const TCm ms = -(TCm)scale;

@@ -40,7 +40,7 @@ class Plan:
     """
 
     def __init__(self, nx, ny, nz, dx, dy, dz, rho0, dtype="fp64", device=None,
-                 lowk_radius2=None, max_sweeps=None, tolerance=None, y_tile=None):
+                 lowk_radius2=None, max_sweeps=None, tolerance=None, y_tile=None, y_kernel=None):
         if dtype not in DTYPES:
             raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
@@ -63,6 +63,8 @@ class Plan:
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_TOLERANCE, tolerance)
         if y_tile is not None:
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_Y_TILE, y_tile)
+        if y_kernel is not None:
+            N.poisson_plan_set_option(self._h, N.POISSON_OPT_Y_KERNEL, y_kernel)
         self._ws = None
 
     # -- lifetime ------------------------------------------------------------

@@ -77,7 +77,8 @@ def test_gradient_workload_forward_512x512x64(dtype):
                                       (48, 12, 33), (8, 16, 130), (18, 27, 6), (36, 8, 3), (64, 64, 512),
                                       (2048, 8, 4), (8, 4096, 2)])
 @pytest.mark.parametrize("dtype", ["fp64", "fp32"])
-def test_sizes(nx, ny, nz, dtype):
+@pytest.mark.parametrize("y_kernel", [0, 1])
+def test_sizes(nx, ny, nz, dtype, y_kernel):
     """Radix 2/3 mixes, ragged tiles, the smallest and largest line lengths.
 
     The horizontal spacing keeps every column well conditioned (smallest
@@ -87,7 +88,7 @@ def test_sizes(nx, ny, nz, dtype):
     covered by the stretched workloads)."""
     h = 8.0 / max(nx, ny)
     d = wl.random_stretched(nx, ny, nz, seed=nx * 7 + ny * 3 + nz, dx=h, dy=1.3 * h)
-    check(d, dtype)
+    check(d, dtype, y_kernel=y_kernel)
 
 
 @pytest.mark.parametrize("nx,ny,nz", [(384, 384, 48), (64, 128, 96), (512, 256, 32)])
