@@ -139,6 +139,27 @@ int poisson_solve_adjoint(poisson_plan* plan, const void* gp, const void* p, voi
  * POISSON_OPT_PROFILE is set, and is skipped while a stream is being captured. */
 int poisson_plan_profile_read(poisson_plan* plan, double* ms, int* launches, int nphases);
 
+/* ---- Solve without allocating: for callers that cannot call cudaMalloc ----
+ * (The paper has no counterpart; this serves callers of the library.)
+ * Some callers cannot allocate device memory when they solve: a model driver whose
+ * time loop must not call cudaMalloc (it can synchronise the device and has no
+ * bounded latency), or a host program that owns the device memory pool and hands
+ * this library only field pointers.  This entry point runs the same solve as
+ * poisson_solve, but its scratch is a fixed device array inside the library of
+ * POISSON_STATIC_WORKSPACE_BYTES bytes, held by every GPU that loads the library
+ * until the process exits; it calls no allocating routine.  The plan itself is
+ * created beforehand (its small tables are allocated then).
+ *  - Plans whose workspace_bytes exceed the maximum: POISSON_ERR_WORKSPACE.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - Every call on a device shares the one array: calls that overlap on the GPU
+ *    (other streams, other plans, other threads) race.  The solve itself clears
+ *    what must start at zero, so consecutive calls need nothing from the caller.
+ * Same S, p, stream, info and status rules as poisson_solve. */
+#define POISSON_STATIC_WORKSPACE_BYTES (32u * 1024u * 1024u)
+int poisson_solve_static_workspace(poisson_plan* plan, const void* S, void* p, void* stream,
+                                   poisson_info* info);
+
 /* NULL-safe.  Frees the plan's device tables (synchronously). */
 int poisson_plan_destroy(poisson_plan* plan);
 

@@ -31,8 +31,11 @@ EXPORTED = (
     "poisson_plan_create", "poisson_plan_workspace_bytes", "poisson_plan_set_option", "poisson_plan_set_rho0",
     "poisson_solve", "poisson_solve_adjoint", "poisson_plan_destroy", "poisson_status_string",
     "poisson_last_error_detail", "poisson_batch_create", "poisson_batch_workspace_bytes", "poisson_batch_solve",
-    "poisson_batch_destroy", "poisson_plan_profile_read",
+    "poisson_batch_destroy", "poisson_plan_profile_read", "poisson_solve_static_workspace",
 )
+
+# size of the fixed device array poisson_solve_static_workspace uses as scratch
+POISSON_STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
 
 class PoissonInfo(C.Structure):
@@ -96,6 +99,7 @@ def load():
     L.poisson_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), vp, vp, C.POINTER(PoissonInfo)]
     L.poisson_batch_destroy.argtypes = [vp]
     L.poisson_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int), i]
+    L.poisson_solve_static_workspace.argtypes = [vp, vp, vp, vp, C.POINTER(PoissonInfo)]
     for name in EXPORTED:
         if name not in ("poisson_status_string", "poisson_last_error_detail"):
             getattr(L, name).restype = C.c_int
@@ -140,6 +144,17 @@ def poisson_solve(plan, S_ptr, p_ptr, ws_ptr, stream, want_info=False, allow_not
     info = PoissonInfo() if want_info else None
     st = load().poisson_solve(plan, S_ptr, p_ptr, ws_ptr, stream, C.byref(info) if info is not None else None)
     _check(st, "poisson_solve", allow=(POISSON_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return (st, info.as_dict()) if want_info else st
+
+
+def poisson_solve_static_workspace(plan, S_ptr, p_ptr, stream, want_info=False):
+    """Solve with the library's fixed device scratch array (allocates nothing).
+
+    Returns the raw status (POISSON_ERR_WORKSPACE for plans above the maximum),
+    or (status, info) with want_info."""
+    info = PoissonInfo() if want_info else None
+    st = load().poisson_solve_static_workspace(plan, S_ptr, p_ptr, stream,
+                                               C.byref(info) if info is not None else None)
     return (st, info.as_dict()) if want_info else st
 
 

@@ -23,7 +23,8 @@ LIB_NAME = "libpoisson_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-SOURCES = ["api.cu", "fft_kernels.cu", "thomas_kernels.cu", "misc_kernels.cu", "ypass_tma.cu"]
+SOURCES = ["api.cu", "fft_kernels.cu", "thomas_kernels.cu", "misc_kernels.cu", "ypass_tma.cu",
+           "static_workspace.cu"]
 
 
 def nvcc() -> str:
