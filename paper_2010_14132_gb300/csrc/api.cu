@@ -16,14 +16,14 @@ namespace {
 
 thread_local char g_last_error[256] = "";
 
-int cuda_fail(cudaError_t e, const char* where) {
-  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+int cuda_fail(cudaError_t e, const char* where, int line = 0) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s (api.cu:%d): %s", where, line, cudaGetErrorString(e));
   return POISSON_ERR_CUDA;
 }
-#define PGB_CUDA(call)                                   \
-  do {                                                   \
-    cudaError_t e_ = (call);                             \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+#define PGB_CUDA(call)                                             \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call, __LINE__);  \
   } while (0)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -359,12 +359,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
   }
   {
     // x-pass block count (rows per CTA as chosen by the launcher)
-    const int nl = pl->fx.n / pl->fx.E;
-    int rbk = 256 / nl;
-    if (rbk < 1) rbk = 1;
-    while (rbk > 1 && (size_t)rbk * (pl->fx.n + 1) * pl->csize() > 64 * 1024) rbk >>= 1;
-    const long long nrows = (long long)ny * nz;
-    pl->xinv_blocks = (int)((nrows + rbk - 1) / rbk);
+    pl->xinv_blocks = xpass_blocks(pl->g, pl->fx, pl->csize());
     long long nb = ((long long)nx * ny + 255) / 256;
     pl->grho_nb = (int)(nb > 1024 ? 1024 : nb);
   }
@@ -567,7 +562,7 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
       ps = prof_begin(pl, POISSON_PHASE_RESIDUAL, st);
       e = launch_residual_ff((const double*)S, p0, sweep > 1 ? q : nullptr, r, pl->g, pl->tb, pl->cx, pl->cy,
-                             &stats->mu_w, done, st);
+                             &stats->mu_ff, done, st);
       prof_end(pl, ps, st);
       PGB_CUDA(e);
       PGB_CUDA(run_pipeline(pl, r, 0, ws, st, 0, done, &stats->pmean));

@@ -76,14 +76,29 @@ template <int R, int SIGN, typename T> __device__ __forceinline__ void dft_r(typ
   else dft8<SIGN, typename CT<T>::t, T>(v);
 }
 
+// Shared-memory address of element idx of a line.
+//  Strided: line-interleaved tiles (element idx of line l at idx*es + l).
+//  Swizzled: contiguous lines; the low 4 bits of the complex index are XORed with
+//  the next 4, a bijection within each 16-element block that spreads the
+//  power-of-two strides of the early Stockham writes (stride R) over all banks.
+struct Strided {
+  int es;
+  __device__ __forceinline__ int operator()(int idx) const { return idx * es; }
+};
+struct Swizzled {
+  __device__ __forceinline__ int operator()(int idx) const { return idx ^ ((idx >> 4) & 15); }
+};
+// line length padded so that the swizzle stays inside the line
+__host__ __device__ constexpr int swizzled_stride(int len) { return (len + 15) / 16 * 16; }
+
 // Synchronisation of the threads that share one line.
 struct SyncBlock { __device__ __forceinline__ void operator()() const { __syncthreads(); } };
 struct SyncWarp { __device__ __forceinline__ void operator()() const { __syncwarp(); } };
 
-// One stage on one line: element idx of the line lives at line[idx * es].
+// One stage on one line: element idx of the line lives at line[addr(idx)].
 // lane in [0, nl) indexes the threads of the line; nl * E == n.
-template <int R, int E, int SIGN, typename T, typename Sync>
-__device__ __forceinline__ void stockham_stage(typename CT<T>::t* line, int es, int n, int Ns, int lane,
+template <int R, int E, int SIGN, typename T, typename Sync, typename Addr>
+__device__ __forceinline__ void stockham_stage(typename CT<T>::t* line, Addr addr, int n, int Ns, int lane,
                                                int nl, const typename CT<T>::t* __restrict__ tw,
                                                Sync sync) {
   using C = typename CT<T>::t;
@@ -94,7 +109,7 @@ __device__ __forceinline__ void stockham_stage(typename CT<T>::t* line, int es, 
   for (int q = 0; q < B; ++q) {
     const int j = lane + nl * q;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = line[(j + r * m) * es];
+    for (int r = 0; r < R; ++r) v[q * R + r] = line[addr(j + r * m)];
   }
   sync();
   const int stride = n / (Ns * R);
@@ -109,31 +124,31 @@ __device__ __forceinline__ void stockham_stage(typename CT<T>::t* line, int es, 
     dft_r<R, SIGN, T>(&v[q * R]);
     const int d = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) line[(d + r * Ns) * es] = v[q * R + r];
+    for (int r = 0; r < R; ++r) line[addr(d + r * Ns)] = v[q * R + r];
   }
   sync();
 }
 
 // All stages of a plan.  E is the compile-time elements-per-thread count the
 // plan was built for; radices that do not divide E never occur in such a plan.
-template <int E, int SIGN, typename T, typename Sync>
-__device__ __forceinline__ void stockham_run(typename CT<T>::t* line, int es, const FftPlan& P, int lane,
+template <int E, int SIGN, typename T, typename Sync, typename Addr>
+__device__ __forceinline__ void stockham_run(typename CT<T>::t* line, Addr addr, const FftPlan& P, int lane,
                                              const typename CT<T>::t* __restrict__ tw, Sync sync) {
   const int nl = P.n / E;
   int Ns = 1;
   for (int s = 0; s < P.nstages; ++s) {
     const int R = P.radix[s];
     if constexpr (E % 8 == 0) {
-      if (R == 8) { stockham_stage<8, E, SIGN, T>(line, es, P.n, Ns, lane, nl, tw, sync); Ns *= 8; continue; }
+      if (R == 8) { stockham_stage<8, E, SIGN, T>(line, addr, P.n, Ns, lane, nl, tw, sync); Ns *= 8; continue; }
     }
     if constexpr (E % 4 == 0) {
-      if (R == 4) { stockham_stage<4, E, SIGN, T>(line, es, P.n, Ns, lane, nl, tw, sync); Ns *= 4; continue; }
+      if (R == 4) { stockham_stage<4, E, SIGN, T>(line, addr, P.n, Ns, lane, nl, tw, sync); Ns *= 4; continue; }
     }
     if constexpr (E % 3 == 0) {
-      if (R == 3) { stockham_stage<3, E, SIGN, T>(line, es, P.n, Ns, lane, nl, tw, sync); Ns *= 3; continue; }
+      if (R == 3) { stockham_stage<3, E, SIGN, T>(line, addr, P.n, Ns, lane, nl, tw, sync); Ns *= 3; continue; }
     }
     if constexpr (E % 2 == 0) {
-      if (R == 2) { stockham_stage<2, E, SIGN, T>(line, es, P.n, Ns, lane, nl, tw, sync); Ns *= 2; continue; }
+      if (R == 2) { stockham_stage<2, E, SIGN, T>(line, addr, P.n, Ns, lane, nl, tw, sync); Ns *= 2; continue; }
     }
   }
 }

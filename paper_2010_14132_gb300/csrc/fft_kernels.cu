@@ -13,6 +13,9 @@
 //    bins kx = 0 and kx = nx/2 contribute their real parts only.  Its epilogue
 //    writes the output field and, in the mixed-precision path, performs the
 //    refinement update and the norm partial sums.
+#include <mutex>
+#include <unordered_map>
+
 #include "kernels.cuh"
 
 namespace pgb {
@@ -37,7 +40,8 @@ __global__ void __launch_bounds__(256) k_xfwd(const TI* __restrict__ in, typenam
   const int lane = threadIdx.x, ty = threadIdx.y;
   const long long row = (long long)blockIdx.x * blockDim.y + ty;
   const bool valid = row < nrows;
-  C* line = sm + ty * (n + 1);
+  C* line = sm + ty * swizzled_stride(n + 1);
+  const Swizzled sw{};
   const typename V2<TI>::t* src = reinterpret_cast<const typename V2<TI>::t*>(in + (valid ? row : 0) * g.nx);
 #pragma unroll
   for (int q = 0; q < E; ++q) {
@@ -48,14 +52,14 @@ __global__ void __launch_bounds__(256) k_xfwd(const TI* __restrict__ in, typenam
       z.x = Cvt<TI, T>::f(v.x);
       z.y = Cvt<TI, T>::f(v.y);
     }
-    line[m] = z;
+    line[sw(m)] = z;
   }
   __syncthreads();
-  stockham_run<E, -1, T>(line, 1, fx, lane, twx, SyncBlock());
+  stockham_run<E, -1, T>(line, sw, fx, lane, twx, SyncBlock());
   C* dst = spec + (valid ? row : 0) * g.P;
   for (int k = lane; k <= n; k += nl) {
-    const C zk = line[k == n ? 0 : k];
-    const C zc = cconj(line[k == 0 ? 0 : n - k]);
+    const C zk = line[sw(k == n ? 0 : k)];
+    const C zc = cconj(line[sw(k == 0 ? 0 : n - k)]);
     const C ev = make_c<T>((T)0.5 * (zk.x + zc.x), (T)0.5 * (zk.y + zc.y));
     const C dd = make_c<T>((T)0.5 * (zk.x - zc.x), (T)0.5 * (zk.y - zc.y));
     const C od = make_c<T>(dd.y, -dd.x);  // -i * dd
@@ -81,16 +85,25 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
   const int lane = threadIdx.x, ty = threadIdx.y;
   const long long row = (long long)blockIdx.x * blockDim.y + ty;
   const bool valid = row < nrows;
-  C* line = sm + ty * (n + 1);
+  C* line = sm + ty * swizzled_stride(n + 1);
+  const Swizzled sw{};
   const C* src = spec + (valid ? row : 0) * g.P;
-  for (int k = lane; k <= n; k += nl) line[k] = valid ? src[k] : make_c<T>(0, 0);
+  {
+    // E independent loads per thread (k < n), then the Nyquist entry k = n
+    C buf[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) buf[q] = valid ? src[lane + nl * q] : make_c<T>(0, 0);
+#pragma unroll
+    for (int q = 0; q < E; ++q) line[sw(lane + nl * q)] = buf[q];
+    if (lane == 0) line[sw(n)] = valid ? src[n] : make_c<T>(0, 0);
+  }
   __syncthreads();
   C zr[E];
 #pragma unroll
   for (int q = 0; q < E; ++q) {
     const int k = lane + nl * q;
-    C xk = line[k];
-    C xc = cconj(line[n - k]);
+    C xk = line[sw(k)];
+    C xc = cconj(line[sw(n - k)]);
     if (k == 0) {  // self-conjugate bins: real parts only
       xk.y = 0;
       xc.y = 0;
@@ -101,9 +114,9 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
   }
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < E; ++q) line[lane + nl * q] = zr[q];
+  for (int q = 0; q < E; ++q) line[sw(lane + nl * q)] = zr[q];
   __syncthreads();
-  stockham_run<E, +1, T>(line, 1, fx, lane, twx, SyncBlock());
+  stockham_run<E, +1, T>(line, sw, fx, lane, twx, SyncBlock());
 
   const long long base = (valid ? row : 0) * g.nx;
   float acc0 = 0.f, acc1 = 0.f;
@@ -111,7 +124,7 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
 #pragma unroll
   for (int q = 0; q < E; ++q) {
     const int m = lane + nl * q;
-    const C z = line[m];
+    const C z = line[sw(m)];
     if (!valid) continue;
     if constexpr (MODE == XINV_PLAIN) {
       typename V2<TO>::t v;
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(ypass_max_threads(E)) k_yfft(typename CT<T>::t
     sm[i * TK + l] = vcol ? base[(long long)i * g.P + l] : make_c<T>(0, 0);
   }
   __syncthreads();
-  stockham_run<E, SIGN, T>(sm + l, TK, fy, lane, twy, SyncBlock());
+  stockham_run<E, SIGN, T>(sm + l, Strided{TK}, fy, lane, twy, SyncBlock());
   if (vcol) {
 #pragma unroll
     for (int q = 0; q < E; ++q) {
@@ -230,9 +243,17 @@ bool fft_e_supported(int E) {
 
 static constexpr int kMaxDynSmem = 227 * 1024;
 
+// Opt a kernel in to `bytes` of dynamic shared memory.  Always done (not only
+// above 48 KB): static shared memory counts against the same default limit.
 template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> granted;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = granted[reinterpret_cast<const void*>(kernel)];
+  if (have >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
 }
 
 // rows per CTA for the x-pass
@@ -240,8 +261,14 @@ static int xpass_rows(int n, int E, size_t csize) {
   const int nl = n / E;
   int rb = 256 / nl;
   if (rb < 1) rb = 1;
-  while (rb > 1 && (size_t)rb * (n + 1) * csize > 64 * 1024) rb >>= 1;
+  while (rb > 1 && (size_t)rb * swizzled_stride(n + 1) * csize > 64 * 1024) rb >>= 1;
   return rb;
+}
+
+int xpass_blocks(const Geom& g, const FftPlan& fx, size_t csize) {
+  const long long nrows = (long long)g.ny * g.nz;
+  const int rb = xpass_rows(fx.n, fx.E, csize);
+  return (int)((nrows + rb - 1) / rb);
 }
 
 template <typename TI, typename T>
@@ -253,7 +280,7 @@ static cudaError_t xfwd_t(const TI* in, typename CT<T>::t* spec, const Geom& g, 
   const int rb = xpass_rows(n, fx.E, sizeof(typename CT<T>::t));
   const dim3 block(n / fx.E, rb);
   const long long nb = (nrows + rb - 1) / rb;
-  const size_t smem = (size_t)rb * (n + 1) * sizeof(typename CT<T>::t);
+  const size_t smem = (size_t)rb * swizzled_stride(n + 1) * sizeof(typename CT<T>::t);
   if (smem > kMaxDynSmem || nb > 0x7fffffffLL) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   PGB_E_SWITCH(fx.E, {
@@ -285,7 +312,7 @@ static cudaError_t xinv_t(const typename CT<T>::t* spec, TO* out, const Geom& g,
   const int rb = xpass_rows(n, fx.E, sizeof(typename CT<T>::t));
   const dim3 block(n / fx.E, rb);
   const long long nb = (nrows + rb - 1) / rb;
-  const size_t smem = (size_t)rb * (n + 1) * sizeof(typename CT<T>::t);
+  const size_t smem = (size_t)rb * swizzled_stride(n + 1) * sizeof(typename CT<T>::t);
   if (nblocks_out) *nblocks_out = (int)nb;
   if (smem > kMaxDynSmem || nb > 0x7fffffffLL) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;

@@ -1,5 +1,6 @@
 // Internal launch interface between the C ABI (api.cu) and the kernel units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include "fft_engine.cuh"
 
@@ -13,6 +14,7 @@ struct Stats {
   double err_est;         // estimated relative error after the last executed pass
   double mu_w;            // weighted mean removed from the source (first solve)
   double pmean;           // mean of the current mixed iterate p0 + q (double-float accurate)
+  float2 mu_ff;           // mu_w as a double-float pair (set after the first solve)
   int done;               // later passes become no-ops once set
   int sweeps;
   int converged;
@@ -62,6 +64,10 @@ cudaError_t launch_xfwd(int ti_is_double, int t_is_double, const void* in, void*
                         const FftPlan& fx, const Tables& tb, const int* done, cudaStream_t st);
 cudaError_t launch_yfft(int t_is_double, int sign, void* spec, const Geom& g, const FftPlan& fy,
                         const Tables& tb, int tile, const int* done, cudaStream_t st);
+// 2-D tensor map over 8-byte elements (dim0 contiguous, dim1 rows of row_stride_bytes);
+// false when the driver entry point is unavailable or the shape is rejected.
+bool encode_tensor_2d(CUtensorMap* tm, void* base, size_t elem_bytes, unsigned long long dim0,
+                      unsigned long long dim1, unsigned long long row_stride_bytes, unsigned box0, unsigned box1);
 // Persistent TMA y-pass; *used = false when the shape is not supported (caller falls back).
 cudaError_t launch_yfft_tma(int t_is_double, int sign, void* spec, const Geom& g, const FftPlan& fy,
                             const Tables& tb, int tile, const int* done, Stats* stats, cudaStream_t st, bool* used);
@@ -87,7 +93,7 @@ struct ThomasArgs {
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
 
 cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
-                               const Tables& tb, float2 cx, float2 cy, const double* mu_w, const int* done,
+                               const Tables& tb, float2 cx, float2 cy, const float2* mu_ff, const int* done,
                                cudaStream_t st);
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
                            double tol, long long npoints, cudaStream_t st);
@@ -96,6 +102,9 @@ cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, do
 cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math*/, const void* g, const void* p, const Geom& g_, const Tables& tb,
                         const double* dz, const double* rho0, double* partials, int nparts_max,
                         double* grho, cudaStream_t st);
+
+// Number of CTAs (and so partial-sum slots) of an x-pass launch.
+int xpass_blocks(const Geom& g, const FftPlan& fx, size_t csize);
 
 // Elements per thread the FFT kernels are instantiated for.
 bool fft_e_supported(int E);

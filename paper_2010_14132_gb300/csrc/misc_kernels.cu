@@ -68,7 +68,7 @@ template <bool HAS_Q>
 __global__ void __launch_bounds__(256) k_residual_ff(const double* __restrict__ S, const float* __restrict__ p0,
                                                      const float* __restrict__ q, float* __restrict__ r, Geom g,
                                                      const float2* __restrict__ a_ff, const float2* __restrict__ c_ff,
-                                                     float2 cx, float2 cy, const double* __restrict__ mu_w,
+                                                     float2 cx, float2 cy, const float2* __restrict__ mu_ff,
                                                      const int* __restrict__ done) {
   if (done && *done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,25 +127,25 @@ __global__ void __launch_bounds__(256) k_residual_ff(const double* __restrict__ 
   two_sum(p1, p2, s2, e2);
   FF tz{s2, (l1 + l2) + e2};
   FF Lp = ff_add(ff_add(tx, ty), tz);
-  float sh, sl, mh, ml, th, tl;
+  float sh, sl, th, tl;
   d2ff_int(S[idx], sh, sl);
-  d2ff_int(*mu_w, mh, ml);
-  two_sum(sh, -mh, th, tl);
-  tl += sl - ml;
+  const float2 mu = *mu_ff;
+  two_sum(sh, -mu.x, th, tl);
+  tl += sl - mu.y;
   float rh, rl;
   two_sum(th, -Lp.h, rh, rl);
   r[idx] = rh + (rl + (tl - Lp.l));
 }
 
 cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
-                               const Tables& tb, float2 cx, float2 cy, const double* mu_w, const int* done,
+                               const Tables& tb, float2 cx, float2 cy, const float2* mu_ff, const int* done,
                                cudaStream_t st) {
   const dim3 block(256);
   const dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
   if (q)
-    k_residual_ff<true><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, cx, cy, mu_w, done);
+    k_residual_ff<true><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, cx, cy, mu_ff, done);
   else
-    k_residual_ff<false><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, cx, cy, mu_w, done);
+    k_residual_ff<false><<<grid, block, 0, st>>>(S, p0, q, r, g, tb.a_ff, tb.c_ff, cx, cy, mu_ff, done);
   return cudaGetLastError();
 }
 
@@ -158,7 +158,7 @@ cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q,
 // ---------------------------------------------------------------------------
 __global__ void k_control(Stats* st, const double* __restrict__ partials, int nblocks, int pass, int max_sweeps,
                           double tol, long long npoints) {
-  __shared__ double s0[256], s1[256], s2[256];
+  __shared__ double s0[1024], s1[1024], s2[1024];
   const int t = threadIdx.x;
   double a = 0, b = 0, c = 0;
   for (int i = t; i < nblocks; i += blockDim.x) {
@@ -181,6 +181,7 @@ __global__ void k_control(Stats* st, const double* __restrict__ partials, int nb
   if (t != 0) return;
   if (st->done) return;
   st->pmean = s2[0] / (double)npoints;
+  if (pass == 0) st->mu_ff = split_ff(st->mu_w);   // for the residual kernels of the sweeps
   const double sd = (pass == 0) ? s1[0] : s0[0];
   const double sp = s1[0];
   st->sq_delta[pass] = sd;
@@ -210,7 +211,7 @@ __global__ void k_control(Stats* st, const double* __restrict__ partials, int nb
 
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps, double tol,
                            long long npoints, cudaStream_t st) {
-  k_control<<<1, 256, 0, st>>>(st_dev, partials, nblocks, pass, max_sweeps, tol, npoints);
+  k_control<<<1, 1024, 0, st>>>(st_dev, partials, nblocks, pass, max_sweeps, tol, npoints);
   return cudaGetLastError();
 }
 

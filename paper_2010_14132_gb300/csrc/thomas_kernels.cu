@@ -13,13 +13,20 @@
 //   adjoint solve M^T x = b:  v_k = (b_k + c_{k-1} v_{k-1})/u_k;   x_k = v_k + (a_{k+1}/u_k) x_{k+1}
 // The spectrum is scaled by 1/(nx ny) here, which makes the inverse transforms
 // unnormalised.
+#include <cstring>
+
 #include "kernels.cuh"
 #include "async_copy.cuh"
 
 namespace pgb {
 
 template <typename T> __device__ __forceinline__ T rcp(T u);
-template <> __device__ __forceinline__ float rcp<float>(float u) { return __frcp_rn(u); }
+// single MUFU reciprocal (max error ~1 ulp) on the critical path of the float recurrence
+template <> __device__ __forceinline__ float rcp<float>(float u) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(u));
+  return r;
+}
 template <> __device__ __forceinline__ double rcp<double>(double u) { return 1.0 / u; }
 
 __device__ __forceinline__ int signed_ky(int ky, int ny) { return ky > ny / 2 ? ky - ny : ky; }
@@ -33,7 +40,8 @@ template <typename T, bool ADJ>
 __global__ void __launch_bounds__(128) k_thomas(typename CT<T>::t* __restrict__ spec, Geom g,
                                                 const T* __restrict__ a, const T* __restrict__ c,
                                                 const T* __restrict__ lamx, const T* __restrict__ lamy, T scale,
-                                                int lowk_r2, const int* __restrict__ done, Stats* stats) {
+                                                int lowk_r2, const int* __restrict__ done, Stats* stats,
+                                                const __grid_constant__ CUtensorMap tm, int use_tma, int box_rows) {
   using C = typename CT<T>::t;
   if (done && *done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -52,8 +60,15 @@ __global__ void __launch_bounds__(128) k_thomas(typename CT<T>::t* __restrict__ 
   }
   __syncthreads();
   if (t == 0) {
-    mbar_arrive_expect_tx(bar, row_bytes * (unsigned)nz);
-    for (int k = 0; k < nz; ++k) bulk_g2s(tile + (size_t)k * TC, spec + k * g.plane + c0, row_bytes, bar);
+    if (use_tma) {
+      // one 2-D box per box_rows levels: TC columns x box_rows levels (out-of-range columns read as 0)
+      constexpr int XM = sizeof(C) / 8;
+      mbar_arrive_expect_tx(bar, (unsigned)(TC * sizeof(C)) * (unsigned)nz);
+      for (int k0 = 0; k0 < nz; k0 += box_rows) tma_load_2d(tile + (size_t)k0 * TC, &tm, (int)c0 * XM, k0, bar);
+    } else {
+      mbar_arrive_expect_tx(bar, row_bytes * (unsigned)nz);
+      for (int k = 0; k < nz; ++k) bulk_g2s(tile + (size_t)k * TC, spec + k * g.plane + c0, row_bytes, bar);
+    }
   }
   if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
     if (t == 0) atomicOr(&stats->err, (unsigned)ERR_WAIT_TIMEOUT);
@@ -135,104 +150,125 @@ __global__ void __launch_bounds__(128) k_thomas(typename CT<T>::t* __restrict__ 
 //            back-substitute, remove the W direction (x -= W sum(x)/sum(W)).
 // ---------------------------------------------------------------------------
 template <typename TS, typename TCm, bool ADJ>
-__global__ void k_thomas_lowk(typename CT<TS>::t* __restrict__ spec, Geom g, const double* __restrict__ a,
-                              const double* __restrict__ c, const double* __restrict__ W,
-                              const double* __restrict__ lamx, const double* __restrict__ lamy, double scale,
-                              const int2* __restrict__ cols, int ncols, double2* __restrict__ zs,
-                              double* __restrict__ ws, Stats* stats, const int* __restrict__ done,
-                              const double* __restrict__ target_mean) {
+__global__ void __launch_bounds__(256) k_thomas_lowk(typename CT<TS>::t* __restrict__ spec, Geom g,
+                                                     const double* __restrict__ a, const double* __restrict__ c,
+                                                     const double* __restrict__ W, const double* __restrict__ lamx,
+                                                     const double* __restrict__ lamy, double scale,
+                                                     const int2* __restrict__ cols, int ncols, Stats* stats,
+                                                     const int* __restrict__ done,
+                                                     const double* __restrict__ target_mean) {
+  // one block per listed column: the strided loads and stores of the column run
+  // in parallel; one thread runs the sequential recurrence out of shared memory
   using CS = typename CT<TS>::t;
   if (done && *done) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncols) return;
-  const int kx = cols[t].x, ky = cols[t].y, nz = g.nz;
+  const int col = blockIdx.x;
+  if (col >= ncols) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nz = g.nz;
+  TCm* zx = reinterpret_cast<TCm*>(smraw);   // right-hand side, then z, then x (real parts)
+  TCm* zy = zx + nz;                          // imaginary parts
+  TCm* w = zy + nz;                           // back-substitution factors
+  __shared__ TCm shift_x, shift_y, sumw, sum_x, sum_y;
+  const int kx = cols[col].x, ky = cols[col].y;
   const bool singular = (kx == 0 && ky == 0);
   CS* colp = spec + (long long)ky * g.P + kx;
-  double2* z = zs + (size_t)t * nz;
-  double* w = ws + (size_t)t * nz;
-  // right-hand side in compute precision
-  TCm mean_x = 0, mean_y = 0;
-  if (singular) {
-    TCm sw = 0;
-    for (int k = 0; k < nz; ++k) {
-      const CS v = colp[(long long)k * g.plane];
-      const TCm wk = ADJ ? (TCm)1 : (TCm)W[k];
-      mean_x += wk * (TCm)v.x;
-      mean_y += wk * (TCm)v.y;
-      sw += wk;
-    }
-    mean_x /= sw;
-    mean_y /= sw;
-    // only the first solve records mu_W (a refinement correction solve has a target mean)
-    if (!ADJ && stats && !target_mean) stats->mu_w = (double)mean_x * scale;
-  }
-  const TCm s = singular ? (TCm)0 : -((TCm)lamx[kx] + (TCm)lamy[ky]);
-  const TCm ms = -(TCm)scale;
-  TCm g_prev = s, inv_prev = 0, yx = 0, yy = 0;
-  for (int k = 0; k < nz; ++k) {
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
     const CS v = colp[(long long)k * g.plane];
-    const TCm bx = ms * ((TCm)v.x - mean_x), by = ms * ((TCm)v.y - mean_y);
-    const TCm gk = (k == 0) ? s : s + (TCm)a[k] * g_prev * inv_prev;
-    const TCm u = gk + (TCm)c[k];
-    const bool last_singular = singular && (k == nz - 1);
-    const TCm inv = last_singular ? (TCm)0 : (TCm)1 / u;
-    if (!ADJ) {
-      TCm nx_ = bx, ny_ = by;
-      if (k > 0) {
-        const TCm f = (TCm)a[k] * inv_prev;
-        nx_ += f * yx;
-        ny_ += f * yy;
+    zx[k] = (TCm)v.x;
+    zy[k] = (TCm)v.y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    TCm mean_x = 0, mean_y = 0;
+    if (singular) {
+      TCm sw = 0;
+      for (int k = 0; k < nz; ++k) {
+        const TCm wk = ADJ ? (TCm)1 : (TCm)W[k];
+        mean_x += wk * zx[k];
+        mean_y += wk * zy[k];
+        sw += wk;
       }
-      yx = nx_;
-      yy = ny_;
-      z[k] = make_double2((double)(yx * inv), (double)(yy * inv));   // pinned 0 at the singular top
-      w[k] = (double)((TCm)c[k] * inv);
-    } else {
-      TCm nx_ = bx, ny_ = by;
-      if (k > 0) {
-        nx_ += (TCm)c[k - 1] * yx;
-        ny_ += (TCm)c[k - 1] * yy;
+      mean_x /= sw;
+      mean_y /= sw;
+      // only the first solve records mu_W (a refinement correction solve has a target mean)
+      if (!ADJ && stats && !target_mean) stats->mu_w = (double)mean_x * scale;
+    }
+    const TCm s = singular ? (TCm)0 : -((TCm)lamx[kx] + (TCm)lamy[ky]);
+    const TCm ms = -(TCm)scale;
+    TCm g_prev = s, inv_prev = 0, yx = 0, yy = 0;
+    for (int k = 0; k < nz; ++k) {
+      const TCm bx = ms * (zx[k] - mean_x), by = ms * (zy[k] - mean_y);
+      const TCm gk = (k == 0) ? s : s + (TCm)a[k] * g_prev * inv_prev;
+      const TCm u = gk + (TCm)c[k];
+      const bool last_singular = singular && (k == nz - 1);
+      const TCm inv = last_singular ? (TCm)0 : (TCm)1 / u;   // the singular top pivot is pinned
+      if (!ADJ) {
+        TCm nx_ = bx, ny_ = by;
+        if (k > 0) {
+          const TCm f = (TCm)a[k] * inv_prev;
+          nx_ += f * yx;
+          ny_ += f * yy;
+        }
+        yx = nx_;
+        yy = ny_;
+        zx[k] = yx * inv;
+        zy[k] = yy * inv;
+        w[k] = (TCm)c[k] * inv;
+      } else {
+        TCm nx_ = bx, ny_ = by;
+        if (k > 0) {
+          nx_ += (TCm)c[k - 1] * yx;
+          ny_ += (TCm)c[k - 1] * yy;
+        }
+        yx = nx_ * inv;
+        yy = ny_ * inv;
+        zx[k] = yx;
+        zy[k] = yy;
+        w[k] = (k + 1 < nz) ? (TCm)a[k + 1] * inv : (TCm)0;
       }
-      yx = nx_ * inv;
-      yy = ny_ * inv;
-      z[k] = make_double2((double)yx, (double)yy);
-      w[k] = (k + 1 < nz) ? (double)((TCm)a[k + 1] * inv) : 0.0;
+      g_prev = gk;
+      inv_prev = inv;
     }
-    g_prev = gk;
-    inv_prev = inv;
-  }
-  TCm xx = (TCm)z[nz - 1].x, xy = (TCm)z[nz - 1].y;
-  z[nz - 1] = make_double2((double)xx, (double)xy);
-  TCm sumx = xx, sumy = xy;
-  for (int k = nz - 2; k >= 0; --k) {
-    const TCm wk = (TCm)w[k];
-    xx = (TCm)z[k].x + wk * xx;
-    xy = (TCm)z[k].y + wk * xy;
-    z[k] = make_double2((double)xx, (double)xy);
-    sumx += xx;
-    sumy += xy;
-  }
-  TCm shx = 0, shy = 0, sw = 0;
-  if (singular) {
-    if (!ADJ) {
-      shx = sumx / (TCm)nz;
-      shy = sumy / (TCm)nz;
-      // refinement sweep: the correction also removes the mean of the current iterate
-      if (target_mean) shx += (TCm)(*target_mean);
-    } else {
-      for (int k = 0; k < nz; ++k) sw += (TCm)W[k];
+    TCm xx = zx[nz - 1], xy = zy[nz - 1];
+    TCm sx = xx, sy = xy;
+    for (int k = nz - 2; k >= 0; --k) {
+      xx = zx[k] + w[k] * xx;
+      xy = zy[k] + w[k] * xy;
+      zx[k] = xx;
+      zy[k] = xy;
+      sx += xx;
+      sy += xy;
     }
-  }
-  for (int k = 0; k < nz; ++k) {
-    TCm ox = (TCm)z[k].x, oy = (TCm)z[k].y;
+    TCm shx = 0, shy = 0, swt = 1;
     if (singular) {
       if (!ADJ) {
-        ox -= shx;
-        oy -= shy;
+        shx = sx / (TCm)nz;
+        shy = sy / (TCm)nz;
+        // refinement sweep: the correction also removes the mean of the current iterate
+        if (target_mean) shx += (TCm)(*target_mean);
       } else {
-        const TCm f = (TCm)W[k] / sw;
-        ox -= f * sumx;
-        oy -= f * sumy;
+        swt = 0;
+        for (int k = 0; k < nz; ++k) swt += (TCm)W[k];
+      }
+    }
+    shift_x = shx;
+    shift_y = shy;
+    sumw = swt;
+    sum_x = sx;
+    sum_y = sy;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    TCm ox = zx[k], oy = zy[k];
+    if (singular) {
+      if (!ADJ) {
+        ox -= shift_x;
+        oy -= shift_y;
+      } else {
+        // remove the W direction (the null vector of the transposed column)
+        const TCm f = (TCm)W[k] / sumw;
+        ox -= f * sum_x;
+        oy -= f * sum_y;
       }
     }
     CS o;
@@ -267,18 +303,33 @@ static cudaError_t thomas_main(const ThomasArgs& A, const Geom& g, const T* a, c
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<(unsigned)nb, tc, smem, st>>>((C*)A.spec, g, a, c, lx, ly, (T)A.scale, A.lowk_r2, A.done, A.stats);
+  // the spectrum as a 2-D tensor: a level's ny*P entries per row, nz rows
+  int box_rows = 1;
+  for (int d = 256; d >= 1; --d)
+    if (g.nz % d == 0) {
+      box_rows = d;
+      break;
+    }
+  constexpr int XM = sizeof(C) / 8;
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  const int use_tma = encode_tensor_2d(&tm, A.spec, 8, (unsigned long long)g.plane * XM, (unsigned long long)g.nz,
+                                       (unsigned long long)g.plane * sizeof(C), (unsigned)(tc * XM),
+                                       (unsigned)box_rows)
+                          ? 1
+                          : 0;
+  kern<<<(unsigned)nb, tc, smem, st>>>((C*)A.spec, g, a, c, lx, ly, (T)A.scale, A.lowk_r2, A.done, A.stats, tm,
+                                       use_tma, box_rows);
   return cudaGetLastError();
 }
 
 template <typename TS, typename TCm, bool ADJ>
 static cudaError_t thomas_lowk(const ThomasArgs& A, const Geom& g, const Tables& tb, cudaStream_t st) {
   if (A.n_lowk <= 0) return cudaSuccess;
-  const int threads = 64;
-  const int blocks = (A.n_lowk + threads - 1) / threads;
-  k_thomas_lowk<TS, TCm, ADJ><<<blocks, threads, 0, st>>>((typename CT<TS>::t*)A.spec, g, tb.a_d, tb.c_d, tb.W_d,
-                                                          tb.lamx_d, tb.lamy_d, A.scale, A.lowk_cols, A.n_lowk,
-                                                          A.lowk_z, A.lowk_w, A.stats, A.done, A.target_mean);
+  const size_t smem = 3 * sizeof(TCm) * (size_t)g.nz;
+  k_thomas_lowk<TS, TCm, ADJ><<<A.n_lowk, 128, smem, st>>>((typename CT<TS>::t*)A.spec, g, tb.a_d, tb.c_d, tb.W_d,
+                                                         tb.lamx_d, tb.lamy_d, A.scale, A.lowk_cols, A.n_lowk,
+                                                         A.stats, A.done, A.target_mean);
   return cudaGetLastError();
 }
 

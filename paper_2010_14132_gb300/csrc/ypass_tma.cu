@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(512) k_yfft_tma(const __grid_constant__ CUtens
       ok = false;
       break;
     }
-    stockham_run<E, SIGN, T>(buf[b] + l, TK, fy, lane, twy, SyncBlock());
+    stockham_run<E, SIGN, T>(buf[b] + l, Strided{TK}, fy, lane, twy, SyncBlock());
     fence_proxy_async_smem();   // this thread's shared writes become visible to the TMA unit
     __syncthreads();
     if (tid == 0) {
@@ -102,6 +102,19 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
+bool encode_tensor_2d(CUtensorMap* tm, void* base, size_t elem_bytes, unsigned long long dim0,
+                      unsigned long long dim1, unsigned long long row_stride_bytes, unsigned box0, unsigned box1) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc || (elem_bytes != 8)) return false;
+  const cuuint64_t gdim[2] = {(cuuint64_t)dim0, (cuuint64_t)dim1};
+  const cuuint64_t gstride[1] = {(cuuint64_t)row_stride_bytes};
+  const cuuint32_t box[2] = {(cuuint32_t)box0, (cuuint32_t)box1};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 static int largest_divisor_upto(int n, int cap) {
   for (int d = cap; d >= 1; --d)
     if (n % d == 0) return d;
@@ -124,20 +137,15 @@ static cudaError_t yfft_tma_t(typename CT<T>::t* spec, const Geom& g, const FftP
                               bool* used) {
   using C = typename CT<T>::t;
   *used = false;
-  EncodeTiledFn enc = encode_fn();
   const int tk = tma_tile(fy.n, fy.E, sizeof(C), tile);
-  if (!enc || tk == 0 || fy.n < 2) return cudaSuccess;
+  if (tk == 0 || fy.n < 2) return cudaSuccess;
   const int XM = sizeof(C) / 8;
   const int box_rows = largest_divisor_upto(fy.n, 256);
   if (((size_t)box_rows * tk * sizeof(C)) % 128 != 0 && box_rows != fy.n) return cudaSuccess;  // unaligned boxes
   CUtensorMap tm;
-  const cuuint64_t gdim[2] = {(cuuint64_t)g.nxh * XM, (cuuint64_t)g.ny * g.nz};
-  const cuuint64_t gstride[1] = {(cuuint64_t)g.P * sizeof(C)};
-  const cuuint32_t box[2] = {(cuuint32_t)(tk * XM), (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUtensorMapDataType dt = (XM == 1) ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-  if (enc(&tm, dt, 2, spec, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+  // 8-byte tensor elements: a float complex is one element, a double complex two
+  if (!encode_tensor_2d(&tm, spec, 8, (unsigned long long)g.nxh * XM, (unsigned long long)g.ny * g.nz,
+                        (unsigned long long)g.P * sizeof(C), (unsigned)(tk * XM), (unsigned)box_rows))
     return cudaSuccess;   // fall back to the plain y-pass
   const int tiles_per_level = (g.nxh + tk - 1) / tk;
   const int ntiles = tiles_per_level * g.nz;
