@@ -137,13 +137,16 @@ def algorithmic_bytes(nx, ny, nz, sweeps):
     N = nx * ny * nz
     Nc = (nx // 2 + 1) * ny * nz
     b = {
-        "xfwd": 8 * N + 8 * Nc + sweeps * (4 * N + 8 * Nc),
+        # first solve reads S (double); each sweep forms the residual from S, p0 (and q
+        # from the second sweep on) inside the forward x-pass
+        "xfwd": 8 * N + 8 * Nc + sum(8 * N + 4 * N + (4 * N if s > 1 else 0) + 8 * Nc
+                                     for s in range(1, sweeps + 1)),
         "yfwd": (1 + sweeps) * 16 * Nc,
         "columns": (1 + sweeps) * 16 * Nc,
         "yinv": (1 + sweeps) * 16 * Nc,
         "xinv": (8 * Nc + 4 * N) + sum(8 * Nc + 4 * N + 4 * N + 8 * N + (4 * N if s > 1 else 0)
                                        for s in range(1, sweeps + 1)),
-        "residual": sum(8 * N + 4 * N + 4 * N + (4 * N if s > 1 else 0) for s in range(1, sweeps + 1)),
+        "residual": 0,
         "control": 0,
     }
     # the solve as a whole: read S, write p once; spectrum written and read once per pass;
@@ -307,7 +310,7 @@ def main():
                         "alg_bytes_per_solve": alg[name], "gbs": gbs}
     dom = max(phases, key=lambda k: phases[k]["ms_per_solve"])
     execd = {"xfwd": 1 + sweeps, "yfwd": 1 + sweeps, "columns": 1 + sweeps, "yinv": 1 + sweeps,
-             "xinv": 1 + sweeps, "residual": sweeps, "control": 1 + sweeps}[dom]
+             "xinv": 1 + sweeps, "residual": max(1, sweeps), "control": 1 + sweeps}[dom]
     dom_ms_launch = phases[dom]["ms_per_solve"] / execd
     dom_bytes_launch = alg[dom] / execd
     achieved = dom_bytes_launch / (dom_ms_launch * 1e-3) / 1e9

@@ -85,7 +85,7 @@ struct poisson_plan {
   int n_lowk = 0;
   float2 cx{}, cy{};
   // workspace layout
-  size_t off_spec = 0, off_stats = 0, off_part = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0, off_r = 0,
+  size_t off_spec = 0, off_stats = 0, off_part = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
          off_gp = 0, ws_bytes = 0;
   int xinv_blocks = 1, grho_nb = 1;
   PhaseProfiler prof;
@@ -150,8 +150,6 @@ void layout_workspace(poisson_plan* pl) {
     pl->off_p0 = off;
     off = align256(off + sizeof(float) * (size_t)N);
     pl->off_q = off;
-    off = align256(off + sizeof(float) * (size_t)N);
-    pl->off_r = off;
     off = align256(off + sizeof(float) * (size_t)N);
   }
   pl->off_gp = off;
@@ -462,12 +460,14 @@ static cudaError_t ypass(poisson_plan* pl, int sign, void* spec, const int* done
 
 // Forward transform -> column solve -> inverse transform of one field.
 static cudaError_t run_pipeline(poisson_plan* pl, const void* in, int in_double, char* ws, cudaStream_t st,
-                                int adjoint, const int* done, const double* target_mean = nullptr) {
+                                int adjoint, const int* done, const double* target_mean = nullptr,
+                                const ResidualArgs* R = nullptr) {
   const bool t_double = pl->fp64();
   void* spec = ws + pl->off_spec;
   Stats* stats = (Stats*)(ws + pl->off_stats);
   int ps = prof_begin(pl, POISSON_PHASE_XFWD, st);
-  cudaError_t e = launch_xfwd(in_double, t_double, in, spec, pl->g, pl->fx, pl->tb, done, st);
+  cudaError_t e = R ? launch_xfwd_residual(*R, spec, pl->g, pl->fx, pl->tb, done, st)
+                    : launch_xfwd(in_double, t_double, in, spec, pl->g, pl->fx, pl->tb, done, st);
   prof_end(pl, ps, st);
   if (e != cudaSuccess) return e;
   ps = prof_begin(pl, POISSON_PHASE_YFWD, st);
@@ -545,7 +545,6 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
     const int* done = &stats->done;
     float* p0 = (float*)(ws + pl->off_p0);
     float* q = (float*)(ws + pl->off_q);
-    float* r = (float*)(ws + pl->off_r);
     int nb = 0;
     // first solve: double source, float transforms, double low-|k| columns
     PGB_CUDA(run_pipeline(pl, S, 1, ws, st, 0, nullptr));
@@ -560,12 +559,10 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
     prof_end(pl, ps, st);
     PGB_CUDA(e);
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
-      ps = prof_begin(pl, POISSON_PHASE_RESIDUAL, st);
-      e = launch_residual_ff((const double*)S, p0, sweep > 1 ? q : nullptr, r, pl->g, pl->tb, pl->cx, pl->cy,
-                             &stats->mu_ff, done, st);
-      prof_end(pl, ps, st);
-      PGB_CUDA(e);
-      PGB_CUDA(run_pipeline(pl, r, 0, ws, st, 0, done, &stats->pmean));
+      // residual computed inside the forward x-pass (its rows are never stored)
+      const ResidualArgs R{(const double*)S, p0, sweep > 1 ? q : nullptr, pl->tb.a_ff, pl->tb.c_ff,
+                           pl->cx,           pl->cy, &stats->mu_ff};
+      PGB_CUDA(run_pipeline(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R));
       XinvExtra eu = ex;
       eu.p0 = p0;
       eu.q = q;

@@ -17,6 +17,7 @@
 #include <unordered_map>
 
 #include "kernels.cuh"
+#include "residual.cuh"
 
 namespace pgb {
 
@@ -27,11 +28,13 @@ template <> struct V2<double> { using t = double2; };
 // ---------------------------------------------------------------------------
 // x-pass forward
 // ---------------------------------------------------------------------------
-template <typename TI, typename T, int E>
+// RES = 0: rows of the input array; RES = 1/2: rows of the refinement residual
+// (without / with the accumulated correction q), computed as they are loaded.
+template <typename TI, typename T, int E, int RES = 0>
 __global__ void __launch_bounds__(256) k_xfwd(const TI* __restrict__ in, typename CT<T>::t* __restrict__ spec,
                                                Geom g, FftPlan fx, const typename CT<T>::t* __restrict__ twx,
                                                const typename CT<T>::t* __restrict__ twr, long long nrows,
-                                               const int* __restrict__ done) {
+                                               const int* __restrict__ done, ResidualArgs R) {
   using C = typename CT<T>::t;
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -42,17 +45,31 @@ __global__ void __launch_bounds__(256) k_xfwd(const TI* __restrict__ in, typenam
   const bool valid = row < nrows;
   C* line = sm + ty * swizzled_stride(n + 1);
   const Swizzled sw{};
-  const typename V2<TI>::t* src = reinterpret_cast<const typename V2<TI>::t*>(in + (valid ? row : 0) * g.nx);
+  if constexpr (RES == 0) {
+    const typename V2<TI>::t* src = reinterpret_cast<const typename V2<TI>::t*>(in + (valid ? row : 0) * g.nx);
 #pragma unroll
-  for (int q = 0; q < E; ++q) {
-    const int m = lane + nl * q;
-    C z = make_c<T>(0, 0);
-    if (valid) {
-      const typename V2<TI>::t v = src[m];
-      z.x = Cvt<TI, T>::f(v.x);
-      z.y = Cvt<TI, T>::f(v.y);
+    for (int q = 0; q < E; ++q) {
+      const int m = lane + nl * q;
+      C z = make_c<T>(0, 0);
+      if (valid) {
+        const typename V2<TI>::t v = src[m];
+        z.x = Cvt<TI, T>::f(v.x);
+        z.y = Cvt<TI, T>::f(v.y);
+      }
+      line[sw(m)] = z;
     }
-    line[sw(m)] = z;
+  } else {
+    const int jr = valid ? (int)(row % g.ny) : 0, kr = valid ? (int)(row / g.ny) : 0;
+#pragma unroll 4
+    for (int q = 0; q < E; ++q) {
+      const int m = lane + nl * q;
+      C z = make_c<T>(0, 0);
+      if (valid) {
+        z.x = residual_point<RES == 2>(R, g, 2 * m, jr, kr);
+        z.y = residual_point<RES == 2>(R, g, 2 * m + 1, jr, kr);
+      }
+      line[sw(m)] = z;
+    }
   }
   __syncthreads();
   stockham_run<E, -1, T>(line, sw, fx, lane, twx, SyncBlock());
@@ -287,8 +304,37 @@ static cudaError_t xfwd_t(const TI* in, typename CT<T>::t* spec, const Geom& g, 
     auto kern = k_xfwd<TI, T, EE>;
     e = allow_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)nb, block, smem, st>>>(in, spec, g, fx, twx, twr, nrows, done);
+    kern<<<(unsigned)nb, block, smem, st>>>(in, spec, g, fx, twx, twr, nrows, done, ResidualArgs{});
   });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xfwd_residual(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx,
+                                 const Tables& tb, const int* done, cudaStream_t st) {
+  using C = float2;
+  const long long nrows = (long long)g.ny * g.nz;
+  const int n = fx.n;
+  const int rb = xpass_rows(n, fx.E, sizeof(C));
+  const dim3 block(n / fx.E, rb);
+  const long long nb = (nrows + rb - 1) / rb;
+  const size_t smem = (size_t)rb * swizzled_stride(n + 1) * sizeof(C);
+  if (smem > kMaxDynSmem || nb > 0x7fffffffLL) return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  if (R.q) {
+    PGB_E_SWITCH(fx.E, {
+      auto kern = k_xfwd<float, float, EE, 2>;
+      e = allow_smem(kern, smem);
+      if (e != cudaSuccess) return e;
+      kern<<<(unsigned)nb, block, smem, st>>>(nullptr, (C*)spec, g, fx, tb.twx_f, tb.twr_f, nrows, done, R);
+    });
+  } else {
+    PGB_E_SWITCH(fx.E, {
+      auto kern = k_xfwd<float, float, EE, 1>;
+      e = allow_smem(kern, smem);
+      if (e != cudaSuccess) return e;
+      kern<<<(unsigned)nb, block, smem, st>>>(nullptr, (C*)spec, g, fx, tb.twx_f, tb.twr_f, nrows, done, R);
+    });
+  }
   return cudaGetLastError();
 }
 

@@ -59,9 +59,24 @@ struct XinvExtra {
   const int* done;      // skip when set (nullable)
 };
 
+// Inputs of the double-float refinement residual r = S - mu_W - L (p0 + q).
+struct ResidualArgs {
+  const double* S;
+  const float* p0;
+  const float* q;        // nullable (first sweep)
+  const float2* a_ff;
+  const float2* c_ff;
+  float2 cx, cy;
+  const float2* mu_ff;
+};
+
 // ---- launchers (stream-ordered, return cudaError_t of the launch) ----
 cudaError_t launch_xfwd(int ti_is_double, int t_is_double, const void* in, void* spec, const Geom& g,
                         const FftPlan& fx, const Tables& tb, const int* done, cudaStream_t st);
+// Forward x-pass of a refinement sweep whose input rows are the residual,
+// computed in the load stage (no r array in memory).
+cudaError_t launch_xfwd_residual(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx,
+                                 const Tables& tb, const int* done, cudaStream_t st);
 cudaError_t launch_yfft(int t_is_double, int sign, void* spec, const Geom& g, const FftPlan& fy,
                         const Tables& tb, int tile, const int* done, cudaStream_t st);
 // 2-D tensor map over 8-byte elements (dim0 contiguous, dim1 rows of row_stride_bytes);

@@ -1,0 +1,97 @@
+// Double-float residual of the mixed refinement at one grid point:
+//   r = S - mu_W - L (p0 + q).
+//
+// mu_W (the weighted mean of S, found by the first solve) is removed here: it is
+// outside the range of L, and left in r it would dominate r's dynamic range, so
+// that the float rounding of r and of its transform would swamp the small
+// compatible part (most visibly in the kx = 0 columns, whose y-transform carries
+// the constant).  The correction solve removes what little constant remains.
+//
+// The refinement needs r to about 2^-44 of |L||p| (the 7-point sum cancels by
+// orders of magnitude for the smooth, large pressure field), which FP32 alone
+// cannot give and FP64 instructions make ALU bound on GB300.  Every product and
+// sum of p0 (exact floats) with the double-float coefficients is formed with
+// error-free transformations; the small correction q enters in plain FP32.
+// S (double) is split into hi + lo floats with integer operations.
+#pragma once
+#include "kernels.cuh"
+
+namespace pgb {
+
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return FF{s, e + a.l + b.l};
+}
+
+template <bool HAS_Q>
+__device__ __forceinline__ float residual_point(const ResidualArgs& R, const Geom& g, int i, int j, int k) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long long pl = (long long)nx * ny;
+  const long long row = ((long long)k * ny + j) * nx;
+  const long long idx = row + i;
+  const int ie = (i + 1 == nx) ? 0 : i + 1, iw = (i == 0) ? nx - 1 : i - 1;
+  const long long rn = ((long long)k * ny + ((j + 1 == ny) ? 0 : j + 1)) * nx;
+  const long long rs = ((long long)k * ny + ((j == 0) ? ny - 1 : j - 1)) * nx;
+  const float* p0 = R.p0;
+  const float pc = p0[idx];
+  const float pe = p0[row + ie], pw = p0[row + iw], pn = p0[rn + i], ps = p0[rs + i];
+  const bool has_dn = k > 0, has_up = k + 1 < nz;
+  const float pd = has_dn ? p0[idx - pl] : pc;
+  const float pu = has_up ? p0[idx + pl] : pc;
+  float qc = 0, qe = 0, qw = 0, qn = 0, qs = 0, qd = 0, qu = 0;
+  if (HAS_Q) {
+    const float* q = R.q;
+    qc = q[idx];
+    qe = q[row + ie];
+    qw = q[row + iw];
+    qn = q[rn + i];
+    qs = q[rs + i];
+    qd = has_dn ? q[idx - pl] : qc;
+    qu = has_up ? q[idx + pl] : qc;
+  }
+  // x: cx (pe + pw - 2 pc)
+  float s1, e1, s2, e2;
+  two_sum(pe, pw, s1, e1);
+  two_sum(s1, -2.f * pc, s2, e2);
+  float dl = e1 + e2 + (qe + qw - 2.f * qc);
+  FF tx;
+  two_prod(R.cx.x, s2, tx.h, tx.l);
+  tx.l = __fmaf_rn(R.cx.x, dl, __fmaf_rn(R.cx.y, s2, tx.l));
+  // y: cy (pn + ps - 2 pc)
+  two_sum(pn, ps, s1, e1);
+  two_sum(s1, -2.f * pc, s2, e2);
+  dl = e1 + e2 + (qn + qs - 2.f * qc);
+  FF ty;
+  two_prod(R.cy.x, s2, ty.h, ty.l);
+  ty.l = __fmaf_rn(R.cy.x, dl, __fmaf_rn(R.cy.y, s2, ty.l));
+  // z: a (pd - pc) + c (pu - pc)   (a = 0 at the bottom, c = 0 at the top).
+  // Differences first: a constant field maps to exactly zero whatever the
+  // rounding of the coefficient splits.  Summing a pd + c pu - (a+c) pc instead
+  // leaves a row-sum mismatch of ~2^-48 (a+c) that the near-null vertical mode of
+  // the lowest-|k| columns amplifies by their condition number.
+  const float2 A = R.a_ff[k], Cc = R.c_ff[k];
+  float dd, ed, du, eu, p1, l1, p2, l2;
+  two_sum(pd, -pc, dd, ed);
+  two_sum(pu, -pc, du, eu);
+  two_prod(A.x, dd, p1, l1);
+  two_prod(Cc.x, du, p2, l2);
+  l1 = __fmaf_rn(A.x, ed + (qd - qc), __fmaf_rn(A.y, dd, l1));
+  l2 = __fmaf_rn(Cc.x, eu + (qu - qc), __fmaf_rn(Cc.y, du, l2));
+  two_sum(p1, p2, s2, e2);
+  FF tz{s2, (l1 + l2) + e2};
+  FF Lp = ff_add(ff_add(tx, ty), tz);
+  float sh, sl, th, tl;
+  d2ff_int(R.S[idx], sh, sl);
+  const float2 mu = *R.mu_ff;
+  two_sum(sh, -mu.x, th, tl);
+  tl += sl - mu.y;
+  float rh, rl;
+  two_sum(th, -Lp.h, rh, rl);
+  return rh + (rl + (tl - Lp.l));
+}
+
+}  // namespace pgb
