@@ -36,22 +36,51 @@ __device__ __forceinline__ int signed_ky(int ky, int ny) { return ky > ny / 2 ? 
 // (flattened (ky, kx) index with pitch P) staged for all nz levels.
 // Shared layout: tile [nz][TC] complex, wv [nz][TC] real, one mbarrier.
 // ---------------------------------------------------------------------------
-template <typename T, bool ADJ>
+struct LowkArgs {
+  const int2* cols;
+  int n;
+  const double* a_d;
+  const double* c_d;
+  const double* W_d;
+  const double* lamx_d;
+  const double* lamy_d;
+  const double* target_mean;
+  double scale;   // 1/(nx ny) in double for the double-precision columns
+};
+
+template <typename TS, typename TCm, bool ADJ>
+__device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS>::t* __restrict__ spec,
+                                            const Geom& g, const double* __restrict__ ag,
+                                            const double* __restrict__ cg, const double* __restrict__ Wg,
+                                            const double* __restrict__ lamx, const double* __restrict__ lamy,
+                                            double scale, int2 colk, Stats* stats,
+                                            const double* __restrict__ target_mean);
+
+// Blocks [0, L.n) solve the listed low-|k| / singular columns (precision TCm);
+// the others solve tiles of TC consecutive columns.  The two sets of columns are
+// disjoint (the tile blocks skip listed columns), so they run concurrently.
+template <typename T, typename TCm, bool ADJ>
 __global__ void __launch_bounds__(128) k_thomas(typename CT<T>::t* __restrict__ spec, Geom g,
                                                 const T* __restrict__ a, const T* __restrict__ c,
                                                 const T* __restrict__ lamx, const T* __restrict__ lamy, T scale,
                                                 int lowk_r2, const int* __restrict__ done, Stats* stats,
-                                                const __grid_constant__ CUtensorMap tm, int use_tma, int box_rows) {
+                                                const __grid_constant__ CUtensorMap tm, int use_tma, int box_rows,
+                                                LowkArgs L) {
   using C = typename CT<T>::t;
   if (done && *done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
+  if ((int)blockIdx.x < L.n) {
+    lowk_column<T, TCm, ADJ>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale,
+                             L.cols[blockIdx.x], stats, L.target_mean);
+    return;
+  }
   const int TC = blockDim.x, t = threadIdx.x, nz = g.nz;
   C* tile = reinterpret_cast<C*>(smraw);
   T* wv = reinterpret_cast<T*>(tile + (size_t)nz * TC);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + (((size_t)nz * TC * (sizeof(C) + sizeof(T)) + 15) & ~(size_t)15));
 
   const long long ncols = g.plane;
-  const long long c0 = (long long)blockIdx.x * TC;
+  const long long c0 = (long long)(blockIdx.x - L.n) * TC;
   const int tcv = (int)((ncols - c0) < TC ? (ncols - c0) : TC);
   const unsigned row_bytes = (unsigned)(tcv * sizeof(C));
   if (t == 0) {
@@ -149,33 +178,35 @@ __global__ void __launch_bounds__(128) k_thomas(typename CT<T>::t* __restrict__ 
 //   adjoint: remove the plain mean of the right-hand side, pin v_{nz-1} = 0,
 //            back-substitute, remove the W direction (x -= W sum(x)/sum(W)).
 // ---------------------------------------------------------------------------
+// One low-|k| or singular column, solved by the whole block: the strided loads
+// and stores of the column and the coefficient tables go through shared memory
+// in parallel; thread 0 runs the sequential recurrence out of shared memory.
 template <typename TS, typename TCm, bool ADJ>
-__global__ void __launch_bounds__(256) k_thomas_lowk(typename CT<TS>::t* __restrict__ spec, Geom g,
-                                                     const double* __restrict__ a, const double* __restrict__ c,
-                                                     const double* __restrict__ W, const double* __restrict__ lamx,
-                                                     const double* __restrict__ lamy, double scale,
-                                                     const int2* __restrict__ cols, int ncols, Stats* stats,
-                                                     const int* __restrict__ done,
-                                                     const double* __restrict__ target_mean) {
-  // one block per listed column: the strided loads and stores of the column run
-  // in parallel; one thread runs the sequential recurrence out of shared memory
+__device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS>::t* __restrict__ spec,
+                                            const Geom& g, const double* __restrict__ ag,
+                                            const double* __restrict__ cg, const double* __restrict__ Wg,
+                                            const double* __restrict__ lamx, const double* __restrict__ lamy,
+                                            double scale, int2 colk, Stats* stats,
+                                            const double* __restrict__ target_mean) {
   using CS = typename CT<TS>::t;
-  if (done && *done) return;
-  const int col = blockIdx.x;
-  if (col >= ncols) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
   const int nz = g.nz;
   TCm* zx = reinterpret_cast<TCm*>(smraw);   // right-hand side, then z, then x (real parts)
   TCm* zy = zx + nz;                          // imaginary parts
   TCm* w = zy + nz;                           // back-substitution factors
-  __shared__ TCm shift_x, shift_y, sumw, sum_x, sum_y;
-  const int kx = cols[col].x, ky = cols[col].y;
+  TCm* a = w + nz;                            // coefficient tables
+  TCm* c = a + nz;
+  TCm* W = c + nz;
+  TCm* red = W + nz;                          // shift_x, shift_y, sumw, sum_x, sum_y
+  const int kx = colk.x, ky = colk.y;
   const bool singular = (kx == 0 && ky == 0);
   CS* colp = spec + (long long)ky * g.P + kx;
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
     const CS v = colp[(long long)k * g.plane];
     zx[k] = (TCm)v.x;
     zy[k] = (TCm)v.y;
+    a[k] = (TCm)ag[k];
+    c[k] = (TCm)cg[k];
+    W[k] = (TCm)Wg[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -251,13 +282,14 @@ __global__ void __launch_bounds__(256) k_thomas_lowk(typename CT<TS>::t* __restr
         for (int k = 0; k < nz; ++k) swt += (TCm)W[k];
       }
     }
-    shift_x = shx;
-    shift_y = shy;
-    sumw = swt;
-    sum_x = sx;
-    sum_y = sy;
+    red[0] = shx;
+    red[1] = shy;
+    red[2] = swt;
+    red[3] = sx;
+    red[4] = sy;
   }
   __syncthreads();
+  const TCm shift_x = red[0], shift_y = red[1], sumw = red[2], sum_x = red[3], sum_y = red[4];
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
     TCm ox = zx[k], oy = zy[k];
     if (singular) {
@@ -290,19 +322,19 @@ static int thomas_tile(int nz, size_t entry_bytes) {
   return 0;
 }
 
-template <typename T, bool ADJ>
-static cudaError_t thomas_main(const ThomasArgs& A, const Geom& g, const T* a, const T* c, const T* lx,
-                               const T* ly, cudaStream_t st) {
+template <typename T, typename TCm, bool ADJ>
+static cudaError_t thomas_launch(const ThomasArgs& A, const Geom& g, const Tables& tb, const T* a, const T* c,
+                                 const T* lx, const T* ly, cudaStream_t st) {
   using C = typename CT<T>::t;
   const int tc = thomas_tile(g.nz, sizeof(C) + sizeof(T));
   if (tc == 0) return cudaErrorInvalidValue;
-  const size_t smem = (((size_t)g.nz * tc * (sizeof(C) + sizeof(T)) + 15) & ~(size_t)15) + 16;
+  size_t smem = (((size_t)g.nz * tc * (sizeof(C) + sizeof(T)) + 15) & ~(size_t)15) + 16;
+  const size_t lowk_smem = (6 * (size_t)g.nz + 8) * sizeof(TCm);
+  if (smem < lowk_smem) smem = lowk_smem;
   const long long nb = (g.plane + tc - 1) / tc;
-  auto kern = k_thomas<T, ADJ>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  auto kern = k_thomas<T, TCm, ADJ>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   // the spectrum as a 2-D tensor: a level's ny*P entries per row, nz rows
   int box_rows = 1;
   for (int d = 256; d >= 1; --d)
@@ -318,37 +350,21 @@ static cudaError_t thomas_main(const ThomasArgs& A, const Geom& g, const T* a, c
                                        (unsigned)box_rows)
                           ? 1
                           : 0;
-  kern<<<(unsigned)nb, tc, smem, st>>>((C*)A.spec, g, a, c, lx, ly, (T)A.scale, A.lowk_r2, A.done, A.stats, tm,
-                                       use_tma, box_rows);
-  return cudaGetLastError();
-}
-
-template <typename TS, typename TCm, bool ADJ>
-static cudaError_t thomas_lowk(const ThomasArgs& A, const Geom& g, const Tables& tb, cudaStream_t st) {
-  if (A.n_lowk <= 0) return cudaSuccess;
-  const size_t smem = 3 * sizeof(TCm) * (size_t)g.nz;
-  k_thomas_lowk<TS, TCm, ADJ><<<A.n_lowk, 128, smem, st>>>((typename CT<TS>::t*)A.spec, g, tb.a_d, tb.c_d, tb.W_d,
-                                                         tb.lamx_d, tb.lamy_d, A.scale, A.lowk_cols, A.n_lowk,
-                                                         A.stats, A.done, A.target_mean);
+  const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale};
+  kern<<<(unsigned)(nb + A.n_lowk), tc, smem, st>>>((C*)A.spec, g, a, c, lx, ly, (T)A.scale, A.lowk_r2, A.done,
+                                                   A.stats, tm, use_tma, box_rows, L);
   return cudaGetLastError();
 }
 
 cudaError_t launch_thomas(const ThomasArgs& A, const Geom& g, const Tables& tb, cudaStream_t st) {
-  cudaError_t e;
-  // the low-|k| kernel reads its columns before the main kernel (which skips them) runs
-  if (A.t_is_double) {
-    e = A.adjoint ? thomas_lowk<double, double, true>(A, g, tb, st) : thomas_lowk<double, double, false>(A, g, tb, st);
-    if (e != cudaSuccess) return e;
-    return A.adjoint ? thomas_main<double, true>(A, g, tb.a_d, tb.c_d, tb.lamx_d, tb.lamy_d, st)
-                     : thomas_main<double, false>(A, g, tb.a_d, tb.c_d, tb.lamx_d, tb.lamy_d, st);
-  }
+  if (A.t_is_double)
+    return A.adjoint ? thomas_launch<double, double, true>(A, g, tb, tb.a_d, tb.c_d, tb.lamx_d, tb.lamy_d, st)
+                     : thomas_launch<double, double, false>(A, g, tb, tb.a_d, tb.c_d, tb.lamx_d, tb.lamy_d, st);
   if (A.lowk_double)
-    e = A.adjoint ? thomas_lowk<float, double, true>(A, g, tb, st) : thomas_lowk<float, double, false>(A, g, tb, st);
-  else
-    e = A.adjoint ? thomas_lowk<float, float, true>(A, g, tb, st) : thomas_lowk<float, float, false>(A, g, tb, st);
-  if (e != cudaSuccess) return e;
-  return A.adjoint ? thomas_main<float, true>(A, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f, st)
-                   : thomas_main<float, false>(A, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f, st);
+    return A.adjoint ? thomas_launch<float, double, true>(A, g, tb, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f, st)
+                     : thomas_launch<float, double, false>(A, g, tb, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f, st);
+  return A.adjoint ? thomas_launch<float, float, true>(A, g, tb, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f, st)
+                   : thomas_launch<float, float, false>(A, g, tb, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f, st);
 }
 
 }  // namespace pgb

@@ -1,0 +1,48 @@
+"""Run a few solves of one grid size, for profilers (ncu) and quick timing.
+
+    python -m paper_2010_14132_gb300.profile_case --nx 1024 --ny 1024 --nz 32 --dtype mixed --reps 1
+
+The grid uses the stretched/anelastic setup (dx = dy = 50 m, dz_k = 10*1.03^k m,
+rho0 = 1.2 exp(-z/8000)) with a seeded N(0,1) source.  With --adjoint the
+adjoint (and rho0 gradient) is run after each solve.  Prints the mean time per
+call measured with CUDA events.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+import torch
+
+from . import workloads as wl
+from .solver import Plan
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=1024)
+    ap.add_argument("--nz", type=int, default=32)
+    ap.add_argument("--dtype", default="mixed", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--adjoint", action="store_true")
+    args = ap.parse_args(argv)
+    d = wl.anelastic_noise(args.nx, args.ny, args.nz, seed=3)
+    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype=args.dtype)
+    S = torch.from_numpy(d.S).cuda().to(plan.field_dtype)
+    p = torch.empty_like(S)
+    w = torch.randn_like(S) if args.adjoint else None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        plan.solve(S, out=p)
+        if args.adjoint:
+            plan.adjoint(w, p=p, want_grho=True)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"{args.nx}x{args.ny}x{args.nz} {args.dtype}: {e0.elapsed_time(e1) / max(1, args.reps):.3f} ms per call")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
