@@ -24,6 +24,9 @@ POISSON_FP64, POISSON_FP32, POISSON_MIXED = 0, 1, 2
 POISSON_OPT_LOWK_RADIUS2, POISSON_OPT_MAX_SWEEPS, POISSON_OPT_TOLERANCE, POISSON_OPT_Y_TILE = 0, 1, 2, 3
 POISSON_OPT_PROFILE = 4
 POISSON_OPT_Y_KERNEL = 5
+POISSON_OPT_X_ELEMS = 6
+POISSON_OPT_Y_ELEMS = 7
+POISSON_OPT_LEVEL_CHUNK = 8
 PHASES = ("xfwd", "yfwd", "columns", "yinv", "xinv", "residual", "control")
 
 # every symbol include/poisson.h declares

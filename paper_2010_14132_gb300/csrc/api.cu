@@ -37,7 +37,8 @@ bool factor23(int n, int& a, int& b) {
 }
 
 // Radix schedule and elements-per-thread for a line of length n = 2^a 3^b.
-bool make_fft_plan(int n, FftPlan& fp) {
+// e_pow2: elements per thread for pure powers of two (8 or 16).
+bool make_fft_plan(int n, FftPlan& fp, int e_pow2 = 16) {
   int a, b;
   if (n < 2 || !factor23(n, a, b)) return false;
   std::memset(&fp, 0, sizeof(fp));
@@ -49,7 +50,7 @@ bool make_fft_plan(int n, FftPlan& fp) {
   if (a % 3 == 2) fp.radix[s++] = 4;
   if (s > kMaxStages) return false;
   fp.nstages = s;
-  if (b == 0) fp.E = n < 16 ? n : 16;
+  if (b == 0) fp.E = n < e_pow2 ? n : e_pow2;
   else fp.E = a >= 3 ? 24 : (a == 2 ? 12 : (a == 1 ? 6 : 3));
   return n % fp.E == 0 && fft_e_supported(fp.E);
 }
@@ -74,7 +75,7 @@ struct poisson_plan {
   int dtype = 0;
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
-  int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0;
+  int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0, xelems = 8, yelems = 16, lchunk = 0;
   double tol = 1e-11;
   Geom g{};
   Tables tb{};
@@ -141,7 +142,7 @@ void layout_workspace(poisson_plan* pl) {
   pl->off_stats = off;
   off = align256(off + sizeof(Stats));
   pl->off_part = off;
-  off = align256(off + 3 * sizeof(double) * (size_t)(pl->xinv_blocks > 0 ? pl->xinv_blocks : 1));
+  off = align256(off + 3 * sizeof(double) * (size_t)(pl->xinv_blocks + pl->nz));   // + one per level chunk
   pl->off_lz = off;
   off = align256(off + sizeof(double2) * (size_t)pl->nz * pl->n_lowk);
   pl->off_lw = off;
@@ -248,7 +249,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
   pl->P = (pl->nxh + pad - 1) / pad * pad;
   pl->dz.assign(dz, dz + nz);
   pl->rho0.assign(rho0, rho0 + nz);
-  if (!make_fft_plan(nx / 2, pl->fx) || !make_fft_plan(ny, pl->fy)) {
+  if (!make_fft_plan(nx / 2, pl->fx, pl->xelems) || !make_fft_plan(ny, pl->fy, pl->yelems)) {
     delete pl;
     return POISSON_ERR_UNSUPPORTED;
   }
@@ -261,6 +262,8 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
   pl->g.N = (long long)nx * ny * nz;
   pl->g.dx = dx;
   pl->g.dy = dy;
+  pl->g.lev0 = 0;
+  pl->g.lev1 = nz;
   pl->cx = split_host(1.0 / (dx * dx));
   pl->cy = split_host(1.0 / (dy * dy));
 
@@ -395,6 +398,27 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value >= 0 && value <= 64)) return POISSON_ERR_INVALID_ARG;
       pl->ytile = (int)value;
       return POISSON_OK;
+    case POISSON_OPT_X_ELEMS:
+    case POISSON_OPT_Y_ELEMS: {
+      if (!(value == 8 || value == 16)) return POISSON_ERR_INVALID_ARG;
+      FftPlan f{};
+      const bool x = option == POISSON_OPT_X_ELEMS;
+      if (!make_fft_plan(x ? pl->nx / 2 : pl->ny, f, (int)value)) return POISSON_ERR_UNSUPPORTED;
+      if (x) {
+        pl->xelems = (int)value;
+        pl->fx = f;
+        pl->xinv_blocks = xpass_blocks(pl->g, pl->fx, pl->csize());
+        layout_workspace(pl);
+      } else {
+        pl->yelems = (int)value;
+        pl->fy = f;
+      }
+      return POISSON_OK;
+    }
+    case POISSON_OPT_LEVEL_CHUNK:
+      if (!(value >= 0 && value <= 4096)) return POISSON_ERR_INVALID_ARG;
+      pl->lchunk = (int)value;
+      return POISSON_OK;
     case POISSON_OPT_Y_KERNEL:
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->ykernel = (int)value;
@@ -448,32 +472,48 @@ static int check_ws(const poisson_plan* pl, void* ws) {
 }
 
 // y-pass: the persistent TMA kernel where the shape allows, else the plain one.
-static cudaError_t ypass(poisson_plan* pl, int sign, void* spec, const int* done, Stats* stats, cudaStream_t st) {
+static cudaError_t ypass(poisson_plan* pl, const Geom& g, int sign, void* spec, const int* done, Stats* stats,
+                         cudaStream_t st) {
   const bool t_double = pl->fp64();
   if (pl->ykernel == 0) {
     bool used = false;
-    cudaError_t e = launch_yfft_tma(t_double, sign, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, stats, st, &used);
+    cudaError_t e = launch_yfft_tma(t_double, sign, spec, g, pl->fy, pl->tb, pl->ytile, done, stats, st, &used);
     if (e != cudaSuccess || used) return e;
   }
-  return launch_yfft(t_double, sign, spec, pl->g, pl->fy, pl->tb, pl->ytile, done, st);
+  return launch_yfft(t_double, sign, spec, g, pl->fy, pl->tb, pl->ytile, done, st);
 }
 
-// Forward transform -> column solve -> inverse transform of one field.
-static cudaError_t run_pipeline(poisson_plan* pl, const void* in, int in_double, char* ws, cudaStream_t st,
-                                int adjoint, const int* done, const double* target_mean = nullptr,
-                                const ResidualArgs* R = nullptr) {
+// Levels per chunk of the transforms: x-pass and y-pass of a chunk run back to
+// back, so the chunk's spectrum (about 32 MB by default) stays in L2 between them.
+static int level_chunk(const poisson_plan* pl) {
+  int c = pl->lchunk;
+  if (c <= 0) c = (int)(32.0 * 1024 * 1024 / ((double)pl->g.plane * (double)pl->csize()));
+  return c < 1 ? 1 : (c > pl->nz ? pl->nz : c);
+}
+
+// Forward transform (chunked x-pass then y-pass) and column solve of one field.
+static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_double, char* ws, cudaStream_t st,
+                                   int adjoint, const int* done, const double* target_mean = nullptr,
+                                   const ResidualArgs* R = nullptr) {
   const bool t_double = pl->fp64();
   void* spec = ws + pl->off_spec;
   Stats* stats = (Stats*)(ws + pl->off_stats);
-  int ps = prof_begin(pl, POISSON_PHASE_XFWD, st);
-  cudaError_t e = R ? launch_xfwd_residual(*R, spec, pl->g, pl->fx, pl->tb, done, st)
-                    : launch_xfwd(in_double, t_double, in, spec, pl->g, pl->fx, pl->tb, done, st);
-  prof_end(pl, ps, st);
-  if (e != cudaSuccess) return e;
-  ps = prof_begin(pl, POISSON_PHASE_YFWD, st);
-  e = ypass(pl, -1, spec, done, stats, st);
-  prof_end(pl, ps, st);
-  if (e != cudaSuccess) return e;
+  const int lc = level_chunk(pl);
+  cudaError_t e = cudaSuccess;
+  for (int l0 = 0; l0 < pl->nz; l0 += lc) {
+    Geom gc = pl->g;
+    gc.lev0 = l0;
+    gc.lev1 = l0 + lc < pl->nz ? l0 + lc : pl->nz;
+    int ps = prof_begin(pl, POISSON_PHASE_XFWD, st);
+    e = R ? launch_xfwd_residual(*R, spec, gc, pl->fx, pl->tb, done, st)
+          : launch_xfwd(in_double, t_double, in, spec, gc, pl->fx, pl->tb, done, st);
+    prof_end(pl, ps, st);
+    if (e != cudaSuccess) return e;
+    ps = prof_begin(pl, POISSON_PHASE_YFWD, st);
+    e = ypass(pl, gc, -1, spec, done, stats, st);
+    prof_end(pl, ps, st);
+    if (e != cudaSuccess) return e;
+  }
   ThomasArgs A{};
   A.spec = spec;
   A.t_is_double = t_double;
@@ -488,13 +528,39 @@ static cudaError_t run_pipeline(poisson_plan* pl, const void* in, int in_double,
   A.stats = stats;
   A.done = done;
   A.target_mean = target_mean;
-  ps = prof_begin(pl, POISSON_PHASE_COLUMNS, st);
+  const int ps = prof_begin(pl, POISSON_PHASE_COLUMNS, st);
   e = launch_thomas(A, pl->g, pl->tb, st);
   prof_end(pl, ps, st);
-  if (e != cudaSuccess) return e;
-  ps = prof_begin(pl, POISSON_PHASE_YINV, st);
-  e = ypass(pl, +1, spec, done, stats, st);
-  prof_end(pl, ps, st);
+  return e;
+}
+
+// Inverse transform (chunked y-pass then x-pass with the given epilogue);
+// *nparts receives the number of partial-sum slots the x-pass launches wrote.
+static cudaError_t inverse(poisson_plan* pl, char* ws, cudaStream_t st, const int* done, int to_double, int mode,
+                           void* out, XinvExtra ex, int* nparts) {
+  const bool t_double = pl->fp64();
+  void* spec = ws + pl->off_spec;
+  Stats* stats = (Stats*)(ws + pl->off_stats);
+  const int lc = level_chunk(pl);
+  int part = 0;
+  cudaError_t e = cudaSuccess;
+  for (int l0 = 0; l0 < pl->nz; l0 += lc) {
+    Geom gc = pl->g;
+    gc.lev0 = l0;
+    gc.lev1 = l0 + lc < pl->nz ? l0 + lc : pl->nz;
+    int ps = prof_begin(pl, POISSON_PHASE_YINV, st);
+    e = ypass(pl, gc, +1, spec, done, stats, st);
+    prof_end(pl, ps, st);
+    if (e != cudaSuccess) return e;
+    ex.part0 = part;
+    int nb = 0;
+    ps = prof_begin(pl, POISSON_PHASE_XINV, st);
+    e = launch_xinv(t_double, to_double, mode, spec, out, gc, pl->fx, pl->tb, ex, &nb, st);
+    prof_end(pl, ps, st);
+    if (e != cudaSuccess) return e;
+    part += nb;
+  }
+  if (nparts) *nparts = part;
   return e;
 }
 
@@ -535,44 +601,34 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
   XinvExtra ex{};
   ex.partials = (double*)(ws + pl->off_part);
   if (!pl->mixed()) {
-    PGB_CUDA(run_pipeline(pl, S, t_double, ws, st, 0, nullptr));
-    const int ps = prof_begin(pl, POISSON_PHASE_XINV, st);
-    const cudaError_t e = launch_xinv(t_double, t_double, XINV_PLAIN, ws + pl->off_spec, p, pl->g, pl->fx, pl->tb,
-                                      ex, nullptr, st);
-    prof_end(pl, ps, st);
-    PGB_CUDA(e);
+    PGB_CUDA(forward_columns(pl, S, t_double, ws, st, 0, nullptr));
+    PGB_CUDA(inverse(pl, ws, st, nullptr, t_double, XINV_PLAIN, p, ex, nullptr));
   } else {
     const int* done = &stats->done;
     float* p0 = (float*)(ws + pl->off_p0);
     float* q = (float*)(ws + pl->off_q);
     int nb = 0;
     // first solve: double source, float transforms, double low-|k| columns
-    PGB_CUDA(run_pipeline(pl, S, 1, ws, st, 0, nullptr));
+    PGB_CUDA(forward_columns(pl, S, 1, ws, st, 0, nullptr));
     ex.p0 = p0;
     ex.p_out = pl->max_sweeps == 0 ? (double*)p : nullptr;
-    int ps = prof_begin(pl, POISSON_PHASE_XINV, st);
-    cudaError_t e = launch_xinv(0, 0, XINV_P0, ws + pl->off_spec, p0, pl->g, pl->fx, pl->tb, ex, &nb, st);
-    prof_end(pl, ps, st);
-    PGB_CUDA(e);
-    ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-    e = launch_control(stats, ex.partials, nb, 0, pl->max_sweeps, pl->tol, pl->g.N, st);
+    PGB_CUDA(inverse(pl, ws, st, nullptr, 0, XINV_P0, p0, ex, &nb));
+    int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
+    cudaError_t e = launch_control(stats, ex.partials, nb, 0, pl->max_sweeps, pl->tol, pl->g.N, st);
     prof_end(pl, ps, st);
     PGB_CUDA(e);
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
       // residual computed inside the forward x-pass (its rows are never stored)
       const ResidualArgs R{(const double*)S, p0, sweep > 1 ? q : nullptr, pl->tb.a_ff, pl->tb.c_ff,
                            pl->cx,           pl->cy, &stats->mu_ff};
-      PGB_CUDA(run_pipeline(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R));
+      PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R));
       XinvExtra eu = ex;
       eu.p0 = p0;
       eu.q = q;
       eu.q_valid = sweep > 1;
       eu.p_out = (double*)p;
       eu.done = done;
-      ps = prof_begin(pl, POISSON_PHASE_XINV, st);
-      e = launch_xinv(0, 0, XINV_UPDATE, ws + pl->off_spec, nullptr, pl->g, pl->fx, pl->tb, eu, &nb, st);
-      prof_end(pl, ps, st);
-      PGB_CUDA(e);
+      PGB_CUDA(inverse(pl, ws, st, done, 0, XINV_UPDATE, nullptr, eu, &nb));
       ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
       e = launch_control(stats, ex.partials, nb, sweep, pl->max_sweeps, pl->tol, pl->g.N, st);
       prof_end(pl, ps, st);
@@ -598,9 +654,9 @@ int poisson_solve_adjoint(poisson_plan* pl, const void* gp, const void* p, void*
   PGB_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), st));
   const bool t_double = pl->fp64();
   const int io_double = pl->dtype != POISSON_FP32;
-  PGB_CUDA(run_pipeline(pl, gp, io_double, ws, st, 1, nullptr));
+  PGB_CUDA(forward_columns(pl, gp, io_double, ws, st, 1, nullptr));
   XinvExtra ex{};
-  PGB_CUDA(launch_xinv(t_double, io_double, XINV_PLAIN, ws + pl->off_spec, gS, pl->g, pl->fx, pl->tb, ex, nullptr, st));
+  PGB_CUDA(inverse(pl, ws, st, nullptr, io_double, XINV_PLAIN, gS, ex, nullptr));
   if (grho) {
     const int kind = pl->fp64() ? 0 : (pl->dtype == POISSON_FP32 ? 1 : 2);
     PGB_CUDA(launch_grho(kind, gS, p, pl->g, pl->tb, pl->dz_d, pl->rho_d, (double*)(ws + pl->off_gp), pl->grho_nb,

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const TI* __restrict__ in, typenam
   C* sm = reinterpret_cast<C*>(smraw);
   const int n = fx.n, nl = n / E;
   const int lane = threadIdx.x, ty = threadIdx.y;
-  const long long row = (long long)blockIdx.x * blockDim.y + ty;
+  const long long row = (long long)g.lev0 * g.ny + (long long)blockIdx.x * blockDim.y + ty;
   const bool valid = row < nrows;
   C* line = sm + ty * swizzled_stride(n + 1);
   const Swizzled sw{};
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const TI* __restrict__ in, typenam
       const int m = lane + nl * q;
       C z = make_c<T>(0, 0);
       if (valid) {
-        const typename V2<TI>::t v = src[m];
+        const typename V2<TI>::t v = __ldcs(&src[m]);   // read once: stream past L2
         z.x = Cvt<TI, T>::f(v.x);
         z.y = Cvt<TI, T>::f(v.y);
       }
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
   C* sm = reinterpret_cast<C*>(smraw);
   const int n = fx.n, nl = n / E;
   const int lane = threadIdx.x, ty = threadIdx.y;
-  const long long row = (long long)blockIdx.x * blockDim.y + ty;
+  const long long row = (long long)g.lev0 * g.ny + (long long)blockIdx.x * blockDim.y + ty;
   const bool valid = row < nrows;
   C* line = sm + ty * swizzled_stride(n + 1);
   const Swizzled sw{};
@@ -147,15 +147,15 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
       typename V2<TO>::t v;
       v.x = Cvt<T, TO>::f(z.x);
       v.y = Cvt<T, TO>::f(z.y);
-      reinterpret_cast<typename V2<TO>::t*>(out + base)[m] = v;
+      __stcs(reinterpret_cast<typename V2<TO>::t*>(out + base) + m, v);
     } else if constexpr (MODE == XINV_P0) {
-      reinterpret_cast<float2*>(ex.p0 + base)[m] = make_float2(z.x, z.y);
+      __stcs(reinterpret_cast<float2*>(ex.p0 + base) + m, make_float2(z.x, z.y));
       acc1 += z.x * z.x + z.y * z.y;
       float e0, e1;
       two_sum(sh, z.x, sh, e0);
       two_sum(sh, z.y, sh, e1);
       sl += e0 + e1;
-      if (ex.p_out) reinterpret_cast<double2*>(ex.p_out + base)[m] = make_double2(f2d_int(z.x), f2d_int(z.y));
+      if (ex.p_out) __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(f2d_int(z.x), f2d_int(z.y)));
     } else {  // XINV_UPDATE
       const float2 p0 = reinterpret_cast<const float2*>(ex.p0 + base)[m];
       float2 qn = make_float2(z.x, z.y);
@@ -164,11 +164,11 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
         qn.x += qo.x;
         qn.y += qo.y;
       }
-      reinterpret_cast<float2*>(ex.q + base)[m] = qn;
+      __stcs(reinterpret_cast<float2*>(ex.q + base) + m, qn);
       float s0, t0, s1, t1;
       two_sum(p0.x, qn.x, s0, t0);
       two_sum(p0.y, qn.y, s1, t1);
-      reinterpret_cast<double2*>(ex.p_out + base)[m] = make_double2(ff2d_int(s0, t0), ff2d_int(s1, t1));
+      __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(ff2d_int(s0, t0), ff2d_int(s1, t1)));
       acc0 += z.x * z.x + z.y * z.y;
       acc1 += s0 * s0 + s1 * s1;
       float e0, e1;
@@ -194,9 +194,10 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
       __syncthreads();
     }
     if (tid == 0) {
-      ex.partials[3 * blockIdx.x] = (double)red[0][0];
-      ex.partials[3 * blockIdx.x + 1] = (double)red[1][0];
-      ex.partials[3 * blockIdx.x + 2] = redd[0];
+      const long long slot = ex.part0 + blockIdx.x;
+      ex.partials[3 * slot] = (double)red[0][0];
+      ex.partials[3 * slot + 1] = (double)red[1][0];
+      ex.partials[3 * slot + 2] = redd[0];
     }
   }
 }
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(ypass_max_threads(E)) k_yfft(typename CT<T>::t
   const int TK = blockDim.x, l = threadIdx.x, lane = threadIdx.y;
   const int nl = fy.n / E;
   const int kx0 = blockIdx.x * TK;
-  C* base = spec + (long long)blockIdx.y * g.plane + kx0;
+  C* base = spec + (long long)(g.lev0 + blockIdx.y) * g.plane + kx0;
   const bool vcol = (kx0 + l) < g.nxh;
 #pragma unroll
   for (int q = 0; q < E; ++q) {
@@ -292,11 +293,11 @@ template <typename TI, typename T>
 static cudaError_t xfwd_t(const TI* in, typename CT<T>::t* spec, const Geom& g, const FftPlan& fx,
                           const typename CT<T>::t* twx, const typename CT<T>::t* twr, const int* done,
                           cudaStream_t st) {
-  const long long nrows = (long long)g.ny * g.nz;
+  const long long nrows = (long long)g.ny * g.lev1;   // end row of the chunk
   const int n = fx.n;
   const int rb = xpass_rows(n, fx.E, sizeof(typename CT<T>::t));
   const dim3 block(n / fx.E, rb);
-  const long long nb = (nrows + rb - 1) / rb;
+  const long long nb = ((long long)g.ny * (g.lev1 - g.lev0) + rb - 1) / rb;
   const size_t smem = (size_t)rb * swizzled_stride(n + 1) * sizeof(typename CT<T>::t);
   if (smem > kMaxDynSmem || nb > 0x7fffffffLL) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
@@ -312,11 +313,11 @@ static cudaError_t xfwd_t(const TI* in, typename CT<T>::t* spec, const Geom& g, 
 cudaError_t launch_xfwd_residual(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx,
                                  const Tables& tb, const int* done, cudaStream_t st) {
   using C = float2;
-  const long long nrows = (long long)g.ny * g.nz;
+  const long long nrows = (long long)g.ny * g.lev1;   // end row of the chunk
   const int n = fx.n;
   const int rb = xpass_rows(n, fx.E, sizeof(C));
   const dim3 block(n / fx.E, rb);
-  const long long nb = (nrows + rb - 1) / rb;
+  const long long nb = ((long long)g.ny * (g.lev1 - g.lev0) + rb - 1) / rb;
   const size_t smem = (size_t)rb * swizzled_stride(n + 1) * sizeof(C);
   if (smem > kMaxDynSmem || nb > 0x7fffffffLL) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
@@ -353,11 +354,11 @@ template <typename T, typename TO, int MODE>
 static cudaError_t xinv_t(const typename CT<T>::t* spec, TO* out, const Geom& g, const FftPlan& fx,
                           const typename CT<T>::t* twx, const typename CT<T>::t* twr, const XinvExtra& ex,
                           int* nblocks_out, cudaStream_t st) {
-  const long long nrows = (long long)g.ny * g.nz;
+  const long long nrows = (long long)g.ny * g.lev1;   // end row of the chunk
   const int n = fx.n;
   const int rb = xpass_rows(n, fx.E, sizeof(typename CT<T>::t));
   const dim3 block(n / fx.E, rb);
-  const long long nb = (nrows + rb - 1) / rb;
+  const long long nb = ((long long)g.ny * (g.lev1 - g.lev0) + rb - 1) / rb;
   const size_t smem = (size_t)rb * swizzled_stride(n + 1) * sizeof(typename CT<T>::t);
   if (nblocks_out) *nblocks_out = (int)nb;
   if (smem > kMaxDynSmem || nb > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -405,7 +406,7 @@ static cudaError_t yfft_t(typename CT<T>::t* spec, const Geom& g, const FftPlan&
                           const typename CT<T>::t* twy, int tile, const int* done, cudaStream_t st) {
   const int tk = ypass_tile(tile, fy.n, fy.E, sizeof(typename CT<T>::t));
   const dim3 block(tk, fy.n / fy.E);
-  const dim3 grid((g.nxh + tk - 1) / tk, g.nz);
+  const dim3 grid((g.nxh + tk - 1) / tk, g.lev1 - g.lev0);
   const size_t smem = (size_t)tk * fy.n * sizeof(typename CT<T>::t);
   if (smem > kMaxDynSmem || (int)(block.x * block.y) > ypass_max_threads(fy.E)) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;

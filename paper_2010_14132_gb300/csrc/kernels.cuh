@@ -41,6 +41,7 @@ struct Geom {
   long long plane;             // ny * P
   long long N;                 // nx * ny * nz
   double dx, dy;
+  int lev0, lev1;              // levels [lev0, lev1) processed by a transform launch (a chunk)
 };
 
 // Output handling of the inverse x-pass.
@@ -56,6 +57,7 @@ struct XinvExtra {
   int q_valid;          // UPDATE: q holds a previous correction
   double* p_out;        // P0 (when final) / UPDATE: double output field
   double* partials;     // per-block partial sums (3 per block: delta^2, p^2, sum p)
+  int part0;            // partial-sum slot of this launch's first block
   const int* done;      // skip when set (nullable)
 };
 

@@ -85,7 +85,7 @@ __device__ __forceinline__ float residual_point(const ResidualArgs& R, const Geo
   FF tz{s2, (l1 + l2) + e2};
   FF Lp = ff_add(ff_add(tx, ty), tz);
   float sh, sl, th, tl;
-  d2ff_int(R.S[idx], sh, sl);
+  d2ff_int(__ldcs(&R.S[idx]), sh, sl);   // S is read once per sweep: stream past L2
   const float2 mu = *R.mu_ff;
   two_sum(sh, -mu.x, th, tl);
   tl += sl - mu.y;

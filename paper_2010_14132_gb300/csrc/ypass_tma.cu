@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(512) k_yfft_tma(const __grid_constant__ CUtens
     for (int r0 = 0; r0 < ny; r0 += box_rows)
       tma_load_2d(dst + (size_t)r0 * TK, &tm, kx0 * XM, level * ny + r0, b);
   };
-  int t = blockIdx.x;
+  // tiles of the levels [g.lev0, g.lev1) of this launch
+  int t = g.lev0 * tiles_per_level + blockIdx.x;
   if (tid == 0 && t < ntiles) issue_load(t, buf[0], &bar[0]);
   bool ok = true;
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
@@ -148,7 +149,8 @@ static cudaError_t yfft_tma_t(typename CT<T>::t* spec, const Geom& g, const FftP
                         (unsigned long long)g.P * sizeof(C), (unsigned)(tk * XM), (unsigned)box_rows))
     return cudaSuccess;   // fall back to the plain y-pass
   const int tiles_per_level = (g.nxh + tk - 1) / tk;
-  const int ntiles = tiles_per_level * g.nz;
+  const int ntiles = tiles_per_level * g.lev1;   // end tile of the chunk
+  const int chunk_tiles = tiles_per_level * (g.lev1 - g.lev0);
   const size_t smem = 2 * ((((size_t)tk * fy.n * sizeof(C)) + 127) & ~(size_t)127) + 64;
   const dim3 block(tk, fy.n / fy.E);
   cudaError_t e = cudaSuccess;
@@ -162,7 +164,7 @@ static cudaError_t yfft_tma_t(typename CT<T>::t* spec, const Geom& g, const FftP
     if (e != cudaSuccess) return e;                                                                             \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block.x * block.y, smem);                      \
     if (per_sm < 1) return cudaSuccess;                                                                         \
-    const int grid = ntiles < sms * per_sm ? ntiles : sms * per_sm;                                             \
+    const int grid = chunk_tiles < sms * per_sm ? chunk_tiles : sms * per_sm;                                   \
     kern<<<grid, block, smem, st>>>(tm, g, fy, twy, box_rows, tiles_per_level, ntiles, done, stats);            \
     *used = true;                                                                                               \
   } break;

@@ -100,6 +100,17 @@ def test_sizes_mixed(nx, ny, nz):
     check(d, "mixed")
 
 
+@pytest.mark.parametrize("opts", [dict(x_elems=16), dict(y_elems=8), dict(x_elems=8, y_elems=8, y_tile=4),
+                                  dict(y_kernel=1, y_tile=16, y_elems=8), dict(y_tile=2), dict(y_tile=16),
+                                  dict(level_chunk=1), dict(level_chunk=5), dict(level_chunk=7, y_kernel=1),
+                                  dict(level_chunk=4096)])
+@pytest.mark.parametrize("dtype", ["fp64", "mixed"])
+def test_kernel_shape_options(opts, dtype):
+    """Every autotuner candidate gives the same answer (tile shapes are not numerics)."""
+    d = wl.anelastic_noise(256, 128, 24, seed=17)
+    check(d, dtype, **opts)
+
+
 # ---------------------------------------------------------------------------
 # closed forms and degenerate cases (no oracle on the expected side)
 # ---------------------------------------------------------------------------
