@@ -286,11 +286,14 @@ def main():
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # profiler range = the timed region (ncu --profile-from-start off captures only these launches)
+    torch.cuda.profiler.start()
     e0.record(stream)
     for _ in range(args.steps):
         plan.solve(S, out=p)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     barrier()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps

@@ -2,7 +2,8 @@
 
 For one grid (nx, ny, nz, dtype) it times candidate settings of the y-pass
 (TMA-staged or plain kernel, kx tile width, elements per thread) and of the
-x-pass (elements per thread), using the library's own per-phase CUDA events
+x-pass (persistent bulk-copy-staged kernel, or one CTA per row group with 8 or
+16 elements per thread), using the library's own per-phase CUDA events
 (POISSON_OPT_PROFILE) on the launching stream, and keeps the fastest setting of
 each pass.  Results are cached in a JSON file keyed by GPU name, sizes and
 dtype, so a plan is tuned once and the choice reused every solve (the
@@ -27,10 +28,11 @@ CACHE = os.environ.get("POISSON_AUTOTUNE_CACHE",
                        os.path.join(os.path.expanduser("~"), ".cache", "poisson_gb300_autotune.json"))
 
 Y_CANDIDATES = [dict(y_kernel=k, y_tile=t, y_elems=e) for k in (0, 1) for t in (2, 4, 8, 16) for e in (8, 16)]
-X_CANDIDATES = [dict(x_elems=e) for e in (8, 16)]
+X_CANDIDATES = [dict(x_kernel=0, x_elems=8)] + [dict(x_kernel=1, x_elems=e) for e in (8, 16)]
 CHUNK_CANDIDATES = [dict(level_chunk=c) for c in (0, 1, 2, 4, 8, 16, 4096)]
 OPT_IDS = {"y_kernel": N.POISSON_OPT_Y_KERNEL, "y_tile": N.POISSON_OPT_Y_TILE, "y_elems": N.POISSON_OPT_Y_ELEMS,
-           "x_elems": N.POISSON_OPT_X_ELEMS, "level_chunk": N.POISSON_OPT_LEVEL_CHUNK}
+           "x_elems": N.POISSON_OPT_X_ELEMS, "level_chunk": N.POISSON_OPT_LEVEL_CHUNK,
+           "x_kernel": N.POISSON_OPT_X_KERNEL}
 
 
 def _key(nx, ny, nz, dtype):

@@ -75,7 +75,7 @@ struct poisson_plan {
   int dtype = 0;
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
-  int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0, xelems = 8, yelems = 16, lchunk = 0;
+  int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0;
   double tol = 1e-11;
   Geom g{};
   Tables tb{};
@@ -423,6 +423,10 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->ykernel = (int)value;
       return POISSON_OK;
+    case POISSON_OPT_X_KERNEL:
+      if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
+      pl->xkernel = (int)value;
+      return POISSON_OK;
     case POISSON_OPT_PROFILE:
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->prof.on = value != 0;
@@ -505,8 +509,14 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
     gc.lev0 = l0;
     gc.lev1 = l0 + lc < pl->nz ? l0 + lc : pl->nz;
     int ps = prof_begin(pl, POISSON_PHASE_XFWD, st);
-    e = R ? launch_xfwd_residual(*R, spec, gc, pl->fx, pl->tb, done, st)
-          : launch_xfwd(in_double, t_double, in, spec, gc, pl->fx, pl->tb, done, st);
+    if (R) {
+      e = launch_xfwd_residual(*R, spec, gc, pl->fx, pl->tb, done, st);
+    } else {
+      bool used = false;
+      if (!t_double && pl->xkernel == 0)
+        e = launch_xfwd_static(in_double, in, spec, gc, pl->fx, pl->tb, done, &stats->err, st, &used);
+      if (e == cudaSuccess && !used) e = launch_xfwd(in_double, t_double, in, spec, gc, pl->fx, pl->tb, done, st);
+    }
     prof_end(pl, ps, st);
     if (e != cudaSuccess) return e;
     ps = prof_begin(pl, POISSON_PHASE_YFWD, st);
@@ -555,7 +565,11 @@ static cudaError_t inverse(poisson_plan* pl, char* ws, cudaStream_t st, const in
     ex.part0 = part;
     int nb = 0;
     ps = prof_begin(pl, POISSON_PHASE_XINV, st);
-    e = launch_xinv(t_double, to_double, mode, spec, out, gc, pl->fx, pl->tb, ex, &nb, st);
+    bool used = false;
+    ex.err = &stats->err;
+    if (!t_double && pl->xkernel == 0)
+      e = launch_xinv_static(to_double, mode, spec, out, gc, pl->fx, pl->tb, ex, &nb, st, &used);
+    if (e == cudaSuccess && !used) e = launch_xinv(t_double, to_double, mode, spec, out, gc, pl->fx, pl->tb, ex, &nb, st);
     prof_end(pl, ps, st);
     if (e != cudaSuccess) return e;
     part += nb;

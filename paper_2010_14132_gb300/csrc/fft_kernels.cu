@@ -286,7 +286,13 @@ static int xpass_rows(int n, int E, size_t csize) {
 int xpass_blocks(const Geom& g, const FftPlan& fx, size_t csize) {
   const long long nrows = (long long)g.ny * g.nz;
   const int rb = xpass_rows(fx.n, fx.E, csize);
-  return (int)((nrows + rb - 1) / rb);
+  long long nb = (nrows + rb - 1) / rb;
+  if (csize == sizeof(float2) && xpass_static_supported(fx.n)) {
+    const long long rbs = 256 / (fx.n / 8);   // rows per group of the persistent kernels
+    const long long ng = (nrows + rbs - 1) / rbs;
+    if (ng > nb) nb = ng;
+  }
+  return (int)nb;
 }
 
 template <typename TI, typename T>

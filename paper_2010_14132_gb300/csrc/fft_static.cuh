@@ -1,0 +1,140 @@
+// Stockham FFT with the line length known at compile time.
+//
+// Same transform as fft_engine.cuh (stage s of radix R and span Ns takes inputs
+// x[j + r n/R], applies exp(SIGN 2 pi i r (j mod Ns)/(Ns R)), an R-point DFT,
+// and writes y[(j - j mod Ns) R + j mod Ns + r Ns]), with every index, span and
+// table stride a constant, so the per-element work is the butterfly itself plus
+// one shared-memory access.  The values of a thread stay in registers between
+// stages; consecutive stages alternate between two shared buffers, so one
+// barrier per stage suffices.  The caller supplies the first stage's inputs in
+// registers (loaded in whatever way suits it) and receives the result either in
+// registers (last stage's layout) or in natural order in a shared buffer.
+#pragma once
+#include "fft_engine.cuh"
+
+namespace pgb {
+
+// Radix schedule for n = 2^a 3^b: radix-3 stages, then radix 8, then a final 2 or 4.
+constexpr int st_count(int n, int p) {
+  int c = 0;
+  while (n > 1 && n % p == 0) {
+    n /= p;
+    ++c;
+  }
+  return c;
+}
+constexpr int st_nstages(int n) {
+  return st_count(n, 3) + st_count(n, 2) / 3 + (st_count(n, 2) % 3 ? 1 : 0);
+}
+constexpr int st_radix(int n, int s) {
+  const int a = st_count(n, 2), b = st_count(n, 3);
+  if (s < b) return 3;
+  if (s - b < a / 3) return 8;
+  return (a % 3 == 1) ? 2 : 4;
+}
+constexpr int st_span(int n, int s) {
+  int ns = 1;
+  for (int i = 0; i < s; ++i) ns *= st_radix(n, i);
+  return ns;
+}
+// E elements per thread must be a multiple of every radix of the schedule.
+constexpr bool st_valid(int n, int e) {
+  if (n < 2 || e < 1 || n % e != 0) return false;
+  for (int s = 0; s < st_nstages(n); ++s)
+    if (e % st_radix(n, s) != 0) return false;
+  return st_span(n, st_nstages(n)) == n;
+}
+
+// Element index held in slot i = q R + r of a thread before stage s (inputs x[j + r n/R]).
+template <int N, int E, int S> __device__ __forceinline__ int st_in_index(int lane, int i) {
+  constexpr int R = st_radix(N, S), nl = N / E, m = N / R;
+  return lane + nl * (i / R) + (i % R) * m;
+}
+// Element index held in slot i after the last stage, when it stays in registers.
+template <int N, int E> __device__ __forceinline__ int st_out_index(int lane, int i) {
+  constexpr int S = st_nstages(N) - 1, R = st_radix(N, S), nl = N / E, Ns = st_span(N, S);
+  // last stage: j < Ns, so j mod Ns = j and the outputs are y[j + r Ns]
+  return lane + nl * (i / R) + (i % R) * Ns;
+}
+
+// Per-line barrier among the nl threads of a line.  Lines of at most 32 threads
+// live inside one warp; wider lines use a named barrier per line (ids 1..15).
+struct LineSync {
+  int id, nthreads;
+  __device__ __forceinline__ void operator()() const {
+    if (nthreads <= 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+  }
+};
+
+template <int R, int E, int N, int Ns, int SIGN, typename T>
+__device__ __forceinline__ void st_butterflies(typename CT<T>::t (&v)[E], int lane,
+                                               const typename CT<T>::t* __restrict__ tw) {
+  constexpr int B = E / R, nl = N / E, stride = N / (Ns * R);
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    if constexpr (Ns > 1) {
+      const int k = (lane + nl * q) % Ns;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q * R + r] = tw_apply<SIGN>(v[q * R + r], tw[r * k * stride]);
+    }
+    dft_r<R, SIGN, T>(&v[q * R]);
+  }
+}
+
+template <int R, int E, int N, int Ns, typename C, typename Addr>
+__device__ __forceinline__ void st_store(const C (&v)[E], C* buf, Addr addr, int lane) {
+  constexpr int B = E / R, nl = N / E;
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    const int j = lane + nl * q;
+    const int k = j % Ns;
+    const int d = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[addr(d + r * Ns)] = v[q * R + r];
+  }
+}
+
+template <int R, int E, int N, typename C, typename Addr>
+__device__ __forceinline__ void st_load(C (&v)[E], const C* buf, Addr addr, int lane) {
+  constexpr int B = E / R, nl = N / E, m = N / R;
+#pragma unroll
+  for (int q = 0; q < B; ++q)
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[q * R + r] = buf[addr(lane + nl * q + r * m)];
+}
+
+template <int N, int E, int SIGN, bool FINAL_IN_REGS, int S, typename T, typename Addr, typename Sync>
+__device__ __forceinline__ typename CT<T>::t* st_run_from(typename CT<T>::t (&v)[E], typename CT<T>::t* cur,
+                                                          typename CT<T>::t* nxt, Addr addr, int lane,
+                                                          const typename CT<T>::t* __restrict__ tw, Sync sync) {
+  constexpr int NST = st_nstages(N), R = st_radix(N, S), Ns = st_span(N, S);
+  st_butterflies<R, E, N, Ns, SIGN, T>(v, lane, tw);
+  if constexpr (S == NST - 1 && FINAL_IN_REGS) {
+    return nullptr;
+  } else {
+    st_store<R, E, N, Ns>(v, cur, addr, lane);
+    sync();
+    if constexpr (S == NST - 1) {
+      return cur;
+    } else {
+      st_load<st_radix(N, S + 1), E, N>(v, cur, addr, lane);
+      return st_run_from<N, E, SIGN, FINAL_IN_REGS, S + 1, T>(v, nxt, cur, addr, lane, tw, sync);
+    }
+  }
+}
+
+// All stages.  v: the first stage's inputs (slot i = element st_in_index<N,E,0>).
+// FINAL_IN_REGS: v ends holding element st_out_index<N,E>(lane, i) in slot i and
+// nullptr is returned; otherwise the result is stored in natural order in the
+// returned buffer (a or b).  tw: exp(-2 pi i t/N), t < N, readable by all threads.
+// The caller makes sure no thread of the line still reads a or b from earlier use.
+template <int N, int E, int SIGN, bool FINAL_IN_REGS, typename T, typename Addr, typename Sync>
+__device__ __forceinline__ typename CT<T>::t* st_fft(typename CT<T>::t (&v)[E], typename CT<T>::t* a,
+                                                     typename CT<T>::t* b, Addr addr, int lane,
+                                                     const typename CT<T>::t* __restrict__ tw, Sync sync) {
+  static_assert(st_valid(N, E), "unsupported static FFT shape");
+  return st_run_from<N, E, SIGN, FINAL_IN_REGS, 0, T>(v, a, b, addr, lane, tw, sync);
+}
+
+}  // namespace pgb

@@ -15,6 +15,8 @@ struct Stats {
   double mu_w;            // weighted mean removed from the source (first solve)
   double pmean;           // mean of the current mixed iterate p0 + q (double-float accurate)
   float2 mu_ff;           // mu_w as a double-float pair (set after the first solve)
+  double control_stage[3 * 64];   // per-block sums of the control reduction
+  unsigned control_ticket;        // blocks of the control reduction that have finished
   int done;               // later passes become no-ops once set
   int sweeps;
   int converged;
@@ -59,6 +61,7 @@ struct XinvExtra {
   double* partials;     // per-block partial sums (3 per block: delta^2, p^2, sum p)
   int part0;            // partial-sum slot of this launch's first block
   const int* done;      // skip when set (nullable)
+  unsigned* err;        // ERR_* bits of the persistent kernels (nullable only when they are not used)
 };
 
 // Inputs of the double-float refinement residual r = S - mu_W - L (p0 + q).
@@ -120,7 +123,16 @@ cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math
                         const double* dz, const double* rho0, double* partials, int nparts_max,
                         double* grho, cudaStream_t st);
 
-// Number of CTAs (and so partial-sum slots) of an x-pass launch.
+// Persistent FP32 x-pass for half lengths 64..2048 (powers of two); *used is
+// false (and nothing is launched) when the shape or alignment does not allow it.
+bool xpass_static_supported(int n_half);
+cudaError_t launch_xfwd_static(int ti_is_double, const void* in, void* spec, const Geom& g, const FftPlan& fx,
+                               const Tables& tb, const int* done, unsigned* err, cudaStream_t st, bool* used);
+cudaError_t launch_xinv_static(int to_is_double, int mode, const void* spec, void* out, const Geom& g,
+                               const FftPlan& fx, const Tables& tb, const XinvExtra& ex, int* nblocks_out,
+                               cudaStream_t st, bool* used);
+
+// Upper bound on the CTAs (and so partial-sum slots) of the x-pass launches of one field.
 int xpass_blocks(const Geom& g, const FftPlan& fx, size_t csize);
 
 // Elements per thread the FFT kernels are instantiated for.

@@ -66,18 +66,28 @@ cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q,
 }
 
 // ---------------------------------------------------------------------------
-// Refinement control (one block): sums the x-pass partials in a fixed order,
+// Refinement control: sums the x-pass partials in a fixed order,
 // records ||delta_n||/||p|| and the error estimate, and sets the done flag.
 // Stopping rule: after sweep n >= 1 the remaining error is estimated as
 // rho_n * ||delta_n||/||p|| with the observed contraction rho_n =
 // (||delta_n||/||p||) / (||delta_{n-1}||/||p||) (||delta_0|| = ||p0||).
 // ---------------------------------------------------------------------------
-__global__ void k_control(Stats* st, const double* __restrict__ partials, int nblocks, int pass, int max_sweeps,
-                          double tol, long long npoints) {
-  __shared__ double s0[1024], s1[1024], s2[1024];
+// Stage 1 (kControlBlocks blocks): each block sums a contiguous range of the
+// partials in a fixed order; the last block to finish (ticket counter) sums the
+// block results in block order and applies the stopping rule.  Deterministic.
+constexpr int kControlBlocks = 64;
+
+__global__ void __launch_bounds__(256) k_control(Stats* st, const double* __restrict__ partials, int nblocks,
+                                                  int pass, int max_sweeps, double tol, long long npoints,
+                                                  double* __restrict__ stage, unsigned* __restrict__ ticket) {
+  __shared__ double s0[256], s1[256], s2[256];
+  __shared__ bool last;
+  if (st->done) return;   // later sweeps after convergence: nothing to do
   const int t = threadIdx.x;
+  const int per = (nblocks + gridDim.x - 1) / gridDim.x;
+  const int b0 = blockIdx.x * per, b1 = min(nblocks, b0 + per);
   double a = 0, b = 0, c = 0;
-  for (int i = t; i < nblocks; i += blockDim.x) {
+  for (int i = b0 + t; i < b1; i += blockDim.x) {
     a += partials[3 * i];
     b += partials[3 * i + 1];
     c += partials[3 * i + 2];
@@ -94,12 +104,26 @@ __global__ void k_control(Stats* st, const double* __restrict__ partials, int nb
     }
     __syncthreads();
   }
-  if (t != 0) return;
-  if (st->done) return;
-  st->pmean = s2[0] / (double)npoints;
-  if (pass == 0) st->mu_ff = split_ff(st->mu_w);   // for the residual kernels of the sweeps
-  const double sd = (pass == 0) ? s1[0] : s0[0];
-  const double sp = s1[0];
+  if (t == 0) {
+    stage[3 * blockIdx.x] = s0[0];
+    stage[3 * blockIdx.x + 1] = s1[0];
+    stage[3 * blockIdx.x + 2] = s2[0];
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last || t != 0) return;
+  __threadfence();
+  double sd0 = 0, sp = 0, sm = 0;
+  for (int i = 0; i < (int)gridDim.x; ++i) {
+    sd0 += stage[3 * i];
+    sp += stage[3 * i + 1];
+    sm += stage[3 * i + 2];
+  }
+  *ticket = 0;   // ready for the next pass
+  st->pmean = sm / (double)npoints;
+  if (pass == 0) st->mu_ff = split_ff(st->mu_w);   // for the residual of the sweeps
+  const double sd = (pass == 0) ? sp : sd0;
   st->sq_delta[pass] = sd;
   st->sq_p[pass] = sp;
   const double rel = (sp > 0) ? sqrt(sd / sp) : 0.0;
@@ -127,7 +151,8 @@ __global__ void k_control(Stats* st, const double* __restrict__ partials, int nb
 
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps, double tol,
                            long long npoints, cudaStream_t st) {
-  k_control<<<1, 1024, 0, st>>>(st_dev, partials, nblocks, pass, max_sweeps, tol, npoints);
+  k_control<<<kControlBlocks, 256, 0, st>>>(st_dev, partials, nblocks, pass, max_sweeps, tol, npoints,
+                                            st_dev->control_stage, &st_dev->control_ticket);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,495 @@
+// Persistent x-pass kernels for FP32 transforms of power-of-two half lengths
+// (Section 2.1: the x transform of every row of every level).
+//
+// One CTA per SM slot walks groups of RB consecutive rows.  Each group's input
+// rows (the field rows for the forward pass, the spectrum rows for the inverse)
+// are brought into a ring of shared staging buffers by 1-D bulk copies (TMA)
+// completing on an mbarrier, so the loads of the next groups are in flight
+// while the current group is transformed.  The FFT runs with the line length
+// fixed at compile time (fft_static.cuh) on twiddle tables held in shared memory.
+//
+//  * forward (R2C): rows packed as n/2 complex points z_m = x_2m + i x_2m+1; after
+//    the transform each thread unpacks the pair of bins (k, n/2 - k):
+//      X_k = E_k + w^k O_k,   X_{n/2-k} = conj(E_k - w^k O_k),
+//    with E_k = (Z_k + conj Z_{n/2-k})/2, O_k = -i (Z_k - conj Z_{n/2-k})/2 and
+//    w = exp(-2 pi i/n) (the second form follows from w^{n/2-k} = -conj(w^k)).
+//  * inverse (C2R): each first-stage input z_m is formed directly from the staged
+//    bins X_m and X_{n/2-m} (self-conjugate bins keep their real parts), the
+//    transform's last stage stays in registers, and the epilogue writes the output
+//    (and, in the mixed-precision path, the refinement update and norm partial
+//    sums) straight from registers.
+#include <mutex>
+#include <unordered_map>
+
+#include "async_copy.cuh"
+#include "fft_static.cuh"
+#include "kernels.cuh"
+
+namespace pgb {
+
+namespace {
+
+constexpr int kXsThreads = 256;
+constexpr int kXsMaxStages = 4;
+
+template <typename T> struct V2s;
+template <> struct V2s<float> { using t = float2; };
+template <> struct V2s<double> { using t = double2; };
+
+template <typename TI> __device__ __forceinline__ float to_f(TI x);
+template <> __device__ __forceinline__ float to_f<float>(float x) { return x; }
+template <> __device__ __forceinline__ float to_f<double>(double x) { return d2f_int(x); }
+
+// Shared layout: twiddles (n/2), unpack twiddles (n/2 + 2), RB rows x 2 line
+// buffers, then the staging ring (128-byte aligned) and its mbarriers.
+struct XsLayout {
+  size_t off_stage, off_bar, total;
+};
+__host__ __device__ constexpr size_t xs_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline XsLayout xs_layout(int N, int RB, int ns, unsigned stage_bytes) {
+  XsLayout L{};
+  size_t off = (size_t)N * 8 + (size_t)(N + 2) * 8 + (size_t)RB * 2 * swizzled_stride(N) * 8;
+  L.off_stage = xs_align(off, 128);
+  L.off_bar = xs_align(L.off_stage + (size_t)ns * stage_bytes, 8);
+  L.total = L.off_bar + (size_t)ns * 8;
+  return L;
+}
+
+// Bounded-wait bookkeeping of the staging ring, kept by the issuing thread.
+struct Ring {
+  int issued[kXsMaxStages];
+  int consumed[kXsMaxStages];
+};
+
+__device__ __forceinline__ void ring_drain(Ring& rg, uint64_t* bar, int ns) {
+  // let every copy still in flight land before the CTA's shared memory is released
+  for (int s = 0; s < ns; ++s)
+    for (int c = rg.consumed[s]; c < rg.issued[s]; ++c) mbar_wait_bounded(&bar[s], (unsigned)(c & 1), kWaitPolls);
+}
+
+// ---------------------------------------------------------------------------
+// forward x-pass
+// ---------------------------------------------------------------------------
+template <int N, int E, typename TI>
+__global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in, float2* __restrict__ spec, Geom g,
+                                                      const float2* __restrict__ twx, const float2* __restrict__ twr,
+                                                      int ns, unsigned stage_bytes, const int* __restrict__ done,
+                                                      unsigned* __restrict__ err) {
+  using C = float2;
+  using TI2 = typename V2s<TI>::t;
+  constexpr int nl = N / E, RB = kXsThreads / nl, LS = swizzled_stride(N);
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const XsLayout L = xs_layout(N, RB, ns, stage_bytes);
+  C* tw_s = reinterpret_cast<C*>(smraw);
+  C* twr_s = tw_s + N;
+  C* lines = twr_s + N + 2;
+  unsigned char* stg = smraw + L.off_stage;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + L.off_bar);
+
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * nl + lane;
+  const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
+  const long long ngroups = (row_end - row_begin + RB - 1) / RB;
+  const unsigned row_bytes = (unsigned)(2 * N * sizeof(TI));
+  for (int t = tid; t < N; t += kXsThreads) tw_s[t] = twx[t];
+  for (int t = tid; t <= N / 2; t += kXsThreads) twr_s[t] = twr[t];
+  Ring rg{};
+  if (tid == 0) {
+    for (int s = 0; s < ns; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](long long grp, int s) {
+    const long long r0 = row_begin + grp * RB;
+    const long long nv = row_end - r0 < RB ? row_end - r0 : RB;
+    const unsigned bytes = (unsigned)(nv * row_bytes);
+    mbar_arrive_expect_tx(&bar[s], bytes);
+    bulk_g2s(stg + (size_t)s * stage_bytes, in + r0 * g.nx, bytes, &bar[s]);
+    rg.issued[s]++;
+  };
+  if (tid == 0)
+    for (int s = 0; s < ns; ++s) {
+      const long long grp = blockIdx.x + (long long)s * gridDim.x;
+      if (grp < ngroups) issue(grp, s);
+    }
+  const LineSync sync{1 + ty, nl};
+  const Swizzled sw{};
+  C* la = lines + (size_t)ty * 2 * LS;
+  C* lb = la + LS;
+  bool ok = true;
+  int it = 0;
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+    const int s = it % ns;
+    const bool got = mbar_wait_bounded(&bar[s], (unsigned)((it / ns) & 1), kWaitPolls);
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      rg.consumed[s]++;
+      if (it > 0) {   // every thread is past the previous group: refill its stage
+        const long long gn = grp - gridDim.x + (long long)ns * gridDim.x;
+        if (gn < ngroups) {
+          fence_proxy_async_smem();
+          issue(gn, (it - 1) % ns);
+        }
+      }
+    }
+    const long long row = row_begin + grp * RB + ty;
+    const bool valid = row < row_end;
+    const TI2* srow = reinterpret_cast<const TI2*>(stg + (size_t)s * stage_bytes + (size_t)ty * row_bytes);
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const TI2 x = srow[st_in_index<N, E, 0>(lane, i)];
+      v[i] = make_float2(to_f<TI>(x.x), to_f<TI>(x.y));
+    }
+    const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
+    C* dst = spec + (valid ? row : 0) * g.P;
+#pragma unroll
+    for (int q = 0; q < E / 2; ++q) {
+      const int k = lane + nl * q;   // k < N/2
+      const C A = fin[sw(k)];
+      const C B = cconj(fin[sw(k == 0 ? 0 : N - k)]);
+      const C ev = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
+      const C dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y - B.y));
+      const C wo = cmul(twr_s[k], make_float2(dd.y, -dd.x));   // w^k * (-i dd)
+      if (valid) {
+        dst[k] = cadd(ev, wo);
+        dst[N - k] = cconj(csub(ev, wo));
+      }
+    }
+    if (lane == 0) {   // the self-paired bin k = N/2
+      const C A = fin[sw(N / 2)];
+      const C B = cconj(A);
+      const C ev = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
+      const C dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y - B.y));
+      const C wo = cmul(twr_s[N / 2], make_float2(dd.y, -dd.x));
+      if (valid) dst[N / 2] = cadd(ev, wo);
+    }
+  }
+  if (tid == 0) {
+    if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
+    ring_drain(rg, bar, ns);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// inverse x-pass with the solver's epilogues
+// ---------------------------------------------------------------------------
+template <int N, int E, typename TO, int MODE>
+__global__ void __launch_bounds__(kXsThreads) k_xinv_s(const float2* __restrict__ spec, TO* __restrict__ out, Geom g,
+                                                      const float2* __restrict__ twx, const float2* __restrict__ twr,
+                                                      int ns, unsigned stage_bytes, XinvExtra ex) {
+  using C = float2;
+  constexpr int nl = N / E, RB = kXsThreads / nl, LS = swizzled_stride(N);
+  if (ex.done && *ex.done) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ float red[2][kXsThreads];
+  __shared__ double redd[kXsThreads];
+  const XsLayout L = xs_layout(N, RB, ns, stage_bytes);
+  C* tw_s = reinterpret_cast<C*>(smraw);
+  C* twr_s = tw_s + N;
+  C* lines = twr_s + N + 2;
+  unsigned char* stg = smraw + L.off_stage;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + L.off_bar);
+
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * nl + lane;
+  const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
+  const long long ngroups = (row_end - row_begin + RB - 1) / RB;
+  const unsigned row_bytes = (unsigned)xs_align((size_t)(N + 1) * sizeof(C), 16);
+  for (int t = tid; t < N; t += kXsThreads) tw_s[t] = twx[t];
+  for (int t = tid; t <= N; t += kXsThreads) twr_s[t] = twr[t];
+  Ring rg{};
+  if (tid == 0) {
+    for (int s = 0; s < ns; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](long long grp, int s) {
+    const long long r0 = row_begin + grp * RB;
+    const int nv = (int)(row_end - r0 < RB ? row_end - r0 : RB);
+    mbar_arrive_expect_tx(&bar[s], (unsigned)nv * row_bytes);
+    for (int r = 0; r < nv; ++r)
+      bulk_g2s(stg + (size_t)s * stage_bytes + (size_t)r * row_bytes, spec + (r0 + r) * g.P, row_bytes, &bar[s]);
+    rg.issued[s]++;
+  };
+  if (tid == 0)
+    for (int s = 0; s < ns; ++s) {
+      const long long grp = blockIdx.x + (long long)s * gridDim.x;
+      if (grp < ngroups) issue(grp, s);
+    }
+  const LineSync sync{1 + ty, nl};
+  const Swizzled sw{};
+  C* la = lines + (size_t)ty * 2 * LS;
+  C* lb = la + LS;
+  float acc0 = 0.f, acc1 = 0.f;
+  float sh = 0.f, sl = 0.f;   // double-float running sum of p
+  bool ok = true;
+  int it = 0;
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+    const int s = it % ns;
+    const long long row = row_begin + grp * RB + ty;
+    const bool valid = row < row_end;
+    const long long base = (valid ? row : 0) * g.nx;
+    // epilogue operands, fetched before the transform so that their latency is hidden
+    float2 p0v[E], qv[E];
+    if constexpr (MODE == XINV_UPDATE) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int m = st_out_index<N, E>(lane, i);
+        p0v[i] = valid ? reinterpret_cast<const float2*>(ex.p0 + base)[m] : make_float2(0.f, 0.f);
+        qv[i] = (valid && ex.q_valid) ? reinterpret_cast<const float2*>(ex.q + base)[m] : make_float2(0.f, 0.f);
+      }
+    }
+    const bool got = mbar_wait_bounded(&bar[s], (unsigned)((it / ns) & 1), kWaitPolls);
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      rg.consumed[s]++;
+      if (it > 0) {
+        const long long gn = grp - gridDim.x + (long long)ns * gridDim.x;
+        if (gn < ngroups) {
+          fence_proxy_async_smem();
+          issue(gn, (it - 1) % ns);
+        }
+      }
+    }
+    const C* X = reinterpret_cast<const C*>(stg + (size_t)s * stage_bytes + (size_t)ty * row_bytes);
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int m = st_in_index<N, E, 0>(lane, i);
+      C xk = X[m];
+      C xc = cconj(X[N - m]);
+      if (m == 0) {   // self-conjugate bins: real parts only
+        xk.y = 0.f;
+        xc.y = 0.f;
+      }
+      const C ev = cadd(xk, xc);
+      const C od = cmul(csub(xk, xc), cconj(twr_s[m]));   // * exp(+2 pi i m/n)
+      v[i] = make_float2(ev.x - od.y, ev.y + od.x);        // ev + i od
+    }
+    st_fft<N, E, +1, true, float>(v, la, lb, sw, lane, tw_s, sync);
+    if (valid) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int m = st_out_index<N, E>(lane, i);
+        const C z = v[i];
+        if constexpr (MODE == XINV_PLAIN) {
+          typename V2s<TO>::t o;
+          o.x = Cvt<float, TO>::f(z.x);
+          o.y = Cvt<float, TO>::f(z.y);
+          __stcs(reinterpret_cast<typename V2s<TO>::t*>(out + base) + m, o);
+        } else if constexpr (MODE == XINV_P0) {
+          __stcs(reinterpret_cast<float2*>(ex.p0 + base) + m, z);
+          acc1 += z.x * z.x + z.y * z.y;
+          float e0, e1;
+          two_sum(sh, z.x, sh, e0);
+          two_sum(sh, z.y, sh, e1);
+          sl += e0 + e1;
+          if (ex.p_out)
+            __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(f2d_int(z.x), f2d_int(z.y)));
+        } else {   // XINV_UPDATE
+          const float2 qn = make_float2(z.x + qv[i].x, z.y + qv[i].y);
+          __stcs(reinterpret_cast<float2*>(ex.q + base) + m, qn);
+          float s0, t0, s1, t1;
+          two_sum(p0v[i].x, qn.x, s0, t0);
+          two_sum(p0v[i].y, qn.y, s1, t1);
+          __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(ff2d_int(s0, t0), ff2d_int(s1, t1)));
+          acc0 += z.x * z.x + z.y * z.y;
+          acc1 += s0 * s0 + s1 * s1;
+          float e0, e1;
+          two_sum(sh, s0, sh, e0);
+          two_sum(sh, s1, sh, e1);
+          sl += (e0 + e1) + (t0 + t1);
+        }
+      }
+    }
+  }
+  if (tid == 0) {
+    if (!ok) atomicOr(ex.err, (unsigned)ERR_WAIT_TIMEOUT);
+    ring_drain(rg, bar, ns);
+  }
+  if constexpr (MODE != XINV_PLAIN) {
+    // deterministic CTA partial sums: fixed-order tree over the CTA's threads
+    red[0][tid] = acc0;
+    red[1][tid] = acc1;
+    redd[tid] = f2d_int(sh) + f2d_int(sl);
+    __syncthreads();
+    for (int h = kXsThreads / 2; h > 0; h >>= 1) {
+      if (tid < h) {
+        red[0][tid] += red[0][tid + h];
+        red[1][tid] += red[1][tid + h];
+        redd[tid] += redd[tid + h];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const long long slot = ex.part0 + blockIdx.x;
+      ex.partials[3 * slot] = (double)red[0][0];
+      ex.partials[3 * slot + 1] = (double)red[1][0];
+      ex.partials[3 * slot + 2] = redd[0];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch configuration
+// ---------------------------------------------------------------------------
+constexpr int kXsE = 8;
+
+int sm_count() {
+  static std::mutex mu;
+  static std::unordered_map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 0;
+  cache[dev] = n;
+  return n;
+}
+
+struct XsConfig {
+  int ns = 0;
+  unsigned stage_bytes = 0;
+  size_t smem = 0;
+};
+
+// Staging depth: two CTAs per SM when two stages fit in half the shared memory,
+// else one CTA per SM with up to four stages.
+XsConfig xs_config(int N, unsigned stage_bytes, size_t static_smem) {
+  const int RB = kXsThreads / (N / kXsE);
+  const size_t half = 110 * 1024 - static_smem, full = 220 * 1024 - static_smem;
+  XsConfig c{};
+  c.stage_bytes = stage_bytes;
+  for (int ns = kXsMaxStages; ns >= 2; --ns)
+    if (xs_layout(N, RB, ns, stage_bytes).total <= half) {
+      c.ns = ns;
+      break;
+    }
+  if (c.ns == 0)
+    for (int ns = kXsMaxStages; ns >= 2; --ns)
+      if (xs_layout(N, RB, ns, stage_bytes).total <= full) {
+        c.ns = ns;
+        break;
+      }
+  if (c.ns) c.smem = xs_layout(N, RB, c.ns, stage_bytes).total;
+  return c;
+}
+
+template <typename K> cudaError_t prepare(K kernel, size_t smem, int& grid_cap) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, std::pair<size_t, int>> done;   // smem granted, CTAs per SM
+  std::lock_guard<std::mutex> lock(mu);
+  auto& ent = done[reinterpret_cast<const void*>(kernel)];
+  if (ent.first < smem || ent.second == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kXsThreads, smem);
+    if (e != cudaSuccess) return e;
+    ent = {smem, per_sm};
+  }
+  grid_cap = ent.second * sm_count();
+  return cudaSuccess;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+#define PGB_XS_N_SWITCH(N, ...)                          \
+  switch (N) {                                           \
+    case 64: { constexpr int NN = 64; __VA_ARGS__; } break;     \
+    case 128: { constexpr int NN = 128; __VA_ARGS__; } break;   \
+    case 256: { constexpr int NN = 256; __VA_ARGS__; } break;   \
+    case 512: { constexpr int NN = 512; __VA_ARGS__; } break;   \
+    case 1024: { constexpr int NN = 1024; __VA_ARGS__; } break; \
+    case 2048: { constexpr int NN = 2048; __VA_ARGS__; } break; \
+    default: return cudaSuccess;                         \
+  }
+
+template <typename TI>
+cudaError_t xfwd_s(const TI* in, float2* spec, const Geom& g, int N, const Tables& tb, const int* done, unsigned* err,
+                   cudaStream_t st, bool* used) {
+  const int RB = kXsThreads / (N / kXsE);
+  const unsigned row_bytes = (unsigned)(g.nx * sizeof(TI));
+  const XsConfig c = xs_config(N, RB * row_bytes, 0);
+  if (c.ns == 0 || !aligned16(in) || row_bytes % 16) return cudaSuccess;
+  const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
+  cudaError_t e = cudaSuccess;
+  PGB_XS_N_SWITCH(N, {
+    auto kern = k_xfwd_s<NN, kXsE, TI>;
+    int cap = 0;
+    e = prepare(kern, c.smem, cap);
+    if (e != cudaSuccess) return e;
+    if (cap <= 0) return cudaSuccess;
+    const long long grid = ngroups < cap ? ngroups : cap;
+    if (grid <= 0) return cudaSuccess;
+    kern<<<(unsigned)grid, dim3(NN / kXsE, RB), c.smem, st>>>(in, spec, g, tb.twx_f, tb.twr_f, c.ns, c.stage_bytes,
+                                                              done, err);
+    *used = true;
+  });
+  return cudaGetLastError();
+}
+
+template <typename TO, int MODE>
+cudaError_t xinv_s(const float2* spec, TO* out, const Geom& g, int N, const Tables& tb, const XinvExtra& ex,
+                   int* nblocks_out, cudaStream_t st, bool* used) {
+  const int RB = kXsThreads / (N / kXsE);
+  const unsigned row_bytes = (unsigned)xs_align((size_t)(N + 1) * sizeof(float2), 16);
+  if ((size_t)g.P * sizeof(float2) < row_bytes || (g.P * sizeof(float2)) % 16 || !aligned16(spec)) return cudaSuccess;
+  const XsConfig c = xs_config(N, RB * row_bytes, 4 * 1024);   // + the reduction arrays
+  if (c.ns == 0) return cudaSuccess;
+  const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
+  cudaError_t e = cudaSuccess;
+  PGB_XS_N_SWITCH(N, {
+    auto kern = k_xinv_s<NN, kXsE, TO, MODE>;
+    int cap = 0;
+    e = prepare(kern, c.smem, cap);
+    if (e != cudaSuccess) return e;
+    if (cap <= 0) return cudaSuccess;
+    const long long grid = ngroups < cap ? ngroups : cap;
+    if (grid <= 0) return cudaSuccess;
+    if (nblocks_out) *nblocks_out = (int)grid;
+    kern<<<(unsigned)grid, dim3(NN / kXsE, RB), c.smem, st>>>(spec, out, g, tb.twx_f, tb.twr_f, c.ns, c.stage_bytes,
+                                                              ex);
+    *used = true;
+  });
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool xpass_static_supported(int n_half) {
+  switch (n_half) {
+    case 64: case 128: case 256: case 512: case 1024: case 2048: return true;
+    default: return false;
+  }
+}
+
+cudaError_t launch_xfwd_static(int ti_is_double, const void* in, void* spec, const Geom& g, const FftPlan& fx,
+                               const Tables& tb, const int* done, unsigned* err, cudaStream_t st, bool* used) {
+  *used = false;
+  if (!xpass_static_supported(fx.n)) return cudaSuccess;
+  if (ti_is_double) return xfwd_s<double>((const double*)in, (float2*)spec, g, fx.n, tb, done, err, st, used);
+  return xfwd_s<float>((const float*)in, (float2*)spec, g, fx.n, tb, done, err, st, used);
+}
+
+cudaError_t launch_xinv_static(int to_is_double, int mode, const void* spec, void* out, const Geom& g,
+                               const FftPlan& fx, const Tables& tb, const XinvExtra& ex, int* nblocks_out,
+                               cudaStream_t st, bool* used) {
+  *used = false;
+  if (!xpass_static_supported(fx.n)) return cudaSuccess;
+  const float2* sp = (const float2*)spec;
+  if (mode == XINV_P0) return xinv_s<float, XINV_P0>(sp, (float*)out, g, fx.n, tb, ex, nblocks_out, st, used);
+  if (mode == XINV_UPDATE) return xinv_s<float, XINV_UPDATE>(sp, (float*)out, g, fx.n, tb, ex, nblocks_out, st, used);
+  if (to_is_double) return xinv_s<double, XINV_PLAIN>(sp, (double*)out, g, fx.n, tb, ex, nblocks_out, st, used);
+  return xinv_s<float, XINV_PLAIN>(sp, (float*)out, g, fx.n, tb, ex, nblocks_out, st, used);
+}
+
+}  // namespace pgb

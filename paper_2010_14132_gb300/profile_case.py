@@ -5,7 +5,10 @@
 The grid uses the stretched/anelastic setup (dx = dy = 50 m, dz_k = 10*1.03^k m,
 rho0 = 1.2 exp(-z/8000)) with a seeded N(0,1) source.  With --adjoint the
 adjoint (and rho0 gradient) is run after each solve.  Prints the mean time per
-call measured with CUDA events.
+call measured with CUDA events.  The measured calls sit inside a CUDA profiler
+range, so ``ncu --profile-from-start off`` captures them and not the set-up.
+Kernel shapes default to the library's defaults; --tuned takes the autotuner's
+choice for this size, and the explicit flags override either.
 """
 from __future__ import annotations
 
@@ -26,13 +29,26 @@ def main(argv=None) -> int:
     ap.add_argument("--dtype", default="mixed", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--tuned", action="store_true")
+    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel"):
+        ap.add_argument("--" + name.replace("_", "-"), dest=name, type=int, default=None)
     args = ap.parse_args(argv)
     d = wl.anelastic_noise(args.nx, args.ny, args.nz, seed=3)
-    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype=args.dtype)
+    opts = {}
+    if args.tuned:
+        from .autotune import tuned_options
+        opts = tuned_options(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, args.dtype)
+    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel"):
+        if getattr(args, name) is not None:
+            opts[name] = getattr(args, name)
+    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype=args.dtype, **opts)
     S = torch.from_numpy(d.S).cuda().to(plan.field_dtype)
     p = torch.empty_like(S)
     w = torch.randn_like(S) if args.adjoint else None
+    plan.solve(S, out=p)   # warm-up: kernel loading, workspace
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
     e0.record()
     for _ in range(args.reps):
         plan.solve(S, out=p)
@@ -40,7 +56,9 @@ def main(argv=None) -> int:
             plan.adjoint(w, p=p, want_grho=True)
     e1.record()
     torch.cuda.synchronize()
-    print(f"{args.nx}x{args.ny}x{args.nz} {args.dtype}: {e0.elapsed_time(e1) / max(1, args.reps):.3f} ms per call")
+    torch.cuda.profiler.stop()
+    print(f"{args.nx}x{args.ny}x{args.nz} {args.dtype} {opts}: "
+          f"{e0.elapsed_time(e1) / max(1, args.reps):.3f} ms per call")
     return 0
 
 

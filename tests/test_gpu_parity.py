@@ -75,7 +75,8 @@ def test_gradient_workload_forward_512x512x64(dtype):
 
 @pytest.mark.parametrize("nx,ny,nz", [(4, 4, 2), (4, 6, 3), (6, 4, 5), (12, 48, 7), (96, 384, 9), (384, 96, 4),
                                       (48, 12, 33), (8, 16, 130), (18, 27, 6), (36, 8, 3), (64, 64, 512),
-                                      (2048, 8, 4), (8, 4096, 2)])
+                                      (2048, 8, 4), (8, 4096, 2), (128, 8, 3), (256, 12, 5), (512, 6, 7),
+                                      (1024, 12, 3), (4096, 4, 3)])
 @pytest.mark.parametrize("dtype", ["fp64", "fp32"])
 @pytest.mark.parametrize("y_kernel", [0, 1])
 def test_sizes(nx, ny, nz, dtype, y_kernel):
@@ -103,8 +104,9 @@ def test_sizes_mixed(nx, ny, nz):
 @pytest.mark.parametrize("opts", [dict(x_elems=16), dict(y_elems=8), dict(x_elems=8, y_elems=8, y_tile=4),
                                   dict(y_kernel=1, y_tile=16, y_elems=8), dict(y_tile=2), dict(y_tile=16),
                                   dict(level_chunk=1), dict(level_chunk=5), dict(level_chunk=7, y_kernel=1),
-                                  dict(level_chunk=4096)])
-@pytest.mark.parametrize("dtype", ["fp64", "mixed"])
+                                  dict(level_chunk=4096), dict(x_kernel=1), dict(x_kernel=1, x_elems=16),
+                                  dict(x_kernel=1, level_chunk=3)])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
 def test_kernel_shape_options(opts, dtype):
     """Every autotuner candidate gives the same answer (tile shapes are not numerics)."""
     d = wl.anelastic_noise(256, 128, 24, seed=17)
