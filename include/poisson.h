@@ -72,7 +72,9 @@ typedef enum {
   POISSON_OPT_PROFILE = 4,       /* 1: record CUDA events around every kernel launch of this plan on
                                     the launching stream (read with poisson_plan_profile_read) */
   POISSON_OPT_Y_KERNEL = 5,      /* y-pass kernel: 0 = persistent TMA-staged kernel where the shape
-                                    allows (default), 1 = plain shared-memory tile kernel */
+                                    allows, with the compile-time FFT for FP32 and power-of-two ny in
+                                    [64, 2048] (default); 1 = plain shared-memory tile kernel;
+                                    2 = persistent TMA-staged kernel with the run-time FFT */
   POISSON_OPT_X_ELEMS = 6,       /* x-pass elements per thread for power-of-two lines: 8 (default) or 16 */
   POISSON_OPT_Y_ELEMS = 7,       /* y-pass elements per thread for power-of-two lines: 8 or 16 (default) */
   POISSON_OPT_LEVEL_CHUNK = 8,   /* levels per transform chunk (x-pass and y-pass of a chunk run back to

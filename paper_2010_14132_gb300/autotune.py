@@ -27,7 +27,7 @@ from .solver import Plan
 CACHE = os.environ.get("POISSON_AUTOTUNE_CACHE",
                        os.path.join(os.path.expanduser("~"), ".cache", "poisson_gb300_autotune.json"))
 
-Y_CANDIDATES = [dict(y_kernel=k, y_tile=t, y_elems=e) for k in (0, 1) for t in (2, 4, 8, 16) for e in (8, 16)]
+Y_CANDIDATES = [dict(y_kernel=k, y_tile=t, y_elems=e) for k in (0, 1, 2) for t in (2, 4, 8, 16) for e in (8, 16)]
 X_CANDIDATES = [dict(x_kernel=0, x_elems=8)] + [dict(x_kernel=1, x_elems=e) for e in (8, 16)]
 CHUNK_CANDIDATES = [dict(level_chunk=c) for c in (0, 1, 2, 4, 8, 16, 4096)]
 OPT_IDS = {"y_kernel": N.POISSON_OPT_Y_KERNEL, "y_tile": N.POISSON_OPT_Y_TILE, "y_elems": N.POISSON_OPT_Y_ELEMS,

@@ -420,7 +420,7 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       pl->lchunk = (int)value;
       return POISSON_OK;
     case POISSON_OPT_Y_KERNEL:
-      if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
+      if (!(value == 0 || value == 1 || value == 2)) return POISSON_ERR_INVALID_ARG;
       pl->ykernel = (int)value;
       return POISSON_OK;
     case POISSON_OPT_X_KERNEL:
@@ -479,7 +479,12 @@ static int check_ws(const poisson_plan* pl, void* ws) {
 static cudaError_t ypass(poisson_plan* pl, const Geom& g, int sign, void* spec, const int* done, Stats* stats,
                          cudaStream_t st) {
   const bool t_double = pl->fp64();
-  if (pl->ykernel == 0) {
+  if (pl->ykernel == 0 && !t_double) {
+    bool used = false;
+    cudaError_t e = launch_yfft_static(sign, spec, g, pl->fy, pl->tb, pl->ytile, done, &stats->err, st, &used);
+    if (e != cudaSuccess || used) return e;
+  }
+  if (pl->ykernel == 0 || pl->ykernel == 2) {
     bool used = false;
     cudaError_t e = launch_yfft_tma(t_double, sign, spec, g, pl->fy, pl->tb, pl->ytile, done, stats, st, &used);
     if (e != cudaSuccess || used) return e;
@@ -510,7 +515,9 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
     gc.lev1 = l0 + lc < pl->nz ? l0 + lc : pl->nz;
     int ps = prof_begin(pl, POISSON_PHASE_XFWD, st);
     if (R) {
-      e = launch_xfwd_residual(*R, spec, gc, pl->fx, pl->tb, done, st);
+      bool used = false;
+      if (pl->xkernel == 0) e = launch_xres_static(*R, spec, gc, pl->fx, pl->tb, done, &stats->err, st, &used);
+      if (e == cudaSuccess && !used) e = launch_xfwd_residual(*R, spec, gc, pl->fx, pl->tb, done, st);
     } else {
       bool used = false;
       if (!t_double && pl->xkernel == 0)

@@ -128,9 +128,16 @@ cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math
 bool xpass_static_supported(int n_half);
 cudaError_t launch_xfwd_static(int ti_is_double, const void* in, void* spec, const Geom& g, const FftPlan& fx,
                                const Tables& tb, const int* done, unsigned* err, cudaStream_t st, bool* used);
+cudaError_t launch_xres_static(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx, const Tables& tb,
+                               const int* done, unsigned* err, cudaStream_t st, bool* used);
 cudaError_t launch_xinv_static(int to_is_double, int mode, const void* spec, void* out, const Geom& g,
                                const FftPlan& fx, const Tables& tb, const XinvExtra& ex, int* nblocks_out,
                                cudaStream_t st, bool* used);
+
+// Persistent FP32 y-pass with the compile-time FFT for power-of-two ny in [64, 2048].
+bool ypass_static_supported(int ny);
+cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPlan& fy, const Tables& tb, int tile,
+                               const int* done, unsigned* err, cudaStream_t st, bool* used);
 
 // Upper bound on the CTAs (and so partial-sum slots) of the x-pass launches of one field.
 int xpass_blocks(const Geom& g, const FftPlan& fx, size_t csize);

@@ -27,6 +27,52 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   return FF{s, e + a.l + b.l};
 }
 
+// Residual at one point from its 7-point stencil values of p0 and q (the q
+// values enter in plain FP32), the double source S, the vertical coefficient
+// splits A = a_k, Cc = c_k, the horizontal ones cx, cy and mu = mu_W.
+// At the bottom (top) level pass pd = pc (pu = pc): a (c) is zero there anyway.
+__device__ __forceinline__ float residual_value(float pc, float pe, float pw, float pn, float ps, float pd, float pu,
+                                                float qc, float qe, float qw, float qn, float qs, float qd, float qu,
+                                                double S, float2 A, float2 Cc, float2 cx, float2 cy, float2 mu) {
+  // x: cx (pe + pw - 2 pc)
+  float s1, e1, s2, e2;
+  two_sum(pe, pw, s1, e1);
+  two_sum(s1, -2.f * pc, s2, e2);
+  float dl = e1 + e2 + (qe + qw - 2.f * qc);
+  FF tx;
+  two_prod(cx.x, s2, tx.h, tx.l);
+  tx.l = __fmaf_rn(cx.x, dl, __fmaf_rn(cx.y, s2, tx.l));
+  // y: cy (pn + ps - 2 pc)
+  two_sum(pn, ps, s1, e1);
+  two_sum(s1, -2.f * pc, s2, e2);
+  dl = e1 + e2 + (qn + qs - 2.f * qc);
+  FF ty;
+  two_prod(cy.x, s2, ty.h, ty.l);
+  ty.l = __fmaf_rn(cy.x, dl, __fmaf_rn(cy.y, s2, ty.l));
+  // z: a (pd - pc) + c (pu - pc)   (a = 0 at the bottom, c = 0 at the top).
+  // Differences first: a constant field maps to exactly zero whatever the
+  // rounding of the coefficient splits.  Summing a pd + c pu - (a+c) pc instead
+  // leaves a row-sum mismatch of ~2^-48 (a+c) that the near-null vertical mode of
+  // the lowest-|k| columns amplifies by their condition number.
+  float dd, ed, du, eu, p1, l1, p2, l2;
+  two_sum(pd, -pc, dd, ed);
+  two_sum(pu, -pc, du, eu);
+  two_prod(A.x, dd, p1, l1);
+  two_prod(Cc.x, du, p2, l2);
+  l1 = __fmaf_rn(A.x, ed + (qd - qc), __fmaf_rn(A.y, dd, l1));
+  l2 = __fmaf_rn(Cc.x, eu + (qu - qc), __fmaf_rn(Cc.y, du, l2));
+  two_sum(p1, p2, s2, e2);
+  FF tz{s2, (l1 + l2) + e2};
+  FF Lp = ff_add(ff_add(tx, ty), tz);
+  float sh, sl, th, tl;
+  d2ff_int(S, sh, sl);
+  two_sum(sh, -mu.x, th, tl);
+  tl += sl - mu.y;
+  float rh, rl;
+  two_sum(th, -Lp.h, rh, rl);
+  return rh + (rl + (tl - Lp.l));
+}
+
 template <bool HAS_Q>
 __device__ __forceinline__ float residual_point(const ResidualArgs& R, const Geom& g, int i, int j, int k) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -53,45 +99,9 @@ __device__ __forceinline__ float residual_point(const ResidualArgs& R, const Geo
     qd = has_dn ? q[idx - pl] : qc;
     qu = has_up ? q[idx + pl] : qc;
   }
-  // x: cx (pe + pw - 2 pc)
-  float s1, e1, s2, e2;
-  two_sum(pe, pw, s1, e1);
-  two_sum(s1, -2.f * pc, s2, e2);
-  float dl = e1 + e2 + (qe + qw - 2.f * qc);
-  FF tx;
-  two_prod(R.cx.x, s2, tx.h, tx.l);
-  tx.l = __fmaf_rn(R.cx.x, dl, __fmaf_rn(R.cx.y, s2, tx.l));
-  // y: cy (pn + ps - 2 pc)
-  two_sum(pn, ps, s1, e1);
-  two_sum(s1, -2.f * pc, s2, e2);
-  dl = e1 + e2 + (qn + qs - 2.f * qc);
-  FF ty;
-  two_prod(R.cy.x, s2, ty.h, ty.l);
-  ty.l = __fmaf_rn(R.cy.x, dl, __fmaf_rn(R.cy.y, s2, ty.l));
-  // z: a (pd - pc) + c (pu - pc)   (a = 0 at the bottom, c = 0 at the top).
-  // Differences first: a constant field maps to exactly zero whatever the
-  // rounding of the coefficient splits.  Summing a pd + c pu - (a+c) pc instead
-  // leaves a row-sum mismatch of ~2^-48 (a+c) that the near-null vertical mode of
-  // the lowest-|k| columns amplifies by their condition number.
-  const float2 A = R.a_ff[k], Cc = R.c_ff[k];
-  float dd, ed, du, eu, p1, l1, p2, l2;
-  two_sum(pd, -pc, dd, ed);
-  two_sum(pu, -pc, du, eu);
-  two_prod(A.x, dd, p1, l1);
-  two_prod(Cc.x, du, p2, l2);
-  l1 = __fmaf_rn(A.x, ed + (qd - qc), __fmaf_rn(A.y, dd, l1));
-  l2 = __fmaf_rn(Cc.x, eu + (qu - qc), __fmaf_rn(Cc.y, du, l2));
-  two_sum(p1, p2, s2, e2);
-  FF tz{s2, (l1 + l2) + e2};
-  FF Lp = ff_add(ff_add(tx, ty), tz);
-  float sh, sl, th, tl;
-  d2ff_int(__ldcs(&R.S[idx]), sh, sl);   // S is read once per sweep: stream past L2
-  const float2 mu = *R.mu_ff;
-  two_sum(sh, -mu.x, th, tl);
-  tl += sl - mu.y;
-  float rh, rl;
-  two_sum(th, -Lp.h, rh, rl);
-  return rh + (rl + (tl - Lp.l));
+  // S is read once per sweep: stream past L2
+  return residual_value(pc, pe, pw, pn, ps, pd, pu, qc, qe, qw, qn, qs, qd, qu, __ldcs(&R.S[idx]), R.a_ff[k],
+                        R.c_ff[k], R.cx, R.cy, *R.mu_ff);
 }
 
 }  // namespace pgb

@@ -24,6 +24,7 @@
 #include "async_copy.cuh"
 #include "fft_static.cuh"
 #include "kernels.cuh"
+#include "residual.cuh"
 
 namespace pgb {
 
@@ -65,6 +66,37 @@ __device__ __forceinline__ void ring_drain(Ring& rg, uint64_t* bar, int ns) {
   // let every copy still in flight land before the CTA's shared memory is released
   for (int s = 0; s < ns; ++s)
     for (int c = rg.consumed[s]; c < rg.issued[s]; ++c) mbar_wait_bounded(&bar[s], (unsigned)(c & 1), kWaitPolls);
+}
+
+// R2C unpacking of a transformed line (natural order in fin) and store of the
+// bins 0..N to dst: each thread takes the bin pairs (k, N - k), k = lane + nl q.
+template <int N, int E>
+__device__ __forceinline__ void r2c_unpack_store(const float2* fin, const float2* twr_s, float2* dst, int lane,
+                                                 bool valid) {
+  using C = float2;
+  constexpr int nl = N / E;
+  const Swizzled sw{};
+#pragma unroll
+  for (int q = 0; q < E / 2; ++q) {
+    const int k = lane + nl * q;   // k < N/2
+    const C A = fin[sw(k)];
+    const C B = cconj(fin[sw(k == 0 ? 0 : N - k)]);
+    const C ev = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
+    const C dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y - B.y));
+    const C wo = cmul(twr_s[k], make_float2(dd.y, -dd.x));   // w^k * (-i dd)
+    if (valid) {
+      dst[k] = cadd(ev, wo);
+      dst[N - k] = cconj(csub(ev, wo));
+    }
+  }
+  if (lane == 0) {   // the self-paired bin k = N/2
+    const C A = fin[sw(N / 2)];
+    const C B = cconj(A);
+    const C ev = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
+    const C dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y - B.y));
+    const C wo = cmul(twr_s[N / 2], make_float2(dd.y, -dd.x));
+    if (valid) dst[N / 2] = cadd(ev, wo);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -145,28 +177,134 @@ __global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in
       v[i] = make_float2(to_f<TI>(x.x), to_f<TI>(x.y));
     }
     const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
-    C* dst = spec + (valid ? row : 0) * g.P;
-#pragma unroll
-    for (int q = 0; q < E / 2; ++q) {
-      const int k = lane + nl * q;   // k < N/2
-      const C A = fin[sw(k)];
-      const C B = cconj(fin[sw(k == 0 ? 0 : N - k)]);
-      const C ev = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
-      const C dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y - B.y));
-      const C wo = cmul(twr_s[k], make_float2(dd.y, -dd.x));   // w^k * (-i dd)
-      if (valid) {
-        dst[k] = cadd(ev, wo);
-        dst[N - k] = cconj(csub(ev, wo));
+    r2c_unpack_store<N, E>(fin, twr_s, spec + (valid ? row : 0) * g.P, lane, valid);
+  }
+  if (tid == 0) {
+    if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
+    ring_drain(rg, bar, ns);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forward x-pass of a refinement sweep: the rows transformed are the residual
+// r = S - mu_W - L (p0 + q), formed as the group is read.  The group's rows of S,
+// p0 (and q) are staged; the x-neighbours come from the staged rows, the y- and
+// z-neighbour rows are read through L1/L2 (the neighbouring groups stage them).
+// ---------------------------------------------------------------------------
+template <int N, int E, bool HAS_Q, bool STAGE_P>
+__global__ void __launch_bounds__(kXsThreads) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
+                                                      const float2* __restrict__ twx, const float2* __restrict__ twr,
+                                                      int ns, unsigned stage_bytes, const int* __restrict__ done,
+                                                      unsigned* __restrict__ err) {
+  using C = float2;
+  constexpr int nl = N / E, RB = kXsThreads / nl, LS = swizzled_stride(N), NX = 2 * N;
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const XsLayout L = xs_layout(N, RB, ns, stage_bytes);
+  C* tw_s = reinterpret_cast<C*>(smraw);
+  C* twr_s = tw_s + N;
+  C* lines = twr_s + N + 2;
+  unsigned char* stg = smraw + L.off_stage;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + L.off_bar);
+
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * nl + lane;
+  const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
+  const long long ngroups = (row_end - row_begin + RB - 1) / RB;
+  constexpr unsigned s_bytes = RB * NX * 8, p_bytes = STAGE_P ? RB * NX * 4 : 0;
+  for (int t = tid; t < N; t += kXsThreads) tw_s[t] = twx[t];
+  for (int t = tid; t <= N / 2; t += kXsThreads) twr_s[t] = twr[t];
+  Ring rg{};
+  if (tid == 0) {
+    for (int s = 0; s < ns; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](long long grp, int s) {
+    const long long r0 = row_begin + grp * RB;
+    const unsigned nv = (unsigned)(row_end - r0 < RB ? row_end - r0 : RB);
+    unsigned char* d = stg + (size_t)s * stage_bytes;
+    mbar_arrive_expect_tx(&bar[s], nv * NX * (8u + (STAGE_P ? 4u + (HAS_Q ? 4u : 0u) : 0u)));
+    bulk_g2s(d, R.S + r0 * NX, nv * NX * 8u, &bar[s]);
+    if constexpr (STAGE_P) {
+      bulk_g2s(d + s_bytes, R.p0 + r0 * NX, nv * NX * 4u, &bar[s]);
+      if constexpr (HAS_Q) bulk_g2s(d + s_bytes + p_bytes, R.q + r0 * NX, nv * NX * 4u, &bar[s]);
+    }
+    rg.issued[s]++;
+  };
+  if (tid == 0)
+    for (int s = 0; s < ns; ++s) {
+      const long long grp = blockIdx.x + (long long)s * gridDim.x;
+      if (grp < ngroups) issue(grp, s);
+    }
+  const LineSync sync{1 + ty, nl};
+  const Swizzled sw{};
+  C* la = lines + (size_t)ty * 2 * LS;
+  C* lb = la + LS;
+  const float2 cx = R.cx, cy = R.cy;
+  bool ok = true;
+  int it = 0;
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+    const int s = it % ns;
+    const long long row = row_begin + grp * RB + ty;
+    const bool valid = row < row_end;
+    const long long rc = valid ? row : row_begin;   // neighbour addressing stays inside the field
+    const int k = (int)(rc / g.ny), j = (int)(rc - (long long)k * g.ny);
+    const long long rn = rc - j + (j + 1 == g.ny ? 0 : j + 1), rs = rc - j + (j == 0 ? g.ny - 1 : j - 1);
+    const bool has_dn = k > 0, has_up = k + 1 < g.nz;
+    const float2* p0n = reinterpret_cast<const float2*>(R.p0 + rn * NX);
+    const float2* p0s = reinterpret_cast<const float2*>(R.p0 + rs * NX);
+    const float2* p0d = reinterpret_cast<const float2*>(R.p0 + (has_dn ? rc - g.ny : rc) * NX);
+    const float2* p0u = reinterpret_cast<const float2*>(R.p0 + (has_up ? rc + g.ny : rc) * NX);
+    const float2 A = R.a_ff[k], Cc = R.c_ff[k], mu = *R.mu_ff;
+    const bool got = mbar_wait_bounded(&bar[s], (unsigned)((it / ns) & 1), kWaitPolls);
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      rg.consumed[s]++;
+      if (it > 0) {
+        const long long gn = grp - gridDim.x + (long long)ns * gridDim.x;
+        if (gn < ngroups) {
+          fence_proxy_async_smem();
+          issue(gn, (it - 1) % ns);
+        }
       }
     }
-    if (lane == 0) {   // the self-paired bin k = N/2
-      const C A = fin[sw(N / 2)];
-      const C B = cconj(A);
-      const C ev = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
-      const C dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y - B.y));
-      const C wo = cmul(twr_s[N / 2], make_float2(dd.y, -dd.x));
-      if (valid) dst[N / 2] = cadd(ev, wo);
+    const unsigned char* d = stg + (size_t)s * stage_bytes;
+    const double2* Srow = reinterpret_cast<const double2*>(d) + (size_t)ty * N;
+    // centre rows of p0 and q: staged, or read through L1 next to the other neighbours
+    const float* prow = STAGE_P ? reinterpret_cast<const float*>(d + s_bytes) + (size_t)ty * NX : R.p0 + rc * NX;
+    const float* qrow = STAGE_P ? reinterpret_cast<const float*>(d + s_bytes + p_bytes) + (size_t)ty * NX
+                                : (HAS_Q ? R.q + rc * NX : nullptr);
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int e = st_in_index<N, E, 0>(lane, i);
+      const float2 pc = reinterpret_cast<const float2*>(prow)[e];
+      const float pw = prow[e == 0 ? NX - 1 : 2 * e - 1];
+      const float pe = prow[e == N - 1 ? 0 : 2 * e + 2];
+      const float2 pn = p0n[e], ps = p0s[e];
+      const float2 pd = has_dn ? p0d[e] : pc, pu = has_up ? p0u[e] : pc;
+      float2 qc = make_float2(0.f, 0.f), qn = qc, qs = qc, qd = qc, qu = qc;
+      float qw = 0.f, qe = 0.f;
+      if constexpr (HAS_Q) {
+        qc = reinterpret_cast<const float2*>(qrow)[e];
+        qw = qrow[e == 0 ? NX - 1 : 2 * e - 1];
+        qe = qrow[e == N - 1 ? 0 : 2 * e + 2];
+        qn = reinterpret_cast<const float2*>(R.q + rn * NX)[e];
+        qs = reinterpret_cast<const float2*>(R.q + rs * NX)[e];
+        qd = has_dn ? reinterpret_cast<const float2*>(R.q + (rc - g.ny) * NX)[e] : qc;
+        qu = has_up ? reinterpret_cast<const float2*>(R.q + (rc + g.ny) * NX)[e] : qc;
+      }
+      const double2 S = Srow[e];
+      v[i].x = residual_value(pc.x, pc.y, pw, pn.x, ps.x, pd.x, pu.x, qc.x, qc.y, qw, qn.x, qs.x, qd.x, qu.x, S.x, A,
+                              Cc, cx, cy, mu);
+      v[i].y = residual_value(pc.y, pe, pc.x, pn.y, ps.y, pd.y, pu.y, qc.y, qe, qc.x, qn.y, qs.y, qd.y, qu.y, S.y, A,
+                              Cc, cx, cy, mu);
     }
+    const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
+    r2c_unpack_store<N, E>(fin, twr_s, spec + (valid ? row : 0) * g.P, lane, valid);
   }
   if (tid == 0) {
     if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
@@ -437,6 +575,49 @@ cudaError_t xfwd_s(const TI* in, float2* spec, const Geom& g, int N, const Table
   return cudaGetLastError();
 }
 
+template <bool HAS_Q>
+cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, const Tables& tb, const int* done,
+                   unsigned* err, cudaStream_t st, bool* used) {
+  const int RB = kXsThreads / (N / kXsE);
+  // stage S, p0 (and q) rows if two CTAs per SM still fit, else S rows only
+  const unsigned row_bytes_all = (unsigned)(g.nx * (8 + 4 + (HAS_Q ? 4 : 0)));
+  const unsigned row_bytes_s = (unsigned)(g.nx * 8);
+  const XsConfig c_all = xs_config(N, RB * row_bytes_all, 0);
+  const bool stage_p = c_all.ns > 0 && c_all.smem <= 110 * 1024;
+  const XsConfig c = stage_p ? c_all : xs_config(N, RB * row_bytes_s, 0);
+  if (c.ns == 0 || !aligned16(R.S) || !aligned16(R.p0) || (HAS_Q && !aligned16(R.q)) || (g.nx * 4) % 16) return cudaSuccess;
+  const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
+  cudaError_t e = cudaSuccess;
+  if (stage_p) {
+    PGB_XS_N_SWITCH(N, {
+      auto kern = k_xres_s<NN, kXsE, HAS_Q, true>;
+      int cap = 0;
+      e = prepare(kern, c.smem, cap);
+      if (e != cudaSuccess) return e;
+      if (cap <= 0) return cudaSuccess;
+      const long long grid = ngroups < cap ? ngroups : cap;
+      if (grid <= 0) return cudaSuccess;
+      kern<<<(unsigned)grid, dim3(NN / kXsE, RB), c.smem, st>>>(R, spec, g, tb.twx_f, tb.twr_f, c.ns, c.stage_bytes,
+                                                                done, err);
+      *used = true;
+    });
+    return cudaGetLastError();
+  }
+  PGB_XS_N_SWITCH(N, {
+    auto kern = k_xres_s<NN, kXsE, HAS_Q, false>;
+    int cap = 0;
+    e = prepare(kern, c.smem, cap);
+    if (e != cudaSuccess) return e;
+    if (cap <= 0) return cudaSuccess;
+    const long long grid = ngroups < cap ? ngroups : cap;
+    if (grid <= 0) return cudaSuccess;
+    kern<<<(unsigned)grid, dim3(NN / kXsE, RB), c.smem, st>>>(R, spec, g, tb.twx_f, tb.twr_f, c.ns, c.stage_bytes,
+                                                              done, err);
+    *used = true;
+  });
+  return cudaGetLastError();
+}
+
 template <typename TO, int MODE>
 cudaError_t xinv_s(const float2* spec, TO* out, const Geom& g, int N, const Tables& tb, const XinvExtra& ex,
                    int* nblocks_out, cudaStream_t st, bool* used) {
@@ -478,6 +659,14 @@ cudaError_t launch_xfwd_static(int ti_is_double, const void* in, void* spec, con
   if (!xpass_static_supported(fx.n)) return cudaSuccess;
   if (ti_is_double) return xfwd_s<double>((const double*)in, (float2*)spec, g, fx.n, tb, done, err, st, used);
   return xfwd_s<float>((const float*)in, (float2*)spec, g, fx.n, tb, done, err, st, used);
+}
+
+cudaError_t launch_xres_static(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx, const Tables& tb,
+                               const int* done, unsigned* err, cudaStream_t st, bool* used) {
+  *used = false;
+  if (!xpass_static_supported(fx.n)) return cudaSuccess;
+  if (R.q) return xres_s<true>(R, (float2*)spec, g, fx.n, tb, done, err, st, used);
+  return xres_s<false>(R, (float2*)spec, g, fx.n, tb, done, err, st, used);
 }
 
 cudaError_t launch_xinv_static(int to_is_double, int mode, const void* spec, void* out, const Geom& g,

@@ -1,0 +1,202 @@
+// Persistent FP32 y-pass for power-of-two ny in [64, 2048] (Section 2.1: the
+// transform along y of every kx column of every level).
+//
+// A tile is one level and TK consecutive kx columns: ny rows of TK complex
+// values, brought into shared memory by 2-D TMA boxes (columns past nx/2 read
+// as zeros).  A CTA walks tiles with a ring of two tile buffers, so the next
+// tile loads while the current one is transformed.  The transform is the
+// compile-time Stockham engine (fft_static.cuh) on the TK interleaved columns:
+// its first stage reads the TMA tile, the stages alternate between a scratch
+// tile and the (by then consumed) input tile in a swizzled layout, and the last
+// stage's outputs go from registers straight to global memory (each warp writes
+// row segments of TK contiguous values).
+#include <mutex>
+#include <unordered_map>
+
+#include "async_copy.cuh"
+#include "fft_static.cuh"
+#include "kernels.cuh"
+
+namespace pgb {
+
+namespace {
+
+// Column-interleaved tile addressing with the complex index swizzled inside
+// blocks of 16 (spreads the stride-R first-stage writes over the banks).
+struct SwStrided {
+  int es;
+  __device__ __forceinline__ int operator()(int idx) const { return (idx ^ ((idx >> 4) & 15)) * es; }
+};
+struct Plain {
+  int es;
+  __device__ __forceinline__ int operator()(int idx) const { return idx * es; }
+};
+
+size_t ys_tile_bytes(int N, int TK) { return ((size_t)N * TK * sizeof(float2) + 127) / 128 * 128; }
+size_t ys_smem(int N, int TK) { return 3 * ys_tile_bytes(N, TK) + (size_t)N * sizeof(float2) + 64; }
+
+constexpr int ys_max_threads(int E) { return E >= 16 ? 512 : 1024; }
+
+template <int N, int E, int SIGN>
+__global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant__ CUtensorMap tm, Geom g,
+                                            const float2* __restrict__ twy, float2* __restrict__ spec, int box_rows,
+                                            int tiles_per_level, int ntiles, const int* __restrict__ done,
+                                            unsigned* __restrict__ err) {
+  using C = float2;
+  constexpr int nl = N / E;
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int TK = blockDim.x, l = threadIdx.x, lane = threadIdx.y;
+  const int tid = lane * TK + l, nthreads = TK * nl;
+  const size_t tb = ((size_t)N * TK * sizeof(C) + 127) / 128 * 128;
+  C* ring[2] = {reinterpret_cast<C*>(smraw), reinterpret_cast<C*>(smraw + tb)};
+  C* scratch = reinterpret_cast<C*>(smraw + 2 * tb);
+  C* tw_s = reinterpret_cast<C*>(smraw + 3 * tb);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + 3 * tb + (size_t)N * sizeof(C));
+  const unsigned tile_bytes = (unsigned)((size_t)N * TK * sizeof(C));
+  for (int t = tid; t < N; t += nthreads) tw_s[t] = twy[t];
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int issued[2] = {0, 0}, consumed[2] = {0, 0};
+  auto issue = [&](int t, int b) {
+    const int level = t / tiles_per_level, kx0 = (t - level * tiles_per_level) * TK;
+    mbar_arrive_expect_tx(&bar[b], tile_bytes);
+    for (int r0 = 0; r0 < N; r0 += box_rows) tma_load_2d(ring[b] + (size_t)r0 * TK, &tm, kx0, level * N + r0, &bar[b]);
+    issued[b]++;
+  };
+  const int t0 = g.lev0 * tiles_per_level + blockIdx.x;
+  if (tid == 0) {
+    if (t0 < ntiles) issue(t0, 0);
+    if (t0 + (int)gridDim.x < ntiles) issue(t0 + gridDim.x, 1);
+  }
+  const SwStrided sw{TK};
+  bool ok = true;
+  int it = 0;
+  for (int t = t0; t < ntiles; t += gridDim.x, ++it) {
+    const int b = it & 1;
+    const bool got = mbar_wait_bounded(&bar[b], (unsigned)((it >> 1) & 1), kWaitPolls);
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      consumed[b]++;
+      // every thread is past the previous tile: its buffer takes the tile after this one
+      const int tn = t + gridDim.x;
+      if (it > 0 && tn < ntiles) {
+        fence_proxy_async_smem();
+        issue(tn, b ^ 1);
+      }
+    }
+    C* in = ring[b];
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = in[Plain{TK}(st_in_index<N, E, 0>(lane, i)) + l];
+    st_fft<N, E, SIGN, true, float>(v, scratch + l, in + l, sw, lane, tw_s, SyncBlock());
+    const int level = t / tiles_per_level, kx = (t - level * tiles_per_level) * TK + l;
+    if (kx < g.nxh) {
+      C* col = spec + (long long)level * g.plane + kx;
+#pragma unroll
+      for (int i = 0; i < E; ++i) col[(long long)st_out_index<N, E>(lane, i) * g.P] = v[i];
+    }
+  }
+  if (tid == 0) {
+    if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
+    for (int b = 0; b < 2; ++b)
+      for (int c = consumed[b]; c < issued[b]; ++c) mbar_wait_bounded(&bar[b], (unsigned)(c & 1), kWaitPolls);
+  }
+}
+
+int largest_divisor_upto(int n, int cap) {
+  for (int d = cap; d >= 1; --d)
+    if (n % d == 0) return d;
+  return 1;
+}
+
+#define PGB_YS_N_SWITCH(N, ...)                                 \
+  switch (N) {                                                  \
+    case 64: { constexpr int NN = 64; __VA_ARGS__; } break;     \
+    case 128: { constexpr int NN = 128; __VA_ARGS__; } break;   \
+    case 256: { constexpr int NN = 256; __VA_ARGS__; } break;   \
+    case 512: { constexpr int NN = 512; __VA_ARGS__; } break;   \
+    case 1024: { constexpr int NN = 1024; __VA_ARGS__; } break; \
+    case 2048: { constexpr int NN = 2048; __VA_ARGS__; } break; \
+    default: return cudaSuccess;                                \
+  }
+
+template <int E, int SIGN>
+cudaError_t ys_launch(float2* spec, const Geom& g, int N, const float2* twy, int tk, const int* done, unsigned* err,
+                      cudaStream_t st, bool* used) {
+  const size_t smem = ys_smem(N, tk);
+  const int nthreads = tk * (N / E);
+  if (smem > 220 * 1024 || nthreads > ys_max_threads(E) || nthreads < 32) return cudaSuccess;
+  const int box_rows = largest_divisor_upto(N, 256);
+  if (((size_t)box_rows * tk * sizeof(float2)) % 128 != 0 && box_rows != N) return cudaSuccess;
+  CUtensorMap tm;
+  if (!encode_tensor_2d(&tm, spec, 8, (unsigned long long)g.nxh, (unsigned long long)g.ny * g.nz,
+                        (unsigned long long)g.P * sizeof(float2), (unsigned)tk, (unsigned)box_rows))
+    return cudaSuccess;
+  const int tiles_per_level = (g.nxh + tk - 1) / tk;
+  const int ntiles = tiles_per_level * g.lev1;
+  const int chunk_tiles = tiles_per_level * (g.lev1 - g.lev0);
+  static std::mutex mu;
+  static std::unordered_map<const void*, std::pair<size_t, int>> granted;   // per kernel: smem, CTAs per SM
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaSuccess;
+  PGB_YS_N_SWITCH(N, {
+    auto kern = k_ys<NN, E, SIGN>;
+    int per_sm = 0;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      auto& ent = granted[reinterpret_cast<const void*>(kern)];
+      if (ent.first != smem || ent.second == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthreads, smem);
+        if (e != cudaSuccess) return e;
+        ent = {smem, per_sm};
+      }
+      per_sm = ent.second;
+    }
+    if (per_sm < 1) return cudaSuccess;
+    const int grid = chunk_tiles < sms * per_sm ? chunk_tiles : sms * per_sm;
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, dim3(tk, N / E), smem, st>>>(tm, g, twy, spec, box_rows, tiles_per_level, ntiles, done, err);
+    *used = true;
+  });
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool ypass_static_supported(int ny) {
+  switch (ny) {
+    case 64: case 128: case 256: case 512: case 1024: case 2048: return true;
+    default: return false;
+  }
+}
+
+cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPlan& fy, const Tables& tb, int tile,
+                               const int* done, unsigned* err, cudaStream_t st, bool* used) {
+  *used = false;
+  if (!ypass_static_supported(fy.n)) return cudaSuccess;
+  int tk = tile > 0 ? tile : 4;
+  if (tk % 2) tk += 1;   // 16-byte inner TMA box
+  const int E = fy.E == 16 ? 16 : 8;
+  while (tk > 2 && (ys_smem(fy.n, tk) > 220 * 1024 || tk * (fy.n / E) > ys_max_threads(E))) tk >>= 1;
+  float2* sp = (float2*)spec;
+  if (E == 16) {
+    if (sign < 0) return ys_launch<16, -1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
+    return ys_launch<16, +1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
+  }
+  if (sign < 0) return ys_launch<8, -1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
+  return ys_launch<8, +1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
+}
+
+}  // namespace pgb
