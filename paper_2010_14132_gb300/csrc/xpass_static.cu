@@ -42,14 +42,17 @@ template <> __device__ __forceinline__ float to_f<float>(float x) { return x; }
 template <> __device__ __forceinline__ float to_f<double>(double x) { return d2f_int(x); }
 
 // Shared layout: twiddles (n/2), unpack twiddles (n/2 + 2), RB rows x 2 line
-// buffers, then the staging ring (128-byte aligned) and its mbarriers.
+// buffers (none when the lines alias the staged rows), then the staging ring
+// (128-byte aligned) and its mbarriers.  A staged row of nx doubles holds
+// exactly the two n/2-point line buffers of its own row, so kernels that stage
+// double rows run the transform inside the consumed row.
 struct XsLayout {
   size_t off_stage, off_bar, total;
 };
 __host__ __device__ constexpr size_t xs_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
-__host__ __device__ inline XsLayout xs_layout(int N, int RB, int ns, unsigned stage_bytes) {
+__host__ __device__ inline XsLayout xs_layout(int N, int RB, int ns, unsigned stage_bytes, bool alias) {
   XsLayout L{};
-  size_t off = (size_t)N * 8 + (size_t)(N + 2) * 8 + (size_t)RB * 2 * swizzled_stride(N) * 8;
+  size_t off = (size_t)N * 8 + (size_t)(N + 2) * 8 + (alias ? 0 : (size_t)RB * 2 * swizzled_stride(N) * 8);
   L.off_stage = xs_align(off, 128);
   L.off_bar = xs_align(L.off_stage + (size_t)ns * stage_bytes, 8);
   L.total = L.off_bar + (size_t)ns * 8;
@@ -110,9 +113,10 @@ __global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in
   using C = float2;
   using TI2 = typename V2s<TI>::t;
   constexpr int nl = N / E, RB = kXsThreads / nl, LS = swizzled_stride(N);
+  constexpr bool ALIAS = sizeof(TI) == 8;
   if (done && *done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
-  const XsLayout L = xs_layout(N, RB, ns, stage_bytes);
+  const XsLayout L = xs_layout(N, RB, ns, stage_bytes, ALIAS);
   C* tw_s = reinterpret_cast<C*>(smraw);
   C* twr_s = tw_s + N;
   C* lines = twr_s + N + 2;
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * nl + lane;
   const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
   const long long ngroups = (row_end - row_begin + RB - 1) / RB;
-  const unsigned row_bytes = (unsigned)(2 * N * sizeof(TI));
+  constexpr unsigned row_bytes = (unsigned)(2 * N * sizeof(TI));
   for (int t = tid; t < N; t += kXsThreads) tw_s[t] = twx[t];
   for (int t = tid; t <= N / 2; t += kXsThreads) twr_s[t] = twr[t];
   Ring rg{};
@@ -152,6 +156,10 @@ __global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in
   int it = 0;
   for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
     const int s = it % ns;
+    if constexpr (ALIAS) {   // this row's two line buffers are its staged row
+      la = reinterpret_cast<C*>(stg + (size_t)s * stage_bytes + (size_t)ty * row_bytes);
+      lb = la + LS;
+    }
     const bool got = mbar_wait_bounded(&bar[s], (unsigned)((it / ns) & 1), kWaitPolls);
     if (!__syncthreads_and(got)) {
       ok = false;
@@ -176,8 +184,11 @@ __global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in
       const TI2 x = srow[st_in_index<N, E, 0>(lane, i)];
       v[i] = make_float2(to_f<TI>(x.x), to_f<TI>(x.y));
     }
+    if constexpr (ALIAS) sync();   // the line's threads have read the row before it is overwritten
     const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
     r2c_unpack_store<N, E>(fin, twr_s, spec + (valid ? row : 0) * g.P, lane, valid);
+    // the staged row was written through the generic proxy; order that before its refill by TMA
+    if constexpr (ALIAS) fence_proxy_async_smem();
   }
   if (tid == 0) {
     if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
@@ -192,7 +203,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in
 // z-neighbour rows are read through L1/L2 (the neighbouring groups stage them).
 // ---------------------------------------------------------------------------
 template <int N, int E, bool HAS_Q, bool STAGE_P>
-__global__ void __launch_bounds__(kXsThreads) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
+__global__ void __launch_bounds__(kXsThreads, 3) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
                                                       int ns, unsigned stage_bytes, const int* __restrict__ done,
                                                       unsigned* __restrict__ err) {
@@ -200,7 +211,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xres_s(ResidualArgs R, float2* _
   constexpr int nl = N / E, RB = kXsThreads / nl, LS = swizzled_stride(N), NX = 2 * N;
   if (done && *done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
-  const XsLayout L = xs_layout(N, RB, ns, stage_bytes);
+  const XsLayout L = xs_layout(N, RB, ns, stage_bytes, true);
   C* tw_s = reinterpret_cast<C*>(smraw);
   C* twr_s = tw_s + N;
   C* lines = twr_s + N + 2;
@@ -238,8 +249,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xres_s(ResidualArgs R, float2* _
     }
   const LineSync sync{1 + ty, nl};
   const Swizzled sw{};
-  C* la = lines + (size_t)ty * 2 * LS;
-  C* lb = la + LS;
+  (void)lines;
   const float2 cx = R.cx, cy = R.cy;
   bool ok = true;
   int it = 0;
@@ -271,8 +281,11 @@ __global__ void __launch_bounds__(kXsThreads) k_xres_s(ResidualArgs R, float2* _
         }
       }
     }
-    const unsigned char* d = stg + (size_t)s * stage_bytes;
+    unsigned char* d = stg + (size_t)s * stage_bytes;
     const double2* Srow = reinterpret_cast<const double2*>(d) + (size_t)ty * N;
+    // the row's two line buffers are its staged S row (used once the residual is formed)
+    C* la = reinterpret_cast<C*>(d + (size_t)ty * NX * 8);
+    C* lb = la + LS;
     // centre rows of p0 and q: staged, or read through L1 next to the other neighbours
     const float* prow = STAGE_P ? reinterpret_cast<const float*>(d + s_bytes) + (size_t)ty * NX : R.p0 + rc * NX;
     const float* qrow = STAGE_P ? reinterpret_cast<const float*>(d + s_bytes + p_bytes) + (size_t)ty * NX
@@ -303,8 +316,10 @@ __global__ void __launch_bounds__(kXsThreads) k_xres_s(ResidualArgs R, float2* _
       v[i].y = residual_value(pc.y, pe, pc.x, pn.y, ps.y, pd.y, pu.y, qc.y, qe, qc.x, qn.y, qs.y, qd.y, qu.y, S.y, A,
                               Cc, cx, cy, mu);
     }
+    sync();   // the line's threads have read the S row before it is overwritten
     const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
     r2c_unpack_store<N, E>(fin, twr_s, spec + (valid ? row : 0) * g.P, lane, valid);
+    fence_proxy_async_smem();   // generic writes to the staged row come before its refill by TMA
   }
   if (tid == 0) {
     if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
@@ -325,7 +340,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xinv_s(const float2* __restrict_
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ float red[2][kXsThreads];
   __shared__ double redd[kXsThreads];
-  const XsLayout L = xs_layout(N, RB, ns, stage_bytes);
+  const XsLayout L = xs_layout(N, RB, ns, stage_bytes, false);
   C* tw_s = reinterpret_cast<C*>(smraw);
   C* twr_s = tw_s + N;
   C* lines = twr_s + N + 2;
@@ -499,25 +514,24 @@ struct XsConfig {
   size_t smem = 0;
 };
 
-// Staging depth: two CTAs per SM when two stages fit in half the shared memory,
-// else one CTA per SM with up to four stages.
-XsConfig xs_config(int N, unsigned stage_bytes, size_t static_smem) {
+// Staging depth and CTAs per SM: the most CTAs per SM (up to three) whose
+// shared memory still allows two stages, then the deepest ring (up to four
+// stages) at that CTA count.
+XsConfig xs_config(int N, unsigned stage_bytes, size_t static_smem, bool alias) {
   const int RB = kXsThreads / (N / kXsE);
-  const size_t half = 110 * 1024 - static_smem, full = 220 * 1024 - static_smem;
+  constexpr size_t kSmPerSm = 228 * 1024, kReserved = 1024, kMaxPerCta = 227 * 1024;
   XsConfig c{};
   c.stage_bytes = stage_bytes;
-  for (int ns = kXsMaxStages; ns >= 2; --ns)
-    if (xs_layout(N, RB, ns, stage_bytes).total <= half) {
-      c.ns = ns;
-      break;
-    }
-  if (c.ns == 0)
+  for (int ctas = 3; ctas >= 1 && c.ns == 0; --ctas) {
+    size_t budget = kSmPerSm / ctas - kReserved - static_smem;
+    if (budget > kMaxPerCta - static_smem) budget = kMaxPerCta - static_smem;
     for (int ns = kXsMaxStages; ns >= 2; --ns)
-      if (xs_layout(N, RB, ns, stage_bytes).total <= full) {
+      if (xs_layout(N, RB, ns, stage_bytes, alias).total <= budget) {
         c.ns = ns;
         break;
       }
-  if (c.ns) c.smem = xs_layout(N, RB, c.ns, stage_bytes).total;
+  }
+  if (c.ns) c.smem = xs_layout(N, RB, c.ns, stage_bytes, alias).total;
   return c;
 }
 
@@ -556,7 +570,7 @@ cudaError_t xfwd_s(const TI* in, float2* spec, const Geom& g, int N, const Table
                    cudaStream_t st, bool* used) {
   const int RB = kXsThreads / (N / kXsE);
   const unsigned row_bytes = (unsigned)(g.nx * sizeof(TI));
-  const XsConfig c = xs_config(N, RB * row_bytes, 0);
+  const XsConfig c = xs_config(N, RB * row_bytes, 0, sizeof(TI) == 8);
   if (c.ns == 0 || !aligned16(in) || row_bytes % 16) return cudaSuccess;
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
   cudaError_t e = cudaSuccess;
@@ -582,9 +596,9 @@ cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, co
   // stage S, p0 (and q) rows if two CTAs per SM still fit, else S rows only
   const unsigned row_bytes_all = (unsigned)(g.nx * (8 + 4 + (HAS_Q ? 4 : 0)));
   const unsigned row_bytes_s = (unsigned)(g.nx * 8);
-  const XsConfig c_all = xs_config(N, RB * row_bytes_all, 0);
-  const bool stage_p = c_all.ns > 0 && c_all.smem <= 110 * 1024;
-  const XsConfig c = stage_p ? c_all : xs_config(N, RB * row_bytes_s, 0);
+  const XsConfig c_all = xs_config(N, RB * row_bytes_all, 0, true);
+  const bool stage_p = c_all.ns > 0 && c_all.smem <= 75 * 1024;
+  const XsConfig c = stage_p ? c_all : xs_config(N, RB * row_bytes_s, 0, true);
   if (c.ns == 0 || !aligned16(R.S) || !aligned16(R.p0) || (HAS_Q && !aligned16(R.q)) || (g.nx * 4) % 16) return cudaSuccess;
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
   cudaError_t e = cudaSuccess;
@@ -624,7 +638,7 @@ cudaError_t xinv_s(const float2* spec, TO* out, const Geom& g, int N, const Tabl
   const int RB = kXsThreads / (N / kXsE);
   const unsigned row_bytes = (unsigned)xs_align((size_t)(N + 1) * sizeof(float2), 16);
   if ((size_t)g.P * sizeof(float2) < row_bytes || (g.P * sizeof(float2)) % 16 || !aligned16(spec)) return cudaSuccess;
-  const XsConfig c = xs_config(N, RB * row_bytes, 4 * 1024);   // + the reduction arrays
+  const XsConfig c = xs_config(N, RB * row_bytes, 4 * 1024, false);   // + the reduction arrays
   if (c.ns == 0) return cudaSuccess;
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
   cudaError_t e = cudaSuccess;

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant_
 #pragma unroll
       for (int i = 0; i < E; ++i) col[(long long)st_out_index<N, E>(lane, i) * g.P] = v[i];
     }
+    fence_proxy_async_smem();   // generic writes to the ring buffer come before its refill by TMA
   }
   if (tid == 0) {
     if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
