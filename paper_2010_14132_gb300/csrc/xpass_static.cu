@@ -25,6 +25,7 @@
 #include "fft_static.cuh"
 #include "kernels.cuh"
 #include "residual.cuh"
+#include "residual2.cuh"
 
 namespace pgb {
 
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kXsThreads, 3) k_xres_s(ResidualArgs R, float2
   const LineSync sync{1 + ty, nl};
   const Swizzled sw{};
   (void)lines;
-  const float2 cx = R.cx, cy = R.cy;
+  const float2 cx = R.cx, cy = R.cy;   // double-float splits of 1/dx^2, 1/dy^2
   bool ok = true;
   int it = 0;
   for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kXsThreads, 3) k_xres_s(ResidualArgs R, float2
     const float2* p0s = reinterpret_cast<const float2*>(R.p0 + rs * NX);
     const float2* p0d = reinterpret_cast<const float2*>(R.p0 + (has_dn ? rc - g.ny : rc) * NX);
     const float2* p0u = reinterpret_cast<const float2*>(R.p0 + (has_up ? rc + g.ny : rc) * NX);
-    const float2 A = R.a_ff[k], Cc = R.c_ff[k], mu = *R.mu_ff;
+    const ResCoef K = res_coef(cx, cy, R.a_ff[k], R.c_ff[k], *R.mu_ff);
     const bool got = mbar_wait_bounded(&bar[s], (unsigned)((it / ns) & 1), kWaitPolls);
     if (!__syncthreads_and(got)) {
       ok = false;
@@ -311,10 +312,12 @@ __global__ void __launch_bounds__(kXsThreads, 3) k_xres_s(ResidualArgs R, float2
         qu = has_up ? reinterpret_cast<const float2*>(R.q + (rc + g.ny) * NX)[e] : qc;
       }
       const double2 S = Srow[e];
-      v[i].x = residual_value(pc.x, pc.y, pw, pn.x, ps.x, pd.x, pu.x, qc.x, qc.y, qw, qn.x, qs.x, qd.x, qu.x, S.x, A,
-                              Cc, cx, cy, mu);
-      v[i].y = residual_value(pc.y, pe, pc.x, pn.y, ps.y, pd.y, pu.y, qc.y, qe, qc.x, qn.y, qs.y, qd.y, qu.y, S.y, A,
-                              Cc, cx, cy, mu);
+      float2 Sh, Sl;
+      d2ff_trunc(S.x, Sh.x, Sl.x);
+      d2ff_trunc(S.y, Sh.y, Sl.y);
+      // the pair's east neighbours are (pc.y, pe), its west neighbours (pw, pc.x)
+      v[i] = residual_value2<HAS_Q>(pc, make_float2(pc.y, pe), make_float2(pw, pc.x), pn, ps, pd, pu, qc,
+                                    make_float2(qc.y, qe), make_float2(qw, qc.x), qn, qs, qd, qu, Sh, Sl, K);
     }
     sync();   // the line's threads have read the S row before it is overwritten
     const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
