@@ -142,6 +142,27 @@ __device__ __forceinline__ double ff2d_int(float s, float t) {
   return __longlong_as_double((long long)bits);
 }
 
+// Normalised double-float pair (s, t), |t| <= ulp(s)/2 -> a double within
+// 2^-47 |s + t| of s + t, in fewer integer steps than ff2d_int: the double bits
+// of s plus t counted in units of 2^6 double ulps of s (half that unit below a
+// power of two whose magnitude t lowers).  |s| < 2^-81 returns s alone.
+__device__ __forceinline__ double ff2d_fast(float s, float t) {
+  const uint32_t sb = __float_as_uint(s);
+  const uint32_t es = (sb >> 23) & 0xffu;
+  const uint32_t hi = (sb & 0x80000000u) | ((es + 896u) << 20) | ((sb >> 3) & 0xfffffu);
+  const uint32_t lo = sb << 29;
+  unsigned long long bits = ((unsigned long long)hi << 32) | lo;
+  bits = (es == 0u) ? ((unsigned long long)(sb & 0x80000000u) << 32) : bits;   // zero (no denormal floats)
+  // t / (2^6 ulp_d(s)) = t * 2^(173 - e_s), |.| <= 2^22: exact scaling, rounded to an integer
+  const int sc = 300 - (int)es;
+  const float scale = __uint_as_float((uint32_t)(sc > 0 && sc < 255 ? sc : 0) << 23);
+  const int ti = __float_as_int(__fmul_rn(t, scale) + 12582912.0f) - 0x4B400000;
+  const int delta = (sb & 0x80000000u) ? -ti : ti;   // change of the magnitude, in units
+  const int shift = ((sb & 0x7fffffu) == 0u && delta < 0) ? 7 : 6;
+  bits += (unsigned long long)((long long)delta << shift);
+  return __longlong_as_double((long long)bits);
+}
+
 // ---------------------------------------------------------------------------
 // Loads/stores of the solver's element types with conversion to compute type.
 // ---------------------------------------------------------------------------

@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(kXsThreads) k_xinv_s(const float2* __restrict_
   const Swizzled sw{};
   C* la = lines + (size_t)ty * 2 * LS;
   C* lb = la + LS;
-  float acc0 = 0.f, acc1 = 0.f;
-  float sh = 0.f, sl = 0.f;   // double-float running sum of p
+  // per-lane partial sums (even / odd points): delta^2, p^2 and the double-float sum of p
+  float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, sh = acc0, sl = acc0;
   bool ok = true;
   int it = 0;
   for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
@@ -441,26 +441,24 @@ __global__ void __launch_bounds__(kXsThreads) k_xinv_s(const float2* __restrict_
           __stcs(reinterpret_cast<typename V2s<TO>::t*>(out + base) + m, o);
         } else if constexpr (MODE == XINV_P0) {
           __stcs(reinterpret_cast<float2*>(ex.p0 + base) + m, z);
-          acc1 += z.x * z.x + z.y * z.y;
-          float e0, e1;
-          two_sum(sh, z.x, sh, e0);
-          two_sum(sh, z.y, sh, e1);
-          sl += e0 + e1;
+          acc1 = fma2(z, z, acc1);
+          float2 e;
+          two_sum2(sh, z, sh, e);
+          sl = add2(sl, e);
           if (ex.p_out)
             __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(f2d_int(z.x), f2d_int(z.y)));
-        } else {   // XINV_UPDATE
-          const float2 qn = make_float2(z.x + qv[i].x, z.y + qv[i].y);
+        } else {   // XINV_UPDATE: q += delta, p = p0 + q as a double
+          const float2 qn = add2(z, qv[i]);
           __stcs(reinterpret_cast<float2*>(ex.q + base) + m, qn);
-          float s0, t0, s1, t1;
-          two_sum(p0v[i].x, qn.x, s0, t0);
-          two_sum(p0v[i].y, qn.y, s1, t1);
-          __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(ff2d_int(s0, t0), ff2d_int(s1, t1)));
-          acc0 += z.x * z.x + z.y * z.y;
-          acc1 += s0 * s0 + s1 * s1;
-          float e0, e1;
-          two_sum(sh, s0, sh, e0);
-          two_sum(sh, s1, sh, e1);
-          sl += (e0 + e1) + (t0 + t1);
+          float2 sp, tp;
+          two_sum2(p0v[i], qn, sp, tp);
+          __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m,
+                 make_double2(ff2d_fast(sp.x, tp.x), ff2d_fast(sp.y, tp.y)));
+          acc0 = fma2(z, z, acc0);
+          acc1 = fma2(sp, sp, acc1);
+          float2 e;
+          two_sum2(sh, sp, sh, e);
+          sl = add2(sl, add2(e, tp));
         }
       }
     }
@@ -471,9 +469,9 @@ __global__ void __launch_bounds__(kXsThreads) k_xinv_s(const float2* __restrict_
   }
   if constexpr (MODE != XINV_PLAIN) {
     // deterministic CTA partial sums: fixed-order tree over the CTA's threads
-    red[0][tid] = acc0;
-    red[1][tid] = acc1;
-    redd[tid] = f2d_int(sh) + f2d_int(sl);
+    red[0][tid] = acc0.x + acc0.y;
+    red[1][tid] = acc1.x + acc1.y;
+    redd[tid] = (f2d_int(sh.x) + f2d_int(sl.x)) + (f2d_int(sh.y) + f2d_int(sl.y));
     __syncthreads();
     for (int h = kXsThreads / 2; h > 0; h >>= 1) {
       if (tid < h) {
