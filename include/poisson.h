@@ -79,9 +79,11 @@ typedef enum {
   POISSON_OPT_Y_ELEMS = 7,       /* y-pass elements per thread for power-of-two lines: 8 or 16 (default) */
   POISSON_OPT_LEVEL_CHUNK = 8,   /* levels per transform chunk (x-pass and y-pass of a chunk run back to
                                     back so its spectrum stays in L2); 0 = about 32 MB (default) */
-  POISSON_OPT_X_KERNEL = 9       /* x-pass kernel of the FP32 transforms: 0 = persistent kernel with bulk-copy
+  POISSON_OPT_X_KERNEL = 9,      /* x-pass kernel of the FP32 transforms: 0 = persistent kernel with bulk-copy
                                     staging where nx/2 is a power of two in [64, 2048] (default),
                                     1 = one CTA per row group */
+  POISSON_OPT_COL_TILE = 10      /* wavenumber columns per CTA of the column solve: 16, 32, 64 or 128;
+                                    0 = the widest tile of at most 56 KB (default) */
 } poisson_option;
 
 /* Kernel phases reported by poisson_plan_profile_read. */

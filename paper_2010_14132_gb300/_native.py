@@ -28,6 +28,7 @@ POISSON_OPT_X_ELEMS = 6
 POISSON_OPT_Y_ELEMS = 7
 POISSON_OPT_LEVEL_CHUNK = 8
 POISSON_OPT_X_KERNEL = 9
+POISSON_OPT_COL_TILE = 10
 PHASES = ("xfwd", "yfwd", "columns", "yinv", "xinv", "residual", "control")
 
 # every symbol include/poisson.h declares

@@ -30,9 +30,10 @@ CACHE = os.environ.get("POISSON_AUTOTUNE_CACHE",
 Y_CANDIDATES = [dict(y_kernel=k, y_tile=t, y_elems=e) for k in (0, 1, 2) for t in (2, 4, 8, 16) for e in (8, 16)]
 X_CANDIDATES = [dict(x_kernel=0, x_elems=8)] + [dict(x_kernel=1, x_elems=e) for e in (8, 16)]
 CHUNK_CANDIDATES = [dict(level_chunk=c) for c in (0, 1, 2, 4, 8, 16, 4096)]
+COL_CANDIDATES = [dict(col_tile=c) for c in (16, 32, 64)]
 OPT_IDS = {"y_kernel": N.POISSON_OPT_Y_KERNEL, "y_tile": N.POISSON_OPT_Y_TILE, "y_elems": N.POISSON_OPT_Y_ELEMS,
            "x_elems": N.POISSON_OPT_X_ELEMS, "level_chunk": N.POISSON_OPT_LEVEL_CHUNK,
-           "x_kernel": N.POISSON_OPT_X_KERNEL}
+           "x_kernel": N.POISSON_OPT_X_KERNEL, "col_tile": N.POISSON_OPT_COL_TILE}
 
 
 def _key(nx, ny, nz, dtype):
@@ -72,7 +73,7 @@ def _time_phases(plan: Plan, S: torch.Tensor, p: torch.Tensor, reps: int):
 
 
 def autotune(nx, ny, nz, dx, dy, dz, rho0, dtype="mixed", reps=3, verbose=False):
-    """Measure the candidates (y-pass, then x-pass, then level chunk); return (best, table)."""
+    """Measure the candidates (y-pass, x-pass, level chunk, column tile); return (best, table)."""
     plan = Plan(nx, ny, nz, dx, dy, dz, rho0, dtype=dtype)
     rng = np.random.default_rng(0)
     S = torch.from_numpy(rng.standard_normal((nz, ny, nx))).cuda().to(plan.field_dtype)
@@ -123,8 +124,25 @@ def autotune(nx, ny, nz, dx, dy, dz, rho0, dtype="mixed", reps=3, verbose=False)
             print("chunk", cand, f"{tt:.3f} ms")
         if tt < best_ct:
             best_c, best_ct = dict(cand), tt
+    for k, v in best_c.items():
+        plan.set_option(OPT_IDS[k], v)
+    # columns per CTA of the column solve
+    best_t, best_tt = {}, float("inf")
+    for cand in COL_CANDIDATES:
+        try:
+            for k, v in cand.items():
+                plan.set_option(OPT_IDS[k], v)
+        except N.PoissonError:
+            continue
+        t = _time_phases(plan, S, p, reps)
+        tt = t["columns"]
+        table.append(("columns", cand, tt))
+        if verbose:
+            print("columns", cand, f"{tt:.3f} ms")
+        if tt < best_tt:
+            best_t, best_tt = dict(cand), tt
     plan.close()
-    return {**best_y, **best_x, **best_c}, table
+    return {**best_y, **best_x, **best_c, **best_t}, table
 
 
 def tuned_options(nx, ny, nz, dx, dy, dz, rho0, dtype="mixed", retune=False):

@@ -75,7 +75,8 @@ struct poisson_plan {
   int dtype = 0;
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
-  int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0;
+  int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
+      coltile = 0;
   double tol = 1e-11;
   Geom g{};
   Tables tb{};
@@ -423,6 +424,10 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value == 0 || value == 1 || value == 2)) return POISSON_ERR_INVALID_ARG;
       pl->ykernel = (int)value;
       return POISSON_OK;
+    case POISSON_OPT_COL_TILE:
+      if (!(value == 0 || value == 16 || value == 32 || value == 64 || value == 128)) return POISSON_ERR_INVALID_ARG;
+      pl->coltile = (int)value;
+      return POISSON_OK;
     case POISSON_OPT_X_KERNEL:
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->xkernel = (int)value;
@@ -545,6 +550,7 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
   A.stats = stats;
   A.done = done;
   A.target_mean = target_mean;
+  A.col_tile = pl->coltile;
   const int ps = prof_begin(pl, POISSON_PHASE_COLUMNS, st);
   e = launch_thomas(A, pl->g, pl->tb, st);
   prof_end(pl, ps, st);

@@ -109,6 +109,7 @@ struct ThomasArgs {
   Stats* stats;
   const int* done;
   const double* target_mean;  // nullable: the (0,0) column then gives the solution mean -(*target_mean)
+  int col_tile;               // requested columns per CTA (0 = default)
 };
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
 

@@ -313,11 +313,14 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
 // ---------------------------------------------------------------------------
 // launcher
 // ---------------------------------------------------------------------------
-static int thomas_tile(int nz, size_t entry_bytes) {
-  // largest TC in {128, 64, 32, 16} whose tile fits about 100 KB (two CTAs per SM)
-  for (int tc = 128; tc >= 16; tc >>= 1)
-    if ((size_t)tc * nz * entry_bytes + 16 <= 100 * 1024) return tc;
-  for (int tc = 32; tc >= 16; tc >>= 1)
+// Columns per CTA: the requested width if its tile fits, else the largest of
+// {64, 32, 16} whose tile fits about 56 KB (four CTAs per SM: while some load
+// their tile, the others run their recurrences), else the largest that fits.
+static int thomas_tile(int nz, size_t entry_bytes, int request) {
+  if (request >= 16 && request <= 128 && (size_t)request * nz * entry_bytes + 16 <= 200 * 1024) return request;
+  for (int tc = 64; tc >= 16; tc >>= 1)
+    if ((size_t)tc * nz * entry_bytes + 16 <= 56 * 1024) return tc;
+  for (int tc = 64; tc >= 16; tc >>= 1)
     if ((size_t)tc * nz * entry_bytes + 16 <= 200 * 1024) return tc;
   return 0;
 }
@@ -326,7 +329,7 @@ template <typename T, typename TCm, bool ADJ>
 static cudaError_t thomas_launch(const ThomasArgs& A, const Geom& g, const Tables& tb, const T* a, const T* c,
                                  const T* lx, const T* ly, cudaStream_t st) {
   using C = typename CT<T>::t;
-  const int tc = thomas_tile(g.nz, sizeof(C) + sizeof(T));
+  const int tc = thomas_tile(g.nz, sizeof(C) + sizeof(T), A.col_tile);
   if (tc == 0) return cudaErrorInvalidValue;
   size_t smem = (((size_t)g.nz * tc * (sizeof(C) + sizeof(T)) + 15) & ~(size_t)15) + 16;
   const size_t lowk_smem = (6 * (size_t)g.nz + 8) * sizeof(TCm);

@@ -30,7 +30,7 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--tuned", action="store_true")
-    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel"):
+    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel", "col_tile"):
         ap.add_argument("--" + name.replace("_", "-"), dest=name, type=int, default=None)
     args = ap.parse_args(argv)
     d = wl.anelastic_noise(args.nx, args.ny, args.nz, seed=3)
@@ -38,7 +38,7 @@ def main(argv=None) -> int:
     if args.tuned:
         from .autotune import tuned_options
         opts = tuned_options(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, args.dtype)
-    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel"):
+    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel", "col_tile"):
         if getattr(args, name) is not None:
             opts[name] = getattr(args, name)
     plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype=args.dtype, **opts)

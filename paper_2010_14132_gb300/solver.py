@@ -41,7 +41,7 @@ class Plan:
 
     def __init__(self, nx, ny, nz, dx, dy, dz, rho0, dtype="fp64", device=None,
                  lowk_radius2=None, max_sweeps=None, tolerance=None, y_tile=None, y_kernel=None,
-                 x_elems=None, y_elems=None, level_chunk=None, x_kernel=None):
+                 x_elems=None, y_elems=None, level_chunk=None, x_kernel=None, col_tile=None):
         if dtype not in DTYPES:
             raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
@@ -74,6 +74,8 @@ class Plan:
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_LEVEL_CHUNK, level_chunk)
         if x_kernel is not None:
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_X_KERNEL, x_kernel)
+        if col_tile is not None:
+            N.poisson_plan_set_option(self._h, N.POISSON_OPT_COL_TILE, col_tile)
         self._ws = None
 
     # -- lifetime ------------------------------------------------------------
