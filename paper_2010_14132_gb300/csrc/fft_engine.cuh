@@ -69,11 +69,64 @@ template <int SIGN, typename C, typename T> __device__ __forceinline__ void dft8
   v[7] = csub(e3, w3o3);
 }
 
+// multiply by W^m = exp(SIGN 2 pi i m/16) for the inner twiddles of dft16
+template <int SIGN, int M, typename C, typename T> __device__ __forceinline__ C w16(C a) {
+  constexpr int m = M % 16;
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;   // cos, sin (pi/8)
+  const T h = (T)0.70710678118654752440;
+  if constexpr (m == 0) {
+    return a;
+  } else if constexpr (m == 4) {
+    return cmul_si<SIGN>(a);
+  } else if constexpr (m == 8) {
+    return C{-a.x, -a.y};
+  } else if constexpr (m == 2 || m == 6) {
+    // (cos + SIGN i sin)(pi m/8) with cos = +-h, sin = h
+    const T cs = (m == 2) ? h : -h;
+    const T sn = (T)SIGN * h;
+    return C{cs * a.x - sn * a.y, cs * a.y + sn * a.x};
+  } else {
+    // m in {1, 3, 9}: cos/sin of pi m/8 from c1, s1
+    const T cs = (m == 1) ? c1 : (m == 3 ? s1 : -c1);
+    const T sn = (T)SIGN * ((m == 1) ? s1 : (m == 3 ? c1 : -s1));
+    return C{cs * a.x - sn * a.y, cs * a.y + sn * a.x};
+  }
+}
+
+// 16-point DFT as 4 x 4: DFT4 over n1 of x[4 n1 + n2], inner twiddles
+// W^(n2 k1), DFT4 over n2; X[k1 + 4 k2] then sits in slot 4 k1 + k2 and is
+// moved to natural order.
+template <int SIGN, typename C, typename T> __device__ __forceinline__ void dft16(C* v) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<SIGN>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+  // slot 4 k1 + n2 holds Y[n2][k1]
+  v[5] = w16<SIGN, 1, C, T>(v[5]);
+  v[6] = w16<SIGN, 2, C, T>(v[6]);
+  v[7] = w16<SIGN, 3, C, T>(v[7]);
+  v[9] = w16<SIGN, 2, C, T>(v[9]);
+  v[10] = w16<SIGN, 4, C, T>(v[10]);
+  v[11] = w16<SIGN, 6, C, T>(v[11]);
+  v[13] = w16<SIGN, 3, C, T>(v[13]);
+  v[14] = w16<SIGN, 6, C, T>(v[14]);
+  v[15] = w16<SIGN, 9, C, T>(v[15]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  // slot 4 k1 + k2 holds X[k1 + 4 k2]: transpose the 4 x 4 block
+  C t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
 template <int R, int SIGN, typename T> __device__ __forceinline__ void dft_r(typename CT<T>::t* v) {
   if constexpr (R == 2) dft2<SIGN>(v);
   else if constexpr (R == 3) dft3<SIGN, typename CT<T>::t, T>(v);
   else if constexpr (R == 4) dft4<SIGN>(v[0], v[1], v[2], v[3]);
-  else dft8<SIGN, typename CT<T>::t, T>(v);
+  else if constexpr (R == 8) dft8<SIGN, typename CT<T>::t, T>(v);
+  else dft16<SIGN, typename CT<T>::t, T>(v);
 }
 
 // Shared-memory address of element idx of a line.

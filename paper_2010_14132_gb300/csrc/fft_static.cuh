@@ -8,13 +8,16 @@
 // stages; consecutive stages alternate between two shared buffers, so one
 // barrier per stage suffices.  The caller supplies the first stage's inputs in
 // registers (loaded in whatever way suits it) and receives the result either in
-// registers (last stage's layout) or in natural order in a shared buffer.
+// registers (last stage's layout) or in natural order in a shared buffer.  With 16
+// elements per thread the main radix is 16 (one stage fewer than radix 8 for
+// most lengths).
 #pragma once
 #include "fft_engine.cuh"
 
 namespace pgb {
 
-// Radix schedule for n = 2^a 3^b: radix-3 stages, then radix 8, then a final 2 or 4.
+// Radix schedule for n = 2^a 3^b and E elements per thread: radix-3 stages,
+// then radix 16 (when E is a multiple of 16) or radix 8, then a final 2, 4 or 8.
 constexpr int st_count(int n, int p) {
   int c = 0;
   while (n > 1 && n % p == 0) {
@@ -23,36 +26,37 @@ constexpr int st_count(int n, int p) {
   }
   return c;
 }
-constexpr int st_nstages(int n) {
-  return st_count(n, 3) + st_count(n, 2) / 3 + (st_count(n, 2) % 3 ? 1 : 0);
+constexpr int st_big_log(int e) { return e % 16 == 0 ? 4 : 3; }   // log2 of the main power-of-two radix
+constexpr int st_nstages(int n, int e) {
+  return st_count(n, 3) + st_count(n, 2) / st_big_log(e) + (st_count(n, 2) % st_big_log(e) ? 1 : 0);
 }
-constexpr int st_radix(int n, int s) {
-  const int a = st_count(n, 2), b = st_count(n, 3);
+constexpr int st_radix(int n, int s, int e) {
+  const int a = st_count(n, 2), b = st_count(n, 3), L = st_big_log(e);
   if (s < b) return 3;
-  if (s - b < a / 3) return 8;
-  return (a % 3 == 1) ? 2 : 4;
+  if (s - b < a / L) return 1 << L;
+  return 1 << (a % L);
 }
-constexpr int st_span(int n, int s) {
+constexpr int st_span(int n, int s, int e) {
   int ns = 1;
-  for (int i = 0; i < s; ++i) ns *= st_radix(n, i);
+  for (int i = 0; i < s; ++i) ns *= st_radix(n, i, e);
   return ns;
 }
 // E elements per thread must be a multiple of every radix of the schedule.
 constexpr bool st_valid(int n, int e) {
   if (n < 2 || e < 1 || n % e != 0) return false;
-  for (int s = 0; s < st_nstages(n); ++s)
-    if (e % st_radix(n, s) != 0) return false;
-  return st_span(n, st_nstages(n)) == n;
+  for (int s = 0; s < st_nstages(n, e); ++s)
+    if (e % st_radix(n, s, e) != 0) return false;
+  return st_span(n, st_nstages(n, e), e) == n;
 }
 
 // Element index held in slot i = q R + r of a thread before stage s (inputs x[j + r n/R]).
 template <int N, int E, int S> __device__ __forceinline__ int st_in_index(int lane, int i) {
-  constexpr int R = st_radix(N, S), nl = N / E, m = N / R;
+  constexpr int R = st_radix(N, S, E), nl = N / E, m = N / R;
   return lane + nl * (i / R) + (i % R) * m;
 }
 // Element index held in slot i after the last stage, when it stays in registers.
 template <int N, int E> __device__ __forceinline__ int st_out_index(int lane, int i) {
-  constexpr int S = st_nstages(N) - 1, R = st_radix(N, S), nl = N / E, Ns = st_span(N, S);
+  constexpr int S = st_nstages(N, E) - 1, R = st_radix(N, S, E), nl = N / E, Ns = st_span(N, S, E);
   // last stage: j < Ns, so j mod Ns = j and the outputs are y[j + r Ns]
   return lane + nl * (i / R) + (i % R) * Ns;
 }
@@ -108,7 +112,7 @@ template <int N, int E, int SIGN, bool FINAL_IN_REGS, int S, typename T, typenam
 __device__ __forceinline__ typename CT<T>::t* st_run_from(typename CT<T>::t (&v)[E], typename CT<T>::t* cur,
                                                           typename CT<T>::t* nxt, Addr addr, int lane,
                                                           const typename CT<T>::t* __restrict__ tw, Sync sync) {
-  constexpr int NST = st_nstages(N), R = st_radix(N, S), Ns = st_span(N, S);
+  constexpr int NST = st_nstages(N, E), R = st_radix(N, S, E), Ns = st_span(N, S, E);
   st_butterflies<R, E, N, Ns, SIGN, T>(v, lane, tw);
   if constexpr (S == NST - 1 && FINAL_IN_REGS) {
     return nullptr;
@@ -118,7 +122,7 @@ __device__ __forceinline__ typename CT<T>::t* st_run_from(typename CT<T>::t (&v)
     if constexpr (S == NST - 1) {
       return cur;
     } else {
-      st_load<st_radix(N, S + 1), E, N>(v, cur, addr, lane);
+      st_load<st_radix(N, S + 1, E), E, N>(v, cur, addr, lane);
       return st_run_from<N, E, SIGN, FINAL_IN_REGS, S + 1, T>(v, nxt, cur, addr, lane, tw, sync);
     }
   }
@@ -134,6 +138,8 @@ __device__ __forceinline__ typename CT<T>::t* st_fft(typename CT<T>::t (&v)[E], 
                                                      typename CT<T>::t* b, Addr addr, int lane,
                                                      const typename CT<T>::t* __restrict__ tw, Sync sync) {
   static_assert(st_valid(N, E), "unsupported static FFT shape");
+  // lane < N/E: lets the compiler split swizzled addresses into a per-thread base plus constants
+  __builtin_assume(lane >= 0 && lane < N / E);
   return st_run_from<N, E, SIGN, FINAL_IN_REGS, 0, T>(v, a, b, addr, lane, tw, sync);
 }
 

@@ -31,7 +31,9 @@ namespace pgb {
 
 namespace {
 
-constexpr int kXsThreads = 256;
+// CTA size: 256 threads with 8 elements per thread, 128 with 16 (one warp per
+// 512-point line); with 16 elements the FFT runs radix-16 stages.
+__host__ __device__ constexpr int xs_threads(int E) { return E >= 16 ? 128 : 256; }
 constexpr int kXsMaxStages = 4;
 
 template <typename T> struct V2s;
@@ -107,13 +109,13 @@ __device__ __forceinline__ void r2c_unpack_store(const float2* fin, const float2
 // forward x-pass
 // ---------------------------------------------------------------------------
 template <int N, int E, typename TI>
-__global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in, float2* __restrict__ spec, Geom g,
+__global__ void __launch_bounds__(xs_threads(E)) k_xfwd_s(const TI* __restrict__ in, float2* __restrict__ spec, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
-                                                      int ns, unsigned stage_bytes, const int* __restrict__ done,
-                                                      unsigned* __restrict__ err) {
+                                                      const int* __restrict__ done, unsigned* __restrict__ err,
+                                                      int ns, unsigned stage_bytes) {
   using C = float2;
   using TI2 = typename V2s<TI>::t;
-  constexpr int nl = N / E, RB = kXsThreads / nl, LS = swizzled_stride(N);
+  constexpr int nl = N / E, RB = xs_threads(E) / nl, LS = swizzled_stride(N);
   constexpr bool ALIAS = sizeof(TI) == 8;
   if (done && *done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -128,8 +130,8 @@ __global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in
   const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
   const long long ngroups = (row_end - row_begin + RB - 1) / RB;
   constexpr unsigned row_bytes = (unsigned)(2 * N * sizeof(TI));
-  for (int t = tid; t < N; t += kXsThreads) tw_s[t] = twx[t];
-  for (int t = tid; t <= N / 2; t += kXsThreads) twr_s[t] = twr[t];
+  for (int t = tid; t < N; t += xs_threads(E)) tw_s[t] = twx[t];
+  for (int t = tid; t <= N / 2; t += xs_threads(E)) twr_s[t] = twr[t];
   Ring rg{};
   if (tid == 0) {
     for (int s = 0; s < ns; ++s) mbar_init(&bar[s], 1);
@@ -204,12 +206,12 @@ __global__ void __launch_bounds__(kXsThreads) k_xfwd_s(const TI* __restrict__ in
 // z-neighbour rows are read through L1/L2 (the neighbouring groups stage them).
 // ---------------------------------------------------------------------------
 template <int N, int E, bool HAS_Q, bool STAGE_P>
-__global__ void __launch_bounds__(kXsThreads, 3) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
+__global__ void __launch_bounds__(xs_threads(E), E >= 16 ? 4 : 3) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
-                                                      int ns, unsigned stage_bytes, const int* __restrict__ done,
-                                                      unsigned* __restrict__ err) {
+                                                      const int* __restrict__ done, unsigned* __restrict__ err,
+                                                      int ns, unsigned stage_bytes) {
   using C = float2;
-  constexpr int nl = N / E, RB = kXsThreads / nl, LS = swizzled_stride(N), NX = 2 * N;
+  constexpr int nl = N / E, RB = xs_threads(E) / nl, LS = swizzled_stride(N), NX = 2 * N;
   if (done && *done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
   const XsLayout L = xs_layout(N, RB, ns, stage_bytes, true);
@@ -223,8 +225,8 @@ __global__ void __launch_bounds__(kXsThreads, 3) k_xres_s(ResidualArgs R, float2
   const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
   const long long ngroups = (row_end - row_begin + RB - 1) / RB;
   constexpr unsigned s_bytes = RB * NX * 8, p_bytes = STAGE_P ? RB * NX * 4 : 0;
-  for (int t = tid; t < N; t += kXsThreads) tw_s[t] = twx[t];
-  for (int t = tid; t <= N / 2; t += kXsThreads) twr_s[t] = twr[t];
+  for (int t = tid; t < N; t += xs_threads(E)) tw_s[t] = twx[t];
+  for (int t = tid; t <= N / 2; t += xs_threads(E)) twr_s[t] = twr[t];
   Ring rg{};
   if (tid == 0) {
     for (int s = 0; s < ns; ++s) mbar_init(&bar[s], 1);
@@ -334,15 +336,15 @@ __global__ void __launch_bounds__(kXsThreads, 3) k_xres_s(ResidualArgs R, float2
 // inverse x-pass with the solver's epilogues
 // ---------------------------------------------------------------------------
 template <int N, int E, typename TO, int MODE>
-__global__ void __launch_bounds__(kXsThreads) k_xinv_s(const float2* __restrict__ spec, TO* __restrict__ out, Geom g,
+__global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restrict__ spec, TO* __restrict__ out, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
-                                                      int ns, unsigned stage_bytes, XinvExtra ex) {
+                                                      XinvExtra ex, int ns, unsigned stage_bytes) {
   using C = float2;
-  constexpr int nl = N / E, RB = kXsThreads / nl, LS = swizzled_stride(N);
+  constexpr int nl = N / E, RB = xs_threads(E) / nl, LS = swizzled_stride(N);
   if (ex.done && *ex.done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
-  __shared__ float red[2][kXsThreads];
-  __shared__ double redd[kXsThreads];
+  __shared__ float red[2][xs_threads(E)];
+  __shared__ double redd[xs_threads(E)];
   const XsLayout L = xs_layout(N, RB, ns, stage_bytes, false);
   C* tw_s = reinterpret_cast<C*>(smraw);
   C* twr_s = tw_s + N;
@@ -354,8 +356,8 @@ __global__ void __launch_bounds__(kXsThreads) k_xinv_s(const float2* __restrict_
   const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
   const long long ngroups = (row_end - row_begin + RB - 1) / RB;
   const unsigned row_bytes = (unsigned)xs_align((size_t)(N + 1) * sizeof(C), 16);
-  for (int t = tid; t < N; t += kXsThreads) tw_s[t] = twx[t];
-  for (int t = tid; t <= N; t += kXsThreads) twr_s[t] = twr[t];
+  for (int t = tid; t < N; t += xs_threads(E)) tw_s[t] = twx[t];
+  for (int t = tid; t <= N; t += xs_threads(E)) twr_s[t] = twr[t];
   Ring rg{};
   if (tid == 0) {
     for (int s = 0; s < ns; ++s) mbar_init(&bar[s], 1);
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(kXsThreads) k_xinv_s(const float2* __restrict_
     red[1][tid] = acc1.x + acc1.y;
     redd[tid] = (f2d_int(sh.x) + f2d_int(sl.x)) + (f2d_int(sh.y) + f2d_int(sl.y));
     __syncthreads();
-    for (int h = kXsThreads / 2; h > 0; h >>= 1) {
+    for (int h = xs_threads(E) / 2; h > 0; h >>= 1) {
       if (tid < h) {
         red[0][tid] += red[0][tid + h];
         red[1][tid] += red[1][tid + h];
@@ -493,7 +495,6 @@ __global__ void __launch_bounds__(kXsThreads) k_xinv_s(const float2* __restrict_
 // ---------------------------------------------------------------------------
 // launch configuration
 // ---------------------------------------------------------------------------
-constexpr int kXsE = 8;
 
 int sm_count() {
   static std::mutex mu;
@@ -518,8 +519,8 @@ struct XsConfig {
 // Staging depth and CTAs per SM: the most CTAs per SM (up to three) whose
 // shared memory still allows two stages, then the deepest ring (up to four
 // stages) at that CTA count.
-XsConfig xs_config(int N, unsigned stage_bytes, size_t static_smem, bool alias) {
-  const int RB = kXsThreads / (N / kXsE);
+XsConfig xs_config(int N, int E, unsigned stage_bytes, size_t static_smem, bool alias) {
+  const int RB = xs_threads(E) / (N / E);
   constexpr size_t kSmPerSm = 228 * 1024, kReserved = 1024, kMaxPerCta = 227 * 1024;
   XsConfig c{};
   c.stage_bytes = stage_bytes;
@@ -536,7 +537,7 @@ XsConfig xs_config(int N, unsigned stage_bytes, size_t static_smem, bool alias) 
   return c;
 }
 
-template <typename K> cudaError_t prepare(K kernel, size_t smem, int& grid_cap) {
+template <typename K> cudaError_t prepare(K kernel, int threads, size_t smem, int& grid_cap) {
   static std::mutex mu;
   static std::unordered_map<const void*, std::pair<size_t, int>> done;   // smem granted, CTAs per SM
   std::lock_guard<std::mutex> lock(mu);
@@ -545,7 +546,7 @@ template <typename K> cudaError_t prepare(K kernel, size_t smem, int& grid_cap) 
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kXsThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
     if (e != cudaSuccess) return e;
     ent = {smem, per_sm};
   }
@@ -555,6 +556,14 @@ template <typename K> cudaError_t prepare(K kernel, size_t smem, int& grid_cap) 
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+#define PGB_XS_E_SWITCH(E, ...)                                 \
+  if ((E) == 16) {                                              \
+    constexpr int EE = 16;                                      \
+    __VA_ARGS__;                                                \
+  } else {                                                      \
+    constexpr int EE = 8;                                       \
+    __VA_ARGS__;                                                \
+  }
 #define PGB_XS_N_SWITCH(N, ...)                          \
   switch (N) {                                           \
     case 64: { constexpr int NN = 64; __VA_ARGS__; } break;     \
@@ -566,97 +575,79 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 
     default: return cudaSuccess;                         \
   }
 
+// Launch one persistent x-pass kernel: grid = min(groups, resident CTAs).
+template <typename K, typename... Args>
+cudaError_t xs_launch(K kern, int threads_x, int RB, const XsConfig& c, long long ngroups, int* nblocks_out,
+                      cudaStream_t st, bool* used, Args... args) {
+  int cap = 0;
+  cudaError_t e = prepare(kern, threads_x * RB, c.smem, cap);
+  if (e != cudaSuccess) return e;
+  if (cap <= 0) return cudaSuccess;
+  const long long grid = ngroups < cap ? ngroups : cap;
+  if (grid <= 0) return cudaSuccess;
+  if (nblocks_out) *nblocks_out = (int)grid;
+  kern<<<(unsigned)grid, dim3(threads_x, RB), c.smem, st>>>(args..., c.ns, c.stage_bytes);
+  *used = true;
+  return cudaGetLastError();
+}
+
 template <typename TI>
-cudaError_t xfwd_s(const TI* in, float2* spec, const Geom& g, int N, const Tables& tb, const int* done, unsigned* err,
-                   cudaStream_t st, bool* used) {
-  const int RB = kXsThreads / (N / kXsE);
+cudaError_t xfwd_s(const TI* in, float2* spec, const Geom& g, int N, int E, const Tables& tb, const int* done,
+                   unsigned* err, cudaStream_t st, bool* used) {
+  const int RB = xs_threads(E) / (N / E);
   const unsigned row_bytes = (unsigned)(g.nx * sizeof(TI));
-  const XsConfig c = xs_config(N, RB * row_bytes, 0, sizeof(TI) == 8);
+  const XsConfig c = xs_config(N, E, RB * row_bytes, 0, sizeof(TI) == 8);
   if (c.ns == 0 || !aligned16(in) || row_bytes % 16) return cudaSuccess;
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
-  cudaError_t e = cudaSuccess;
-  PGB_XS_N_SWITCH(N, {
-    auto kern = k_xfwd_s<NN, kXsE, TI>;
-    int cap = 0;
-    e = prepare(kern, c.smem, cap);
-    if (e != cudaSuccess) return e;
-    if (cap <= 0) return cudaSuccess;
-    const long long grid = ngroups < cap ? ngroups : cap;
-    if (grid <= 0) return cudaSuccess;
-    kern<<<(unsigned)grid, dim3(NN / kXsE, RB), c.smem, st>>>(in, spec, g, tb.twx_f, tb.twr_f, c.ns, c.stage_bytes,
-                                                              done, err);
-    *used = true;
-  });
-  return cudaGetLastError();
+  PGB_XS_E_SWITCH(E, PGB_XS_N_SWITCH(N, {
+    return xs_launch(k_xfwd_s<NN, EE, TI>, NN / EE, RB, c, ngroups, nullptr, st, used, in, spec, g, tb.twx_f,
+                     tb.twr_f, done, err);
+  }));
+  return cudaSuccess;
 }
 
 template <bool HAS_Q>
-cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, const Tables& tb, const int* done,
-                   unsigned* err, cudaStream_t st, bool* used) {
-  const int RB = kXsThreads / (N / kXsE);
-  // stage S, p0 (and q) rows if two CTAs per SM still fit, else S rows only
+cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, int E, const Tables& tb,
+                   const int* done, unsigned* err, cudaStream_t st, bool* used) {
+  const int RB = xs_threads(E) / (N / E);
+  // stage S, p0 (and q) rows while three CTAs per SM still fit, else S rows only
   const unsigned row_bytes_all = (unsigned)(g.nx * (8 + 4 + (HAS_Q ? 4 : 0)));
   const unsigned row_bytes_s = (unsigned)(g.nx * 8);
-  const XsConfig c_all = xs_config(N, RB * row_bytes_all, 0, true);
-  const bool stage_p = c_all.ns > 0 && c_all.smem <= 75 * 1024;
-  const XsConfig c = stage_p ? c_all : xs_config(N, RB * row_bytes_s, 0, true);
-  if (c.ns == 0 || !aligned16(R.S) || !aligned16(R.p0) || (HAS_Q && !aligned16(R.q)) || (g.nx * 4) % 16) return cudaSuccess;
+  const XsConfig c_all = xs_config(N, E, RB * row_bytes_all, 0, true);
+  const bool stage_p = c_all.ns > 0 && c_all.smem <= 75 * 1024 * (size_t)xs_threads(E) / 256;
+  const XsConfig c = stage_p ? c_all : xs_config(N, E, RB * row_bytes_s, 0, true);
+  if (c.ns == 0 || !aligned16(R.S) || !aligned16(R.p0) || (HAS_Q && !aligned16(R.q)) || (g.nx * 4) % 16)
+    return cudaSuccess;
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
-  cudaError_t e = cudaSuccess;
   if (stage_p) {
-    PGB_XS_N_SWITCH(N, {
-      auto kern = k_xres_s<NN, kXsE, HAS_Q, true>;
-      int cap = 0;
-      e = prepare(kern, c.smem, cap);
-      if (e != cudaSuccess) return e;
-      if (cap <= 0) return cudaSuccess;
-      const long long grid = ngroups < cap ? ngroups : cap;
-      if (grid <= 0) return cudaSuccess;
-      kern<<<(unsigned)grid, dim3(NN / kXsE, RB), c.smem, st>>>(R, spec, g, tb.twx_f, tb.twr_f, c.ns, c.stage_bytes,
-                                                                done, err);
-      *used = true;
-    });
-    return cudaGetLastError();
+    PGB_XS_E_SWITCH(E, PGB_XS_N_SWITCH(N, {
+      return xs_launch(k_xres_s<NN, EE, HAS_Q, true>, NN / EE, RB, c, ngroups, nullptr, st, used, R, spec, g,
+                       tb.twx_f, tb.twr_f, done, err);
+    }));
+  } else {
+    PGB_XS_E_SWITCH(E, PGB_XS_N_SWITCH(N, {
+      return xs_launch(k_xres_s<NN, EE, HAS_Q, false>, NN / EE, RB, c, ngroups, nullptr, st, used, R, spec, g,
+                       tb.twx_f, tb.twr_f, done, err);
+    }));
   }
-  PGB_XS_N_SWITCH(N, {
-    auto kern = k_xres_s<NN, kXsE, HAS_Q, false>;
-    int cap = 0;
-    e = prepare(kern, c.smem, cap);
-    if (e != cudaSuccess) return e;
-    if (cap <= 0) return cudaSuccess;
-    const long long grid = ngroups < cap ? ngroups : cap;
-    if (grid <= 0) return cudaSuccess;
-    kern<<<(unsigned)grid, dim3(NN / kXsE, RB), c.smem, st>>>(R, spec, g, tb.twx_f, tb.twr_f, c.ns, c.stage_bytes,
-                                                              done, err);
-    *used = true;
-  });
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template <typename TO, int MODE>
-cudaError_t xinv_s(const float2* spec, TO* out, const Geom& g, int N, const Tables& tb, const XinvExtra& ex,
+cudaError_t xinv_s(const float2* spec, TO* out, const Geom& g, int N, int E, const Tables& tb, const XinvExtra& ex,
                    int* nblocks_out, cudaStream_t st, bool* used) {
-  const int RB = kXsThreads / (N / kXsE);
+  const int RB = xs_threads(E) / (N / E);
   const unsigned row_bytes = (unsigned)xs_align((size_t)(N + 1) * sizeof(float2), 16);
   if ((size_t)g.P * sizeof(float2) < row_bytes || (g.P * sizeof(float2)) % 16 || !aligned16(spec)) return cudaSuccess;
-  const XsConfig c = xs_config(N, RB * row_bytes, 4 * 1024, false);   // + the reduction arrays
+  // + the reduction arrays (12 bytes per thread)
+  const XsConfig c = xs_config(N, E, RB * row_bytes, 12 * (size_t)xs_threads(E), false);
   if (c.ns == 0) return cudaSuccess;
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
-  cudaError_t e = cudaSuccess;
-  PGB_XS_N_SWITCH(N, {
-    auto kern = k_xinv_s<NN, kXsE, TO, MODE>;
-    int cap = 0;
-    e = prepare(kern, c.smem, cap);
-    if (e != cudaSuccess) return e;
-    if (cap <= 0) return cudaSuccess;
-    const long long grid = ngroups < cap ? ngroups : cap;
-    if (grid <= 0) return cudaSuccess;
-    if (nblocks_out) *nblocks_out = (int)grid;
-    kern<<<(unsigned)grid, dim3(NN / kXsE, RB), c.smem, st>>>(spec, out, g, tb.twx_f, tb.twr_f, c.ns, c.stage_bytes,
-                                                              ex);
-    *used = true;
-  });
-  return cudaGetLastError();
+  PGB_XS_E_SWITCH(E, PGB_XS_N_SWITCH(N, {
+    return xs_launch(k_xinv_s<NN, EE, TO, MODE>, NN / EE, RB, c, ngroups, nblocks_out, st, used, spec, out, g,
+                     tb.twx_f, tb.twr_f, ex);
+  }));
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -672,16 +663,18 @@ cudaError_t launch_xfwd_static(int ti_is_double, const void* in, void* spec, con
                                const Tables& tb, const int* done, unsigned* err, cudaStream_t st, bool* used) {
   *used = false;
   if (!xpass_static_supported(fx.n)) return cudaSuccess;
-  if (ti_is_double) return xfwd_s<double>((const double*)in, (float2*)spec, g, fx.n, tb, done, err, st, used);
-  return xfwd_s<float>((const float*)in, (float2*)spec, g, fx.n, tb, done, err, st, used);
+  const int E = fx.E == 16 ? 16 : 8;
+  if (ti_is_double) return xfwd_s<double>((const double*)in, (float2*)spec, g, fx.n, E, tb, done, err, st, used);
+  return xfwd_s<float>((const float*)in, (float2*)spec, g, fx.n, E, tb, done, err, st, used);
 }
 
 cudaError_t launch_xres_static(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx, const Tables& tb,
                                const int* done, unsigned* err, cudaStream_t st, bool* used) {
   *used = false;
   if (!xpass_static_supported(fx.n)) return cudaSuccess;
-  if (R.q) return xres_s<true>(R, (float2*)spec, g, fx.n, tb, done, err, st, used);
-  return xres_s<false>(R, (float2*)spec, g, fx.n, tb, done, err, st, used);
+  const int E = fx.E == 16 ? 16 : 8;
+  if (R.q) return xres_s<true>(R, (float2*)spec, g, fx.n, E, tb, done, err, st, used);
+  return xres_s<false>(R, (float2*)spec, g, fx.n, E, tb, done, err, st, used);
 }
 
 cudaError_t launch_xinv_static(int to_is_double, int mode, const void* spec, void* out, const Geom& g,
@@ -690,10 +683,12 @@ cudaError_t launch_xinv_static(int to_is_double, int mode, const void* spec, voi
   *used = false;
   if (!xpass_static_supported(fx.n)) return cudaSuccess;
   const float2* sp = (const float2*)spec;
-  if (mode == XINV_P0) return xinv_s<float, XINV_P0>(sp, (float*)out, g, fx.n, tb, ex, nblocks_out, st, used);
-  if (mode == XINV_UPDATE) return xinv_s<float, XINV_UPDATE>(sp, (float*)out, g, fx.n, tb, ex, nblocks_out, st, used);
-  if (to_is_double) return xinv_s<double, XINV_PLAIN>(sp, (double*)out, g, fx.n, tb, ex, nblocks_out, st, used);
-  return xinv_s<float, XINV_PLAIN>(sp, (float*)out, g, fx.n, tb, ex, nblocks_out, st, used);
+  const int E = fx.E == 16 ? 16 : 8;
+  if (mode == XINV_P0) return xinv_s<float, XINV_P0>(sp, (float*)out, g, fx.n, E, tb, ex, nblocks_out, st, used);
+  if (mode == XINV_UPDATE)
+    return xinv_s<float, XINV_UPDATE>(sp, (float*)out, g, fx.n, E, tb, ex, nblocks_out, st, used);
+  if (to_is_double) return xinv_s<double, XINV_PLAIN>(sp, (double*)out, g, fx.n, E, tb, ex, nblocks_out, st, used);
+  return xinv_s<float, XINV_PLAIN>(sp, (float*)out, g, fx.n, E, tb, ex, nblocks_out, st, used);
 }
 
 }  // namespace pgb
