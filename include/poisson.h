@@ -82,8 +82,11 @@ typedef enum {
   POISSON_OPT_X_KERNEL = 9,      /* x-pass kernel of the FP32 transforms: 0 = persistent kernel with bulk-copy
                                     staging where nx/2 is a power of two in [64, 2048] (default),
                                     1 = one CTA per row group */
-  POISSON_OPT_COL_TILE = 10      /* wavenumber columns per CTA of the column solve: 16, 32, 64 or 128;
-                                    0 = the widest tile of at most 56 KB (default) */
+  POISSON_OPT_COL_TILE = 10      /* column-solve kernel: 0 = default (FP32 forward solves: two threads per
+                                    column meeting mid-column, 32 columns per CTA; FP32 adjoint solves: the
+                                    paired-ky kernel); 1, 2, 4 = two threads per column with 16, 32, 64
+                                    columns; 3 = paired-ky kernel; 16, 32, 64, 128 = one thread per column
+                                    with that many columns per CTA */
 } poisson_option;
 
 /* Kernel phases reported by poisson_plan_profile_read. */

@@ -280,7 +280,9 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
     lx[k] = -(4.0 / (dx * dx)) * sn * sn;
   }
   for (int k = 0; k < ny; ++k) {
-    const double sn = std::sin(M_PI * k / ny);
+    // ky and ny - ky share one eigenvalue, bit for bit (the paired column solves use one pivot chain)
+    const int kk = (k <= ny / 2) ? k : ny - k;
+    const double sn = std::sin(M_PI * kk / ny);
     ly[k] = -(4.0 / (dy * dy)) * sn * sn;
   }
 
@@ -425,7 +427,9 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       pl->ykernel = (int)value;
       return POISSON_OK;
     case POISSON_OPT_COL_TILE:
-      if (!(value == 0 || value == 16 || value == 32 || value == 64 || value == 128)) return POISSON_ERR_INVALID_ARG;
+      if (!((value >= 0 && value <= 4 && value == (int)value) || value == 16 || value == 32 || value == 64 ||
+            value == 128))
+        return POISSON_ERR_INVALID_ARG;
       pl->coltile = (int)value;
       return POISSON_OK;
     case POISSON_OPT_X_KERNEL:

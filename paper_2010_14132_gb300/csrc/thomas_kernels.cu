@@ -310,6 +310,253 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Paired FP32 column kernel: ky and ny - ky have the same eigenvalue, so the
+// columns (kx, ky) and (kx, ny - ky) share one pivot chain.  A CTA takes TC
+// consecutive kx of such a pair of rows (a single row for ky = 0 and ky = ny/2),
+// stages both [nz][TC] tiles with one 2-D TMA box each, and every thread runs
+// the shared pivots with two right-hand sides.  Shared layout: tile a, tile b
+// [nz][TC] complex, factors [nz][TC], (a_k, c_k) pairs [nz], one mbarrier.
+// ---------------------------------------------------------------------------
+template <bool ADJ>
+__device__ __forceinline__ void column_solve_pair(float2* ca, float2* cb, float* wp, int TC, int nz, float s, float ms,
+                                                  const float2* __restrict__ ac, float2* __restrict__ oa,
+                                                  float2* __restrict__ ob, long long plane, bool two) {
+  float g_prev = s, inv_prev = 0.f;
+  float2 ya = make_float2(0.f, 0.f), yb = ya;
+  for (int k = 0; k < nz; ++k) {
+    const float2 akc = ac[k];   // (a_k, c_k)
+    const float2 da = ca[(size_t)k * TC];
+    const float2 db = two ? cb[(size_t)k * TC] : make_float2(0.f, 0.f);
+    float gk;
+    if (!ADJ) gk = (k == 0) ? s : s + (akc.x * inv_prev) * g_prev;
+    else gk = (k == 0) ? s : s + akc.x * g_prev * inv_prev;
+    const float u = gk + akc.y;
+    const float inv = rcp(u);
+    if (!ADJ) {
+      const float f = (k == 0) ? 0.f : akc.x * inv_prev;
+      ya = make_float2(fmaf(ms, da.x, f * ya.x), fmaf(ms, da.y, f * ya.y));
+      yb = make_float2(fmaf(ms, db.x, f * yb.x), fmaf(ms, db.y, f * yb.y));
+      ca[(size_t)k * TC] = make_float2(ya.x * inv, ya.y * inv);
+      if (two) cb[(size_t)k * TC] = make_float2(yb.x * inv, yb.y * inv);
+      wp[(size_t)k * TC] = akc.y * inv;
+    } else {
+      const float cm = (k == 0) ? 0.f : ac[k - 1].y;
+      ya = make_float2(fmaf(ms, da.x, cm * ya.x) * inv, fmaf(ms, da.y, cm * ya.y) * inv);
+      yb = make_float2(fmaf(ms, db.x, cm * yb.x) * inv, fmaf(ms, db.y, cm * yb.y) * inv);
+      ca[(size_t)k * TC] = ya;
+      if (two) cb[(size_t)k * TC] = yb;
+      wp[(size_t)k * TC] = (k + 1 < nz) ? ac[k + 1].x * inv : 0.f;
+    }
+    g_prev = gk;
+    inv_prev = inv;
+  }
+  float2 xa = ca[(size_t)(nz - 1) * TC], xb = two ? cb[(size_t)(nz - 1) * TC] : make_float2(0.f, 0.f);
+  oa[(long long)(nz - 1) * plane] = xa;
+  if (two) ob[(long long)(nz - 1) * plane] = xb;
+  for (int k = nz - 2; k >= 0; --k) {
+    const float w = wp[(size_t)k * TC];
+    const float2 za = ca[(size_t)k * TC];
+    xa = make_float2(za.x + w * xa.x, za.y + w * xa.y);
+    oa[(long long)k * plane] = xa;
+    if (two) {
+      const float2 zb = cb[(size_t)k * TC];
+      xb = make_float2(zb.x + w * xb.x, zb.y + w * xb.y);
+      ob[(long long)k * plane] = xb;
+    }
+  }
+}
+
+template <typename TCm, bool ADJ>
+__global__ void __launch_bounds__(64) k_thomas_pair(float2* __restrict__ spec, Geom g, const float* __restrict__ a,
+                                                    const float* __restrict__ c, const float* __restrict__ lamx,
+                                                    const float* __restrict__ lamy, float scale, int lowk_r2,
+                                                    const int* __restrict__ done, Stats* stats,
+                                                    const __grid_constant__ CUtensorMap tm, int box_rows,
+                                                    int kx_chunks, LowkArgs L) {
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  if ((int)blockIdx.x < L.n) {
+    lowk_column<float, TCm, ADJ>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale,
+                                 L.cols[blockIdx.x], stats, L.target_mean);
+    return;
+  }
+  const int TC = blockDim.x, t = threadIdx.x, nz = g.nz;
+  const size_t tile_bytes = (size_t)nz * TC * sizeof(float2);
+  float2* ta = reinterpret_cast<float2*>(smraw);
+  float2* tb = reinterpret_cast<float2*>(smraw + tile_bytes);
+  float* wv = reinterpret_cast<float*>(smraw + 2 * tile_bytes);
+  float2* ac = reinterpret_cast<float2*>(smraw + 2 * tile_bytes + (((size_t)nz * TC * sizeof(float) + 15) & ~(size_t)15));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ac + nz + (nz & 1));
+  const int u = (int)blockIdx.x - L.n;
+  const int pair = u / kx_chunks, chunk = u - pair * kx_chunks;
+  const int ky_a = pair, ky_b = (g.ny - pair) % g.ny;
+  const bool two = ky_b != ky_a;
+  const int kx0 = chunk * TC;
+  for (int k = t; k < nz; k += TC) ac[k] = make_float2(a[k], c[k]);
+  if (t == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (t == 0) {
+    mbar_arrive_expect_tx(bar, (unsigned)tile_bytes * (two ? 2u : 1u));
+    for (int k0 = 0; k0 < nz; k0 += box_rows) {
+      tma_load_2d(ta + (size_t)k0 * TC, &tm, ky_a * g.P + kx0, k0, bar);
+      if (two) tma_load_2d(tb + (size_t)k0 * TC, &tm, ky_b * g.P + kx0, k0, bar);
+    }
+  }
+  if (!mbar_wait_bounded(bar, 0, kWaitPolls)) {
+    if (t == 0) atomicOr(&stats->err, (unsigned)ERR_WAIT_TIMEOUT);
+    mbar_wait_bounded(bar, 0, kWaitPolls);   // let copies in flight land before the CTA exits
+    return;
+  }
+  const int kx = kx0 + t;
+  const int kys = signed_ky(ky_a, g.ny);
+  if (kx >= g.nxh || kx * kx + kys * kys <= lowk_r2) return;
+  const float s = -(lamx[kx] + lamy[ky_a]);
+  column_solve_pair<ADJ>(ta + t, tb + t, wv + t, TC, nz, s, -scale, ac, spec + (long long)ky_a * g.P + kx,
+                         spec + (long long)ky_b * g.P + kx, g.plane, two);
+}
+
+
+// ---------------------------------------------------------------------------
+// Twisted FP32 column kernel (forward solves): two threads per column.  The
+// lower thread eliminates levels 0..m-1 upward with the pivots above
+// (g_k, u_k = g_k + c_k), the upper thread eliminates levels nz-1..m+1 downward
+// with the mirror recurrence h_{nz-1} = s, h_k = s + c_k h_{k+1}/v_{k+1},
+// v_k = h_k + a_k (again subtraction-free); they meet at level m = nz/2:
+//   x_m = (b_m + a_m z_{m-1} + c_m zt_{m+1}) / (s + a_m g_{m-1}/u_{m-1} + c_m h_{m+1}/v_{m+1}),
+// then substitute back outward: x_k = z_k + (c_k/u_k) x_{k+1} below m,
+// x_k = zt_k + (a_k/v_k) x_{k-1} above m.  Half the sequential chain of the
+// one-thread recurrence and twice the threads for the same shared memory.
+// Shared layout: tile [nz][TC] complex, factors [nz][TC], (a_k, c_k) [nz], the
+// meeting terms [TC] x 4, one mbarrier.
+// ---------------------------------------------------------------------------
+template <typename TCm>
+__global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Geom g, const float* __restrict__ a,
+                                                  const float* __restrict__ c, const float* __restrict__ lamx,
+                                                  const float* __restrict__ lamy, float scale, int lowk_r2,
+                                                  const int* __restrict__ done, Stats* stats,
+                                                  const __grid_constant__ CUtensorMap tm, int box_rows, LowkArgs L) {
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  if ((int)blockIdx.x < L.n) {
+    lowk_column<float, TCm, false>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale,
+                                   L.cols[blockIdx.x], stats, L.target_mean);
+    return;
+  }
+  const int TC = blockDim.x / 2, t = threadIdx.x, col_t = t % TC, upper = t / TC, nz = g.nz;
+  float2* tile = reinterpret_cast<float2*>(smraw);
+  float* wv = reinterpret_cast<float*>(tile + (size_t)nz * TC);
+  float2* ac = reinterpret_cast<float2*>(smraw + (((size_t)nz * TC * (sizeof(float2) + sizeof(float)) + 15) & ~(size_t)15));
+  float4* meet = reinterpret_cast<float4*>(ac + nz + (nz & 1));   // [TC]: lower part's (g-term, z-term re, im, -)
+  float2* xm_s = reinterpret_cast<float2*>(meet + TC);             // [TC]: x_m
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xm_s + TC);
+  const long long c0 = (long long)(blockIdx.x - L.n) * TC;
+  for (int k = t; k < nz; k += blockDim.x) ac[k] = make_float2(a[k], c[k]);
+  if (t == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (t == 0) {
+    mbar_arrive_expect_tx(bar, (unsigned)(TC * sizeof(float2)) * (unsigned)nz);
+    for (int k0 = 0; k0 < nz; k0 += box_rows) tma_load_2d(tile + (size_t)k0 * TC, &tm, (int)c0, k0, bar);
+  }
+  const bool got = mbar_wait_bounded(bar, 0, kWaitPolls);
+  if (!__syncthreads_and(got)) {
+    if (t == 0) {
+      atomicOr(&stats->err, (unsigned)ERR_WAIT_TIMEOUT);
+      mbar_wait_bounded(bar, 0, kWaitPolls);   // let copies in flight land before the CTA exits
+    }
+    return;
+  }
+  const long long col = c0 + col_t;
+  const int ky = (int)(col / g.P), kx = (int)(col - (long long)ky * g.P);
+  const int kys = signed_ky(ky, g.ny);
+  const bool valid = col < g.plane && kx < g.nxh && (kx * kx + kys * kys > lowk_r2);
+  const float s = valid ? -(lamx[kx] + lamy[ky]) : 1.f;
+  const float ms = -scale;
+  const int m = nz / 2;
+  float2* colp = tile + col_t;
+  float* wp = wv + col_t;
+  float2* out = spec + (valid ? col : 0);
+  if (upper == 0) {
+    // levels 0..m-1, upward elimination
+    float g_prev = s, inv_prev = 0.f;
+    float2 y = make_float2(0.f, 0.f);
+    for (int k = 0; k < m; ++k) {
+      const float2 akc = ac[k];
+      const float2 d = colp[(size_t)k * TC];
+      const float f = (k == 0) ? 0.f : akc.x * inv_prev;
+      const float gk = (k == 0) ? s : s + f * g_prev;
+      const float inv = rcp(gk + akc.y);
+      y = make_float2(fmaf(ms, d.x, f * y.x), fmaf(ms, d.y, f * y.y));
+      colp[(size_t)k * TC] = make_float2(y.x * inv, y.y * inv);
+      wp[(size_t)k * TC] = akc.y * inv;
+      g_prev = gk;
+      inv_prev = inv;
+    }
+    // the level-m terms of the lower part: a_m g_{m-1}/u_{m-1} and a_m z_{m-1}
+    const float am = ac[m].x;
+    const float2 z = (m > 0) ? colp[(size_t)(m - 1) * TC] : make_float2(0.f, 0.f);
+    meet[col_t] = (m > 0) ? make_float4(am * g_prev * inv_prev, am * z.x, am * z.y, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    // levels nz-1..m+1, downward elimination with the mirror recurrence
+    float h_prev = s, inv_prev = 0.f;
+    float2 y = make_float2(0.f, 0.f);
+    for (int k = nz - 1; k > m; --k) {
+      const float2 akc = ac[k];
+      const float2 d = colp[(size_t)k * TC];
+      const float f = (k == nz - 1) ? 0.f : akc.y * inv_prev;   // c_k / v_{k+1}
+      const float hk = (k == nz - 1) ? s : s + f * h_prev;
+      const float inv = rcp(hk + akc.x);
+      y = make_float2(fmaf(ms, d.x, f * y.x), fmaf(ms, d.y, f * y.y));
+      colp[(size_t)k * TC] = make_float2(y.x * inv, y.y * inv);
+      wp[(size_t)k * TC] = akc.x * inv;
+      h_prev = hk;
+      inv_prev = inv;
+    }
+    xm_s[col_t] = (m + 1 < nz) ? make_float2(h_prev * inv_prev, 0.f) : make_float2(0.f, 0.f);   // h_{m+1}/v_{m+1}
+  }
+  __syncthreads();
+  if (upper == 0) {
+    const float2 akc = ac[m];
+    const float cm = akc.y;
+    const float hterm = cm * xm_s[col_t].x;
+    const float2 zt = (m + 1 < nz) ? colp[(size_t)(m + 1) * TC] : make_float2(0.f, 0.f);
+    const float4 lo = meet[col_t];
+    const float2 dm = colp[(size_t)m * TC];
+    const float den = s + lo.x + hterm;
+    const float2 num = make_float2(fmaf(ms, dm.x, lo.y + cm * zt.x), fmaf(ms, dm.y, lo.z + cm * zt.y));
+    const float2 xm = make_float2(__fdiv_rn(num.x, den), __fdiv_rn(num.y, den));
+    xm_s[col_t] = xm;   // this thread has read the h-term; no other thread touches the slot before the barrier
+  }
+  __syncthreads();
+  const float2 xm = xm_s[col_t];
+  if (!valid) return;
+  if (upper == 0) {
+    out[(long long)m * g.plane] = xm;
+    float2 x = xm;
+    for (int k = m - 1; k >= 0; --k) {
+      const float2 z = colp[(size_t)k * TC];
+      const float w = wp[(size_t)k * TC];
+      x = make_float2(z.x + w * x.x, z.y + w * x.y);
+      out[(long long)k * g.plane] = x;
+    }
+  } else {
+    float2 x = xm;
+    for (int k = m + 1; k < nz; ++k) {
+      const float2 z = colp[(size_t)k * TC];
+      const float w = wp[(size_t)k * TC];
+      x = make_float2(z.x + w * x.x, z.y + w * x.y);
+      out[(long long)k * g.plane] = x;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launcher
 // ---------------------------------------------------------------------------
@@ -325,10 +572,103 @@ static int thomas_tile(int nz, size_t entry_bytes, int request) {
   return 0;
 }
 
+// Paired FP32 column kernel (col_tile = 0, the default); *used = false when it does not fit.
+template <typename TCm, bool ADJ>
+static cudaError_t thomas_pair_launch(const ThomasArgs& A, const Geom& g, const Tables& tb, cudaStream_t st,
+                                      bool* used) {
+  *used = false;
+  int tc = 0;
+  for (int t = 32; t >= 16; t >>= 1) {   // 16 or 32 columns per row, tiles of at most ~64 KB
+    const size_t sm = 2 * (size_t)g.nz * t * sizeof(float2) + (size_t)g.nz * t * sizeof(float);
+    if (sm <= 64 * 1024) {
+      tc = t;
+      break;
+    }
+  }
+  if (tc == 0) {
+    const size_t sm16 = 2 * (size_t)g.nz * 16 * sizeof(float2) + (size_t)g.nz * 16 * sizeof(float);
+    if (sm16 > 200 * 1024) return cudaSuccess;
+    tc = 16;
+  }
+  size_t smem = 2 * (size_t)g.nz * tc * sizeof(float2) + (((size_t)g.nz * tc * sizeof(float) + 15) & ~(size_t)15) +
+                ((size_t)g.nz + 1) * sizeof(float2) + 16;
+  const size_t lowk_smem = (6 * (size_t)g.nz + 8) * sizeof(TCm);
+  if (smem < lowk_smem) smem = lowk_smem;
+  int box_rows = 1;
+  for (int d = 256; d >= 1; --d)
+    if (g.nz % d == 0) {
+      box_rows = d;
+      break;
+    }
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  if (!encode_tensor_2d(&tm, A.spec, 8, (unsigned long long)g.plane, (unsigned long long)g.nz,
+                        (unsigned long long)g.plane * sizeof(float2), (unsigned)tc, (unsigned)box_rows))
+    return cudaSuccess;
+  auto kern = k_thomas_pair<TCm, ADJ>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int kx_chunks = (g.nxh + tc - 1) / tc;
+  const int npairs = g.ny / 2 + 1;
+  const long long nb = (long long)npairs * kx_chunks;
+  const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale};
+  kern<<<(unsigned)(nb + A.n_lowk), tc, smem, st>>>((float2*)A.spec, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f,
+                                                    (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows,
+                                                    kx_chunks, L);
+  *used = true;
+  return cudaGetLastError();
+}
+
+// Twisted FP32 column kernel for forward solves; *used = false when it does not fit.
+template <typename TCm>
+static cudaError_t thomas_tw_launch(const ThomasArgs& A, const Geom& g, const Tables& tb, int tc, cudaStream_t st,
+                                    bool* used) {
+  *used = false;
+  size_t smem = (((size_t)g.nz * tc * (sizeof(float2) + sizeof(float)) + 15) & ~(size_t)15) +
+                ((size_t)g.nz + 1) * sizeof(float2) + (size_t)tc * (sizeof(float4) + sizeof(float2)) + 16;
+  const size_t lowk_smem = (6 * (size_t)g.nz + 8) * sizeof(TCm);
+  if (smem < lowk_smem) smem = lowk_smem;
+  if (smem > 200 * 1024) return cudaSuccess;
+  int box_rows = 1;
+  for (int d = 256; d >= 1; --d)
+    if (g.nz % d == 0) {
+      box_rows = d;
+      break;
+    }
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  if (!encode_tensor_2d(&tm, A.spec, 8, (unsigned long long)g.plane, (unsigned long long)g.nz,
+                        (unsigned long long)g.plane * sizeof(float2), (unsigned)tc, (unsigned)box_rows))
+    return cudaSuccess;
+  auto kern = k_thomas_tw<TCm>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long nb = (g.plane + tc - 1) / tc;
+  const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale};
+  kern<<<(unsigned)(nb + A.n_lowk), 2 * tc, smem, st>>>((float2*)A.spec, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f,
+                                                        (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows, L);
+  *used = true;
+  return cudaGetLastError();
+}
+
 template <typename T, typename TCm, bool ADJ>
 static cudaError_t thomas_launch(const ThomasArgs& A, const Geom& g, const Tables& tb, const T* a, const T* c,
                                  const T* lx, const T* ly, cudaStream_t st) {
   using C = typename CT<T>::t;
+  if constexpr (sizeof(T) == 4) {
+    if (!ADJ && (A.col_tile <= 2 || A.col_tile == 4)) {
+      // twisted two-thread columns: 32 columns per CTA by default (col_tile 0 or 2), 16 (1) or 64 (4)
+      const int tc = A.col_tile == 1 ? 16 : (A.col_tile == 4 ? 64 : 32);
+      bool used = false;
+      cudaError_t e = thomas_tw_launch<TCm>(A, g, tb, tc, st, &used);
+      if (e != cudaSuccess || used) return e;
+    }
+    if (A.col_tile == 0 || A.col_tile == 3) {
+      bool used = false;
+      cudaError_t e = thomas_pair_launch<TCm, ADJ>(A, g, tb, st, &used);
+      if (e != cudaSuccess || used) return e;
+    }
+  }
   const int tc = thomas_tile(g.nz, sizeof(C) + sizeof(T), A.col_tile);
   if (tc == 0) return cudaErrorInvalidValue;
   size_t smem = (((size_t)g.nz * tc * (sizeof(C) + sizeof(T)) + 15) & ~(size_t)15) + 16;

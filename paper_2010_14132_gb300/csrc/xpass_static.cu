@@ -343,8 +343,6 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restri
   constexpr int nl = N / E, RB = xs_threads(E) / nl, LS = swizzled_stride(N);
   if (ex.done && *ex.done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
-  __shared__ float red[2][xs_threads(E)];
-  __shared__ double redd[xs_threads(E)];
   const XsLayout L = xs_layout(N, RB, ns, stage_bytes, false);
   C* tw_s = reinterpret_cast<C*>(smraw);
   C* twr_s = tw_s + N;
@@ -470,7 +468,13 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restri
     ring_drain(rg, bar, ns);
   }
   if constexpr (MODE != XINV_PLAIN) {
-    // deterministic CTA partial sums: fixed-order tree over the CTA's threads
+    // deterministic CTA partial sums: fixed-order tree over the CTA's threads, in the
+    // line buffers (no longer in use: every thread is past its last transform)
+    constexpr int TH = xs_threads(E);
+    static_assert((size_t)TH * 16 <= (size_t)RB * 2 * LS * sizeof(C), "reduction does not fit the line buffers");
+    __syncthreads();
+    double* redd = reinterpret_cast<double*>(lines);
+    float (*red)[TH] = reinterpret_cast<float (*)[TH]>(redd + TH);
     red[0][tid] = acc0.x + acc0.y;
     red[1][tid] = acc1.x + acc1.y;
     redd[tid] = (f2d_int(sh.x) + f2d_int(sl.x)) + (f2d_int(sh.y) + f2d_int(sl.y));
@@ -639,8 +643,7 @@ cudaError_t xinv_s(const float2* spec, TO* out, const Geom& g, int N, int E, con
   const int RB = xs_threads(E) / (N / E);
   const unsigned row_bytes = (unsigned)xs_align((size_t)(N + 1) * sizeof(float2), 16);
   if ((size_t)g.P * sizeof(float2) < row_bytes || (g.P * sizeof(float2)) % 16 || !aligned16(spec)) return cudaSuccess;
-  // + the reduction arrays (12 bytes per thread)
-  const XsConfig c = xs_config(N, E, RB * row_bytes, 12 * (size_t)xs_threads(E), false);
+  const XsConfig c = xs_config(N, E, RB * row_bytes, 0, false);
   if (c.ns == 0) return cudaSuccess;
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
   PGB_XS_E_SWITCH(E, PGB_XS_N_SWITCH(N, {

@@ -107,7 +107,8 @@ def test_sizes_mixed(nx, ny, nz):
                                   dict(level_chunk=4096), dict(x_kernel=1), dict(x_kernel=1, x_elems=16),
                                   dict(x_kernel=1, level_chunk=3), dict(y_kernel=2), dict(y_kernel=2, y_elems=8),
                                   dict(y_elems=8, y_tile=8), dict(y_elems=8, y_tile=2), dict(y_tile=8),
-                                  dict(col_tile=16), dict(col_tile=32), dict(col_tile=64), dict(col_tile=128)])
+                                  dict(col_tile=16), dict(col_tile=32), dict(col_tile=64), dict(col_tile=128),
+                                  dict(col_tile=1), dict(col_tile=3), dict(col_tile=4)])
 @pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
 def test_kernel_shape_options(opts, dtype):
     """Every autotuner candidate gives the same answer (tile shapes are not numerics)."""
