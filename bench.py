@@ -325,27 +325,31 @@ def main():
                 "alg_bytes_per_launch": dom_bytes_launch, "ms_per_launch": dom_ms_launch}
     solve_gbs = alg_total / (ms * 1e-3) / 1e9
 
-    # ---- end to end through the public API with host buffers
-    Sh = torch.from_numpy(d.S).pin_memory()
-    ph = torch.empty_like(Sh).pin_memory()
+    # ---- end to end through the public API with host buffers: the library's pipeline copies each
+    # step's source in from page-locked host memory, solves it and copies the solution back out;
+    # the copies of neighbouring steps overlap the solve of the current one
+    from paper_2010_14132_gb300.solver import Pipe
+    pipe = Pipe(plan)
+    Sh = [torch.from_numpy(d.S).pin_memory() for _ in range(2)]
+    ph = [torch.empty_like(Sh[0]).pin_memory() for _ in range(2)]
     K2 = max(3, min(args.steps, 30))
-    for _ in range(2):
-        S.copy_(Sh, non_blocking=True)
-        plan.solve(S, out=p)
-        ph.copy_(p, non_blocking=True)
+    for i in range(2):
+        pipe.submit(Sh[i], ph[i])
+    pipe.wait()
     torch.cuda.synchronize()
     barrier()
-    e0.record(stream)
-    for _ in range(K2):
-        S.copy_(Sh, non_blocking=True)
-        plan.solve(S, out=p)
-        ph.copy_(p, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    t_e2e = time.perf_counter()
+    for i in range(K2):
+        pipe.submit(Sh[i % 2], ph[i % 2])
+    pipe.wait()
+    t_e2e = time.perf_counter() - t_e2e
     barrier()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / K2)
+    ms_e2e = max_over_ranks(t_e2e * 1e3 / K2)
+    pipe.close()
     e2e = {"value": world * d.npoints / (ms_e2e * 1e-3) / 1e6, "unit": "Mpoints/s",
-           "h2d_bytes_per_step": int(S.numel() * 8), "d2h_bytes_per_step": int(p.numel() * 8)}
+           "h2d_bytes_per_step": int(S.numel() * 8), "d2h_bytes_per_step": int(p.numel() * 8),
+           "ms_per_step": ms_e2e, "steps": K2,
+           "how": "poisson_pipe: H2D of step i+1 and D2H of step i-1 overlap the solve of step i; host wall clock"}
 
     # ---- plain FP64 GPU solve of the same grid (the comparison the metric names)
     fp64 = None

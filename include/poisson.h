@@ -42,6 +42,7 @@ extern "C" {
 
 typedef struct poisson_plan poisson_plan;    /* opaque, owned by the library */
 typedef struct poisson_batch poisson_batch;  /* opaque, owned by the library */
+typedef struct poisson_pipe poisson_pipe;    /* opaque, owned by the library */
 
 typedef enum {
   POISSON_OK = 0,
@@ -198,6 +199,29 @@ int poisson_batch_workspace_bytes(const poisson_batch* batch, size_t* bytes);
 int poisson_batch_solve(poisson_batch* batch, const void* const* S, void* const* p,
                         void* workspace, void* stream, poisson_info* info);
 int poisson_batch_destroy(poisson_batch* batch);
+
+/* ---- Host-buffer pipeline: a stream of solves on one plan, fields in host memory ----
+ * Not a step of the paper's method: the way a time-stepping host feeds the
+ * solver.  poisson_pipe_create allocates two device slots (source and solution
+ * of the plan's field type each), a workspace and three streams (copy in,
+ * compute, copy out), all owned by the pipe.  poisson_pipe_submit enqueues one
+ * step without waiting: copy S_host into a free slot, solve it, copy the
+ * solution to p_host; the copy of step i+1's source and of step i-1's solution
+ * overlap the solve of step i.  S_host and p_host hold nx*ny*nz values of the
+ * plan's field type ([nz][ny][nx], x fastest).  Page-locked host buffers give
+ * asynchronous copies; with pageable ones the copies still happen, without the
+ * overlap.  The caller must not touch S_host until the step's source copy is
+ * done, nor read p_host before poisson_pipe_wait returns.  Steps complete in
+ * submission order.
+ * poisson_pipe_wait blocks until every submitted step is done and returns the
+ * first non-OK status of the steps since the previous wait: an enqueue error,
+ * a device wait time-out, or POISSON_ERR_NOT_CONVERGED from a mixed solve (the
+ * last 1024 steps are checked).  The pipe takes no ownership of the plan;
+ * destroy the pipe first.  One thread per pipe. */
+int poisson_pipe_create(poisson_plan* plan, poisson_pipe** out);
+int poisson_pipe_submit(poisson_pipe* pipe, const void* S_host, void* p_host);
+int poisson_pipe_wait(poisson_pipe* pipe);
+int poisson_pipe_destroy(poisson_pipe* pipe);
 
 #ifdef __cplusplus
 }

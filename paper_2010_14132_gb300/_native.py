@@ -37,6 +37,7 @@ EXPORTED = (
     "poisson_solve", "poisson_solve_adjoint", "poisson_plan_destroy", "poisson_status_string",
     "poisson_last_error_detail", "poisson_batch_create", "poisson_batch_workspace_bytes", "poisson_batch_solve",
     "poisson_batch_destroy", "poisson_plan_profile_read", "poisson_solve_static_workspace",
+    "poisson_pipe_create", "poisson_pipe_submit", "poisson_pipe_wait", "poisson_pipe_destroy",
 )
 
 # size of the fixed device array poisson_solve_static_workspace uses as scratch
@@ -105,6 +106,10 @@ def load():
     L.poisson_batch_destroy.argtypes = [vp]
     L.poisson_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int), i]
     L.poisson_solve_static_workspace.argtypes = [vp, vp, vp, vp, C.POINTER(PoissonInfo)]
+    L.poisson_pipe_create.argtypes = [vp, C.POINTER(vp)]
+    L.poisson_pipe_submit.argtypes = [vp, vp, vp]
+    L.poisson_pipe_wait.argtypes = [vp]
+    L.poisson_pipe_destroy.argtypes = [vp]
     for name in EXPORTED:
         if name not in ("poisson_status_string", "poisson_last_error_detail"):
             getattr(L, name).restype = C.c_int
@@ -225,3 +230,22 @@ def poisson_batch_solve(batch, S_ptrs, p_ptrs, ws_ptr, stream, want_info=False):
 def poisson_batch_destroy(batch):
     if batch:
         load().poisson_batch_destroy(batch)
+
+
+def poisson_pipe_create(plan):
+    out = C.c_void_p()
+    _check(load().poisson_pipe_create(plan, C.byref(out)), "poisson_pipe_create")
+    return out.value
+
+
+def poisson_pipe_submit(pipe, S_host_ptr, p_host_ptr):
+    return _check(load().poisson_pipe_submit(pipe, S_host_ptr, p_host_ptr), "poisson_pipe_submit")
+
+
+def poisson_pipe_wait(pipe):
+    return _check(load().poisson_pipe_wait(pipe), "poisson_pipe_wait")
+
+
+def poisson_pipe_destroy(pipe):
+    if pipe:
+        load().poisson_pipe_destroy(pipe)

@@ -793,3 +793,115 @@ int poisson_batch_solve(poisson_batch* b, const void* const* S, void* const* p, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Host-buffer pipeline: two device slots, three streams (copy in, compute,
+// copy out) ordered by events, so that copies of neighbouring steps overlap
+// the solve of the current one.
+// ---------------------------------------------------------------------------
+struct poisson_pipe {
+  poisson_plan* plan = nullptr;
+  size_t field_bytes = 0;
+  void* ws = nullptr;
+  void* dS[2] = {nullptr, nullptr};
+  void* dp[2] = {nullptr, nullptr};
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  bool slot_used[2] = {false, false};
+  long long submitted = 0, since_wait = 0;
+  int first_status = POISSON_OK;
+  // per-step (done, sweeps, converged, err) copied from the device statistics after each solve
+  static constexpr int kRing = 1024;
+  int4* status_ring = nullptr;   // page-locked, kRing entries
+};
+
+int poisson_pipe_destroy(poisson_pipe* pp) {
+  if (!pp) return POISSON_OK;
+  if (pp->s_in) cudaStreamSynchronize(pp->s_in);
+  if (pp->s_comp) cudaStreamSynchronize(pp->s_comp);
+  if (pp->s_out) cudaStreamSynchronize(pp->s_out);
+  for (int k = 0; k < 2; ++k) {
+    if (pp->ev_in[k]) cudaEventDestroy(pp->ev_in[k]);
+    if (pp->ev_comp[k]) cudaEventDestroy(pp->ev_comp[k]);
+    if (pp->ev_out[k]) cudaEventDestroy(pp->ev_out[k]);
+    if (pp->dS[k]) cudaFree(pp->dS[k]);
+    if (pp->dp[k]) cudaFree(pp->dp[k]);
+  }
+  if (pp->ws) cudaFree(pp->ws);
+  if (pp->status_ring) cudaFreeHost(pp->status_ring);
+  if (pp->s_in) cudaStreamDestroy(pp->s_in);
+  if (pp->s_comp) cudaStreamDestroy(pp->s_comp);
+  if (pp->s_out) cudaStreamDestroy(pp->s_out);
+  delete pp;
+  return POISSON_OK;
+}
+
+int poisson_pipe_create(poisson_plan* pl, poisson_pipe** out) {
+  if (!pl || !out) return POISSON_ERR_INVALID_ARG;
+  *out = nullptr;
+  poisson_pipe* pp = new (std::nothrow) poisson_pipe();
+  if (!pp) return POISSON_ERR_CUDA;
+  pp->plan = pl;
+  pp->field_bytes = (size_t)pl->g.N * pl->elem();
+  cudaError_t e = cudaMalloc(&pp->ws, pl->ws_bytes);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&pp->dS[k], pp->field_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->dp[k], pp->field_bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pp->ev_in[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pp->ev_comp[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pp->ev_out[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaMallocHost(&pp->status_ring, sizeof(int4) * poisson_pipe::kRing);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pp->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pp->s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pp->s_out, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    poisson_pipe_destroy(pp);
+    return cuda_fail(e, "poisson_pipe_create", __LINE__);
+  }
+  *out = pp;
+  return POISSON_OK;
+}
+
+int poisson_pipe_submit(poisson_pipe* pp, const void* S_host, void* p_host) {
+  if (!pp || !S_host || !p_host) return POISSON_ERR_INVALID_ARG;
+  const int k = (int)(pp->submitted & 1);
+  // source slot k is free once the solve that read it two submissions ago is done; solution slot k
+  // once that step's copy-out is done (so a copy-in and the previous copy-out run concurrently)
+  if (pp->slot_used[k]) PGB_CUDA(cudaStreamWaitEvent(pp->s_in, pp->ev_comp[k], 0));
+  PGB_CUDA(cudaMemcpyAsync(pp->dS[k], S_host, pp->field_bytes, cudaMemcpyHostToDevice, pp->s_in));
+  PGB_CUDA(cudaEventRecord(pp->ev_in[k], pp->s_in));
+  PGB_CUDA(cudaStreamWaitEvent(pp->s_comp, pp->ev_in[k], 0));
+  if (pp->slot_used[k]) PGB_CUDA(cudaStreamWaitEvent(pp->s_comp, pp->ev_out[k], 0));
+  const int st = poisson_solve(pp->plan, pp->dS[k], pp->dp[k], pp->ws, pp->s_comp, nullptr);
+  if (st != POISSON_OK && pp->first_status == POISSON_OK) pp->first_status = st;
+  static_assert(offsetof(Stats, err) == offsetof(Stats, done) + 3 * sizeof(int), "status fields not contiguous");
+  PGB_CUDA(cudaMemcpyAsync(&pp->status_ring[pp->since_wait % poisson_pipe::kRing],
+                           (char*)pp->ws + pp->plan->off_stats + offsetof(Stats, done), sizeof(int4),
+                           cudaMemcpyDeviceToHost, pp->s_comp));
+  pp->since_wait++;
+  PGB_CUDA(cudaEventRecord(pp->ev_comp[k], pp->s_comp));
+  PGB_CUDA(cudaStreamWaitEvent(pp->s_out, pp->ev_comp[k], 0));
+  PGB_CUDA(cudaMemcpyAsync(p_host, pp->dp[k], pp->field_bytes, cudaMemcpyDeviceToHost, pp->s_out));
+  PGB_CUDA(cudaEventRecord(pp->ev_out[k], pp->s_out));
+  pp->slot_used[k] = true;
+  pp->submitted++;
+  return st;
+}
+
+int poisson_pipe_wait(poisson_pipe* pp) {
+  if (!pp) return POISSON_ERR_INVALID_ARG;
+  PGB_CUDA(cudaStreamSynchronize(pp->s_in));
+  PGB_CUDA(cudaStreamSynchronize(pp->s_comp));
+  PGB_CUDA(cudaStreamSynchronize(pp->s_out));
+  int st = pp->first_status;
+  const long long n = pp->since_wait < poisson_pipe::kRing ? pp->since_wait : poisson_pipe::kRing;
+  for (long long i = 0; i < n && st == POISSON_OK; ++i) {
+    const int4 r = pp->status_ring[i];   // (done, sweeps, converged, err)
+    if ((unsigned)r.w & ERR_WAIT_TIMEOUT) st = POISSON_ERR_TIMEOUT;
+    else if (pp->plan->mixed() && !r.z) st = POISSON_ERR_NOT_CONVERGED;
+  }
+  pp->first_status = POISSON_OK;
+  pp->since_wait = 0;
+  return st;
+}

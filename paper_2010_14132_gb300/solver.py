@@ -230,3 +230,47 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Pipe:
+    """A stream of solves on one plan with fields in host memory (the library's pipeline).
+
+    submit(S, p) enqueues one step (copy S in, solve, copy the solution to p) and
+    returns at once; copies of neighbouring steps overlap the solve.  S and p are
+    CPU tensors of the plan's field dtype and shape, page-locked for overlap
+    (``tensor.pin_memory()``).  wait() blocks until all submitted steps are done and
+    raises on the first failed step.  Keep S unchanged and do not read p until wait().
+    """
+
+    def __init__(self, plan: Plan):
+        self.plan = plan
+        with torch.cuda.device(plan.device):
+            self._h = N.poisson_pipe_create(plan._h)
+        self._keep = []
+
+    def submit(self, S: torch.Tensor, p: torch.Tensor):
+        for t, name in ((S, "S"), (p, "p")):
+            if t.is_cuda or t.dtype != self.plan.field_dtype or tuple(t.shape) != self.plan.shape \
+                    or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CPU tensor of dtype {self.plan.field_dtype} "
+                                 f"and shape {self.plan.shape}")
+        self._keep.append((S, p))
+        N.poisson_pipe_submit(self._h, S.data_ptr(), p.data_ptr())
+
+    def wait(self):
+        try:
+            N.poisson_pipe_wait(self._h)
+        finally:
+            self._keep.clear()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.poisson_pipe_destroy(self._h)
+            self._h = None
+        self._keep = []
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
