@@ -71,16 +71,35 @@ struct LineSync {
   }
 };
 
+// Twiddles in stage order: the stage of span Ns and radix R keeps exp(-2 pi i r k/(Ns R))
+// at [(Ns - 1) + (r - 1) Ns + k], r = 1..R-1, k = 0..Ns-1 (N - 1 entries in all, as the
+// earlier stages' (R - 1) Ns sum to Ns - 1).  Threads of a line read consecutive k, so the
+// reads are free of bank conflicts, unlike the strided r k (N/(Ns R)) reads of one table.
+template <int N, int E, typename C>
+__device__ __forceinline__ void st_build_twiddles(C* dst, const C* __restrict__ tw_n, int tid, int nthreads) {
+  for (int t = tid; t < N - 1; t += nthreads) {
+    int Ns = 1, R = st_radix(N, 0, E);
+#pragma unroll 1
+    for (int s = 0; s < st_nstages(N, E); ++s) {
+      R = st_radix(N, s, E);
+      if (t < Ns * R - 1) break;
+      Ns *= R;
+    }
+    const int u = t - (Ns - 1), r = u / Ns + 1, k = u - (r - 1) * Ns;
+    dst[t] = tw_n[r * k * (N / (Ns * R))];
+  }
+}
+
 template <int R, int E, int N, int Ns, int SIGN, typename T>
 __device__ __forceinline__ void st_butterflies(typename CT<T>::t (&v)[E], int lane,
                                                const typename CT<T>::t* __restrict__ tw) {
-  constexpr int B = E / R, nl = N / E, stride = N / (Ns * R);
+  constexpr int B = E / R, nl = N / E;
 #pragma unroll
   for (int q = 0; q < B; ++q) {
     if constexpr (Ns > 1) {
       const int k = (lane + nl * q) % Ns;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[q * R + r] = tw_apply<SIGN>(v[q * R + r], tw[r * k * stride]);
+      for (int r = 1; r < R; ++r) v[q * R + r] = tw_apply<SIGN>(v[q * R + r], tw[(Ns - 1) + (r - 1) * Ns + k]);
     }
     dft_r<R, SIGN, T>(&v[q * R]);
   }
@@ -131,7 +150,7 @@ __device__ __forceinline__ typename CT<T>::t* st_run_from(typename CT<T>::t (&v)
 // All stages.  v: the first stage's inputs (slot i = element st_in_index<N,E,0>).
 // FINAL_IN_REGS: v ends holding element st_out_index<N,E>(lane, i) in slot i and
 // nullptr is returned; otherwise the result is stored in natural order in the
-// returned buffer (a or b).  tw: exp(-2 pi i t/N), t < N, readable by all threads.
+// returned buffer (a or b).  tw: the stage-ordered table built by st_build_twiddles.
 // The caller makes sure no thread of the line still reads a or b from earlier use.
 template <int N, int E, int SIGN, bool FINAL_IN_REGS, typename T, typename Addr, typename Sync>
 __device__ __forceinline__ typename CT<T>::t* st_fft(typename CT<T>::t (&v)[E], typename CT<T>::t* a,

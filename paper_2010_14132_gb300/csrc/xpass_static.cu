@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xfwd_s(const TI* __restrict__
   const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
   const long long ngroups = (row_end - row_begin + RB - 1) / RB;
   constexpr unsigned row_bytes = (unsigned)(2 * N * sizeof(TI));
-  for (int t = tid; t < N; t += xs_threads(E)) tw_s[t] = twx[t];
+  st_build_twiddles<N, E>(tw_s, twx, tid, xs_threads(E));
   for (int t = tid; t <= N / 2; t += xs_threads(E)) twr_s[t] = twr[t];
   Ring rg{};
   if (tid == 0) {
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(xs_threads(E), E >= 16 ? 4 : 3) k_xres_s(Resid
   const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
   const long long ngroups = (row_end - row_begin + RB - 1) / RB;
   constexpr unsigned s_bytes = RB * NX * 8, p_bytes = STAGE_P ? RB * NX * 4 : 0;
-  for (int t = tid; t < N; t += xs_threads(E)) tw_s[t] = twx[t];
+  st_build_twiddles<N, E>(tw_s, twx, tid, xs_threads(E));
   for (int t = tid; t <= N / 2; t += xs_threads(E)) twr_s[t] = twr[t];
   Ring rg{};
   if (tid == 0) {
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restri
   const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
   const long long ngroups = (row_end - row_begin + RB - 1) / RB;
   const unsigned row_bytes = (unsigned)xs_align((size_t)(N + 1) * sizeof(C), 16);
-  for (int t = tid; t < N; t += xs_threads(E)) tw_s[t] = twx[t];
+  st_build_twiddles<N, E>(tw_s, twx, tid, xs_threads(E));
   for (int t = tid; t <= N; t += xs_threads(E)) twr_s[t] = twr[t];
   Ring rg{};
   if (tid == 0) {

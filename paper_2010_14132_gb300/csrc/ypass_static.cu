@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant_
   C* tw_s = reinterpret_cast<C*>(smraw + 3 * tb);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + 3 * tb + (size_t)N * sizeof(C));
   const unsigned tile_bytes = (unsigned)((size_t)N * TK * sizeof(C));
-  for (int t = tid; t < N; t += nthreads) tw_s[t] = twy[t];
+  st_build_twiddles<N, E>(tw_s, twy, tid, nthreads);
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
