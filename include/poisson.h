@@ -75,11 +75,15 @@ typedef enum {
   POISSON_OPT_Y_KERNEL = 5,      /* y-pass kernel: 0 = persistent TMA-staged kernel where the shape
                                     allows, with the compile-time FFT for FP32 and power-of-two ny in
                                     [64, 2048] (default); 1 = plain shared-memory tile kernel;
-                                    2 = persistent TMA-staged kernel with the run-time FFT */
+                                    2 = persistent TMA-staged kernel with the run-time FFT;
+                                    3 = as 0, transforming in place in the TMA tile (two barriers per
+                                    stage, a third less shared memory) */
   POISSON_OPT_X_ELEMS = 6,       /* x-pass elements per thread for power-of-two lines: 8 (default) or 16 */
   POISSON_OPT_Y_ELEMS = 7,       /* y-pass elements per thread for power-of-two lines: 8 or 16 (default) */
   POISSON_OPT_LEVEL_CHUNK = 8,   /* levels per transform chunk (x-pass and y-pass of a chunk run back to
-                                    back so its spectrum stays in L2); 0 = about 32 MB (default) */
+                                    back so its spectrum stays in L2); 0 = all levels in one chunk
+                                    (default: the persistent kernels lose more to per-launch start-up
+                                    than L2 reuse gains) */
   POISSON_OPT_X_KERNEL = 9,      /* x-pass kernel of the FP32 transforms: 0 = persistent kernel with bulk-copy
                                     staging where nx/2 is a power of two in [64, 2048] (default),
                                     1 = one CTA per row group */

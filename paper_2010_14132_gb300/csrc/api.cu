@@ -423,7 +423,7 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       pl->lchunk = (int)value;
       return POISSON_OK;
     case POISSON_OPT_Y_KERNEL:
-      if (!(value == 0 || value == 1 || value == 2)) return POISSON_ERR_INVALID_ARG;
+      if (!(value == 0 || value == 1 || value == 2 || value == 3)) return POISSON_ERR_INVALID_ARG;
       pl->ykernel = (int)value;
       return POISSON_OK;
     case POISSON_OPT_COL_TILE:
@@ -488,9 +488,10 @@ static int check_ws(const poisson_plan* pl, void* ws) {
 static cudaError_t ypass(poisson_plan* pl, const Geom& g, int sign, void* spec, const int* done, Stats* stats,
                          cudaStream_t st) {
   const bool t_double = pl->fp64();
-  if (pl->ykernel == 0 && !t_double) {
+  if ((pl->ykernel == 0 || pl->ykernel == 3) && !t_double) {
     bool used = false;
-    cudaError_t e = launch_yfft_static(sign, spec, g, pl->fy, pl->tb, pl->ytile, done, &stats->err, st, &used);
+    cudaError_t e = launch_yfft_static(sign, spec, g, pl->fy, pl->tb, pl->ytile, pl->ykernel == 3, done,
+                                       &stats->err, st, &used);
     if (e != cudaSuccess || used) return e;
   }
   if (pl->ykernel == 0 || pl->ykernel == 2) {
@@ -504,8 +505,7 @@ static cudaError_t ypass(poisson_plan* pl, const Geom& g, int sign, void* spec, 
 // Levels per chunk of the transforms: x-pass and y-pass of a chunk run back to
 // back, so the chunk's spectrum (about 32 MB by default) stays in L2 between them.
 static int level_chunk(const poisson_plan* pl) {
-  int c = pl->lchunk;
-  if (c <= 0) c = (int)(32.0 * 1024 * 1024 / ((double)pl->g.plane * (double)pl->csize()));
+  const int c = pl->lchunk <= 0 ? pl->nz : pl->lchunk;   // default: one chunk (all levels)
   return c < 1 ? 1 : (c > pl->nz ? pl->nz : c);
 }
 
@@ -564,7 +564,8 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
 // Inverse transform (chunked y-pass then x-pass with the given epilogue);
 // *nparts receives the number of partial-sum slots the x-pass launches wrote.
 static cudaError_t inverse(poisson_plan* pl, char* ws, cudaStream_t st, const int* done, int to_double, int mode,
-                           void* out, XinvExtra ex, int* nparts) {
+                           void* out, XinvExtra ex, int* nparts, bool* control_fused = nullptr) {
+  if (control_fused) *control_fused = false;
   const bool t_double = pl->fp64();
   void* spec = ws + pl->off_spec;
   Stats* stats = (Stats*)(ws + pl->off_stats);
@@ -584,8 +585,13 @@ static cudaError_t inverse(poisson_plan* pl, char* ws, cudaStream_t st, const in
     ps = prof_begin(pl, POISSON_PHASE_XINV, st);
     bool used = false;
     ex.err = &stats->err;
+    XinvExtra exs = ex;
+    // one chunk: the static kernel's last CTA runs the refinement control itself
+    const bool fuse = control_fused && mode != XINV_PLAIN && lc >= pl->nz;
+    if (!fuse) exs.ctl_stats = nullptr;
     if (!t_double && pl->xkernel == 0)
-      e = launch_xinv_static(to_double, mode, spec, out, gc, pl->fx, pl->tb, ex, &nb, st, &used);
+      e = launch_xinv_static(to_double, mode, spec, out, gc, pl->fx, pl->tb, exs, &nb, st, &used);
+    if (used && fuse) *control_fused = true;
     if (e == cudaSuccess && !used) e = launch_xinv(t_double, to_double, mode, spec, out, gc, pl->fx, pl->tb, ex, &nb, st);
     prof_end(pl, ps, st);
     if (e != cudaSuccess) return e;
@@ -643,11 +649,20 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
     PGB_CUDA(forward_columns(pl, S, 1, ws, st, 0, nullptr));
     ex.p0 = p0;
     ex.p_out = pl->max_sweeps == 0 ? (double*)p : nullptr;
-    PGB_CUDA(inverse(pl, ws, st, nullptr, 0, XINV_P0, p0, ex, &nb));
-    int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-    cudaError_t e = launch_control(stats, ex.partials, nb, 0, pl->max_sweeps, pl->tol, pl->g.N, st);
-    prof_end(pl, ps, st);
-    PGB_CUDA(e);
+    ex.ctl_stats = stats;
+    ex.ctl_max_sweeps = pl->max_sweeps;
+    ex.ctl_tol = pl->tol;
+    ex.ctl_npoints = pl->g.N;
+    ex.ctl_pass = 0;
+    bool fused = false;
+    PGB_CUDA(inverse(pl, ws, st, nullptr, 0, XINV_P0, p0, ex, &nb, &fused));
+    cudaError_t e = cudaSuccess;
+    if (!fused) {
+      int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
+      e = launch_control(stats, ex.partials, nb, 0, pl->max_sweeps, pl->tol, pl->g.N, st);
+      prof_end(pl, ps, st);
+      PGB_CUDA(e);
+    }
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
       // residual computed inside the forward x-pass (its rows are never stored)
       const ResidualArgs R{(const double*)S, p0, sweep > 1 ? q : nullptr, pl->tb.a_ff, pl->tb.c_ff,
@@ -659,11 +674,14 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
       eu.q_valid = sweep > 1;
       eu.p_out = (double*)p;
       eu.done = done;
-      PGB_CUDA(inverse(pl, ws, st, done, 0, XINV_UPDATE, nullptr, eu, &nb));
-      ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-      e = launch_control(stats, ex.partials, nb, sweep, pl->max_sweeps, pl->tol, pl->g.N, st);
-      prof_end(pl, ps, st);
-      PGB_CUDA(e);
+      eu.ctl_pass = sweep;
+      PGB_CUDA(inverse(pl, ws, st, done, 0, XINV_UPDATE, nullptr, eu, &nb, &fused));
+      if (!fused) {
+        int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
+        e = launch_control(stats, ex.partials, nb, sweep, pl->max_sweeps, pl->tol, pl->g.N, st);
+        prof_end(pl, ps, st);
+        PGB_CUDA(e);
+      }
     }
   }
   if (info) return fill_info(pl, ws, st, info);

@@ -127,7 +127,7 @@ __device__ __forceinline__ void st_load(C (&v)[E], const C* buf, Addr addr, int 
     for (int r = 0; r < R; ++r) v[q * R + r] = buf[addr(lane + nl * q + r * m)];
 }
 
-template <int N, int E, int SIGN, bool FINAL_IN_REGS, int S, typename T, typename Addr, typename Sync>
+template <int N, int E, int SIGN, bool FINAL_IN_REGS, int S, bool INPLACE, typename T, typename Addr, typename Sync>
 __device__ __forceinline__ typename CT<T>::t* st_run_from(typename CT<T>::t (&v)[E], typename CT<T>::t* cur,
                                                           typename CT<T>::t* nxt, Addr addr, int lane,
                                                           const typename CT<T>::t* __restrict__ tw, Sync sync) {
@@ -142,7 +142,8 @@ __device__ __forceinline__ typename CT<T>::t* st_run_from(typename CT<T>::t (&v)
       return cur;
     } else {
       st_load<st_radix(N, S + 1, E), E, N>(v, cur, addr, lane);
-      return st_run_from<N, E, SIGN, FINAL_IN_REGS, S + 1, T>(v, nxt, cur, addr, lane, tw, sync);
+      if constexpr (INPLACE) sync();   // one buffer: every read of this stage precedes the next writes
+      return st_run_from<N, E, SIGN, FINAL_IN_REGS, S + 1, INPLACE, T>(v, nxt, cur, addr, lane, tw, sync);
     }
   }
 }
@@ -152,14 +153,23 @@ __device__ __forceinline__ typename CT<T>::t* st_run_from(typename CT<T>::t (&v)
 // nullptr is returned; otherwise the result is stored in natural order in the
 // returned buffer (a or b).  tw: the stage-ordered table built by st_build_twiddles.
 // The caller makes sure no thread of the line still reads a or b from earlier use.
-template <int N, int E, int SIGN, bool FINAL_IN_REGS, typename T, typename Addr, typename Sync>
+template <int N, int E, int SIGN, bool FINAL_IN_REGS, typename T, typename Addr, typename Sync,
+          bool INPLACE = false>
 __device__ __forceinline__ typename CT<T>::t* st_fft(typename CT<T>::t (&v)[E], typename CT<T>::t* a,
                                                      typename CT<T>::t* b, Addr addr, int lane,
                                                      const typename CT<T>::t* __restrict__ tw, Sync sync) {
   static_assert(st_valid(N, E), "unsupported static FFT shape");
   // lane < N/E: lets the compiler split swizzled addresses into a per-thread base plus constants
   __builtin_assume(lane >= 0 && lane < N / E);
-  return st_run_from<N, E, SIGN, FINAL_IN_REGS, 0, T>(v, a, b, addr, lane, tw, sync);
+  return st_run_from<N, E, SIGN, FINAL_IN_REGS, 0, INPLACE, T>(v, a, b, addr, lane, tw, sync);
+}
+// In-place variant: one buffer, two barriers per stage.  The caller makes sure every
+// thread has read its first-stage inputs from buf before the first store.
+template <int N, int E, int SIGN, bool FINAL_IN_REGS, typename T, typename Addr, typename Sync>
+__device__ __forceinline__ typename CT<T>::t* st_fft_inplace(typename CT<T>::t (&v)[E], typename CT<T>::t* buf,
+                                                             Addr addr, int lane,
+                                                             const typename CT<T>::t* __restrict__ tw, Sync sync) {
+  return st_fft<N, E, SIGN, FINAL_IN_REGS, T, Addr, Sync, true>(v, buf, buf, addr, lane, tw, sync);
 }
 
 }  // namespace pgb

@@ -23,6 +23,44 @@ struct Stats {
   unsigned err;           // ERR_* bits
 };
 
+// Refinement control after pass `pass` (0 = first solve) from the norm sums of
+// that pass: sd0 = sum delta^2, sp = sum p^2, sm = sum p.  Records the norms,
+// the relative update and the error estimate rel_n (rel_n / rel_{n-1}), and sets
+// `done` (and `converged`) once the estimate is at most tol or the sweeps are
+// used up.  One thread.
+__device__ __forceinline__ void control_decide(Stats* st, double sd0, double sp, double sm, int pass, int max_sweeps,
+                                               double tol, long long npoints) {
+  st->pmean = sm / (double)npoints;
+  if (pass == 0) {   // mu_W as a double-float pair, for the residual of the sweeps
+    const float h = __double2float_rn(st->mu_w);
+    st->mu_ff = make_float2(h, __double2float_rn(st->mu_w - (double)h));
+  }
+  const double sd = (pass == 0) ? sp : sd0;
+  st->sq_delta[pass] = sd;
+  st->sq_p[pass] = sp;
+  const double rel = (sp > 0) ? sqrt(sd / sp) : 0.0;
+  st->rel_update[pass] = (pass == 0) ? 1.0 : rel;
+  st->sweeps = pass;
+  if (pass == 0) {
+    st->err_est = -1.0;
+    if (max_sweeps == 0) {
+      st->done = 1;
+      st->converged = 1;
+    }
+    return;
+  }
+  const double prev = st->rel_update[pass - 1];
+  const double est = (prev > 0) ? rel * (rel / prev) : rel;
+  st->err_est = est;
+  if (est <= tol || rel == 0.0) {
+    st->done = 1;
+    st->converged = 1;
+  } else if (pass >= max_sweeps) {
+    st->done = 1;
+    st->converged = 0;
+  }
+}
+
 // Device-resident tables owned by a plan.
 struct Tables {
   // vertical coefficients, level k
@@ -62,6 +100,11 @@ struct XinvExtra {
   int part0;            // partial-sum slot of this launch's first block
   const int* done;      // skip when set (nullable)
   unsigned* err;        // ERR_* bits of the persistent kernels (nullable only when they are not used)
+  // refinement control run by the launch's last CTA (persistent kernels; ctl_stats nullable = not fused)
+  Stats* ctl_stats;
+  int ctl_pass, ctl_max_sweeps;
+  double ctl_tol;
+  long long ctl_npoints;
 };
 
 // Inputs of the double-float refinement residual r = S - mu_W - L (p0 + q).
@@ -138,7 +181,7 @@ cudaError_t launch_xinv_static(int to_is_double, int mode, const void* spec, voi
 // Persistent FP32 y-pass with the compile-time FFT for power-of-two ny in [64, 2048].
 bool ypass_static_supported(int ny);
 cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPlan& fy, const Tables& tb, int tile,
-                               const int* done, unsigned* err, cudaStream_t st, bool* used);
+                               bool inplace, const int* done, unsigned* err, cudaStream_t st, bool* used);
 
 // Upper bound on the CTAs (and so partial-sum slots) of the x-pass launches of one field.
 int xpass_blocks(const Geom& g, const FftPlan& fx, size_t csize);

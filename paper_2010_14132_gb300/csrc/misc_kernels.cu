@@ -121,32 +121,7 @@ __global__ void __launch_bounds__(256) k_control(Stats* st, const double* __rest
     sm += stage[3 * i + 2];
   }
   *ticket = 0;   // ready for the next pass
-  st->pmean = sm / (double)npoints;
-  if (pass == 0) st->mu_ff = split_ff(st->mu_w);   // for the residual of the sweeps
-  const double sd = (pass == 0) ? sp : sd0;
-  st->sq_delta[pass] = sd;
-  st->sq_p[pass] = sp;
-  const double rel = (sp > 0) ? sqrt(sd / sp) : 0.0;
-  st->rel_update[pass] = (pass == 0) ? 1.0 : rel;
-  st->sweeps = pass;
-  if (pass == 0) {
-    st->err_est = -1.0;
-    if (max_sweeps == 0) {
-      st->done = 1;
-      st->converged = 1;
-    }
-    return;
-  }
-  const double prev = st->rel_update[pass - 1];
-  const double est = (prev > 0) ? rel * (rel / prev) : rel;
-  st->err_est = est;
-  if (est <= tol || rel == 0.0) {
-    st->done = 1;
-    st->converged = 1;
-  } else if (pass >= max_sweeps) {
-    st->done = 1;
-    st->converged = 0;
-  }
+  control_decide(st, sd0, sp, sm, pass, max_sweeps, tol, npoints);
 }
 
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps, double tol,

@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restri
     // deterministic CTA partial sums: fixed-order tree over the CTA's threads, in the
     // line buffers (no longer in use: every thread is past its last transform)
     constexpr int TH = xs_threads(E);
-    static_assert((size_t)TH * 16 <= (size_t)RB * 2 * LS * sizeof(C), "reduction does not fit the line buffers");
+    static_assert((size_t)TH * 24 <= (size_t)RB * 2 * LS * sizeof(C), "reduction does not fit the line buffers");
     __syncthreads();
     double* redd = reinterpret_cast<double*>(lines);
     float (*red)[TH] = reinterpret_cast<float (*)[TH]>(redd + TH);
@@ -487,11 +487,48 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restri
       }
       __syncthreads();
     }
+    __shared__ bool last;
     if (tid == 0) {
       const long long slot = ex.part0 + blockIdx.x;
       ex.partials[3 * slot] = (double)red[0][0];
       ex.partials[3 * slot + 1] = (double)red[1][0];
       ex.partials[3 * slot + 2] = redd[0];
+      last = false;
+      if (ex.ctl_stats) {
+        __threadfence();
+        last = atomicAdd(&ex.ctl_stats->control_ticket, 1u) == gridDim.x - 1;
+      }
+    }
+    __syncthreads();
+    if (last) {
+      // the last CTA to finish sums every CTA's partials in a fixed order and runs the control
+      __threadfence();
+      double* sums = redd;   // [3][TH] in the line buffers
+      double a0 = 0, a1 = 0, a2 = 0;
+      for (int i = tid; i < (int)gridDim.x; i += TH) {
+        const long long slot = ex.part0 + i;
+        a0 += __ldcg(&ex.partials[3 * slot]);
+        a1 += __ldcg(&ex.partials[3 * slot + 1]);
+        a2 += __ldcg(&ex.partials[3 * slot + 2]);
+      }
+      __syncthreads();
+      sums[tid] = a0;
+      sums[TH + tid] = a1;
+      sums[2 * TH + tid] = a2;
+      __syncthreads();
+      for (int h = TH / 2; h > 0; h >>= 1) {
+        if (tid < h) {
+          sums[tid] += sums[tid + h];
+          sums[TH + tid] += sums[TH + tid + h];
+          sums[2 * TH + tid] += sums[2 * TH + tid + h];
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {
+        ex.ctl_stats->control_ticket = 0u;   // ready for the next pass
+        control_decide(ex.ctl_stats, sums[0], sums[TH], sums[2 * TH], ex.ctl_pass, ex.ctl_max_sweeps, ex.ctl_tol,
+                       ex.ctl_npoints);
+      }
     }
   }
 }

@@ -33,11 +33,13 @@ struct Plain {
 };
 
 size_t ys_tile_bytes(int N, int TK) { return ((size_t)N * TK * sizeof(float2) + 127) / 128 * 128; }
-size_t ys_smem(int N, int TK) { return 3 * ys_tile_bytes(N, TK) + (size_t)N * sizeof(float2) + 64; }
+size_t ys_smem(int N, int TK, bool inplace) {
+  return (inplace ? 2 : 3) * ys_tile_bytes(N, TK) + (size_t)N * sizeof(float2) + 64;
+}
 
 constexpr int ys_max_threads(int E) { return E >= 16 ? 512 : 1024; }
 
-template <int N, int E, int SIGN>
+template <int N, int E, int SIGN, bool INPLACE>
 __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant__ CUtensorMap tm, Geom g,
                                             const float2* __restrict__ twy, float2* __restrict__ spec, int box_rows,
                                             int tiles_per_level, int ntiles, const int* __restrict__ done,
@@ -49,10 +51,11 @@ __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant_
   const int TK = blockDim.x, l = threadIdx.x, lane = threadIdx.y;
   const int tid = lane * TK + l, nthreads = TK * nl;
   const size_t tb = ((size_t)N * TK * sizeof(C) + 127) / 128 * 128;
+  constexpr int NT = INPLACE ? 2 : 3;   // tile buffers: the TMA ring (+ a scratch tile)
   C* ring[2] = {reinterpret_cast<C*>(smraw), reinterpret_cast<C*>(smraw + tb)};
   C* scratch = reinterpret_cast<C*>(smraw + 2 * tb);
-  C* tw_s = reinterpret_cast<C*>(smraw + 3 * tb);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + 3 * tb + (size_t)N * sizeof(C));
+  C* tw_s = reinterpret_cast<C*>(smraw + NT * tb);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + NT * tb + (size_t)N * sizeof(C));
   const unsigned tile_bytes = (unsigned)((size_t)N * TK * sizeof(C));
   st_build_twiddles<N, E>(tw_s, twy, tid, nthreads);
   if (tid == 0) {
@@ -96,7 +99,13 @@ __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant_
     C v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = in[Plain{TK}(st_in_index<N, E, 0>(lane, i)) + l];
-    st_fft<N, E, SIGN, true, float>(v, scratch + l, in + l, sw, lane, tw_s, SyncBlock());
+    if constexpr (INPLACE) {
+      __syncthreads();   // every thread has its inputs before the tile is overwritten
+      st_fft_inplace<N, E, SIGN, true, float>(v, in + l, sw, lane, tw_s, SyncBlock());
+    } else {
+      st_fft<N, E, SIGN, true, float>(v, scratch + l, in + l, sw, lane, tw_s, SyncBlock());
+    }
+    (void)scratch;
     const int level = t / tiles_per_level, kx = (t - level * tiles_per_level) * TK + l;
     if (kx < g.nxh) {
       C* col = spec + (long long)level * g.plane + kx;
@@ -129,10 +138,10 @@ int largest_divisor_upto(int n, int cap) {
     default: return cudaSuccess;                                \
   }
 
-template <int E, int SIGN>
+template <int E, int SIGN, bool INPLACE>
 cudaError_t ys_launch(float2* spec, const Geom& g, int N, const float2* twy, int tk, const int* done, unsigned* err,
                       cudaStream_t st, bool* used) {
-  const size_t smem = ys_smem(N, tk);
+  const size_t smem = ys_smem(N, tk, INPLACE);
   const int nthreads = tk * (N / E);
   if (smem > 220 * 1024 || nthreads > ys_max_threads(E) || nthreads < 32) return cudaSuccess;
   const int box_rows = largest_divisor_upto(N, 256);
@@ -151,7 +160,7 @@ cudaError_t ys_launch(float2* spec, const Geom& g, int N, const float2* twy, int
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e = cudaSuccess;
   PGB_YS_N_SWITCH(N, {
-    auto kern = k_ys<NN, E, SIGN>;
+    auto kern = k_ys<NN, E, SIGN, INPLACE>;
     int per_sm = 0;
     {
       std::lock_guard<std::mutex> lock(mu);
@@ -184,20 +193,24 @@ bool ypass_static_supported(int ny) {
 }
 
 cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPlan& fy, const Tables& tb, int tile,
-                               const int* done, unsigned* err, cudaStream_t st, bool* used) {
+                               bool inplace, const int* done, unsigned* err, cudaStream_t st, bool* used) {
   *used = false;
   if (!ypass_static_supported(fy.n)) return cudaSuccess;
   int tk = tile > 0 ? tile : 4;
   if (tk % 2) tk += 1;   // 16-byte inner TMA box
   const int E = fy.E == 16 ? 16 : 8;
-  while (tk > 2 && (ys_smem(fy.n, tk) > 220 * 1024 || tk * (fy.n / E) > ys_max_threads(E))) tk >>= 1;
+  while (tk > 2 && (ys_smem(fy.n, tk, inplace) > 220 * 1024 || tk * (fy.n / E) > ys_max_threads(E))) tk >>= 1;
   float2* sp = (float2*)spec;
+#define PGB_YS_CALL(EE, SG)                                                                   \
+  return inplace ? ys_launch<EE, SG, true>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)    \
+                 : ys_launch<EE, SG, false>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)
   if (E == 16) {
-    if (sign < 0) return ys_launch<16, -1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
-    return ys_launch<16, +1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
+    if (sign < 0) PGB_YS_CALL(16, -1);
+    PGB_YS_CALL(16, +1);
   }
-  if (sign < 0) return ys_launch<8, -1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
-  return ys_launch<8, +1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
+  if (sign < 0) PGB_YS_CALL(8, -1);
+  PGB_YS_CALL(8, +1);
+#undef PGB_YS_CALL
 }
 
 }  // namespace pgb
