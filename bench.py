@@ -227,6 +227,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -372,6 +373,32 @@ def main():
                 "steps": K3, "bound": "alu (FP64 at 1/65 of FP32 on GB300)"}
         del plan64, p64
 
+    # ---- the batched form: 64 uneven domains (nx = ny in {64..512}, nz in {32..96}) in one graph launch
+    batch = None
+    if not args.no_batch:
+        from paper_2010_14132_gb300.solver import Batch
+        doms = wl.uneven_batch(64)
+        bt = Batch(doms, dtype="mixed")
+        Sb = [torch.from_numpy(dd.S).cuda() for dd in doms]
+        Pb = [torch.empty_like(x) for x in Sb]
+        for _ in range(3):
+            bt.solve(Sb, Pb)
+        torch.cuda.synchronize()
+        K4 = 10
+        barrier()
+        e0.record(stream)
+        for _ in range(K4):
+            bt.solve(Sb, Pb, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        msb = max_over_ranks(e0.elapsed_time(e1) / K4)
+        npb = sum(dd.npoints for dd in doms)
+        batch = {"workload": "uneven_batch_64_mixed", "domains": len(doms), "points": npb, "ms_per_batch": msb,
+                 "value": world * npb / (msb * 1e-3) / 1e6, "unit": "Mpoints/s", "steps": K4}
+        bt.close()
+        del Sb, Pb
+
     n_launches_per_solve = sum(int(round(v["launches_per_solve"])) for v in phases.values())
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -396,6 +423,7 @@ def main():
                                "peak": peak, "peak_kind": peak_kind},
             "phases": phases,
             "fp64": fp64,
+            "batch": batch,
             "e2e": e2e,
             "gpu_launches": n_launches_per_solve * args.steps,
             "clocks": clocks,

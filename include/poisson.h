@@ -196,13 +196,18 @@ int poisson_batch_create(int n, const int* nx, const int* ny, const int* nz, con
                          int dtype, poisson_batch** out);
 int poisson_batch_workspace_bytes(const poisson_batch* batch, size_t* bytes);
 /* S[b], p[b]: device fields of domain b.  info: nullable array of n structs.
- * The first call captures the launch sequence of all domains into a CUDA graph
- * bound to the given pointers and workspace; later calls with the same pointers,
- * workspace and stream replay it with a single graph launch, other pointers
- * re-capture.  Returns the first failing domain's status. */
+ * The first call captures the launch sequences of all domains into one CUDA graph
+ * of concurrent branches (domains largest first, each to the least-loaded of 8
+ * branches), bound to the given pointers and workspace; later calls with the
+ * same pointers, workspace and plan options replay it with a single graph
+ * launch, anything else re-captures.  Returns the first failing domain's status. */
 int poisson_batch_solve(poisson_batch* batch, const void* const* S, void* const* p,
                         void* workspace, void* stream, poisson_info* info);
 int poisson_batch_destroy(poisson_batch* batch);
+/* The plan of domain i (owned by the batch): for poisson_plan_set_option, e.g. to apply
+ * autotuned kernel shapes.  Option changes re-capture the graph at the next solve;
+ * query poisson_batch_workspace_bytes again after changing options. */
+int poisson_batch_plan(poisson_batch* batch, int i, poisson_plan** plan);
 
 /* ---- Host-buffer pipeline: a stream of solves on one plan, fields in host memory ----
  * Not a step of the paper's method: the way a time-stepping host feeds the

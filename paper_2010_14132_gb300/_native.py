@@ -38,6 +38,7 @@ EXPORTED = (
     "poisson_last_error_detail", "poisson_batch_create", "poisson_batch_workspace_bytes", "poisson_batch_solve",
     "poisson_batch_destroy", "poisson_plan_profile_read", "poisson_solve_static_workspace",
     "poisson_pipe_create", "poisson_pipe_submit", "poisson_pipe_wait", "poisson_pipe_destroy",
+    "poisson_batch_plan",
 )
 
 # size of the fixed device array poisson_solve_static_workspace uses as scratch
@@ -107,6 +108,7 @@ def load():
     L.poisson_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int), i]
     L.poisson_solve_static_workspace.argtypes = [vp, vp, vp, vp, C.POINTER(PoissonInfo)]
     L.poisson_pipe_create.argtypes = [vp, C.POINTER(vp)]
+    L.poisson_batch_plan.argtypes = [vp, i, C.POINTER(vp)]
     L.poisson_pipe_submit.argtypes = [vp, vp, vp]
     L.poisson_pipe_wait.argtypes = [vp]
     L.poisson_pipe_destroy.argtypes = [vp]
@@ -249,3 +251,9 @@ def poisson_pipe_wait(pipe):
 def poisson_pipe_destroy(pipe):
     if pipe:
         load().poisson_pipe_destroy(pipe)
+
+
+def poisson_batch_plan(batch, i):
+    out = C.c_void_p()
+    _check(load().poisson_batch_plan(batch, int(i), C.byref(out)), "poisson_batch_plan")
+    return out.value

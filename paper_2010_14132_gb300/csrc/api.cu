@@ -3,6 +3,7 @@
 // of each call.  Section 2.1: plan once, execute every timestep.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -77,6 +78,7 @@ struct poisson_plan {
   FftPlan fx{}, fy{};
   int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
       coltile = 0;
+  unsigned version = 0;   // bumped by every option change (invalidates captured batch graphs)
   double tol = 1e-11;
   Geom g{};
   Tables tb{};
@@ -98,15 +100,19 @@ struct poisson_plan {
 };
 
 struct poisson_batch {
+  static constexpr int kBranches = 8;   // concurrent graph branches
   int n = 0;
   int dtype = 0;
   std::vector<poisson_plan*> plans;
   std::vector<size_t> off;
   size_t ws_bytes = 0;
   cudaStream_t cap = nullptr;
+  cudaStream_t branch[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> capS;
   std::vector<void*> capP;
+  std::vector<unsigned> capV;   // plan versions at capture
   void* capW = nullptr;
 };
 
@@ -380,6 +386,7 @@ int poisson_plan_workspace_bytes(const poisson_plan* pl, size_t* bytes) {
 
 int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
   if (!pl) return POISSON_ERR_INVALID_ARG;
+  pl->version++;
   switch (option) {
     case POISSON_OPT_LOWK_RADIUS2: {
       if (!(value >= 0) || value > 1e6) return POISSON_ERR_INVALID_ARG;
@@ -722,6 +729,11 @@ int poisson_batch_destroy(poisson_batch* b) {
   if (!b) return POISSON_OK;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int k = 0; k < poisson_batch::kBranches; ++k) {
+    if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+    if (b->join[k]) cudaEventDestroy(b->join[k]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   for (auto* p : b->plans) poisson_plan_destroy(p);
   delete b;
   return POISSON_OK;
@@ -752,6 +764,11 @@ int poisson_batch_create(int n, const int* nx, const int* ny, const int* nz, con
   }
   b->ws_bytes = off;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int k = 0; k < poisson_batch::kBranches && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     poisson_batch_destroy(b);
     return cuda_fail(e, "cudaStreamCreate");
@@ -760,9 +777,27 @@ int poisson_batch_create(int n, const int* nx, const int* ny, const int* nz, con
   return POISSON_OK;
 }
 
+// Workspace offsets of the domains (plans' workspace sizes change with their options).
+static void batch_layout(poisson_batch* b) {
+  size_t off = 0;
+  for (int i = 0; i < b->n; ++i) {
+    b->off[i] = off;
+    off = align256(off + b->plans[i]->ws_bytes);
+  }
+  b->ws_bytes = off;
+}
+
+int poisson_batch_plan(poisson_batch* b, int i, poisson_plan** out) {
+  if (!b || !out || i < 0 || i >= b->n) return POISSON_ERR_INVALID_ARG;
+  *out = b->plans[i];
+  return POISSON_OK;
+}
+
 int poisson_batch_workspace_bytes(const poisson_batch* b, size_t* bytes) {
   if (!b || !bytes) return POISSON_ERR_INVALID_ARG;
-  *bytes = b->ws_bytes;
+  size_t off = 0;   // the domains' current workspace sizes (options can change them)
+  for (int i = 0; i < b->n; ++i) off = align256(off + b->plans[i]->ws_bytes);
+  *bytes = off;
   return POISSON_OK;
 }
 
@@ -774,18 +809,44 @@ int poisson_batch_solve(poisson_batch* b, const void* const* S, void* const* p, 
     if (!S[i] || !p[i]) return POISSON_ERR_INVALID_ARG;
   bool same = b->exec && b->capW == workspace;
   if (same)
-    for (int i = 0; i < b->n; ++i) same = same && b->capS[i] == S[i] && b->capP[i] == p[i];
+    for (int i = 0; i < b->n; ++i)
+      same = same && b->capS[i] == S[i] && b->capP[i] == p[i] && b->capV[i] == b->plans[i]->version;
   if (!same) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
     }
+    batch_layout(b);
+    // domains largest first, each to the least-loaded of the concurrent branches
+    std::vector<int> order(b->n);
+    for (int i = 0; i < b->n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b->plans[x]->g.N > b->plans[y]->g.N; });
+    const int nbr = b->n < poisson_batch::kBranches ? b->n : poisson_batch::kBranches;
+    std::vector<long long> load(nbr, 0);
+    std::vector<int> branch_of(b->n, 0);
+    for (int i : order) {
+      int best = 0;
+      for (int k = 1; k < nbr; ++k)
+        if (load[k] < load[best]) best = k;
+      branch_of[i] = best;
+      load[best] += b->plans[i]->g.N;
+    }
     PGB_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
     int rc = POISSON_OK;
-    for (int i = 0; i < b->n && rc == POISSON_OK; ++i)
-      rc = poisson_solve(b->plans[i], S[i], p[i], (char*)workspace + b->off[i], b->cap, nullptr);
+    cudaError_t ce = cudaEventRecord(b->fork, b->cap);
+    for (int k = 0; k < nbr && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
+    for (int i : order) {
+      if (rc != POISSON_OK || ce != cudaSuccess) break;
+      rc = poisson_solve(b->plans[i], S[i], p[i], (char*)workspace + b->off[i], b->branch[branch_of[i]], nullptr);
+    }
+    for (int k = 0; k < nbr && ce == cudaSuccess; ++k) {
+      ce = cudaEventRecord(b->join[k], b->branch[k]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->join[k], 0);
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (ce != cudaSuccess && rc == POISSON_OK) rc = cuda_fail(ce, "batch capture branches", __LINE__);
     if (rc != POISSON_OK) {
       if (graph) cudaGraphDestroy(graph);
       return rc;
@@ -796,6 +857,8 @@ int poisson_batch_solve(poisson_batch* b, const void* const* S, void* const* p, 
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     b->capS.assign(S, S + b->n);
     b->capP.assign(p, p + b->n);
+    b->capV.resize(b->n);
+    for (int i = 0; i < b->n; ++i) b->capV[i] = b->plans[i]->version;
     b->capW = workspace;
   }
   PGB_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));

@@ -187,9 +187,14 @@ def poisson_solve(S: torch.Tensor, plan: Plan, rho0: torch.Tensor | None = None)
 
 
 class Batch:
-    """Many independent domains of uneven sizes, solved by one CUDA-graph launch."""
+    """Many independent domains of uneven sizes, solved by one CUDA-graph launch.
 
-    def __init__(self, domains, dtype="mixed", device=None):
+    The graph runs the domains on concurrent branches.  With ``tune=True`` every
+    distinct grid shape gets the autotuner's kernel shapes (measured once per GPU,
+    shape and dtype, then cached), applied to the domains' plans.
+    """
+
+    def __init__(self, domains, dtype="mixed", device=None, tune=False):
         if dtype not in ("fp32", "mixed"):
             raise ValueError("batched solves support dtype 'fp32' or 'mixed'")
         self.dtype = dtype
@@ -201,6 +206,14 @@ class Batch:
                                              [d.nz for d in domains], [d.dx for d in domains],
                                              [d.dy for d in domains], [d.dz for d in domains],
                                              [d.rho0 for d in domains], DTYPES[dtype])
+        if tune:
+            from .autotune import tuned_options, OPT_IDS
+            with torch.cuda.device(self.device):
+                for i, d in enumerate(domains):
+                    opts = tuned_options(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype)
+                    ph = N.poisson_batch_plan(self._h, i)
+                    for k, v in opts.items():
+                        N.poisson_plan_set_option(ph, OPT_IDS[k], v)
         nb = N.poisson_batch_workspace_bytes(self._h)
         self._ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
 

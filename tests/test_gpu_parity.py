@@ -211,3 +211,43 @@ def test_batch_uneven_domains(dtype):
         ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
         assert O.relative_l2(p.double().cpu().numpy(), ref) <= TOL[dtype]
         assert torch.equal(p, p2)
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "mixed"])
+def test_batch_autotuned_shapes(dtype, tmp_path, monkeypatch):
+    """Autotuned kernel shapes per domain give the same answers (concurrent graph branches)."""
+    monkeypatch.setenv("POISSON_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    import importlib
+    from paper_2010_14132_gb300 import autotune
+    importlib.reload(autotune)
+    doms = wl.uneven_batch(5, seed=71, nxy_choices=(64, 128), nz_choices=(16, 24))
+    b = Batch(doms, dtype=dtype, tune=True)
+    fd = torch.float32 if dtype == "fp32" else torch.float64
+    S = [torch.from_numpy(d.S).to("cuda", fd) for d in doms]
+    outs = b.solve(S)
+    torch.cuda.synchronize()
+    for d, p in zip(doms, outs):
+        ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
+        assert O.relative_l2(p.double().cpu().numpy(), ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "mixed"])
+def test_batch_64_uneven_domains_sampled(dtype):
+    """The 64-domain uneven batch (nx = ny in {64..512}, nz in {32..96}) in one graph launch:
+    the four smallest domains against the oracle, every domain's solution zero-mean and finite."""
+    doms = wl.uneven_batch(64)
+    b = Batch(doms, dtype=dtype)
+    fd = torch.float32 if dtype == "fp32" else torch.float64
+    S = [torch.from_numpy(d.S).to("cuda", fd) for d in doms]
+    outs, infos = b.solve(S, info=True)
+    torch.cuda.synchronize()
+    if dtype == "mixed":
+        assert all(i["converged"] for i in infos)
+    for p in outs:
+        pv = p.double()
+        assert torch.isfinite(pv).all()
+        assert abs(pv.mean().item()) <= 1e-6 * pv.abs().max().item()
+    for i in sorted(range(len(doms)), key=lambda i: doms[i].nx * doms[i].ny * doms[i].nz)[:4]:
+        d = doms[i]
+        ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
+        assert O.relative_l2(outs[i].double().cpu().numpy(), ref) <= TOL[dtype]
