@@ -184,6 +184,21 @@ def cpu_baseline(budget_s=20.0):
                       f"{d.nx}x{d.ny}x{d.nz} slab of the workload, {t:.2f} s, BLAS threads = host cores"}
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_rank, world, ms_max):
+    """Mpoints/s of the whole job: every rank solves its own replica in the slowest rank's time."""
+    return world * points_per_rank / (ms_max * 1e-3) / 1e6
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -192,7 +207,7 @@ def run_reference(args, rank, world):
     d = oracle_sample_domain(4)
     t4 = oracle_step(d.S, d, O)
     per_level = t4 / 4
-    budget = 150.0 / max(1, K + W)
+    budget = args.ref_budget / max(1, K + W)
     nz_s = int(max(2, min(WORKLOAD["nz"], budget / max(per_level, 1e-4))))
     d = oracle_sample_domain(nz_s)
     for _ in range(W):
@@ -228,6 +243,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="seconds of oracle time the reference arm aims for (all steps)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -272,12 +289,6 @@ def main():
         if dist:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # ---- timed region: device time, per-kernel events live on the launching stream
     plan.set_option(N.POISSON_OPT_PROFILE, 1)
@@ -298,10 +309,10 @@ def main():
     barrier()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = max_over_ranks(ms)
+    ms_max = max_over_ranks(ms, dist, "cuda")
     prof = N.poisson_plan_profile_read(plan._h)
     plan.set_option(N.POISSON_OPT_PROFILE, 0)
-    value = world * d.npoints / (ms_max * 1e-3) / 1e6
+    value = whole_job_rate(d.npoints, world, ms_max)
 
     # ---- roofline of the dominant kernel phase
     peak, peak_kind = measured_peaks()
@@ -345,7 +356,7 @@ def main():
     pipe.wait()
     t_e2e = time.perf_counter() - t_e2e
     barrier()
-    ms_e2e = max_over_ranks(t_e2e * 1e3 / K2)
+    ms_e2e = max_over_ranks(t_e2e * 1e3 / K2, dist, "cuda")
     pipe.close()
     e2e = {"value": world * d.npoints / (ms_e2e * 1e-3) / 1e6, "unit": "Mpoints/s",
            "h2d_bytes_per_step": int(S.numel() * 8), "d2h_bytes_per_step": int(p.numel() * 8),
@@ -368,7 +379,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms64 = max_over_ranks(e0.elapsed_time(e1) / K3)
+        ms64 = max_over_ranks(e0.elapsed_time(e1) / K3, dist, "cuda")
         fp64 = {"value": world * d.npoints / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
                 "steps": K3, "bound": "alu (FP64 at 1/65 of FP32 on GB300)"}
         del plan64, p64
@@ -392,7 +403,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        msb = max_over_ranks(e0.elapsed_time(e1) / K4)
+        msb = max_over_ranks(e0.elapsed_time(e1) / K4, dist, "cuda")
         npb = sum(dd.npoints for dd in doms)
         batch = {"workload": "uneven_batch_64_mixed", "domains": len(doms), "points": npb, "ms_per_batch": msb,
                  "value": world * npb / (msb * 1e-3) / 1e6, "unit": "Mpoints/s", "steps": K4}

@@ -1,0 +1,69 @@
+"""Multi-process (replica) host logic on CPU with the gloo backend, world size 2.
+
+The solver does not shard (DESIGN: replicas only): each rank solves its own
+grid and the bench reports the whole job's rate over the slowest rank's time.
+These tests run that reduction across two real processes, and the reference arm
+under torchrun, where rank 0 alone prints its line and both ranks exit 0.
+"""
+import importlib.util
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    b = _bench()
+    ms_local = 2.0 + 3.0 * rank          # the ranks' own step times
+    ms_max = b.max_over_ranks(ms_local, dist, "cpu")
+    value = b.whole_job_rate(1_000_000, world, ms_max)
+    with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+        json.dump({"ms_max": ms_max, "value": value}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_reduction_two_gloo_ranks(tmp_path):
+    port = _free_port()
+    mp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(2)]
+    for r in res:
+        assert r["ms_max"] == 5.0                          # the slowest rank's time on every rank
+        assert r["value"] == pytest.approx(2 * 1e6 / 5e-3 / 1e6)   # both replicas' points over that time
+
+
+def test_reference_arm_under_torchrun_prints_once(tmp_path):
+    port = _free_port()
+    env = dict(os.environ, MASTER_ADDR="127.0.0.1", OMP_NUM_THREADS="2")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-budget", "0.5"]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
