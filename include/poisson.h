@@ -77,7 +77,8 @@ typedef enum {
                                     [64, 2048] (default); 1 = plain shared-memory tile kernel;
                                     2 = persistent TMA-staged kernel with the run-time FFT;
                                     3 = as 0, transforming in place in the TMA tile (two barriers per
-                                    stage, a third less shared memory) */
+                                    stage, a third less shared memory); 4 = one tile per CTA, in
+                                    place, two CTAs per SM */
   POISSON_OPT_X_ELEMS = 6,       /* x-pass elements per thread for power-of-two lines: 8 (default) or 16 */
   POISSON_OPT_Y_ELEMS = 7,       /* y-pass elements per thread for power-of-two lines: 8 or 16 (default) */
   POISSON_OPT_LEVEL_CHUNK = 8,   /* levels per transform chunk (x-pass and y-pass of a chunk run back to

@@ -27,7 +27,7 @@ from .solver import Plan
 CACHE = os.environ.get("POISSON_AUTOTUNE_CACHE",
                        os.path.join(os.path.expanduser("~"), ".cache", "poisson_gb300_autotune.json"))
 
-Y_CANDIDATES = [dict(y_kernel=k, y_tile=t, y_elems=e) for k in (0, 3, 1, 2) for t in (2, 4, 8, 16) for e in (8, 16)]
+Y_CANDIDATES = [dict(y_kernel=k, y_tile=t, y_elems=e) for k in (0, 4, 3, 1, 2) for t in (2, 4, 8, 16) for e in (8, 16)]
 X_CANDIDATES = [dict(x_kernel=k, x_elems=e) for k in (0, 1) for e in (8, 16)]
 CHUNK_CANDIDATES = [dict(level_chunk=c) for c in (0, 1, 2, 4, 8, 16, 4096)]
 COL_CANDIDATES = [dict(col_tile=c) for c in (0, 1, 4, 3, 16, 32)]

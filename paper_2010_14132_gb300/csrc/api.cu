@@ -430,7 +430,7 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       pl->lchunk = (int)value;
       return POISSON_OK;
     case POISSON_OPT_Y_KERNEL:
-      if (!(value == 0 || value == 1 || value == 2 || value == 3)) return POISSON_ERR_INVALID_ARG;
+      if (!(value == 0 || value == 1 || value == 2 || value == 3 || value == 4)) return POISSON_ERR_INVALID_ARG;
       pl->ykernel = (int)value;
       return POISSON_OK;
     case POISSON_OPT_COL_TILE:
@@ -495,10 +495,11 @@ static int check_ws(const poisson_plan* pl, void* ws) {
 static cudaError_t ypass(poisson_plan* pl, const Geom& g, int sign, void* spec, const int* done, Stats* stats,
                          cudaStream_t st) {
   const bool t_double = pl->fp64();
-  if ((pl->ykernel == 0 || pl->ykernel == 3) && !t_double) {
+  if ((pl->ykernel == 0 || pl->ykernel == 3 || pl->ykernel == 4) && !t_double) {
     bool used = false;
-    cudaError_t e = launch_yfft_static(sign, spec, g, pl->fy, pl->tb, pl->ytile, pl->ykernel == 3, done,
-                                       &stats->err, st, &used);
+    const int variant = pl->ykernel == 3 ? 1 : (pl->ykernel == 4 ? 2 : 0);
+    cudaError_t e = launch_yfft_static(sign, spec, g, pl->fy, pl->tb, pl->ytile, variant, done, &stats->err, st,
+                                       &used);
     if (e != cudaSuccess || used) return e;
   }
   if (pl->ykernel == 0 || pl->ykernel == 2) {

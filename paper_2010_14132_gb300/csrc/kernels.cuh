@@ -180,8 +180,9 @@ cudaError_t launch_xinv_static(int to_is_double, int mode, const void* spec, voi
 
 // Persistent FP32 y-pass with the compile-time FFT for power-of-two ny in [64, 2048].
 bool ypass_static_supported(int ny);
+// variant 0: two-slot ring + scratch tile; 1: two-slot ring, in place; 2: one tile, in place, two CTAs/SM.
 cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPlan& fy, const Tables& tb, int tile,
-                               bool inplace, const int* done, unsigned* err, cudaStream_t st, bool* used);
+                               int variant, const int* done, unsigned* err, cudaStream_t st, bool* used);
 
 // Upper bound on the CTAs (and so partial-sum slots) of the x-pass launches of one field.
 int xpass_blocks(const Geom& g, const FftPlan& fx, size_t csize);

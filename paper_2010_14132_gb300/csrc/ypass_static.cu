@@ -121,6 +121,68 @@ __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant_
   }
 }
 
+
+// Single-buffered variant: one tile per CTA, transformed in place, two CTAs per
+// SM (registers capped for it), so one CTA's load overlaps the other's transform.
+template <int N, int E, int SIGN>
+__global__ void __launch_bounds__(ys_max_threads(E), 2) k_ys1(const __grid_constant__ CUtensorMap tm, Geom g,
+                                                             const float2* __restrict__ twy,
+                                                             float2* __restrict__ spec, int box_rows,
+                                                             int tiles_per_level, int ntiles,
+                                                             const int* __restrict__ done, unsigned* __restrict__ err) {
+  using C = float2;
+  constexpr int nl = N / E;
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int TK = blockDim.x, l = threadIdx.x, lane = threadIdx.y;
+  const int tid = lane * TK + l, nthreads = TK * nl;
+  const size_t tb = ((size_t)N * TK * sizeof(C) + 127) / 128 * 128;
+  C* tile = reinterpret_cast<C*>(smraw);
+  C* tw_s = reinterpret_cast<C*>(smraw + tb);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + tb + (size_t)N * sizeof(C));
+  const unsigned tile_bytes = (unsigned)((size_t)N * TK * sizeof(C));
+  st_build_twiddles<N, E>(tw_s, twy, tid, nthreads);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const SwStrided sw{TK};
+  int it = 0, pending = 0;
+  bool ok = true;
+  for (int t = g.lev0 * tiles_per_level + blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int level = t / tiles_per_level, kx0 = (t - level * tiles_per_level) * TK;
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, tile_bytes);
+      for (int r0 = 0; r0 < N; r0 += box_rows) tma_load_2d(tile + (size_t)r0 * TK, &tm, kx0, level * N + r0, bar);
+      pending = 1;
+    }
+    const bool got = mbar_wait_bounded(bar, (unsigned)(it & 1), kWaitPolls);
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    pending = 0;
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = tile[Plain{TK}(st_in_index<N, E, 0>(lane, i)) + l];
+    __syncthreads();   // every thread has its inputs before the tile is overwritten
+    st_fft_inplace<N, E, SIGN, true, float>(v, tile + l, sw, lane, tw_s, SyncBlock());
+    const int kx = kx0 + l;
+    if (kx < g.nxh) {
+      C* col = spec + (long long)level * g.plane + kx;
+#pragma unroll
+      for (int i = 0; i < E; ++i) col[(long long)st_out_index<N, E>(lane, i) * g.P] = v[i];
+    }
+    fence_proxy_async_smem();   // generic writes to the tile come before its refill by TMA
+    __syncthreads();            // every thread is done with the tile
+  }
+  if (tid == 0) {
+    if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
+    if (pending) mbar_wait_bounded(bar, (unsigned)(it & 1), kWaitPolls);   // let a copy in flight land
+  }
+}
+
 int largest_divisor_upto(int n, int cap) {
   for (int d = cap; d >= 1; --d)
     if (n % d == 0) return d;
@@ -183,6 +245,42 @@ cudaError_t ys_launch(float2* spec, const Geom& g, int N, const float2* twy, int
   return cudaGetLastError();
 }
 
+
+template <int E, int SIGN>
+cudaError_t ys1_launch(float2* spec, const Geom& g, int N, const float2* twy, int tk, const int* done, unsigned* err,
+                       cudaStream_t st, bool* used) {
+  const size_t smem = ys_tile_bytes(N, tk) + (size_t)N * sizeof(float2) + 64;
+  const int nthreads = tk * (N / E);
+  if (smem > 110 * 1024 || nthreads > ys_max_threads(E) || nthreads < 32) return cudaSuccess;
+  const int box_rows = largest_divisor_upto(N, 256);
+  if (((size_t)box_rows * tk * sizeof(float2)) % 128 != 0 && box_rows != N) return cudaSuccess;
+  CUtensorMap tm;
+  if (!encode_tensor_2d(&tm, spec, 8, (unsigned long long)g.nxh, (unsigned long long)g.ny * g.nz,
+                        (unsigned long long)g.P * sizeof(float2), (unsigned)tk, (unsigned)box_rows))
+    return cudaSuccess;
+  const int tiles_per_level = (g.nxh + tk - 1) / tk;
+  const int ntiles = tiles_per_level * g.lev1;
+  const int chunk_tiles = tiles_per_level * (g.lev1 - g.lev0);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaSuccess;
+  PGB_YS_N_SWITCH(N, {
+    auto kern = k_ys1<NN, E, SIGN>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaSuccess;
+    const int grid = chunk_tiles < sms * per_sm ? chunk_tiles : sms * per_sm;
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, dim3(tk, N / E), smem, st>>>(tm, g, twy, spec, box_rows, tiles_per_level, ntiles, done, err);
+    *used = true;
+  });
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool ypass_static_supported(int ny) {
@@ -193,12 +291,21 @@ bool ypass_static_supported(int ny) {
 }
 
 cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPlan& fy, const Tables& tb, int tile,
-                               bool inplace, const int* done, unsigned* err, cudaStream_t st, bool* used) {
+                               int variant, const int* done, unsigned* err, cudaStream_t st, bool* used) {
   *used = false;
   if (!ypass_static_supported(fy.n)) return cudaSuccess;
   int tk = tile > 0 ? tile : 4;
   if (tk % 2) tk += 1;   // 16-byte inner TMA box
   const int E = fy.E == 16 ? 16 : 8;
+  if (variant == 2) {   // single-buffered, in place, two CTAs per SM
+    while (tk > 2 && tk * (fy.n / E) > ys_max_threads(E)) tk >>= 1;
+    float2* sp = (float2*)spec;
+    if (E == 16) return sign < 0 ? ys1_launch<16, -1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)
+                                 : ys1_launch<16, +1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
+    return sign < 0 ? ys1_launch<8, -1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)
+                    : ys1_launch<8, +1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
+  }
+  const bool inplace = variant == 1;
   while (tk > 2 && (ys_smem(fy.n, tk, inplace) > 220 * 1024 || tk * (fy.n / E) > ys_max_threads(E))) tk >>= 1;
   float2* sp = (float2*)spec;
 #define PGB_YS_CALL(EE, SG)                                                                   \

@@ -78,7 +78,7 @@ def test_gradient_workload_forward_512x512x64(dtype):
                                       (2048, 8, 4), (8, 4096, 2), (128, 8, 3), (256, 12, 5), (512, 6, 7),
                                       (1024, 12, 3), (4096, 4, 3)])
 @pytest.mark.parametrize("dtype", ["fp64", "fp32"])
-@pytest.mark.parametrize("y_kernel", [0, 1, 2, 3])
+@pytest.mark.parametrize("y_kernel", [0, 1, 2, 3, 4])
 def test_sizes(nx, ny, nz, dtype, y_kernel):
     """Radix 2/3 mixes, ragged tiles, the smallest and largest line lengths.
 
@@ -109,7 +109,8 @@ def test_sizes_mixed(nx, ny, nz):
                                   dict(y_elems=8, y_tile=8), dict(y_elems=8, y_tile=2), dict(y_tile=8),
                                   dict(col_tile=16), dict(col_tile=32), dict(col_tile=64), dict(col_tile=128),
                                   dict(col_tile=1), dict(col_tile=3), dict(col_tile=4), dict(y_kernel=3),
-                                  dict(y_kernel=3, y_tile=4), dict(y_kernel=3, y_elems=8, y_tile=8)])
+                                  dict(y_kernel=3, y_tile=4), dict(y_kernel=3, y_elems=8, y_tile=8),
+                                  dict(y_kernel=4, y_tile=8), dict(y_kernel=4, y_tile=4, y_elems=8)])
 @pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
 def test_kernel_shape_options(opts, dtype):
     """Every autotuner candidate gives the same answer (tile shapes are not numerics)."""
