@@ -1,0 +1,180 @@
+// Persistent forward x-pass of a refinement sweep: the transformed rows are the residual.
+// (Section 2.1: the x transform of every row of every level; see xpass_common.cuh
+// for the persistent staging scheme the kernels share.)
+#include "xpass_common.cuh"
+
+namespace pgb {
+namespace {
+
+// ---------------------------------------------------------------------------
+// forward x-pass of a refinement sweep: the rows transformed are the residual
+// r = S - mu_W - L (p0 + q), formed as the group is read.  The group's rows of S,
+// p0 (and q) are staged; the x-neighbours come from the staged rows, the y- and
+// z-neighbour rows are read through L1/L2 (the neighbouring groups stage them).
+// ---------------------------------------------------------------------------
+template <int N, int E, bool HAS_Q, bool STAGE_P>
+__global__ void __launch_bounds__(xs_threads(E), E >= 24 ? 2 : (E >= 16 ? 4 : 3)) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
+                                                      const float2* __restrict__ twx, const float2* __restrict__ twr,
+                                                      const int* __restrict__ done, unsigned* __restrict__ err,
+                                                      int ns, unsigned stage_bytes) {
+  using C = float2;
+  constexpr int nl = N / E, RB = xs_threads(E) / nl, LS = swizzled_stride(N), NX = 2 * N;
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const XsLayout L = xs_layout(N, RB, ns, stage_bytes, true);
+  C* tw_s = reinterpret_cast<C*>(smraw);
+  C* twr_s = tw_s + N;
+  C* lines = twr_s + N + 2;
+  unsigned char* stg = smraw + L.off_stage;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + L.off_bar);
+
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * nl + lane;
+  const long long row_begin = (long long)g.lev0 * g.ny, row_end = (long long)g.lev1 * g.ny;
+  const long long ngroups = (row_end - row_begin + RB - 1) / RB;
+  constexpr unsigned s_bytes = RB * NX * 8, p_bytes = STAGE_P ? RB * NX * 4 : 0;
+  st_build_twiddles<N, E>(tw_s, twx, tid, xs_threads(E));
+  for (int t = tid; t <= N / 2; t += xs_threads(E)) twr_s[t] = twr[t];
+  Ring rg{};
+  if (tid == 0) {
+    for (int s = 0; s < ns; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](long long grp, int s) {
+    const long long r0 = row_begin + grp * RB;
+    const unsigned nv = (unsigned)(row_end - r0 < RB ? row_end - r0 : RB);
+    unsigned char* d = stg + (size_t)s * stage_bytes;
+    mbar_arrive_expect_tx(&bar[s], nv * NX * (8u + (STAGE_P ? 4u + (HAS_Q ? 4u : 0u) : 0u)));
+    bulk_g2s(d, R.S + r0 * NX, nv * NX * 8u, &bar[s]);
+    if constexpr (STAGE_P) {
+      bulk_g2s(d + s_bytes, R.p0 + r0 * NX, nv * NX * 4u, &bar[s]);
+      if constexpr (HAS_Q) bulk_g2s(d + s_bytes + p_bytes, R.q + r0 * NX, nv * NX * 4u, &bar[s]);
+    }
+    rg.issued[s]++;
+  };
+  if (tid == 0)
+    for (int s = 0; s < ns; ++s) {
+      const long long grp = blockIdx.x + (long long)s * gridDim.x;
+      if (grp < ngroups) issue(grp, s);
+    }
+  const LineSync sync{1 + ty, nl};
+  const Swizzled sw{};
+  (void)lines;
+  const float2 cx = R.cx, cy = R.cy;   // double-float splits of 1/dx^2, 1/dy^2
+  bool ok = true;
+  int it = 0;
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+    const int s = it % ns;
+    const long long row = row_begin + grp * RB + ty;
+    const bool valid = row < row_end;
+    const long long rc = valid ? row : row_begin;   // neighbour addressing stays inside the field
+    const int k = (int)(rc / g.ny), j = (int)(rc - (long long)k * g.ny);
+    const long long rn = rc - j + (j + 1 == g.ny ? 0 : j + 1), rs = rc - j + (j == 0 ? g.ny - 1 : j - 1);
+    const bool has_dn = k > 0, has_up = k + 1 < g.nz;
+    const float2* p0n = reinterpret_cast<const float2*>(R.p0 + rn * NX);
+    const float2* p0s = reinterpret_cast<const float2*>(R.p0 + rs * NX);
+    const float2* p0d = reinterpret_cast<const float2*>(R.p0 + (has_dn ? rc - g.ny : rc) * NX);
+    const float2* p0u = reinterpret_cast<const float2*>(R.p0 + (has_up ? rc + g.ny : rc) * NX);
+    const ResCoef K = res_coef(cx, cy, R.a_ff[k], R.c_ff[k], *R.mu_ff);
+    const bool got = mbar_wait_bounded(&bar[s], (unsigned)((it / ns) & 1), kWaitPolls);
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      rg.consumed[s]++;
+      if (it > 0) {
+        const long long gn = grp - gridDim.x + (long long)ns * gridDim.x;
+        if (gn < ngroups) {
+          fence_proxy_async_smem();
+          issue(gn, (it - 1) % ns);
+        }
+      }
+    }
+    unsigned char* d = stg + (size_t)s * stage_bytes;
+    const double2* Srow = reinterpret_cast<const double2*>(d) + (size_t)ty * N;
+    // the row's two line buffers are its staged S row (used once the residual is formed)
+    C* la = reinterpret_cast<C*>(d + (size_t)ty * NX * 8);
+    C* lb = la + LS;
+    // centre rows of p0 and q: staged, or read through L1 next to the other neighbours
+    const float* prow = STAGE_P ? reinterpret_cast<const float*>(d + s_bytes) + (size_t)ty * NX : R.p0 + rc * NX;
+    const float* qrow = STAGE_P ? reinterpret_cast<const float*>(d + s_bytes + p_bytes) + (size_t)ty * NX
+                                : (HAS_Q ? R.q + rc * NX : nullptr);
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int e = st_in_index<N, E, 0>(lane, i);
+      const float2 pc = reinterpret_cast<const float2*>(prow)[e];
+      const float pw = prow[e == 0 ? NX - 1 : 2 * e - 1];
+      const float pe = prow[e == N - 1 ? 0 : 2 * e + 2];
+      const float2 pn = p0n[e], ps = p0s[e];
+      const float2 pd = has_dn ? p0d[e] : pc, pu = has_up ? p0u[e] : pc;
+      float2 qc = make_float2(0.f, 0.f), qn = qc, qs = qc, qd = qc, qu = qc;
+      float qw = 0.f, qe = 0.f;
+      if constexpr (HAS_Q) {
+        qc = reinterpret_cast<const float2*>(qrow)[e];
+        qw = qrow[e == 0 ? NX - 1 : 2 * e - 1];
+        qe = qrow[e == N - 1 ? 0 : 2 * e + 2];
+        qn = reinterpret_cast<const float2*>(R.q + rn * NX)[e];
+        qs = reinterpret_cast<const float2*>(R.q + rs * NX)[e];
+        qd = has_dn ? reinterpret_cast<const float2*>(R.q + (rc - g.ny) * NX)[e] : qc;
+        qu = has_up ? reinterpret_cast<const float2*>(R.q + (rc + g.ny) * NX)[e] : qc;
+      }
+      const double2 S = Srow[e];
+      float2 Sh, Sl;
+      d2ff_trunc(S.x, Sh.x, Sl.x);
+      d2ff_trunc(S.y, Sh.y, Sl.y);
+      // the pair's east neighbours are (pc.y, pe), its west neighbours (pw, pc.x)
+      v[i] = residual_value2<HAS_Q>(pc, make_float2(pc.y, pe), make_float2(pw, pc.x), pn, ps, pd, pu, qc,
+                                    make_float2(qc.y, qe), make_float2(qw, qc.x), qn, qs, qd, qu, Sh, Sl, K);
+    }
+    sync();   // the line's threads have read the S row before it is overwritten
+    const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
+    r2c_unpack_store<N, E>(fin, twr_s, spec + (valid ? row : 0) * g.P, lane, valid);
+    fence_proxy_async_smem();   // generic writes to the staged row come before its refill by TMA
+  }
+  if (tid == 0) {
+    if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
+    ring_drain(rg, bar, ns);
+  }
+}
+
+template <bool HAS_Q>
+cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, int E, const Tables& tb,
+                   const int* done, unsigned* err, cudaStream_t st, bool* used) {
+  const int RB = xs_threads(E) / (N / E);
+  // stage S, p0 (and q) rows while three CTAs per SM still fit, else S rows only
+  const unsigned row_bytes_all = (unsigned)(g.nx * (8 + 4 + (HAS_Q ? 4 : 0)));
+  const unsigned row_bytes_s = (unsigned)(g.nx * 8);
+  const XsConfig c_all = xs_config(N, E, RB * row_bytes_all, 0, true);
+  const bool stage_p = c_all.ns > 0 && c_all.smem <= 75 * 1024 * (size_t)xs_threads(E) / 256;
+  const XsConfig c = stage_p ? c_all : xs_config(N, E, RB * row_bytes_s, 0, true);
+  if (c.ns == 0 || !aligned16(R.S) || !aligned16(R.p0) || (HAS_Q && !aligned16(R.q)) || (g.nx * 4) % 16)
+    return cudaSuccess;
+  const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
+  if (stage_p) {
+    PGB_XS_E8_24_SWITCH(E, PGB_XS_N_SWITCH(N, {
+      return xs_launch(k_xres_s<NN, EE, HAS_Q, true>, NN / EE, RB, c, ngroups, nullptr, st, used, R, spec, g,
+                       tb.twx_f, tb.twr_f, done, err);
+    }));
+  } else {
+    PGB_XS_E8_24_SWITCH(E, PGB_XS_N_SWITCH(N, {
+      return xs_launch(k_xres_s<NN, EE, HAS_Q, false>, NN / EE, RB, c, ngroups, nullptr, st, used, R, spec, g,
+                       tb.twx_f, tb.twr_f, done, err);
+    }));
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_xres_static(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx, const Tables& tb,
+                               const int* done, unsigned* err, cudaStream_t st, bool* used) {
+  *used = false;
+  if (!xpass_static_supported(fx.n)) return cudaSuccess;
+  const int E = fx.n % 3 == 0 ? 24 : 8;   // the residual kernel: 8 elements per thread for powers of two
+  if (R.q) return xres_s<true>(R, (float2*)spec, g, fx.n, E, tb, done, err, st, used);
+  return xres_s<false>(R, (float2*)spec, g, fx.n, E, tb, done, err, st, used);
+}
+
+}  // namespace pgb

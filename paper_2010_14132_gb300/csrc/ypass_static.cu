@@ -189,15 +189,22 @@ int largest_divisor_upto(int n, int cap) {
   return 1;
 }
 
-#define PGB_YS_N_SWITCH(N, ...)                                 \
-  switch (N) {                                                  \
-    case 64: { constexpr int NN = 64; __VA_ARGS__; } break;     \
-    case 128: { constexpr int NN = 128; __VA_ARGS__; } break;   \
-    case 256: { constexpr int NN = 256; __VA_ARGS__; } break;   \
-    case 512: { constexpr int NN = 512; __VA_ARGS__; } break;   \
-    case 1024: { constexpr int NN = 1024; __VA_ARGS__; } break; \
-    case 2048: { constexpr int NN = 2048; __VA_ARGS__; } break; \
-    default: return cudaSuccess;                                \
+#define PGB_YS_N_CASE(V, ...) \
+  case V: { constexpr int NN = V; if constexpr (st_valid(NN, E)) { __VA_ARGS__; } } break;
+#define PGB_YS_N_SWITCH(N, ...)        \
+  switch (N) {                         \
+    PGB_YS_N_CASE(64, __VA_ARGS__)     \
+    PGB_YS_N_CASE(96, __VA_ARGS__)     \
+    PGB_YS_N_CASE(128, __VA_ARGS__)    \
+    PGB_YS_N_CASE(192, __VA_ARGS__)    \
+    PGB_YS_N_CASE(256, __VA_ARGS__)    \
+    PGB_YS_N_CASE(384, __VA_ARGS__)    \
+    PGB_YS_N_CASE(512, __VA_ARGS__)    \
+    PGB_YS_N_CASE(768, __VA_ARGS__)    \
+    PGB_YS_N_CASE(1024, __VA_ARGS__)   \
+    PGB_YS_N_CASE(1536, __VA_ARGS__)   \
+    PGB_YS_N_CASE(2048, __VA_ARGS__)   \
+    default: return cudaSuccess;       \
   }
 
 template <int E, int SIGN, bool INPLACE>
@@ -285,7 +292,8 @@ cudaError_t ys1_launch(float2* spec, const Geom& g, int N, const float2* twy, in
 
 bool ypass_static_supported(int ny) {
   switch (ny) {
-    case 64: case 128: case 256: case 512: case 1024: case 2048: return true;
+    case 64: case 96: case 128: case 192: case 256: case 384: case 512: case 768: case 1024: case 1536: case 2048:
+      return true;
     default: return false;
   }
 }
@@ -296,14 +304,15 @@ cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPla
   if (!ypass_static_supported(fy.n)) return cudaSuccess;
   int tk = tile > 0 ? tile : 4;
   if (tk % 2) tk += 1;   // 16-byte inner TMA box
-  const int E = fy.E == 16 ? 16 : 8;
-  if (variant == 2) {   // single-buffered, in place, two CTAs per SM
-    while (tk > 2 && tk * (fy.n / E) > ys_max_threads(E)) tk >>= 1;
+  // 24 elements per thread when ny has a factor 3 (radix 3, then 8)
+  const int E = fy.n % 3 == 0 ? 24 : (fy.E == 16 ? 16 : 8);
+  if (variant == 2 && E == 16) {   // single-buffered, in place, two CTAs per SM (16 elements per thread)
+    int tk1 = tk;
+    while (tk1 > 2 && tk1 * (fy.n / E) > ys_max_threads(E)) tk1 >>= 1;
     float2* sp = (float2*)spec;
-    if (E == 16) return sign < 0 ? ys1_launch<16, -1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)
-                                 : ys1_launch<16, +1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
-    return sign < 0 ? ys1_launch<8, -1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)
-                    : ys1_launch<8, +1>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used);
+    cudaError_t e = sign < 0 ? ys1_launch<16, -1>(sp, g, fy.n, tb.twy_f, tk1, done, err, st, used)
+                             : ys1_launch<16, +1>(sp, g, fy.n, tb.twy_f, tk1, done, err, st, used);
+    if (e != cudaSuccess || *used) return e;
   }
   const bool inplace = variant == 1;
   while (tk > 2 && (ys_smem(fy.n, tk, inplace) > 220 * 1024 || tk * (fy.n / E) > ys_max_threads(E))) tk >>= 1;
@@ -311,6 +320,10 @@ cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPla
 #define PGB_YS_CALL(EE, SG)                                                                   \
   return inplace ? ys_launch<EE, SG, true>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)    \
                  : ys_launch<EE, SG, false>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)
+  if (E == 24) {
+    if (sign < 0) PGB_YS_CALL(24, -1);
+    PGB_YS_CALL(24, +1);
+  }
   if (E == 16) {
     if (sign < 0) PGB_YS_CALL(16, -1);
     PGB_YS_CALL(16, +1);
