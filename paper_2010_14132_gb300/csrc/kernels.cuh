@@ -159,6 +159,9 @@ cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, 
 cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
                                const Tables& tb, float2 cx, float2 cy, const float2* mu_ff, const int* done,
                                cudaStream_t st);
+// q = p - p0 (float) from the stored double iterate, before a second or third sweep (skipped when done).
+cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long long n, const int* done,
+                             cudaStream_t st);
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
                            double tol, long long npoints, cudaStream_t st);
 cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
@@ -167,7 +170,7 @@ cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math
                         const double* dz, const double* rho0, double* partials, int nparts_max,
                         double* grho, cudaStream_t st);
 
-// Persistent FP32 x-pass for half lengths 64..2048 (powers of two); *used is
+// Persistent FP32 x-pass for the half lengths xpass_static_supported accepts; *used is
 // false (and nothing is launched) when the shape or alignment does not allow it.
 bool xpass_static_supported(int n_half);
 cudaError_t launch_xfwd_static(int ti_is_double, const void* in, void* spec, const Geom& g, const FftPlan& fx,

@@ -1,6 +1,7 @@
 // Residual, refinement control, coefficient tables and rho0-gradient reductions.
 #include "kernels.cuh"
 #include "residual.cuh"
+#include "residual2.cuh"
 
 namespace pgb {
 
@@ -122,6 +123,41 @@ __global__ void __launch_bounds__(256) k_control(Stats* st, const double* __rest
   }
   *ticket = 0;   // ready for the next pass
   control_decide(st, sd0, sp, sm, pass, max_sweeps, tol, npoints);
+}
+
+// ---------------------------------------------------------------------------
+// Accumulated correction of the refinement, rebuilt before a second or third
+// sweep: q = p - p0 to float accuracy, from the double iterate p = p0 + q the
+// previous sweep stored ((h, l) = p split into floats; h - p0 is exact when h
+// and p0 are within a factor 2, and rounds at 2^-24 |q| otherwise).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_q_rebuild(const double2* __restrict__ p, const float2* __restrict__ p0,
+                                                   float2* __restrict__ q, long long npairs,
+                                                   const int* __restrict__ done) {
+  if (done && *done) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npairs;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 pv = __ldcs(&p[i]);
+    const float2 a = __ldcs(&p0[i]);
+    float hx, lx, hy, ly;
+    d2ff_trunc(pv.x, hx, lx);
+    d2ff_trunc(pv.y, hy, ly);
+    __stcs(&q[i], make_float2(__fadd_rn(__fsub_rn(hx, a.x), lx), __fadd_rn(__fsub_rn(hy, a.y), ly)));
+  }
+}
+
+cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long long n, const int* done,
+                             cudaStream_t st) {
+  const long long npairs = n / 2;   // nx is even
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (npairs + 255) / 256;
+  const long long cap = (long long)(sms > 0 ? sms : 1) * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_q_rebuild<<<(unsigned)blocks, 256, 0, st>>>((const double2*)p, (const float2*)p0, (float2*)q, npairs, done);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps, double tol,

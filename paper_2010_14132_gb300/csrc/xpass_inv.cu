@@ -121,9 +121,8 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restri
           sl = add2(sl, e);
           if (ex.p_out)
             __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(f2d_int(z.x), f2d_int(z.y)));
-        } else {   // XINV_UPDATE: q += delta, p = p0 + q as a double
+        } else {   // XINV_UPDATE: p = p0 + (q + delta) as a double (q is rebuilt from p if a later sweep runs)
           const float2 qn = add2(z, qv[i]);
-          __stcs(reinterpret_cast<float2*>(ex.q + base) + m, qn);
           float2 sp, tp;
           two_sum2(p0v[i], qn, sp, tp);
           __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m,

@@ -195,6 +195,20 @@ def test_mixed_lowk_radius_zero_still_converges():
     check(d, "mixed", lowk_radius2=0)
 
 
+@pytest.mark.parametrize("x_kernel", [0, 1])
+def test_mixed_three_sweeps(x_kernel):
+    """A tolerance no estimate can meet runs all three sweeps: the later sweeps rebuild the
+    correction from the stored double iterate, and every sweep keeps (or improves) accuracy."""
+    d = wl.anelastic_noise(128, 96, 32, seed=18)
+    p, info, _ = gpu_solve(d, "mixed", tolerance=1e-30, x_kernel=x_kernel)
+    assert info["sweeps"] == 3 and not info["converged"], info
+    ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
+    assert O.relative_l2(p, ref) <= 1e-11
+    # relative updates shrink sweep after sweep
+    ru = info["rel_update"]
+    assert ru[2] < ru[1] and ru[3] < ru[2] * 10, info
+
+
 # ---------------------------------------------------------------------------
 # batched solve (uneven sizes, one graph launch)
 # ---------------------------------------------------------------------------
