@@ -348,6 +348,17 @@ def main():
     for i in range(2):
         pipe.submit(Sh[i], ph[i])
     pipe.wait()
+    # the host link the pipeline is bound by: one H2D and one D2H of a step's bytes, concurrently
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t_link = time.perf_counter()
+    for _ in range(3):
+        with torch.cuda.stream(s_in):
+            S.copy_(Sh[0], non_blocking=True)
+        with torch.cuda.stream(s_out):
+            ph[1].copy_(p, non_blocking=True)
+    torch.cuda.synchronize()
+    link_gbs = 3 * 2 * S.numel() * 8 / (time.perf_counter() - t_link) / 1e9
     torch.cuda.synchronize()
     barrier()
     t_e2e = time.perf_counter()
@@ -360,7 +371,7 @@ def main():
     pipe.close()
     e2e = {"value": world * d.npoints / (ms_e2e * 1e-3) / 1e6, "unit": "Mpoints/s",
            "h2d_bytes_per_step": int(S.numel() * 8), "d2h_bytes_per_step": int(p.numel() * 8),
-           "ms_per_step": ms_e2e, "steps": K2,
+           "ms_per_step": ms_e2e, "steps": K2, "host_link_gbs_both_directions": link_gbs,
            "how": "poisson_pipe: H2D of step i+1 and D2H of step i-1 overlap the solve of step i; host wall clock"}
 
     # ---- plain FP64 GPU solve of the same grid (the comparison the metric names)
