@@ -156,9 +156,6 @@ struct ThomasArgs {
 };
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
 
-cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
-                               const Tables& tb, float2 cx, float2 cy, const float2* mu_ff, const int* done,
-                               cudaStream_t st);
 // q = p - p0 (float) from the stored double iterate, before a second or third sweep (skipped when done).
 cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long long n, const int* done,
                              cudaStream_t st);

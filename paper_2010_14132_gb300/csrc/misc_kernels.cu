@@ -41,32 +41,6 @@ cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, do
 }
 
 // ---------------------------------------------------------------------------
-// Residual r = S - mu_W - L (p0 + q) (mixed path), one thread per point; see residual.cuh.
-// ---------------------------------------------------------------------------
-template <bool HAS_Q>
-__global__ void __launch_bounds__(256) k_residual_ff(ResidualArgs R, float* __restrict__ r, Geom g,
-                                                     const int* __restrict__ done) {
-  if (done && *done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y, k = blockIdx.z;
-  if (i >= g.nx) return;
-  r[((long long)k * g.ny + j) * g.nx + i] = residual_point<HAS_Q>(R, g, i, j, k);
-}
-
-cudaError_t launch_residual_ff(const double* S, const float* p0, const float* q, float* r, const Geom& g,
-                               const Tables& tb, float2 cx, float2 cy, const float2* mu_ff, const int* done,
-                               cudaStream_t st) {
-  const dim3 block(256);
-  const dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
-  const ResidualArgs R{S, p0, q, tb.a_ff, tb.c_ff, cx, cy, mu_ff};
-  if (q)
-    k_residual_ff<true><<<grid, block, 0, st>>>(R, r, g, done);
-  else
-    k_residual_ff<false><<<grid, block, 0, st>>>(R, r, g, done);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Refinement control: sums the x-pass partials in a fixed order,
 // records ||delta_n||/||p|| and the error estimate, and sets the done flag.
 // Stopping rule: after sweep n >= 1 the remaining error is estimated as
