@@ -1,6 +1,5 @@
-// Residual, refinement control, coefficient tables and rho0-gradient reductions.
+// Refinement control, correction rebuild, coefficient tables and rho0-gradient reductions.
 #include "kernels.cuh"
-#include "residual.cuh"
 #include "residual2.cuh"
 
 namespace pgb {
