@@ -15,10 +15,15 @@
  *             + a_k (p_{k-1}-p_k) + c_k (p_{k+1}-p_k)
  *   W_k = rho0_k dz_k, a_k = rho_{k-1/2}/(W_k h_{k-1/2}), c_k = rho_{k+1/2}/(W_k h_{k+1/2}),
  *   h_{k+1/2} = (dz_k + dz_{k+1})/2, rho_{k+1/2} = (rho0_k + rho0_{k+1})/2,
- *   a_0 = c_{nz-1} = 0 (zero flux through the bottom and top faces),
- *   periodic in x and y.
- * The solve returns the unique p with  L p = S - mu_W  and plain mean zero,
- * mu_W = sum W_k S_ijk / (nx ny sum W_k) (the part of S outside the range of L).
+ *   a_0 = 0 (zero flux through the bottom face), periodic in x and y; at the top
+ *   face either zero flux, c_{nz-1} = 0 (POISSON_BC_PERIODIC_XY_NEUMANN_Z), or
+ *   p = 0 on the face (POISSON_BC_PERIODIC_XY_NEUMANN_BOTTOM_DIRICHLET_TOP):
+ *   c_{nz-1} = rho0_{nz-1}/(W_{nz-1} dz_{nz-1}/2), i.e. the face density taken
+ *   from the top cell and the half-cell distance to the face.
+ * With zero flux at the top the solve returns the unique p with
+ * L p = S - mu_W  and plain mean zero, mu_W = sum W_k S_ijk / (nx ny sum W_k)
+ * (the part of S outside the range of L).  With p = 0 on the top face L is
+ * nonsingular and the solve returns p = L^-1 S (nothing is projected or pinned).
  *
  * Memory conventions (all calls):
  *   - fields are C-contiguous [nz][ny][nx] arrays, x fastest, in DEVICE memory;
@@ -54,7 +59,11 @@ typedef enum {
   POISSON_ERR_TIMEOUT = -6         /* a bounded device-side wait gave up (batched scheduler) */
 } poisson_status;
 
-typedef enum { POISSON_BC_PERIODIC_XY_NEUMANN_Z = 0 } poisson_bc;
+/* Vertical boundary conditions (x and y are always periodic). */
+typedef enum {
+  POISSON_BC_PERIODIC_XY_NEUMANN_Z = 0,                  /* zero flux through the bottom and top faces */
+  POISSON_BC_PERIODIC_XY_NEUMANN_BOTTOM_DIRICHLET_TOP = 1 /* zero flux at the bottom, p = 0 on the top face */
+} poisson_bc;
 
 typedef enum {
   POISSON_FP64 = 0,   /* all arithmetic in double */
@@ -115,7 +124,8 @@ typedef struct {
   double removed_weighted_mean;/* mu_W removed from S (first solve) */
 } poisson_info;
 
-/* Create a plan.  dz and rho0 are HOST arrays of nz doubles (copied).
+/* Create a plan.  dz and rho0 are HOST arrays of nz doubles (copied); bc is a
+ * poisson_bc value (anything else: INVALID_ARG).
  * Supported: nx even, nx >= 4, ny >= 4, each of nx, ny of the form 2^a 3^b and
  * <= 4096, nz in [2, 512]; dx, dy > 0; dz[k] > 0; rho0[k] > 0.
  * Returns POISSON_ERR_UNSUPPORTED for other sizes, INVALID_ARG for bad values.
@@ -191,6 +201,7 @@ const char* poisson_last_error_detail(void);
 
 /* ---- Batched: many independent domains of uneven sizes in one graph launch ----
  * Arrays have n entries; dz[b], rho0[b] are host arrays of nz[b] doubles.
+ * Every domain has zero flux at the bottom and top (POISSON_BC_PERIODIC_XY_NEUMANN_Z).
  * dtype POISSON_FP32 (float fields) or POISSON_MIXED (double fields). */
 int poisson_batch_create(int n, const int* nx, const int* ny, const int* nz, const double* dx,
                          const double* dy, const double* const* dz, const double* const* rho0,

@@ -16,7 +16,7 @@ listed in the design notes:
   * cell-centred finite-volume 7-point operator, periodic in x and y with
     uniform dx, dy; cell thicknesses dz[k]; reference density rho0[k] at cell
     centres, faces by arithmetic mean; homogeneous Neumann (zero flux) at the
-    bottom and top faces;
+    bottom face and, by default, at the top face;
         (L p) = (p[i+1]-2p[i]+p[i-1])/dx^2 + (p[j+1]-2p[j]+p[j-1])/dy^2
                 + a_k (p[k-1]-p[k]) + c_k (p[k+1]-p[k]),
         W_k = rho_k dz_k,  a_k = rho_{k-1/2}/(W_k h_{k-1/2}),
@@ -24,6 +24,11 @@ listed in the design notes:
   * compatibility: the source is projected, Q_W S = S - mu_W with mu_W the
     W-weighted mean of S over all cells;
   * the solution is the unique p with L p = Q_W S and plain mean zero.
+
+With bc="dirichlet_top" the top face instead carries p = 0: its flux is
+rho_top (0 - p_{nz-1}) / (dz_{nz-1}/2) with rho_top = rho0[nz-1] (the paper gives
+densities at centres only), so c_{nz-1} = rho_top / (W_{nz-1} dz_{nz-1}/2).  L is
+then nonsingular and the solution is p = L^{-1} S: no projection, no pinning.
 
 The solve is exact ("provides the exact solution every time", Section 3), so
 the oracle is that definition written out: a naive O(n^2) DFT per line built
@@ -51,12 +56,23 @@ def _f64(x):
 # Operator pieces (Section 2: the elliptic pressure equation, read as above)
 # ---------------------------------------------------------------------------
 
-def vertical_coefficients(dz, rho0):
+BCS = ("neumann", "dirichlet_top")
+
+
+def _check_bc(bc):
+    if bc not in BCS:
+        raise ValueError(f"bc must be one of {BCS}")
+
+
+def vertical_coefficients(dz, rho0, bc="neumann"):
     """Return (W, a, c) of the density-weighted vertical operator.
 
-    W_k = rho_k dz_k; a_k couples level k to k-1 (a_0 = 0), c_k couples k to k+1
-    (c_{nz-1} = 0): zero flux through the bottom and top faces.
+    W_k = rho_k dz_k; a_k couples level k to k-1 (a_0 = 0: zero flux through the
+    bottom face), c_k couples k to k+1.  Top face: c_{nz-1} = 0 for zero flux
+    ("neumann"); for p = 0 on the face ("dirichlet_top") c_{nz-1} couples the top
+    cell to the face value 0 over half a cell, with the top cell's density.
     """
+    _check_bc(bc)
     dz = _f64(dz)
     rho0 = _f64(rho0)
     nz = dz.size
@@ -68,6 +84,8 @@ def vertical_coefficients(dz, rho0):
     c = np.zeros(nz)
     c[:-1] = conductance / W[:-1]
     a[1:] = conductance / W[1:]
+    if bc == "dirichlet_top":
+        c[-1] = rho0[-1] / (0.5 * dz[-1]) / W[-1]
     return W, a, c
 
 
@@ -98,20 +116,29 @@ def project_compatible(S, W):
 
 
 def apply_L(p, dx, dy, a, c):
-    """Matrix-free 7-point operator L p (periodic x/y, zero-flux z)."""
+    """Matrix-free 7-point operator L p (periodic x/y).
+
+    Bottom: no term below level 0 (a_0 = 0).  Top: c_{nz-1} (0 - p_{nz-1}), the
+    coupling to the face value 0; it vanishes with zero flux (c_{nz-1} = 0).
+    """
     p = _f64(p)
     Lx = (np.roll(p, -1, axis=2) - 2.0 * p + np.roll(p, 1, axis=2)) / (dx * dx)
     Ly = (np.roll(p, -1, axis=1) - 2.0 * p + np.roll(p, 1, axis=1)) / (dy * dy)
     Lz = np.zeros_like(p)
     Lz[1:] += a[1:, None, None] * (p[:-1] - p[1:])
     Lz[:-1] += c[:-1, None, None] * (p[1:] - p[:-1])
+    Lz[-1] += c[-1] * (0.0 - p[-1])
     return Lx + Ly + Lz
 
 
-def residual(S, p, dx, dy, dz, rho0):
-    """r = Q_W S - L p (the quantity the relative-residual measure of Section 2.2 uses)."""
-    W, a, c = vertical_coefficients(dz, rho0)
-    return project_compatible(S, W) - apply_L(p, dx, dy, a, c)
+def residual(S, p, dx, dy, dz, rho0, bc="neumann"):
+    """r = Q_W S - L p (the quantity the relative-residual measure of Section 2.2 uses).
+
+    With p = 0 on the top face nothing is projected: r = S - L p.
+    """
+    W, a, c = vertical_coefficients(dz, rho0, bc)
+    rhs = project_compatible(S, W) if bc == "neumann" else _f64(S)
+    return rhs - apply_L(p, dx, dy, a, c)
 
 
 # ---------------------------------------------------------------------------
@@ -229,41 +256,45 @@ def singular_column_solve(a, c, rhs, transpose=False):
     return np.linalg.solve(B, r)[:nz]
 
 
-def _spectral_diag(a, c, dx, dy, nx, ny):
+def _spectral_diag(a, c, dx, dy, nx, ny, singular00=True):
     lx = horizontal_eigenvalues(nx, dx, nx // 2 + 1)     # (nxh,)
     ly = horizontal_eigenvalues(ny, dy, ny)              # (ny,)
     lam = ly[:, None] + lx[None, :]                      # (ny, nxh)
     diag = -(a + c)[:, None, None] + lam[None, :, :]
-    # the (0,0) column is singular; it is solved separately, so give the
-    # textbook recurrence a diagonally dominant stand-in there and discard it
-    diag[:, 0, 0] = -(a + c) - 1.0
+    if singular00:
+        # the (0,0) column is singular; it is solved separately, so give the
+        # textbook recurrence a diagonally dominant stand-in there and discard it
+        diag[:, 0, 0] = -(a + c) - 1.0
     return diag
 
 
-def solve(S, dx, dy, dz, rho0, return_info=False):
+def solve(S, dx, dy, dz, rho0, return_info=False, bc="neumann"):
     """p = the zero-mean solution of L p = Q_W S (Section 2.1 structure).
 
     Forward DFT in x then y at every level, textbook Thomas per (kx, ky)
     column with T = L_z + (lambda_x + lambda_y) I, bordered solve for the
-    (0,0) column, inverse DFT in y then x.
+    (0,0) column, inverse DFT in y then x.  With bc="dirichlet_top" every
+    column, (0,0) included, is nonsingular: p = L^{-1} S by Thomas throughout.
     """
     S = _f64(S)
     nz, ny, nx = S.shape
-    W, a, c = vertical_coefficients(dz, rho0)
-    mu_W = weighted_mean(S, W)
+    W, a, c = vertical_coefficients(dz, rho0, bc)
+    neumann = bc == "neumann"
+    mu_W = weighted_mean(S, W) if neumann else 0.0
     Shat = dft_y(dft_x(S - mu_W))                          # (nz, ny, nxh)
-    diag = _spectral_diag(a, c, dx, dy, nx, ny)
+    diag = _spectral_diag(a, c, dx, dy, nx, ny, singular00=neumann)
     sub = a[:, None, None]
     sup = c[:, None, None]
     phat = thomas(sub, diag, sup, Shat)
-    phat[:, 0, 0] = singular_column_solve(a, c, Shat[:, 0, 0])
+    if neumann:
+        phat[:, 0, 0] = singular_column_solve(a, c, Shat[:, 0, 0])
     p = idft_x(idft_y(phat), nx)
     if return_info:
         return p, {"removed_weighted_mean": mu_W}
     return p
 
 
-def adjoint(wgt, dx, dy, dz, rho0):
+def adjoint(wgt, dx, dy, dz, rho0, bc="neumann"):
     """g = G^T wgt where G: S -> p is the map computed by solve().
 
     G = P_1 L^+ Q_W with P_1 the plain-mean projection.  The 2-D DFT matrix is
@@ -272,49 +303,57 @@ def adjoint(wgt, dx, dy, dz, rho0):
     inverse DFT.  In the (0,0) column P_1 removes the plain mean of the
     transformed weights, the transposed singular column (null vector W) is
     solved by the bordered system, and Q_W^T v = v - W (sum v)/(nx ny sum W)
-    removes the W direction.
+    removes the W direction.  With bc="dirichlet_top" G = L^{-1} and
+    G^T = F^{-1} T_k^{-T} F in every column.
     """
     wgt = _f64(wgt)
     nz, ny, nx = wgt.shape
-    W, a, c = vertical_coefficients(dz, rho0)
+    W, a, c = vertical_coefficients(dz, rho0, bc)
+    neumann = bc == "neumann"
     What = dft_y(dft_x(wgt))
-    What[:, 0, 0] -= What[:, 0, 0].mean()                  # P_1
-    diag = _spectral_diag(a, c, dx, dy, nx, ny)
+    if neumann:
+        What[:, 0, 0] -= What[:, 0, 0].mean()              # P_1
+    diag = _spectral_diag(a, c, dx, dy, nx, ny, singular00=neumann)
     # T^T: row k has T[k-1,k] = c_{k-1} below the diagonal and T[k+1,k] = a_{k+1} above
     sub_t = np.zeros(nz)
     sup_t = np.zeros(nz)
     sub_t[1:] = c[:-1]
     sup_t[:-1] = a[1:]
     mhat = thomas(sub_t[:, None, None], diag, sup_t[:, None, None], What)
-    mhat[:, 0, 0] = singular_column_solve(a, c, What[:, 0, 0], transpose=True)
+    if neumann:
+        mhat[:, 0, 0] = singular_column_solve(a, c, What[:, 0, 0], transpose=True)
     m = idft_x(idft_y(mhat), nx)
-    m -= W[:, None, None] * (m.sum() / (nx * ny * W.sum()))  # Q_W^T
+    if neumann:
+        m -= W[:, None, None] * (m.sum() / (nx * ny * W.sum()))  # Q_W^T
     return m
 
 
-def rho0_gradient(wgt, S, dx, dy, dz, rho0, p=None, g=None):
+def rho0_gradient(wgt, S, dx, dy, dz, rho0, p=None, g=None, bc="neumann"):
     """d(sum wgt*p)/d rho0_m for p = solve(S; rho0).
 
     Differentiating L p = Q_W S with 1^T p = 0 gives
         dl/drho_m = g^T (dQ_W/drho_m S - dL/drho_m p),  g = G^T wgt.
     dL/drho_m only touches the vertical coefficients a_k, c_k of rows m-1, m,
-    m+1 (through W_m and the face densities at m-1/2, m+1/2).
+    m+1 (through W_m and the face densities at m-1/2, m+1/2).  With p = 0 on the
+    top face there is no projection (Q_W = I) and c_{nz-1} = rho_{nz-1} /
+    (W_{nz-1} dz_{nz-1}/2) also depends on rho_{nz-1}.
     """
     dz = _f64(dz)
     rho0 = _f64(rho0)
     S = _f64(S)
     nz, ny, nx = S.shape
-    W, a, c = vertical_coefficients(dz, rho0)
+    W, a, c = vertical_coefficients(dz, rho0, bc)
     if p is None:
-        p = solve(S, dx, dy, dz, rho0)
+        p = solve(S, dx, dy, dz, rho0, bc=bc)
     if g is None:
-        g = adjoint(wgt, dx, dy, dz, rho0)
+        g = adjoint(wgt, dx, dy, dz, rho0, bc=bc)
     h = 0.5 * (dz[:-1] + dz[1:])
     # per-level contractions  Ma_k = sum_ij g_k (p_{k-1}-p_k),  Mc_k = sum_ij g_k (p_{k+1}-p_k)
     Ma = np.zeros(nz)
     Mc = np.zeros(nz)
     Ma[1:] = np.einsum("kji,kji->k", g[1:], p[:-1] - p[1:])
     Mc[:-1] = np.einsum("kji,kji->k", g[:-1], p[1:] - p[:-1])
+    Mc[-1] = np.einsum("ji,ji->", g[-1], 0.0 - p[-1])      # coupling to the top face value 0
     level_S = S.reshape(nz, -1).sum(axis=1)
     level_g = g.reshape(nz, -1).sum(axis=1)
     sumW = W.sum()
@@ -331,10 +370,15 @@ def rho0_gradient(wgt, S, dx, dy, dz, rho0, p=None, g=None):
             if k < nz - 1:   # c_k = rho_face[k] / (W_k h[k])
                 dnum = 0.5 if m in (k, k + 1) else 0.0
                 dc[k] = dnum / (W[k] * h[k]) - c[k] * dW / W[k]
+            elif bc == "dirichlet_top":   # c_{nz-1} = rho_{nz-1} / (W_{nz-1} dz_{nz-1}/2)
+                dnum = 1.0 if m == k else 0.0
+                dc[k] = dnum / (W[k] * 0.5 * dz[k]) - c[k] * dW / W[k]
         dL_term = np.dot(da, Ma) + np.dot(dc, Mc)
-        # Q_W S = S - mu_W 1:  d/drho_m (-mu_W) contracted with g
-        dmu = dz[m] * (level_S[m] - nx * ny * mu_W) / (nx * ny * sumW)
-        dQ_term = -dmu * level_g.sum()
+        dQ_term = 0.0
+        if bc == "neumann":
+            # Q_W S = S - mu_W 1:  d/drho_m (-mu_W) contracted with g
+            dmu = dz[m] * (level_S[m] - nx * ny * mu_W) / (nx * ny * sumW)
+            dQ_term = -dmu * level_g.sum()
         grad[m] = dQ_term - dL_term
     return grad
 

@@ -20,6 +20,7 @@ POISSON_ERR_NOT_CONVERGED = -5
 POISSON_ERR_TIMEOUT = -6
 
 POISSON_BC_PERIODIC_XY_NEUMANN_Z = 0
+POISSON_BC_PERIODIC_XY_NEUMANN_BOTTOM_DIRICHLET_TOP = 1
 POISSON_FP64, POISSON_FP32, POISSON_MIXED = 0, 1, 2
 POISSON_OPT_LOWK_RADIUS2, POISSON_OPT_MAX_SWEEPS, POISSON_OPT_TOLERANCE, POISSON_OPT_Y_TILE = 0, 1, 2, 3
 POISSON_OPT_PROFILE = 4

@@ -74,6 +74,7 @@ struct poisson_plan {
   int nx = 0, ny = 0, nz = 0, nxh = 0, P = 0;
   double dx = 0, dy = 0;
   int dtype = 0;
+  int bc = POISSON_BC_PERIODIC_XY_NEUMANN_Z;
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
   int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
@@ -95,6 +96,7 @@ struct poisson_plan {
   PhaseProfiler prof;
   bool mixed() const { return dtype == POISSON_MIXED; }
   bool fp64() const { return dtype == POISSON_FP64; }
+  int top_dirichlet() const { return bc == POISSON_BC_PERIODIC_XY_NEUMANN_BOTTOM_DIRICHLET_TOP ? 1 : 0; }
   size_t elem() const { return dtype == POISSON_FP32 ? 4 : 8; }
   size_t csize() const { return dtype == POISSON_FP64 ? 16 : 8; }
 };
@@ -233,7 +235,8 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
   if (!out) return POISSON_ERR_INVALID_ARG;
   *out = nullptr;
   if (!dz || !rho0) return POISSON_ERR_INVALID_ARG;
-  if (bc != POISSON_BC_PERIODIC_XY_NEUMANN_Z) return POISSON_ERR_INVALID_ARG;
+  if (bc != POISSON_BC_PERIODIC_XY_NEUMANN_Z && bc != POISSON_BC_PERIODIC_XY_NEUMANN_BOTTOM_DIRICHLET_TOP)
+    return POISSON_ERR_INVALID_ARG;
   if (dtype != POISSON_FP64 && dtype != POISSON_FP32 && dtype != POISSON_MIXED) return POISSON_ERR_INVALID_ARG;
   if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy)) return POISSON_ERR_INVALID_ARG;
   for (int k = 0; k < nz; ++k)
@@ -251,6 +254,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
   pl->dx = dx;
   pl->dy = dy;
   pl->dtype = dtype;
+  pl->bc = bc;
   pl->nxh = nx / 2 + 1;
   const int pad = dtype == POISSON_FP64 ? 8 : 16;  // 128-byte rows
   pl->P = (pl->nxh + pad - 1) / pad * pad;
@@ -355,7 +359,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
   pl->rho_d = (double*)(base + o_rho);
   if (ce == cudaSuccess)
     ce = launch_coefficients(pl->dz_d, pl->rho_d, nz, (double*)tb.a_d, (double*)tb.c_d, (double*)tb.W_d,
-                             (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff, 0);
+                             (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff, pl->top_dirichlet(), 0);
   if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
   if (ce != cudaSuccess) {
     int rc = cuda_fail(ce, "plan tables");
@@ -480,7 +484,8 @@ int poisson_plan_set_rho0(poisson_plan* pl, const double* rho0_dev, void* stream
   PGB_CUDA(cudaMemcpyAsync(pl->rho_d, rho0_dev, sizeof(double) * pl->nz, cudaMemcpyDeviceToDevice, st));
   const Tables& tb = pl->tb;
   PGB_CUDA(launch_coefficients(pl->dz_d, pl->rho_d, pl->nz, (double*)tb.a_d, (double*)tb.c_d, (double*)tb.W_d,
-                               (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff, st));
+                               (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff,
+                               pl->top_dirichlet(), st));
   return POISSON_OK;
 }
 
@@ -556,6 +561,7 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
   A.lowk_r2 = pl->mixed() ? pl->lowk_r2 : 0;
   A.lowk_double = pl->mixed() || t_double;
   A.lowk_cols = pl->lowk_d;
+  A.singular00 = !pl->top_dirichlet();
   A.n_lowk = pl->n_lowk;
   A.lowk_z = (double2*)(ws + pl->off_lz);
   A.lowk_w = (double*)(ws + pl->off_lw);

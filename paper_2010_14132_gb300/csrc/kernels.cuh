@@ -153,6 +153,7 @@ struct ThomasArgs {
   const int* done;
   const double* target_mean;  // nullable: the (0,0) column then gives the solution mean -(*target_mean)
   int col_tile;               // requested columns per CTA (0 = default)
+  int singular00;             // 1: zero flux at the top, so the (0,0) column is singular (projected, pinned)
 };
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
 
@@ -162,7 +163,8 @@ cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long lo
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
                            double tol, long long npoints, cudaStream_t st);
 cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
-                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff, cudaStream_t st);
+                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff, int top_dirichlet,
+                                cudaStream_t st);
 cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math*/, const void* g, const void* p, const Geom& g_, const Tables& tb,
                         const double* dz, const double* rho0, double* partials, int nparts_max,
                         double* grho, cudaStream_t st);

@@ -7,7 +7,10 @@ namespace pgb {
 // ---------------------------------------------------------------------------
 // Vertical coefficient tables (one thread per level, FP64; nz values only).
 //   W_k = rho_k dz_k, a_k = rho_{k-1/2}/(W_k h_{k-1/2}), c_k = rho_{k+1/2}/(W_k h_{k+1/2}),
-//   h_{k+1/2} = (dz_k + dz_{k+1})/2, rho_{k+1/2} = (rho_k + rho_{k+1})/2; a_0 = c_{nz-1} = 0.
+//   h_{k+1/2} = (dz_k + dz_{k+1})/2, rho_{k+1/2} = (rho_k + rho_{k+1})/2; a_0 = 0 (zero flux
+//   through the bottom face).  Top face: zero flux gives c_{nz-1} = 0; p = 0 on it (Dirichlet)
+//   gives the flux rho_top (0 - p_{nz-1})/(dz_{nz-1}/2), so c_{nz-1} = rho_top/(W h) with
+//   h = dz_{nz-1}/2 and rho_top = rho_{nz-1} (only centre densities are given).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 split_ff(double x) {
   const float h = __double2float_rn(x);
@@ -17,10 +20,12 @@ __device__ __forceinline__ float2 split_ff(double x) {
 
 __global__ void k_coefficients(const double* __restrict__ dz, const double* __restrict__ rho, int nz,
                                double* a_d, double* c_d, double* W_d, float* a_f, float* c_f, float2* a_ff,
-                               float2* c_ff) {
+                               float2* c_ff, int top_dirichlet) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nz; k += blockDim.x * gridDim.x) {
     const double W = rho[k] * dz[k];
-    const double up = (k + 1 < nz) ? (0.5 * (rho[k] + rho[k + 1])) / (0.5 * (dz[k] + dz[k + 1])) : 0.0;
+    const double up = (k + 1 < nz)      ? (0.5 * (rho[k] + rho[k + 1])) / (0.5 * (dz[k] + dz[k + 1]))
+                      : top_dirichlet ? rho[k] / (0.5 * dz[k])
+                                      : 0.0;
     const double dn = (k > 0) ? (0.5 * (rho[k - 1] + rho[k])) / (0.5 * (dz[k - 1] + dz[k])) : 0.0;
     const double a = dn / W, c = up / W;
     a_d[k] = a;
@@ -34,8 +39,9 @@ __global__ void k_coefficients(const double* __restrict__ dz, const double* __re
 }
 
 cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
-                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff, cudaStream_t st) {
-  k_coefficients<<<(nz + 127) / 128, 128, 0, st>>>(dz, rho0, nz, a_d, c_d, W_d, a_f, c_f, a_ff, c_ff);
+                                double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff, int top_dirichlet,
+                                cudaStream_t st) {
+  k_coefficients<<<(nz + 127) / 128, 128, 0, st>>>(dz, rho0, nz, a_d, c_d, W_d, a_f, c_f, a_ff, c_ff, top_dirichlet);
   return cudaGetLastError();
 }
 

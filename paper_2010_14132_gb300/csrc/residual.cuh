@@ -30,7 +30,8 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
 // Residual at one point from its 7-point stencil values of p0 and q (the q
 // values enter in plain FP32), the double source S, the vertical coefficient
 // splits A = a_k, Cc = c_k, the horizontal ones cx, cy and mu = mu_W.
-// At the bottom (top) level pass pd = pc (pu = pc): a (c) is zero there anyway.
+// At the bottom level pass pd = pc (a_0 = 0); at the top level pass pu = 0: the
+// Dirichlet ghost value, and with zero flux c_{nz-1} = 0 makes the term vanish.
 __device__ __forceinline__ float residual_value(float pc, float pe, float pw, float pn, float ps, float pd, float pu,
                                                 float qc, float qe, float qw, float qn, float qs, float qd, float qu,
                                                 double S, float2 A, float2 Cc, float2 cx, float2 cy, float2 mu) {
@@ -49,7 +50,7 @@ __device__ __forceinline__ float residual_value(float pc, float pe, float pw, fl
   FF ty;
   two_prod(cy.x, s2, ty.h, ty.l);
   ty.l = __fmaf_rn(cy.x, dl, __fmaf_rn(cy.y, s2, ty.l));
-  // z: a (pd - pc) + c (pu - pc)   (a = 0 at the bottom, c = 0 at the top).
+  // z: a (pd - pc) + c (pu - pc)   (a = 0 at the bottom).
   // Differences first: a constant field maps to exactly zero whatever the
   // rounding of the coefficient splits.  Summing a pd + c pu - (a+c) pc instead
   // leaves a row-sum mismatch of ~2^-48 (a+c) that the near-null vertical mode of
@@ -87,7 +88,7 @@ __device__ __forceinline__ float residual_point(const ResidualArgs& R, const Geo
   const float pe = p0[row + ie], pw = p0[row + iw], pn = p0[rn + i], ps = p0[rs + i];
   const bool has_dn = k > 0, has_up = k + 1 < nz;
   const float pd = has_dn ? p0[idx - pl] : pc;
-  const float pu = has_up ? p0[idx + pl] : pc;
+  const float pu = has_up ? p0[idx + pl] : 0.f;
   float qc = 0, qe = 0, qw = 0, qn = 0, qs = 0, qd = 0, qu = 0;
   if (HAS_Q) {
     const float* q = R.q;
@@ -97,7 +98,7 @@ __device__ __forceinline__ float residual_point(const ResidualArgs& R, const Geo
     qn = q[rn + i];
     qs = q[rs + i];
     qd = has_dn ? q[idx - pl] : qc;
-    qu = has_up ? q[idx + pl] : qc;
+    qu = has_up ? q[idx + pl] : 0.f;
   }
   // S is read once per sweep: stream past L2
   return residual_value(pc, pe, pw, pn, ps, pd, pu, qc, qe, qw, qn, qs, qd, qu, __ldcs(&R.S[idx]), R.a_ff[k],

@@ -68,7 +68,7 @@ __device__ __forceinline__ ResCoef res_coef(float2 cx, float2 cy, float2 A, floa
 
 // r at the two points.  pc, pe, pw, pn, ps, pd, pu: p0 at the points and at their
 // east, west, north, south, lower and upper neighbours (pd = pc at the bottom,
-// pu = pc at the top level); likewise for q when HAS_Q.  Sh, Sl: the split of S.
+// pu = 0 above the top level); likewise for q when HAS_Q.  Sh, Sl: the split of S.
 template <bool HAS_Q>
 __device__ __forceinline__ float2 residual_value2(float2 pc, float2 pe, float2 pw, float2 pn, float2 ps, float2 pd,
                                                   float2 pu, float2 qc, float2 qe, float2 qw, float2 qn, float2 qs,

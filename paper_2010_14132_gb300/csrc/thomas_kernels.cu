@@ -8,7 +8,9 @@
 //     g_0 = s,  u_k = g_k + c_k,  g_k = s + a_k g_{k-1} / u_{k-1},
 // (g_k is the row sum of the reduced row k), so every pivot is relatively
 // accurate however close s is to 0.  For s = 0 (the (0,0) column) g vanishes
-// identically and the last pivot is exactly 0, the singular mode.
+// identically; with zero flux through the top face the last pivot is then
+// exactly 0, the singular mode.  With p = 0 on the top face (Dirichlet) the top
+// coupling c_{nz-1} > 0 enters the last pivot and every column is nonsingular.
 //   forward solve   M x = b:  y_k = b_k + (a_k/u_{k-1}) y_{k-1};  x_k = y_k/u_k + (c_k/u_k) x_{k+1}
 //   adjoint solve M^T x = b:  v_k = (b_k + c_{k-1} v_{k-1})/u_k;   x_k = v_k + (a_{k+1}/u_k) x_{k+1}
 // The spectrum is scaled by 1/(nx ny) here, which makes the inverse transforms
@@ -46,6 +48,7 @@ struct LowkArgs {
   const double* lamy_d;
   const double* target_mean;
   double scale;   // 1/(nx ny) in double for the double-precision columns
+  int singular00; // zero flux at the top: the (0,0) column is singular
 };
 
 template <typename TS, typename TCm, bool ADJ>
@@ -54,7 +57,7 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
                                             const double* __restrict__ cg, const double* __restrict__ Wg,
                                             const double* __restrict__ lamx, const double* __restrict__ lamy,
                                             double scale, int2 colk, Stats* stats,
-                                            const double* __restrict__ target_mean);
+                                            const double* __restrict__ target_mean, bool singular00);
 
 // Blocks [0, L.n) solve the listed low-|k| / singular columns (precision TCm);
 // the others solve tiles of TC consecutive columns.  The two sets of columns are
@@ -71,7 +74,7 @@ __global__ void __launch_bounds__(128) k_thomas(typename CT<T>::t* __restrict__ 
   extern __shared__ __align__(128) unsigned char smraw[];
   if ((int)blockIdx.x < L.n) {
     lowk_column<T, TCm, ADJ>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale,
-                             L.cols[blockIdx.x], stats, L.target_mean);
+                             L.cols[blockIdx.x], stats, L.target_mean, L.singular00 != 0);
     return;
   }
   const int TC = blockDim.x, t = threadIdx.x, nz = g.nz;
@@ -172,7 +175,8 @@ __global__ void __launch_bounds__(128) k_thomas(typename CT<T>::t* __restrict__ 
 
 // ---------------------------------------------------------------------------
 // Low-|k| and singular columns: one thread per listed column, compute type TCm
-// (double in the mixed path), scratch in global memory.  The (0,0) column:
+// (double in the mixed path), scratch in global memory.  The (0,0) column, when
+// zero flux at the top makes it singular:
 //   forward: remove the W-weighted mean of the right-hand side (compatibility),
 //            pin x_{nz-1} = 0, back-substitute, shift to zero mean;
 //   adjoint: remove the plain mean of the right-hand side, pin v_{nz-1} = 0,
@@ -187,7 +191,7 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
                                             const double* __restrict__ cg, const double* __restrict__ Wg,
                                             const double* __restrict__ lamx, const double* __restrict__ lamy,
                                             double scale, int2 colk, Stats* stats,
-                                            const double* __restrict__ target_mean) {
+                                            const double* __restrict__ target_mean, bool singular00) {
   using CS = typename CT<TS>::t;
   const int nz = g.nz;
   TCm* zx = reinterpret_cast<TCm*>(smraw);   // right-hand side, then z, then x (real parts)
@@ -198,7 +202,7 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
   TCm* W = c + nz;
   TCm* red = W + nz;                          // shift_x, shift_y, sumw, sum_x, sum_y
   const int kx = colk.x, ky = colk.y;
-  const bool singular = (kx == 0 && ky == 0);
+  const bool singular = singular00 && kx == 0 && ky == 0;   // nonsingular with p = 0 on the top face
   CS* colp = spec + (long long)ky * g.P + kx;
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
     const CS v = colp[(long long)k * g.plane];
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(64) k_thomas_pair(float2* __restrict__ spec, G
   extern __shared__ __align__(128) unsigned char smraw[];
   if ((int)blockIdx.x < L.n) {
     lowk_column<float, TCm, ADJ>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale,
-                                 L.cols[blockIdx.x], stats, L.target_mean);
+                                 L.cols[blockIdx.x], stats, L.target_mean, L.singular00 != 0);
     return;
   }
   const int TC = blockDim.x, t = threadIdx.x, nz = g.nz;
@@ -425,9 +429,11 @@ __global__ void __launch_bounds__(64) k_thomas_pair(float2* __restrict__ spec, G
 // Twisted FP32 column kernel (forward solves): two threads per column.  The
 // lower thread eliminates levels 0..m-1 upward with the pivots above
 // (g_k, u_k = g_k + c_k), the upper thread eliminates levels nz-1..m+1 downward
-// with the mirror recurrence h_{nz-1} = s, h_k = s + c_k h_{k+1}/v_{k+1},
+// with the mirror recurrence h_{nz-1} = s + c_{nz-1} (the top row's sum: c_{nz-1} = 0
+// with zero flux, the Dirichlet coupling otherwise), h_k = s + c_k h_{k+1}/v_{k+1},
 // v_k = h_k + a_k (again subtraction-free); they meet at level m = nz/2:
 //   x_m = (b_m + a_m z_{m-1} + c_m zt_{m+1}) / (s + a_m g_{m-1}/u_{m-1} + c_m h_{m+1}/v_{m+1}),
+// (h_{nz}/v_{nz} = 1 and zt_{nz} = 0 when m is the top level),
 // then substitute back outward: x_k = z_k + (c_k/u_k) x_{k+1} below m,
 // x_k = zt_k + (a_k/v_k) x_{k-1} above m.  Half the sequential chain of the
 // one-thread recurrence and twice the threads for the same shared memory.
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Ge
   extern __shared__ __align__(128) unsigned char smraw[];
   if ((int)blockIdx.x < L.n) {
     lowk_column<float, TCm, false>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale,
-                                   L.cols[blockIdx.x], stats, L.target_mean);
+                                   L.cols[blockIdx.x], stats, L.target_mean, L.singular00 != 0);
     return;
   }
   const int TC = blockDim.x / 2, t = threadIdx.x, col_t = t % TC, upper = t / TC, nz = g.nz;
@@ -511,7 +517,7 @@ __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Ge
       const float2 akc = ac[k];
       const float2 d = colp[(size_t)k * TC];
       const float f = (k == nz - 1) ? 0.f : akc.y * inv_prev;   // c_k / v_{k+1}
-      const float hk = (k == nz - 1) ? s : s + f * h_prev;
+      const float hk = (k == nz - 1) ? s + akc.y : s + f * h_prev;
       const float inv = rcp(hk + akc.x);
       y = make_float2(fmaf(ms, d.x, f * y.x), fmaf(ms, d.y, f * y.y));
       colp[(size_t)k * TC] = make_float2(y.x * inv, y.y * inv);
@@ -519,7 +525,7 @@ __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Ge
       h_prev = hk;
       inv_prev = inv;
     }
-    xm_s[col_t] = (m + 1 < nz) ? make_float2(h_prev * inv_prev, 0.f) : make_float2(0.f, 0.f);   // h_{m+1}/v_{m+1}
+    xm_s[col_t] = make_float2((m + 1 < nz) ? h_prev * inv_prev : 1.f, 0.f);   // h_{m+1}/v_{m+1}
   }
   __syncthreads();
   if (upper == 0) {
@@ -611,7 +617,8 @@ static cudaError_t thomas_pair_launch(const ThomasArgs& A, const Geom& g, const 
   const int kx_chunks = (g.nxh + tc - 1) / tc;
   const int npairs = g.ny / 2 + 1;
   const long long nb = (long long)npairs * kx_chunks;
-  const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale};
+  const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale,
+                   A.singular00};
   kern<<<(unsigned)(nb + A.n_lowk), tc, smem, st>>>((float2*)A.spec, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f,
                                                     (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows,
                                                     kx_chunks, L);
@@ -644,7 +651,8 @@ static cudaError_t thomas_tw_launch(const ThomasArgs& A, const Geom& g, const Ta
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long nb = (g.plane + tc - 1) / tc;
-  const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale};
+  const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale,
+                   A.singular00};
   kern<<<(unsigned)(nb + A.n_lowk), 2 * tc, smem, st>>>((float2*)A.spec, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f,
                                                         (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows, L);
   *used = true;
@@ -693,7 +701,8 @@ static cudaError_t thomas_launch(const ThomasArgs& A, const Geom& g, const Table
                                        (unsigned)box_rows)
                           ? 1
                           : 0;
-  const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale};
+  const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale,
+                   A.singular00};
   kern<<<(unsigned)(nb + A.n_lowk), tc, smem, st>>>((C*)A.spec, g, a, c, lx, ly, (T)A.scale, A.lowk_r2, A.done,
                                                    A.stats, tm, use_tma, box_rows, L);
   return cudaGetLastError();

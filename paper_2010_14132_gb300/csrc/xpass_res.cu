@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(xs_threads(E), E >= 24 ? 2 : (E >= 16 ? 4 : 3)
       const float pw = prow[e == 0 ? NX - 1 : 2 * e - 1];
       const float pe = prow[e == N - 1 ? 0 : 2 * e + 2];
       const float2 pn = p0n[e], ps = p0s[e];
-      const float2 pd = has_dn ? p0d[e] : pc, pu = has_up ? p0u[e] : pc;
+      const float2 pd = has_dn ? p0d[e] : pc, pu = has_up ? p0u[e] : make_float2(0.f, 0.f);
       float2 qc = make_float2(0.f, 0.f), qn = qc, qs = qc, qd = qc, qu = qc;
       float qw = 0.f, qe = 0.f;
       if constexpr (HAS_Q) {
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(xs_threads(E), E >= 24 ? 2 : (E >= 16 ? 4 : 3)
         qn = reinterpret_cast<const float2*>(R.q + rn * NX)[e];
         qs = reinterpret_cast<const float2*>(R.q + rs * NX)[e];
         qd = has_dn ? reinterpret_cast<const float2*>(R.q + (rc - g.ny) * NX)[e] : qc;
-        qu = has_up ? reinterpret_cast<const float2*>(R.q + (rc + g.ny) * NX)[e] : qc;
+        qu = has_up ? reinterpret_cast<const float2*>(R.q + (rc + g.ny) * NX)[e] : make_float2(0.f, 0.f);
       }
       const double2 S = Srow[e];
       float2 Sh, Sl;

@@ -13,6 +13,8 @@ import torch
 from . import _native as N
 
 DTYPES = {"fp64": N.POISSON_FP64, "fp32": N.POISSON_FP32, "mixed": N.POISSON_MIXED}
+BCS = {"neumann": N.POISSON_BC_PERIODIC_XY_NEUMANN_Z,
+       "dirichlet_top": N.POISSON_BC_PERIODIC_XY_NEUMANN_BOTTOM_DIRICHLET_TOP}
 FIELD_DTYPE = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float64}
 
 
@@ -36,14 +38,19 @@ class Plan:
     nx, ny: periodic horizontal sizes (2^a 3^b, nx even); nz levels; dx, dy
     spacings; dz, rho0: per-level thickness and reference density (length nz).
     dtype: "fp64", "fp32" or "mixed" (double fields, float transforms, double
-    low-|k| columns and double-float refinement).
+    low-|k| columns and double-float refinement).  bc: "neumann" (zero flux
+    through the bottom and top faces; p is projected and pinned to zero mean) or
+    "dirichlet_top" (zero flux at the bottom, p = 0 on the top face).
     """
 
-    def __init__(self, nx, ny, nz, dx, dy, dz, rho0, dtype="fp64", device=None,
+    def __init__(self, nx, ny, nz, dx, dy, dz, rho0, dtype="fp64", device=None, bc="neumann",
                  lowk_radius2=None, max_sweeps=None, tolerance=None, y_tile=None, y_kernel=None,
                  x_elems=None, y_elems=None, level_chunk=None, x_kernel=None, col_tile=None):
         if dtype not in DTYPES:
             raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
+        if bc not in BCS:
+            raise ValueError(f"bc must be one of {sorted(BCS)}")
+        self.bc = bc
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.dx, self.dy = float(dx), float(dy)
         self.dz = np.asarray(dz, dtype=np.float64).copy()
@@ -55,7 +62,7 @@ class Plan:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             self._h = N.poisson_plan_create(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.rho0,
-                                            N.POISSON_BC_PERIODIC_XY_NEUMANN_Z, DTYPES[dtype])
+                                            BCS[bc], DTYPES[dtype])
         if lowk_radius2 is not None:
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_LOWK_RADIUS2, lowk_radius2)
         if max_sweeps is not None:
@@ -125,7 +132,9 @@ class Plan:
 
     # -- calls ---------------------------------------------------------------
     def solve(self, S: torch.Tensor, out: torch.Tensor | None = None, info: bool = False, stream=None):
-        """p with L p = S - mu_W and zero mean.  Returns p, or (p, info dict) if info."""
+        """p with L p = S - mu_W and zero mean (L p = S with p = 0 on the top face).
+
+        Returns p, or (p, info dict) if info."""
         _require_cuda(S, self.field_dtype, self.shape, "S")
         p = out if out is not None else torch.empty_like(S)
         _require_cuda(p, self.field_dtype, self.shape, "out")

@@ -1,0 +1,121 @@
+"""Accuracy against time per solve: a synthetic analogue of the paper's Table 1.
+
+Section 3 (Table 1) sets the iterative solver's termination residual against the
+mean per-element difference from the direct FFT solution and the time per solve.
+The direct solve has no termination residual, but it has a precision ladder:
+
+    fp32                 FP32 transforms and FP32 columns on float fields
+    mixed, k sweeps      FP32 transforms, FP64 low-|k| columns, then k double-float
+                         residual refinement sweeps (k = 0..3), no early stop
+    mixed, stop rule     the default: sweeps until the update estimate is below
+                         the plan's tolerance
+    fp64                 FP64 throughout (the reference of the comparison)
+
+For each rung this reports the time per solve (CUDA events on the solving
+stream, inputs resident, median over repetitions), the mean |p - p_fp64| per
+element (the paper's "mean difference"), the relative L2 difference, and the
+sweeps and update estimate the library reported.  The FP64 GPU solution is the
+reference here; it matches the FP64 CPU oracle to 1e-12 relative L2 in the
+parity tests.
+
+    python -m paper_2010_14132_gb300.tradeoff [--nx 1024 --ny 1024 --nz 128 --reps 20]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import workloads as wl
+from .solver import Plan
+
+
+def _time_solve(plan, S, p, reps):
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        plan.solve(S, out=p)
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.solve(S, out=p)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times))
+
+
+def rungs():
+    """(label, dtype, plan options) of the precision ladder, cheapest first."""
+    out = [("fp32", "fp32", {})]
+    for k in range(4):
+        # a tolerance no update estimate reaches: exactly k sweeps
+        out.append((f"mixed, {k} sweep{'s' if k != 1 else ''}", "mixed", {"max_sweeps": k, "tolerance": 1e-300}))
+    out.append(("mixed, stop rule", "mixed", {}))
+    out.append(("fp64", "fp64", {}))
+    return out
+
+
+def run(domain, reps=20, device="cuda"):
+    d = domain
+    S64 = torch.from_numpy(d.S).to(device)
+    ref_plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype="fp64", device=device)
+    p64 = ref_plan.solve(S64)
+    torch.cuda.synchronize()
+    rows = []
+    for label, dtype, opts in rungs():
+        plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype=dtype, device=device, **opts)
+        S = S64 if dtype != "fp32" else S64.to(torch.float32)
+        p = torch.empty_like(S)
+        ms = _time_solve(plan, S, p, reps if dtype != "fp64" else max(3, reps // 4))
+        _, info = plan.solve(S, out=p, info=True)
+        torch.cuda.synchronize()
+        diff = p.to(torch.float64) - p64
+        rows.append({
+            "solve": label,
+            "ms_per_solve": ms,
+            "mpoints_s": d.npoints / (ms * 1e-3) / 1e6,
+            "mean_abs_diff": float(diff.abs().mean()),
+            "rel_l2_diff": float(torch.linalg.vector_norm(diff) / torch.linalg.vector_norm(p64)),
+            "sweeps": info["sweeps"] if dtype == "mixed" else None,
+            "error_estimate": info["error_estimate"] if dtype == "mixed" else None,
+        })
+        plan.close()
+    ref_plan.close()
+    return {"workload": d.name, "nx": d.nx, "ny": d.ny, "nz": d.nz,
+            "p_mean_abs": float(p64.abs().mean()), "rows": rows}
+
+
+def markdown(res):
+    lines = [f"Workload {res['workload']} ({res['nx']} x {res['ny']} x {res['nz']}); "
+             f"mean |p| of the FP64 solution = {res['p_mean_abs']:.3e}.", "",
+             "| solve | time per solve (ms) | Mpoints/s | mean difference | rel. L2 difference | sweeps | update estimate |",
+             "|---|---|---|---|---|---|---|"]
+    for r in res["rows"]:
+        sw = "-" if r["sweeps"] is None else str(r["sweeps"])
+        est = "-" if r["error_estimate"] is None else f"{r['error_estimate']:.1e}"
+        diff = "reference" if r["solve"] == "fp64" else f"{r['mean_abs_diff']:.2e}"
+        rel = "reference" if r["solve"] == "fp64" else f"{r['rel_l2_diff']:.2e}"
+        lines.append(f"| {r['solve']} | {r['ms_per_solve']:.3f} | {r['mpoints_s']:.0f} | {diff} | {rel} | {sw} | {est} |")
+    return "\n".join(lines)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=1024)
+    ap.add_argument("--nz", type=int, default=128)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--json", action="store_true", help="print JSON instead of a markdown table")
+    a = ap.parse_args(argv)
+    d = wl.anelastic_noise(a.nx, a.ny, a.nz, seed=a.seed)
+    res = run(d, reps=a.reps)
+    print(json.dumps(res) if a.json else markdown(res))
+
+
+if __name__ == "__main__":
+    main()

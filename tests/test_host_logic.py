@@ -54,7 +54,7 @@ def test_unsupported_sizes(dims):
     assert out is None
 
 
-@pytest.mark.parametrize("kw", [dict(dx=0.0), dict(dy=-1.0), dict(dx=float("nan")), dict(bc=3), dict(dtype=7),
+@pytest.mark.parametrize("kw", [dict(dx=0.0), dict(dy=-1.0), dict(dx=float("nan")), dict(bc=3), dict(bc=2), dict(bc=-1), dict(dtype=7),
                                 dict(dz=np.array([1.0, 0.0, 1.0, 1.0])), dict(rho=np.array([1.0, 1.0, -2.0, 1.0]))])
 def test_invalid_arguments(kw):
     st, out = _create(8, 8, 4, **kw)
@@ -81,3 +81,9 @@ def test_python_wrapper_raises_on_bad_size():
     with pytest.raises(N.PoissonError) as e:
         N.poisson_plan_create(9, 8, 4, 1.0, 1.0, np.ones(4), np.ones(4), 0, 0)
     assert e.value.status == N.POISSON_ERR_UNSUPPORTED
+
+
+def test_plan_rejects_unknown_boundary_condition_before_any_device_call():
+    from paper_2010_14132_gb300.solver import Plan
+    with pytest.raises(ValueError):
+        Plan(8, 8, 4, 1.0, 1.0, np.ones(4), np.ones(4), dtype="fp64", bc="dirichlet")

@@ -15,6 +15,9 @@ wrong sign, a wrong index, a transposed operand) fails at least one of them:
   equivariance);
 * the adjoint by the dot-product test and a dense transpose; the rho0 gradient
   by central finite differences.
+* the p = 0 top-face option likewise: its own eigenfunctions, second-order
+  convergence to the continuous problem, a dense nonsingular solve, the dense
+  transposed solve and central differences of the rho0 gradient.
 """
 import numpy as np
 import pytest
@@ -322,3 +325,146 @@ def test_source_gradient_matches_central_differences():
         lp = (w * O.solve(Sp.reshape(d.S.shape), d.dx, d.dy, d.dz, d.rho0)).sum()
         lm = (w * O.solve(Sm.reshape(d.S.shape), d.dx, d.dy, d.dz, d.rho0)).sum()
         assert abs((lp - lm) / 2e-4 - g.ravel()[q]) < 1e-8 * np.abs(g).max()
+
+
+# ---------------------------------------------------------------------------
+# p = 0 on the top face (bc="dirichlet_top")
+# ---------------------------------------------------------------------------
+
+def _cos_mode_dt(nx, ny, nz, ax, by, cz, phx=0.3, phy=-0.7):
+    """Discrete eigenfunction with zero flux at the bottom and a zero ghost mirror
+    at the top face: cos(pi (2c+1)(k+1/2)/(2 nz)) vanishes midway between the top
+    centre and its mirror image."""
+    i = np.arange(nx)[None, None, :]
+    j = np.arange(ny)[None, :, None]
+    k = np.arange(nz)[:, None, None]
+    return (np.cos(2 * np.pi * ax * i / nx + phx) * np.cos(2 * np.pi * by * j / ny + phy)
+            * np.cos(np.pi * (2 * cz + 1) * (k + 0.5) / (2 * nz)))
+
+
+def _cos_mode_dt_eig(nx, ny, nz, ax, by, cz, dx, dy, dz):
+    return (-4 / dx**2 * np.sin(np.pi * ax / nx) ** 2 - 4 / dy**2 * np.sin(np.pi * by / ny) ** 2
+            - 4 / dz**2 * np.sin(np.pi * (2 * cz + 1) / (4 * nz)) ** 2)
+
+
+def test_dirichlet_top_coefficient_uniform():
+    h = 0.7
+    W, a, c = O.vertical_coefficients(np.full(6, h), np.full(6, 1.3), bc="dirichlet_top")
+    assert a[0] == 0.0
+    assert np.allclose(a[1:], 1 / h**2, rtol=1e-14)
+    assert np.allclose(c[:-1], 1 / h**2, rtol=1e-14)
+    # half a cell from the top centre to the face: twice the interior coupling
+    assert np.isclose(c[-1], 2 / h**2, rtol=1e-14)
+    with pytest.raises(ValueError):
+        O.vertical_coefficients(np.full(6, h), np.full(6, 1.3), bc="dirichlet")
+
+
+@pytest.mark.parametrize("mode", [(0, 0, 0), (1, 0, 0), (0, 0, 4), (3, 2, 5), (8, 6, 9), (4, 3, 0)])
+def test_operator_eigenfunctions_dirichlet_top(mode):
+    nx, ny, nz, dx, dy, dz = 16, 12, 10, 0.9, 1.7, 0.6
+    p = _cos_mode_dt(nx, ny, nz, *mode)
+    W, a, c = O.vertical_coefficients(np.full(nz, dz), np.full(nz, 2.0), bc="dirichlet_top")
+    Lp = O.apply_L(p, dx, dy, a, c)
+    lam = _cos_mode_dt_eig(nx, ny, nz, *mode, dx, dy, dz)
+    assert np.abs(Lp - lam * p).max() <= 1e-13 * np.abs(lam)
+
+
+@pytest.mark.parametrize("mode", [(0, 0, 0), (1, 0, 0), (0, 0, 7), (3, 2, 5), (8, 6, 0)])
+def test_solve_eigenfunctions_dirichlet_top(mode):
+    nx, ny, nz, dx, dy, dz = 16, 12, 10, 0.9, 1.7, 0.6
+    p_exact = _cos_mode_dt(nx, ny, nz, *mode)
+    lam = _cos_mode_dt_eig(nx, ny, nz, *mode, dx, dy, dz)
+    p = O.solve(lam * p_exact, dx, dy, np.full(nz, dz), np.full(nz, 1.0), bc="dirichlet_top")
+    assert O.relative_l2(p, p_exact) < 1e-13
+
+
+def test_dirichlet_top_converges_to_continuous_anelastic_problem():
+    """Second-order convergence with p = 0 at z = H and zero flux at z = 0.
+
+    Exact solution p = cos(2 pi i/nx) cos(pi z/(2H)) with rho = 1.2 exp(-z/Hs) on
+    smoothly stretched levels.  The top flux carries the top cell's density over
+    half a cell; measuring the distance to the face as a whole cell instead
+    converges at first order only.
+    """
+    H, Hs, nx, dx = 3000.0, 2500.0, 8, 400.0
+    i = np.arange(nx)
+    lx = -(4 / dx**2) * np.sin(np.pi / nx) ** 2
+    q = np.pi / (2 * H)
+    errs = []
+    for nz in (32, 64, 128, 256):
+        dz = _smooth_grid(nz, H)
+        z = wl.cell_centres(dz)
+        rho = 1.2 * np.exp(-z / Hs)
+        f = np.cos(q * z)
+        Lf = -q**2 * np.cos(q * z) + q / Hs * np.sin(q * z)
+        hx = np.cos(2 * np.pi * i / nx)[None, None, :] * np.ones((1, 2, 1))
+        S = (Lf + lx * f)[:, None, None] * hx
+        p = O.solve(S, dx, 1.0, dz, rho, bc="dirichlet_top")
+        exact = f[:, None, None] * hx
+        errs.append(np.abs(p - exact).max() / np.abs(exact).max())
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(ratios > 3.4) and np.all(ratios < 4.3), (errs, ratios)
+
+
+def test_dirichlet_top_operator_structure():
+    d = wl.random_stretched(6, 5, 7, seed=12)
+    W, a, c = O.vertical_coefficients(d.dz, d.rho0, bc="dirichlet_top")
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal(d.S.shape)
+    v = rng.standard_normal(d.S.shape)
+    Wf = W[:, None, None]
+    # W L stays symmetric (the top coupling only adds to the diagonal)
+    lhs = (u * Wf * O.apply_L(v, d.dx, d.dy, a, c)).sum()
+    rhs = (Wf * O.apply_L(u, d.dx, d.dy, a, c) * v).sum()
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # a constant loses exactly the top-face flux
+    Lone = O.apply_L(np.ones(d.S.shape), d.dx, d.dy, a, c)
+    assert np.abs(Lone[:-1]).max() < 1e-13
+    assert np.allclose(Lone[-1], -c[-1], rtol=1e-14)
+
+
+@pytest.mark.parametrize("dims,seed", [((4, 6, 5), 1), ((6, 4, 7), 2), ((5, 4, 2), 3), ((8, 6, 4), 4)])
+def test_dirichlet_top_matches_brute_force(dims, seed):
+    nx, ny, nz = dims
+    d = wl.random_stretched(nx, ny, nz, seed=seed)
+    W, a, c = O.vertical_coefficients(d.dz, d.rho0, bc="dirichlet_top")
+    A = _dense_L(d.S.shape, d.dx, d.dy, a, c)
+    S = d.S + 0.4          # no compatibility condition: a mean in S is solved for, not removed
+    ref = np.linalg.solve(A, S.ravel()).reshape(d.S.shape)
+    p = O.solve(S, d.dx, d.dy, d.dz, d.rho0, bc="dirichlet_top")
+    assert O.relative_l2(p, ref) < 1e-12
+    r = O.residual(S, p, d.dx, d.dy, d.dz, d.rho0, bc="dirichlet_top")
+    assert np.linalg.norm(r) < 1e-12 * np.linalg.norm(S)
+
+
+@pytest.mark.parametrize("dims,seed", [((6, 4, 5), 1), ((5, 6, 3), 3)])
+def test_dirichlet_top_adjoint_dot_product_and_dense_transpose(dims, seed):
+    nx, ny, nz = dims
+    d = wl.random_stretched(nx, ny, nz, seed=seed)
+    W, a, c = O.vertical_coefficients(d.dz, d.rho0, bc="dirichlet_top")
+    rng = np.random.default_rng(seed + 200)
+    w = rng.standard_normal(d.S.shape)
+    g = O.adjoint(w, d.dx, d.dy, d.dz, d.rho0, bc="dirichlet_top")
+    A = _dense_L(d.S.shape, d.dx, d.dy, a, c)
+    ref = np.linalg.solve(A.T, w.ravel())
+    assert O.relative_l2(g.ravel(), ref) < 1e-12
+
+
+def test_dirichlet_top_rho0_gradient_matches_central_differences():
+    d = wl.random_stretched(6, 5, 6, seed=23)
+    rng = np.random.default_rng(9)
+    w = rng.standard_normal(d.S.shape)
+    g = O.rho0_gradient(w, d.S, d.dx, d.dy, d.dz, d.rho0, bc="dirichlet_top")
+
+    def loss(rho):
+        return (w * O.solve(d.S, d.dx, d.dy, d.dz, rho, bc="dirichlet_top")).sum()
+
+    fd = np.zeros(d.nz)
+    for m in range(d.nz):
+        eps = 1e-6 * d.rho0[m]
+        rp = d.rho0.copy()
+        rm = d.rho0.copy()
+        rp[m] += eps
+        rm[m] -= eps
+        fd[m] = (loss(rp) - loss(rm)) / (2 * eps)
+    assert np.abs(g - fd).max() <= 1e-6 * np.abs(g).max(), (g, fd)
