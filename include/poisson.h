@@ -120,7 +120,11 @@ typedef struct {
   int sweeps;                  /* refinement sweeps executed (mixed path; 0 otherwise) */
   int converged;               /* 1 if the mixed stopping test passed (always 1 for FP64/FP32) */
   double rel_update[4];        /* ||delta_n||_2/||p||_2 of sweep n (index 0 = first solve = 1) */
-  double error_estimate;       /* estimated relative L2 error of the returned p (mixed path) */
+  double error_estimate;       /* mixed path: rel_update[n] * (rel_update[n] / rel_update[n-1]) after
+                                  sweep n (linear-convergence extrapolation; -1 before any sweep).  After
+                                  sweep 1 it takes the first solve's accuracy as the contraction and can be
+                                  optimistic by orders of magnitude; the stopping test compares it with
+                                  the tolerance */
   double removed_weighted_mean;/* mu_W removed from S (first solve) */
 } poisson_info;
 
