@@ -26,7 +26,8 @@
  * nonsingular and the solve returns p = L^-1 S (nothing is projected or pinned).
  *
  * Memory conventions (all calls):
- *   - fields are C-contiguous [nz][ny][nx] arrays, x fastest, in DEVICE memory;
+ *   - fields are C-contiguous [nz][ny][nx] arrays, x fastest, in DEVICE memory
+ *     (or [nx][ny][nz], z fastest, with POISSON_OPT_LAYOUT = POISSON_LAYOUT_X_Y_Z);
  *   - element type: double for POISSON_FP64 and POISSON_MIXED, float for POISSON_FP32;
  *   - the caller owns every field and the workspace; the plan owns only its small
  *     device tables (coefficients, twiddles), allocated by create, freed by destroy;
@@ -97,12 +98,24 @@ typedef enum {
   POISSON_OPT_X_KERNEL = 9,      /* x-pass kernel of the FP32 transforms: 0 = persistent kernel with bulk-copy
                                     staging where nx/2 is a power of two in [64, 2048] (default),
                                     1 = one CTA per row group */
-  POISSON_OPT_COL_TILE = 10      /* column-solve kernel: 0 = default (FP32 forward solves: two threads per
+  POISSON_OPT_COL_TILE = 10,     /* column-solve kernel: 0 = default (FP32 forward solves: two threads per
                                     column meeting mid-column, 32 columns per CTA; FP32 adjoint solves: the
                                     paired-ky kernel); 1, 2, 4 = two threads per column with 16, 32, 64
                                     columns; 3 = paired-ky kernel; 16, 32, 64, 128 = one thread per column
                                     with that many columns per CTA */
+  POISSON_OPT_LAYOUT = 11        /* layout of the caller's fields (S, p, gp, gS), a poisson_layout value;
+                                    default POISSON_LAYOUT_Z_Y_X.  Any other layout adds two field-sized
+                                    buffers to the workspace (query the size after setting it) */
 } poisson_option;
+
+/* Field layouts (POISSON_OPT_LAYOUT), C order, outermost index first. */
+typedef enum {
+  POISSON_LAYOUT_Z_Y_X = 0,  /* [nz][ny][nx], x fastest: the solver's own layout */
+  POISSON_LAYOUT_X_Y_Z = 1   /* [nx][ny][nz], z fastest: MONC's field order (its Fortran fields are
+                                indexed data(z, y, x), as in the solver listings of Section 2.2);
+                                converted to and from the solver's layout in the workspace by tiled
+                                transposes, two extra passes over each field */
+} poisson_layout;
 
 /* Kernel phases reported by poisson_plan_profile_read. */
 typedef enum {

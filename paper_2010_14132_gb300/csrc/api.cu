@@ -75,6 +75,7 @@ struct poisson_plan {
   double dx = 0, dy = 0;
   int dtype = 0;
   int bc = POISSON_BC_PERIODIC_XY_NEUMANN_Z;
+  int layout = POISSON_LAYOUT_Z_Y_X;   // caller's field layout (the solver works on [nz][ny][nx])
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
   int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
@@ -91,7 +92,7 @@ struct poisson_plan {
   float2 cx{}, cy{};
   // workspace layout
   size_t off_spec = 0, off_stats = 0, off_part = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
-         off_gp = 0, ws_bytes = 0;
+         off_gp = 0, off_fa = 0, off_fb = 0, ws_bytes = 0;
   int xinv_blocks = 1, grho_nb = 1;
   PhaseProfiler prof;
   bool mixed() const { return dtype == POISSON_MIXED; }
@@ -164,6 +165,12 @@ void layout_workspace(poisson_plan* pl) {
   }
   pl->off_gp = off;
   off = align256(off + 2 * sizeof(double) * (size_t)(pl->nz - 1) * pl->grho_nb);
+  if (pl->layout != POISSON_LAYOUT_Z_Y_X) {   // the caller's fields in the solver's layout
+    pl->off_fa = off;
+    off = align256(off + pl->elem() * (size_t)N);
+    pl->off_fb = off;
+    off = align256(off + pl->elem() * (size_t)N);
+  }
   pl->ws_bytes = off;
 }
 
@@ -447,6 +454,11 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->xkernel = (int)value;
       return POISSON_OK;
+    case POISSON_OPT_LAYOUT:
+      if (!(value == POISSON_LAYOUT_Z_Y_X || value == POISSON_LAYOUT_X_Y_Z)) return POISSON_ERR_INVALID_ARG;
+      pl->layout = (int)value;
+      layout_workspace(pl);
+      return POISSON_OK;
     case POISSON_OPT_PROFILE:
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->prof.on = value != 0;
@@ -636,16 +648,16 @@ static int fill_info(poisson_plan* pl, char* ws, cudaStream_t st, poisson_info* 
   return s.converged ? POISSON_OK : POISSON_ERR_NOT_CONVERGED;
 }
 
-int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, void* stream, poisson_info* info) {
-  if (!pl || !S || !p) return POISSON_ERR_INVALID_ARG;
-  int rc = check_ws(pl, workspace);
-  if (rc != POISSON_OK) return rc;
-  const size_t fbytes = (size_t)pl->g.N * pl->elem();
-  if (ranges_overlap(S, fbytes, p, fbytes)) return POISSON_ERR_INVALID_ARG;
-  if (ranges_overlap(S, fbytes, workspace, pl->ws_bytes) || ranges_overlap(p, fbytes, workspace, pl->ws_bytes))
-    return POISSON_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  char* ws = (char*)workspace;
+// [nx][ny][nz] (k fastest) <-> [nz][ny][nx] (i fastest)
+static cudaError_t to_solver_layout(const poisson_plan* pl, const void* src, void* dst, cudaStream_t st) {
+  return launch_swap_outer_inner(src, dst, pl->nx, pl->ny, pl->nz, (int)pl->elem(), st);
+}
+static cudaError_t from_solver_layout(const poisson_plan* pl, const void* src, void* dst, cudaStream_t st) {
+  return launch_swap_outer_inner(src, dst, pl->nz, pl->ny, pl->nx, (int)pl->elem(), st);
+}
+
+// The solve on fields in the solver's layout.
+static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cudaStream_t st) {
   Stats* stats = (Stats*)(ws + pl->off_stats);
   PGB_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), st));
   const bool t_double = pl->fp64();
@@ -700,6 +712,29 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
       }
     }
   }
+  return POISSON_OK;
+}
+
+int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, void* stream, poisson_info* info) {
+  if (!pl || !S || !p) return POISSON_ERR_INVALID_ARG;
+  int rc = check_ws(pl, workspace);
+  if (rc != POISSON_OK) return rc;
+  const size_t fbytes = (size_t)pl->g.N * pl->elem();
+  if (ranges_overlap(S, fbytes, p, fbytes)) return POISSON_ERR_INVALID_ARG;
+  if (ranges_overlap(S, fbytes, workspace, pl->ws_bytes) || ranges_overlap(p, fbytes, workspace, pl->ws_bytes))
+    return POISSON_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  if (pl->layout == POISSON_LAYOUT_Z_Y_X) {
+    rc = solve_fields(pl, S, p, ws, st);
+  } else {
+    void* Sa = ws + pl->off_fa;
+    void* pb = ws + pl->off_fb;
+    PGB_CUDA(to_solver_layout(pl, S, Sa, st));
+    rc = solve_fields(pl, Sa, pb, ws, st);
+    if (rc == POISSON_OK) PGB_CUDA(from_solver_layout(pl, pb, p, st));
+  }
+  if (rc != POISSON_OK) return rc;
   if (info) return fill_info(pl, ws, st, info);
   return POISSON_OK;
 }
@@ -719,14 +754,20 @@ int poisson_solve_adjoint(poisson_plan* pl, const void* gp, const void* p, void*
   PGB_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), st));
   const bool t_double = pl->fp64();
   const int io_double = pl->dtype != POISSON_FP32;
-  PGB_CUDA(forward_columns(pl, gp, io_double, ws, st, 1, nullptr));
+  const bool swap = pl->layout != POISSON_LAYOUT_Z_Y_X;
+  void* fa = ws + pl->off_fa;
+  void* gS_s = swap ? (void*)(ws + pl->off_fb) : gS;
+  if (swap) PGB_CUDA(to_solver_layout(pl, gp, fa, st));
+  PGB_CUDA(forward_columns(pl, swap ? fa : gp, io_double, ws, st, 1, nullptr));
   XinvExtra ex{};
-  PGB_CUDA(inverse(pl, ws, st, nullptr, io_double, XINV_PLAIN, gS, ex, nullptr));
+  PGB_CUDA(inverse(pl, ws, st, nullptr, io_double, XINV_PLAIN, gS_s, ex, nullptr));
   if (grho) {
     const int kind = pl->fp64() ? 0 : (pl->dtype == POISSON_FP32 ? 1 : 2);
-    PGB_CUDA(launch_grho(kind, gS, p, pl->g, pl->tb, pl->dz_d, pl->rho_d, (double*)(ws + pl->off_gp), pl->grho_nb,
-                         grho, st));
+    if (swap) PGB_CUDA(to_solver_layout(pl, p, fa, st));   // gp's copy is no longer read
+    PGB_CUDA(launch_grho(kind, gS_s, swap ? fa : p, pl->g, pl->tb, pl->dz_d, pl->rho_d, (double*)(ws + pl->off_gp),
+                         pl->grho_nb, grho, st));
   }
+  if (swap) PGB_CUDA(from_solver_layout(pl, gS_s, gS, st));
   return POISSON_OK;
 }
 

@@ -162,6 +162,9 @@ cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long lo
                              cudaStream_t st);
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
                            double tol, long long npoints, cudaStream_t st);
+// dst[b][m][a] = src[a][m][b]: [nx][ny][nz] <-> [nz][ny][nx] field layouts (elem_bytes 4 or 8).
+cudaError_t launch_swap_outer_inner(const void* src, void* dst, int A, int M, int B, int elem_bytes,
+                                    cudaStream_t st);
 cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
                                 double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff, int top_dirichlet,
                                 cudaStream_t st);

@@ -1,4 +1,5 @@
-// Refinement control, correction rebuild, coefficient tables and rho0-gradient reductions.
+// Refinement control, correction rebuild, coefficient tables, rho0-gradient reductions and
+// the field-layout conversion.
 #include "kernels.cuh"
 #include "residual2.cuh"
 
@@ -268,6 +269,46 @@ cudaError_t launch_grho(int kind, const void* g, const void* p, const Geom& g_, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_grho_final<<<(g_.nz + 127) / 128, 128, 0, st>>>(partials, nb, g_.nz, dz, rho0, tb.a_d, tb.c_d, tb.W_d, grho);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Field layout conversion.  MONC keeps its fields with the vertical index
+// fastest, [nx][ny][nz]; the solver works on [nz][ny][nx].  Both directions are
+// the same operation, dst[b][m][a] = src[a][m][b] (a < A, m < M, b < B): a swap
+// of the outer and inner axes, done in 32 x 32 tiles of one m through shared
+// memory so that the reads (along b) and the writes (along a) are coalesced.
+// The padded row (33) keeps the transposed shared reads free of bank conflicts
+// for 4-byte elements and for each half-warp of 8-byte ones.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_swap_outer_inner(const T* __restrict__ src, T* __restrict__ dst, int A,
+                                                          int M, int B) {
+  __shared__ T tile[32][33];
+  const int b0 = blockIdx.x * 32, a0 = blockIdx.y * 32, m = blockIdx.z;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long long src_a = (long long)M * B, dst_b = (long long)M * A;
+#pragma unroll
+  for (int r = ty; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx;
+    if (a < A && b < B) tile[r][tx] = __ldcs(&src[a * src_a + (long long)m * B + b]);   // read once
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = ty; r < 32; r += 8) {
+    const int b = b0 + r, a = a0 + tx;
+    if (a < A && b < B) dst[b * dst_b + (long long)m * A + a] = tile[tx][r];
+  }
+}
+
+cudaError_t launch_swap_outer_inner(const void* src, void* dst, int A, int M, int B, int elem_bytes,
+                                    cudaStream_t st) {
+  if (A <= 0 || M <= 0 || B <= 0 || M > 65535) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((B + 31) / 32), (unsigned)((A + 31) / 32), (unsigned)M), block(32, 8);
+  if (elem_bytes == 8)
+    k_swap_outer_inner<double><<<grid, block, 0, st>>>((const double*)src, (double*)dst, A, M, B);
+  else
+    k_swap_outer_inner<float><<<grid, block, 0, st>>>((const float*)src, (float*)dst, A, M, B);
   return cudaGetLastError();
 }
 

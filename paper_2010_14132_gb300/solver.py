@@ -13,6 +13,7 @@ import torch
 from . import _native as N
 
 DTYPES = {"fp64": N.POISSON_FP64, "fp32": N.POISSON_FP32, "mixed": N.POISSON_MIXED}
+LAYOUTS = {"zyx": N.POISSON_LAYOUT_Z_Y_X, "xyz": N.POISSON_LAYOUT_X_Y_Z}
 BCS = {"neumann": N.POISSON_BC_PERIODIC_XY_NEUMANN_Z,
        "dirichlet_top": N.POISSON_BC_PERIODIC_XY_NEUMANN_BOTTOM_DIRICHLET_TOP}
 FIELD_DTYPE = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float64}
@@ -40,17 +41,22 @@ class Plan:
     dtype: "fp64", "fp32" or "mixed" (double fields, float transforms, double
     low-|k| columns and double-float refinement).  bc: "neumann" (zero flux
     through the bottom and top faces; p is projected and pinned to zero mean) or
-    "dirichlet_top" (zero flux at the bottom, p = 0 on the top face).
+    "dirichlet_top" (zero flux at the bottom, p = 0 on the top face).  layout:
+    "zyx" (fields of shape (nz, ny, nx), x fastest) or "xyz" (shape (nx, ny, nz),
+    z fastest, MONC's order; converted inside the library's workspace).
     """
 
-    def __init__(self, nx, ny, nz, dx, dy, dz, rho0, dtype="fp64", device=None, bc="neumann",
+    def __init__(self, nx, ny, nz, dx, dy, dz, rho0, dtype="fp64", device=None, bc="neumann", layout="zyx",
                  lowk_radius2=None, max_sweeps=None, tolerance=None, y_tile=None, y_kernel=None,
                  x_elems=None, y_elems=None, level_chunk=None, x_kernel=None, col_tile=None):
         if dtype not in DTYPES:
             raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
         if bc not in BCS:
             raise ValueError(f"bc must be one of {sorted(BCS)}")
+        if layout not in LAYOUTS:
+            raise ValueError(f"layout must be one of {sorted(LAYOUTS)}")
         self.bc = bc
+        self.layout = layout
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.dx, self.dy = float(dx), float(dy)
         self.dz = np.asarray(dz, dtype=np.float64).copy()
@@ -83,6 +89,8 @@ class Plan:
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_X_KERNEL, x_kernel)
         if col_tile is not None:
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_COL_TILE, col_tile)
+        if layout != "zyx":
+            N.poisson_plan_set_option(self._h, N.POISSON_OPT_LAYOUT, LAYOUTS[layout])
         self._ws = None
 
     # -- lifetime ------------------------------------------------------------
@@ -100,7 +108,7 @@ class Plan:
 
     @property
     def shape(self):
-        return (self.nz, self.ny, self.nx)
+        return (self.nz, self.ny, self.nx) if self.layout == "zyx" else (self.nx, self.ny, self.nz)
 
     @property
     def npoints(self):
