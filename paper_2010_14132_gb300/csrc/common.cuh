@@ -175,4 +175,35 @@ template <> struct Cvt<float, double> { static __device__ __forceinline__ double
 // Device-side error word bits (workspace stats area).
 enum : unsigned { ERR_WAIT_TIMEOUT = 1u, ERR_BAD_SIZE = 2u };
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of the solve chain are launched
+// with pdl_launch: the next kernel's CTAs may start (and build their shared
+// tables from the plan's constant tables) while the previous kernel drains.
+// Every such kernel calls pdl_wait() before it touches memory that an earlier
+// kernel of the stream writes or reads: the wait returns once those kernels
+// have completed and their writes are visible.  pdl_trigger() lets the next
+// kernel launch early; its CTAs take SM resources only as this kernel's leave.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline cudaError_t pdl_launch(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+#ifdef PGB_NO_PDL
+  at[0].val.programmaticStreamSerializationAllowed = 0;
+#else
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+#endif
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 }  // namespace pgb

@@ -114,6 +114,8 @@ __global__ void __launch_bounds__(256) k_control(Stats* st, const double* __rest
 __global__ void __launch_bounds__(256) k_q_rebuild(const double2* __restrict__ p, const float2* __restrict__ p0,
                                                    float2* __restrict__ q, long long npairs,
                                                    const int* __restrict__ done) {
+  pdl_trigger();
+  pdl_wait();   // the previous kernels of the stream are complete
   if (done && *done) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npairs;
        i += (long long)gridDim.x * blockDim.x) {
@@ -136,8 +138,8 @@ cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long lo
   const long long cap = (long long)(sms > 0 ? sms : 1) * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  k_q_rebuild<<<(unsigned)blocks, 256, 0, st>>>((const double2*)p, (const float2*)p0, (float2*)q, npairs, done);
-  return cudaGetLastError();
+  return pdl_launch(k_q_rebuild, dim3((unsigned)blocks), dim3(256), 0, st, (const double2*)p, (const float2*)p0,
+                    (float2*)q, npairs, done);
 }
 
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps, double tol,

@@ -446,6 +446,8 @@ __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Ge
                                                   const float* __restrict__ lamy, float scale, int lowk_r2,
                                                   const int* __restrict__ done, Stats* stats,
                                                   const __grid_constant__ CUtensorMap tm, int box_rows, LowkArgs L) {
+  pdl_trigger();
+  pdl_wait();   // the previous kernels of the stream are complete
   if (done && *done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
   if ((int)blockIdx.x < L.n) {
@@ -653,10 +655,9 @@ static cudaError_t thomas_tw_launch(const ThomasArgs& A, const Geom& g, const Ta
   const long long nb = (g.plane + tc - 1) / tc;
   const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale,
                    A.singular00};
-  kern<<<(unsigned)(nb + A.n_lowk), 2 * tc, smem, st>>>((float2*)A.spec, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f,
-                                                        (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows, L);
   *used = true;
-  return cudaGetLastError();
+  return pdl_launch(kern, dim3((unsigned)(nb + A.n_lowk)), dim3(2 * tc), smem, st, (float2*)A.spec, g, tb.a_f, tb.c_f,
+                    tb.lamx_f, tb.lamy_f, (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows, L);
 }
 
 template <typename T, typename TCm, bool ADJ>

@@ -226,9 +226,8 @@ cudaError_t xs_launch(K kern, int threads_x, int RB, const XsConfig& c, long lon
   const long long grid = ngroups < cap ? ngroups : cap;
   if (grid <= 0) return cudaSuccess;
   if (nblocks_out) *nblocks_out = (int)grid;
-  kern<<<(unsigned)grid, dim3(threads_x, RB), c.smem, st>>>(args..., c.ns, c.stage_bytes);
   *used = true;
-  return cudaGetLastError();
+  return pdl_launch(kern, dim3((unsigned)grid), dim3(threads_x, RB), c.smem, st, args..., c.ns, c.stage_bytes);
 }
 
 }  // namespace

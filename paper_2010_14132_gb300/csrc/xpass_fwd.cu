@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xfwd_s(const TI* __restrict__
   using TI2 = typename V2s<TI>::t;
   constexpr int nl = N / E, RB = xs_threads(E) / nl, LS = swizzled_stride(N);
   constexpr bool ALIAS = sizeof(TI) == 8;
-  if (done && *done) return;
+  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smraw[];
   const XsLayout L = xs_layout(N, RB, ns, stage_bytes, ALIAS);
   C* tw_s = reinterpret_cast<C*>(smraw);
@@ -39,6 +39,8 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xfwd_s(const TI* __restrict__
     mbar_fence_init();
   }
   __syncthreads();
+  pdl_wait();   // the previous kernels of the stream are complete
+  if (done && *done) return;
   auto issue = [&](long long grp, int s) {
     const long long r0 = row_begin + grp * RB;
     const long long nv = row_end - r0 < RB ? row_end - r0 : RB;

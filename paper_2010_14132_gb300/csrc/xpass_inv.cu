@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restri
                                                       XinvExtra ex, int ns, unsigned stage_bytes) {
   using C = float2;
   constexpr int nl = N / E, RB = xs_threads(E) / nl, LS = swizzled_stride(N);
-  if (ex.done && *ex.done) return;
+  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smraw[];
   const XsLayout L = xs_layout(N, RB, ns, stage_bytes, false);
   C* tw_s = reinterpret_cast<C*>(smraw);
@@ -36,6 +36,8 @@ __global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restri
     mbar_fence_init();
   }
   __syncthreads();
+  pdl_wait();   // the previous kernels of the stream are complete
+  if (ex.done && *ex.done) return;
   auto issue = [&](long long grp, int s) {
     const long long r0 = row_begin + grp * RB;
     const int nv = (int)(row_end - r0 < RB ? row_end - r0 : RB);

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(xs_threads(E), E >= 24 ? 2 : (E >= 16 ? 4 : 3)
                                                       int ns, unsigned stage_bytes) {
   using C = float2;
   constexpr int nl = N / E, RB = xs_threads(E) / nl, LS = swizzled_stride(N), NX = 2 * N;
-  if (done && *done) return;
+  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smraw[];
   const XsLayout L = xs_layout(N, RB, ns, stage_bytes, true);
   C* tw_s = reinterpret_cast<C*>(smraw);
@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(xs_threads(E), E >= 24 ? 2 : (E >= 16 ? 4 : 3)
     mbar_fence_init();
   }
   __syncthreads();
+  pdl_wait();   // the previous kernels of the stream are complete
+  if (done && *done) return;
   auto issue = [&](long long grp, int s) {
     const long long r0 = row_begin + grp * RB;
     const unsigned nv = (unsigned)(row_end - r0 < RB ? row_end - r0 : RB);

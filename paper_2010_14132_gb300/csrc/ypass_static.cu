@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant_
                                             unsigned* __restrict__ err) {
   using C = float2;
   constexpr int nl = N / E;
-  if (done && *done) return;
+  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smraw[];
   const int TK = blockDim.x, l = threadIdx.x, lane = threadIdx.y;
   const int tid = lane * TK + l, nthreads = TK * nl;
@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant_
     mbar_fence_init();
   }
   __syncthreads();
+  pdl_wait();   // the previous kernels of the stream are complete
+  if (done && *done) return;
   int issued[2] = {0, 0}, consumed[2] = {0, 0};
   auto issue = [&](int t, int b) {
     const int level = t / tiles_per_level, kx0 = (t - level * tiles_per_level) * TK;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(ys_max_threads(E), 2) k_ys1(const __grid_const
                                                              const int* __restrict__ done, unsigned* __restrict__ err) {
   using C = float2;
   constexpr int nl = N / E;
-  if (done && *done) return;
+  pdl_trigger();
   extern __shared__ __align__(128) unsigned char smraw[];
   const int TK = blockDim.x, l = threadIdx.x, lane = threadIdx.y;
   const int tid = lane * TK + l, nthreads = TK * nl;
@@ -147,6 +149,8 @@ __global__ void __launch_bounds__(ys_max_threads(E), 2) k_ys1(const __grid_const
     mbar_fence_init();
   }
   __syncthreads();
+  pdl_wait();   // the previous kernels of the stream are complete
+  if (done && *done) return;
   const SwStrided sw{TK};
   int it = 0, pending = 0;
   bool ok = true;
@@ -246,7 +250,9 @@ cudaError_t ys_launch(float2* spec, const Geom& g, int N, const float2* twy, int
     if (per_sm < 1) return cudaSuccess;
     const int grid = chunk_tiles < sms * per_sm ? chunk_tiles : sms * per_sm;
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, dim3(tk, N / E), smem, st>>>(tm, g, twy, spec, box_rows, tiles_per_level, ntiles, done, err);
+    e = pdl_launch(kern, dim3(grid), dim3(tk, N / E), smem, st, tm, g, twy, spec, box_rows, tiles_per_level, ntiles,
+                   done, err);
+    if (e != cudaSuccess) return e;
     *used = true;
   });
   return cudaGetLastError();
@@ -282,7 +288,9 @@ cudaError_t ys1_launch(float2* spec, const Geom& g, int N, const float2* twy, in
     if (per_sm < 1) return cudaSuccess;
     const int grid = chunk_tiles < sms * per_sm ? chunk_tiles : sms * per_sm;
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, dim3(tk, N / E), smem, st>>>(tm, g, twy, spec, box_rows, tiles_per_level, ntiles, done, err);
+    e = pdl_launch(kern, dim3(grid), dim3(tk, N / E), smem, st, tm, g, twy, spec, box_rows, tiles_per_level, ntiles,
+                   done, err);
+    if (e != cudaSuccess) return e;
     *used = true;
   });
   return cudaGetLastError();
