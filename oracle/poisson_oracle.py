@@ -44,7 +44,7 @@ __all__ = [
     "vertical_coefficients", "horizontal_eigenvalues", "weighted_mean", "project_compatible",
     "apply_L", "residual", "dft_x", "dft_y", "idft_y", "idft_x", "thomas",
     "column_matrix", "singular_column_solve", "solve", "adjoint", "rho0_gradient",
-    "relative_l2",
+    "relative_l2", "apply_A_var", "weights_var", "solve_var",
 ]
 
 
@@ -388,3 +388,106 @@ def relative_l2(x, ref):
     x = _f64(x)
     ref = _f64(ref)
     return float(np.linalg.norm((x - ref).ravel()) / np.linalg.norm(ref.ravel()))
+
+
+# ---------------------------------------------------------------------------
+# Variable density (the case an iterative solver opens, Section 2.2): rho varies
+# in x, y and z, so the Fourier transform no longer separates the operator.
+# ---------------------------------------------------------------------------
+
+def weights_var(dz, rho3):
+    """W_ijk = rho_ijk dz_k, the cell weights of the variable-density operator."""
+    return _f64(rho3) * _f64(dz)[:, None, None]
+
+
+def apply_A_var(p, dx, dy, dz, rho3, bc="neumann"):
+    """Flux-form 7-point operator of div(rho grad p)/rho on the same cells as L.
+
+    (A p)_ijk = (1/W_ijk) [ dz_k ((F^x_{i+1/2} - F^x_{i-1/2})/dx + (F^y_{j+1/2} - F^y_{j-1/2})/dy)
+                           + F^z_{k+1/2} - F^z_{k-1/2} ],
+    with fluxes F^x_{i+1/2} = rho_{i+1/2} (p_{i+1} - p_i)/dx (periodic),
+    F^y likewise, F^z_{k+1/2} = rho_{k+1/2} (p_{k+1} - p_k)/h_{k+1/2}, face
+    densities by arithmetic mean of the two cells, zero flux through the bottom
+    face and through the top face ("neumann") or F^z_top = rho_{nz-1} (0 - p_{nz-1})
+    / (dz_{nz-1}/2) ("dirichlet_top").  With rho_ijk = rho0_k this is L.
+    """
+    _check_bc(bc)
+    p = _f64(p)
+    rho = _f64(rho3)
+    dz = _f64(dz)
+    nz = p.shape[0]
+    Fx = 0.5 * (rho + np.roll(rho, -1, axis=2)) * (np.roll(p, -1, axis=2) - p) / dx   # at i+1/2
+    Fy = 0.5 * (rho + np.roll(rho, -1, axis=1)) * (np.roll(p, -1, axis=1) - p) / dy   # at j+1/2
+    h = 0.5 * (dz[:-1] + dz[1:])
+    Fz = np.zeros((nz + 1,) + p.shape[1:])                                          # at k-1/2, k = 0..nz
+    Fz[1:nz] = 0.5 * (rho[:-1] + rho[1:]) * (p[1:] - p[:-1]) / h[:, None, None]
+    if bc == "dirichlet_top":
+        Fz[nz] = rho[-1] * (0.0 - p[-1]) / (0.5 * dz[-1])
+    div = (dz[:, None, None] * ((Fx - np.roll(Fx, 1, axis=2)) / dx + (Fy - np.roll(Fy, 1, axis=1)) / dy)
+           + (Fz[1:] - Fz[:-1]))
+    return div / weights_var(dz, rho)
+
+
+def solve_var(S, dx, dy, dz, rho3, bc="neumann"):
+    """p with A p = Q S (zero plain mean with zero flux at the top; A^-1 S with p = 0 there).
+
+    Q S = S - sum(W S)/sum(W) removes the part of S outside the range of A.  The
+    matrix is assembled column by column from apply_A_var and solved by a library
+    sparse LU (with zero flux, after fixing one cell and then removing the mean):
+    tiny and moderate grids only.
+    """
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    S = _f64(S)
+    shape = S.shape
+    N = S.size
+    nz, ny, nx = shape
+    W = weights_var(dz, rho3)
+    rhs = S.ravel().copy()
+    if bc == "neumann":
+        rhs -= (W * S).sum() / W.sum()
+    # columns of A by probing with sums of unit vectors whose stencils never overlap: indices
+    # of one colour differ by a multiple of m >= 3 (m divides a periodic extent, so the
+    # wrap-around keeps the spacing)
+    def colours(n, periodic):
+        if not periodic:
+            return 3
+        return next((m for m in range(3, n + 1) if n % m == 0), n)
+
+    mz, my, mx = colours(nz, False), colours(ny, True), colours(nx, True)
+    rows, cols, vals = [], [], []
+    idx = np.arange(N).reshape(shape)
+    for ck in range(min(mz, nz)):
+        for cj in range(min(my, ny)):
+            for ci in range(min(mx, nx)):
+                e = np.zeros(shape)
+                sel = np.zeros(shape, dtype=bool)
+                sel[ck::mz, cj::my, ci::mx] = True
+                e[sel] = 1.0
+                Ae = apply_A_var(e, dx, dy, dz, rho3, bc)
+                for q in idx[sel]:
+                    k, j, i = np.unravel_index(q, shape)
+                    # the rows of q's stencil, each once (with 2 cells in a periodic direction
+                    # the two neighbours there are one cell)
+                    stencil = {(k + dk, (j + dj) % ny, (i + di) % nx)
+                               for dk, dj, di in ((0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                                                  (0, 0, 1), (0, 0, -1))
+                               if 0 <= k + dk < nz}
+                    for kk, jj, ii in stencil:
+                        rows.append(idx[kk, jj, ii])
+                        cols.append(q)
+                        vals.append(Ae[kk, jj, ii])
+    A = sp.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
+    A.sum_duplicates()
+    if bc == "neumann":
+        # constants span the null space: fix p at cell 0 (its row is implied by the others,
+        # since the W-weighted rows of A sum to zero and Q S is compatible), then remove the mean
+        A = A.tolil()
+        A[0, :] = 0.0
+        A[0, 0] = 1.0
+        rhs[0] = 0.0
+        x = spla.spsolve(A.tocsc(), rhs)
+        x -= x.mean()
+    else:
+        x = spla.spsolve(A.tocsc(), rhs)
+    return x.reshape(shape)

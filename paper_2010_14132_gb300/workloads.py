@@ -185,3 +185,29 @@ def random_stretched(nx: int, ny: int, nz: int, seed: int, dx: float = 1.0, dy: 
     S = rng.standard_normal((nz, ny, nx))
     S -= S.mean()
     return Domain(nx, ny, nz, dx, dy, dz, rho, S, name=f"random_{nx}x{ny}x{nz}_s{seed}")
+
+
+def perturbed_density(nx: int, ny: int, rho0: np.ndarray, eps: float, seed: int, modes: int = 4) -> np.ndarray:
+    """rho_ijk = rho0_k (1 + eps g_ijk): a seeded smooth perturbation of a level profile.
+
+    g is a normalised sum of `modes` periodic cosines in x and y (wavenumbers 1..3)
+    times a slow variation in z, with max |g| = 1, so rho stays positive for eps < 1.
+    Stands in for the horizontally varying density (e.g. moist or terrain-following
+    cases) that the FFT solve cannot separate.
+    """
+    rng = np.random.default_rng(seed)
+    rho0 = np.asarray(rho0, dtype=np.float64)
+    nz = rho0.size
+    i = np.arange(nx)[None, None, :]
+    j = np.arange(ny)[None, :, None]
+    k = np.arange(nz)[:, None, None]
+    g = np.zeros((nz, ny, nx))
+    for _ in range(modes):
+        a, b = rng.integers(0, 4, size=2)
+        if a == 0 and b == 0:
+            a = 1
+        ph = rng.uniform(0, 2 * np.pi, size=3)
+        g += (np.cos(2 * np.pi * a * i / nx + ph[0]) * np.cos(2 * np.pi * b * j / ny + ph[1])
+              * (1.0 + 0.5 * np.cos(np.pi * (k + 0.5) / nz + ph[2])))
+    g /= np.abs(g).max()
+    return rho0[:, None, None] * (1.0 + eps * g)

@@ -468,3 +468,82 @@ def test_dirichlet_top_rho0_gradient_matches_central_differences():
         rm[m] -= eps
         fd[m] = (loss(rp) - loss(rm)) / (2 * eps)
     assert np.abs(g - fd).max() <= 1e-6 * np.abs(g).max(), (g, fd)
+
+
+# ---------------------------------------------------------------------------
+# variable density (the operator the conjugate-gradient solver inverts)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bc", ["neumann", "dirichlet_top"])
+def test_variable_operator_reduces_to_L_for_level_density(bc):
+    d = wl.random_stretched(7, 6, 5, seed=31)
+    rho3 = d.rho0[:, None, None] * np.ones(d.S.shape)
+    W, a, c = O.vertical_coefficients(d.dz, d.rho0, bc)
+    Ap = O.apply_A_var(d.S, d.dx, d.dy, d.dz, rho3, bc)
+    assert np.abs(Ap - O.apply_L(d.S, d.dx, d.dy, a, c)).max() <= 1e-13 * np.abs(Ap).max()
+
+
+@pytest.mark.parametrize("bc", ["neumann", "dirichlet_top"])
+def test_variable_operator_structure(bc):
+    d = wl.random_stretched(6, 5, 6, seed=32)
+    rho3 = wl.perturbed_density(d.nx, d.ny, d.rho0, 0.4, seed=3)
+    W = O.weights_var(d.dz, rho3)
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal(d.S.shape)
+    v = rng.standard_normal(d.S.shape)
+    Av = O.apply_A_var(v, d.dx, d.dy, d.dz, rho3, bc)
+    Au = O.apply_A_var(u, d.dx, d.dy, d.dz, rho3, bc)
+    # W A is symmetric and negative (semi)definite
+    assert abs((u * W * Av).sum() - (W * Au * v).sum()) < 1e-12 * np.abs(u * W * Av).sum()
+    assert (v * W * Av).sum() < 0
+    if bc == "neumann":
+        assert abs((W * Av).sum()) < 1e-12 * np.abs(W * Av).sum()                 # conservation
+        assert np.abs(O.apply_A_var(np.full(d.S.shape, 2.0), d.dx, d.dy, d.dz, rho3)).max() < 1e-13
+
+
+@pytest.mark.parametrize("dims", [(6, 5, 4), (4, 4, 2), (8, 6, 3)])
+@pytest.mark.parametrize("bc", ["neumann", "dirichlet_top"])
+def test_variable_solve_reduces_to_fft_solve(dims, bc):
+    d = wl.random_stretched(*dims, seed=33)
+    rho3 = d.rho0[:, None, None] * np.ones(d.S.shape)
+    p = O.solve_var(d.S, d.dx, d.dy, d.dz, rho3, bc)
+    assert O.relative_l2(p, O.solve(d.S, d.dx, d.dy, d.dz, d.rho0, bc=bc)) < 1e-12
+
+
+def test_variable_solve_residual_and_mean():
+    d = wl.random_stretched(12, 10, 6, seed=34)
+    rho3 = wl.perturbed_density(d.nx, d.ny, d.rho0, 0.5, seed=4)
+    p = O.solve_var(d.S, d.dx, d.dy, d.dz, rho3)
+    W = O.weights_var(d.dz, rho3)
+    r = d.S - (W * d.S).sum() / W.sum() - O.apply_A_var(p, d.dx, d.dy, d.dz, rho3)
+    assert np.linalg.norm(r) < 1e-12 * np.linalg.norm(d.S)
+    assert abs(p.mean()) < 1e-14 * np.abs(p).mean()
+
+
+def test_variable_operator_converges_to_continuous_problem():
+    """Second-order convergence to (1/rho) div(rho grad p) with rho varying in x and z.
+
+    rho = exp(-z/Hs) (1 + 0.3 cos(kx x)), p = cos(kx x) cos(kz z), kz = pi/H (zero
+    flux at z = 0 and H); the source is the continuous operator at the centres,
+    made compatible by the discrete projection.  A face density that is not the
+    two-cell mean, or a missing 1/rho weighting, spoils the ratio.
+    """
+    Lx, H, Hs = 4000.0, 3000.0, 2500.0
+    kx, kz = 2 * np.pi / Lx, np.pi / H
+    errs = []
+    for n in (8, 16, 32, 64):
+        nx, nz = 2 * n, n
+        dx = Lx / nx
+        dz = _smooth_grid(nz, H, beta=1.0)
+        z = wl.cell_centres(dz)[:, None, None]
+        x = ((np.arange(nx) + 0.5) * dx)[None, None, :] * np.ones((1, 2, 1))
+        rho3 = np.exp(-z / Hs) * (1 + 0.3 * np.cos(kx * x)) * np.ones((nz, 2, nx))
+        p_ex = np.cos(kx * x) * np.cos(kz * z) * np.ones((nz, 2, nx))
+        dlnr_dx = -0.3 * kx * np.sin(kx * x) / (1 + 0.3 * np.cos(kx * x))
+        Ap = (-(kx**2 + kz**2) * p_ex + dlnr_dx * (-kx * np.sin(kx * x) * np.cos(kz * z))
+              + (-1 / Hs) * (-kz * np.cos(kx * x) * np.sin(kz * z)))
+        p = O.solve_var(Ap, dx, 1.0, dz, rho3)
+        ex = p_ex - p_ex.mean()
+        errs.append(np.abs(p - ex).max() / np.abs(ex).max())
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(ratios > 3.4) and np.all(ratios < 4.6), (errs, ratios)
