@@ -180,6 +180,35 @@ int poisson_solve(poisson_plan* plan, const void* S, void* p, void* workspace, v
 int poisson_solve_adjoint(poisson_plan* plan, const void* gp, const void* p, void* gS,
                           double* grho, void* workspace, void* stream);
 
+/* ---- Variable density: preconditioned conjugate gradients (the iterative route of Section 2.2) ----
+ * Solves  A p = S - mu_W  (zero plain mean; with p = 0 on the top face: A p = S) for a density
+ * rho3 that varies in x, y and z, which the Fourier transform cannot separate:
+ *   (A p)_ijk = (1/W_ijk) [ dz_k ((F^x_{i+1/2} - F^x_{i-1/2})/dx + (F^y_{j+1/2} - F^y_{j-1/2})/dy)
+ *                          + F^z_{k+1/2} - F^z_{k-1/2} ],   W_ijk = rho3_ijk dz_k,
+ *   F^x_{i+1/2} = (rho3_i + rho3_{i+1})/2 (p_{i+1} - p_i)/dx (periodic), F^y likewise,
+ *   F^z_{k+1/2} = (rho3_k + rho3_{k+1})/2 (p_{k+1} - p_k)/h_{k+1/2}; the plan's vertical boundary
+ *   condition at the bottom and top faces; mu_W = sum W S / sum W.  With rho3_ijk = rho0_k, A = L.
+ * Conjugate gradients on -W A (symmetric) in FP64, preconditioned by this plan's direct solve
+ * for its own rho0 profile (typically the horizontal mean of rho3); Polak-Ribiere directions.
+ * The plan must have double fields (POISSON_FP64 or POISSON_MIXED; MIXED with
+ * POISSON_OPT_MAX_SWEEPS = 0 is the cheapest preconditioner) and the default field layout.
+ * rho3, S, p: DEVICE double [nz][ny][nx]; rho3 > 0 (not checked); none may overlap each other or
+ * the workspace.  Stops when ||S - mu_W - A p||_2 / ||S||_2 <= tol or after max_iter iterations
+ * (POISSON_ERR_NOT_CONVERGED, p holds the last iterate).  Synchronises the stream a few times per
+ * iteration (the step lengths come back to the host, summed in a fixed order). */
+typedef struct {
+  int iterations;              /* CG iterations run */
+  int converged;               /* 1 if the relative residual reached tol */
+  double rel_residual;         /* ||S - mu_W - A p||_2 / ||S||_2 at exit */
+  double removed_weighted_mean;/* mu_W (0 with p = 0 on the top face) */
+} poisson_cg_info;
+
+/* Workspace bytes for poisson_cg_solve (the plan's own workspace plus five fields). */
+int poisson_cg_workspace_bytes(const poisson_plan* plan, size_t* bytes);
+
+int poisson_cg_solve(poisson_plan* plan, const double* rho3, const double* S, double* p, double tol,
+                     int max_iter, void* workspace, void* stream, poisson_cg_info* info);
+
 /* Sum of the recorded per-phase kernel times (milliseconds) and launch counts
  * since the last read, for phases 0..nphases-1 (host arrays); synchronises on
  * the recorded events and clears them.  Recording is off unless

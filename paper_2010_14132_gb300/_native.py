@@ -42,7 +42,7 @@ EXPORTED = (
     "poisson_last_error_detail", "poisson_batch_create", "poisson_batch_workspace_bytes", "poisson_batch_solve",
     "poisson_batch_destroy", "poisson_plan_profile_read", "poisson_solve_static_workspace",
     "poisson_pipe_create", "poisson_pipe_submit", "poisson_pipe_wait", "poisson_pipe_destroy",
-    "poisson_batch_plan",
+    "poisson_batch_plan", "poisson_cg_workspace_bytes", "poisson_cg_solve",
 )
 
 # size of the fixed device array poisson_solve_static_workspace uses as scratch
@@ -64,6 +64,19 @@ class PoissonInfo(C.Structure):
             "rel_update": list(self.rel_update), "error_estimate": self.error_estimate,
             "removed_weighted_mean": self.removed_weighted_mean,
         }
+
+
+class PoissonCgInfo(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int),
+        ("converged", C.c_int),
+        ("rel_residual", C.c_double),
+        ("removed_weighted_mean", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "converged": bool(self.converged),
+                "rel_residual": self.rel_residual, "removed_weighted_mean": self.removed_weighted_mean}
 
 
 class PoissonError(RuntimeError):
@@ -116,6 +129,8 @@ def load():
     L.poisson_pipe_submit.argtypes = [vp, vp, vp]
     L.poisson_pipe_wait.argtypes = [vp]
     L.poisson_pipe_destroy.argtypes = [vp]
+    L.poisson_cg_workspace_bytes.argtypes = [vp, C.POINTER(sz)]
+    L.poisson_cg_solve.argtypes = [vp, vp, vp, vp, d, i, vp, vp, C.POINTER(PoissonCgInfo)]
     for name in EXPORTED:
         if name not in ("poisson_status_string", "poisson_last_error_detail"):
             getattr(L, name).restype = C.c_int
@@ -261,3 +276,18 @@ def poisson_batch_plan(batch, i):
     out = C.c_void_p()
     _check(load().poisson_batch_plan(batch, int(i), C.byref(out)), "poisson_batch_plan")
     return out.value
+
+
+def poisson_cg_workspace_bytes(plan):
+    n = C.c_size_t(0)
+    _check(load().poisson_cg_workspace_bytes(plan, C.byref(n)), "poisson_cg_workspace_bytes")
+    return n.value
+
+
+def poisson_cg_solve(plan, rho_ptr, S_ptr, p_ptr, tol, max_iter, ws_ptr, stream, allow_not_converged=True):
+    """Returns (status, info dict)."""
+    info = PoissonCgInfo()
+    st = load().poisson_cg_solve(plan, rho_ptr, S_ptr, p_ptr, float(tol), int(max_iter), ws_ptr, stream,
+                                 C.byref(info))
+    _check(st, "poisson_cg_solve", allow=(POISSON_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return st, info.as_dict()

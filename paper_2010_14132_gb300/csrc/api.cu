@@ -772,6 +772,151 @@ int poisson_solve_adjoint(poisson_plan* pl, const void* gp, const void* p, void*
 }
 
 // ---------------------------------------------------------------------------
+// Preconditioned conjugate gradients for a density varying in x, y and z, with
+// this plan's direct solve (its rho0 profile) as the preconditioner.
+// ---------------------------------------------------------------------------
+struct CgLayout {
+  size_t off_r, off_d, off_q, off_t, off_z, off_part, bytes;
+};
+static CgLayout cg_layout(const poisson_plan* pl) {
+  CgLayout L{};
+  const size_t f = align256(sizeof(double) * (size_t)pl->g.N);
+  size_t off = align256(pl->ws_bytes);
+  L.off_r = off;
+  off += f;
+  L.off_d = off;
+  off += f;
+  L.off_q = off;
+  off += f;
+  L.off_t = off;
+  off += f;
+  L.off_z = off;
+  off += f;
+  L.off_part = off;
+  off += align256(2 * sizeof(double) * (size_t)cg_blocks());
+  L.bytes = off;
+  return L;
+}
+
+int poisson_cg_workspace_bytes(const poisson_plan* pl, size_t* bytes) {
+  if (!pl || !bytes) return POISSON_ERR_INVALID_ARG;
+  *bytes = cg_layout(pl).bytes;
+  return POISSON_OK;
+}
+
+// Sum the two-per-block partials of the last reduction on the host, in block order.
+static int cg_sums(const double* partials_dev, unsigned nb, cudaStream_t st, double* s0, double* s1) {
+  std::vector<double> h(2 * (size_t)nb);
+  PGB_CUDA(cudaMemcpyAsync(h.data(), partials_dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+  PGB_CUDA(cudaStreamSynchronize(st));
+  double a = 0, b = 0;
+  for (unsigned i = 0; i < nb; ++i) {
+    a += h[2 * i];
+    b += h[2 * i + 1];
+  }
+  *s0 = a;
+  if (s1) *s1 = b;
+  return POISSON_OK;
+}
+
+int poisson_cg_solve(poisson_plan* pl, const double* rho3, const double* S, double* p, double tol, int max_iter,
+                     void* workspace, void* stream, poisson_cg_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!pl || !rho3 || !S || !p) return POISSON_ERR_INVALID_ARG;
+  if (pl->dtype == POISSON_FP32 || pl->layout != POISSON_LAYOUT_Z_Y_X) return POISSON_ERR_UNSUPPORTED;
+  if (!(tol > 0) || max_iter < 1) return POISSON_ERR_INVALID_ARG;
+  int rc = check_ws(pl, workspace);
+  if (rc != POISSON_OK) return rc;
+  const CgLayout L = cg_layout(pl);
+  const size_t fbytes = sizeof(double) * (size_t)pl->g.N;
+  if (ranges_overlap(S, fbytes, p, fbytes) || ranges_overlap(rho3, fbytes, p, fbytes) ||
+      ranges_overlap(S, fbytes, workspace, L.bytes) || ranges_overlap(p, fbytes, workspace, L.bytes) ||
+      ranges_overlap(rho3, fbytes, workspace, L.bytes))
+    return POISSON_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  const CgKernels K = cg_kernels(pl->nx, pl->ny, pl->nz, pl->dx, pl->dy, pl->top_dirichlet());
+  const int nbmax = cg_blocks();
+  const unsigned nb = cg_grid(K, nbmax);
+  CgArgs a{};
+  a.rho = rho3;
+  a.S = S;
+  a.dz = pl->dz_d;
+  a.Wbar = pl->tb.W_d;
+  a.p = p;
+  a.r = (double*)(ws + L.off_r);
+  a.d = (double*)(ws + L.off_d);
+  a.q = (double*)(ws + L.off_q);
+  a.t = (double*)(ws + L.off_t);
+  a.z = (const double*)(ws + L.off_z);
+  a.partials = (double*)(ws + L.off_part);
+  double* z = (double*)(ws + L.off_z);
+  double s0 = 0, s1 = 0;
+  // compatibility: with zero flux at the top remove mu_W = sum W S / sum W
+  double mu = 0;
+  if (!pl->top_dirichlet()) {
+    PGB_CUDA(cg_launch(CG_WMEAN, K, a, nbmax, st));
+    if ((rc = cg_sums(a.partials, nb, st, &s0, &s1)) != POISSON_OK) return rc;
+    mu = s1 > 0 ? s0 / s1 : 0.0;
+  }
+  a.scalar = mu;
+  PGB_CUDA(cg_launch(CG_START, K, a, nbmax, st));
+  if ((rc = cg_sums(a.partials, nb, st, &s0, nullptr)) != POISSON_OK) return rc;
+  const double snorm = std::sqrt(s0);
+  double rel = snorm > 0 ? 1.0 : 0.0;
+  int it = 0;
+  bool conv = snorm == 0;
+  if (!conv) {
+    // z = M r, d = z, rz = r . z
+    if ((rc = solve_fields(pl, a.t, z, ws, st)) != POISSON_OK) return rc;
+    a.q = nullptr;
+    PGB_CUDA(cg_launch(CG_DOTS, K, a, nbmax, st));
+    a.q = (double*)(ws + L.off_q);
+    if ((rc = cg_sums(a.partials, nb, st, &s0, nullptr)) != POISSON_OK) return rc;
+    double rz = s0;
+    a.flag = 1;
+    PGB_CUDA(cg_launch(CG_DIR, K, a, nbmax, st));
+    a.flag = 0;
+    for (it = 1; it <= max_iter; ++it) {
+      PGB_CUDA(cg_launch(CG_APPLY, K, a, nbmax, st));
+      if ((rc = cg_sums(a.partials, nb, st, &s0, nullptr)) != POISSON_OK) return rc;
+      if (!(s0 > 0)) break;   // d in the null space (or a breakdown): nothing left to reduce
+      const double alpha = rz / s0;
+      a.scalar = alpha;
+      PGB_CUDA(cg_launch(CG_UPDATE, K, a, nbmax, st));
+      if ((rc = cg_sums(a.partials, nb, st, &s0, nullptr)) != POISSON_OK) return rc;
+      rel = std::sqrt(s0) / snorm;
+      if (rel <= tol) {
+        conv = true;
+        break;
+      }
+      if (it == max_iter) break;
+      if ((rc = solve_fields(pl, a.t, z, ws, st)) != POISSON_OK) return rc;
+      PGB_CUDA(cg_launch(CG_DOTS, K, a, nbmax, st));
+      if ((rc = cg_sums(a.partials, nb, st, &s0, &s1)) != POISSON_OK) return rc;
+      const double beta = -alpha * s1 / rz;   // Polak-Ribiere: z_new . (r_new - r_old) / (r_old . z_old)
+      rz = s0;
+      a.scalar = beta;
+      PGB_CUDA(cg_launch(CG_DIR, K, a, nbmax, st));
+    }
+    if (it > max_iter) it = max_iter;
+  }
+  if (!pl->top_dirichlet()) {   // plain mean zero, as the direct solve
+    PGB_CUDA(cg_launch(CG_SUM, K, a, nbmax, st));
+    if ((rc = cg_sums(a.partials, nb, st, &s0, nullptr)) != POISSON_OK) return rc;
+    a.scalar = s0 / (double)pl->g.N;
+    PGB_CUDA(cg_launch(CG_SHIFT, K, a, nbmax, st));
+  }
+  if (info) {
+    info->iterations = it;
+    info->converged = conv ? 1 : 0;
+    info->rel_residual = rel;
+    info->removed_weighted_mean = mu;
+  }
+  return conv ? POISSON_OK : POISSON_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
 // Batched solve: per-domain plans; the launch sequence of all domains is
 // captured once into a CUDA graph and replayed with one graph launch.
 // ---------------------------------------------------------------------------

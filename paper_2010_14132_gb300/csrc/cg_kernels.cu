@@ -1,0 +1,241 @@
+// Preconditioned conjugate gradients for a density that varies in x, y and z,
+// with the direct FFT solve as the preconditioner.  This is the iterative
+// alternative of Section 2.2 (a matrix-free CG whose cost per iteration is a
+// stencil application and a few vector updates, "post-conditioned" by a cheap
+// approximate inverse), for the case the direct method alone cannot handle: a
+// horizontally varying density does not separate under the Fourier transform.
+//
+// Operator (flux form, cell weights W_ijk = rho_ijk dz_k):
+//   (W A d)_ijk = dz_k [ (F^x_{i+1/2} - F^x_{i-1/2})/dx + (F^y_{j+1/2} - F^y_{j-1/2})/dy ]
+//               + F^z_{k+1/2} - F^z_{k-1/2},
+//   F^x_{i+1/2} = rho_{i+1/2} (d_{i+1} - d_i)/dx, rho_{i+1/2} = (rho_i + rho_{i+1})/2 (periodic);
+//   F^y likewise; F^z_{k+1/2} = rho_{k+1/2} (d_{k+1} - d_k)/h_{k+1/2}, zero at the bottom face and
+//   at the top face, or rho_{nz-1} (0 - d_{nz-1})/(dz_{nz-1}/2) with p = 0 on the top face.
+// CG runs on K = -W A (symmetric, positive semidefinite) with b = -W (S - mu_W); the
+// preconditioner is z = -G(r / Wbar): G is the plan's solve for the level density
+// rho0 (weights Wbar_k = rho0_k dz_k).  Polak-Ribiere beta = -alpha (q . z_new)/(r . z)
+// keeps the iteration robust to a preconditioner that is applied in reduced precision.
+// All vectors and reductions are FP64; the partial sums go to the host in block order.
+#include "kernels.cuh"
+
+namespace pgb {
+namespace {
+
+struct CgDims {
+  int nx, ny, nz;
+  long long plane, n;
+  double idx2, idy2;   // 1/dx^2, 1/dy^2
+  int top_dirichlet;
+};
+
+__device__ __forceinline__ void block_sum2(double a, double b, double* partials) {
+  __shared__ double s0[256], s1[256];
+  const int t = threadIdx.x;
+  s0[t] = a;
+  s1[t] = b;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h) {
+      s0[t] += s0[t + h];
+      s1[t] += s1[t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    partials[2 * blockIdx.x] = s0[0];
+    partials[2 * blockIdx.x + 1] = s1[0];
+  }
+}
+
+// q = K d = -(W A d); partials: d . q
+__global__ void __launch_bounds__(256) k_cg_apply(const double* __restrict__ rho, const double* __restrict__ d,
+                                                  double* __restrict__ q, const double* __restrict__ dz, CgDims D,
+                                                  double* __restrict__ partials) {
+  double acc = 0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < D.n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % D.nx);
+    const long long rj = idx / D.nx;
+    const int j = (int)(rj % D.ny), k = (int)(rj / D.ny);
+    const long long e = idx + (i + 1 == D.nx ? 1 - D.nx : 1), w = idx + (i == 0 ? D.nx - 1 : -1);
+    const long long nn = idx + (j + 1 == D.ny ? (1 - D.ny) * (long long)D.nx : D.nx);
+    const long long ss = idx + (j == 0 ? (D.ny - 1) * (long long)D.nx : -(long long)D.nx);
+    const double rc = rho[idx], dc = d[idx];
+    const double hx = D.idx2 * ((0.5 * (rc + rho[e])) * (d[e] - dc) - (0.5 * (rc + rho[w])) * (dc - d[w]));
+    const double hy = D.idy2 * ((0.5 * (rc + rho[nn])) * (d[nn] - dc) - (0.5 * (rc + rho[ss])) * (dc - d[ss]));
+    const double dzk = dz[k];
+    double fz_up = 0, fz_dn = 0;
+    if (k + 1 < D.nz) {
+      const long long u = idx + D.plane;
+      fz_up = (0.5 * (rc + rho[u])) * (d[u] - dc) / (0.5 * (dzk + dz[k + 1]));
+    } else if (D.top_dirichlet) {
+      fz_up = rc * (0.0 - dc) / (0.5 * dzk);
+    }
+    if (k > 0) {
+      const long long l = idx - D.plane;
+      fz_dn = (0.5 * (rc + rho[l])) * (dc - d[l]) / (0.5 * (dzk + dz[k - 1]));
+    }
+    const double Kd = -(dzk * (hx + hy) + (fz_up - fz_dn));
+    q[idx] = Kd;
+    acc += dc * Kd;
+  }
+  block_sum2(acc, 0.0, partials);
+}
+
+// r = b = -W (S - mu), p = 0, t = -r/Wbar (the preconditioner's source); partials: S . S
+__global__ void __launch_bounds__(256) k_cg_start(const double* __restrict__ rho, const double* __restrict__ S,
+                                                  double mu, double* __restrict__ r, double* __restrict__ p,
+                                                  double* __restrict__ t, const double* __restrict__ dz,
+                                                  const double* __restrict__ Wbar, CgDims D,
+                                                  double* __restrict__ partials) {
+  double ss = 0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < D.n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / D.plane);
+    const double s = S[idx];
+    const double b = -(rho[idx] * dz[k]) * (s - mu);
+    r[idx] = b;
+    p[idx] = 0.0;
+    t[idx] = -b / Wbar[k];
+    ss += s * s;
+  }
+  block_sum2(ss, 0.0, partials);
+}
+
+// partials: W S, W (for the compatibility projection mu_W = sum W S / sum W)
+__global__ void __launch_bounds__(256) k_cg_wmean(const double* __restrict__ rho, const double* __restrict__ S,
+                                                  const double* __restrict__ dz, CgDims D,
+                                                  double* __restrict__ partials) {
+  double ws = 0, w = 0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < D.n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double wk = rho[idx] * dz[(int)(idx / D.plane)];
+    ws += wk * S[idx];
+    w += wk;
+  }
+  block_sum2(ws, w, partials);
+}
+
+// p += alpha d, r -= alpha q, t = -r/Wbar; partials: (r/W)^2 (the residual of A p = S - mu)
+__global__ void __launch_bounds__(256) k_cg_update(const double* __restrict__ rho, double alpha,
+                                                   const double* __restrict__ d, const double* __restrict__ q,
+                                                   double* __restrict__ p, double* __restrict__ r,
+                                                   double* __restrict__ t, const double* __restrict__ dz,
+                                                   const double* __restrict__ Wbar, CgDims D,
+                                                   double* __restrict__ partials) {
+  double rr = 0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < D.n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / D.plane);
+    p[idx] += alpha * d[idx];
+    const double rn = r[idx] - alpha * q[idx];
+    r[idx] = rn;
+    t[idx] = -rn / Wbar[k];
+    const double ra = rn / (rho[idx] * dz[k]);
+    rr += ra * ra;
+  }
+  block_sum2(rr, 0.0, partials);
+}
+
+// partials: z . r, z . q
+__global__ void __launch_bounds__(256) k_cg_dots(const double* __restrict__ z, const double* __restrict__ r,
+                                                 const double* __restrict__ q, CgDims D,
+                                                 double* __restrict__ partials) {
+  double zr = 0, zq = 0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < D.n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double zv = z[idx];
+    zr += zv * r[idx];
+    if (q) zq += zv * q[idx];
+  }
+  block_sum2(zr, zq, partials);
+}
+
+// d = z + beta d (beta_is_zero: d = z, whatever d held)
+__global__ void __launch_bounds__(256) k_cg_dir(const double* __restrict__ z, double beta, int beta_is_zero,
+                                                double* __restrict__ d, long long n) {
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    d[idx] = beta_is_zero ? z[idx] : z[idx] + beta * d[idx];
+}
+
+// partials: sum p; then (second launch) p -= shift
+__global__ void __launch_bounds__(256) k_cg_sum(const double* __restrict__ p, long long n,
+                                                double* __restrict__ partials) {
+  double s = 0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    s += p[idx];
+  block_sum2(s, 0.0, partials);
+}
+__global__ void __launch_bounds__(256) k_cg_shift(double* __restrict__ p, double shift, long long n) {
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    p[idx] -= shift;
+}
+
+}  // namespace
+
+// Host side ---------------------------------------------------------------------
+
+int cg_blocks() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (sms > 0 ? sms : 1) * 8;
+}
+
+CgKernels cg_kernels(int nx, int ny, int nz, double dx, double dy, int top_dirichlet) {
+  CgKernels K{};
+  K.nx = nx;
+  K.ny = ny;
+  K.nz = nz;
+  K.idx2 = 1.0 / (dx * dx);
+  K.idy2 = 1.0 / (dy * dy);
+  K.top_dirichlet = top_dirichlet;
+  return K;
+}
+
+static CgDims dims_of(const CgKernels& K) {
+  CgDims D{};
+  D.nx = K.nx;
+  D.ny = K.ny;
+  D.nz = K.nz;
+  D.plane = (long long)K.nx * K.ny;
+  D.n = D.plane * K.nz;
+  D.idx2 = K.idx2;
+  D.idy2 = K.idy2;
+  D.top_dirichlet = K.top_dirichlet;
+  return D;
+}
+
+static unsigned grid_for(long long n, int nb) {
+  long long g = (n + 255) / 256;
+  if (g > nb) g = nb;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+cudaError_t cg_launch(int op, const CgKernels& K, const CgArgs& a, int nb, cudaStream_t st) {
+  const CgDims D = dims_of(K);
+  const unsigned g = grid_for(D.n, nb);
+  switch (op) {
+    case CG_WMEAN: k_cg_wmean<<<g, 256, 0, st>>>(a.rho, a.S, a.dz, D, a.partials); break;
+    case CG_START:
+      k_cg_start<<<g, 256, 0, st>>>(a.rho, a.S, a.scalar, a.r, a.p, a.t, a.dz, a.Wbar, D, a.partials);
+      break;
+    case CG_APPLY: k_cg_apply<<<g, 256, 0, st>>>(a.rho, a.d, a.q, a.dz, D, a.partials); break;
+    case CG_UPDATE:
+      k_cg_update<<<g, 256, 0, st>>>(a.rho, a.scalar, a.d, a.q, a.p, a.r, a.t, a.dz, a.Wbar, D, a.partials);
+      break;
+    case CG_DOTS: k_cg_dots<<<g, 256, 0, st>>>(a.z, a.r, a.q, D, a.partials); break;
+    case CG_DIR: k_cg_dir<<<g, 256, 0, st>>>(a.z, a.scalar, a.flag, a.d, D.n); break;
+    case CG_SUM: k_cg_sum<<<g, 256, 0, st>>>(a.p, D.n, a.partials); break;
+    case CG_SHIFT: k_cg_shift<<<g, 256, 0, st>>>(a.p, a.scalar, D.n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+unsigned cg_grid(const CgKernels& K, int nb) { return grid_for((long long)K.nx * K.ny * K.nz, nb); }
+
+}  // namespace pgb

@@ -162,6 +162,33 @@ cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long lo
                              cudaStream_t st);
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
                            double tol, long long npoints, cudaStream_t st);
+// Conjugate gradients for a density varying in x, y and z (cg_kernels.cu).
+enum CgOp { CG_WMEAN = 0, CG_START, CG_APPLY, CG_UPDATE, CG_DOTS, CG_DIR, CG_SUM, CG_SHIFT };
+struct CgKernels {
+  int nx, ny, nz;
+  double idx2, idy2;
+  int top_dirichlet;
+};
+struct CgArgs {
+  const double* rho;    // [nz][ny][nx] density
+  const double* S;      // source
+  const double* dz;     // level thicknesses (device)
+  const double* Wbar;   // preconditioner's level weights rho0_k dz_k (device)
+  double* p;            // iterate
+  double* r;            // residual of K p = b
+  double* d;            // search direction
+  double* q;            // K d
+  double* t;            // preconditioner source -r/Wbar
+  const double* z;      // preconditioned residual
+  double* partials;     // 2 doubles per block
+  double scalar;        // mu, alpha, beta or shift
+  int flag;             // CG_DIR: beta is zero
+};
+CgKernels cg_kernels(int nx, int ny, int nz, double dx, double dy, int top_dirichlet);
+cudaError_t cg_launch(int op, const CgKernels& K, const CgArgs& a, int nb, cudaStream_t st);
+int cg_blocks();
+unsigned cg_grid(const CgKernels& K, int nb);
+
 // dst[b][m][a] = src[a][m][b]: [nx][ny][nz] <-> [nz][ny][nx] field layouts (elem_bytes 4 or 8).
 cudaError_t launch_swap_outer_inner(const void* src, void* dst, int A, int M, int B, int elem_bytes,
                                     cudaStream_t st);

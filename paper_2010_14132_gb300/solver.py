@@ -173,6 +173,32 @@ class Plan:
         return gS, grho
 
 
+    # -- variable density (preconditioned conjugate gradients) ------------------
+    def cg_solve(self, rho3: torch.Tensor, S: torch.Tensor, out: torch.Tensor | None = None, tol: float = 1e-10,
+                 max_iter: int = 50, stream=None):
+        """p with A(rho3) p = S - mu_W for a density varying in x, y and z.
+
+        Conjugate gradients in FP64, preconditioned by this plan's direct solve for
+        its own rho0 profile (create the plan with the horizontal mean of rho3).
+        Needs a "fp64" or "mixed" plan with the default layout.  Returns (p, info).
+        """
+        if self.layout != "zyx" or self.dtype == "fp32":
+            raise ValueError("cg_solve needs a fp64 or mixed plan with the default layout")
+        shape = (self.nz, self.ny, self.nx)
+        _require_cuda(rho3, torch.float64, shape, "rho3")
+        _require_cuda(S, torch.float64, shape, "S")
+        p = out if out is not None else torch.empty_like(S)
+        _require_cuda(p, torch.float64, shape, "out")
+        nb = N.poisson_cg_workspace_bytes(self._h)
+        if getattr(self, "_cg_ws", None) is None or self._cg_ws.numel() < nb + 256:
+            self._cg_ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        ptr = self._cg_ws.data_ptr()
+        ptr += (-ptr) % 256
+        _, info = N.poisson_cg_solve(self._h, rho3.data_ptr(), S.data_ptr(), p.data_ptr(), tol, max_iter, ptr,
+                                     _stream_handle(stream))
+        return p, info
+
+
 class PoissonSolve(torch.autograd.Function):
     """p = G(rho0) S as a differentiable op (gradients w.r.t. S and rho0).
 
