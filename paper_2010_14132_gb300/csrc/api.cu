@@ -776,7 +776,7 @@ int poisson_solve_adjoint(poisson_plan* pl, const void* gp, const void* p, void*
 // this plan's direct solve (its rho0 profile) as the preconditioner.
 // ---------------------------------------------------------------------------
 struct CgLayout {
-  size_t off_r, off_d, off_q, off_t, off_z, off_part, bytes;
+  size_t off_r, off_d, off_q, off_t, off_z, off_part, off_lv, bytes;
 };
 static CgLayout cg_layout(const poisson_plan* pl) {
   CgLayout L{};
@@ -794,6 +794,8 @@ static CgLayout cg_layout(const poisson_plan* pl) {
   off += f;
   L.off_part = off;
   off += align256(2 * sizeof(double) * (size_t)cg_blocks());
+  L.off_lv = off;
+  off += align256(sizeof(CgLevel) * (size_t)pl->nz);
   L.bytes = off;
   return L;
 }
@@ -842,7 +844,26 @@ int poisson_cg_solve(poisson_plan* pl, const double* rho3, const double* S, doub
   a.rho = rho3;
   a.S = S;
   a.dz = pl->dz_d;
-  a.Wbar = pl->tb.W_d;
+  {
+    // per-level constants; the preconditioner's weights come from the plan's device table (set_rho0)
+    const int nz = pl->nz;
+    std::vector<double> Wb(nz);
+    PGB_CUDA(cudaMemcpyAsync(Wb.data(), pl->tb.W_d, sizeof(double) * nz, cudaMemcpyDeviceToHost, st));
+    PGB_CUDA(cudaStreamSynchronize(st));
+    std::vector<CgLevel> lv(nz);
+    for (int k = 0; k < nz; ++k) {
+      const double dzk = pl->dz[k];
+      lv[k].dz = dzk;
+      lv[k].idz = 1.0 / dzk;
+      lv[k].hup = (k + 1 < nz) ? 0.5 / (0.5 * (dzk + pl->dz[k + 1])) : (pl->top_dirichlet() ? 1.0 / (0.5 * dzk) : 0.0);
+      lv[k].hdn = (k > 0) ? 0.5 / (0.5 * (dzk + pl->dz[k - 1])) : 0.0;
+      lv[k].iwbar = 1.0 / Wb[k];
+    }
+    CgLevel* lv_d = (CgLevel*)(ws + L.off_lv);
+    PGB_CUDA(cudaMemcpyAsync(lv_d, lv.data(), sizeof(CgLevel) * nz, cudaMemcpyHostToDevice, st));
+    PGB_CUDA(cudaStreamSynchronize(st));   // lv is a local vector
+    a.lv = lv_d;
+  }
   a.p = p;
   a.r = (double*)(ws + L.off_r);
   a.d = (double*)(ws + L.off_d);

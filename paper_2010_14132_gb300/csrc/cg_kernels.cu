@@ -16,6 +16,9 @@
 // rho0 (weights Wbar_k = rho0_k dz_k).  Polak-Ribiere beta = -alpha (q . z_new)/(r . z)
 // keeps the iteration robust to a preconditioner that is applied in reduced precision.
 // All vectors and reductions are FP64; the partial sums go to the host in block order.
+// The FP64 pipe (1/65 of the FP32 rate here) bounds these kernels, so no FP64
+// division runs per point: the level reciprocals come from small tables, and the
+// residual's weight 1/rho (needed only for the stopping test) is a float reciprocal.
 #include "kernels.cuh"
 
 namespace pgb {
@@ -24,7 +27,7 @@ namespace {
 struct CgDims {
   int nx, ny, nz;
   long long plane, n;
-  double idx2, idy2;   // 1/dx^2, 1/dy^2
+  double hx2, hy2;     // 0.5/dx^2, 0.5/dy^2 (the 0.5 of the face-density mean folded in)
   int top_dirichlet;
 };
 
@@ -47,37 +50,42 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* partials)
   }
 }
 
-// q = K d = -(W A d); partials: d . q
+// q = K d = -(W A d); partials: d . q.  Level tables: hup[k] = 0.5/h_{k+1/2} (top: 2/dz with p = 0
+// on the top face, which multiplies rho_k alone), hdn[k] = 0.5/h_{k-1/2} (0 at the bottom).
 __global__ void __launch_bounds__(256) k_cg_apply(const double* __restrict__ rho, const double* __restrict__ d,
-                                                  double* __restrict__ q, const double* __restrict__ dz, CgDims D,
+                                                  double* __restrict__ q, const double* __restrict__ dz,
+                                                  const CgLevel* __restrict__ lv, CgDims D,
                                                   double* __restrict__ partials) {
   double acc = 0;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < D.n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % D.nx);
-    const long long rj = idx / D.nx;
-    const int j = (int)(rj % D.ny), k = (int)(rj / D.ny);
+  const long long rows = (long long)D.nz * D.ny;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {   // one x row per block step
+    const int k = (int)(row / D.ny), j = (int)(row - (long long)k * D.ny);
+    const long long base = row * D.nx;
+    const long long dn_ = (j + 1 == D.ny ? (1 - D.ny) * (long long)D.nx : D.nx);
+    const long long ds_ = (j == 0 ? (D.ny - 1) * (long long)D.nx : -(long long)D.nx);
+    const CgLevel L = lv[k];
+  for (int i = threadIdx.x; i < D.nx; i += blockDim.x) {
+    const long long idx = base + i;
     const long long e = idx + (i + 1 == D.nx ? 1 - D.nx : 1), w = idx + (i == 0 ? D.nx - 1 : -1);
-    const long long nn = idx + (j + 1 == D.ny ? (1 - D.ny) * (long long)D.nx : D.nx);
-    const long long ss = idx + (j == 0 ? (D.ny - 1) * (long long)D.nx : -(long long)D.nx);
+    const long long nn = idx + dn_, ss = idx + ds_;
     const double rc = rho[idx], dc = d[idx];
-    const double hx = D.idx2 * ((0.5 * (rc + rho[e])) * (d[e] - dc) - (0.5 * (rc + rho[w])) * (dc - d[w]));
-    const double hy = D.idy2 * ((0.5 * (rc + rho[nn])) * (d[nn] - dc) - (0.5 * (rc + rho[ss])) * (dc - d[ss]));
-    const double dzk = dz[k];
-    double fz_up = 0, fz_dn = 0;
+    const double hx = D.hx2 * ((rc + rho[e]) * (d[e] - dc) - (rc + rho[w]) * (dc - d[w]));
+    const double hy = D.hy2 * ((rc + rho[nn]) * (d[nn] - dc) - (rc + rho[ss]) * (dc - d[ss]));
+    double fz = 0;
     if (k + 1 < D.nz) {
       const long long u = idx + D.plane;
-      fz_up = (0.5 * (rc + rho[u])) * (d[u] - dc) / (0.5 * (dzk + dz[k + 1]));
+      fz = (rc + rho[u]) * (d[u] - dc) * L.hup;
     } else if (D.top_dirichlet) {
-      fz_up = rc * (0.0 - dc) / (0.5 * dzk);
+      fz = rc * (0.0 - dc) * L.hup;
     }
     if (k > 0) {
       const long long l = idx - D.plane;
-      fz_dn = (0.5 * (rc + rho[l])) * (dc - d[l]) / (0.5 * (dzk + dz[k - 1]));
+      fz -= (rc + rho[l]) * (dc - d[l]) * L.hdn;
     }
-    const double Kd = -(dzk * (hx + hy) + (fz_up - fz_dn));
+    const double Kd = -(L.dz * (hx + hy) + fz);
     q[idx] = Kd;
     acc += dc * Kd;
+  }
   }
   block_sum2(acc, 0.0, partials);
 }
@@ -86,18 +94,21 @@ __global__ void __launch_bounds__(256) k_cg_apply(const double* __restrict__ rho
 __global__ void __launch_bounds__(256) k_cg_start(const double* __restrict__ rho, const double* __restrict__ S,
                                                   double mu, double* __restrict__ r, double* __restrict__ p,
                                                   double* __restrict__ t, const double* __restrict__ dz,
-                                                  const double* __restrict__ Wbar, CgDims D,
+                                                  const CgLevel* __restrict__ lv, CgDims D,
                                                   double* __restrict__ partials) {
   double ss = 0;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < D.n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(idx / D.plane);
-    const double s = S[idx];
-    const double b = -(rho[idx] * dz[k]) * (s - mu);
-    r[idx] = b;
-    p[idx] = 0.0;
-    t[idx] = -b / Wbar[k];
-    ss += s * s;
+  const long long rows = (long long)D.nz * D.ny;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const CgLevel L = lv[(int)(row / D.ny)];
+    for (int i = threadIdx.x; i < D.nx; i += blockDim.x) {
+      const long long idx = row * D.nx + i;
+      const double s = S[idx];
+      const double b = -(rho[idx] * L.dz) * (s - mu);
+      r[idx] = b;
+      p[idx] = 0.0;
+      t[idx] = -b * L.iwbar;
+      ss += s * s;
+    }
   }
   block_sum2(ss, 0.0, partials);
 }
@@ -107,11 +118,15 @@ __global__ void __launch_bounds__(256) k_cg_wmean(const double* __restrict__ rho
                                                   const double* __restrict__ dz, CgDims D,
                                                   double* __restrict__ partials) {
   double ws = 0, w = 0;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < D.n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const double wk = rho[idx] * dz[(int)(idx / D.plane)];
-    ws += wk * S[idx];
-    w += wk;
+  const long long rows = (long long)D.nz * D.ny;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const double dzk = dz[(int)(row / D.ny)];
+    for (int i = threadIdx.x; i < D.nx; i += blockDim.x) {
+      const long long idx = row * D.nx + i;
+      const double wk = rho[idx] * dzk;
+      ws += wk * S[idx];
+      w += wk;
+    }
   }
   block_sum2(ws, w, partials);
 }
@@ -120,19 +135,22 @@ __global__ void __launch_bounds__(256) k_cg_wmean(const double* __restrict__ rho
 __global__ void __launch_bounds__(256) k_cg_update(const double* __restrict__ rho, double alpha,
                                                    const double* __restrict__ d, const double* __restrict__ q,
                                                    double* __restrict__ p, double* __restrict__ r,
-                                                   double* __restrict__ t, const double* __restrict__ dz,
-                                                   const double* __restrict__ Wbar, CgDims D,
+                                                   double* __restrict__ t, const CgLevel* __restrict__ lv, CgDims D,
                                                    double* __restrict__ partials) {
   double rr = 0;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < D.n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(idx / D.plane);
+  const long long rows = (long long)D.nz * D.ny;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const CgLevel L = lv[(int)(row / D.ny)];
+  for (int i = threadIdx.x; i < D.nx; i += blockDim.x) {
+    const long long idx = row * D.nx + i;
     p[idx] += alpha * d[idx];
     const double rn = r[idx] - alpha * q[idx];
     r[idx] = rn;
-    t[idx] = -rn / Wbar[k];
-    const double ra = rn / (rho[idx] * dz[k]);
+    t[idx] = -rn * L.iwbar;
+    // residual of A p = S - mu: r / (rho dz), weighted to float accuracy (a stopping test)
+    const double ra = rn * L.idz * (double)__frcp_rn((float)rho[idx]);
     rr += ra * ra;
+  }
   }
   block_sum2(rr, 0.0, partials);
 }
@@ -203,29 +221,33 @@ static CgDims dims_of(const CgKernels& K) {
   D.nz = K.nz;
   D.plane = (long long)K.nx * K.ny;
   D.n = D.plane * K.nz;
-  D.idx2 = K.idx2;
-  D.idy2 = K.idy2;
+  D.hx2 = 0.5 * K.idx2;
+  D.hy2 = 0.5 * K.idy2;
   D.top_dirichlet = K.top_dirichlet;
   return D;
 }
 
+// the row kernels step over x rows, the flat ones over points
 static unsigned grid_for(long long n, int nb) {
   long long g = (n + 255) / 256;
   if (g > nb) g = nb;
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// blocks of every CG kernel: one x row per block step (at most nb blocks)
+unsigned cg_grid(const CgKernels& K, int nb) { return grid_for((long long)K.nz * K.ny * 256, nb); }
+
 cudaError_t cg_launch(int op, const CgKernels& K, const CgArgs& a, int nb, cudaStream_t st) {
   const CgDims D = dims_of(K);
-  const unsigned g = grid_for(D.n, nb);
+  const unsigned g = cg_grid(K, nb), gr = g;   // every kernel: the same grid, so the host sums g partials
   switch (op) {
-    case CG_WMEAN: k_cg_wmean<<<g, 256, 0, st>>>(a.rho, a.S, a.dz, D, a.partials); break;
+    case CG_WMEAN: k_cg_wmean<<<gr, 256, 0, st>>>(a.rho, a.S, a.dz, D, a.partials); break;
     case CG_START:
-      k_cg_start<<<g, 256, 0, st>>>(a.rho, a.S, a.scalar, a.r, a.p, a.t, a.dz, a.Wbar, D, a.partials);
+      k_cg_start<<<gr, 256, 0, st>>>(a.rho, a.S, a.scalar, a.r, a.p, a.t, a.dz, a.lv, D, a.partials);
       break;
-    case CG_APPLY: k_cg_apply<<<g, 256, 0, st>>>(a.rho, a.d, a.q, a.dz, D, a.partials); break;
+    case CG_APPLY: k_cg_apply<<<gr, 256, 0, st>>>(a.rho, a.d, a.q, a.dz, a.lv, D, a.partials); break;
     case CG_UPDATE:
-      k_cg_update<<<g, 256, 0, st>>>(a.rho, a.scalar, a.d, a.q, a.p, a.r, a.t, a.dz, a.Wbar, D, a.partials);
+      k_cg_update<<<gr, 256, 0, st>>>(a.rho, a.scalar, a.d, a.q, a.p, a.r, a.t, a.lv, D, a.partials);
       break;
     case CG_DOTS: k_cg_dots<<<g, 256, 0, st>>>(a.z, a.r, a.q, D, a.partials); break;
     case CG_DIR: k_cg_dir<<<g, 256, 0, st>>>(a.z, a.scalar, a.flag, a.d, D.n); break;
@@ -236,6 +258,6 @@ cudaError_t cg_launch(int op, const CgKernels& K, const CgArgs& a, int nb, cudaS
   return cudaGetLastError();
 }
 
-unsigned cg_grid(const CgKernels& K, int nb) { return grid_for((long long)K.nx * K.ny * K.nz, nb); }
+
 
 }  // namespace pgb

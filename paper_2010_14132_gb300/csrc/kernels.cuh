@@ -164,6 +164,13 @@ cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, i
                            double tol, long long npoints, cudaStream_t st);
 // Conjugate gradients for a density varying in x, y and z (cg_kernels.cu).
 enum CgOp { CG_WMEAN = 0, CG_START, CG_APPLY, CG_UPDATE, CG_DOTS, CG_DIR, CG_SUM, CG_SHIFT };
+struct CgLevel {      // per-level constants, so that no FP64 division runs per point
+  double dz;          // dz_k
+  double idz;         // 1/dz_k
+  double hup;         // 0.5/h_{k+1/2}; at the top 2/dz_k with p = 0 on the face, else 0
+  double hdn;         // 0.5/h_{k-1/2}; 0 at the bottom
+  double iwbar;       // 1/(rho0_k dz_k), the preconditioner's weight
+};
 struct CgKernels {
   int nx, ny, nz;
   double idx2, idy2;
@@ -173,7 +180,7 @@ struct CgArgs {
   const double* rho;    // [nz][ny][nx] density
   const double* S;      // source
   const double* dz;     // level thicknesses (device)
-  const double* Wbar;   // preconditioner's level weights rho0_k dz_k (device)
+  const CgLevel* lv;    // per-level constants (device, nz entries)
   double* p;            // iterate
   double* r;            // residual of K p = b
   double* d;            // search direction
