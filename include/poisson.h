@@ -1,7 +1,7 @@
 /*
  * poisson.h -- C ABI of the GB300 direct FFT pressure solver.
  *
- * The solver computes the pressure p of the Poisson-like elliptic equation that
+ * The solver computes the pressure p of the elliptic pressure equation of Poisson type that
  * a dynamical core solves every timestep (Brown, "A comparison of techniques
  * for solving the Poisson equation in CFD", Section 2), by the direct method of
  * Section 2.1: a forward real Fourier transform over the periodic x/y plane at

@@ -9,7 +9,7 @@ What it computes (Brown, "A comparison of techniques for solving the Poisson
 equation in CFD", Section 2.1): a forward Fourier transform over the periodic
 x/y plane at every level, an independent vertical tridiagonal solve per
 (kx, ky) column, and a backward transform that gives the pressure.  The paper
-names a "Poisson-like elliptic equation" (Section 2) and nabla^2 x = b
+names an elliptic equation of Poisson type (Section 2) and nabla^2 x = b
 (Section 2.2) but prints no discretisation, so this module fixes one reading,
 listed in the design notes:
 
@@ -30,7 +30,11 @@ rho_top (0 - p_{nz-1}) / (dz_{nz-1}/2) with rho_top = rho0[nz-1] (the paper give
 densities at centres only), so c_{nz-1} = rho_top / (W_{nz-1} dz_{nz-1}/2).  L is
 then nonsingular and the solution is p = L^{-1} S: no projection, no pinning.
 
-The solve is exact ("provides the exact solution every time", Section 3), so
+For the iterative alternative (Section 2.2) with a density that also varies in x
+and y, apply_A_var and solve_var give the flux-form operator and a library sparse
+direct solve of it on moderate grids.
+
+The solve is exact (Section 3 calls it a direct method that solves the system exactly each time), so
 the oracle is that definition written out: a naive O(n^2) DFT per line built
 from exactly index-reduced twiddles (matrix products are the library step), the
 textbook Thomas recurrence per column, a dense bordered solve for the singular

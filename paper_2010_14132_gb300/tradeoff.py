@@ -13,7 +13,7 @@ The direct solve has no termination residual, but it has a precision ladder:
 
 For each rung this reports the time per solve (CUDA events on the solving
 stream, inputs resident, median over repetitions), the mean |p - p_fp64| per
-element (the paper's "mean difference"), the relative L2 difference, and the
+element (the paper's mean-difference column), the relative L2 difference, and the
 sweeps and update estimate the library reported.  The FP64 GPU solution is the
 reference here; it matches the FP64 CPU oracle to 1e-12 relative L2 in the
 parity tests.
