@@ -188,7 +188,8 @@ int poisson_solve_adjoint(poisson_plan* plan, const void* gp, const void* p, voi
  *   F^x_{i+1/2} = (rho3_i + rho3_{i+1})/2 (p_{i+1} - p_i)/dx (periodic), F^y likewise,
  *   F^z_{k+1/2} = (rho3_k + rho3_{k+1})/2 (p_{k+1} - p_k)/h_{k+1/2}; the plan's vertical boundary
  *   condition at the bottom and top faces; mu_W = sum W S / sum W.  With rho3_ijk = rho0_k, A = L.
- * Conjugate gradients on -W A (symmetric) in FP64, preconditioned by this plan's direct solve
+ * Conjugate gradients on -W A (symmetric): FP64 vectors and reductions, the operator applied in
+ * double-float arithmetic (face coefficients formed once per call), preconditioned by this plan's direct solve
  * for its own rho0 profile (typically the horizontal mean of rho3); Polak-Ribiere directions.
  * The plan must have double fields (POISSON_FP64 or POISSON_MIXED; MIXED with
  * POISSON_OPT_MAX_SWEEPS = 0 is the cheapest preconditioner) and the default field layout.
@@ -203,7 +204,8 @@ typedef struct {
   double removed_weighted_mean;/* mu_W (0 with p = 0 on the top face) */
 } poisson_cg_info;
 
-/* Workspace bytes for poisson_cg_solve (the plan's own workspace plus five fields). */
+/* Workspace bytes for poisson_cg_solve (the plan's own workspace, five double fields and the
+ * operator's three face-coefficient fields as float pairs). */
 int poisson_cg_workspace_bytes(const poisson_plan* plan, size_t* bytes);
 
 int poisson_cg_solve(poisson_plan* plan, const double* rho3, const double* S, double* p, double tol,

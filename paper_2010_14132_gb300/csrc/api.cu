@@ -776,7 +776,7 @@ int poisson_solve_adjoint(poisson_plan* pl, const void* gp, const void* p, void*
 // this plan's direct solve (its rho0 profile) as the preconditioner.
 // ---------------------------------------------------------------------------
 struct CgLayout {
-  size_t off_r, off_d, off_q, off_t, off_z, off_part, off_lv, bytes;
+  size_t off_r, off_d, off_q, off_t, off_z, off_part, off_lv, off_ce, off_cn, off_cu, bytes;
 };
 static CgLayout cg_layout(const poisson_plan* pl) {
   CgLayout L{};
@@ -796,6 +796,13 @@ static CgLayout cg_layout(const poisson_plan* pl) {
   off += align256(2 * sizeof(double) * (size_t)cg_blocks());
   L.off_lv = off;
   off += align256(sizeof(CgLevel) * (size_t)pl->nz);
+  const size_t fc = align256(sizeof(float2) * (size_t)pl->g.N);   // face coefficients as float pairs
+  L.off_ce = off;
+  off += fc;
+  L.off_cn = off;
+  off += fc;
+  L.off_cu = off;
+  off += fc;
   L.bytes = off;
   return L;
 }
@@ -864,6 +871,10 @@ int poisson_cg_solve(poisson_plan* pl, const double* rho3, const double* S, doub
     PGB_CUDA(cudaStreamSynchronize(st));   // lv is a local vector
     a.lv = lv_d;
   }
+  a.ce = (float2*)(ws + L.off_ce);
+  a.cn = (float2*)(ws + L.off_cn);
+  a.cu = (float2*)(ws + L.off_cu);
+  PGB_CUDA(cg_launch(CG_FACES, K, a, nbmax, st));
   a.p = p;
   a.r = (double*)(ws + L.off_r);
   a.d = (double*)(ws + L.off_d);

@@ -16,10 +16,15 @@
 // rho0 (weights Wbar_k = rho0_k dz_k).  Polak-Ribiere beta = -alpha (q . z_new)/(r . z)
 // keeps the iteration robust to a preconditioner that is applied in reduced precision.
 // All vectors and reductions are FP64; the partial sums go to the host in block order.
-// The FP64 pipe (1/65 of the FP32 rate here) bounds these kernels, so no FP64
+// The FP64 pipe (1/65 of the FP32 rate here) would bound these kernels, so no FP64
 // division runs per point: the level reciprocals come from small tables, and the
 // residual's weight 1/rho (needed only for the stopping test) is a float reciprocal.
+// The operator itself runs in double-float arithmetic: its six face coefficients are
+// formed once per solve in FP64 and stored as float pairs, and each application
+// splits the FP64 direction into float pairs with integer operations and forms
+// sum_f c_f (d_f - d_c) with error-free transformations, differences first.
 #include "kernels.cuh"
+#include "residual2.cuh"
 
 namespace pgb {
 namespace {
@@ -50,12 +55,51 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* partials)
   }
 }
 
-// q = K d = -(W A d); partials: d . q.  Level tables: hup[k] = 0.5/h_{k+1/2} (top: 2/dz with p = 0
-// on the top face, which multiplies rho_k alone), hdn[k] = 0.5/h_{k-1/2} (0 at the bottom).
-__global__ void __launch_bounds__(256) k_cg_apply(const double* __restrict__ rho, const double* __restrict__ d,
-                                                  double* __restrict__ q, const double* __restrict__ dz,
-                                                  const CgLevel* __restrict__ lv, CgDims D,
-                                                  double* __restrict__ partials) {
+// Face coefficients of W A, once per solve, as float pairs (hi, lo):
+//   ce = 0.5/dx^2 (rho_i + rho_{i+1}) dz_k (east face), cn = 0.5/dy^2 (rho_j + rho_{j+1}) dz_k (north),
+//   cu = (rho_k + rho_{k+1}) 0.5/h_{k+1/2} (upper; at the top rho_k 2/dz_k with p = 0 on the face, else 0).
+__device__ __forceinline__ float2 split_rn(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+__global__ void __launch_bounds__(256) k_cg_faces(const double* __restrict__ rho, float2* __restrict__ ce,
+                                                  float2* __restrict__ cn, float2* __restrict__ cu,
+                                                  const CgLevel* __restrict__ lv, CgDims D) {
+  const long long rows = (long long)D.nz * D.ny;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int k = (int)(row / D.ny), j = (int)(row - (long long)k * D.ny);
+    const CgLevel L = lv[k];
+    const long long base = row * D.nx;
+    const long long dn_ = (j + 1 == D.ny ? (1 - D.ny) * (long long)D.nx : D.nx);
+    for (int i = threadIdx.x; i < D.nx; i += blockDim.x) {
+      const long long idx = base + i;
+      const long long e = idx + (i + 1 == D.nx ? 1 - D.nx : 1);
+      const double rc = rho[idx];
+      ce[idx] = split_rn(D.hx2 * (rc + rho[e]) * L.dz);
+      cn[idx] = split_rn(D.hy2 * (rc + rho[idx + dn_]) * L.dz);
+      double up = 0.0;
+      if (k + 1 < D.nz) up = (rc + rho[idx + D.plane]) * L.hup;
+      else if (D.top_dirichlet) up = rc * L.hup;
+      cu[idx] = split_rn(up);
+    }
+  }
+}
+
+// c (d_f - d_c) as an unnormalised float pair (ph, pl): the difference of the split values first
+// (exact high part), then the product with the split coefficient (exact high product).
+__device__ __forceinline__ void face_term(float fh, float fl, float ch, float cl, float2 c, float& ph, float& pl) {
+  float s, e;
+  two_sum(fh, -ch, s, e);
+  const float lo = e + (fl - cl);
+  two_prod(c.x, s, ph, pl);
+  pl = __fmaf_rn(c.x, lo, __fmaf_rn(c.y, s, pl));
+}
+
+// q = K d = -(W A d) = -sum_f c_f (d_f - d_c); partials: d . q
+__global__ void __launch_bounds__(256) k_cg_apply(const double* __restrict__ d, const float2* __restrict__ ce,
+                                                  const float2* __restrict__ cn, const float2* __restrict__ cu,
+                                                  double* __restrict__ q, CgDims D, double* __restrict__ partials) {
   double acc = 0;
   const long long rows = (long long)D.nz * D.ny;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {   // one x row per block step
@@ -63,29 +107,35 @@ __global__ void __launch_bounds__(256) k_cg_apply(const double* __restrict__ rho
     const long long base = row * D.nx;
     const long long dn_ = (j + 1 == D.ny ? (1 - D.ny) * (long long)D.nx : D.nx);
     const long long ds_ = (j == 0 ? (D.ny - 1) * (long long)D.nx : -(long long)D.nx);
-    const CgLevel L = lv[k];
-  for (int i = threadIdx.x; i < D.nx; i += blockDim.x) {
-    const long long idx = base + i;
-    const long long e = idx + (i + 1 == D.nx ? 1 - D.nx : 1), w = idx + (i == 0 ? D.nx - 1 : -1);
-    const long long nn = idx + dn_, ss = idx + ds_;
-    const double rc = rho[idx], dc = d[idx];
-    const double hx = D.hx2 * ((rc + rho[e]) * (d[e] - dc) - (rc + rho[w]) * (dc - d[w]));
-    const double hy = D.hy2 * ((rc + rho[nn]) * (d[nn] - dc) - (rc + rho[ss]) * (dc - d[ss]));
-    double fz = 0;
-    if (k + 1 < D.nz) {
-      const long long u = idx + D.plane;
-      fz = (rc + rho[u]) * (d[u] - dc) * L.hup;
-    } else if (D.top_dirichlet) {
-      fz = rc * (0.0 - dc) * L.hup;
+    const bool has_up = k + 1 < D.nz, has_dn = k > 0;
+    for (int i = threadIdx.x; i < D.nx; i += blockDim.x) {
+      const long long idx = base + i;
+      const long long w = idx + (i == 0 ? D.nx - 1 : -1), e = idx + (i + 1 == D.nx ? 1 - D.nx : 1);
+      const double dc = d[idx];
+      float ch, cl;
+      d2ff_trunc(dc, ch, cl);
+      float H = 0.f, Lo = 0.f;
+      auto add = [&](double df, float2 c) {
+        float fh, fl, ph, pl, s, t;
+        d2ff_trunc(df, fh, fl);
+        face_term(fh, fl, ch, cl, c, ph, pl);
+        two_sum(H, ph, s, t);
+        H = s;
+        Lo += t + pl;
+      };
+      add(d[e], ce[idx]);
+      add(d[w], ce[w]);
+      add(d[idx + dn_], cn[idx]);
+      add(d[idx + ds_], cn[idx + ds_]);
+      if (has_up) add(d[idx + D.plane], cu[idx]);
+      else add(0.0, cu[idx]);   // the face value 0 above the top (cu = 0 there with zero flux)
+      if (has_dn) add(d[idx - D.plane], cu[idx - D.plane]);
+      float s, t;
+      two_sum(H, Lo, s, t);
+      const double Kd = -ff2d_fast(s, t);
+      q[idx] = Kd;
+      acc += dc * Kd;
     }
-    if (k > 0) {
-      const long long l = idx - D.plane;
-      fz -= (rc + rho[l]) * (dc - d[l]) * L.hdn;
-    }
-    const double Kd = -(L.dz * (hx + hy) + fz);
-    q[idx] = Kd;
-    acc += dc * Kd;
-  }
   }
   block_sum2(acc, 0.0, partials);
 }
@@ -245,7 +295,8 @@ cudaError_t cg_launch(int op, const CgKernels& K, const CgArgs& a, int nb, cudaS
     case CG_START:
       k_cg_start<<<gr, 256, 0, st>>>(a.rho, a.S, a.scalar, a.r, a.p, a.t, a.dz, a.lv, D, a.partials);
       break;
-    case CG_APPLY: k_cg_apply<<<gr, 256, 0, st>>>(a.rho, a.d, a.q, a.dz, a.lv, D, a.partials); break;
+    case CG_FACES: k_cg_faces<<<gr, 256, 0, st>>>(a.rho, a.ce, a.cn, a.cu, a.lv, D); break;
+    case CG_APPLY: k_cg_apply<<<gr, 256, 0, st>>>(a.d, a.ce, a.cn, a.cu, a.q, D, a.partials); break;
     case CG_UPDATE:
       k_cg_update<<<gr, 256, 0, st>>>(a.rho, a.scalar, a.d, a.q, a.p, a.r, a.t, a.lv, D, a.partials);
       break;

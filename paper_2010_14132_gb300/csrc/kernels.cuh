@@ -163,7 +163,7 @@ cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long lo
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
                            double tol, long long npoints, cudaStream_t st);
 // Conjugate gradients for a density varying in x, y and z (cg_kernels.cu).
-enum CgOp { CG_WMEAN = 0, CG_START, CG_APPLY, CG_UPDATE, CG_DOTS, CG_DIR, CG_SUM, CG_SHIFT };
+enum CgOp { CG_WMEAN = 0, CG_START, CG_APPLY, CG_UPDATE, CG_DOTS, CG_DIR, CG_SUM, CG_SHIFT, CG_FACES };
 struct CgLevel {      // per-level constants, so that no FP64 division runs per point
   double dz;          // dz_k
   double idz;         // 1/dz_k
@@ -181,6 +181,9 @@ struct CgArgs {
   const double* S;      // source
   const double* dz;     // level thicknesses (device)
   const CgLevel* lv;    // per-level constants (device, nz entries)
+  float2* ce;           // face coefficients of W A as float pairs: east, north, upper (CG_FACES writes them)
+  float2* cn;
+  float2* cu;
   double* p;            // iterate
   double* r;            // residual of K p = b
   double* d;            // search direction

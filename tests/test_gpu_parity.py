@@ -51,11 +51,30 @@ def test_anelastic_blobs_256x256x64(dtype):
     check(wl.anelastic_blobs(256, 256, 64, seed=2), dtype)
 
 
-def test_anelastic_noise_1024x1024x128_mixed_full_size():
+@pytest.fixture(scope="module")
+def full_size():
+    """The bench workload and the oracle's solution of it (computed once for the module)."""
     d = wl.anelastic_noise(1024, 1024, 128, seed=3)
-    err, info = check(d, "mixed")
+    return d, O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
+
+
+def test_anelastic_noise_1024x1024x128_mixed_full_size(full_size):
+    d, ref = full_size
+    p, info, _ = gpu_solve(d, "mixed")
+    err = O.relative_l2(p, ref)
+    assert err <= TOL["mixed"], (err, info)
     assert info["converged"] and 1 <= info["sweeps"] <= 3, info
     assert info["error_estimate"] <= 1e-10
+
+
+def test_full_size_in_the_bench_launch_configuration(full_size):
+    """The kernel shapes the bench times (the autotuner's choice on this GPU) at the full size."""
+    from paper_2010_14132_gb300.autotune import tuned_options
+    d, ref = full_size
+    opts = tuned_options(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, "mixed")
+    p, info, _ = gpu_solve(d, "mixed", **opts)
+    err = O.relative_l2(p, ref)
+    assert err <= TOL["mixed"], (err, opts, info)
 
 
 @pytest.mark.parametrize("dtype", ["fp64", "fp32", "mixed"])
