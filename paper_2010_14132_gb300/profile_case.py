@@ -4,7 +4,9 @@
 
 The grid uses the stretched/anelastic setup (dx = dy = 50 m, dz_k = 10*1.03^k m,
 rho0 = 1.2 exp(-z/8000)) with a seeded N(0,1) source.  With --adjoint the
-adjoint (and rho0 gradient) is run after each solve.  Prints the mean time per
+adjoint (and rho0 gradient) is run after each solve.  With --cg EPS each call is
+instead a conjugate-gradient solve for the density rho0(z) (1 + EPS g(x, y, z)),
+preconditioned by the plan's direct solve for the level-mean density (tolerance 1e-10).  Prints the mean time per
 call measured with CUDA events.  The measured calls sit inside a CUDA profiler
 range, so ``ncu --profile-from-start off`` captures them and not the set-up.
 Kernel shapes default to the library's defaults; --tuned takes the autotuner's
@@ -30,6 +32,8 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--tuned", action="store_true")
+    ap.add_argument("--cg", type=float, default=None, metavar="EPS")
+    ap.add_argument("--max-sweeps", dest="max_sweeps", type=int, default=None)
     for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel", "col_tile"):
         ap.add_argument("--" + name.replace("_", "-"), dest=name, type=int, default=None)
     args = ap.parse_args(argv)
@@ -41,17 +45,31 @@ def main(argv=None) -> int:
     for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel", "col_tile"):
         if getattr(args, name) is not None:
             opts[name] = getattr(args, name)
-    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype=args.dtype, **opts)
+    if args.max_sweeps is not None:
+        opts["max_sweeps"] = args.max_sweeps
+    rho0, rho3 = d.rho0, None
+    if args.cg is not None:
+        rho3 = wl.perturbed_density(d.nx, d.ny, d.rho0, args.cg, seed=8)
+        rho0 = rho3.mean(axis=(1, 2))
+    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, rho0, dtype=args.dtype, **opts)
     S = torch.from_numpy(d.S).cuda().to(plan.field_dtype)
     p = torch.empty_like(S)
     w = torch.randn_like(S) if args.adjoint else None
-    plan.solve(S, out=p)   # warm-up: kernel loading, workspace
+    rho_t = torch.from_numpy(rho3).cuda() if rho3 is not None else None
+
+    def call():
+        if rho_t is not None:
+            plan.cg_solve(rho_t, S, out=p, tol=1e-10, max_iter=100)
+        else:
+            plan.solve(S, out=p)
+
+    call()   # warm-up: kernel loading, workspace
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.profiler.start()
     e0.record()
     for _ in range(args.reps):
-        plan.solve(S, out=p)
+        call()
         if args.adjoint:
             plan.adjoint(w, p=p, want_grho=True)
     e1.record()
