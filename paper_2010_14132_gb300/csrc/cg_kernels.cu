@@ -187,22 +187,26 @@ __global__ void __launch_bounds__(256) k_cg_update(const double* __restrict__ rh
                                                    double* __restrict__ p, double* __restrict__ r,
                                                    double* __restrict__ t, const CgLevel* __restrict__ lv, CgDims D,
                                                    double* __restrict__ partials) {
-  double rr = 0;
+  float rr = 0.f;
   const long long rows = (long long)D.nz * D.ny;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
     const CgLevel L = lv[(int)(row / D.ny)];
+    const float idz = (float)L.idz;
   for (int i = threadIdx.x; i < D.nx; i += blockDim.x) {
     const long long idx = row * D.nx + i;
     p[idx] += alpha * d[idx];
     const double rn = r[idx] - alpha * q[idx];
     r[idx] = rn;
     t[idx] = -rn * L.iwbar;
-    // residual of A p = S - mu: r / (rho dz), weighted to float accuracy (a stopping test)
-    const double ra = rn * L.idz * (double)__frcp_rn((float)rho[idx]);
-    rr += ra * ra;
+    // residual of A p = S - mu: r / (rho dz), to float accuracy (a stopping test), in the FP32 pipe
+    float rh, rl, h, l;
+    d2ff_trunc(rn, rh, rl);
+    d2ff_trunc(rho[idx], h, l);
+    const float ra = rh * idz * __frcp_rn(h);
+    rr = __fmaf_rn(ra, ra, rr);
   }
   }
-  block_sum2(rr, 0.0, partials);
+  block_sum2((double)rr, 0.0, partials);
 }
 
 // partials: z . r, z . q
