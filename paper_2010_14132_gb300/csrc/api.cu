@@ -896,6 +896,7 @@ int poisson_cg_solve(poisson_plan* pl, const double* rho3, const double* S, doub
   if ((rc = cg_sums(a.partials, nb, st, &s0, nullptr)) != POISSON_OK) return rc;
   const double snorm = std::sqrt(s0);
   double rel = snorm > 0 ? 1.0 : 0.0;
+  a.inv_snorm = snorm > 0 ? 1.0 / snorm : 0.0;
   int it = 0;
   bool conv = snorm == 0;
   if (!conv) {
@@ -917,7 +918,7 @@ int poisson_cg_solve(poisson_plan* pl, const double* rho3, const double* S, doub
       a.scalar = alpha;
       PGB_CUDA(cg_launch(CG_UPDATE, K, a, nbmax, st));
       if ((rc = cg_sums(a.partials, nb, st, &s0, nullptr)) != POISSON_OK) return rc;
-      rel = std::sqrt(s0) / snorm;
+      rel = std::sqrt(s0);   // the update kernel's sum is already relative to ||S||
       if (rel <= tol) {
         conv = true;
         break;

@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(256) k_cg_wmean(const double* __restrict__ rho
   block_sum2(ws, w, partials);
 }
 
-// p += alpha d, r -= alpha q, t = -r/Wbar; partials: (r/W)^2 (the residual of A p = S - mu)
-__global__ void __launch_bounds__(256) k_cg_update(const double* __restrict__ rho, double alpha,
+// p += alpha d, r -= alpha q, t = -r/Wbar; partials: (r/(W ||S||))^2 (the relative residual of A p = S - mu)
+__global__ void __launch_bounds__(256) k_cg_update(const double* __restrict__ rho, double alpha, float inv_snorm,
                                                    const double* __restrict__ d, const double* __restrict__ q,
                                                    double* __restrict__ p, double* __restrict__ r,
                                                    double* __restrict__ t, const CgLevel* __restrict__ lv, CgDims D,
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) k_cg_update(const double* __restrict__ rh
   const long long rows = (long long)D.nz * D.ny;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
     const CgLevel L = lv[(int)(row / D.ny)];
-    const float idz = (float)L.idz;
+    const float idz = (float)L.idz * inv_snorm;   // the norm comes out relative to ||S||
   for (int i = threadIdx.x; i < D.nx; i += blockDim.x) {
     const long long idx = row * D.nx + i;
     p[idx] += alpha * d[idx];
@@ -302,7 +302,8 @@ cudaError_t cg_launch(int op, const CgKernels& K, const CgArgs& a, int nb, cudaS
     case CG_FACES: k_cg_faces<<<gr, 256, 0, st>>>(a.rho, a.ce, a.cn, a.cu, a.lv, D); break;
     case CG_APPLY: k_cg_apply<<<gr, 256, 0, st>>>(a.d, a.ce, a.cn, a.cu, a.q, D, a.partials); break;
     case CG_UPDATE:
-      k_cg_update<<<gr, 256, 0, st>>>(a.rho, a.scalar, a.d, a.q, a.p, a.r, a.t, a.lv, D, a.partials);
+      k_cg_update<<<gr, 256, 0, st>>>(a.rho, a.scalar, (float)a.inv_snorm, a.d, a.q, a.p, a.r, a.t, a.lv, D,
+                                      a.partials);
       break;
     case CG_DOTS: k_cg_dots<<<g, 256, 0, st>>>(a.z, a.r, a.q, D, a.partials); break;
     case CG_DIR: k_cg_dir<<<g, 256, 0, st>>>(a.z, a.scalar, a.flag, a.d, D.n); break;

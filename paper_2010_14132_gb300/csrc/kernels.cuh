@@ -192,6 +192,7 @@ struct CgArgs {
   const double* z;      // preconditioned residual
   double* partials;     // 2 doubles per block
   double scalar;        // mu, alpha, beta or shift
+  double inv_snorm;     // 1/||S|| (CG_UPDATE: the residual norm comes out relative)
   int flag;             // CG_DIR: beta is zero
 };
 CgKernels cg_kernels(int nx, int ny, int nz, double dx, double dy, int top_dirichlet);
