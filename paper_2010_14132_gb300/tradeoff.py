@@ -19,6 +19,15 @@ reference here; it matches the FP64 CPU oracle to 1e-12 relative L2 in the
 parity tests.
 
     python -m paper_2010_14132_gb300.tradeoff [--nx 1024 --ny 1024 --nz 128 --reps 20]
+
+With --cg EPS the study takes Table 1's own form for the library's iterative
+solver: conjugate gradients for the density rho0(z) (1 + EPS g(x, y, z)),
+preconditioned by the direct solve, run to termination residuals 1e-2 ... 1e-8.
+Each row gives the iterations, the time per solve and the mean difference from a
+1e-12 solution. A last row gives the direct solve for the level-mean density
+alone: the error of ignoring the horizontal variation.
+
+    python -m paper_2010_14132_gb300.tradeoff --cg 0.1
 """
 from __future__ import annotations
 
@@ -89,6 +98,65 @@ def run(domain, reps=20, device="cuda"):
             "p_mean_abs": float(p64.abs().mean()), "rows": rows}
 
 
+def run_cg(domain, eps, tols=(1e-2, 1e-4, 1e-6, 1e-8), reps=3, device="cuda"):
+    """Termination residual against mean difference and time (Table 1's columns) for the CG."""
+    import time
+    d = domain
+    rho3 = wl.perturbed_density(d.nx, d.ny, d.rho0, eps, seed=8)
+    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, rho3.mean(axis=(1, 2)), dtype="mixed", device=device,
+                max_sweeps=0)
+    rho_t = torch.from_numpy(rho3).to(device)
+    del rho3
+    S = torch.from_numpy(d.S).to(device)
+    ref, rinfo = plan.cg_solve(rho_t, S, tol=1e-12, max_iter=200)
+    torch.cuda.synchronize()
+    rows = []
+    p = torch.empty_like(S)
+    for tol in tols:
+        plan.cg_solve(rho_t, S, out=p, tol=tol, max_iter=200)   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            _, info = plan.cg_solve(rho_t, S, out=p, tol=tol, max_iter=200)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / reps
+        diff = p - ref
+        rows.append({"solve": f"CG to {tol:.0e}", "tol": tol, "iterations": info["iterations"],
+                     "rel_residual": info["rel_residual"], "ms_per_solve": ms,
+                     "mean_abs_diff": float(diff.abs().mean()),
+                     "rel_l2_diff": float(torch.linalg.vector_norm(diff) / torch.linalg.vector_norm(ref))})
+    # the direct solve alone (level-mean density): no iteration, the horizontal variation ignored
+    plan.solve(S, out=p)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.solve(S, out=p)
+    e1.record()
+    torch.cuda.synchronize()
+    diff = p - ref
+    rows.append({"solve": "direct solve, level-mean density", "tol": None, "iterations": 0, "rel_residual": None,
+                 "ms_per_solve": e0.elapsed_time(e1) / reps, "mean_abs_diff": float(diff.abs().mean()),
+                 "rel_l2_diff": float(torch.linalg.vector_norm(diff) / torch.linalg.vector_norm(ref))})
+    plan.close()
+    return {"workload": d.name, "nx": d.nx, "ny": d.ny, "nz": d.nz, "eps": eps,
+            "reference_iterations": rinfo["iterations"], "reference_rel_residual": rinfo["rel_residual"],
+            "p_mean_abs": float(ref.abs().mean()), "rows": rows}
+
+
+def markdown_cg(res):
+    lines = [f"Workload {res['workload']} ({res['nx']} x {res['ny']} x {res['nz']}), density rho0(z) "
+             f"(1 + {res['eps']} g); reference: CG to 1e-12 ({res['reference_iterations']} iterations); "
+             f"mean |p| = {res['p_mean_abs']:.3e}.", "",
+             "| solve | iterations | relative residual | mean difference | rel. L2 difference | time per solve (ms) |",
+             "|---|---|---|---|---|---|"]
+    for r in res["rows"]:
+        rr = "-" if r["rel_residual"] is None else f"{r['rel_residual']:.1e}"
+        lines.append(f"| {r['solve']} | {r['iterations']} | {rr} | {r['mean_abs_diff']:.2e} | "
+                     f"{r['rel_l2_diff']:.2e} | {r['ms_per_solve']:.2f} |")
+    return "\n".join(lines)
+
+
 def markdown(res):
     lines = [f"Workload {res['workload']} ({res['nx']} x {res['ny']} x {res['nz']}); "
              f"mean |p| of the FP64 solution = {res['p_mean_abs']:.3e}.", "",
@@ -111,8 +179,14 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--json", action="store_true", help="print JSON instead of a markdown table")
+    ap.add_argument("--cg", type=float, default=None, metavar="EPS",
+                    help="the conjugate-gradient study for the density rho0(z) (1 + EPS g)")
     a = ap.parse_args(argv)
     d = wl.anelastic_noise(a.nx, a.ny, a.nz, seed=a.seed)
+    if a.cg is not None:
+        res = run_cg(d, a.cg, reps=max(1, min(a.reps, 5)))
+        print(json.dumps(res) if a.json else markdown_cg(res))
+        return
     res = run(d, reps=a.reps)
     print(json.dumps(res) if a.json else markdown(res))
 

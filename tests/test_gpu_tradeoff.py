@@ -45,3 +45,22 @@ def test_precision_ladder_orders_accuracy():
     assert rows["mixed, 0 sweeps"]["mean_abs_diff"] <= rows["fp32"]["mean_abs_diff"] * 1.5
     for r in res["rows"]:
         assert r["ms_per_solve"] > 0
+
+
+def test_cg_termination_residual_orders_accuracy_and_cost():
+    """Table 1's form for the iterative solver: a tighter termination residual costs more
+    iterations and lands closer to the converged solution; the direct solve for the level-mean
+    density alone (the horizontal variation ignored) is further off than CG to 1e-4."""
+    d = wl.anelastic_noise(128, 96, 24, seed=44)
+    res = tradeoff.run_cg(d, 0.2, reps=1)
+    cg = res["rows"][:-1]
+    direct = res["rows"][-1]
+    assert [r["tol"] for r in cg] == [1e-2, 1e-4, 1e-6, 1e-8]
+    assert res["reference_rel_residual"] <= 1e-12
+    for r in cg:
+        assert r["rel_residual"] <= r["tol"], r
+    its = [r["iterations"] for r in cg]
+    diffs = [r["mean_abs_diff"] for r in cg]
+    assert its == sorted(its) and its[-1] > its[0], its
+    assert all(b < a for a, b in zip(diffs, diffs[1:])), diffs
+    assert direct["iterations"] == 0 and direct["mean_abs_diff"] > diffs[1]
