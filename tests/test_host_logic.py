@@ -87,3 +87,14 @@ def test_plan_rejects_unknown_boundary_condition_before_any_device_call():
     from paper_2010_14132_gb300.solver import Plan
     with pytest.raises(ValueError):
         Plan(8, 8, 4, 1.0, 1.0, np.ones(4), np.ones(4), dtype="fp64", bc="dirichlet")
+
+
+def test_cg_entry_points_reject_null_arguments():
+    lib = N.load()
+    n = C.c_size_t(0)
+    assert lib.poisson_cg_workspace_bytes(None, C.byref(n)) == N.POISSON_ERR_INVALID_ARG
+    info = N.PoissonCgInfo()
+    info.iterations = 7
+    st = lib.poisson_cg_solve(None, None, None, None, 1e-10, 10, None, None, C.byref(info))
+    assert st == N.POISSON_ERR_INVALID_ARG
+    assert info.iterations == 0 and info.converged == 0   # cleared before any check
