@@ -112,7 +112,7 @@ def autotune(nx, ny, nz, dx, dy, dz, rho0, dtype="mixed", reps=3, verbose=False)
             best_x, best_xt = dict(cand), tx
     for k, v in best_x.items():
         plan.set_option(OPT_IDS[k], v)
-    # levels per transform chunk: judged on the whole solve (it trades L2 reuse against launch count)
+    # levels per transform chunk: timed on the whole solve (it trades L2 reuse against launch count)
     best_c, best_ct = {}, float("inf")
     for cand in CHUNK_CANDIDATES:
         for k, v in cand.items():
