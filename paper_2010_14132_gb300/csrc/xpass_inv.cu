@@ -10,7 +10,11 @@ namespace {
 // inverse x-pass with the solver's epilogues
 // ---------------------------------------------------------------------------
 template <int N, int E, typename TO, int MODE>
-__global__ void __launch_bounds__(xs_threads(E)) k_xinv_s(const float2* __restrict__ spec, TO* __restrict__ out, Geom g,
+// Three CTAs per SM: the update epilogue otherwise takes 124 registers, which caps it at two.
+#ifndef PGB_XINV_MIN_BLOCKS
+#define PGB_XINV_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(xs_threads(E), PGB_XINV_MIN_BLOCKS) k_xinv_s(const float2* __restrict__ spec, TO* __restrict__ out, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
                                                       XinvExtra ex, int ns, unsigned stage_bytes) {
   using C = float2;
