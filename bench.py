@@ -146,7 +146,8 @@ def algorithmic_bytes(nx, ny, nz, sweeps):
         "yinv": (1 + sweeps) * 16 * Nc,
         "xinv": (8 * Nc + 4 * N) + sum(8 * Nc + 4 * N + 4 * N + 8 * N + (4 * N if s > 1 else 0)
                                        for s in range(1, sweeps + 1)),
-        "residual": 0,
+        # correction rebuild before sweeps 2 and 3: reads p (double) and p0, writes q
+        "residual": sum(16 * N for s in range(2, sweeps + 1)),
         "control": 0,
     }
     # the solve as a whole: read S, write p once; spectrum written and read once per pass;

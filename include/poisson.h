@@ -124,7 +124,8 @@ typedef enum {
   POISSON_PHASE_COLUMNS = 2,   /* tridiagonal column solves (low-|k| + main kernels) */
   POISSON_PHASE_YINV = 3,      /* inverse y-pass */
   POISSON_PHASE_XINV = 4,      /* inverse x-pass (C2R) with its epilogue */
-  POISSON_PHASE_RESIDUAL = 5,  /* double-float residual of a refinement sweep */
+  POISSON_PHASE_RESIDUAL = 5,  /* correction rebuild before refinement sweeps 2 and 3 (the residual itself
+                                  is formed inside the sweep's forward x-pass) */
   POISSON_PHASE_CONTROL = 6,   /* refinement control */
   POISSON_NPHASES = 7
 } poisson_phase;

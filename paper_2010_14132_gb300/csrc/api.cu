@@ -691,7 +691,12 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
     }
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
       // the inverse x-pass stores only the double iterate; a later sweep rebuilds q from it
-      if (sweep > 1) PGB_CUDA(launch_q_rebuild((const double*)p, p0, q, pl->g.N, done, st));
+      if (sweep > 1) {
+        const int ps = prof_begin(pl, POISSON_PHASE_RESIDUAL, st);
+        const cudaError_t eq = launch_q_rebuild((const double*)p, p0, q, pl->g.N, done, st);
+        prof_end(pl, ps, st);
+        PGB_CUDA(eq);
+      }
       // residual computed inside the forward x-pass (its rows are never stored)
       const ResidualArgs R{(const double*)S, p0, sweep > 1 ? q : nullptr, pl->tb.a_ff, pl->tb.c_ff,
                            pl->cx,           pl->cy, &stats->mu_ff};
