@@ -178,7 +178,8 @@ enum : unsigned { ERR_WAIT_TIMEOUT = 1u, ERR_BAD_SIZE = 2u };
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch.  The kernels of the solve chain are launched
 // with pdl_launch: the next kernel's CTAs may start (and build their shared
-// tables from the plan's constant tables) while the previous kernel drains.
+// tables from the plan's constant tables) while the previous kernel drains
+// (outside stream capture; captured launches keep ordinary stream order).
 // Every such kernel calls pdl_wait() before it touches memory that an earlier
 // kernel of the stream writes or reads: the wait returns once those kernels
 // have completed and their writes are visible.  pdl_trigger() lets the next
@@ -199,7 +200,11 @@ inline cudaError_t pdl_launch(void (*kern)(P...), dim3 grid, dim3 block, size_t 
 #ifdef PGB_NO_PDL
   at[0].val.programmaticStreamSerializationAllowed = 0;
 #else
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  // not inside a stream capture: the batched graphs run many small domains on concurrent branches,
+  // where plain edges measured faster (FP32 batch of 64 domains: 4.30 against 4.46 ms)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusActive;
+  at[0].val.programmaticStreamSerializationAllowed = (cs == cudaStreamCaptureStatusNone) ? 1 : 0;
 #endif
   cfg.attrs = at;
   cfg.numAttrs = 1;

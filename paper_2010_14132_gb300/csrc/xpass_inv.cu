@@ -9,12 +9,15 @@ namespace {
 // ---------------------------------------------------------------------------
 // inverse x-pass with the solver's epilogues
 // ---------------------------------------------------------------------------
-template <int N, int E, typename TO, int MODE>
-// Three CTAs per SM: the update epilogue otherwise takes 124 registers, which caps it at two.
+// Three CTAs per SM for 8 or 16 elements per thread: the update epilogue otherwise takes 124 registers,
+// which caps it at two.  With 24 elements (lengths with a factor 3) that bound would spill, so those
+// kernels keep their registers.
 #ifndef PGB_XINV_MIN_BLOCKS
 #define PGB_XINV_MIN_BLOCKS 3
 #endif
-__global__ void __launch_bounds__(xs_threads(E), PGB_XINV_MIN_BLOCKS) k_xinv_s(const float2* __restrict__ spec, TO* __restrict__ out, Geom g,
+constexpr int xinv_min_blocks(int e) { return e >= 24 ? 1 : PGB_XINV_MIN_BLOCKS; }
+template <int N, int E, typename TO, int MODE>
+__global__ void __launch_bounds__(xs_threads(E), xinv_min_blocks(E)) k_xinv_s(const float2* __restrict__ spec, TO* __restrict__ out, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
                                                       XinvExtra ex, int ns, unsigned stage_bytes) {
   using C = float2;
