@@ -1,7 +1,7 @@
 // Preconditioned conjugate gradients for a density that varies in x, y and z,
 // with the direct FFT solve as the preconditioner.  This is the iterative
 // alternative of Section 2.2 (a matrix-free CG whose cost per iteration is a
-// stencil application and a few vector updates, "post-conditioned" by a cheap
+// stencil application and a few vector updates, preconditioned by a cheap
 // approximate inverse), for the case the direct method alone cannot handle: a
 // horizontally varying density does not separate under the Fourier transform.
 //
@@ -58,9 +58,12 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* partials)
 // Face coefficients of W A, once per solve, as float pairs (hi, lo):
 //   ce = 0.5/dx^2 (rho_i + rho_{i+1}) dz_k (east face), cn = 0.5/dy^2 (rho_j + rho_{j+1}) dz_k (north),
 //   cu = (rho_k + rho_{k+1}) 0.5/h_{k+1/2} (upper; at the top rho_k 2/dz_k with p = 0 on the face, else 0).
-__device__ __forceinline__ float2 split_rn(double x) {
-  const float h = __double2float_rn(x);
-  return make_float2(h, __double2float_rn(x - (double)h));
+// x as a float pair (h, l) with integer operations (h + l within 2^-47 |x|), keeping the
+// conversions off the FP64 pipe; the sums and products above stay in FP64 (6 operations per point)
+__device__ __forceinline__ float2 split_int(double x) {
+  float h, l;
+  d2ff_trunc(x, h, l);
+  return make_float2(h, l);
 }
 
 __global__ void __launch_bounds__(256) k_cg_faces(const double* __restrict__ rho, float2* __restrict__ ce,
@@ -76,12 +79,12 @@ __global__ void __launch_bounds__(256) k_cg_faces(const double* __restrict__ rho
       const long long idx = base + i;
       const long long e = idx + (i + 1 == D.nx ? 1 - D.nx : 1);
       const double rc = rho[idx];
-      ce[idx] = split_rn(D.hx2 * (rc + rho[e]) * L.dz);
-      cn[idx] = split_rn(D.hy2 * (rc + rho[idx + dn_]) * L.dz);
+      ce[idx] = split_int(D.hx2 * (rc + rho[e]) * L.dz);
+      cn[idx] = split_int(D.hy2 * (rc + rho[idx + dn_]) * L.dz);
       double up = 0.0;
       if (k + 1 < D.nz) up = (rc + rho[idx + D.plane]) * L.hup;
       else if (D.top_dirichlet) up = rc * L.hup;
-      cu[idx] = split_rn(up);
+      cu[idx] = split_int(up);
     }
   }
 }
