@@ -163,8 +163,8 @@ int poisson_plan_set_option(poisson_plan* plan, int option, double value);
  * host (the call stays asynchronous). */
 int poisson_plan_set_rho0(poisson_plan* plan, const double* rho0_dev, void* stream);
 
-/* Solve for p given the source S (both device fields of the plan's element type;
- * they must not overlap: INVALID_ARG).  workspace: device, >= workspace_bytes,
+/* Solve for p given the source S (both device fields of the plan's element type and
+ * field layout; they must not overlap: INVALID_ARG).  workspace: device, >= workspace_bytes,
  * 256-byte aligned.  info: nullable host struct; when given, the call synchronises
  * the stream and fills it.  Mixed path: returns POISSON_ERR_NOT_CONVERGED (p still
  * written) when info is given and the error estimate stays above the tolerance. */
@@ -278,7 +278,7 @@ int poisson_batch_plan(poisson_batch* batch, int i, poisson_plan** plan);
  * step without waiting: copy S_host into a free slot, solve it, copy the
  * solution to p_host; the copy of step i+1's source and of step i-1's solution
  * overlap the solve of step i.  S_host and p_host hold nx*ny*nz values of the
- * plan's field type ([nz][ny][nx], x fastest).  Page-locked host buffers give
+ * plan's field type in its field layout ([nz][ny][nx], x fastest, by default).  Page-locked host buffers give
  * asynchronous copies; with pageable ones the copies still happen, without the
  * overlap.  The caller must not touch S_host until the step's source copy is
  * done, nor read p_host before poisson_pipe_wait returns.  Steps complete in
