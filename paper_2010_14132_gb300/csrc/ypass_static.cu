@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant_
 
 // Single-buffered variant: one tile per CTA, transformed in place, two CTAs per
 // SM (registers capped for it), so one CTA's load overlaps the other's transform.
+// The next tile's load is issued as soon as the transform has finished reading the
+// tile (its outputs are in registers), so it also overlaps this tile's stores.
 template <int N, int E, int SIGN>
 __global__ void __launch_bounds__(ys_max_threads(E), 2) k_ys1(const __grid_constant__ CUtensorMap tm, Geom g,
                                                              const float2* __restrict__ twy,
@@ -154,13 +156,16 @@ __global__ void __launch_bounds__(ys_max_threads(E), 2) k_ys1(const __grid_const
   const SwStrided sw{TK};
   int it = 0, pending = 0;
   bool ok = true;
-  for (int t = g.lev0 * tiles_per_level + blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+  auto issue = [&](int tt) {
+    const int lv = tt / tiles_per_level, k0 = (tt - lv * tiles_per_level) * TK;
+    mbar_arrive_expect_tx(bar, tile_bytes);
+    for (int r0 = 0; r0 < N; r0 += box_rows) tma_load_2d(tile + (size_t)r0 * TK, &tm, k0, lv * N + r0, bar);
+    pending = 1;
+  };
+  int t = g.lev0 * tiles_per_level + blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(t);
+  for (; t < ntiles; t += gridDim.x, ++it) {
     const int level = t / tiles_per_level, kx0 = (t - level * tiles_per_level) * TK;
-    if (tid == 0) {
-      mbar_arrive_expect_tx(bar, tile_bytes);
-      for (int r0 = 0; r0 < N; r0 += box_rows) tma_load_2d(tile + (size_t)r0 * TK, &tm, kx0, level * N + r0, bar);
-      pending = 1;
-    }
     const bool got = mbar_wait_bounded(bar, (unsigned)(it & 1), kWaitPolls);
     if (!__syncthreads_and(got)) {
       ok = false;
@@ -172,14 +177,17 @@ __global__ void __launch_bounds__(ys_max_threads(E), 2) k_ys1(const __grid_const
     for (int i = 0; i < E; ++i) v[i] = tile[Plain{TK}(st_in_index<N, E, 0>(lane, i)) + l];
     __syncthreads();   // every thread has its inputs before the tile is overwritten
     st_fft_inplace<N, E, SIGN, true, float>(v, tile + l, sw, lane, tw_s, SyncBlock());
+    // The in-place transform ends on a barrier after its last reads of the tile, and its outputs are in
+    // registers: refill the tile with the next one while this one is stored.
+    fence_proxy_async_smem();   // generic writes to the tile come before its refill by TMA
+    __syncthreads();
+    if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
     const int kx = kx0 + l;
     if (kx < g.nxh) {
       C* col = spec + (long long)level * g.plane + kx;
 #pragma unroll
       for (int i = 0; i < E; ++i) col[(long long)st_out_index<N, E>(lane, i) * g.P] = v[i];
     }
-    fence_proxy_async_smem();   // generic writes to the tile come before its refill by TMA
-    __syncthreads();            // every thread is done with the tile
   }
   if (tid == 0) {
     if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
