@@ -12,13 +12,14 @@ The direct solve has no termination residual, but it has a precision ladder:
     fp64                 FP64 throughout (the reference of the comparison)
 
 For each rung this reports the time per solve (CUDA events on the solving
-stream, inputs resident, median over repetitions), the mean |p - p_fp64| per
+stream around back-to-back solves, inputs resident; with --tuned the autotuner's
+kernel shapes), the mean |p - p_fp64| per
 element (the paper's mean-difference column), the relative L2 difference, and the
 sweeps and update estimate the library reported.  The FP64 GPU solution is the
 reference here; it matches the FP64 CPU oracle to 1e-12 relative L2 in the
 parity tests.
 
-    python -m paper_2010_14132_gb300.tradeoff [--nx 1024 --ny 1024 --nz 128 --reps 20]
+    python -m paper_2010_14132_gb300.tradeoff [--nx 1024 --ny 1024 --nz 128 --reps 20] [--tuned]
 
 With --cg EPS the study takes Table 1's own form for the library's iterative
 solver: conjugate gradients for the density rho0(z) (1 + EPS g(x, y, z)),
@@ -42,18 +43,20 @@ from .solver import Plan
 
 
 def _time_solve(plan, S, p, reps):
+    """Mean device time per solve over `reps` back-to-back solves (median of three such runs)."""
     stream = torch.cuda.current_stream()
     for _ in range(3):
         plan.solve(S, out=p)
     times = []
-    for _ in range(reps):
+    for _ in range(3):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        plan.solve(S, out=p)
+        for _ in range(reps):
+            plan.solve(S, out=p)
         e1.record(stream)
         e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+        times.append(e0.elapsed_time(e1) / reps)
     return float(np.median(times))
 
 
@@ -68,7 +71,7 @@ def rungs():
     return out
 
 
-def run(domain, reps=20, device="cuda"):
+def run(domain, reps=20, device="cuda", tuned=False):
     d = domain
     S64 = torch.from_numpy(d.S).to(device)
     ref_plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype="fp64", device=device)
@@ -76,6 +79,9 @@ def run(domain, reps=20, device="cuda"):
     torch.cuda.synchronize()
     rows = []
     for label, dtype, opts in rungs():
+        if tuned and dtype != "fp64":
+            from .autotune import tuned_options
+            opts = dict(tuned_options(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype), **opts)
         plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype=dtype, device=device, **opts)
         S = S64 if dtype != "fp32" else S64.to(torch.float32)
         p = torch.empty_like(S)
@@ -179,6 +185,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--json", action="store_true", help="print JSON instead of a markdown table")
+    ap.add_argument("--tuned", action="store_true", help="the autotuner's kernel shapes (as the bench)")
     ap.add_argument("--cg", type=float, default=None, metavar="EPS",
                     help="the conjugate-gradient study for the density rho0(z) (1 + EPS g)")
     a = ap.parse_args(argv)
@@ -187,7 +194,7 @@ def main(argv=None):
         res = run_cg(d, a.cg, reps=max(1, min(a.reps, 5)))
         print(json.dumps(res) if a.json else markdown_cg(res))
         return
-    res = run(d, reps=a.reps)
+    res = run(d, reps=a.reps, tuned=a.tuned)
     print(json.dumps(res) if a.json else markdown(res))
 
 
