@@ -1,0 +1,43 @@
+"""Host logic of bench.py's roofline accounting (no GPU): the algorithmic bytes of a mixed
+solve, per phase and in total, against the counts the method fixes."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+_spec = importlib.util.spec_from_file_location("bench_acc", os.path.join(ROOT, "bench.py"))
+B = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(B)
+
+
+@pytest.mark.parametrize("sweeps", [0, 1, 2, 3])
+def test_total_is_read_S_write_p_and_one_spectrum_round_trip_per_pass(sweeps):
+    nx, ny, nz = 1024, 1024, 128
+    N, Nc = nx * ny * nz, (nx // 2 + 1) * ny * nz
+    per_phase, total = B.algorithmic_bytes(nx, ny, nz, sweeps)
+    # first solve: S (8 B) in, p (8 B) out, spectrum (8 B/entry) written and read once
+    # each sweep: S and p read, p updated (read + write), spectrum once
+    assert total == 16 * N + 16 * Nc + sweeps * (32 * N + 16 * Nc)
+    # the 1024^2 x 128 workload with one sweep moves 8.59 GB (64 B per point)
+    if sweeps == 1:
+        assert abs(total / 1e9 - 8.594) < 1e-3
+    # every pass moves the spectrum once each way on the y-passes and the columns
+    for name in ("yfwd", "columns", "yinv"):
+        assert per_phase[name] == (1 + sweeps) * 16 * Nc
+    # the correction rebuild runs before sweeps 2 and 3 only
+    assert per_phase["residual"] == max(0, sweeps - 1) * 16 * N
+    assert per_phase["control"] == 0
+
+
+def test_forward_x_phase_bytes_are_the_roofline_unit():
+    nx, ny, nz = 1024, 1024, 128
+    N, Nc = nx * ny * nz, (nx // 2 + 1) * ny * nz
+    per_phase, _ = B.algorithmic_bytes(nx, ny, nz, 1)
+    # first solve 8N + 8Nc (S in, spectrum out); sweep 1: 12N + 8Nc (S and p0 in, spectrum out)
+    assert per_phase["xfwd"] == (8 * N + 8 * Nc) + (12 * N + 8 * Nc)
+    assert abs(per_phase["xfwd"] / 2 / 1e9 - 1.880) < 1e-3
+
+
+def test_whole_job_rate_counts_all_ranks():
+    assert B.whole_job_rate(1_000_000, 4, 2.0) == pytest.approx(4 * 1_000_000 / 2e-3 / 1e6)
