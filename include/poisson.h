@@ -79,16 +79,18 @@ typedef enum {
                                     double; default 64 (|k| <= 8); the (0,0) column always does */
   POISSON_OPT_MAX_SWEEPS = 1,    /* mixed: refinement sweeps after the first solve, 0..3; default 3 */
   POISSON_OPT_TOLERANCE = 2,     /* mixed: target relative L2 error estimate; default 1e-11 */
-  POISSON_OPT_Y_TILE = 3,        /* y-pass kx tile width (autotuner hook); 0 = plan default */
+  POISSON_OPT_Y_TILE = 3,        /* y-pass kx tile width (autotuner hook); 0 = plan default (8 for the
+                                    FP32 compile-time-FFT kernels) */
   POISSON_OPT_PROFILE = 4,       /* 1: record CUDA events around every kernel launch of this plan on
                                     the launching stream (read with poisson_plan_profile_read) */
   POISSON_OPT_Y_KERNEL = 5,      /* y-pass kernel: 0 = persistent TMA-staged kernel where the shape
-                                    allows, with the compile-time FFT for FP32 and power-of-two ny in
-                                    [64, 2048] (default); 1 = plain shared-memory tile kernel;
+                                    allows, with the compile-time FFT for FP32 and ny in {64, ..., 2048}
+                                    of the form 2^a 3^b; 1 = plain shared-memory tile kernel;
                                     2 = persistent TMA-staged kernel with the run-time FFT;
                                     3 = as 0, transforming in place in the TMA tile (two barriers per
-                                    stage, a third less shared memory); 4 = one tile per CTA, in
-                                    place, two CTAs per SM */
+                                    stage, a third less shared memory); 4 (default) = one tile per CTA,
+                                    in place, two CTAs per SM, the next tile's load overlapping this
+                                    tile's stores (16 elements per thread; otherwise as 0) */
   POISSON_OPT_X_ELEMS = 6,       /* x-pass elements per thread for power-of-two lines: 8 (default) or 16 */
   POISSON_OPT_Y_ELEMS = 7,       /* y-pass elements per thread for power-of-two lines: 8 or 16 (default) */
   POISSON_OPT_LEVEL_CHUNK = 8,   /* levels per transform chunk (x-pass and y-pass of a chunk run back to

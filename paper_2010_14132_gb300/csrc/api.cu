@@ -78,7 +78,7 @@ struct poisson_plan {
   int layout = POISSON_LAYOUT_Z_Y_X;   // caller's field layout (the solver works on [nz][ny][nx])
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
-  int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 0, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
+  int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 4, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
       coltile = 0;
   unsigned version = 0;   // bumped by every option change (invalidates captured batch graphs)
   double tol = 1e-11;
