@@ -547,3 +547,19 @@ def test_variable_operator_converges_to_continuous_problem():
         errs.append(np.abs(p - ex).max() / np.abs(ex).max())
     ratios = np.array(errs[:-1]) / np.array(errs[1:])
     assert np.all(ratios > 3.4) and np.all(ratios < 4.6), (errs, ratios)
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 6), (12, 9), (10, 16)])
+def test_dft_parseval_with_half_spectrum_weights(nx, ny):
+    """sum |S|^2 = (1/(nx ny)) sum_k w_kx |S_hat|^2, with w = 1 for kx = 0 (and kx = nx/2 when nx is
+    even) and 2 for the other stored bins: energy is kept by the real half-spectrum transform."""
+    rng = np.random.default_rng(nx * ny)
+    S = rng.standard_normal((3, ny, nx))
+    Sh = O.dft_y(O.dft_x(S))
+    w = np.full(nx // 2 + 1, 2.0)
+    w[0] = 1.0
+    if nx % 2 == 0:
+        w[-1] = 1.0
+    lhs = (S ** 2).sum()
+    rhs = (w[None, None, :] * np.abs(Sh) ** 2).sum() / (nx * ny)
+    assert abs(lhs - rhs) <= 1e-12 * lhs
