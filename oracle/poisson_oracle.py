@@ -10,8 +10,7 @@ equation in CFD", Section 2.1): a forward Fourier transform over the periodic
 x/y plane at every level, an independent vertical tridiagonal solve per
 (kx, ky) column, and a backward transform that gives the pressure.  The paper
 names an elliptic equation of Poisson type (Section 2) and nabla^2 x = b
-(Section 2.2) but prints no discretisation, so this module fixes one reading,
-listed in the design notes:
+(Section 2.2) but prints no discretisation, so this module fixes one reading:
 
   * cell-centred finite-volume 7-point operator, periodic in x and y with
     uniform dx, dy; cell thicknesses dz[k]; reference density rho0[k] at cell
@@ -34,8 +33,8 @@ For the iterative alternative (Section 2.2) with a density that also varies in x
 and y, apply_A_var and solve_var give the flux-form operator and a library sparse
 direct solve of it on moderate grids.
 
-The solve is exact (Section 3 calls it a direct method that solves the system exactly each time), so
-the oracle is that definition written out: a naive O(n^2) DFT per line built
+The solve is exact (Section 3 describes the direct method as solving the
+system exactly every time), so the oracle is that definition written out: a naive O(n^2) DFT per line built
 from exactly index-reduced twiddles (matrix products are the library step), the
 textbook Thomas recurrence per column, a dense bordered solve for the singular
 (0,0) column, and the naive inverse DFT.  No blocking, fusion or reordering.
