@@ -1,6 +1,6 @@
 """Multi-process (replica) host logic on CPU with the gloo backend, world size 2.
 
-The solver does not shard (DESIGN: replicas only): each rank solves its own
+The solver does not shard (replicas only): each rank solves its own
 grid and the bench reports the whole job's rate over the slowest rank's time.
 These tests run that reduction across two real processes, and the reference arm
 under torchrun, where rank 0 alone prints its line and both ranks exit 0.
