@@ -129,31 +129,53 @@ def recorded_traffic(phase):
     return None
 
 
-def algorithmic_bytes(nx, ny, nz, sweeps):
-    """Per-phase algorithmic bytes of one mixed solve with `sweeps` executed sweeps.
+def algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3):
+    """Per-phase bytes of one mixed solve with `sweeps` executed sweeps (of at most max_sweeps),
+    and the solve's algorithmic total.
 
-    N points, Nc = (nx/2+1) ny nz spectral entries (complex float, 8 B).
+    N points, Nc = (nx/2+1) ny nz spectral entries (complex float, 8 B).  Per phase, the fields the
+    kernels read and write: the first solve reads S (double) and stores p0 (float); sweep 1 forms
+    the residual from S and p0 and stores the correction q (float), or p (double) when it is the
+    last sweep allowed; a later sweep also reads q and stores p.  A third sweep first rebuilds q
+    from p ("residual" phase); the final p = p0 + q after a stop at sweep 1 is the "control" phase.
     """
     N = nx * ny * nz
     Nc = (nx // 2 + 1) * ny * nz
+    q_only = max_sweeps >= 2   # sweep 1 stores q, not p
+
+    def xinv_sweep(s):
+        reads = 8 * Nc + 4 * N + (4 * N if s > 1 else 0)
+        writes = 4 * N if (s == 1 and q_only) else 8 * N
+        return reads + writes
+
     b = {
-        # first solve reads S (double); each sweep forms the residual from S, p0 (and q
-        # from the second sweep on) inside the forward x-pass
         "xfwd": 8 * N + 8 * Nc + sum(8 * N + 4 * N + (4 * N if s > 1 else 0) + 8 * Nc
                                      for s in range(1, sweeps + 1)),
         "yfwd": (1 + sweeps) * 16 * Nc,
         "columns": (1 + sweeps) * 16 * Nc,
         "yinv": (1 + sweeps) * 16 * Nc,
-        "xinv": (8 * Nc + 4 * N) + sum(8 * Nc + 4 * N + 4 * N + 8 * N + (4 * N if s > 1 else 0)
-                                       for s in range(1, sweeps + 1)),
-        # correction rebuild before sweeps 2 and 3: reads p (double) and p0, writes q
-        "residual": sum(16 * N for s in range(2, sweeps + 1)),
-        "control": 0,
+        "xinv": (8 * Nc + 4 * N) + sum(xinv_sweep(s) for s in range(1, sweeps + 1)),
+        # q rebuilt from p and p0 before a third sweep
+        "residual": 16 * N if sweeps >= 3 else 0,
+        # p = p0 + q written after a stop at sweep 1
+        "control": 16 * N if (sweeps == 1 and q_only) else 0,
     }
     # the solve as a whole: read S, write p once; spectrum written and read once per pass;
     # each sweep also reads S and p and updates p
     total = 16 * N + 16 * Nc + sweeps * (32 * N + 16 * Nc)
     return b, total
+
+
+def fp64_flops_per_point(nx, ny, nz):
+    """FP64 operations per grid point of one FP64 solve, by the usual FFT count (5 n log2 n for a
+    complex transform of length n, 2.5 n log2 n for a real one) and the column recurrences as
+    written (forward elimination 14, back substitution 4 per complex entry)."""
+    import math
+    nxh = nx // 2 + 1
+    x = 2.5 * math.log2(nx)                         # real transform per point, each direction
+    y = 5.0 * math.log2(ny) * nxh / nx              # complex transforms of the half spectrum
+    cols = 18.0 * nxh / nx
+    return 2 * (x + y) + cols
 
 
 # ---------------------------------------------------------------------------
@@ -327,7 +349,7 @@ def main():
     # ---- roofline of the dominant kernel phase
     peak, peak_kind = measured_peaks()
     sweeps = int(info["sweeps"])
-    alg, alg_total = algorithmic_bytes(nx, ny, nz, sweeps)
+    alg, alg_total = algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3)
     phases = {}
     for name, (tms, cnt) in prof.items():
         if cnt == 0:
@@ -338,7 +360,7 @@ def main():
                         "alg_bytes_per_solve": alg[name], "gbs": gbs}
     dom = max(phases, key=lambda k: phases[k]["ms_per_solve"])
     execd = {"xfwd": 1 + sweeps, "yfwd": 1 + sweeps, "columns": 1 + sweeps, "yinv": 1 + sweeps,
-             "xinv": 1 + sweeps, "residual": max(1, sweeps), "control": 1 + sweeps}[dom]
+             "xinv": 1 + sweeps, "residual": 1, "control": 1}[dom]
     dom_ms_launch = phases[dom]["ms_per_solve"] / execd
     dom_bytes_launch = alg[dom] / execd
     achieved = dom_bytes_launch / (dom_ms_launch * 1e-3) / 1e9
@@ -403,12 +425,38 @@ def main():
         ms64 = max_over_ranks(e0.elapsed_time(e1) / K3, dist, "cuda")
         # the accuracy the metric names: the mixed solution (still in p) against the FP64 one
         diff = p - p64
+        # FP64 roofline: the solve's FP64 operations per second against a measured FP64 rate (cuBLAS
+        # DGEMM through torch, 2 n^3 operations, best of 5; its FMAs run on the same FP64 units)
+        del plan64
+        torch.cuda.empty_cache()
+        nd = 4096
+        A64 = torch.randn(nd, nd, device="cuda", dtype=torch.float64)
+        B64 = torch.randn(nd, nd, device="cuda", dtype=torch.float64)
+        torch.matmul(A64, B64)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(5):
+            e0.record(stream)
+            torch.matmul(A64, B64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        dgemm_tflops = 2 * nd ** 3 / (best * 1e-3) / 1e12
+        del A64, B64
+        f64pp = fp64_flops_per_point(nx, ny, nz)
+        f64_tflops = d.npoints * f64pp / (ms64 * 1e-3) / 1e12
         fp64 = {"value": world * d.npoints / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
-                "steps": K3, "bound": "alu (FP64 at 1/65 of FP32 on GB300)",
+                "steps": K3,
+                "roofline": {"bound": "alu", "achieved": f64_tflops, "peak": dgemm_tflops, "unit": "TFLOP/s (FP64)",
+                             "frac": f64_tflops / dgemm_tflops, "flops_per_point": f64pp,
+                             "peak_kind": "measured: cuBLAS DGEMM 4096^3 through torch, best of 5",
+                             "count": "5 n log2 n per complex FFT, 2.5 n log2 n per real FFT, "
+                                      "18 per complex column entry"},
                 "mixed_rel_l2_vs_fp64": float(torch.linalg.vector_norm(diff) / torch.linalg.vector_norm(p64)),
                 "mixed_mean_abs_diff_vs_fp64": float(diff.abs().mean())}
         del diff
-        del plan64, p64
+        del p64
 
     # ---- the same mixed solve on fields in MONC's z-fastest order ([nx][ny][nz]): the library
     # transposes S into its workspace and p back out, two extra passes over each field
@@ -468,7 +516,8 @@ def main():
     if not args.no_batch:
         from paper_2010_14132_gb300.solver import Batch
         doms = wl.uneven_batch(64)
-        bt = Batch(doms, dtype="mixed")
+        # kernel shapes per domain from the autotuner (cached per GPU, size and dtype)
+        bt = Batch(doms, dtype="mixed", tune=True)
         Sb = [torch.from_numpy(dd.S).cuda() for dd in doms]
         Pb = [torch.empty_like(x) for x in Sb]
         for _ in range(3):
@@ -484,8 +533,14 @@ def main():
         barrier()
         msb = max_over_ranks(e0.elapsed_time(e1) / K4, dist, "cuda")
         npb = sum(dd.npoints for dd in doms)
+        _, binfo = bt.solve(Sb, Pb, info=True)
+        torch.cuda.synchronize()
         batch = {"workload": "uneven_batch_64_mixed", "domains": len(doms), "points": npb, "ms_per_batch": msb,
-                 "value": world * npb / (msb * 1e-3) / 1e6, "unit": "Mpoints/s", "steps": K4}
+                 "value": world * npb / (msb * 1e-3) / 1e6, "unit": "Mpoints/s", "steps": K4,
+                 "autotuned_shapes": True,
+                 "sweeps": sorted({int(i["sweeps"]) for i in binfo}),
+                 "all_converged": all(bool(i["converged"]) for i in binfo),
+                 "max_error_bound": max(float(i["error_estimate"]) for i in binfo)}
         bt.close()
         del Sb, Pb
 
@@ -505,7 +560,12 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "nx": nx, "ny": ny, "nz": nz, "dx": 50.0,
                        "dz": "10*1.03^k m", "rho0": "1.2*exp(-z/8000)", "source": "N(0,1) mean removed, seed 3",
-                       "sweeps": sweeps, "update_estimate": info["error_estimate"],
+                       "sweeps": sweeps, "converged": bool(info["converged"]),
+                       "stopping_rule": "error bound ||delta_n||/||p|| (x phi/(1-phi) if the measured "
+                                        "contraction phi > 1/2) <= 1e-10",
+                       "error_bound": info["error_estimate"],
+                       "rel_update": info["rel_update"][:sweeps + 1],
+                       "rel_residual": info["rel_residual"][:sweeps],
                        "rel_l2_vs_fp64": fp64["mixed_rel_l2_vs_fp64"] if fp64 else None,
                        "l2": "inputs larger than L2 (1.07 GB source per solve)", "parallelism": f"replicas x{world}",
                        "tuned": tuned},

@@ -57,7 +57,9 @@ typedef enum {
   POISSON_ERR_CUDA = -3,           /* a CUDA runtime call failed (allocation, launch, copy) */
   POISSON_ERR_WORKSPACE = -4,      /* workspace pointer NULL or not 256-byte aligned */
   POISSON_ERR_NOT_CONVERGED = -5,  /* mixed path: refinement stopped above its tolerance; p is written */
-  POISSON_ERR_TIMEOUT = -6         /* a bounded device-side wait gave up (batched scheduler) */
+  POISSON_ERR_TIMEOUT = -6         /* a bounded device-side wait gave up: a kernel's wait for its own
+                                      asynchronous copies, or a persistent kernel's wait on a work
+                                      counter, ran out of polls; the kernel stopped and flagged it */
 } poisson_status;
 
 /* Vertical boundary conditions (x and y are always periodic). */
@@ -78,7 +80,8 @@ typedef enum {
   POISSON_OPT_LOWK_RADIUS2 = 0,  /* mixed: columns with kx^2 + ky'^2 <= value (ky' signed) use
                                     double; default 64 (|k| <= 8); the (0,0) column always does */
   POISSON_OPT_MAX_SWEEPS = 1,    /* mixed: refinement sweeps after the first solve, 0..3; default 3 */
-  POISSON_OPT_TOLERANCE = 2,     /* mixed: target relative L2 error estimate; default 1e-11 */
+  POISSON_OPT_TOLERANCE = 2,     /* mixed: the refinement stops once its error bound (error_estimate of
+                                    poisson_info) is at most this relative L2 error; default 1e-10 */
   POISSON_OPT_Y_TILE = 3,        /* y-pass kx tile width (autotuner hook); 0 = plan default (8 for the
                                     FP32 compile-time-FFT kernels) */
   POISSON_OPT_PROFILE = 4,       /* 1: record CUDA events around every kernel launch of this plan on
@@ -126,25 +129,38 @@ typedef enum {
   POISSON_PHASE_COLUMNS = 2,   /* tridiagonal column solves (low-|k| + main kernels) */
   POISSON_PHASE_YINV = 3,      /* inverse y-pass */
   POISSON_PHASE_XINV = 4,      /* inverse x-pass (C2R) with its epilogue */
-  POISSON_PHASE_RESIDUAL = 5,  /* correction rebuild before refinement sweeps 2 and 3 (the residual itself
-                                  is formed inside the sweep's forward x-pass) */
-  POISSON_PHASE_CONTROL = 6,   /* refinement control */
+  POISSON_PHASE_RESIDUAL = 5,  /* correction rebuild before refinement sweep 3 (the residual itself is
+                                  formed inside the sweep's forward x-pass) */
+  POISSON_PHASE_CONTROL = 6,   /* refinement control and the final p = p0 + q after an early stop */
   POISSON_NPHASES = 7
 } poisson_phase;
 
+/* Per-solve report of the mixed path's iterative refinement (the relative-residual
+ * measure of Section 2.2 and the refinement stopping of Section 2.2's termination
+ * idea, applied to the direct solve).  Sweep n computes the residual of iterate
+ * p_{n-1} (p_0 = the first FP32 solve), solves for its correction delta_n and
+ * updates p_n = p_{n-1} + delta_n. */
 typedef struct {
   int sweeps;                  /* refinement sweeps executed (mixed path; 0 otherwise) */
   int converged;               /* 1 if the mixed stopping test passed (always 1 for FP64/FP32) */
-  double rel_update[4];        /* ||delta_n||_2/||p||_2 of sweep n (index 0 = first solve = 1) */
-  double error_estimate;       /* mixed path: rel_update[n] * (rel_update[n] / rel_update[n-1]) after
-                                  sweep n (linear-convergence extrapolation; -1 before any sweep).  After
-                                  sweep 1 it takes the first solve's accuracy as the contraction and can be
-                                  optimistic by orders of magnitude; the stopping test compares it with
-                                  the tolerance */
+  double rel_update[4];        /* ||delta_n||_2/||p_n||_2 of sweep n (index 0 = first solve = 1) */
+  double error_estimate;       /* mixed path, after the last sweep n: a bound on ||p_n - p||_2/||p||_2
+                                  from the successive corrections.  With e_n the error of p_n,
+                                  e_{n-1} = delta_n + e_n, so a sweep contracting the error by
+                                  phi <= 1/2 gives ||e_n|| <= phi/(1-phi) ||delta_n|| <= ||delta_n||:
+                                  the bound is rel_update[n], times phi/(1-phi) when the measured
+                                  contraction phi = rel_update[n]/rel_update[n-1] exceeds 1/2, and
+                                  +inf when phi >= 1.  The solve converges when it is at most the
+                                  tolerance.  -1 when no sweep ran */
   double removed_weighted_mean;/* mu_W removed from S (first solve) */
+  double rel_residual[4];      /* ||S - mu_W - L p_n||_2 / ||S||_2 of iterate n (index 0 = the first
+                                  solve), formed in double-float arithmetic in the forward x-pass of
+                                  sweep n+1; entries n >= sweeps are -1 (the last iterate's residual
+                                  is not formed).  -1 for FP64/FP32 plans */
 } poisson_info;
 
-/* Create a plan.  dz and rho0 are HOST arrays of nz doubles (copied); bc is a
+/* Create a plan (Section 2.1: the solver plans once per grid and reuses the plan every
+ * timestep).  dz and rho0 are HOST arrays of nz doubles (copied); bc is a
  * poisson_bc value (anything else: INVALID_ARG).
  * Supported: nx even, nx >= 4, ny >= 4, each of nx, ny of the form 2^a 3^b and
  * <= 4096, nz in [2, 512]; dx, dy > 0; dz[k] > 0; rho0[k] > 0.
@@ -153,7 +169,11 @@ typedef struct {
 int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const double* dz,
                         const double* rho0, int bc, int dtype, poisson_plan** out);
 
-/* Bytes of device workspace one solve/adjoint call of this plan needs. */
+/* Bytes of device workspace one solve/adjoint call of this plan needs: the half
+ * spectrum [nz][ny][P] of Section 2.1's forward transform (P = nx/2+1 rounded up to
+ * 128 bytes; float2 entries, double2 for FP64), the mixed path's float iterate and
+ * correction fields, and small reduction buffers.  The caller allocates it (256-byte
+ * aligned) and owns it. */
 int poisson_plan_workspace_bytes(const poisson_plan* plan, size_t* bytes);
 
 /* Set a plan option (see poisson_option).  Values out of range: INVALID_ARG. */
@@ -165,7 +185,9 @@ int poisson_plan_set_option(poisson_plan* plan, int option, double value);
  * host (the call stays asynchronous). */
 int poisson_plan_set_rho0(poisson_plan* plan, const double* rho0_dev, void* stream);
 
-/* Solve for p given the source S (both device fields of the plan's element type and
+/* The direct solve of Section 2.1: forward real Fourier transform of S over x and y at
+ * every level, one tridiagonal solve per (kx, ky) column along z, inverse transform.
+ * Solve for p given the source S (both device fields of the plan's element type and
  * field layout; they must not overlap: INVALID_ARG).  workspace: device, >= workspace_bytes,
  * 256-byte aligned.  info: nullable host struct; when given, the call synchronises
  * the stream and fills it.  Mixed path: returns POISSON_ERR_NOT_CONVERGED (p still
@@ -173,7 +195,11 @@ int poisson_plan_set_rho0(poisson_plan* plan, const double* rho0_dev, void* stre
 int poisson_solve(poisson_plan* plan, const void* S, void* p, void* workspace, void* stream,
                   poisson_info* info);
 
-/* Adjoint of the solve map G: S -> p (a linear map for fixed rho0).
+/* Adjoint of the solve map G: S -> p of Section 2.1 (a linear map for fixed rho0): the
+ * same transform / column / inverse-transform pipeline with each column's transposed
+ * tridiagonal system (the real DFT pair is its own adjoint up to scaling), so that the
+ * pressure solve can sit inside gradient-based training.  The paper has no adjoint;
+ * this is the derivative of its direct solve.
  * gp: dL/dp (device field); gS (out, device field): G^T gp = dL/dS.
  * grho (out, nullable, device array of nz doubles): dL/drho0 for p = G(rho0) S,
  * which needs p, the forward result (ignored when grho is NULL).
@@ -232,7 +258,10 @@ int poisson_plan_profile_read(poisson_plan* plan, double* ms, int* launches, int
  * created beforehand (its small tables are allocated then).
  *  - Plans whose workspace_bytes exceed the maximum: POISSON_ERR_WORKSPACE.
  *  - The first call on a device looks up the array's device address with that
- *    device current; make that first call before any stream capture.
+ *    device current; make that first call before any stream capture.  The address
+ *    is then kept for the life of the process: it belongs to the device's primary
+ *    context, so after cudaDeviceReset (which ends that context) this entry point
+ *    must not be called again in the same process.
  *  - Every call on a device shares the one array: calls that overlap on the GPU
  *    (other streams, other plans, other threads) race.  The solve itself clears
  *    what must start at zero, so consecutive calls need nothing from the caller.

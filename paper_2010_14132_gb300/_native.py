@@ -56,6 +56,7 @@ class PoissonInfo(C.Structure):
         ("rel_update", C.c_double * 4),
         ("error_estimate", C.c_double),
         ("removed_weighted_mean", C.c_double),
+        ("rel_residual", C.c_double * 4),
     ]
 
     def as_dict(self):
@@ -63,6 +64,7 @@ class PoissonInfo(C.Structure):
             "sweeps": self.sweeps, "converged": bool(self.converged),
             "rel_update": list(self.rel_update), "error_estimate": self.error_estimate,
             "removed_weighted_mean": self.removed_weighted_mean,
+            "rel_residual": list(self.rel_residual),
         }
 
 

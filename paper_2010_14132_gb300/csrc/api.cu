@@ -81,7 +81,7 @@ struct poisson_plan {
   int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 4, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
       coltile = 0;
   unsigned version = 0;   // bumped by every option change (invalidates captured batch graphs)
-  double tol = 1e-11;
+  double tol = 1e-10;
   Geom g{};
   Tables tb{};
   double* dz_d = nullptr;
@@ -91,7 +91,7 @@ struct poisson_plan {
   int n_lowk = 0;
   float2 cx{}, cy{};
   // workspace layout
-  size_t off_spec = 0, off_stats = 0, off_part = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
+  size_t off_spec = 0, off_stats = 0, off_part = 0, off_rpart = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
          off_gp = 0, off_fa = 0, off_fb = 0, ws_bytes = 0;
   int xinv_blocks = 1, grho_nb = 1;
   PhaseProfiler prof;
@@ -153,6 +153,8 @@ void layout_workspace(poisson_plan* pl) {
   off = align256(off + sizeof(Stats));
   pl->off_part = off;
   off = align256(off + 3 * sizeof(double) * (size_t)(pl->xinv_blocks + pl->nz));   // + one per level chunk
+  pl->off_rpart = off;
+  off = align256(off + 2 * sizeof(double) * (size_t)(pl->xinv_blocks + pl->nz));
   pl->off_lz = off;
   off = align256(off + sizeof(double2) * (size_t)pl->nz * pl->n_lowk);
   pl->off_lw = off;
@@ -535,14 +537,17 @@ static int level_chunk(const poisson_plan* pl) {
 }
 
 // Forward transform (chunked x-pass then y-pass) and column solve of one field.
+// With a residual source R, *res_nblocks receives the number of per-block residual-norm
+// partials the forward x-pass launches wrote (from R->part0 on).
 static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_double, char* ws, cudaStream_t st,
                                    int adjoint, const int* done, const double* target_mean = nullptr,
-                                   const ResidualArgs* R = nullptr) {
+                                   const ResidualArgs* R = nullptr, int* res_nblocks = nullptr) {
   const bool t_double = pl->fp64();
   void* spec = ws + pl->off_spec;
   Stats* stats = (Stats*)(ws + pl->off_stats);
   const int lc = level_chunk(pl);
   cudaError_t e = cudaSuccess;
+  int rparts = 0;
   for (int l0 = 0; l0 < pl->nz; l0 += lc) {
     Geom gc = pl->g;
     gc.lev0 = l0;
@@ -550,8 +555,12 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
     int ps = prof_begin(pl, POISSON_PHASE_XFWD, st);
     if (R) {
       bool used = false;
-      if (pl->xkernel == 0) e = launch_xres_static(*R, spec, gc, pl->fx, pl->tb, done, &stats->err, st, &used);
-      if (e == cudaSuccess && !used) e = launch_xfwd_residual(*R, spec, gc, pl->fx, pl->tb, done, st);
+      ResidualArgs Rc = *R;
+      Rc.part0 = R->part0 + rparts;
+      int nb = 0;
+      if (pl->xkernel == 0) e = launch_xres_static(Rc, spec, gc, pl->fx, pl->tb, done, &stats->err, &nb, st, &used);
+      if (e == cudaSuccess && !used) e = launch_xfwd_residual(Rc, spec, gc, pl->fx, pl->tb, done, &nb, st);
+      rparts += nb;
     } else {
       bool used = false;
       if (!t_double && pl->xkernel == 0)
@@ -584,6 +593,7 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
   const int ps = prof_begin(pl, POISSON_PHASE_COLUMNS, st);
   e = launch_thomas(A, pl->g, pl->tb, st);
   prof_end(pl, ps, st);
+  if (res_nblocks) *res_nblocks = rparts;
   return e;
 }
 
@@ -639,11 +649,13 @@ static int fill_info(poisson_plan* pl, char* ws, cudaStream_t st, poisson_info* 
     info->sweeps = 0;
     info->rel_update[0] = 1.0;
     info->error_estimate = -1.0;
+    for (int i = 0; i < 4; ++i) info->rel_residual[i] = -1.0;
     return POISSON_OK;
   }
   info->sweeps = s.sweeps;
   info->converged = s.converged;
   for (int i = 0; i < 4; ++i) info->rel_update[i] = s.rel_update[i];
+  for (int i = 0; i < 4; ++i) info->rel_residual[i] = i < s.sweeps ? s.rel_residual[i] : -1.0;
   info->error_estimate = s.err_est;
   return s.converged ? POISSON_OK : POISSON_ERR_NOT_CONVERGED;
 }
@@ -685,33 +697,58 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
     cudaError_t e = cudaSuccess;
     if (!fused) {
       int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-      e = launch_control(stats, ex.partials, nb, 0, pl->max_sweeps, pl->tol, pl->g.N, st);
+      e = launch_control(stats, ex.partials, nb, nullptr, 0, 0, pl->max_sweeps, pl->tol, pl->g.N,
+                         ex.p_out != nullptr, st);
       prof_end(pl, ps, st);
       PGB_CUDA(e);
     }
+    // Sweep 1 stores the correction q (and p only when it is the last sweep allowed); a later sweep
+    // reads q and stores p.  If the stopping rule ends the refinement after sweep 1, k_finalize forms
+    // p = p0 + q.  A third sweep first rebuilds q from the double iterate of the second.
+    double* rpart = (double*)(ws + pl->off_rpart);
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
-      // the inverse x-pass stores only the double iterate; a later sweep rebuilds q from it
-      if (sweep > 1) {
+      if (sweep > 2) {
         const int ps = prof_begin(pl, POISSON_PHASE_RESIDUAL, st);
         const cudaError_t eq = launch_q_rebuild((const double*)p, p0, q, pl->g.N, done, st);
         prof_end(pl, ps, st);
         PGB_CUDA(eq);
       }
       // residual computed inside the forward x-pass (its rows are never stored)
-      const ResidualArgs R{(const double*)S, p0, sweep > 1 ? q : nullptr, pl->tb.a_ff, pl->tb.c_ff,
-                           pl->cx,           pl->cy, &stats->mu_ff};
-      PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R));
+      ResidualArgs R{};
+      R.partials = rpart;
+      R.part0 = 0;
+      R.S = (const double*)S;
+      R.p0 = p0;
+      R.q = sweep > 1 ? q : nullptr;
+      R.a_ff = pl->tb.a_ff;
+      R.c_ff = pl->tb.c_ff;
+      R.cx = pl->cx;
+      R.cy = pl->cy;
+      R.mu_ff = &stats->mu_ff;
+      int nres = 0;
+      PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R, &nres));
+      const bool last_allowed = sweep == pl->max_sweeps;
       XinvExtra eu = ex;
       eu.p0 = p0;
       eu.q = q;
       eu.q_valid = sweep > 1;
-      eu.p_out = (double*)p;
+      eu.q_out = (sweep == 1 && !last_allowed) ? q : nullptr;
+      eu.p_out = (sweep == 1 && !last_allowed) ? nullptr : (double*)p;
       eu.done = done;
       eu.ctl_pass = sweep;
+      eu.res_partials = rpart;
+      eu.res_nblocks = nres;
       PGB_CUDA(inverse(pl, ws, st, done, 0, XINV_UPDATE, nullptr, eu, &nb, &fused));
       if (!fused) {
         int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-        e = launch_control(stats, ex.partials, nb, sweep, pl->max_sweeps, pl->tol, pl->g.N, st);
+        e = launch_control(stats, ex.partials, nb, rpart, nres, sweep, pl->max_sweeps, pl->tol, pl->g.N,
+                           eu.p_out != nullptr, st);
+        prof_end(pl, ps, st);
+        PGB_CUDA(e);
+      }
+      if (eu.p_out == nullptr) {
+        int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
+        e = launch_finalize(p0, q, (double*)p, pl->g.N, stats, st);
         prof_end(pl, ps, st);
         PGB_CUDA(e);
       }

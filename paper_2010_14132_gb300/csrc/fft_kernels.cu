@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const TI* __restrict__ in, typenam
     }
   } else {
     const int jr = valid ? (int)(row % g.ny) : 0, kr = valid ? (int)(row / g.ny) : 0;
+    float racc = 0.f, sacc = 0.f;   // sums of r^2 and S^2 over this thread's points
 #pragma unroll 4
     for (int q = 0; q < E; ++q) {
       const int m = lane + nl * q;
@@ -67,8 +68,29 @@ __global__ void __launch_bounds__(256) k_xfwd(const TI* __restrict__ in, typenam
       if (valid) {
         z.x = residual_point<RES == 2>(R, g, 2 * m, jr, kr);
         z.y = residual_point<RES == 2>(R, g, 2 * m + 1, jr, kr);
+        const double2 Sv = reinterpret_cast<const double2*>(R.S + row * g.nx)[m];
+        racc += (float)z.x * (float)z.x + (float)z.y * (float)z.y;
+        sacc += __double2float_rn(Sv.x) * __double2float_rn(Sv.x) + __double2float_rn(Sv.y) * __double2float_rn(Sv.y);
       }
       line[sw(m)] = z;
+    }
+    // per-block sums of r^2 and S^2 (fixed-order tree over the block's threads)
+    __shared__ float rred[2][256];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthreads = blockDim.x * blockDim.y;
+    rred[0][tid] = racc;
+    rred[1][tid] = sacc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+      if (tid < h && tid + h < nthreads) {
+        rred[0][tid] += rred[0][tid + h];
+        rred[1][tid] += rred[1][tid + h];
+      }
+      __syncthreads();
+    }
+    if (tid == 0 && R.partials) {
+      const long long slot = R.part0 + blockIdx.x;
+      R.partials[2 * slot] = (double)rred[0][0];
+      R.partials[2 * slot + 1] = (double)rred[1][0];
     }
   }
   __syncthreads();
@@ -164,11 +186,12 @@ __global__ void __launch_bounds__(256) k_xinv(const typename CT<T>::t* __restric
         qn.x += qo.x;
         qn.y += qo.y;
       }
-      __stcs(reinterpret_cast<float2*>(ex.q + base) + m, qn);
+      if (ex.q_out) __stcs(reinterpret_cast<float2*>(ex.q_out + base) + m, qn);
       float s0, t0, s1, t1;
       two_sum(p0.x, qn.x, s0, t0);
       two_sum(p0.y, qn.y, s1, t1);
-      __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(ff2d_int(s0, t0), ff2d_int(s1, t1)));
+      if (ex.p_out)
+        __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(ff2d_int(s0, t0), ff2d_int(s1, t1)));
       acc0 += z.x * z.x + z.y * z.y;
       acc1 += s0 * s0 + s1 * s1;
       float e0, e1;
@@ -317,7 +340,7 @@ static cudaError_t xfwd_t(const TI* in, typename CT<T>::t* spec, const Geom& g, 
 }
 
 cudaError_t launch_xfwd_residual(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx,
-                                 const Tables& tb, const int* done, cudaStream_t st) {
+                                 const Tables& tb, const int* done, int* nblocks_out, cudaStream_t st) {
   using C = float2;
   const long long nrows = (long long)g.ny * g.lev1;   // end row of the chunk
   const int n = fx.n;
@@ -326,6 +349,7 @@ cudaError_t launch_xfwd_residual(const ResidualArgs& R, void* spec, const Geom& 
   const long long nb = ((long long)g.ny * (g.lev1 - g.lev0) + rb - 1) / rb;
   const size_t smem = (size_t)rb * swizzled_stride(n + 1) * sizeof(C);
   if (smem > kMaxDynSmem || nb > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (nblocks_out) *nblocks_out = (int)nb;
   cudaError_t e = cudaSuccess;
   if (R.q) {
     PGB_E_SWITCH(fx.E, {

@@ -11,12 +11,16 @@ struct Stats {
   double sq_delta[4];     // ||delta_n||^2 of pass n (pass 0 = first solve, delta_0 = p0)
   double sq_p[4];         // ||p||^2 after pass n
   double rel_update[4];
-  double err_est;         // estimated relative error after the last executed pass
+  double sq_res[4];       // ||S - mu_W - L p_n||^2 of iterate n, formed in the forward x-pass of sweep n+1
+  double sq_src[4];       // ||S||^2, summed in the same pass
+  double rel_residual[4]; // sqrt(sq_res / sq_src)
+  double err_est;         // bound on the relative error after the last executed pass
   double mu_w;            // weighted mean removed from the source (first solve)
   double pmean;           // mean of the current mixed iterate p0 + q (double-float accurate)
   float2 mu_ff;           // mu_w as a double-float pair (set after the first solve)
-  double control_stage[3 * 64];   // per-block sums of the control reduction
+  double control_stage[5 * 64];   // per-block sums of the control reduction
   unsigned control_ticket;        // blocks of the control reduction that have finished
+  int need_final;         // the refinement stopped after a sweep that stored q but not p: p = p0 + q still to write
   int done;               // later passes become no-ops once set
   int sweeps;
   int converged;
@@ -24,12 +28,23 @@ struct Stats {
 };
 
 // Refinement control after pass `pass` (0 = first solve) from the norm sums of
-// that pass: sd0 = sum delta^2, sp = sum p^2, sm = sum p.  Records the norms,
-// the relative update and the error estimate rel_n (rel_n / rel_{n-1}), and sets
-// `done` (and `converged`) once the estimate is at most tol or the sweeps are
-// used up.  One thread.
-__device__ __forceinline__ void control_decide(Stats* st, double sd0, double sp, double sm, int pass, int max_sweeps,
-                                               double tol, long long npoints) {
+// that pass: sd0 = sum delta^2, sp = sum p^2, sm = sum p (inverse x-pass), and
+// sr = sum r^2, ss = sum S^2 of the residual the pass started from (its forward
+// x-pass; unused for pass 0).  wrote_p: the pass's inverse x-pass stored the
+// double iterate p.  One thread.
+//
+// Stopping rule (iterative refinement, successive corrections): with delta_n the
+// correction of sweep n and e_n the error of the iterate after it,
+// e_{n-1} = delta_n + e_n, so a sweep that contracts the error by phi <= 1/2 gives
+//     ||e_n|| <= phi/(1 - phi) ||delta_n|| <= ||delta_n||.
+// The estimate after sweep n is therefore rel_n = ||delta_n||/||p||, enlarged to
+// rel_n phi/(1 - phi) when the contraction measured between the last two sweeps,
+// phi = rel_n/rel_{n-1}, exceeds 1/2, and infinite when phi >= 1 (stagnation).
+// Converged when the estimate is at most tol; otherwise the next sweep runs, up to
+// max_sweeps.
+__device__ __forceinline__ void control_decide(Stats* st, double sd0, double sp, double sm, double sr, double ss,
+                                               int pass, int max_sweeps, double tol, long long npoints,
+                                               int wrote_p) {
   st->pmean = sm / (double)npoints;
   if (pass == 0) {   // mu_W as a double-float pair, for the residual of the sweeps
     const float h = __double2float_rn(st->mu_w);
@@ -49,8 +64,16 @@ __device__ __forceinline__ void control_decide(Stats* st, double sd0, double sp,
     }
     return;
   }
-  const double prev = st->rel_update[pass - 1];
-  const double est = (prev > 0) ? rel * (rel / prev) : rel;
+  st->sq_res[pass - 1] = sr;
+  st->sq_src[pass - 1] = ss;
+  st->rel_residual[pass - 1] = (ss > 0) ? sqrt(sr / ss) : 0.0;
+  double est = rel;
+  if (pass >= 2) {
+    const double prev = st->rel_update[pass - 1];
+    const double phi = (prev > 0) ? rel / prev : 0.0;
+    if (phi >= 1.0) est = __longlong_as_double(0x7ff0000000000000LL);   // +inf: no contraction
+    else if (phi > 0.5) est = rel * (phi / (1.0 - phi));
+  }
   st->err_est = est;
   if (est <= tol || rel == 0.0) {
     st->done = 1;
@@ -59,6 +82,7 @@ __device__ __forceinline__ void control_decide(Stats* st, double sd0, double sp,
     st->done = 1;
     st->converged = 0;
   }
+  if (st->done && !wrote_p) st->need_final = 1;
 }
 
 // Device-resident tables owned by a plan.
@@ -88,16 +112,20 @@ struct Geom {
 enum XinvMode : int {
   XINV_PLAIN = 0,   // out[TO] = result
   XINV_P0 = 1,      // mixed first solve: p0 (float) + partial sums of p0^2; optional double output
-  XINV_UPDATE = 2   // mixed sweep: q += delta, p(double) = p0 + q, partial sums of delta^2, p^2
+  XINV_UPDATE = 2   // mixed sweep: q += delta, then q (float) and/or p (double) = p0 + q stored,
+                    // partial sums of delta^2, p^2
 };
 
 struct XinvExtra {
   float* p0;            // P0: written; UPDATE: read
-  float* q;             // UPDATE: read (unless first sweep) and written
+  float* q;             // UPDATE: the previous correction (read when q_valid)
   int q_valid;          // UPDATE: q holds a previous correction
-  double* p_out;        // P0 (when final) / UPDATE: double output field
+  float* q_out;         // UPDATE: the new correction q + delta is stored here (nullable)
+  double* p_out;        // P0 (when final) / UPDATE: double output field (nullable in UPDATE)
   double* partials;     // per-block partial sums (3 per block: delta^2, p^2, sum p)
   int part0;            // partial-sum slot of this launch's first block
+  const double* res_partials;   // the forward x-pass's per-block sums (2 per block: r^2, S^2)
+  int res_nblocks;              // their count (0 for the first solve)
   const int* done;      // skip when set (nullable)
   unsigned* err;        // ERR_* bits of the persistent kernels (nullable only when they are not used)
   // refinement control run by the launch's last CTA (persistent kernels; ctl_stats nullable = not fused)
@@ -109,6 +137,8 @@ struct XinvExtra {
 
 // Inputs of the double-float refinement residual r = S - mu_W - L (p0 + q).
 struct ResidualArgs {
+  double* partials;      // per-block sums of r^2 and S^2 (2 per block), from slot part0 on
+  int part0;
   const double* S;
   const float* p0;
   const float* q;        // nullable (first sweep)
@@ -124,13 +154,17 @@ cudaError_t launch_xfwd(int ti_is_double, int t_is_double, const void* in, void*
 // Forward x-pass of a refinement sweep whose input rows are the residual,
 // computed in the load stage (no r array in memory).
 cudaError_t launch_xfwd_residual(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx,
-                                 const Tables& tb, const int* done, cudaStream_t st);
+                                 const Tables& tb, const int* done, int* nblocks_out, cudaStream_t st);
 cudaError_t launch_yfft(int t_is_double, int sign, void* spec, const Geom& g, const FftPlan& fy,
                         const Tables& tb, int tile, const int* done, cudaStream_t st);
 // 2-D tensor map over 8-byte elements (dim0 contiguous, dim1 rows of row_stride_bytes);
 // false when the driver entry point is unavailable or the shape is rejected.
 bool encode_tensor_2d(CUtensorMap* tm, void* base, size_t elem_bytes, unsigned long long dim0,
                       unsigned long long dim1, unsigned long long row_stride_bytes, unsigned box0, unsigned box1);
+// 3-D tensor map over 8-byte elements: dim0 contiguous, dim1 and dim2 with the given byte strides.
+bool encode_tensor_3d(CUtensorMap* tm, void* base, unsigned long long dim0, unsigned long long dim1,
+                      unsigned long long dim2, unsigned long long stride1_bytes, unsigned long long stride2_bytes,
+                      unsigned box0, unsigned box1, unsigned box2);
 // Persistent TMA y-pass; *used = false when the shape is not supported (caller falls back).
 cudaError_t launch_yfft_tma(int t_is_double, int sign, void* spec, const Geom& g, const FftPlan& fy,
                             const Tables& tb, int tile, const int* done, Stats* stats, cudaStream_t st, bool* used);
@@ -160,8 +194,12 @@ cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, 
 // q = p - p0 (float) from the stored double iterate, before a second or third sweep (skipped when done).
 cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long long n, const int* done,
                              cudaStream_t st);
-cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps,
-                           double tol, long long npoints, cudaStream_t st);
+cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, const double* res_partials,
+                           int res_nblocks, int pass, int max_sweeps, double tol, long long npoints, int wrote_p,
+                           cudaStream_t st);
+// p = p0 + q (double) when the refinement stopped after a sweep that stored only q (Stats::need_final).
+cudaError_t launch_finalize(const float* p0, const float* q, double* p, long long n, const Stats* stats,
+                            cudaStream_t st);
 // Conjugate gradients for a density varying in x, y and z (cg_kernels.cu).
 enum CgOp { CG_WMEAN = 0, CG_START, CG_APPLY, CG_UPDATE, CG_DOTS, CG_DIR, CG_SUM, CG_SHIFT, CG_FACES };
 struct CgLevel {      // per-level constants, so that no FP64 division runs per point
@@ -216,7 +254,7 @@ bool xpass_static_supported(int n_half);
 cudaError_t launch_xfwd_static(int ti_is_double, const void* in, void* spec, const Geom& g, const FftPlan& fx,
                                const Tables& tb, const int* done, unsigned* err, cudaStream_t st, bool* used);
 cudaError_t launch_xres_static(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx, const Tables& tb,
-                               const int* done, unsigned* err, cudaStream_t st, bool* used);
+                               const int* done, unsigned* err, int* nblocks_out, cudaStream_t st, bool* used);
 cudaError_t launch_xinv_static(int to_is_double, int mode, const void* spec, void* out, const Geom& g,
                                const FftPlan& fx, const Tables& tb, const XinvExtra& ex, int* nblocks_out,
                                cudaStream_t st, bool* used);

@@ -47,11 +47,10 @@ cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, do
 }
 
 // ---------------------------------------------------------------------------
-// Refinement control: sums the x-pass partials in a fixed order,
-// records ||delta_n||/||p|| and the error estimate, and sets the done flag.
-// Stopping rule: after sweep n >= 1 the remaining error is estimated as
-// rho_n * ||delta_n||/||p|| with the observed contraction rho_n =
-// (||delta_n||/||p||) / (||delta_{n-1}||/||p||) (||delta_0|| = ||p0||).
+// Refinement control: sums the x-pass partials in a fixed order (the inverse
+// x-pass's delta^2, p^2, sum p and the forward x-pass's r^2, S^2), records the
+// relative update, relative residual and error bound, and sets the done flag
+// (control_decide in kernels.cuh states the stopping rule).
 // ---------------------------------------------------------------------------
 // Stage 1 (kControlBlocks blocks): each block sums a contiguous range of the
 // partials in a fixed order; the last block to finish (ticket counter) sums the
@@ -59,50 +58,75 @@ cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, do
 constexpr int kControlBlocks = 64;
 
 __global__ void __launch_bounds__(256) k_control(Stats* st, const double* __restrict__ partials, int nblocks,
+                                                  const double* __restrict__ res_partials, int res_nblocks,
                                                   int pass, int max_sweeps, double tol, long long npoints,
-                                                  double* __restrict__ stage, unsigned* __restrict__ ticket) {
-  __shared__ double s0[256], s1[256], s2[256];
+                                                  int wrote_p, double* __restrict__ stage,
+                                                  unsigned* __restrict__ ticket) {
+  __shared__ double sh[5][256];
   __shared__ bool last;
   if (st->done) return;   // later sweeps after convergence: nothing to do
   const int t = threadIdx.x;
   const int per = (nblocks + gridDim.x - 1) / gridDim.x;
   const int b0 = blockIdx.x * per, b1 = min(nblocks, b0 + per);
-  double a = 0, b = 0, c = 0;
+  const int rper = (res_nblocks + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * rper, r1 = min(res_nblocks, r0 + rper);
+  double v[5] = {0, 0, 0, 0, 0};
   for (int i = b0 + t; i < b1; i += blockDim.x) {
-    a += partials[3 * i];
-    b += partials[3 * i + 1];
-    c += partials[3 * i + 2];
+    v[0] += partials[3 * i];
+    v[1] += partials[3 * i + 1];
+    v[2] += partials[3 * i + 2];
   }
-  s0[t] = a;
-  s1[t] = b;
-  s2[t] = c;
+  for (int i = r0 + t; i < r1; i += blockDim.x) {
+    v[3] += res_partials[2 * i];
+    v[4] += res_partials[2 * i + 1];
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) sh[k][t] = v[k];
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
     if (t < h) {
-      s0[t] += s0[t + h];
-      s1[t] += s1[t + h];
-      s2[t] += s2[t + h];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sh[k][t] += sh[k][t + h];
     }
     __syncthreads();
   }
   if (t == 0) {
-    stage[3 * blockIdx.x] = s0[0];
-    stage[3 * blockIdx.x + 1] = s1[0];
-    stage[3 * blockIdx.x + 2] = s2[0];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) stage[5 * blockIdx.x + k] = sh[k][0];
     __threadfence();
     last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   }
   __syncthreads();
   if (!last || t != 0) return;
   __threadfence();
-  double sd0 = 0, sp = 0, sm = 0;
-  for (int i = 0; i < (int)gridDim.x; ++i) {
-    sd0 += stage[3 * i];
-    sp += stage[3 * i + 1];
-    sm += stage[3 * i + 2];
-  }
+  double tot[5] = {0, 0, 0, 0, 0};
+  for (int i = 0; i < (int)gridDim.x; ++i)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) tot[k] += stage[5 * i + k];
   *ticket = 0;   // ready for the next pass
-  control_decide(st, sd0, sp, sm, pass, max_sweeps, tol, npoints);
+  control_decide(st, tot[0], tot[1], tot[2], tot[3], tot[4], pass, max_sweeps, tol, npoints, wrote_p);
+}
+
+// ---------------------------------------------------------------------------
+// Final iterate when the refinement stopped after a sweep that stored only the
+// float correction q: p = p0 + q as a double (exact sum of the two floats up to
+// the double rounding).  A no-op unless Stats::need_final is set.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_finalize(const float2* __restrict__ p0, const float2* __restrict__ q,
+                                                  double2* __restrict__ p, long long npairs,
+                                                  const Stats* __restrict__ stats) {
+  pdl_trigger();
+  pdl_wait();   // the previous kernels of the stream are complete
+  if (!stats->need_final) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npairs;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 a = __ldcs(&p0[i]);
+    const float2 b = __ldcs(&q[i]);
+    float sx, ex, sy, ey;
+    two_sum(a.x, b.x, sx, ex);
+    two_sum(a.y, b.y, sy, ey);
+    __stcs(&p[i], make_double2(ff2d_int(sx, ex), ff2d_int(sy, ey)));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -142,11 +166,26 @@ cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long lo
                     (float2*)q, npairs, done);
 }
 
-cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, int pass, int max_sweeps, double tol,
-                           long long npoints, cudaStream_t st) {
-  k_control<<<kControlBlocks, 256, 0, st>>>(st_dev, partials, nblocks, pass, max_sweeps, tol, npoints,
-                                            st_dev->control_stage, &st_dev->control_ticket);
+cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, const double* res_partials,
+                           int res_nblocks, int pass, int max_sweeps, double tol, long long npoints, int wrote_p,
+                           cudaStream_t st) {
+  k_control<<<kControlBlocks, 256, 0, st>>>(st_dev, partials, nblocks, res_partials, res_nblocks, pass, max_sweeps,
+                                            tol, npoints, wrote_p, st_dev->control_stage, &st_dev->control_ticket);
   return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const float* p0, const float* q, double* p, long long n, const Stats* stats,
+                            cudaStream_t st) {
+  const long long npairs = n / 2;   // nx is even
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (npairs + 255) / 256;
+  const long long cap = (long long)(sms > 0 ? sms : 1) * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return pdl_launch(k_finalize, dim3((unsigned)blocks), dim3(256), 0, st, (const float2*)p0, (const float2*)q,
+                    (double2*)p, npairs, stats);
 }
 
 // ---------------------------------------------------------------------------

@@ -11,7 +11,12 @@
 // orders of magnitude for the smooth, large pressure field), which FP32 alone
 // cannot give and FP64 instructions make ALU bound on GB300.  Every product and
 // sum of p0 (exact floats) with the double-float coefficients is formed with
-// error-free transformations; the small correction q enters in plain FP32.
+// error-free transformations.  The vertical differences of the correction q are
+// formed exactly too and folded into those of p0: a_k (q_{k-1} - q_k) is a few
+// 1e-5 of |S| while the converged residual is near 1e-12 of it, so an FP32
+// rounding there (6e-8 relative) would leave the same bias in every sweep and
+// stall the refinement near 1e-12 relative error.  The horizontal q terms carry
+// the 25-100x smaller coefficients 1/dx^2, 1/dy^2 and enter in plain FP32.
 // S (double) is split into hi + lo floats with integer operations.
 #pragma once
 #include "kernels.cuh"
@@ -58,10 +63,22 @@ __device__ __forceinline__ float residual_value(float pc, float pe, float pw, fl
   float dd, ed, du, eu, p1, l1, p2, l2;
   two_sum(pd, -pc, dd, ed);
   two_sum(pu, -pc, du, eu);
+  {
+    // + (q_d - q_c) and (q_u - q_c), exactly: (pd - pc) + (qd - qc) = dd + ed + dq + eq
+    float dq, eq, t, et;
+    two_sum(qd, -qc, dq, eq);
+    two_sum(dd, dq, t, et);
+    dd = t;
+    ed = ed + (eq + et);
+    two_sum(qu, -qc, dq, eq);
+    two_sum(du, dq, t, et);
+    du = t;
+    eu = eu + (eq + et);
+  }
   two_prod(A.x, dd, p1, l1);
   two_prod(Cc.x, du, p2, l2);
-  l1 = __fmaf_rn(A.x, ed + (qd - qc), __fmaf_rn(A.y, dd, l1));
-  l2 = __fmaf_rn(Cc.x, eu + (qu - qc), __fmaf_rn(Cc.y, du, l2));
+  l1 = __fmaf_rn(A.x, ed, __fmaf_rn(A.y, dd, l1));
+  l2 = __fmaf_rn(Cc.x, eu, __fmaf_rn(Cc.y, du, l2));
   two_sum(p1, p2, s2, e2);
   FF tz{s2, (l1 + l2) + e2};
   FF Lp = ff_add(ff_add(tx, ty), tz);

@@ -4,8 +4,9 @@
 // instruction (add/mul/fma .f32x2, sm_100 and later).
 //
 // Same arithmetic as residual_value (residual.cuh), point for point: exact
-// neighbour sums and differences by TwoSum, products with the double-float
-// coefficient splits by FMA-based TwoProduct, one double-float accumulation;
+// neighbour sums and differences by TwoSum (the vertical differences of q
+// included), products with the double-float coefficient splits by FMA-based
+// TwoProduct, one double-float accumulation;
 // the x-, y- and z-parts are the 7-point stencil of the cell-centred operator.
 // The source S is split into a float pair by integer operations (truncated high
 // part, 23 further bits below it).
@@ -91,12 +92,21 @@ __device__ __forceinline__ float2 residual_value2(float2 pc, float2 pe, float2 p
   const float2 ntyh = mul2(k.ncyh, s2);
   const float2 tyl = fma2(k.cyh, dl, fma2(k.cyl, s2, fma2(k.cyh, s2, ntyh)));
   // z: a (pd - pc) + c (pu - pc), differences first (exact for a constant field)
+  // (the q differences exactly as well: a_k (q_d - q_c) is far above the converged residual, so an FP32
+  // rounding there would bias every sweep alike and stall the refinement)
   float2 dd, ed, du, eu;
   two_diff2(pd, pc, dd, ed);
   two_diff2(pu, pc, du, eu);
   if (HAS_Q) {
-    ed = add2(ed, sub2(qd, qc));
-    eu = add2(eu, sub2(qu, qc));
+    float2 dq, eq, t, et;
+    two_diff2(qd, qc, dq, eq);
+    two_sum2(dd, dq, t, et);
+    dd = t;
+    ed = add2(ed, add2(eq, et));
+    two_diff2(qu, qc, dq, eq);
+    two_sum2(du, dq, t, et);
+    du = t;
+    eu = add2(eu, add2(eq, et));
   }
   const float2 np1 = mul2(k.nah, dd);
   const float2 l1 = fma2(k.ah, ed, fma2(k.al, dd, fma2(k.ah, dd, np1)));

@@ -130,12 +130,14 @@ __global__ void __launch_bounds__(xs_threads(E), xinv_min_blocks(E)) k_xinv_s(co
           sl = add2(sl, e);
           if (ex.p_out)
             __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m, make_double2(f2d_int(z.x), f2d_int(z.y)));
-        } else {   // XINV_UPDATE: p = p0 + (q + delta) as a double (q is rebuilt from p if a later sweep runs)
+        } else {   // XINV_UPDATE: q + delta stored as the new q and/or p = p0 + (q + delta) as a double
           const float2 qn = add2(z, qv[i]);
+          if (ex.q_out) __stcs(reinterpret_cast<float2*>(ex.q_out + base) + m, qn);
           float2 sp, tp;
           two_sum2(p0v[i], qn, sp, tp);
-          __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m,
-                 make_double2(ff2d_fast(sp.x, tp.x), ff2d_fast(sp.y, tp.y)));
+          if (ex.p_out)
+            __stcs(reinterpret_cast<double2*>(ex.p_out + base) + m,
+                   make_double2(ff2d_fast(sp.x, tp.x), ff2d_fast(sp.y, tp.y)));
           acc0 = fma2(z, z, acc0);
           acc1 = fma2(sp, sp, acc1);
           float2 e;
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(xs_threads(E), xinv_min_blocks(E)) k_xinv_s(co
     // deterministic CTA partial sums: fixed-order tree over the CTA's threads, in the
     // line buffers (no longer in use: every thread is past its last transform)
     constexpr int TH = xs_threads(E);
-    static_assert((size_t)TH * 24 <= (size_t)RB * 2 * LS * sizeof(C), "reduction does not fit the line buffers");
+    static_assert((size_t)TH * 40 <= (size_t)RB * 2 * LS * sizeof(C), "reduction does not fit the line buffers");
     __syncthreads();
     double* redd = reinterpret_cast<double*>(lines);
     float (*red)[TH] = reinterpret_cast<float (*)[TH]>(redd + TH);
@@ -185,31 +187,36 @@ __global__ void __launch_bounds__(xs_threads(E), xinv_min_blocks(E)) k_xinv_s(co
     if (last) {
       // the last CTA to finish sums every CTA's partials in a fixed order and runs the control
       __threadfence();
-      double* sums = redd;   // [3][TH] in the line buffers
-      double a0 = 0, a1 = 0, a2 = 0;
+      double* sums = redd;   // [5][TH] in the line buffers
+      double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
       for (int i = tid; i < (int)gridDim.x; i += TH) {
         const long long slot = ex.part0 + i;
         a0 += __ldcg(&ex.partials[3 * slot]);
         a1 += __ldcg(&ex.partials[3 * slot + 1]);
         a2 += __ldcg(&ex.partials[3 * slot + 2]);
       }
+      for (int i = tid; i < ex.res_nblocks; i += TH) {   // the sweep's residual norms (forward x-pass)
+        a3 += __ldcg(&ex.res_partials[2 * i]);
+        a4 += __ldcg(&ex.res_partials[2 * i + 1]);
+      }
       __syncthreads();
       sums[tid] = a0;
       sums[TH + tid] = a1;
       sums[2 * TH + tid] = a2;
+      sums[3 * TH + tid] = a3;
+      sums[4 * TH + tid] = a4;
       __syncthreads();
       for (int h = TH / 2; h > 0; h >>= 1) {
         if (tid < h) {
-          sums[tid] += sums[tid + h];
-          sums[TH + tid] += sums[TH + tid + h];
-          sums[2 * TH + tid] += sums[2 * TH + tid + h];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) sums[v * TH + tid] += sums[v * TH + tid + h];
         }
         __syncthreads();
       }
       if (tid == 0) {
         ex.ctl_stats->control_ticket = 0u;   // ready for the next pass
-        control_decide(ex.ctl_stats, sums[0], sums[TH], sums[2 * TH], ex.ctl_pass, ex.ctl_max_sweeps, ex.ctl_tol,
-                       ex.ctl_npoints);
+        control_decide(ex.ctl_stats, sums[0], sums[TH], sums[2 * TH], sums[3 * TH], sums[4 * TH], ex.ctl_pass,
+                       ex.ctl_max_sweeps, ex.ctl_tol, ex.ctl_npoints, ex.p_out != nullptr);
       }
     }
   }

@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(xs_threads(E), E >= 24 ? 2 : (E >= 16 ? 4 : 3)
   const Swizzled sw{};
   (void)lines;
   const float2 cx = R.cx, cy = R.cy;   // double-float splits of 1/dx^2, 1/dy^2
+  float2 racc = make_float2(0.f, 0.f), sacc = racc;   // per-lane sums of r^2 and S^2 (even / odd points)
   bool ok = true;
   int it = 0;
   for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
@@ -129,6 +130,10 @@ __global__ void __launch_bounds__(xs_threads(E), E >= 24 ? 2 : (E >= 16 ? 4 : 3)
       // the pair's east neighbours are (pc.y, pe), its west neighbours (pw, pc.x)
       v[i] = residual_value2<HAS_Q>(pc, make_float2(pc.y, pe), make_float2(pw, pc.x), pn, ps, pd, pu, qc,
                                     make_float2(qc.y, qe), make_float2(qw, qc.x), qn, qs, qd, qu, Sh, Sl, K);
+      if (valid) {
+        racc = fma2(v[i], v[i], racc);
+        sacc = fma2(Sh, Sh, sacc);
+      }
     }
     sync();   // the line's threads have read the S row before it is overwritten
     const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
@@ -139,11 +144,31 @@ __global__ void __launch_bounds__(xs_threads(E), E >= 24 ? 2 : (E >= 16 ? 4 : 3)
     if (!ok) atomicOr(err, (unsigned)ERR_WAIT_TIMEOUT);
     ring_drain(rg, bar, ns);
   }
+  // per-CTA sums of r^2 and S^2 (fixed-order tree) in the drained staging ring
+  constexpr int TH = xs_threads(E);
+  static_assert((size_t)TH * 8 <= (size_t)RB * NX * 8, "reduction does not fit the staging ring");
+  __syncthreads();
+  float (*red)[TH] = reinterpret_cast<float (*)[TH]>(stg);
+  red[0][tid] = racc.x + racc.y;
+  red[1][tid] = sacc.x + sacc.y;
+  __syncthreads();
+  for (int h = TH / 2; h > 0; h >>= 1) {
+    if (tid < h) {
+      red[0][tid] += red[0][tid + h];
+      red[1][tid] += red[1][tid + h];
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && R.partials) {
+    const long long slot = R.part0 + blockIdx.x;
+    R.partials[2 * slot] = (double)red[0][0];
+    R.partials[2 * slot + 1] = (double)red[1][0];
+  }
 }
 
 template <bool HAS_Q>
 cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, int E, const Tables& tb,
-                   const int* done, unsigned* err, cudaStream_t st, bool* used) {
+                   const int* done, unsigned* err, int* nblocks_out, cudaStream_t st, bool* used) {
   const int RB = xs_threads(E) / (N / E);
   // stage S, p0 (and q) rows while three CTAs per SM still fit, else S rows only
   const unsigned row_bytes_all = (unsigned)(g.nx * (8 + 4 + (HAS_Q ? 4 : 0)));
@@ -156,12 +181,12 @@ cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, in
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
   if (stage_p) {
     PGB_XS_E8_24_SWITCH(E, PGB_XS_N_SWITCH(N, {
-      return xs_launch(k_xres_s<NN, EE, HAS_Q, true>, NN / EE, RB, c, ngroups, nullptr, st, used, R, spec, g,
+      return xs_launch(k_xres_s<NN, EE, HAS_Q, true>, NN / EE, RB, c, ngroups, nblocks_out, st, used, R, spec, g,
                        tb.twx_f, tb.twr_f, done, err);
     }));
   } else {
     PGB_XS_E8_24_SWITCH(E, PGB_XS_N_SWITCH(N, {
-      return xs_launch(k_xres_s<NN, EE, HAS_Q, false>, NN / EE, RB, c, ngroups, nullptr, st, used, R, spec, g,
+      return xs_launch(k_xres_s<NN, EE, HAS_Q, false>, NN / EE, RB, c, ngroups, nblocks_out, st, used, R, spec, g,
                        tb.twx_f, tb.twr_f, done, err);
     }));
   }
@@ -171,12 +196,12 @@ cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, in
 }  // namespace
 
 cudaError_t launch_xres_static(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx, const Tables& tb,
-                               const int* done, unsigned* err, cudaStream_t st, bool* used) {
+                               const int* done, unsigned* err, int* nblocks_out, cudaStream_t st, bool* used) {
   *used = false;
   if (!xpass_static_supported(fx.n)) return cudaSuccess;
   const int E = fx.n % 3 == 0 ? 24 : 8;   // the residual kernel: 8 elements per thread for powers of two
-  if (R.q) return xres_s<true>(R, (float2*)spec, g, fx.n, E, tb, done, err, st, used);
-  return xres_s<false>(R, (float2*)spec, g, fx.n, E, tb, done, err, st, used);
+  if (R.q) return xres_s<true>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
+  return xres_s<false>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
 }
 
 }  // namespace pgb

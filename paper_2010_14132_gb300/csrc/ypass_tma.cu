@@ -116,6 +116,20 @@ bool encode_tensor_2d(CUtensorMap* tm, void* base, size_t elem_bytes, unsigned l
          CUDA_SUCCESS;
 }
 
+bool encode_tensor_3d(CUtensorMap* tm, void* base, unsigned long long dim0, unsigned long long dim1,
+                      unsigned long long dim2, unsigned long long stride1_bytes, unsigned long long stride2_bytes,
+                      unsigned box0, unsigned box1, unsigned box2) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t gdim[3] = {(cuuint64_t)dim0, (cuuint64_t)dim1, (cuuint64_t)dim2};
+  const cuuint64_t gstride[2] = {(cuuint64_t)stride1_bytes, (cuuint64_t)stride2_bytes};
+  const cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, (cuuint32_t)box2};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 static int largest_divisor_upto(int n, int cap) {
   for (int d = cap; d >= 1; --d)
     if (n % d == 0) return d;

@@ -25,9 +25,28 @@ def test_total_is_read_S_write_p_and_one_spectrum_round_trip_per_pass(sweeps):
     # every pass moves the spectrum once each way on the y-passes and the columns
     for name in ("yfwd", "columns", "yinv"):
         assert per_phase[name] == (1 + sweeps) * 16 * Nc
-    # the correction rebuild runs before sweeps 2 and 3 only
-    assert per_phase["residual"] == max(0, sweeps - 1) * 16 * N
+    # the correction rebuild runs before a third sweep only; a stop after sweep 1 writes p = p0 + q
+    assert per_phase["residual"] == (16 * N if sweeps >= 3 else 0)
+    assert per_phase["control"] == (16 * N if sweeps == 1 else 0)
+    # sweep 1 stores q (4 B) when more sweeps are allowed; every later sweep stores p (8 B)
+    xinv = (8 * Nc + 4 * N) + sum(8 * Nc + 4 * N + (4 * N if s > 1 else 0) + (4 * N if s == 1 else 8 * N)
+                                  for s in range(1, sweeps + 1))
+    assert per_phase["xinv"] == xinv
+
+
+def test_one_sweep_allowed_stores_p_in_its_inverse_pass():
+    nx, ny, nz = 256, 256, 64
+    N, Nc = nx * ny * nz, (nx // 2 + 1) * ny * nz
+    per_phase, _ = B.algorithmic_bytes(nx, ny, nz, 1, max_sweeps=1)
+    assert per_phase["xinv"] == (8 * Nc + 4 * N) + (8 * Nc + 4 * N + 8 * N)
     assert per_phase["control"] == 0
+
+
+def test_fp64_operation_count():
+    # 1024 x 1024: real transforms 2.5 log2(1024) = 25 per point each way; complex y transforms of the
+    # 513 half-spectrum columns 5 log2(1024) 513/1024 per point each way; columns 18 per complex entry
+    f = B.fp64_flops_per_point(1024, 1024, 128)
+    assert f == pytest.approx(2 * (25 + 50 * 513 / 1024) + 18 * 513 / 1024)
 
 
 def test_forward_x_phase_bytes_are_the_roofline_unit():
