@@ -239,36 +239,99 @@ def column_matrix(a, c, lam):
     return T
 
 
+# Extended precision of the platform (x87 80-bit on x86-64, IEEE binary128 on aarch64):
+# used for the columns whose FP64 rounding is amplified (see _column_solves).
+XP = np.longdouble
+# Columns with |lambda_x + lambda_y| below this fraction of the largest vertical coupling
+# a_k + c_k are solved in XP.
+WEAK_COLUMN_RATIO = 1e-3
+
+
+def gauss_solve(A, B):
+    """Dense Gaussian elimination with partial pivoting in A's dtype (B: one or more columns)."""
+    A = np.array(A, copy=True)
+    B = np.array(B, copy=True)
+    n = A.shape[0]
+    for k in range(n):
+        piv = k + int(np.argmax(np.abs(A[k:, k])))
+        if piv != k:
+            A[[k, piv]] = A[[piv, k]]
+            B[[k, piv]] = B[[piv, k]]
+        f = A[k + 1:, k] / A[k, k]
+        A[k + 1:, k:] -= f[:, None] * A[k, k:][None, :]
+        B[k + 1:] -= f.reshape((-1,) + (1,) * (B.ndim - 1)) * B[k]
+    X = np.empty_like(B)
+    for k in range(n - 1, -1, -1):
+        X[k] = (B[k] - A[k, k + 1:] @ X[k + 1:]) / A[k, k]
+    return X
+
+
 def singular_column_solve(a, c, rhs, transpose=False):
     """Unique zero-sum solution of T x = rhs for the singular (0,0) column.
 
     T = L_z has null vector 1 (T^T has null vector W); the bordered matrix
     [[T, 1], [1^T, 0]] is nonsingular and, for a compatible right-hand side,
-    its solution is the zero-sum x with multiplier 0.  Dense library solve.
+    its solution is the zero-sum x with multiplier 0.  Dense Gaussian
+    elimination with partial pivoting in extended precision (the bordered
+    matrix's condition grows as the inverse of the smallest vertical eigenvalue,
+    about 1e6 on 128 stretched levels, which FP64 would pass on to x).
     """
     nz = a.size
-    T = column_matrix(a, c, 0.0)
+    T = np.zeros((nz, nz), dtype=XP)       # L_z with its diagonal -(a_k + c_k) formed in XP
+    for k in range(nz):
+        T[k, k] = -(XP(a[k]) + XP(c[k]))
+        if k > 0:
+            T[k, k - 1] = a[k]
+        if k < nz - 1:
+            T[k, k + 1] = c[k]
     if transpose:
         T = T.T
-    B = np.zeros((nz + 1, nz + 1))
+    B = np.zeros((nz + 1, nz + 1), dtype=XP)
     B[:nz, :nz] = T
     B[:nz, nz] = 1.0
     B[nz, :nz] = 1.0
-    r = np.zeros(nz + 1, dtype=np.result_type(rhs, np.float64))
-    r[:nz] = rhs
-    return np.linalg.solve(B, r)[:nz]
+    rhs = np.asarray(rhs)
+    r = np.zeros((nz + 1, 2), dtype=XP)
+    r[:nz, 0] = rhs.real
+    if np.iscomplexobj(rhs):
+        r[:nz, 1] = rhs.imag
+    x = gauss_solve(B, r)[:nz].astype(np.float64)
+    return x[:, 0] + 1j * x[:, 1] if np.iscomplexobj(rhs) else x[:, 0]
 
 
-def _spectral_diag(a, c, dx, dy, nx, ny, singular00=True):
+def _spectral_lambda(dx, dy, nx, ny):
+    """lambda_x(kx) + lambda_y(ky) on the half spectrum, shape (ny, nx//2 + 1)."""
     lx = horizontal_eigenvalues(nx, dx, nx // 2 + 1)     # (nxh,)
     ly = horizontal_eigenvalues(ny, dy, ny)              # (ny,)
-    lam = ly[:, None] + lx[None, :]                      # (ny, nxh)
+    return ly[:, None] + lx[None, :]
+
+
+def _column_solves(sub, sup, a, c, lam, rhs, skip00):
+    """Textbook Thomas on every column of rhs (nz, ny, nxh): T = L_z + lam I.
+
+    sub/sup: the (nz,) couplings below/above the diagonal (a, c for T; c shifted,
+    a shifted for T^T).  The diagonal -(a_k + c_k) + lam holds the column's row
+    sum lam only to FP64 rounding of a_k + c_k, so a column with |lam| far below
+    the couplings loses about eps (a + c)/|lam| of relative accuracy in FP64:
+    those columns are solved again in extended precision.  skip00: the (0,0)
+    column is solved elsewhere (zero-flux top); it gets a dominant stand-in here.
+    """
     diag = -(a + c)[:, None, None] + lam[None, :, :]
-    if singular00:
-        # the (0,0) column is singular; it is solved separately, so give the
-        # textbook recurrence a diagonally dominant stand-in there and discard it
+    if skip00:
         diag[:, 0, 0] = -(a + c) - 1.0
-    return diag
+    x = thomas(sub[:, None, None], diag, sup[:, None, None], rhs)
+    weak = np.abs(lam) < WEAK_COLUMN_RATIO * np.max(a + c)
+    if skip00:
+        weak[0, 0] = False
+    jj, ii = np.nonzero(weak)
+    if jj.size:
+        dxp = -(a.astype(XP) + c.astype(XP))[:, None] + lam[jj, ii].astype(XP)[None, :]
+        sb, sp = sub.astype(XP)[:, None], sup.astype(XP)[:, None]
+        col = rhs[:, jj, ii]
+        re = thomas(sb, dxp, sp, col.real.astype(XP)).astype(np.float64)
+        im = thomas(sb, dxp, sp, col.imag.astype(XP)).astype(np.float64)
+        x[:, jj, ii] = re + 1j * im
+    return x
 
 
 def solve(S, dx, dy, dz, rho0, return_info=False, bc="neumann"):
@@ -278,6 +341,9 @@ def solve(S, dx, dy, dz, rho0, return_info=False, bc="neumann"):
     column with T = L_z + (lambda_x + lambda_y) I, bordered solve for the
     (0,0) column, inverse DFT in y then x.  With bc="dirichlet_top" every
     column, (0,0) included, is nonsingular: p = L^{-1} S by Thomas throughout.
+    The direct method is exact (Section 3), so the oracle's own rounding must
+    stay far below the tolerances it checks: columns whose diagonal dominance
+    is weak are solved in extended precision (_column_solves).
     """
     S = _f64(S)
     nz, ny, nx = S.shape
@@ -285,10 +351,7 @@ def solve(S, dx, dy, dz, rho0, return_info=False, bc="neumann"):
     neumann = bc == "neumann"
     mu_W = weighted_mean(S, W) if neumann else 0.0
     Shat = dft_y(dft_x(S - mu_W))                          # (nz, ny, nxh)
-    diag = _spectral_diag(a, c, dx, dy, nx, ny, singular00=neumann)
-    sub = a[:, None, None]
-    sup = c[:, None, None]
-    phat = thomas(sub, diag, sup, Shat)
+    phat = _column_solves(a, c, a, c, _spectral_lambda(dx, dy, nx, ny), Shat, skip00=neumann)
     if neumann:
         phat[:, 0, 0] = singular_column_solve(a, c, Shat[:, 0, 0])
     p = idft_x(idft_y(phat), nx)
@@ -316,13 +379,12 @@ def adjoint(wgt, dx, dy, dz, rho0, bc="neumann"):
     What = dft_y(dft_x(wgt))
     if neumann:
         What[:, 0, 0] -= What[:, 0, 0].mean()              # P_1
-    diag = _spectral_diag(a, c, dx, dy, nx, ny, singular00=neumann)
     # T^T: row k has T[k-1,k] = c_{k-1} below the diagonal and T[k+1,k] = a_{k+1} above
     sub_t = np.zeros(nz)
     sup_t = np.zeros(nz)
     sub_t[1:] = c[:-1]
     sup_t[:-1] = a[1:]
-    mhat = thomas(sub_t[:, None, None], diag, sup_t[:, None, None], What)
+    mhat = _column_solves(sub_t, sup_t, a, c, _spectral_lambda(dx, dy, nx, ny), What, skip00=neumann)
     if neumann:
         mhat[:, 0, 0] = singular_column_solve(a, c, What[:, 0, 0], transpose=True)
     m = idft_x(idft_y(mhat), nx)

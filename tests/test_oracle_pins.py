@@ -194,6 +194,84 @@ def test_singular_column_solve():
     assert np.allclose(x - x.mean(), xp - xp.mean(), atol=1e-11)
 
 
+def _mp_column_solve(T, rhs, dps=40):
+    """Reference solve of a small dense system in mpmath at dps digits (independent of numpy).
+
+    T: a callable (mpmath module) -> mpmath matrix, so that entries such as -(a_k + c_k) + lam are
+    formed at dps digits, or an array of exact entries."""
+    mpmath = pytest.importorskip("mpmath")
+    with mpmath.workdps(dps):
+        A = T(mpmath) if callable(T) else mpmath.matrix([[mpmath.mpf(float(v)) for v in row] for row in T])
+        b = mpmath.matrix([mpmath.mpf(float(v)) for v in rhs])
+        x = mpmath.lu_solve(A, b)
+        return np.array([float(v) for v in x])
+
+
+def _mp_column(a, c, lam, border=False):
+    """T = L_z + lam I (bordered by ones when border) with its entries formed in mpmath."""
+    nz = a.size
+
+    def build(mp):
+        n = nz + 1 if border else nz
+        A = mp.matrix(n, n)
+        for k in range(nz):
+            A[k, k] = -(mp.mpf(float(a[k])) + mp.mpf(float(c[k]))) + mp.mpf(float(lam))
+            if k > 0:
+                A[k, k - 1] = mp.mpf(float(a[k]))
+            if k < nz - 1:
+                A[k, k + 1] = mp.mpf(float(c[k]))
+            if border:
+                A[k, nz] = 1
+                A[nz, k] = 1
+        return A
+    return build
+
+
+@pytest.mark.parametrize("nz,lam", [(3, -6.0e-8), (17, -2.4e-8), (128, -1.5e-8)])
+def test_weak_column_solve_is_accurate_to_fp64(nz, lam):
+    """A column whose row sum lam is 1e5-1e6 times below its couplings (the lowest horizontal
+    wavenumbers of the stretched, 50 m grids): the oracle's column solve matches a 40-digit solve
+    to FP64 accuracy, where the plain FP64 recurrence loses eps (a + c)/|lam|."""
+    dz = wl.stretched_levels(nz)
+    rho = wl.exponential_density(dz)
+    W, a, c = O.vertical_coefficients(dz, rho)
+    rng = np.random.default_rng(nz)
+    rhs = rng.standard_normal(nz)
+    ref = _mp_column_solve(_mp_column(a, c, lam), rhs)
+    lam_arr = np.array([[lam]])
+    x = O.poisson_oracle._column_solves(a, c, a, c, lam_arr, rhs[:, None, None].astype(complex),
+                                        skip00=False)[:, 0, 0].real
+    err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+    assert err <= 5e-15, err
+    # the same recurrence carried in FP64 (the diagonal -(a + c) + lam rounded to double) is far worse
+    x64 = O.thomas(a, -(a + c) + lam, c, rhs)
+    err64 = np.linalg.norm(x64 - ref) / np.linalg.norm(ref)
+    assert err64 > 20 * err + 1e-14, (err64, err)
+
+
+def test_singular_column_solve_is_accurate_to_fp64():
+    """The (0,0) column on 128 stretched, density-weighted levels (bordered matrix condition ~1e6)
+    against a 40-digit bordered solve."""
+    nz = 128
+    dz = wl.stretched_levels(nz)
+    rho = wl.exponential_density(dz)
+    W, a, c = O.vertical_coefficients(dz, rho)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(nz)
+    b -= W * (W @ b) / (W @ W)
+    ref = _mp_column_solve(_mp_column(a, c, 0.0, border=True), np.r_[b, 0.0])[:nz]
+    x = O.singular_column_solve(a, c, b)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 5e-15
+
+
+def test_gauss_solve_against_mpmath():
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((7, 7))
+    b = rng.standard_normal(7)
+    x = O.poisson_oracle.gauss_solve(A.astype(O.poisson_oracle.XP), b.astype(O.poisson_oracle.XP)).astype(float)
+    assert np.allclose(x, _mp_column_solve(A, b), rtol=1e-14, atol=0)
+
+
 # ---------------------------------------------------------------------------
 # full solve
 # ---------------------------------------------------------------------------
