@@ -108,9 +108,14 @@ typedef enum {
                                     paired-ky kernel); 1, 2, 4 = two threads per column with 16, 32, 64
                                     columns; 3 = paired-ky kernel; 16, 32, 64, 128 = one thread per column
                                     with that many columns per CTA */
-  POISSON_OPT_LAYOUT = 11        /* layout of the caller's fields (S, p, gp, gS), a poisson_layout value;
+  POISSON_OPT_LAYOUT = 11,       /* layout of the caller's fields (S, p, gp, gS), a poisson_layout value;
                                     default POISSON_LAYOUT_Z_Y_X.  Any other layout adds two field-sized
                                     buffers to the workspace (query the size after setting it) */
+  POISSON_OPT_SPECTRAL_FUSED = 12 /* 1: the forward y-pass, the column solves and the inverse y-pass of
+                                    each forward solve run as one persistent kernel over strips of 8 kx,
+                                    each strip's spectrum kept in L2 between the three steps, where the
+                                    plan allows it (float spectrum, ny in {256, 512, 1024}, nz <= 256,
+                                    one level chunk); 0 (default): three separate kernels */
 } poisson_option;
 
 /* Field layouts (POISSON_OPT_LAYOUT), C order, outermost index first. */
@@ -132,7 +137,9 @@ typedef enum {
   POISSON_PHASE_RESIDUAL = 5,  /* correction rebuild before refinement sweep 3 (the residual itself is
                                   formed inside the sweep's forward x-pass) */
   POISSON_PHASE_CONTROL = 6,   /* refinement control and the final p = p0 + q after an early stop */
-  POISSON_NPHASES = 7
+  POISSON_PHASE_SPECTRAL = 7,  /* the fused spectral middle (y-pass, columns, inverse y-pass in one
+                                  kernel; POISSON_OPT_SPECTRAL_FUSED) */
+  POISSON_NPHASES = 8
 } poisson_phase;
 
 /* Per-solve report of the mixed path's iterative refinement (the relative-residual

@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(HERE, LIB_NAME)
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 SOURCES = ["api.cu", "fft_kernels.cu", "thomas_kernels.cu", "misc_kernels.cu", "ypass_tma.cu", "cg_kernels.cu",
-           "static_workspace.cu", "xpass_fwd.cu", "xpass_res.cu", "xpass_inv.cu", "ypass_static.cu"]
+           "static_workspace.cu", "xpass_fwd.cu", "xpass_res.cu", "xpass_inv.cu", "ypass_static.cu",
+           "spectral_fused.cu"]
 
 
 def nvcc() -> str:

@@ -79,7 +79,7 @@ struct poisson_plan {
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
   int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 4, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
-      coltile = 0;
+      coltile = 0, fused = 0;
   unsigned version = 0;   // bumped by every option change (invalidates captured batch graphs)
   double tol = 1e-10;
   Geom g{};
@@ -89,9 +89,13 @@ struct poisson_plan {
   void* tables = nullptr;
   int2* lowk_d = nullptr;
   int n_lowk = 0;
+  std::vector<int> lowk_kx;     // kx of every listed low-|k| column (host copy)
+  int* mid_d = nullptr;         // item list of the fused spectral middle (device)
+  int mid_nitems = 0;
+  int sched_words = 0;          // per-pass scheduling counters of the fused middle
   float2 cx{}, cy{};
   // workspace layout
-  size_t off_spec = 0, off_stats = 0, off_part = 0, off_rpart = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
+  size_t off_spec = 0, off_stats = 0, off_sched = 0, stats_bytes = 0, off_part = 0, off_rpart = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
          off_gp = 0, off_fa = 0, off_fb = 0, ws_bytes = 0;
   int xinv_blocks = 1, grho_nb = 1;
   PhaseProfiler prof;
@@ -141,6 +145,24 @@ int build_lowk(poisson_plan* pl) {
   PGB_CUDA(cudaMalloc(&pl->lowk_d, cols.size() * sizeof(int2)));
   PGB_CUDA(cudaMemcpy(pl->lowk_d, cols.data(), cols.size() * sizeof(int2), cudaMemcpyHostToDevice));
   pl->n_lowk = (int)cols.size();
+  pl->lowk_kx.clear();
+  for (const int2& c : cols) pl->lowk_kx.push_back(c.x);
+  return POISSON_OK;
+}
+
+// Item list of the fused spectral middle (float spectra of a supported shape; rebuilt with the
+// low-|k| list).
+int build_mid(poisson_plan* pl) {
+  if (pl->mid_d) cudaFree(pl->mid_d);
+  pl->mid_d = nullptr;
+  pl->mid_nitems = 0;
+  if (pl->fp64() || !spectral_fused_supported(pl->ny, pl->nz)) return POISSON_OK;
+  int n = 0;
+  const std::vector<int> items = spectral_fused_items(pl->nxh, pl->ny, pl->nz, pl->lowk_kx, &n);
+  if (n == 0) return POISSON_OK;
+  PGB_CUDA(cudaMalloc(&pl->mid_d, items.size() * sizeof(int)));
+  PGB_CUDA(cudaMemcpy(pl->mid_d, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice));
+  pl->mid_nitems = n;
   return POISSON_OK;
 }
 
@@ -150,7 +172,12 @@ void layout_workspace(poisson_plan* pl) {
   pl->off_spec = off;
   off = align256(off + (size_t)pl->nz * pl->g.plane * pl->csize());
   pl->off_stats = off;
-  off = align256(off + sizeof(Stats));
+  // the fused middle's scheduling counters (one set per pass of a solve) follow Stats, so one
+  // memset at the start of a solve clears both
+  pl->sched_words = spectral_fused_sched_words(pl->nxh);
+  pl->off_sched = off + ((sizeof(Stats) + 15) & ~(size_t)15);
+  pl->stats_bytes = pl->off_sched - pl->off_stats + 4 * sizeof(unsigned) * (size_t)pl->sched_words;
+  off = align256(off + pl->stats_bytes);
   pl->off_part = off;
   off = align256(off + 3 * sizeof(double) * (size_t)(pl->xinv_blocks + pl->nz));   // + one per level chunk
   pl->off_rpart = off;
@@ -235,6 +262,7 @@ int poisson_plan_destroy(poisson_plan* pl) {
   for (cudaEvent_t e : pl->prof.pool) cudaEventDestroy(e);
   if (pl->tables) cudaFree(pl->tables);
   if (pl->lowk_d) cudaFree(pl->lowk_d);
+  if (pl->mid_d) cudaFree(pl->mid_d);
   delete pl;
   return POISSON_OK;
 }
@@ -376,6 +404,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
     return rc;
   }
   int rc = build_lowk(pl);
+  if (rc == POISSON_OK) rc = build_mid(pl);
   if (rc != POISSON_OK) {
     poisson_plan_destroy(pl);
     return rc;
@@ -405,6 +434,7 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value >= 0) || value > 1e6) return POISSON_ERR_INVALID_ARG;
       pl->lowk_r2 = (int)value;
       int rc = build_lowk(pl);
+      if (rc == POISSON_OK) rc = build_mid(pl);
       if (rc != POISSON_OK) return rc;
       layout_workspace(pl);
       return POISSON_OK;
@@ -460,6 +490,10 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value == POISSON_LAYOUT_Z_Y_X || value == POISSON_LAYOUT_X_Y_Z)) return POISSON_ERR_INVALID_ARG;
       pl->layout = (int)value;
       layout_workspace(pl);
+      return POISSON_OK;
+    case POISSON_OPT_SPECTRAL_FUSED:
+      if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
+      pl->fused = (int)value;
       return POISSON_OK;
     case POISSON_OPT_PROFILE:
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
@@ -538,14 +572,21 @@ static int level_chunk(const poisson_plan* pl) {
 
 // Forward transform (chunked x-pass then y-pass) and column solve of one field.
 // With a residual source R, *res_nblocks receives the number of per-block residual-norm
-// partials the forward x-pass launches wrote (from R->part0 on).
+// partials the forward x-pass launches wrote (from R->part0 on).  pass: index of the pass
+// within the solve (0 = first solve, n = sweep n).  *middle_fused is set when the fused
+// spectral kernel ran the y-pass, the columns and the inverse y-pass (the inverse
+// transform then runs its x-pass only).
 static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_double, char* ws, cudaStream_t st,
                                    int adjoint, const int* done, const double* target_mean = nullptr,
-                                   const ResidualArgs* R = nullptr, int* res_nblocks = nullptr) {
+                                   const ResidualArgs* R = nullptr, int* res_nblocks = nullptr, int pass = 0,
+                                   bool* middle_fused = nullptr) {
   const bool t_double = pl->fp64();
   void* spec = ws + pl->off_spec;
   Stats* stats = (Stats*)(ws + pl->off_stats);
   const int lc = level_chunk(pl);
+  if (middle_fused) *middle_fused = false;
+  const bool try_fused = middle_fused && pl->fused && pl->mid_nitems > 0 && !adjoint && !t_double &&
+                         lc >= pl->nz && pass >= 0 && pass < 4;
   cudaError_t e = cudaSuccess;
   int rparts = 0;
   for (int l0 = 0; l0 < pl->nz; l0 += lc) {
@@ -569,6 +610,7 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
     }
     prof_end(pl, ps, st);
     if (e != cudaSuccess) return e;
+    if (try_fused) continue;
     ps = prof_begin(pl, POISSON_PHASE_YFWD, st);
     e = ypass(pl, gc, -1, spec, done, stats, st);
     prof_end(pl, ps, st);
@@ -590,17 +632,34 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
   A.done = done;
   A.target_mean = target_mean;
   A.col_tile = pl->coltile;
+  if (res_nblocks) *res_nblocks = rparts;
+  if (try_fused) {
+    bool used = false;
+    unsigned* sched = (unsigned*)(ws + pl->off_sched) + (size_t)pass * pl->sched_words;
+    int ps = prof_begin(pl, POISSON_PHASE_SPECTRAL, st);
+    e = launch_spectral_fused(A, pl->g, pl->fy, pl->tb, pl->mid_d, pl->mid_nitems, sched, st, &used);
+    prof_end(pl, ps, st);
+    if (e != cudaSuccess) return e;
+    if (used) {
+      *middle_fused = true;
+      return cudaSuccess;
+    }
+    ps = prof_begin(pl, POISSON_PHASE_YFWD, st);   // not launched: the separate y-pass after all
+    e = ypass(pl, pl->g, -1, spec, done, stats, st);
+    prof_end(pl, ps, st);
+    if (e != cudaSuccess) return e;
+  }
   const int ps = prof_begin(pl, POISSON_PHASE_COLUMNS, st);
   e = launch_thomas(A, pl->g, pl->tb, st);
   prof_end(pl, ps, st);
-  if (res_nblocks) *res_nblocks = rparts;
   return e;
 }
 
 // Inverse transform (chunked y-pass then x-pass with the given epilogue);
 // *nparts receives the number of partial-sum slots the x-pass launches wrote.
 static cudaError_t inverse(poisson_plan* pl, char* ws, cudaStream_t st, const int* done, int to_double, int mode,
-                           void* out, XinvExtra ex, int* nparts, bool* control_fused = nullptr) {
+                           void* out, XinvExtra ex, int* nparts, bool* control_fused = nullptr,
+                           bool skip_ypass = false) {
   if (control_fused) *control_fused = false;
   const bool t_double = pl->fp64();
   void* spec = ws + pl->off_spec;
@@ -612,10 +671,13 @@ static cudaError_t inverse(poisson_plan* pl, char* ws, cudaStream_t st, const in
     Geom gc = pl->g;
     gc.lev0 = l0;
     gc.lev1 = l0 + lc < pl->nz ? l0 + lc : pl->nz;
-    int ps = prof_begin(pl, POISSON_PHASE_YINV, st);
-    e = ypass(pl, gc, +1, spec, done, stats, st);
-    prof_end(pl, ps, st);
-    if (e != cudaSuccess) return e;
+    int ps = -1;
+    if (!skip_ypass) {
+      ps = prof_begin(pl, POISSON_PHASE_YINV, st);
+      e = ypass(pl, gc, +1, spec, done, stats, st);
+      prof_end(pl, ps, st);
+      if (e != cudaSuccess) return e;
+    }
     ex.part0 = part;
     int nb = 0;
     ps = prof_begin(pl, POISSON_PHASE_XINV, st);
@@ -671,20 +733,22 @@ static cudaError_t from_solver_layout(const poisson_plan* pl, const void* src, v
 // The solve on fields in the solver's layout.
 static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cudaStream_t st) {
   Stats* stats = (Stats*)(ws + pl->off_stats);
-  PGB_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), st));
+  PGB_CUDA(cudaMemsetAsync(stats, 0, pl->stats_bytes, st));
   const bool t_double = pl->fp64();
   XinvExtra ex{};
   ex.partials = (double*)(ws + pl->off_part);
   if (!pl->mixed()) {
-    PGB_CUDA(forward_columns(pl, S, t_double, ws, st, 0, nullptr));
-    PGB_CUDA(inverse(pl, ws, st, nullptr, t_double, XINV_PLAIN, p, ex, nullptr));
+    bool mid = false;
+    PGB_CUDA(forward_columns(pl, S, t_double, ws, st, 0, nullptr, nullptr, nullptr, nullptr, 0, &mid));
+    PGB_CUDA(inverse(pl, ws, st, nullptr, t_double, XINV_PLAIN, p, ex, nullptr, nullptr, mid));
   } else {
     const int* done = &stats->done;
     float* p0 = (float*)(ws + pl->off_p0);
     float* q = (float*)(ws + pl->off_q);
     int nb = 0;
     // first solve: double source, float transforms, double low-|k| columns
-    PGB_CUDA(forward_columns(pl, S, 1, ws, st, 0, nullptr));
+    bool mid = false;
+    PGB_CUDA(forward_columns(pl, S, 1, ws, st, 0, nullptr, nullptr, nullptr, nullptr, 0, &mid));
     ex.p0 = p0;
     ex.p_out = pl->max_sweeps == 0 ? (double*)p : nullptr;
     ex.ctl_stats = stats;
@@ -693,7 +757,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
     ex.ctl_npoints = pl->g.N;
     ex.ctl_pass = 0;
     bool fused = false;
-    PGB_CUDA(inverse(pl, ws, st, nullptr, 0, XINV_P0, p0, ex, &nb, &fused));
+    PGB_CUDA(inverse(pl, ws, st, nullptr, 0, XINV_P0, p0, ex, &nb, &fused, mid));
     cudaError_t e = cudaSuccess;
     if (!fused) {
       int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
@@ -726,7 +790,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
       R.cy = pl->cy;
       R.mu_ff = &stats->mu_ff;
       int nres = 0;
-      PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R, &nres));
+      PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R, &nres, sweep, &mid));
       const bool last_allowed = sweep == pl->max_sweeps;
       XinvExtra eu = ex;
       eu.p0 = p0;
@@ -738,7 +802,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
       eu.ctl_pass = sweep;
       eu.res_partials = rpart;
       eu.res_nblocks = nres;
-      PGB_CUDA(inverse(pl, ws, st, done, 0, XINV_UPDATE, nullptr, eu, &nb, &fused));
+      PGB_CUDA(inverse(pl, ws, st, done, 0, XINV_UPDATE, nullptr, eu, &nb, &fused, mid));
       if (!fused) {
         int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
         e = launch_control(stats, ex.partials, nb, rpart, nres, sweep, pl->max_sweeps, pl->tol, pl->g.N,

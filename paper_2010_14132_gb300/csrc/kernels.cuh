@@ -2,6 +2,9 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <vector>
+
 #include "fft_engine.cuh"
 
 namespace pgb {
@@ -190,6 +193,17 @@ struct ThomasArgs {
   int singular00;             // 1: zero flux at the top, so the (0,0) column is singular (projected, pinned)
 };
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
+
+// Fused spectral middle (spectral_fused.cu): forward y-pass, forward column solves and inverse
+// y-pass of one pass in one persistent kernel over per-strip items.  Float spectra, ny in
+// {256, 512, 1024}, nz <= 256.  The item list is built once per plan on the host (lowk_kx: kx of
+// every listed low-|k| column, in list order); sched: spectral_fused_sched_words(nxh) zeroed words
+// per launch.  *used = false when the shape or the arguments do not allow it.
+bool spectral_fused_supported(int ny, int nz);
+std::vector<int> spectral_fused_items(int nxh, int ny, int nz, const std::vector<int>& lowk_kx, int* nitems);
+int spectral_fused_sched_words(int nxh);
+cudaError_t launch_spectral_fused(const ThomasArgs& T, const Geom& g, const FftPlan& fy, const Tables& tb,
+                                  const int* items, int nitems, unsigned* sched, cudaStream_t st, bool* used);
 
 // q = p - p0 (float) from the stored double iterate, before a second or third sweep (skipped when done).
 cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long long n, const int* done,
