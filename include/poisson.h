@@ -111,11 +111,16 @@ typedef enum {
   POISSON_OPT_LAYOUT = 11,       /* layout of the caller's fields (S, p, gp, gS), a poisson_layout value;
                                     default POISSON_LAYOUT_Z_Y_X.  Any other layout adds two field-sized
                                     buffers to the workspace (query the size after setting it) */
-  POISSON_OPT_SPECTRAL_FUSED = 12 /* 1: the forward y-pass, the column solves and the inverse y-pass of
+  POISSON_OPT_SPECTRAL_FUSED = 12,/* 1: the forward y-pass, the column solves and the inverse y-pass of
                                     each forward solve run as one persistent kernel over strips of 8 kx,
                                     each strip's spectrum kept in L2 between the three steps, where the
                                     plan allows it (float spectrum, ny in {256, 512, 1024}, nz <= 256,
                                     one level chunk); 0 (default): three separate kernels */
+  POISSON_OPT_RESIDUAL_PASS = 13  /* mixed: how a sweep forms its residual.  0 (default): the x-pass forms
+                                    r while it loads its rows; 1 (where nx % 64 == 0, ny % 8 == 0, one
+                                    level chunk): a stencil pass marching up the levels writes r as
+                                    float (one more field-sized buffer in the workspace; query the size
+                                    after setting it), then the plain R2C x-pass transforms it */
 } poisson_option;
 
 /* Field layouts (POISSON_OPT_LAYOUT), C order, outermost index first. */

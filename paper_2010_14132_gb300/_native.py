@@ -32,6 +32,7 @@ POISSON_OPT_X_KERNEL = 9
 POISSON_OPT_COL_TILE = 10
 POISSON_OPT_LAYOUT = 11
 POISSON_OPT_SPECTRAL_FUSED = 12
+POISSON_OPT_RESIDUAL_PASS = 13
 POISSON_LAYOUT_Z_Y_X = 0
 POISSON_LAYOUT_X_Y_Z = 1
 PHASES = ("xfwd", "yfwd", "columns", "yinv", "xinv", "residual", "control", "spectral")

@@ -34,7 +34,7 @@ COL_CANDIDATES = [dict(col_tile=c) for c in (0, 1, 4, 3, 16, 32)]
 OPT_IDS = {"y_kernel": N.POISSON_OPT_Y_KERNEL, "y_tile": N.POISSON_OPT_Y_TILE, "y_elems": N.POISSON_OPT_Y_ELEMS,
            "x_elems": N.POISSON_OPT_X_ELEMS, "level_chunk": N.POISSON_OPT_LEVEL_CHUNK,
            "x_kernel": N.POISSON_OPT_X_KERNEL, "col_tile": N.POISSON_OPT_COL_TILE,
-           "spectral_fused": N.POISSON_OPT_SPECTRAL_FUSED}
+           "spectral_fused": N.POISSON_OPT_SPECTRAL_FUSED, "residual_pass": N.POISSON_OPT_RESIDUAL_PASS}
 
 
 def _key(nx, ny, nz, dtype):

@@ -79,7 +79,7 @@ struct poisson_plan {
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
   int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 4, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
-      coltile = 0, fused = 0;
+      coltile = 0, fused = 0, respass = 0;
   unsigned version = 0;   // bumped by every option change (invalidates captured batch graphs)
   double tol = 1e-10;
   Geom g{};
@@ -95,7 +95,7 @@ struct poisson_plan {
   int sched_words = 0;          // per-pass scheduling counters of the fused middle
   float2 cx{}, cy{};
   // workspace layout
-  size_t off_spec = 0, off_stats = 0, off_sched = 0, stats_bytes = 0, off_part = 0, off_rpart = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
+  size_t off_spec = 0, off_stats = 0, off_sched = 0, stats_bytes = 0, off_part = 0, off_rpart = 0, off_r = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
          off_gp = 0, off_fa = 0, off_fb = 0, ws_bytes = 0;
   int xinv_blocks = 1, grho_nb = 1;
   PhaseProfiler prof;
@@ -191,6 +191,12 @@ void layout_workspace(poisson_plan* pl) {
     off = align256(off + sizeof(float) * (size_t)N);
     pl->off_q = off;
     off = align256(off + sizeof(float) * (size_t)N);
+    if (pl->respass && residual_stencil_supported(pl->nx, pl->ny)) {   // the sweep's residual r (float)
+      pl->off_r = off;
+      off = align256(off + sizeof(float) * (size_t)N);
+    } else {
+      pl->off_r = 0;
+    }
   }
   pl->off_gp = off;
   off = align256(off + 2 * sizeof(double) * (size_t)(pl->nz - 1) * pl->grho_nb);
@@ -495,6 +501,11 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->fused = (int)value;
       return POISSON_OK;
+    case POISSON_OPT_RESIDUAL_PASS:
+      if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
+      pl->respass = (int)value;
+      layout_workspace(pl);
+      return POISSON_OK;
     case POISSON_OPT_PROFILE:
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->prof.on = value != 0;
@@ -599,7 +610,18 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
       ResidualArgs Rc = *R;
       Rc.part0 = R->part0 + rparts;
       int nb = 0;
-      if (pl->xkernel == 0) e = launch_xres_static(Rc, spec, gc, pl->fx, pl->tb, done, &stats->err, &nb, st, &used);
+      if (pl->respass && pl->off_r && pl->xkernel == 0 && lc >= pl->nz) {
+        // the residual as its own pass into a float field, then the plain R2C x-pass of it
+        float* r = (float*)(ws + pl->off_r);
+        e = launch_residual_stencil(Rc, r, gc, done, &nb, st, &used);
+        if (e == cudaSuccess && used) {
+          bool xused = false;
+          e = launch_xfwd_static(0, r, spec, gc, pl->fx, pl->tb, done, &stats->err, st, &xused);
+          if (e == cudaSuccess && !xused) e = launch_xfwd(0, 0, r, spec, gc, pl->fx, pl->tb, done, st);
+        }
+      }
+      if (e == cudaSuccess && !used && pl->xkernel == 0)
+        e = launch_xres_static(Rc, spec, gc, pl->fx, pl->tb, done, &stats->err, &nb, st, &used);
       if (e == cudaSuccess && !used) e = launch_xfwd_residual(Rc, spec, gc, pl->fx, pl->tb, done, &nb, st);
       rparts += nb;
     } else {

@@ -194,6 +194,14 @@ struct ThomasArgs {
 };
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
 
+// Refinement residual as its own pass (residual_stencil.cu): r = S - mu_W - L (p0 + q) as float
+// into r_out, one z-marching tile kernel; per-CTA r^2, S^2 partials from R.part0.  nx % 64 == 0,
+// ny % 8 == 0, all levels in one launch; *used = false otherwise.
+bool residual_stencil_supported(int nx, int ny);
+long long residual_stencil_blocks(int nx, int ny, int nz);
+cudaError_t launch_residual_stencil(const ResidualArgs& R, float* r_out, const Geom& g, const int* done,
+                                    int* nblocks_out, cudaStream_t st, bool* used);
+
 // Fused spectral middle (spectral_fused.cu): forward y-pass, forward column solves and inverse
 // y-pass of one pass in one persistent kernel over per-strip items.  Float spectra, ny in
 // {256, 512, 1024}, nz <= 256.  The item list is built once per plan on the host (lowk_kx: kx of

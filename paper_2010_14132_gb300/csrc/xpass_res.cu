@@ -12,8 +12,14 @@ namespace {
 // p0 (and q) are staged; the x-neighbours come from the staged rows, the y- and
 // z-neighbour rows are read through L1/L2 (the neighbouring groups stage them).
 // ---------------------------------------------------------------------------
+// CTAs per SM the register budget is set for: the correction q's extra stencil values spill at
+// three CTAs of 256 threads (80 registers), so the q variant takes two (PGB_XRES_Q_BLOCKS)
+#ifndef PGB_XRES_Q_BLOCKS
+#define PGB_XRES_Q_BLOCKS 2
+#endif
+constexpr int xres_min_blocks(int e, bool has_q) { return e >= 24 ? 2 : (e >= 16 ? 4 : (has_q ? PGB_XRES_Q_BLOCKS : 3)); }
 template <int N, int E, bool HAS_Q, bool STAGE_P>
-__global__ void __launch_bounds__(xs_threads(E), E >= 24 ? 2 : (E >= 16 ? 4 : 3)) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
+__global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
                                                       const int* __restrict__ done, unsigned* __restrict__ err,
                                                       int ns, unsigned stage_bytes) {

@@ -34,7 +34,7 @@ def main(argv=None) -> int:
     ap.add_argument("--tuned", action="store_true")
     ap.add_argument("--cg", type=float, default=None, metavar="EPS")
     ap.add_argument("--max-sweeps", dest="max_sweeps", type=int, default=None)
-    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel", "col_tile", "spectral_fused"):
+    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel", "col_tile", "spectral_fused", "residual_pass"):
         ap.add_argument("--" + name.replace("_", "-"), dest=name, type=int, default=None)
     args = ap.parse_args(argv)
     d = wl.anelastic_noise(args.nx, args.ny, args.nz, seed=3)
@@ -42,7 +42,7 @@ def main(argv=None) -> int:
     if args.tuned:
         from .autotune import tuned_options
         opts = tuned_options(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, args.dtype)
-    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel", "col_tile", "spectral_fused"):
+    for name in ("y_kernel", "y_tile", "y_elems", "x_elems", "level_chunk", "x_kernel", "col_tile", "spectral_fused", "residual_pass"):
         if getattr(args, name) is not None:
             opts[name] = getattr(args, name)
     if args.max_sweeps is not None:

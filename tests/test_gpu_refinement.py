@@ -90,3 +90,21 @@ def test_stop_after_first_sweep_writes_the_double_iterate():
     np.testing.assert_allclose(p_loose, p_one, rtol=2e-14, atol=2e-14 * np.abs(p_one).max())
     ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
     assert O.relative_l2(p_loose, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("shape", [(256, 192, 48), (128, 64, 17), (64, 8, 3), (192, 256, 40)])
+def test_residual_pass_equals_fused_residual(shape):
+    """The sweep's residual as its own stencil pass (z-marching tiles, then the plain x-pass of r)
+    gives bit for bit the fused residual x-pass's result: the same double-float arithmetic on the
+    same stencil values, the same transform.  Shapes: several tiles and z-chunks, a ragged last
+    z-chunk (17 levels), one tile of eight rows (the y halo wraps onto the tile itself), and
+    192 = 3 x 64 points in x."""
+    nx, ny, nz = shape
+    d = wl.anelastic_noise(nx, ny, nz, seed=50 + nz)
+    p1, i1 = _solve(d, residual_pass=1, max_sweeps=3, tolerance=1e-300)
+    p0, i0 = _solve(d, residual_pass=0, max_sweeps=3, tolerance=1e-300)
+    np.testing.assert_array_equal(p1, p0)
+    assert i1["rel_update"] == i0["rel_update"]
+    assert i1["rel_residual"][:3] == pytest.approx(i0["rel_residual"][:3], rel=1e-5)
+    ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
+    assert O.relative_l2(p1, ref) <= 1e-10
