@@ -70,10 +70,52 @@ __device__ __forceinline__ ResCoef res_coef(float2 cx, float2 cy, float2 A, floa
 // r at the two points.  pc, pe, pw, pn, ps, pd, pu: p0 at the points and at their
 // east, west, north, south, lower and upper neighbours (pd = pc at the bottom,
 // pu = 0 above the top level); likewise for q when HAS_Q.  Sh, Sl: the split of S.
-template <bool HAS_Q>
+// ISO: dx == dy (cx == cy as double-float pairs).  The x and y second differences are then
+// summed first, pe + pw + pn + ps - 4 pc exactly as a double-float pair (four TwoSums; -4 pc is
+// exact), and multiplied by 1/dx^2 once: one product chain and one TwoSum fewer than the
+// general form, with the same double-float accuracy.
+template <bool HAS_Q, bool ISO = false>
 __device__ __forceinline__ float2 residual_value2(float2 pc, float2 pe, float2 pw, float2 pn, float2 ps, float2 pd,
                                                   float2 pu, float2 qc, float2 qe, float2 qw, float2 qn, float2 qs,
                                                   float2 qd, float2 qu, float2 Sh, float2 Sl, const ResCoef& k) {
+  if constexpr (ISO) {
+    float2 s1, e1, s2, e2, s3, e3, s4, e4;
+    two_sum2(pe, pw, s1, e1);
+    two_sum2(pn, ps, s2, e2);
+    two_sum2(s1, s2, s3, e3);
+    two_sum2(s3, mul2(pc, make_float2(-4.f, -4.f)), s4, e4);
+    float2 dl = add2(add2(e1, e2), add2(e3, e4));
+    if (HAS_Q) dl = add2(dl, fma2(qc, make_float2(-4.f, -4.f), add2(add2(qe, qw), add2(qn, qs))));
+    const float2 nthh = mul2(k.ncxh, s4);                      // -(cx s4) rounded
+    const float2 thl = fma2(k.cxh, dl, fma2(k.cxl, s4, fma2(k.cxh, s4, nthh)));
+    // z: a (pd - pc) + c (pu - pc), differences first, q's exactly as well
+    float2 dd, ed, du, eu;
+    two_diff2(pd, pc, dd, ed);
+    two_diff2(pu, pc, du, eu);
+    if (HAS_Q) {
+      float2 dq, eq, t, et;
+      two_diff2(qd, qc, dq, eq);
+      two_sum2(dd, dq, t, et);
+      dd = t;
+      ed = add2(ed, add2(eq, et));
+      two_diff2(qu, qc, dq, eq);
+      two_sum2(du, dq, t, et);
+      du = t;
+      eu = add2(eu, add2(eq, et));
+    }
+    const float2 np1 = mul2(k.nah, dd);
+    const float2 l1 = fma2(k.ah, ed, fma2(k.al, dd, fma2(k.ah, dd, np1)));
+    const float2 np2 = mul2(k.nch, du);
+    const float2 l2 = fma2(k.ch, eu, fma2(k.cl, du, fma2(k.ch, du, np2)));
+    float2 b, eb, c, ec;
+    two_sum2(np1, np2, b, eb);
+    two_sum2(nthh, b, c, ec);                                  // -Lp high, exact with eb + ec
+    const float2 lp_lo = sub2(add2(thl, add2(l1, l2)), add2(eb, ec));   // Lp low
+    float2 t, et, r, er;
+    two_diff2(Sh, k.muh, t, et);
+    two_sum2(t, c, r, er);
+    return add2(r, add2(er, sub2(add2(et, sub2(Sl, k.mul)), lp_lo)));
+  }
   const float2 m2 = make_float2(-2.f, -2.f);
   const float2 m2pc = mul2(pc, m2);
   float2 s1, e1, s2, e2;

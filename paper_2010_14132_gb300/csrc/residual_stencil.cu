@@ -41,7 +41,7 @@ __device__ __forceinline__ float2 load_one(const ResidualArgs& R, long long idx)
   return make_float2(__ldg(R.p0 + idx), HAS_Q ? __ldg(R.q + idx) : 0.f);
 }
 
-template <bool HAS_Q>
+template <bool HAS_Q, bool ISO>
 __global__ void __launch_bounds__(kRsTX / 2 * kRsTY, 3) k_res_stencil(ResidualArgs R, float* __restrict__ r_out, Geom g,
                                                                    const int* __restrict__ done) {
   pdl_trigger();
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kRsTX / 2 * kRsTY, 3) k_res_stencil(ResidualAr
     d2ff_trunc(Sv.y, Sh.y, Sl.y);
     const ResCoef K = res_coef(cx, cy, R.a_ff[k], R.c_ff[k], mu);
     const float2 pu = has_up ? up.p : make_float2(0.f, 0.f), qu = has_up ? up.q : make_float2(0.f, 0.f);
-    const float2 rr = residual_value2<HAS_Q>(c.p, make_float2(c.p.y, pe), make_float2(pw, c.p.x), north.p, south.p,
+    const float2 rr = residual_value2<HAS_Q, ISO>(c.p, make_float2(c.p.y, pe), make_float2(pw, c.p.x), north.p, south.p,
                                              dn.p, pu, c.q, make_float2(c.q.y, qe), make_float2(qw, c.q.x), north.q,
                                              south.q, dn.q, qu, Sh, Sl, K);
     __stcs(reinterpret_cast<float2*>(r_out) + (long long)k * plane2 + row2, rr);
@@ -167,8 +167,13 @@ cudaError_t launch_residual_stencil(const ResidualArgs& R, float* r_out, const G
   const dim3 grid(g.nx / kRsTX, g.ny / kRsTY, (g.nz + kRsZC - 1) / kRsZC);
   if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
   *used = true;
-  if (R.q) return pdl_launch(k_res_stencil<true>, grid, dim3(kRsTX / 2 * kRsTY), 0, st, R, r_out, g, done);
-  return pdl_launch(k_res_stencil<false>, grid, dim3(kRsTX / 2 * kRsTY), 0, st, R, r_out, g, done);
+  const dim3 block(kRsTX / 2 * kRsTY);
+  if (R.cx.x == R.cy.x && R.cx.y == R.cy.y) {   // dx == dy: merged horizontal term
+    if (R.q) return pdl_launch(k_res_stencil<true, true>, grid, block, 0, st, R, r_out, g, done);
+    return pdl_launch(k_res_stencil<false, true>, grid, block, 0, st, R, r_out, g, done);
+  }
+  if (R.q) return pdl_launch(k_res_stencil<true, false>, grid, block, 0, st, R, r_out, g, done);
+  return pdl_launch(k_res_stencil<false, false>, grid, block, 0, st, R, r_out, g, done);
 }
 
 }  // namespace pgb

@@ -3,6 +3,12 @@
 // for the persistent staging scheme the kernels share.)
 #include "xpass_common.cuh"
 
+// This file is compiled twice: PGB_XRES_ISO 0 here (the general kernels and the dispatcher), and 1
+// from xpass_res_iso.cu (the dx == dy kernels), so that the two sets of instances build in parallel.
+#ifndef PGB_XRES_ISO
+#define PGB_XRES_ISO 0
+#endif
+
 namespace pgb {
 namespace {
 
@@ -18,7 +24,7 @@ namespace {
 #define PGB_XRES_Q_BLOCKS 2
 #endif
 constexpr int xres_min_blocks(int e, bool has_q) { return e >= 24 ? 2 : (e >= 16 ? 4 : (has_q ? PGB_XRES_Q_BLOCKS : 3)); }
-template <int N, int E, bool HAS_Q, bool STAGE_P>
+template <int N, int E, bool HAS_Q, bool STAGE_P, bool ISO>
 __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
                                                       const int* __restrict__ done, unsigned* __restrict__ err,
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xr
       d2ff_trunc(S.x, Sh.x, Sl.x);
       d2ff_trunc(S.y, Sh.y, Sl.y);
       // the pair's east neighbours are (pc.y, pe), its west neighbours (pw, pc.x)
-      v[i] = residual_value2<HAS_Q>(pc, make_float2(pc.y, pe), make_float2(pw, pc.x), pn, ps, pd, pu, qc,
+      v[i] = residual_value2<HAS_Q, ISO>(pc, make_float2(pc.y, pe), make_float2(pw, pc.x), pn, ps, pd, pu, qc,
                                     make_float2(qc.y, qe), make_float2(qw, qc.x), qn, qs, qd, qu, Sh, Sl, K);
       if (valid) {
         racc = fma2(v[i], v[i], racc);
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xr
   }
 }
 
-template <bool HAS_Q>
+template <bool HAS_Q, bool ISO>
 cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, int E, const Tables& tb,
                    const int* done, unsigned* err, int* nblocks_out, cudaStream_t st, bool* used) {
   const int RB = xs_threads(E) / (N / E);
@@ -187,12 +193,12 @@ cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, in
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
   if (stage_p) {
     PGB_XS_E8_24_SWITCH(E, PGB_XS_N_SWITCH(N, {
-      return xs_launch(k_xres_s<NN, EE, HAS_Q, true>, NN / EE, RB, c, ngroups, nblocks_out, st, used, R, spec, g,
+      return xs_launch(k_xres_s<NN, EE, HAS_Q, true, ISO>, NN / EE, RB, c, ngroups, nblocks_out, st, used, R, spec, g,
                        tb.twx_f, tb.twr_f, done, err);
     }));
   } else {
     PGB_XS_E8_24_SWITCH(E, PGB_XS_N_SWITCH(N, {
-      return xs_launch(k_xres_s<NN, EE, HAS_Q, false>, NN / EE, RB, c, ngroups, nblocks_out, st, used, R, spec, g,
+      return xs_launch(k_xres_s<NN, EE, HAS_Q, false, ISO>, NN / EE, RB, c, ngroups, nblocks_out, st, used, R, spec, g,
                        tb.twx_f, tb.twr_f, done, err);
     }));
   }
@@ -201,13 +207,30 @@ cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, in
 
 }  // namespace
 
+#if PGB_XRES_ISO
+cudaError_t launch_xres_static_iso(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx,
+                                   const Tables& tb, const int* done, unsigned* err, int* nblocks_out,
+                                   cudaStream_t st, bool* used) {
+  const int E = fx.n % 3 == 0 ? 24 : 8;
+  if (R.q) return xres_s<true, true>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
+  return xres_s<false, true>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
+}
+#else
+cudaError_t launch_xres_static_iso(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx,
+                                   const Tables& tb, const int* done, unsigned* err, int* nblocks_out,
+                                   cudaStream_t st, bool* used);
+
 cudaError_t launch_xres_static(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx, const Tables& tb,
                                const int* done, unsigned* err, int* nblocks_out, cudaStream_t st, bool* used) {
   *used = false;
   if (!xpass_static_supported(fx.n)) return cudaSuccess;
   const int E = fx.n % 3 == 0 ? 24 : 8;   // the residual kernel: 8 elements per thread for powers of two
-  if (R.q) return xres_s<true>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
-  return xres_s<false>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
+  // dx == dy: the kernels with the merged horizontal term
+  if (R.cx.x == R.cy.x && R.cx.y == R.cy.y)
+    return launch_xres_static_iso(R, spec, g, fx, tb, done, err, nblocks_out, st, used);
+  if (R.q) return xres_s<true, false>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
+  return xres_s<false, false>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
 }
+#endif
 
 }  // namespace pgb
