@@ -81,7 +81,8 @@ typedef enum {
                                     double; default 64 (|k| <= 8); the (0,0) column always does */
   POISSON_OPT_MAX_SWEEPS = 1,    /* mixed: refinement sweeps after the first solve, 0..3; default 3 */
   POISSON_OPT_TOLERANCE = 2,     /* mixed: the refinement stops once its error bound (error_estimate of
-                                    poisson_info) is at most this relative L2 error; default 1e-10 */
+                                    poisson_info) is at most this relative L2 error; default 1e-10.  A
+                                    tolerance below the plan's accuracy_floor is never met */
   POISSON_OPT_Y_TILE = 3,        /* y-pass kx tile width (autotuner hook); 0 = plan default (8 for the
                                     FP32 compile-time-FFT kernels) */
   POISSON_OPT_PROFILE = 4,       /* 1: record CUDA events around every kernel launch of this plan on
@@ -116,11 +117,19 @@ typedef enum {
                                     each strip's spectrum kept in L2 between the three steps, where the
                                     plan allows it (float spectrum, ny in {256, 512, 1024}, nz <= 256,
                                     one level chunk); 0 (default): three separate kernels */
-  POISSON_OPT_RESIDUAL_PASS = 13  /* mixed: how a sweep forms its residual.  0 (default): the x-pass forms
+  POISSON_OPT_RESIDUAL_PASS = 13, /* mixed: how a sweep forms its residual.  0 (default): the x-pass forms
                                     r while it loads its rows; 1 (where nx % 64 == 0, ny % 8 == 0, one
                                     level chunk): a stencil pass marching up the levels writes r as
                                     float (one more field-sized buffer in the workspace; query the size
                                     after setting it), then the plain R2C x-pass transforms it */
+  POISSON_OPT_VERIFY = 14         /* mixed: 1 (default): from the second sweep on, once a sweep's column
+                                    solves are done, the norm of its correction delta_n (Parseval on the
+                                    solved half spectrum) bounds the error of the current iterate,
+                                    ||e_{n-1}|| <= ||delta_n||/(1 - phi) <= 2 ||delta_n|| for a contraction
+                                    phi <= 1/2 (||delta_n||/(1 - phi) with the measured phi when that is
+                                    above 1/2); if that bound is at most the tolerance the solve returns
+                                    p_{n-1} without the sweep's inverse transforms (the two-threads-per-
+                                    column kernel only).  0: every sweep is applied in full */
 } poisson_option;
 
 /* Field layouts (POISSON_OPT_LAYOUT), C order, outermost index first. */
@@ -153,22 +162,41 @@ typedef enum {
  * p_{n-1} (p_0 = the first FP32 solve), solves for its correction delta_n and
  * updates p_n = p_{n-1} + delta_n. */
 typedef struct {
-  int sweeps;                  /* refinement sweeps executed (mixed path; 0 otherwise) */
+  int sweeps;                  /* refinement corrections applied (mixed path; 0 otherwise): the result is
+                                  iterate p_sweeps */
   int converged;               /* 1 if the mixed stopping test passed (always 1 for FP64/FP32) */
-  double rel_update[4];        /* ||delta_n||_2/||p_n||_2 of sweep n (index 0 = first solve = 1) */
-  double error_estimate;       /* mixed path, after the last sweep n: a bound on ||p_n - p||_2/||p||_2
-                                  from the successive corrections.  With e_n the error of p_n,
+  double rel_update[4];        /* ||delta_n||_2/||p_n||_2 of sweep n (index 0 = first solve = 1).  When the
+                                  solve stopped on a verification (POISSON_OPT_VERIFY), entry sweeps + 1
+                                  holds the relative norm of the correction that certified the result
+                                  and was not applied */
+  double error_estimate;       /* mixed path: a bound on ||p_n - p||_2/||p||_2 for the returned iterate
+                                  p_n, from the successive corrections.  With e_n the error of p_n,
                                   e_{n-1} = delta_n + e_n, so a sweep contracting the error by
-                                  phi <= 1/2 gives ||e_n|| <= phi/(1-phi) ||delta_n|| <= ||delta_n||:
-                                  the bound is rel_update[n], times phi/(1-phi) when the measured
-                                  contraction phi = rel_update[n]/rel_update[n-1] exceeds 1/2, and
-                                  +inf when phi >= 1.  The solve converges when it is at most the
-                                  tolerance.  -1 when no sweep ran */
+                                  phi <= 1/2 gives ||e_n|| <= phi/(1-phi) ||delta_n|| <= ||delta_n||
+                                  (bound rel_update[n] after applying delta_n) and
+                                  ||e_{n-1}|| <= ||delta_n||/(1-phi) <= 2 ||delta_n|| (bound
+                                  2 rel_update[n] for p_{n-1}, when delta_n verified it and was not
+                                  applied); with a measured contraction
+                                  phi = rel_update[n]/rel_update[n-1] above 1/2 the factors are
+                                  phi/(1-phi) and 1/(1-phi), and the bound is +inf when phi >= 1.  The
+                                  corrections see only the error that sweeps can remove; the bound adds
+                                  accuracy_floor for the part the residual's rounding leaves.  The
+                                  solve converges when it is at most the tolerance.  -1 when no sweep
+                                  ran */
   double removed_weighted_mean;/* mu_W removed from S (first solve) */
   double rel_residual[4];      /* ||S - mu_W - L p_n||_2 / ||S||_2 of iterate n (index 0 = the first
                                   solve), formed in double-float arithmetic in the forward x-pass of
-                                  sweep n+1; entries n >= sweeps are -1 (the last iterate's residual
-                                  is not formed).  -1 for FP64/FP32 plans */
+                                  sweep n+1; -1 where no such sweep ran (the returned iterate's own
+                                  residual is formed only when a verification sweep ran).  mu_W is the
+                                  one removed_weighted_mean reports.  -1 for FP64/FP32 plans */
+  double accuracy_floor;       /* mixed path: the limiting accuracy F included in error_estimate, the
+                                  relative error that the double-float residual's rounding (unit
+                                  roundoff u = 2^-48) leaves however many sweeps run:
+                                  F = u K sqrt(eta) sqrt(mean over the operator's nonsingular modes
+                                  of 1/lambda^2), K the largest coefficient sum of the 7-point
+                                  operator, eta = nz sum W_k^2/(sum W_k)^2.  A plan constant (it
+                                  changes with poisson_plan_set_rho0); tolerances below it are never
+                                  met.  -1 for FP64/FP32 plans */
 } poisson_info;
 
 /* Create a plan (Section 2.1: the solver plans once per grid and reuses the plan every

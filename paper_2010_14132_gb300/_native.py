@@ -33,6 +33,7 @@ POISSON_OPT_COL_TILE = 10
 POISSON_OPT_LAYOUT = 11
 POISSON_OPT_SPECTRAL_FUSED = 12
 POISSON_OPT_RESIDUAL_PASS = 13
+POISSON_OPT_VERIFY = 14
 POISSON_LAYOUT_Z_Y_X = 0
 POISSON_LAYOUT_X_Y_Z = 1
 PHASES = ("xfwd", "yfwd", "columns", "yinv", "xinv", "residual", "control", "spectral")
@@ -59,6 +60,7 @@ class PoissonInfo(C.Structure):
         ("error_estimate", C.c_double),
         ("removed_weighted_mean", C.c_double),
         ("rel_residual", C.c_double * 4),
+        ("accuracy_floor", C.c_double),
     ]
 
     def as_dict(self):
@@ -66,7 +68,7 @@ class PoissonInfo(C.Structure):
             "sweeps": self.sweeps, "converged": bool(self.converged),
             "rel_update": list(self.rel_update), "error_estimate": self.error_estimate,
             "removed_weighted_mean": self.removed_weighted_mean,
-            "rel_residual": list(self.rel_residual),
+            "rel_residual": list(self.rel_residual), "accuracy_floor": self.accuracy_floor,
         }
 
 

@@ -79,7 +79,7 @@ struct poisson_plan {
   std::vector<double> dz, rho0;
   FftPlan fx{}, fy{};
   int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 4, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
-      coltile = 0, fused = 0, respass = 0;
+      coltile = 0, fused = 0, respass = 0, verify = 1;
   unsigned version = 0;   // bumped by every option change (invalidates captured batch graphs)
   double tol = 1e-10;
   Geom g{};
@@ -95,7 +95,8 @@ struct poisson_plan {
   int sched_words = 0;          // per-pass scheduling counters of the fused middle
   float2 cx{}, cy{};
   // workspace layout
-  size_t off_spec = 0, off_stats = 0, off_sched = 0, stats_bytes = 0, off_part = 0, off_rpart = 0, off_r = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
+  size_t off_spec = 0, off_stats = 0, off_sched = 0, stats_bytes = 0, off_part = 0, off_rpart = 0, off_sqn = 0,
+         off_r = 0, off_lz = 0, off_lw = 0, off_p0 = 0, off_q = 0,
          off_gp = 0, off_fa = 0, off_fb = 0, ws_bytes = 0;
   int xinv_blocks = 1, grho_nb = 1;
   PhaseProfiler prof;
@@ -182,6 +183,8 @@ void layout_workspace(poisson_plan* pl) {
   off = align256(off + 3 * sizeof(double) * (size_t)(pl->xinv_blocks + pl->nz));   // + one per level chunk
   pl->off_rpart = off;
   off = align256(off + 2 * sizeof(double) * (size_t)(pl->xinv_blocks + pl->nz));
+  pl->off_sqn = off;   // per-CTA squared norms of a verification solve (column tiles of >= 16 columns)
+  off = align256(off + sizeof(double) * (size_t)(pl->g.plane / 16 + 1 + pl->n_lowk));
   pl->off_lz = off;
   off = align256(off + sizeof(double2) * (size_t)pl->nz * pl->n_lowk);
   pl->off_lw = off;
@@ -350,7 +353,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
                o_aff = take(nz * 8), o_cff = take(nz * 8), o_lxd = take(pl->nxh * 8),
                o_lyd = take(ny * 8), o_lxf = take(pl->nxh * 4), o_lyf = take(ny * 4), o_twxd = take(n * 16),
                o_twrd = take(pl->nxh * 16), o_twyd = take(ny * 16), o_twxf = take(n * 8), o_twrf = take(pl->nxh * 8),
-               o_twyf = take(ny * 8), o_dz = take(nz * 8), o_rho = take(nz * 8);
+               o_twyf = take(ny * 8), o_dz = take(nz * 8), o_rho = take(nz * 8), o_floor = take(8);
   cudaError_t e = cudaMalloc(&pl->tables, off);
   if (e != cudaSuccess) {
     delete pl;
@@ -398,11 +401,14 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
   tb.twx_f = (float2*)(base + o_twxf);
   tb.twr_f = (float2*)(base + o_twrf);
   tb.twy_f = (float2*)(base + o_twyf);
+  tb.floor_d = (double*)(base + o_floor);
   pl->dz_d = (double*)(base + o_dz);
   pl->rho_d = (double*)(base + o_rho);
   if (ce == cudaSuccess)
     ce = launch_coefficients(pl->dz_d, pl->rho_d, nz, (double*)tb.a_d, (double*)tb.c_d, (double*)tb.W_d,
                              (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff, pl->top_dirichlet(), 0);
+  if (ce == cudaSuccess)
+    ce = launch_accuracy_floor(tb.a_d, tb.c_d, tb.W_d, nz, nx, ny, dx, dy, pl->top_dirichlet(), (double*)tb.floor_d, 0);
   if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
   if (ce != cudaSuccess) {
     int rc = cuda_fail(ce, "plan tables");
@@ -501,6 +507,10 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->fused = (int)value;
       return POISSON_OK;
+    case POISSON_OPT_VERIFY:
+      if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
+      pl->verify = (int)value;
+      return POISSON_OK;
     case POISSON_OPT_RESIDUAL_PASS:
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->respass = (int)value;
@@ -545,6 +555,8 @@ int poisson_plan_set_rho0(poisson_plan* pl, const double* rho0_dev, void* stream
   PGB_CUDA(launch_coefficients(pl->dz_d, pl->rho_d, pl->nz, (double*)tb.a_d, (double*)tb.c_d, (double*)tb.W_d,
                                (float*)tb.a_f, (float*)tb.c_f, (float2*)tb.a_ff, (float2*)tb.c_ff,
                                pl->top_dirichlet(), st));
+  PGB_CUDA(launch_accuracy_floor(tb.a_d, tb.c_d, tb.W_d, pl->nz, pl->nx, pl->ny, pl->g.dx, pl->g.dy,
+                                 pl->top_dirichlet(), (double*)tb.floor_d, st));
   return POISSON_OK;
 }
 
@@ -590,12 +602,14 @@ static int level_chunk(const poisson_plan* pl) {
 static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_double, char* ws, cudaStream_t st,
                                    int adjoint, const int* done, const double* target_mean = nullptr,
                                    const ResidualArgs* R = nullptr, int* res_nblocks = nullptr, int pass = 0,
-                                   bool* middle_fused = nullptr) {
+                                   bool* middle_fused = nullptr, double* sqnorm = nullptr,
+                                   int* sqnorm_blocks = nullptr, bool* res_stored_p = nullptr) {
   const bool t_double = pl->fp64();
   void* spec = ws + pl->off_spec;
   Stats* stats = (Stats*)(ws + pl->off_stats);
   const int lc = level_chunk(pl);
   if (middle_fused) *middle_fused = false;
+  if (res_stored_p) *res_stored_p = false;
   const bool try_fused = middle_fused && pl->fused && pl->mid_nitems > 0 && !adjoint && !t_double &&
                          lc >= pl->nz && pass >= 0 && pass < 4;
   cudaError_t e = cudaSuccess;
@@ -620,8 +634,13 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
           if (e == cudaSuccess && !xused) e = launch_xfwd(0, 0, r, spec, gc, pl->fx, pl->tb, done, st);
         }
       }
-      if (e == cudaSuccess && !used && pl->xkernel == 0)
+      bool stat = false;
+      if (e == cudaSuccess && !used && pl->xkernel == 0) {
         e = launch_xres_static(Rc, spec, gc, pl->fx, pl->tb, done, &stats->err, &nb, st, &used);
+        stat = used;
+      }
+      if (res_stored_p && stat && Rc.q && Rc.p_out && lc >= pl->nz) *res_stored_p = true;
+      Rc.p_out = nullptr;   // the other residual forms do not store the iterate
       if (e == cudaSuccess && !used) e = launch_xfwd_residual(Rc, spec, gc, pl->fx, pl->tb, done, &nb, st);
       rparts += nb;
     } else {
@@ -655,6 +674,7 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
   A.target_mean = target_mean;
   A.col_tile = pl->coltile;
   if (res_nblocks) *res_nblocks = rparts;
+  if (sqnorm_blocks) *sqnorm_blocks = 0;
   if (try_fused) {
     bool used = false;
     unsigned* sched = (unsigned*)(ws + pl->off_sched) + (size_t)pass * pl->sched_words;
@@ -671,6 +691,8 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
     prof_end(pl, ps, st);
     if (e != cudaSuccess) return e;
   }
+  A.sqnorm = sqnorm;
+  A.sqnorm_blocks = sqnorm_blocks;
   const int ps = prof_begin(pl, POISSON_PHASE_COLUMNS, st);
   e = launch_thomas(A, pl->g, pl->tb, st);
   prof_end(pl, ps, st);
@@ -723,9 +745,12 @@ static cudaError_t inverse(poisson_plan* pl, char* ws, cudaStream_t st, const in
 
 static int fill_info(poisson_plan* pl, char* ws, cudaStream_t st, poisson_info* info) {
   Stats s{};
+  double floor = -1.0;
   PGB_CUDA(cudaMemcpyAsync(&s, ws + pl->off_stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+  if (pl->mixed()) PGB_CUDA(cudaMemcpyAsync(&floor, pl->tb.floor_d, sizeof(double), cudaMemcpyDeviceToHost, st));
   PGB_CUDA(cudaStreamSynchronize(st));
   std::memset(info, 0, sizeof(*info));
+  info->accuracy_floor = floor;
   info->removed_weighted_mean = s.mu_w;
   if (s.err & ERR_WAIT_TIMEOUT) return POISSON_ERR_TIMEOUT;
   if (!pl->mixed()) {
@@ -739,7 +764,7 @@ static int fill_info(poisson_plan* pl, char* ws, cudaStream_t st, poisson_info* 
   info->sweeps = s.sweeps;
   info->converged = s.converged;
   for (int i = 0; i < 4; ++i) info->rel_update[i] = s.rel_update[i];
-  for (int i = 0; i < 4; ++i) info->rel_residual[i] = i < s.sweeps ? s.rel_residual[i] : -1.0;
+  for (int i = 0; i < 4; ++i) info->rel_residual[i] = s.sq_src[i] > 0 ? s.rel_residual[i] : -1.0;
   info->error_estimate = s.err_est;
   return s.converged ? POISSON_OK : POISSON_ERR_NOT_CONVERGED;
 }
@@ -776,6 +801,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
     ex.ctl_stats = stats;
     ex.ctl_max_sweeps = pl->max_sweeps;
     ex.ctl_tol = pl->tol;
+    ex.ctl_floor = pl->tb.floor_d;
     ex.ctl_npoints = pl->g.N;
     ex.ctl_pass = 0;
     bool fused = false;
@@ -783,14 +809,15 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
     cudaError_t e = cudaSuccess;
     if (!fused) {
       int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-      e = launch_control(stats, ex.partials, nb, nullptr, 0, 0, pl->max_sweeps, pl->tol, pl->g.N,
+      e = launch_control(stats, ex.partials, nb, nullptr, 0, 0, pl->max_sweeps, pl->tol, pl->tb.floor_d, pl->g.N,
                          ex.p_out != nullptr, st);
       prof_end(pl, ps, st);
       PGB_CUDA(e);
     }
     // Sweep 1 stores the correction q (and p only when it is the last sweep allowed); a later sweep
-    // reads q and stores p.  If the stopping rule ends the refinement after sweep 1, k_finalize forms
-    // p = p0 + q.  A third sweep first rebuilds q from the double iterate of the second.
+    // reads q and stores p.  If the refinement ends on sweep 1's iterate (the stopping rule after
+    // sweep 1, or sweep 2's correction certifying it), k_finalize forms p = p0 + q.  A third sweep
+    // first rebuilds q from the double iterate of the second.
     double* rpart = (double*)(ws + pl->off_rpart);
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
       if (sweep > 2) {
@@ -811,8 +838,22 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
       R.cx = pl->cx;
       R.cy = pl->cy;
       R.mu_ff = &stats->mu_ff;
-      int nres = 0;
-      PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R, &nres, sweep, &mid));
+      int nres = 0, nsq = 0;
+      // from the second sweep on, the correction's norm (Parseval on the solved spectrum) can already
+      // certify the current iterate: then the sweep stops before its inverse transforms.  Sweep 2's
+      // residual x-pass stores sweep 1's iterate p0 + q as p on the way, in case it does.
+      double* sqn = (pl->verify && sweep >= 2) ? (double*)(ws + pl->off_sqn) : nullptr;
+      R.p_out = (sqn && sweep == 2) ? (double*)p : nullptr;
+      bool stored = false;
+      PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R, &nres, sweep, &mid, sqn, &nsq,
+                               &stored));
+      if (sqn && nsq > 0) {
+        const int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
+        e = launch_verify(stats, sqn, nsq, rpart, nres, sweep, pl->tol, pl->tb.floor_d, (double)pl->nx * pl->ny,
+                          stored ? 1 : 0, st);
+        prof_end(pl, ps, st);
+        PGB_CUDA(e);
+      }
       const bool last_allowed = sweep == pl->max_sweeps;
       XinvExtra eu = ex;
       eu.p0 = p0;
@@ -827,17 +868,20 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
       PGB_CUDA(inverse(pl, ws, st, done, 0, XINV_UPDATE, nullptr, eu, &nb, &fused, mid));
       if (!fused) {
         int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-        e = launch_control(stats, ex.partials, nb, rpart, nres, sweep, pl->max_sweeps, pl->tol, pl->g.N,
+        e = launch_control(stats, ex.partials, nb, rpart, nres, sweep, pl->max_sweeps, pl->tol, pl->tb.floor_d,
+                           pl->g.N,
                            eu.p_out != nullptr, st);
         prof_end(pl, ps, st);
         PGB_CUDA(e);
       }
-      if (eu.p_out == nullptr) {
-        int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-        e = launch_finalize(p0, q, (double*)p, pl->g.N, stats, st);
-        prof_end(pl, ps, st);
-        PGB_CUDA(e);
-      }
+    }
+    if (pl->max_sweeps >= 2) {
+      // p = p0 + q when the refinement ended on sweep 1's iterate (stopped after sweep 1, or verified by
+      // sweep 2's correction); a no-op otherwise
+      int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
+      e = launch_finalize(p0, q, (double*)p, pl->g.N, stats, st);
+      prof_end(pl, ps, st);
+      PGB_CUDA(e);
     }
   }
   return POISSON_OK;

@@ -43,13 +43,15 @@ struct LowkArgs {
 // One low-|k| or singular column, solved by the whole block: the strided loads
 // and stores of the column and the coefficient tables go through shared memory
 // in parallel; thread 0 runs the sequential recurrence out of shared memory.
+// sq_out (nullable): thread 0 stores the solution's sum of |x_k|^2 over the levels (forward solve).
 template <typename TS, typename TCm, bool ADJ>
 __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS>::t* __restrict__ spec,
                                             const Geom& g, const double* __restrict__ ag,
                                             const double* __restrict__ cg, const double* __restrict__ Wg,
                                             const double* __restrict__ lamx, const double* __restrict__ lamy,
                                             double scale, int2 colk, Stats* stats,
-                                            const double* __restrict__ target_mean, bool singular00) {
+                                            const double* __restrict__ target_mean, bool singular00,
+                                            double* sq_out = nullptr) {
   using CS = typename CT<TS>::t;
   const int nz = g.nz;
   TCm* zx = reinterpret_cast<TCm*>(smraw);   // right-hand side, then z, then x (real parts)
@@ -152,6 +154,14 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
   }
   __syncthreads();
   const TCm shift_x = red[0], shift_y = red[1], sumw = red[2], sum_x = red[3], sum_y = red[4];
+  if (!ADJ && sq_out && threadIdx.x == 0) {
+    TCm sq = 0;
+    for (int k = 0; k < nz; ++k) {
+      const TCm ox = singular ? zx[k] - shift_x : zx[k], oy = singular ? zy[k] - shift_y : zy[k];
+      sq += ox * ox + oy * oy;
+    }
+    *sq_out = (double)sq;
+  }
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
     TCm ox = zx[k], oy = zy[k];
     if (singular) {
@@ -186,10 +196,11 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
 // this solve handles; s its row sum -(lambda_x + lambda_y); out: its level-0
 // entry in the spectrum (levels plane entries apart).  wp/colp: the column's
 // factor and tile slots.  Shared: ac [nz] (a_k, c_k), meet [TC], xm_s [TC].
+// Returns the sum of |x_k|^2 over the levels the thread wrote (0 when it wrote none).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tw_solve_tile(float2* colp, float* wp, const float2* __restrict__ ac, float4* meet,
-                                              float2* xm_s, int TC, int nz, int col_t, int upper, bool part,
-                                              bool valid, float s, float ms, float2* out, long long plane) {
+__device__ __forceinline__ float tw_solve_tile(float2* colp, float* wp, const float2* __restrict__ ac, float4* meet,
+                                               float2* xm_s, int TC, int nz, int col_t, int upper, bool part,
+                                               bool valid, float s, float ms, float2* out, long long plane) {
   const int m = nz / 2;
   if (part && upper == 0) {
     // levels 0..m-1, upward elimination
@@ -243,16 +254,19 @@ __device__ __forceinline__ void tw_solve_tile(float2* colp, float* wp, const flo
     xm_s[col_t] = xm;   // this thread has read the h-term; no other thread touches the slot before the barrier
   }
   __syncthreads();
-  if (!part || !valid) return;
+  float sq = 0.f;   // sum of |x_k|^2 over the levels this thread writes (x_m by the lower thread)
+  if (!part || !valid) return sq;
   const float2 xm = xm_s[col_t];
   if (upper == 0) {
     out[(long long)m * plane] = xm;
+    sq = xm.x * xm.x + xm.y * xm.y;
     float2 x = xm;
     for (int k = m - 1; k >= 0; --k) {
       const float2 z = colp[(size_t)k * TC];
       const float w = wp[(size_t)k * TC];
       x = make_float2(z.x + w * x.x, z.y + w * x.y);
       out[(long long)k * plane] = x;
+      sq = fmaf(x.x, x.x, fmaf(x.y, x.y, sq));
     }
   } else {
     float2 x = xm;
@@ -261,8 +275,10 @@ __device__ __forceinline__ void tw_solve_tile(float2* colp, float* wp, const flo
       const float w = wp[(size_t)k * TC];
       x = make_float2(z.x + w * x.x, z.y + w * x.y);
       out[(long long)k * plane] = x;
+      sq = fmaf(x.x, x.x, fmaf(x.y, x.y, sq));
     }
   }
+  return sq;
 }
 
 }  // namespace pgb

@@ -18,12 +18,14 @@ struct Stats {
   double sq_src[4];       // ||S||^2, summed in the same pass
   double rel_residual[4]; // sqrt(sq_res / sq_src)
   double err_est;         // bound on the relative error after the last executed pass
+  double err_floor;       // limiting-accuracy term included in err_est (plan constant, see launch_accuracy_floor)
   double mu_w;            // weighted mean removed from the source (first solve)
   double pmean;           // mean of the current mixed iterate p0 + q (double-float accurate)
   float2 mu_ff;           // mu_w as a double-float pair (set after the first solve)
   double control_stage[5 * 64];   // per-block sums of the control reduction
   unsigned control_ticket;        // blocks of the control reduction that have finished
   int need_final;         // the refinement stopped after a sweep that stored q but not p: p = p0 + q still to write
+  int p_written;          // the last executed pass stored the double iterate p
   int done;               // later passes become no-ops once set
   int sweeps;
   int converged;
@@ -43,11 +45,14 @@ struct Stats {
 // The estimate after sweep n is therefore rel_n = ||delta_n||/||p||, enlarged to
 // rel_n phi/(1 - phi) when the contraction measured between the last two sweeps,
 // phi = rel_n/rel_{n-1}, exceeds 1/2, and infinite when phi >= 1 (stagnation).
+// The bound adds the limiting accuracy F of the double-float residual (floor,
+// launch_accuracy_floor): the successive corrections measure the error that the
+// sweeps can still remove, not the part that the residual's rounding leaves.
 // Converged when the estimate is at most tol; otherwise the next sweep runs, up to
 // max_sweeps.
 __device__ __forceinline__ void control_decide(Stats* st, double sd0, double sp, double sm, double sr, double ss,
                                                int pass, int max_sweeps, double tol, long long npoints,
-                                               int wrote_p) {
+                                               int wrote_p, double floor) {
   st->pmean = sm / (double)npoints;
   if (pass == 0) {   // mu_W as a double-float pair, for the residual of the sweeps
     const float h = __double2float_rn(st->mu_w);
@@ -77,14 +82,17 @@ __device__ __forceinline__ void control_decide(Stats* st, double sd0, double sp,
     if (phi >= 1.0) est = __longlong_as_double(0x7ff0000000000000LL);   // +inf: no contraction
     else if (phi > 0.5) est = rel * (phi / (1.0 - phi));
   }
+  est += floor;
+  st->err_floor = floor;
   st->err_est = est;
-  if (est <= tol || rel == 0.0) {
+  if (est <= tol || sp == 0.0) {   // sp == 0: the solution is exactly zero
     st->done = 1;
     st->converged = 1;
-  } else if (pass >= max_sweeps) {
+  } else if (rel == 0.0 || pass >= max_sweeps) {   // an exactly zero correction changes nothing more
     st->done = 1;
     st->converged = 0;
   }
+  st->p_written = wrote_p;
   if (st->done && !wrote_p) st->need_final = 1;
 }
 
@@ -101,6 +109,8 @@ struct Tables {
   // twiddles exp(-2 pi i m / n): x line (n = nx/2), R2C post (m = 0..nx/2 over nx), y line
   const double2* twx_d; const double2* twr_d; const double2* twy_d;
   const float2* twx_f; const float2* twr_f; const float2* twy_f;
+  // limiting accuracy of the mixed refinement's error bound (one double, launch_accuracy_floor)
+  const double* floor_d;
 };
 
 struct Geom {
@@ -135,6 +145,7 @@ struct XinvExtra {
   Stats* ctl_stats;
   int ctl_pass, ctl_max_sweeps;
   double ctl_tol;
+  const double* ctl_floor;   // limiting accuracy added to the bound (one double)
   long long ctl_npoints;
 };
 
@@ -142,6 +153,9 @@ struct XinvExtra {
 struct ResidualArgs {
   double* partials;      // per-block sums of r^2 and S^2 (2 per block), from slot part0 on
   int part0;
+  double* p_out;         // nullable: the residual x-pass with q also stores the iterate p0 + q here (as
+                         // the double the inverse x-pass would write), so that a verification stop
+                         // needs no separate pass to form it
   const double* S;
   const float* p0;
   const float* q;        // nullable (first sweep)
@@ -191,6 +205,9 @@ struct ThomasArgs {
   const double* target_mean;  // nullable: the (0,0) column then gives the solution mean -(*target_mean)
   int col_tile;               // requested columns per CTA (0 = default)
   int singular00;             // 1: zero flux at the top, so the (0,0) column is singular (projected, pinned)
+  double* sqnorm;             // nullable: per-CTA w-weighted sums of |x|^2 of the solved spectrum (the
+                              // two-threads-per-column kernel only); *sqnorm_blocks receives their count
+  int* sqnorm_blocks;
 };
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
 
@@ -217,8 +234,18 @@ cudaError_t launch_spectral_fused(const ThomasArgs& T, const Geom& g, const FftP
 cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long long n, const int* done,
                              cudaStream_t st);
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, const double* res_partials,
-                           int res_nblocks, int pass, int max_sweeps, double tol, long long npoints, int wrote_p,
-                           cudaStream_t st);
+                           int res_nblocks, int pass, int max_sweeps, double tol, const double* floor,
+                           long long npoints, int wrote_p, cudaStream_t st);
+// Verification after the column solves of sweep n >= 2 (before its inverse transforms): the norm of
+// the correction delta_n, from the solved half spectrum by Parseval (sq = per-CTA sums of
+// w |x|^2, w = 1 for kx = 0 and nx/2, 2 otherwise; ||delta_n||^2 = nx ny sum w |x|^2), bounds the
+// error of the current iterate p_{n-1}: ||e_{n-1}|| <= ||delta_n||/(1 - phi), taken as
+// 2 ||delta_n|| (phi <= 1/2), or ||delta_n||/(1 - phi) with the measured contraction
+// phi = ||delta_n||/||delta_{n-1}|| when that exceeds 1/2.  When the bound is at most tol the
+// refinement stops on p_{n-1} (done; p still to be written when pass n-1 stored only q).  res_partials:
+// the sweep's residual norms (its forward x-pass).  p_stored: that x-pass also stored p_{n-1} as p.
+cudaError_t launch_verify(Stats* st_dev, const double* sq, int nsq, const double* res_partials, int res_nblocks,
+                          int pass, double tol, const double* floor, double nxny, int p_stored, cudaStream_t st);
 // p = p0 + q (double) when the refinement stopped after a sweep that stored only q (Stats::need_final).
 cudaError_t launch_finalize(const float* p0, const float* q, double* p, long long n, const Stats* stats,
                             cudaStream_t st);
@@ -266,6 +293,11 @@ cudaError_t launch_swap_outer_inner(const void* src, void* dst, int A, int M, in
 cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
                                 double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff, int top_dirichlet,
                                 cudaStream_t st);
+// Limiting accuracy F of the mixed refinement from the plan's coefficients (one block; nz <= 512):
+// the relative error that the double-float residual's rounding leaves after any number of sweeps,
+// added to every error bound.  Written to *out.
+cudaError_t launch_accuracy_floor(const double* a_d, const double* c_d, const double* W_d, int nz, int nx, int ny,
+                                  double dx, double dy, int top_dirichlet, double* out, cudaStream_t st);
 cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math*/, const void* g, const void* p, const Geom& g_, const Tables& tb,
                         const double* dz, const double* rho0, double* partials, int nparts_max,
                         double* grho, cudaStream_t st);

@@ -47,6 +47,156 @@ cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, do
 }
 
 // ---------------------------------------------------------------------------
+// Limiting accuracy of the mixed refinement: the part of the error that no sweep
+// removes, because the residual r = S - mu_W - L p is formed in double-float
+// arithmetic (unit roundoff u = 2^-48).  Each of the operator's products rounds
+// at about u K |p| (K = max_k (a_k + c_k) + 2/dx^2 + 2/dy^2, the largest
+// coefficient sum), so r carries noise of size about u K ||p|| that is
+// uncorrelated from point to point, and the correction solved from it carries
+// L^{-1} of that noise.  For noise of equal variance in every mode the expected
+// norm is u K ||p|| sqrt(mean over the modes of 1/lambda^2), lambda running over
+// the eigenvalues lambda_h(kx, ky) + mu_m of the discrete operator (the singular
+// mode of the Neumann problem excluded: the solve projects it out).  The
+// vertical operator W^{-1} M (M symmetric) is similar to the symmetric
+// tridiagonal B = W^{-1/2} M W^{-1/2}; its mu_m come from Sturm-count bisection.
+// The similarity is not orthogonal, so a noise vector's plain norm can grow by up
+// to the factor eta = nz sum W^2/(sum W)^2 >= 1 in the dominant (vertically
+// constant) modes; the term is multiplied by sqrt(eta).  Result:
+//     F = u K sqrt(eta) sqrt(sum_{modes} 1/lambda^2 / N),   N = nx ny nz,
+// the relative error below which the refinement's error bound cannot certify a
+// result; it is added to every bound.  The sum over (kx, ky) uses the
+// geometric-grid value g(t_j) >= g(lambda_h), t_j <= lambda_h, of the decreasing
+// g(lambda) = sum_m 1/(lambda + mu_m)^2 (at most (t_{j+1}/t_j)^2 = 1.06 too large).
+// One block; fixed-order sums (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int kFloorThreads = 512;   // >= the largest nz a plan accepts
+constexpr int kFloorGrid = 512;
+
+__device__ int sturm_count(const double* d, const double* e2, int nz, double x) {
+  // eigenvalues of B below x = negative pivots of the LDL^T factorisation of B - x I
+  int cnt = 0;
+  double q = d[0] - x;
+  for (int k = 0;;) {
+    if (q < 0) ++cnt;
+    if (++k == nz) break;
+    const double qq = (q != 0.0) ? q : -1e-300;
+    q = d[k] - x - e2[k - 1] / qq;
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(kFloorThreads) k_accuracy_floor(const double* __restrict__ a,
+                                                                   const double* __restrict__ c,
+                                                                   const double* __restrict__ W, int nz, int nx,
+                                                                   int ny, double dx, double dy, int top_dirichlet,
+                                                                   double* __restrict__ out) {
+  __shared__ double d[kFloorThreads], e2[kFloorThreads], mu[kFloorThreads];
+  __shared__ double g[kFloorGrid];
+  __shared__ double red[4][kFloorThreads];
+  const int t = threadIdx.x;
+  double kmax = 0, sw = 0, sw2 = 0, gmax = 0;
+  for (int k = t; k < nz; k += blockDim.x) {
+    d[k] = a[k] + c[k];
+    e2[k] = (k + 1 < nz) ? c[k] * a[k + 1] : 0.0;   // squared off-diagonal of B between k and k+1
+  }
+  __syncthreads();
+  for (int k = t; k < nz; k += blockDim.x) {
+    kmax = fmax(kmax, d[k]);
+    sw += W[k];
+    sw2 += W[k] * W[k];
+    const double off = ((k > 0) ? sqrt(e2[k - 1]) : 0.0) + ((k + 1 < nz) ? sqrt(e2[k]) : 0.0);
+    gmax = fmax(gmax, d[k] + off);   // Gershgorin bound on the spectrum of B
+  }
+  red[0][t] = kmax;
+  red[1][t] = sw;
+  red[2][t] = sw2;
+  red[3][t] = gmax;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (t < h) {
+      red[0][t] = fmax(red[0][t], red[0][t + h]);
+      red[1][t] += red[1][t + h];
+      red[2][t] += red[2][t + h];
+      red[3][t] = fmax(red[3][t], red[3][t + h]);
+    }
+    __syncthreads();
+  }
+  const double K = red[0][0] + 2.0 / (dx * dx) + 2.0 / (dy * dy);
+  const double eta = (red[1][0] > 0) ? nz * red[2][0] / (red[1][0] * red[1][0]) : 1.0;
+  const double top = red[3][0] * (1.0 + 1e-12) + 1e-300;
+  // mu_m, m-th smallest eigenvalue of B (count(x) <= m exactly for x <= mu_m), to a relative
+  // 1e-7; with zero flux through top and bottom mu_0 = 0 (the constants are the null space)
+  for (int m = t; m < nz; m += blockDim.x) {
+    double lo = 0.0, hi = top;
+    if (m > 0 || top_dirichlet) {
+      for (int it = 0; it < 200 && hi - lo > 1e-7 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(d, e2, nz, mid) <= m) lo = mid;
+        else hi = mid;
+      }
+      mu[m] = 0.5 * (lo + hi);
+    } else {
+      mu[m] = 0.0;
+    }
+  }
+  __syncthreads();
+  // g on the grid t_j = lam_lo exp(j h) spanning the nonzero horizontal eigenvalues
+  const double sx = sinpi(1.0 / nx), sy = sinpi(1.0 / ny);
+  const double lam_lo = fmin(4.0 / (dx * dx) * sx * sx, 4.0 / (dy * dy) * sy * sy);
+  const double lam_hi = 4.0 / (dx * dx) + 4.0 / (dy * dy);
+  const double hstep = log(lam_hi / lam_lo) / (kFloorGrid - 1);
+  for (int j = t; j < kFloorGrid; j += blockDim.x) {
+    const double tj = lam_lo * exp(j * hstep);
+    double s = 0;
+    for (int m = 0; m < nz; ++m) {
+      const double v = 1.0 / (tj + mu[m]);
+      s += v * v;
+    }
+    g[j] = s;
+  }
+  __syncthreads();
+  // sum over the wavenumber pairs, each unique |kx|, |ky| with its multiplicity
+  const int ux = nx / 2 + 1, uy = ny / 2 + 1;
+  double acc = 0;
+  for (long long pidx = t; pidx < (long long)ux * uy; pidx += blockDim.x) {
+    const int kx = (int)(pidx % ux), ky = (int)(pidx / ux);
+    const double mx = (kx == 0 || 2 * kx == nx) ? 1.0 : 2.0;
+    const double my = (ky == 0 || 2 * ky == ny) ? 1.0 : 2.0;
+    const double s1 = sinpi((double)kx / nx), s2 = sinpi((double)ky / ny);
+    const double lam = 4.0 / (dx * dx) * s1 * s1 + 4.0 / (dy * dy) * s2 * s2;
+    double gv;
+    if (kx == 0 && ky == 0) {   // the mean column: its own eigenvalues, the singular one excluded
+      gv = 0;
+      for (int m = top_dirichlet ? 0 : 1; m < nz; ++m) gv += 1.0 / (mu[m] * mu[m]);
+    } else {
+      int j = (int)floor(log(lam / lam_lo) / hstep);
+      j = max(0, min(kFloorGrid - 1, j));
+      while (j > 0 && lam_lo * exp(j * hstep) > lam) --j;
+      gv = g[j];
+    }
+    acc += mx * my * gv;
+  }
+  red[0][t] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (t < h) red[0][t] += red[0][t + h];
+    __syncthreads();
+  }
+  if (t == 0) {
+    const double u = 0x1p-48;
+    const double npts = (double)nx * ny * nz;
+    *out = u * K * sqrt(eta) * sqrt(red[0][0] / npts);
+  }
+}
+
+cudaError_t launch_accuracy_floor(const double* a_d, const double* c_d, const double* W_d, int nz, int nx, int ny,
+                                  double dx, double dy, int top_dirichlet, double* out, cudaStream_t st) {
+  if (nz > kFloorThreads) return cudaErrorInvalidValue;
+  k_accuracy_floor<<<1, kFloorThreads, 0, st>>>(a_d, c_d, W_d, nz, nx, ny, dx, dy, top_dirichlet, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Refinement control: sums the x-pass partials in a fixed order (the inverse
 // x-pass's delta^2, p^2, sum p and the forward x-pass's r^2, S^2), records the
 // relative update, relative residual and error bound, and sets the done flag
@@ -59,7 +209,8 @@ constexpr int kControlBlocks = 64;
 
 __global__ void __launch_bounds__(256) k_control(Stats* st, const double* __restrict__ partials, int nblocks,
                                                   const double* __restrict__ res_partials, int res_nblocks,
-                                                  int pass, int max_sweeps, double tol, long long npoints,
+                                                  int pass, int max_sweeps, double tol,
+                                                  const double* __restrict__ floor, long long npoints,
                                                   int wrote_p, double* __restrict__ stage,
                                                   unsigned* __restrict__ ticket) {
   __shared__ double sh[5][256];
@@ -104,7 +255,68 @@ __global__ void __launch_bounds__(256) k_control(Stats* st, const double* __rest
 #pragma unroll
     for (int k = 0; k < 5; ++k) tot[k] += stage[5 * i + k];
   *ticket = 0;   // ready for the next pass
-  control_decide(st, tot[0], tot[1], tot[2], tot[3], tot[4], pass, max_sweeps, tol, npoints, wrote_p);
+  control_decide(st, tot[0], tot[1], tot[2], tot[3], tot[4], pass, max_sweeps, tol, npoints, wrote_p, *floor);
+}
+
+// ---------------------------------------------------------------------------
+// Verification of the current iterate by the next correction's norm (see launch_verify in
+// kernels.cuh).  One block; fixed-order sums.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_verify(Stats* st, const double* __restrict__ sq, int nsq,
+                                                 const double* __restrict__ res_partials, int res_nblocks, int pass,
+                                                 double tol, const double* __restrict__ floor, double nxny,
+                                                 int p_stored) {
+  __shared__ double sh[3][1024];
+  if (st->done) return;   // an earlier pass already ended the refinement
+  const int t = threadIdx.x;
+  double a = 0, b = 0, c = 0;
+  for (int i = t; i < nsq; i += blockDim.x) a += sq[i];
+  for (int i = t; i < res_nblocks; i += blockDim.x) {
+    b += res_partials[2 * i];
+    c += res_partials[2 * i + 1];
+  }
+  sh[0][t] = a;
+  sh[1][t] = b;
+  sh[2][t] = c;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (t < h) {
+      sh[0][t] += sh[0][t + h];
+      sh[1][t] += sh[1][t + h];
+      sh[2][t] += sh[2][t + h];
+    }
+    __syncthreads();
+  }
+  if (t != 0) return;
+  const double sd = nxny * sh[0][0];          // ||delta_pass||^2 (Parseval)
+  const double sp = st->sq_p[pass - 1];       // ||p_{pass-1}||^2
+  const double rel = (sp > 0) ? sqrt(sd / sp) : 0.0;
+  const double prev = st->rel_update[pass - 1];
+  const double phi = (pass >= 2 && prev > 0) ? rel / prev : 0.0;
+  double est;
+  if (phi >= 1.0) est = __longlong_as_double(0x7ff0000000000000LL);
+  else est = rel * (phi > 0.5 ? 1.0 / (1.0 - phi) : 2.0);
+  est += *floor;   // the limiting accuracy of the residual (control_decide)
+  st->sq_res[pass - 1] = sh[1][0];
+  st->sq_src[pass - 1] = sh[2][0];
+  st->rel_residual[pass - 1] = (sh[2][0] > 0) ? sqrt(sh[1][0] / sh[2][0]) : 0.0;
+  if (est <= tol || sp == 0.0) {
+    // the refinement ends on p_{pass-1}: the correction just solved for is not applied
+    st->rel_update[pass] = rel;
+    st->sq_delta[pass] = sd;
+    st->err_est = est;
+    st->err_floor = *floor;
+    st->done = 1;
+    st->converged = 1;
+    st->sweeps = pass - 1;
+    if (!st->p_written && !p_stored) st->need_final = 1;
+  }
+}
+
+cudaError_t launch_verify(Stats* st_dev, const double* sq, int nsq, const double* res_partials, int res_nblocks,
+                          int pass, double tol, const double* floor, double nxny, int p_stored, cudaStream_t st) {
+  k_verify<<<1, 1024, 0, st>>>(st_dev, sq, nsq, res_partials, res_nblocks, pass, tol, floor, nxny, p_stored);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -167,10 +379,11 @@ cudaError_t launch_q_rebuild(const double* p, const float* p0, float* q, long lo
 }
 
 cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, const double* res_partials,
-                           int res_nblocks, int pass, int max_sweeps, double tol, long long npoints, int wrote_p,
-                           cudaStream_t st) {
+                           int res_nblocks, int pass, int max_sweeps, double tol, const double* floor,
+                           long long npoints, int wrote_p, cudaStream_t st) {
   k_control<<<kControlBlocks, 256, 0, st>>>(st_dev, partials, nblocks, res_partials, res_nblocks, pass, max_sweeps,
-                                            tol, npoints, wrote_p, st_dev->control_stage, &st_dev->control_ticket);
+                                            tol, floor, npoints, wrote_p, st_dev->control_stage,
+                                            &st_dev->control_ticket);
   return cudaGetLastError();
 }
 

@@ -15,8 +15,9 @@
 // formed exactly too and folded into those of p0: a_k (q_{k-1} - q_k) is a few
 // 1e-5 of |S| while the converged residual is near 1e-12 of it, so an FP32
 // rounding there (6e-8 relative) would leave the same bias in every sweep and
-// stall the refinement near 1e-12 relative error.  The horizontal q terms carry
-// the 25-100x smaller coefficients 1/dx^2, 1/dy^2 and enter in plain FP32.
+// stall the refinement near 1e-12 relative error.  The horizontal q sums are
+// formed error-free for the same reason: on grids dominated by weak horizontal
+// modes |p| reaches 1e5 |S|, and their FP32 rounding became a 1e-12 bias too.
 // S (double) is split into hi + lo floats with integer operations.
 #pragma once
 #include "kernels.cuh"
@@ -44,14 +45,28 @@ __device__ __forceinline__ float residual_value(float pc, float pe, float pw, fl
   float s1, e1, s2, e2;
   two_sum(pe, pw, s1, e1);
   two_sum(s1, -2.f * pc, s2, e2);
-  float dl = e1 + e2 + (qe + qw - 2.f * qc);
+  float dl = e1 + e2;
+  {   // q's stencil sum error-free, folded into (s2, dl) (see add_q_sum in residual2.cuh)
+    float a1, f1, t, et;
+    two_sum(qe, qw, a1, f1);
+    two_sum(s2, __fmaf_rn(qc, -2.f, a1), t, et);
+    s2 = t;
+    dl += et + f1;
+  }
   FF tx;
   two_prod(cx.x, s2, tx.h, tx.l);
   tx.l = __fmaf_rn(cx.x, dl, __fmaf_rn(cx.y, s2, tx.l));
   // y: cy (pn + ps - 2 pc)
   two_sum(pn, ps, s1, e1);
   two_sum(s1, -2.f * pc, s2, e2);
-  dl = e1 + e2 + (qn + qs - 2.f * qc);
+  dl = e1 + e2;
+  {
+    float a1, f1, t, et;
+    two_sum(qn, qs, a1, f1);
+    two_sum(s2, __fmaf_rn(qc, -2.f, a1), t, et);
+    s2 = t;
+    dl += et + f1;
+  }
   FF ty;
   two_prod(cy.x, s2, ty.h, ty.l);
   ty.l = __fmaf_rn(cy.x, dl, __fmaf_rn(cy.y, s2, ty.l));

@@ -70,6 +70,19 @@ __device__ __forceinline__ ResCoef res_coef(float2 cx, float2 cy, float2 A, floa
 // r at the two points.  pc, pe, pw, pn, ps, pd, pu: p0 at the points and at their
 // east, west, north, south, lower and upper neighbours (pd = pc at the bottom,
 // pu = 0 above the top level); likewise for q when HAS_Q.  Sh, Sl: the split of S.
+// Adds the correction's stencil sum qa + qb (+ qc2 + qd2) - m qc to the double-float pair (s, dl) of
+// p0's, error-free up to the pair's own rounding: the neighbour sums by TwoSum, the (small) second
+// difference rounded once by FMA, then TwoSum into s.  In plain FP32 the sum of q's neighbours (a few
+// 1e-7 of |p|) rounds at 6e-8 of itself; on grids whose solution is dominated by weak horizontal
+// modes (|p| ~ 1e5 |S|) that left a fixed 1e-12 relative bias in every sweep.
+__device__ __forceinline__ void add_q_sum(float2& s, float2& dl, float2 x, float2 ex, float2 qc, float2 m) {
+  const float2 qh = fma2(qc, m, x);        // (neighbour sum) + m qc, rounded once: error eps |second difference|
+  float2 t, et;
+  two_sum2(s, qh, t, et);
+  s = t;
+  dl = add2(dl, add2(et, ex));
+}
+
 // ISO: dx == dy (cx == cy as double-float pairs).  The x and y second differences are then
 // summed first, pe + pw + pn + ps - 4 pc exactly as a double-float pair (four TwoSums; -4 pc is
 // exact), and multiplied by 1/dx^2 once: one product chain and one TwoSum fewer than the
@@ -85,7 +98,13 @@ __device__ __forceinline__ float2 residual_value2(float2 pc, float2 pe, float2 p
     two_sum2(s1, s2, s3, e3);
     two_sum2(s3, mul2(pc, make_float2(-4.f, -4.f)), s4, e4);
     float2 dl = add2(add2(e1, e2), add2(e3, e4));
-    if (HAS_Q) dl = add2(dl, fma2(qc, make_float2(-4.f, -4.f), add2(add2(qe, qw), add2(qn, qs))));
+    if (HAS_Q) {
+      float2 a1, f1, a2, f2, a3, f3;
+      two_sum2(qe, qw, a1, f1);
+      two_sum2(qn, qs, a2, f2);
+      two_sum2(a1, a2, a3, f3);
+      add_q_sum(s4, dl, a3, add2(add2(f1, f2), f3), qc, make_float2(-4.f, -4.f));
+    }
     const float2 nthh = mul2(k.ncxh, s4);                      // -(cx s4) rounded
     const float2 thl = fma2(k.cxh, dl, fma2(k.cxl, s4, fma2(k.cxh, s4, nthh)));
     // z: a (pd - pc) + c (pu - pc), differences first, q's exactly as well
@@ -123,14 +142,22 @@ __device__ __forceinline__ float2 residual_value2(float2 pc, float2 pe, float2 p
   two_sum2(pe, pw, s1, e1);
   two_sum2(s1, m2pc, s2, e2);
   float2 dl = add2(e1, e2);
-  if (HAS_Q) dl = add2(dl, fma2(qc, m2, add2(qe, qw)));
+  if (HAS_Q) {
+    float2 a1, f1;
+    two_sum2(qe, qw, a1, f1);
+    add_q_sum(s2, dl, a1, f1, qc, m2);
+  }
   const float2 ntxh = mul2(k.ncxh, s2);                       // -(cx s2) rounded
   const float2 txl = fma2(k.cxh, dl, fma2(k.cxl, s2, fma2(k.cxh, s2, ntxh)));
   // y: cy (pn + ps - 2 pc)
   two_sum2(pn, ps, s1, e1);
   two_sum2(s1, m2pc, s2, e2);
   dl = add2(e1, e2);
-  if (HAS_Q) dl = add2(dl, fma2(qc, m2, add2(qn, qs)));
+  if (HAS_Q) {
+    float2 a1, f1;
+    two_sum2(qn, qs, a1, f1);
+    add_q_sum(s2, dl, a1, f1, qc, m2);
+  }
   const float2 ntyh = mul2(k.ncyh, s2);
   const float2 tyl = fma2(k.cyh, dl, fma2(k.cyl, s2, fma2(k.cyh, s2, ntyh)));
   // z: a (pd - pc) + c (pu - pc), differences first (exact for a constant field)

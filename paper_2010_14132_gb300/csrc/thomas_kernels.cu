@@ -272,19 +272,26 @@ __global__ void __launch_bounds__(64) k_thomas_pair(float2* __restrict__ spec, G
 // Shared layout: tile [nz][TC] complex, factors [nz][TC], (a_k, c_k) [nz], the
 // meeting terms [TC] x 4, one mbarrier.
 // ---------------------------------------------------------------------------
+// sqn (nullable): CTA b stores sqn[b] = sum over its columns of w_kx sum_k |x_k|^2 (w = 1 for
+// kx = 0 and nx/2, 2 otherwise), so that Parseval gives the norm of the correction this solve
+// computed before the inverse transforms.
 template <typename TCm>
 __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Geom g, const float* __restrict__ a,
                                                   const float* __restrict__ c, const float* __restrict__ lamx,
                                                   const float* __restrict__ lamy, float scale, int lowk_r2,
                                                   const int* __restrict__ done, Stats* stats,
-                                                  const __grid_constant__ CUtensorMap tm, int box_rows, LowkArgs L) {
+                                                  const __grid_constant__ CUtensorMap tm, int box_rows, LowkArgs L,
+                                                  double* __restrict__ sqn) {
   pdl_trigger();
   pdl_wait();   // the previous kernels of the stream are complete
   if (done && *done) return;
   extern __shared__ __align__(128) unsigned char smraw[];
   if ((int)blockIdx.x < L.n) {
-    lowk_column<float, TCm, false>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale,
-                                   L.cols[blockIdx.x], stats, L.target_mean, L.singular00 != 0);
+    double sq = 0.0;
+    const int2 ck = L.cols[blockIdx.x];
+    lowk_column<float, TCm, false>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale, ck, stats,
+                                   L.target_mean, L.singular00 != 0, sqn ? &sq : nullptr);
+    if (sqn && threadIdx.x == 0) sqn[blockIdx.x] = (ck.x == 0 || ck.x == g.nxh - 1 ? 1.0 : 2.0) * sq;
     return;
   }
   const int TC = blockDim.x / 2, t = threadIdx.x, col_t = t % TC, upper = t / TC, nz = g.nz;
@@ -318,8 +325,21 @@ __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Ge
   const int kys = signed_ky(ky, g.ny);
   const bool valid = col < g.plane && kx < g.nxh && (kx * kx + kys * kys > lowk_r2);
   const float s = valid ? -(lamx[kx] + lamy[ky]) : 1.f;
-  tw_solve_tile(tile + col_t, wv + col_t, ac, meet, xm_s, TC, nz, col_t, upper, true, valid, s, -scale,
-                spec + (valid ? col : 0), g.plane);
+  const float sq = tw_solve_tile(tile + col_t, wv + col_t, ac, meet, xm_s, TC, nz, col_t, upper, true, valid, s,
+                                 -scale, spec + (valid ? col : 0), g.plane);
+  if (sqn) {   // fixed-order CTA sum of the weighted squares (in the drained tile's shared memory)
+    float v = (kx == 0 || kx == g.nxh - 1) ? sq : 2.f * sq;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    float* wsum = reinterpret_cast<float*>(meet);   // meet is free after the solve's last barrier
+    __syncthreads();
+    if ((t & 31) == 0) wsum[t >> 5] = v;
+    __syncthreads();
+    if (t == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += (double)wsum[w];
+      sqn[blockIdx.x] = tot;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -413,8 +433,9 @@ static cudaError_t thomas_tw_launch(const ThomasArgs& A, const Geom& g, const Ta
   const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale,
                    A.singular00};
   *used = true;
+  if (A.sqnorm && A.sqnorm_blocks) *A.sqnorm_blocks = (int)(nb + A.n_lowk);
   return pdl_launch(kern, dim3((unsigned)(nb + A.n_lowk)), dim3(2 * tc), smem, st, (float2*)A.spec, g, tb.a_f, tb.c_f,
-                    tb.lamx_f, tb.lamy_f, (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows, L);
+                    tb.lamx_f, tb.lamy_f, (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows, L, A.sqnorm);
 }
 
 template <typename T, typename TCm, bool ADJ>

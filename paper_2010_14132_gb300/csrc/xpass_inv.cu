@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(xs_threads(E), xinv_min_blocks(E)) k_xinv_s(co
       if (tid == 0) {
         ex.ctl_stats->control_ticket = 0u;   // ready for the next pass
         control_decide(ex.ctl_stats, sums[0], sums[TH], sums[2 * TH], sums[3 * TH], sums[4 * TH], ex.ctl_pass,
-                       ex.ctl_max_sweeps, ex.ctl_tol, ex.ctl_npoints, ex.p_out != nullptr);
+                       ex.ctl_max_sweeps, ex.ctl_tol, ex.ctl_npoints, ex.p_out != nullptr, *ex.ctl_floor);
       }
     }
   }

@@ -145,6 +145,14 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xr
       if (valid) {
         racc = fma2(v[i], v[i], racc);
         sacc = fma2(Sh, Sh, sacc);
+        if constexpr (HAS_Q) {
+          if (R.p_out) {   // the iterate p0 + q as the double the inverse x-pass would store
+            float2 sp, tp;
+            two_sum2(pc, qc, sp, tp);
+            __stcs(reinterpret_cast<double2*>(R.p_out + row * NX) + e,
+                   make_double2(ff2d_fast(sp.x, tp.x), ff2d_fast(sp.y, tp.y)));
+          }
+        }
       }
     }
     sync();   // the line's threads have read the S row before it is overwritten

@@ -60,3 +60,15 @@ def test_forward_x_phase_bytes_are_the_roofline_unit():
 
 def test_whole_job_rate_counts_all_ranks():
     assert B.whole_job_rate(1_000_000, 4, 2.0) == pytest.approx(4 * 1_000_000 / 2e-3 / 1e6)
+
+
+def test_verified_solve_counts_one_sweep_plus_the_verification():
+    nx, ny, nz = 1024, 1024, 128
+    N, Nc = nx * ny * nz, (nx // 2 + 1) * ny * nz
+    per_phase, total = B.algorithmic_bytes(nx, ny, nz, 1, max_sweeps=3, verified=True)
+    # first solve + one applied sweep + a verification sweep (S and p read, spectrum once)
+    assert total == 16 * N + 16 * Nc + (32 * N + 16 * Nc) + (16 * N + 16 * Nc)
+    for name in ("yfwd", "columns"):
+        assert per_phase[name] == 3 * 16 * Nc
+    assert per_phase["yinv"] == 2 * 16 * Nc
+    assert per_phase["control"] == 16 * N     # p = p0 + q written at the end
