@@ -34,6 +34,8 @@ POISSON_OPT_LAYOUT = 11
 POISSON_OPT_SPECTRAL_FUSED = 12
 POISSON_OPT_RESIDUAL_PASS = 13
 POISSON_OPT_VERIFY = 14
+POISSON_BATCH_OPT_PERSISTENT = 0
+POISSON_BATCH_OPT_STALL_TEST = 1
 POISSON_LAYOUT_Z_Y_X = 0
 POISSON_LAYOUT_X_Y_Z = 1
 PHASES = ("xfwd", "yfwd", "columns", "yinv", "xinv", "residual", "control", "spectral")
@@ -45,7 +47,7 @@ EXPORTED = (
     "poisson_last_error_detail", "poisson_batch_create", "poisson_batch_workspace_bytes", "poisson_batch_solve",
     "poisson_batch_destroy", "poisson_plan_profile_read", "poisson_solve_static_workspace",
     "poisson_pipe_create", "poisson_pipe_submit", "poisson_pipe_wait", "poisson_pipe_destroy",
-    "poisson_batch_plan", "poisson_cg_workspace_bytes", "poisson_cg_solve",
+    "poisson_batch_plan", "poisson_cg_workspace_bytes", "poisson_cg_solve", "poisson_batch_set_option",
 )
 
 # size of the fixed device array poisson_solve_static_workspace uses as scratch
@@ -132,6 +134,7 @@ def load():
     L.poisson_solve_static_workspace.argtypes = [vp, vp, vp, vp, C.POINTER(PoissonInfo)]
     L.poisson_pipe_create.argtypes = [vp, C.POINTER(vp)]
     L.poisson_batch_plan.argtypes = [vp, i, C.POINTER(vp)]
+    L.poisson_batch_set_option.argtypes = [vp, i, d]
     L.poisson_pipe_submit.argtypes = [vp, vp, vp]
     L.poisson_pipe_wait.argtypes = [vp]
     L.poisson_pipe_destroy.argtypes = [vp]
@@ -282,6 +285,10 @@ def poisson_batch_plan(batch, i):
     out = C.c_void_p()
     _check(load().poisson_batch_plan(batch, int(i), C.byref(out)), "poisson_batch_plan")
     return out.value
+
+
+def poisson_batch_set_option(batch, option, value):
+    _check(load().poisson_batch_set_option(batch, int(option), float(value)), "poisson_batch_set_option")
 
 
 def poisson_cg_workspace_bytes(plan):

@@ -25,7 +25,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 SOURCES = ["api.cu", "fft_kernels.cu", "thomas_kernels.cu", "misc_kernels.cu", "ypass_tma.cu", "cg_kernels.cu",
            "static_workspace.cu", "xpass_fwd.cu", "xpass_res.cu", "xpass_inv.cu", "ypass_static.cu",
-           "spectral_fused.cu", "residual_stencil.cu", "xpass_res_iso.cu"]
+           "spectral_fused.cu", "residual_stencil.cu", "xpass_res_iso.cu", "batch_persistent.cu"]
 
 
 def nvcc() -> str:

@@ -122,6 +122,9 @@ struct poisson_batch {
   std::vector<void*> capP;
   std::vector<unsigned> capV;   // plan versions at capture
   void* capW = nullptr;
+  int persistent = 1;           // POISSON_BATCH_OPT_PERSISTENT
+  int stall_test = -1;          // POISSON_BATCH_OPT_STALL_TEST
+  BatchPersistent bp;           // descriptors and item list of the persistent kernel (when it is used)
 };
 
 namespace {
@@ -1128,6 +1131,7 @@ int poisson_cg_solve(poisson_plan* pl, const double* rho3, const double* S, doub
 int poisson_batch_destroy(poisson_batch* b) {
   if (!b) return POISSON_OK;
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  batch_persistent_free(&b->bp);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (int k = 0; k < poisson_batch::kBranches; ++k) {
     if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
@@ -1187,6 +1191,63 @@ static void batch_layout(poisson_batch* b) {
   b->ws_bytes = off;
 }
 
+// The persistent kernel takes the batch: mixed precision, every domain of a supported shape in the
+// solver's own layout.
+static bool batch_uses_persistent(const poisson_batch* b) {
+  if (!b->persistent || b->dtype != POISSON_MIXED) return false;
+  for (const poisson_plan* pl : b->plans)
+    if (!batch_persistent_supported(pl->nx, pl->ny, pl->nz) || pl->layout != POISSON_LAYOUT_Z_Y_X) return false;
+  return true;
+}
+
+static std::vector<BatchDomIn> batch_dom_inputs(const poisson_batch* b, const void* const* S, void* const* p,
+                                                char* ws) {
+  std::vector<BatchDomIn> d(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    const poisson_plan* pl = b->plans[i];
+    char* w = ws ? ws + b->off[i] : nullptr;
+    BatchDomIn& in = d[i];
+    in.g = pl->g;
+    in.g.lev0 = 0;
+    in.g.lev1 = pl->nz;
+    in.tb = &pl->tb;
+    in.cx = pl->cx;
+    in.cy = pl->cy;
+    in.lowk_r2 = pl->lowk_r2;
+    in.n_lowk = pl->n_lowk;
+    in.singular00 = !pl->top_dirichlet();
+    in.lowk_cols = pl->lowk_d;
+    in.max_sweeps = pl->max_sweeps;
+    in.verify = pl->verify;
+    in.tol = pl->tol;
+    in.S = S ? (const double*)S[i] : nullptr;
+    in.p = p ? (double*)p[i] : nullptr;
+    in.spec = w ? (float2*)(w + pl->off_spec) : nullptr;
+    in.p0 = w ? (float*)(w + pl->off_p0) : nullptr;
+    in.q = w ? (float*)(w + pl->off_q) : nullptr;
+    in.stats = w ? (Stats*)(w + pl->off_stats) : nullptr;
+  }
+  return d;
+}
+
+int poisson_batch_set_option(poisson_batch* b, int option, double value) {
+  if (!b) return POISSON_ERR_INVALID_ARG;
+  if (option == POISSON_BATCH_OPT_PERSISTENT) {
+    if (value != 0.0 && value != 1.0) return POISSON_ERR_INVALID_ARG;
+    b->persistent = (int)value;
+  } else if (option == POISSON_BATCH_OPT_STALL_TEST) {
+    if (value != std::floor(value) || value < -1.0 || value >= (double)b->n) return POISSON_ERR_INVALID_ARG;
+    b->stall_test = (int)value;
+  } else {
+    return POISSON_ERR_INVALID_ARG;
+  }
+  if (b->exec) {   // the next solve re-captures
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return POISSON_OK;
+}
+
 int poisson_batch_plan(poisson_batch* b, int i, poisson_plan** out) {
   if (!b || !out || i < 0 || i >= b->n) return POISSON_ERR_INVALID_ARG;
   *out = b->plans[i];
@@ -1197,6 +1258,8 @@ int poisson_batch_workspace_bytes(const poisson_batch* b, size_t* bytes) {
   if (!b || !bytes) return POISSON_ERR_INVALID_ARG;
   size_t off = 0;   // the domains' current workspace sizes (options can change them)
   for (int i = 0; i < b->n; ++i) off = align256(off + b->plans[i]->ws_bytes);
+  if (batch_uses_persistent(b))   // the persistent kernel's counters and partial sums follow
+    off = align256(off + batch_persistent_scratch_bytes(batch_dom_inputs(b, nullptr, nullptr, nullptr)));
   *bytes = off;
   return POISSON_OK;
 }
@@ -1217,6 +1280,32 @@ int poisson_batch_solve(poisson_batch* b, const void* const* S, void* const* p, 
       b->exec = nullptr;
     }
     batch_layout(b);
+    if (batch_uses_persistent(b)) {
+      // one persistent kernel over every domain's work items, captured with its initialisation
+      const std::vector<BatchDomIn> in = batch_dom_inputs(b, S, p, (char*)workspace);
+      if (batch_persistent_build(&b->bp, in, (char*)workspace + b->ws_bytes, b->stall_test) != 0)
+        return cuda_fail(cudaErrorInvalidValue, "batch_persistent_build", __LINE__);
+      PGB_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+      const cudaError_t le = batch_persistent_launch(b->bp, b->cap);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+      if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(le, "batch_persistent_launch", __LINE__);
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&b->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      b->capS.assign(S, S + b->n);
+      b->capP.assign(p, p + b->n);
+      b->capV.resize(b->n);
+      for (int i = 0; i < b->n; ++i) b->capV[i] = b->plans[i]->version;
+      b->capW = workspace;
+    }
+  }
+  if (!same && !b->exec) {
+    batch_persistent_free(&b->bp);
     // domains largest first, each to the least-loaded of the concurrent branches
     std::vector<int> order(b->n);
     for (int i = 0; i < b->n; ++i) order[i] = i;

@@ -64,8 +64,10 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
   const int kx = colk.x, ky = colk.y;
   const bool singular = singular00 && kx == 0 && ky == 0;   // nonsingular with p = 0 on the top face
   CS* colp = spec + (long long)ky * g.P + kx;
+  // the column and the target mean are read at L2 (not through L1), so a persistent kernel that
+  // produced them earlier in the same launch on another SM is seen
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-    const CS v = colp[(long long)k * g.plane];
+    const CS v = __ldcg(&colp[(long long)k * g.plane]);
     zx[k] = (TCm)v.x;
     zy[k] = (TCm)v.y;
     a[k] = (TCm)ag[k];
@@ -140,7 +142,7 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
         shx = sx / (TCm)nz;
         shy = sy / (TCm)nz;
         // refinement sweep: the correction also removes the mean of the current iterate
-        if (target_mean) shx += (TCm)(*target_mean);
+        if (target_mean) shx += (TCm)__ldcg(target_mean);
       } else {
         swt = 0;
         for (int k = 0; k < nz; ++k) swt += (TCm)W[k];

@@ -96,6 +96,38 @@ __device__ __forceinline__ void control_decide(Stats* st, double sd0, double sp,
   if (st->done && !wrote_p) st->need_final = 1;
 }
 
+// Verification of iterate p_{pass-1} by the correction of sweep `pass` (solved, not applied):
+// sd = ||delta_pass||^2 (Parseval on the solved spectrum), sr, ss the residual norms of the sweep's
+// forward x-pass.  With contraction phi <= 1/2, ||e_{pass-1}|| <= ||delta||/(1 - phi) <= 2 ||delta||;
+// above 1/2 the factor is 1/(1 - phi), +inf at phi >= 1; the limiting accuracy `floor` is added.
+// On success the refinement ends on p_{pass-1}.  p_stored: the sweep's forward pass stored that
+// iterate as the double output already.  One thread.
+__device__ __forceinline__ void verify_decide(Stats* st, double sd, double sr, double ss, int pass, double tol,
+                                              double floor, int p_stored) {
+  const double sp = st->sq_p[pass - 1];       // ||p_{pass-1}||^2
+  const double rel = (sp > 0) ? sqrt(sd / sp) : 0.0;
+  const double prev = st->rel_update[pass - 1];
+  const double phi = (pass >= 2 && prev > 0) ? rel / prev : 0.0;
+  double est;
+  if (phi >= 1.0) est = __longlong_as_double(0x7ff0000000000000LL);
+  else est = rel * (phi > 0.5 ? 1.0 / (1.0 - phi) : 2.0);
+  est += floor;
+  st->sq_res[pass - 1] = sr;
+  st->sq_src[pass - 1] = ss;
+  st->rel_residual[pass - 1] = (ss > 0) ? sqrt(sr / ss) : 0.0;
+  if (est <= tol || sp == 0.0) {
+    // the refinement ends on p_{pass-1}: the correction just solved for is not applied
+    st->rel_update[pass] = rel;
+    st->sq_delta[pass] = sd;
+    st->err_est = est;
+    st->err_floor = floor;
+    st->done = 1;
+    st->converged = 1;
+    st->sweeps = pass - 1;
+    if (!st->p_written && !p_stored) st->need_final = 1;
+  }
+}
+
 // Device-resident tables owned by a plan.
 struct Tables {
   // vertical coefficients, level k
@@ -293,6 +325,46 @@ cudaError_t launch_swap_outer_inner(const void* src, void* dst, int A, int M, in
 cudaError_t launch_coefficients(const double* dz, const double* rho0, int nz, double* a_d, double* c_d,
                                 double* W_d, float* a_f, float* c_f, float2* a_ff, float2* c_ff, int top_dirichlet,
                                 cudaStream_t st);
+// ---- persistent multi-domain solve of the mixed path (batch_persistent.cu) ----
+// One domain as the batch hands it over: its plan's geometry, tables and options, its fields
+// and its workspace (spectrum, p0, q, Stats).
+struct BatchDomIn {
+  Geom g;
+  const Tables* tb;
+  float2 cx, cy;            // double-float 1/dx^2, 1/dy^2
+  int lowk_r2, n_lowk, singular00;
+  const int2* lowk_cols;
+  int max_sweeps, verify;
+  double tol;
+  const double* S;
+  double* p;
+  float2* spec;
+  float* p0;
+  float* q;
+  Stats* stats;
+};
+// Device tables of one batch configuration (descriptors and item list, owned by the batch) and
+// the ticket in the caller's workspace.
+struct BatchPersistent {
+  void* doms = nullptr;
+  void* items = nullptr;
+  int n = 0, nitems = 0, stall_dom = -1;
+  size_t smem = 0;
+  unsigned* ticket = nullptr;
+};
+// Shapes the persistent kernel takes: nx in {64, 128, 256, 384, 512}, ny in {64, 128, 256, 384, 512},
+// 2 <= nz <= 128.
+bool batch_persistent_supported(int nx, int ny, int nz);
+// Workspace scratch (ticket, per-domain counters and partial sums) for the given domains.
+size_t batch_persistent_scratch_bytes(const std::vector<BatchDomIn>& d);
+// Builds the descriptors and the item list (host, synchronous copies); scratch: the workspace
+// region of batch_persistent_scratch_bytes.  stall_dom >= 0: test hook, the first control item of
+// that domain waits for a count that never arrives (its bounded wait runs out).  0 on success.
+int batch_persistent_build(BatchPersistent* bp, const std::vector<BatchDomIn>& d, char* scratch, int stall_dom);
+// The initialisation kernel (Stats, counters, ticket) and the persistent kernel, stream-ordered.
+cudaError_t batch_persistent_launch(const BatchPersistent& bp, cudaStream_t st);
+void batch_persistent_free(BatchPersistent* bp);
+
 // Limiting accuracy F of the mixed refinement from the plan's coefficients (one block; nz <= 512):
 // the relative error that the double-float residual's rounding leaves after any number of sweeps,
 // added to every error bound.  Written to *out.

@@ -288,29 +288,7 @@ __global__ void __launch_bounds__(1024) k_verify(Stats* st, const double* __rest
     __syncthreads();
   }
   if (t != 0) return;
-  const double sd = nxny * sh[0][0];          // ||delta_pass||^2 (Parseval)
-  const double sp = st->sq_p[pass - 1];       // ||p_{pass-1}||^2
-  const double rel = (sp > 0) ? sqrt(sd / sp) : 0.0;
-  const double prev = st->rel_update[pass - 1];
-  const double phi = (pass >= 2 && prev > 0) ? rel / prev : 0.0;
-  double est;
-  if (phi >= 1.0) est = __longlong_as_double(0x7ff0000000000000LL);
-  else est = rel * (phi > 0.5 ? 1.0 / (1.0 - phi) : 2.0);
-  est += *floor;   // the limiting accuracy of the residual (control_decide)
-  st->sq_res[pass - 1] = sh[1][0];
-  st->sq_src[pass - 1] = sh[2][0];
-  st->rel_residual[pass - 1] = (sh[2][0] > 0) ? sqrt(sh[1][0] / sh[2][0]) : 0.0;
-  if (est <= tol || sp == 0.0) {
-    // the refinement ends on p_{pass-1}: the correction just solved for is not applied
-    st->rel_update[pass] = rel;
-    st->sq_delta[pass] = sd;
-    st->err_est = est;
-    st->err_floor = *floor;
-    st->done = 1;
-    st->converged = 1;
-    st->sweeps = pass - 1;
-    if (!st->p_written && !p_stored) st->need_final = 1;
-  }
+  verify_decide(st, nxny * sh[0][0], sh[1][0], sh[2][0], pass, tol, *floor, p_stored);
 }
 
 cudaError_t launch_verify(Stats* st_dev, const double* sq, int nsq, const double* res_partials, int res_nblocks,
@@ -332,12 +310,7 @@ __global__ void __launch_bounds__(256) k_finalize(const float2* __restrict__ p0,
   if (!stats->need_final) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npairs;
        i += (long long)gridDim.x * blockDim.x) {
-    const float2 a = __ldcs(&p0[i]);
-    const float2 b = __ldcs(&q[i]);
-    float sx, ex, sy, ey;
-    two_sum(a.x, b.x, sx, ex);
-    two_sum(a.y, b.y, sy, ey);
-    __stcs(&p[i], make_double2(ff2d_int(sx, ex), ff2d_int(sy, ey)));
+    __stcs(&p[i], finalize_pair(__ldcs(&p0[i]), __ldcs(&q[i])));
   }
 }
 
@@ -355,12 +328,7 @@ __global__ void __launch_bounds__(256) k_q_rebuild(const double2* __restrict__ p
   if (done && *done) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npairs;
        i += (long long)gridDim.x * blockDim.x) {
-    const double2 pv = __ldcs(&p[i]);
-    const float2 a = __ldcs(&p0[i]);
-    float hx, lx, hy, ly;
-    d2ff_trunc(pv.x, hx, lx);
-    d2ff_trunc(pv.y, hy, ly);
-    __stcs(&q[i], make_float2(__fadd_rn(__fsub_rn(hx, a.x), lx), __fadd_rn(__fsub_rn(hy, a.y), ly)));
+    __stcs(&q[i], q_rebuild_pair(__ldcs(&p[i]), __ldcs(&p0[i])));
   }
 }
 

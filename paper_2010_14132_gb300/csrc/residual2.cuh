@@ -52,6 +52,23 @@ __device__ __forceinline__ void d2ff_trunc(double x, float& h, float& l) {
   l = __uint_as_float(__float_as_uint(m * sc) ^ sign);
 }
 
+// The double iterate p = p0 + q of two points (exact float sum, then to double).
+__device__ __forceinline__ double2 finalize_pair(float2 a, float2 b) {
+  float sx, ex, sy, ey;
+  two_sum(a.x, b.x, sx, ex);
+  two_sum(a.y, b.y, sy, ey);
+  return make_double2(ff2d_int(sx, ex), ff2d_int(sy, ey));
+}
+// The correction q = p - p0 of two points to float accuracy, from the double iterate p ((h, l) = p
+// split into floats; h - p0 is exact when h and p0 are within a factor 2, and rounds at 2^-24 |q|
+// otherwise).
+__device__ __forceinline__ float2 q_rebuild_pair(double2 pv, float2 a) {
+  float hx, lx, hy, ly;
+  d2ff_trunc(pv.x, hx, lx);
+  d2ff_trunc(pv.y, hy, ly);
+  return make_float2(__fadd_rn(__fsub_rn(hx, a.x), lx), __fadd_rn(__fsub_rn(hy, a.y), ly));
+}
+
 // Coefficients of one level, as lane-broadcast pairs (h = high part, l = low
 // part of the double-float split; n* = negated high part).
 struct ResCoef {

@@ -239,12 +239,15 @@ def poisson_solve(S: torch.Tensor, plan: Plan, rho0: torch.Tensor | None = None)
 class Batch:
     """Many independent domains of uneven sizes, solved by one CUDA-graph launch.
 
-    The graph runs the domains on concurrent branches.  With ``tune=True`` every
-    distinct grid shape gets the autotuner's kernel shapes (measured once per GPU,
-    shape and dtype, then cached), applied to the domains' plans.
+    Mixed batches of supported shapes (nx, ny in {64, 128, 256, 384, 512}, nz <= 128)
+    run as one persistent kernel over a (domain, phase, tile) work list
+    (``persistent=True``, the default); otherwise the graph runs the domains'
+    launch sequences on concurrent branches.  With ``tune=True`` every distinct grid
+    shape gets the autotuner's kernel shapes (measured once per GPU, shape and
+    dtype, then cached), applied to the domains' plans (the graph form uses them).
     """
 
-    def __init__(self, domains, dtype="mixed", device=None, tune=False):
+    def __init__(self, domains, dtype="mixed", device=None, tune=False, persistent=True):
         if dtype not in ("fp32", "mixed"):
             raise ValueError("batched solves support dtype 'fp32' or 'mixed'")
         self.dtype = dtype
@@ -264,8 +267,19 @@ class Batch:
                     ph = N.poisson_batch_plan(self._h, i)
                     for k, v in opts.items():
                         N.poisson_plan_set_option(ph, OPT_IDS[k], v)
+        N.poisson_batch_set_option(self._h, N.POISSON_BATCH_OPT_PERSISTENT, 1 if persistent else 0)
+        self._ws = None
+        self._alloc_ws()
+
+    def _alloc_ws(self):
         nb = N.poisson_batch_workspace_bytes(self._h)
-        self._ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        if self._ws is None or self._ws.numel() < nb + 256:
+            self._ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+
+    def set_option(self, option, value):
+        """A batch option (POISSON_BATCH_OPT_*); the workspace grows if the new form needs more."""
+        N.poisson_batch_set_option(self._h, option, value)
+        self._alloc_ws()
 
     def _ws_ptr(self):
         ptr = self._ws.data_ptr()

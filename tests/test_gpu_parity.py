@@ -269,7 +269,7 @@ def test_batch_autotuned_shapes(dtype, tmp_path, monkeypatch):
     from paper_2010_14132_gb300 import autotune
     importlib.reload(autotune)
     doms = wl.uneven_batch(5, seed=71, nxy_choices=(64, 128), nz_choices=(16, 24))
-    b = Batch(doms, dtype=dtype, tune=True)
+    b = Batch(doms, dtype=dtype, tune=True, persistent=False)
     fd = torch.float32 if dtype == "fp32" else torch.float64
     S = [torch.from_numpy(d.S).to("cuda", fd) for d in doms]
     outs = b.solve(S)
@@ -287,12 +287,13 @@ def batch_64():
     return doms, refs
 
 
-@pytest.mark.parametrize("dtype", ["fp32", "mixed"])
-def test_batch_64_uneven_domains_all_against_oracle(dtype, batch_64):
-    """The 64-domain uneven batch (nx = ny in {64..512}, nz in {32..96}) in one graph launch,
-    every domain against the oracle at the dtype's tolerance."""
+@pytest.mark.parametrize("dtype,persistent", [("fp32", False), ("mixed", True), ("mixed", False)])
+def test_batch_64_uneven_domains_all_against_oracle(dtype, persistent, batch_64):
+    """The 64-domain uneven batch (nx = ny in {64..512}, nz in {32..96}) in one graph launch (mixed: the
+    persistent kernel over every domain's work items, or the graph of per-domain launches), every
+    domain against the oracle at the dtype's tolerance."""
     doms, refs = batch_64
-    b = Batch(doms, dtype=dtype)
+    b = Batch(doms, dtype=dtype, persistent=persistent)
     fd = torch.float32 if dtype == "fp32" else torch.float64
     S = [torch.from_numpy(d.S).to("cuda", fd) for d in doms]
     outs, infos = b.solve(S, info=True)
