@@ -54,6 +54,7 @@ constexpr size_t kBSmemCap = 110 * 1024;  // dynamic shared memory per CTA (two 
 constexpr int kBXPoints = 32768;          // grid points per x item (about)
 constexpr int kBYPoints = 16384;          // complex entries per y item (about)
 constexpr int kBEPairs = 32768;           // point pairs per elementwise item
+constexpr int kBLowk = 32;                // low-|k| columns per column item (one thread each)
 
 enum BPhase : int { BP_XF0 = 0, BP_XR, BP_YF, BP_YI, BP_COL, BP_XI0, BP_XIU, BP_CTL, BP_VER, BP_QR, BP_FIN };
 
@@ -94,13 +95,14 @@ struct BDom {
   Stats* stats;
   double* xpart;   // [n_x][3]: delta^2, p^2, sum p of an inverse x item
   double* rpart;   // [n_x][2]: r^2, S^2 of a residual x item
-  double* cpart;   // [n_lowk + n_ct]: weighted sum |x|^2 of a column item
+  double* cpart;   // [n_lk + n_ct]: weighted sum |x|^2 of a column item
   unsigned* cnt;   // [nph]: items done per phase
   int max_sweeps, verify;
   double tol;
   int x_rows, n_x;                    // rows per x item, x items
   int y_tk, y_lv, n_ystrips, n_y;     // kx per strip, levels per y item, strips, y items
   int c_tc, n_ct;                     // columns per FP32 column tile, tiles
+  int n_lk;                           // low-|k| column items (kBLowk columns each); COL items: n_lk + n_ct
   int e_pairs, n_e;                   // point pairs per elementwise item, items
   int nph;
   BPh ph[kBMaxPh];
@@ -137,15 +139,21 @@ __device__ __forceinline__ void block_sum_store(double* red, const double (&v)[K
 __device__ __noinline__ void fill_xf0(const double* __restrict__ Srow, float2* line, int lane, int nl, int N) {
   const Swizzled sw{};
   const double2* s2 = reinterpret_cast<const double2*>(Srow);
-  for (int e = lane; e < N; e += nl) {
-    const double2 s = __ldg(s2 + e);
-    line[sw(e)] = make_float2(d2f_int(s.x), d2f_int(s.y));
+  for (int e0 = lane; e0 < N; e0 += 4 * nl) {   // four loads in flight before the conversions
+    double2 s[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = (e0 + j * nl < N) ? __ldg(s2 + e0 + j * nl) : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (e0 + j * nl < N) line[sw(e0 + j * nl)] = make_float2(d2f_int(s[j].x), d2f_int(s[j].y));
   }
 }
 
 // The double-float residual of one row into the line (natural order, swizzled); returns the row's
 // sums of r^2 (x, y) and S^2 (z, w) when valid.  store_p: the iterate p0 + q is also stored as the
 // double output (the verification sweep's speculative copy).
+// The double-float residual of one row into the line, one element at a time with the next one's
+// operands in flight.
 template <bool HAS_Q, bool ISO>
 __device__ __noinline__ float4 fill_xr(const BDom& D, const ResCoef K, long long row, float2* line, int lane,
                                        int nl, bool valid, bool store_p) {
@@ -170,38 +178,53 @@ __device__ __noinline__ float4 fill_xr(const BDom& D, const ResCoef K, long long
   double2* prow_out = reinterpret_cast<double2*>(D.p + row * NX);
   const Swizzled sw{};
   float2 racc = make_float2(0.f, 0.f), sacc = racc;
-  for (int e = lane; e < N; e += nl) {
-    const float2 pc = __ldcg(p0c + e);
-    const float pw = __ldcg(prow + (e == 0 ? NX - 1 : 2 * e - 1));
-    const float pe = __ldcg(prow + (e == N - 1 ? 0 : 2 * e + 2));
-    const float2 pn = __ldcg(p0n + e), ps = __ldcg(p0s + e);
-    const float2 pd = has_dn ? __ldcg(p0d + e) : pc, pu = has_up ? __ldcg(p0u + e) : make_float2(0.f, 0.f);
-    float2 qc = make_float2(0.f, 0.f), qn = qc, qs = qc, qd = qc, qu = qc;
-    float qw = 0.f, qe = 0.f;
+  // operands of one element pair; the next pair's are loaded before this pair's arithmetic
+  struct Ops {
+    float2 pc, pn, ps, pd, pu, qc, qn, qs, qd, qu;
+    float pw, pe, qw, qe;
+    double2 S;
+  };
+  auto load = [&](int e) {
+    Ops o;
+    o.pc = __ldcg(p0c + e);
+    o.pw = __ldcg(prow + (e == 0 ? NX - 1 : 2 * e - 1));
+    o.pe = __ldcg(prow + (e == N - 1 ? 0 : 2 * e + 2));
+    o.pn = __ldcg(p0n + e);
+    o.ps = __ldcg(p0s + e);
+    o.pd = has_dn ? __ldcg(p0d + e) : o.pc;
+    o.pu = has_up ? __ldcg(p0u + e) : make_float2(0.f, 0.f);
+    o.qc = o.qn = o.qs = o.qd = o.qu = make_float2(0.f, 0.f);
+    o.qw = o.qe = 0.f;
     if constexpr (HAS_Q) {
-      qc = __ldcg(qc2 + e);
-      qw = __ldcg(qrow + (e == 0 ? NX - 1 : 2 * e - 1));
-      qe = __ldcg(qrow + (e == N - 1 ? 0 : 2 * e + 2));
-      qn = __ldcg(qn2 + e);
-      qs = __ldcg(qs2 + e);
-      qd = has_dn ? __ldcg(qd2 + e) : qc;
-      qu = has_up ? __ldcg(qu2 + e) : make_float2(0.f, 0.f);
+      o.qc = __ldcg(qc2 + e);
+      o.qw = __ldcg(qrow + (e == 0 ? NX - 1 : 2 * e - 1));
+      o.qe = __ldcg(qrow + (e == N - 1 ? 0 : 2 * e + 2));
+      o.qn = __ldcg(qn2 + e);
+      o.qs = __ldcg(qs2 + e);
+      o.qd = has_dn ? __ldcg(qd2 + e) : o.qc;
+      o.qu = has_up ? __ldcg(qu2 + e) : make_float2(0.f, 0.f);
     }
-    const double2 S = __ldg(Srow + e);
+    o.S = __ldg(Srow + e);
+    return o;
+  };
+  Ops nxt = load(lane);
+  for (int e = lane; e < N; e += nl) {
+    const Ops o = nxt;
+    if (e + nl < N) nxt = load(e + nl);
     float2 Sh, Sl;
-    d2ff_trunc(S.x, Sh.x, Sl.x);
-    d2ff_trunc(S.y, Sh.y, Sl.y);
+    d2ff_trunc(o.S.x, Sh.x, Sl.x);
+    d2ff_trunc(o.S.y, Sh.y, Sl.y);
     // the pair's east neighbours are (pc.y, pe), its west neighbours (pw, pc.x)
-    const float2 r = residual_value2<HAS_Q, ISO>(pc, make_float2(pc.y, pe), make_float2(pw, pc.x), pn, ps, pd, pu, qc,
-                                                 make_float2(qc.y, qe), make_float2(qw, qc.x), qn, qs, qd, qu, Sh, Sl,
-                                                 K);
+    const float2 r = residual_value2<HAS_Q, ISO>(o.pc, make_float2(o.pc.y, o.pe), make_float2(o.pw, o.pc.x), o.pn,
+                                                 o.ps, o.pd, o.pu, o.qc, make_float2(o.qc.y, o.qe),
+                                                 make_float2(o.qw, o.qc.x), o.qn, o.qs, o.qd, o.qu, Sh, Sl, K);
     line[sw(e)] = r;
     if (valid) {
       racc = fma2(r, r, racc);
       sacc = fma2(Sh, Sh, sacc);
       if (HAS_Q && store_p) {
         float2 sp, tp;
-        two_sum2(pc, qc, sp, tp);
+        two_sum2(o.pc, o.qc, sp, tp);
         __stcg(prow_out + e, make_double2(ff2d_fast(sp.x, tp.x), ff2d_fast(sp.y, tp.y)));
       }
     }
@@ -241,10 +264,14 @@ __device__ __noinline__ XAcc epi_upd(const BDom& D, long long row, const float2*
   const float2* p0r = reinterpret_cast<const float2*>(D.p0 + row * 2 * N);
   float2* qr = reinterpret_cast<float2*>(D.q + row * 2 * N);
   double2* pr = reinterpret_cast<double2*>(D.p + row * 2 * N);
+  float2 p0n = __ldcg(p0r + lane), qvn = q_valid ? __ldcg(qr + lane) : make_float2(0.f, 0.f);
   for (int e = lane; e < N; e += nl) {
     const float2 z = line[sw(e)];
-    const float2 p0v = __ldcg(p0r + e);
-    const float2 qv = q_valid ? __ldcg(qr + e) : make_float2(0.f, 0.f);
+    const float2 p0v = p0n, qv = qvn;
+    if (e + nl < N) {   // the next element's operands, in flight during this one's arithmetic
+      p0n = __ldcg(p0r + e + nl);
+      if (q_valid) qvn = __ldcg(qr + e + nl);
+    }
     const float2 qn = add2(z, qv);
     if (q_out) __stcg(qr + e, qn);
     float2 sp, tp;
@@ -381,24 +408,79 @@ __device__ void item_y(const BDom& D, int sub, unsigned char* sm) {
 }
 
 // ---------------------------------------------------------------------------
-// column items: a listed low-|k| column (double), or a tile of c_tc consecutive
-// plane entries (FP32, two threads per column); the weighted sum of |x|^2 of the
-// solved columns goes to the item's slot (the verification's Parseval norm)
+// column items: kBLowk listed low-|k| columns (double, one thread each, the
+// recurrence of lowk_column), or a tile of c_tc consecutive plane entries (FP32,
+// two threads per column); the weighted sum of |x|^2 of the solved columns goes
+// to the item's slot (the verification's Parseval norm)
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr size_t col_tile_bytes(int nz, int tc) {
   return b_align((size_t)nz * tc * 12, 16) + (size_t)(nz + (nz & 1)) * 8 + (size_t)tc * 24;
+}
+__host__ __device__ constexpr size_t lowk_item_bytes(int nz) {
+  return ((size_t)3 * nz + (size_t)3 * nz * kBLowk + 6 * kBLowk) * 8;
+}
+
+__device__ void item_lowk(const BDom& D, int pass, int sub, unsigned char* sm) {
+  const Geom& g = D.g;
+  const int nz = g.nz, tid = threadIdx.x, j0 = sub * kBLowk, ncol = min(kBLowk, D.n_lowk - j0);
+  double* a = reinterpret_cast<double*>(sm);
+  double* c = a + nz;
+  double* W = c + nz;
+  double* zx = W + nz;                  // [nz][kBLowk]
+  double* zy = zx + nz * kBLowk;
+  double* w = zy + nz * kBLowk;
+  double* red = w + nz * kBLowk;        // [kBLowk][5]
+  double* sq = red + 5 * kBLowk;        // [kBLowk]
+  const double* target_mean = pass > 0 ? &D.stats->pmean : nullptr;
+  for (int k = tid; k < nz; k += kBT) {
+    a[k] = __ldg(&D.a_d[k]);
+    c[k] = __ldg(&D.c_d[k]);
+    W[k] = __ldg(&D.W_d[k]);
+  }
+  for (int i = tid; i < nz * kBLowk; i += kBT) {
+    const int k = i / kBLowk, j = i - k * kBLowk;
+    if (j < ncol) {
+      const int2 ck = __ldg(&D.lowk_cols[j0 + j]);
+      const float2 v = __ldcg(D.spec + (long long)k * g.plane + (long long)ck.y * g.P + ck.x);
+      zx[i] = (double)v.x;
+      zy[i] = (double)v.y;
+    }
+  }
+  __syncthreads();
+  if (tid < ncol) {
+    const int2 ck = __ldg(&D.lowk_cols[j0 + tid]);
+    const bool singular = D.singular00 && ck.x == 0 && ck.y == 0;
+    lowk_recurrence<double, false>(zx + tid, zy + tid, w + tid, kBLowk, a, c, W, nz, ck.x, ck.y, singular, D.lamx_d,
+                                   D.lamy_d, D.scale_d, target_mean, D.stats, red + 5 * tid, sq + tid);
+  }
+  __syncthreads();
+  for (int i = tid; i < nz * kBLowk; i += kBT) {
+    const int k = i / kBLowk, j = i - k * kBLowk;
+    if (j < ncol) {
+      const int2 ck = __ldg(&D.lowk_cols[j0 + j]);
+      double ox = zx[i], oy = zy[i];
+      if (D.singular00 && ck.x == 0 && ck.y == 0) {
+        ox -= red[5 * j];
+        oy -= red[5 * j + 1];
+      }
+      D.spec[(long long)k * g.plane + (long long)ck.y * g.P + ck.x] = make_float2((float)ox, (float)oy);
+    }
+  }
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int j = 0; j < ncol; ++j) {
+      const int kx = __ldg(&D.lowk_cols[j0 + j]).x;
+      tot += (kx == 0 || kx == g.nxh - 1 ? 1.0 : 2.0) * sq[j];
+    }
+    __stcg(&D.cpart[sub], tot);
+  }
 }
 
 __device__ void item_col(const BDom& D, int pass, int sub, unsigned char* sm) {
   const Geom& g = D.g;
   const int tid = threadIdx.x;
-  const double* target_mean = pass > 0 ? &D.stats->pmean : nullptr;
-  if (sub < D.n_lowk) {
-    double sq = 0.0;
-    const int2 ck = __ldg(&D.lowk_cols[sub]);
-    lowk_column<float, double, false>(sm, D.spec, g, D.a_d, D.c_d, D.W_d, D.lamx_d, D.lamy_d, D.scale_d, ck,
-                                      D.stats, target_mean, D.singular00 != 0, &sq);
-    if (tid == 0) __stcg(&D.cpart[sub], (ck.x == 0 || ck.x == g.nxh - 1 ? 1.0 : 2.0) * sq);
+  if (sub < D.n_lk) {
+    item_lowk(D, pass, sub, sm);
     return;
   }
   const int TC = D.c_tc, nz = g.nz;
@@ -407,11 +489,19 @@ __device__ void item_col(const BDom& D, int pass, int sub, unsigned char* sm) {
   float2* ac = reinterpret_cast<float2*>(sm + b_align((size_t)nz * TC * 12, 16));
   float4* meet = reinterpret_cast<float4*>(ac + nz + (nz & 1));
   float2* xm_s = reinterpret_cast<float2*>(meet + TC);
-  const long long c0 = (long long)(sub - D.n_lowk) * TC;
+  const long long c0 = (long long)(sub - D.n_lk) * TC;
   for (int k = tid; k < nz; k += kBT) ac[k] = make_float2(__ldg(&D.a_f[k]), __ldg(&D.c_f[k]));
-  for (int i = tid; i < nz * TC; i += kBT) {
-    const int k = i / TC, c = i - k * TC;
-    tile[i] = (c0 + c < g.plane) ? __ldcg(D.spec + (long long)k * g.plane + c0 + c) : make_float2(0.f, 0.f);
+  for (int i0 = tid; i0 < nz * TC; i0 += 8 * kBT) {   // eight loads in flight per thread
+    float2 r[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + j * kBT, k = i / TC, c = i - k * TC;
+      r[j] = (i < nz * TC && c0 + c < g.plane) ? __ldcg(D.spec + (long long)k * g.plane + c0 + c)
+                                               : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (i0 + j * kBT < nz * TC) tile[i0 + j * kBT] = r[j];
   }
   __syncthreads();
   const bool part = tid < 2 * TC;
@@ -466,7 +556,7 @@ __device__ void item_ctl(const BDom& D, int type, int pass, unsigned char* sm) {
       v[2] += __ldcg(&D.xpart[3 * (size_t)i + 2]);
     }
   } else {
-    for (int i = tid; i < D.n_lowk + D.n_ct; i += kBT) v[0] += __ldcg(&D.cpart[i]);
+    for (int i = tid; i < D.n_lk + D.n_ct; i += kBT) v[0] += __ldcg(&D.cpart[i]);
   }
   if (pass > 0)
     for (int i = tid; i < D.n_x; i += kBT) {
@@ -620,7 +710,7 @@ __global__ void __launch_bounds__(kBT) k_batch_init(const BDom* __restrict__ dom
 // host side
 // ---------------------------------------------------------------------------
 struct BGeo {
-  int N, Ex, nl, RB, x_rows, n_x, Ey, y_tk, n_ystrips, y_lv, n_y, c_tc, n_ct, e_pairs, n_e;
+  int N, Ex, nl, RB, x_rows, n_x, Ey, y_tk, n_ystrips, y_lv, n_y, c_tc, n_ct, n_lk, e_pairs, n_e;
   size_t smem;
 };
 
@@ -647,12 +737,13 @@ BGeo b_geometry(const BatchDomIn& in) {
       break;
     }
   b.n_ct = (int)((g.plane + b.c_tc - 1) / b.c_tc);
+  b.n_lk = (in.n_lowk + kBLowk - 1) / kBLowk;
   b.e_pairs = kBEPairs;
   b.n_e = (int)((g.N / 2 + b.e_pairs - 1) / b.e_pairs);
   const size_t sx = (size_t)(2 * b.N + 2) * 8 + (size_t)b.RB * swizzled_stride(b.N) * 8;
   const size_t sy = (size_t)((g.ny + 1) & ~1) * 8 + (size_t)g.ny * b.y_tk * 8;
   const size_t sc = col_tile_bytes(g.nz, b.c_tc);
-  const size_t sl = (6 * (size_t)g.nz + 8) * 8;
+  const size_t sl = lowk_item_bytes(g.nz);
   const size_t sctl = b_align(sizeof(Stats), 128) + 5 * (size_t)kBT * 8;
   b.smem = std::max({sx, sy, sc, sl, sctl, (size_t)3 * kBT * 8});
   return b;
@@ -660,7 +751,7 @@ BGeo b_geometry(const BatchDomIn& in) {
 
 std::vector<BPh> b_chain(const BatchDomIn& in, const BGeo& b) {
   std::vector<BPh> ph;
-  const int ncol = in.n_lowk + b.n_ct;
+  const int ncol = b.n_lk + b.n_ct;
   ph.push_back({BP_XF0, 0, b.n_x});
   ph.push_back({BP_YF, 0, b.n_y});
   ph.push_back({BP_COL, 0, ncol});
@@ -684,7 +775,7 @@ std::vector<BPh> b_chain(const BatchDomIn& in, const BGeo& b) {
 // Scratch of one domain: counters, then the x, residual and column partial sums.
 size_t b_dom_scratch(const BatchDomIn& in, const BGeo& b) {
   return b_align(kBMaxPh * 4, 256) + b_align((size_t)3 * b.n_x * 8, 256) + b_align((size_t)2 * b.n_x * 8, 256) +
-         b_align((size_t)(in.n_lowk + b.n_ct) * 8, 256);
+         b_align((size_t)(b.n_lk + b.n_ct) * 8, 256);
 }
 
 }  // namespace
@@ -777,6 +868,7 @@ int batch_persistent_build(BatchPersistent* bp, const std::vector<BatchDomIn>& d
     D.n_y = b.n_y;
     D.c_tc = b.c_tc;
     D.n_ct = b.n_ct;
+    D.n_lk = b.n_lk;
     D.e_pairs = b.e_pairs;
     D.n_e = b.n_e;
     D.nph = (int)ch.size();

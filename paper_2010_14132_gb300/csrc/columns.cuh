@@ -40,6 +40,105 @@ struct LowkArgs {
 //   adjoint: remove the plain mean of the right-hand side, pin v_{nz-1} = 0,
 //            back-substitute, remove the W direction (x -= W sum(x)/sum(W)).
 // ---------------------------------------------------------------------------
+// The sequential recurrence of one low-|k| or singular column, run by one thread
+// out of shared memory: the right-hand side at zx[k ld], zy[k ld] (real and
+// imaginary parts; overwritten by the solution before any mean shift), the
+// back-substitution factors in w[k ld], the level tables a, c, W (stride 1).
+// red receives (shift_x, shift_y, sum W, sum x, sum y) for the caller's output
+// pass; sq_out (nullable, forward only) the sum of |x_k|^2 of the output.
+template <typename TCm, bool ADJ>
+__device__ __forceinline__ void lowk_recurrence(TCm* zx, TCm* zy, TCm* w, int ld, const TCm* a, const TCm* c,
+                                                const TCm* W, int nz, int kx, int ky, bool singular,
+                                                const double* __restrict__ lamx, const double* __restrict__ lamy,
+                                                double scale, const double* __restrict__ target_mean,
+                                                Stats* stats, TCm* red, double* sq_out) {
+  TCm mean_x = 0, mean_y = 0;
+  if (singular) {
+    TCm sw = 0;
+    for (int k = 0; k < nz; ++k) {
+      const TCm wk = ADJ ? (TCm)1 : (TCm)W[k];
+      mean_x += wk * zx[k * ld];
+      mean_y += wk * zy[k * ld];
+      sw += wk;
+    }
+    mean_x /= sw;
+    mean_y /= sw;
+    // only the first solve records mu_W (a refinement correction solve has a target mean)
+    if (!ADJ && stats && !target_mean) stats->mu_w = (double)mean_x * scale;
+  }
+  const TCm s = singular ? (TCm)0 : -((TCm)lamx[kx] + (TCm)lamy[ky]);
+  const TCm ms = -(TCm)scale;
+  TCm g_prev = s, inv_prev = 0, yx = 0, yy = 0;
+  for (int k = 0; k < nz; ++k) {
+    const TCm bx = ms * (zx[k * ld] - mean_x), by = ms * (zy[k * ld] - mean_y);
+    const TCm gk = (k == 0) ? s : s + (TCm)a[k] * g_prev * inv_prev;
+    const TCm u = gk + (TCm)c[k];
+    const bool last_singular = singular && (k == nz - 1);
+    const TCm inv = last_singular ? (TCm)0 : (TCm)1 / u;   // the singular top pivot is pinned
+    if (!ADJ) {
+      TCm nx_ = bx, ny_ = by;
+      if (k > 0) {
+        const TCm f = (TCm)a[k] * inv_prev;
+        nx_ += f * yx;
+        ny_ += f * yy;
+      }
+      yx = nx_;
+      yy = ny_;
+      zx[k * ld] = yx * inv;
+      zy[k * ld] = yy * inv;
+      w[k * ld] = (TCm)c[k] * inv;
+    } else {
+      TCm nx_ = bx, ny_ = by;
+      if (k > 0) {
+        nx_ += (TCm)c[k - 1] * yx;
+        ny_ += (TCm)c[k - 1] * yy;
+      }
+      yx = nx_ * inv;
+      yy = ny_ * inv;
+      zx[k * ld] = yx;
+      zy[k * ld] = yy;
+      w[k * ld] = (k + 1 < nz) ? (TCm)a[k + 1] * inv : (TCm)0;
+    }
+    g_prev = gk;
+    inv_prev = inv;
+  }
+  TCm xx = zx[(nz - 1) * ld], xy = zy[(nz - 1) * ld];
+  TCm sx = xx, sy = xy;
+  for (int k = nz - 2; k >= 0; --k) {
+    xx = zx[k * ld] + w[k * ld] * xx;
+    xy = zy[k * ld] + w[k * ld] * xy;
+    zx[k * ld] = xx;
+    zy[k * ld] = xy;
+    sx += xx;
+    sy += xy;
+  }
+  TCm shx = 0, shy = 0, swt = 1;
+  if (singular) {
+    if (!ADJ) {
+      shx = sx / (TCm)nz;
+      shy = sy / (TCm)nz;
+      // refinement sweep: the correction also removes the mean of the current iterate
+      if (target_mean) shx += (TCm)__ldcg(target_mean);
+    } else {
+      swt = 0;
+      for (int k = 0; k < nz; ++k) swt += (TCm)W[k];
+    }
+  }
+  red[0] = shx;
+  red[1] = shy;
+  red[2] = swt;
+  red[3] = sx;
+  red[4] = sy;
+  if (!ADJ && sq_out) {
+    TCm sq = 0;
+    for (int k = 0; k < nz; ++k) {
+      const TCm ox = singular ? zx[k * ld] - shx : zx[k * ld], oy = singular ? zy[k * ld] - shy : zy[k * ld];
+      sq += ox * ox + oy * oy;
+    }
+    *sq_out = (double)sq;
+  }
+}
+
 // One low-|k| or singular column, solved by the whole block: the strided loads
 // and stores of the column and the coefficient tables go through shared memory
 // in parallel; thread 0 runs the sequential recurrence out of shared memory.
@@ -75,95 +174,11 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
     W[k] = (TCm)Wg[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    TCm mean_x = 0, mean_y = 0;
-    if (singular) {
-      TCm sw = 0;
-      for (int k = 0; k < nz; ++k) {
-        const TCm wk = ADJ ? (TCm)1 : (TCm)W[k];
-        mean_x += wk * zx[k];
-        mean_y += wk * zy[k];
-        sw += wk;
-      }
-      mean_x /= sw;
-      mean_y /= sw;
-      // only the first solve records mu_W (a refinement correction solve has a target mean)
-      if (!ADJ && stats && !target_mean) stats->mu_w = (double)mean_x * scale;
-    }
-    const TCm s = singular ? (TCm)0 : -((TCm)lamx[kx] + (TCm)lamy[ky]);
-    const TCm ms = -(TCm)scale;
-    TCm g_prev = s, inv_prev = 0, yx = 0, yy = 0;
-    for (int k = 0; k < nz; ++k) {
-      const TCm bx = ms * (zx[k] - mean_x), by = ms * (zy[k] - mean_y);
-      const TCm gk = (k == 0) ? s : s + (TCm)a[k] * g_prev * inv_prev;
-      const TCm u = gk + (TCm)c[k];
-      const bool last_singular = singular && (k == nz - 1);
-      const TCm inv = last_singular ? (TCm)0 : (TCm)1 / u;   // the singular top pivot is pinned
-      if (!ADJ) {
-        TCm nx_ = bx, ny_ = by;
-        if (k > 0) {
-          const TCm f = (TCm)a[k] * inv_prev;
-          nx_ += f * yx;
-          ny_ += f * yy;
-        }
-        yx = nx_;
-        yy = ny_;
-        zx[k] = yx * inv;
-        zy[k] = yy * inv;
-        w[k] = (TCm)c[k] * inv;
-      } else {
-        TCm nx_ = bx, ny_ = by;
-        if (k > 0) {
-          nx_ += (TCm)c[k - 1] * yx;
-          ny_ += (TCm)c[k - 1] * yy;
-        }
-        yx = nx_ * inv;
-        yy = ny_ * inv;
-        zx[k] = yx;
-        zy[k] = yy;
-        w[k] = (k + 1 < nz) ? (TCm)a[k + 1] * inv : (TCm)0;
-      }
-      g_prev = gk;
-      inv_prev = inv;
-    }
-    TCm xx = zx[nz - 1], xy = zy[nz - 1];
-    TCm sx = xx, sy = xy;
-    for (int k = nz - 2; k >= 0; --k) {
-      xx = zx[k] + w[k] * xx;
-      xy = zy[k] + w[k] * xy;
-      zx[k] = xx;
-      zy[k] = xy;
-      sx += xx;
-      sy += xy;
-    }
-    TCm shx = 0, shy = 0, swt = 1;
-    if (singular) {
-      if (!ADJ) {
-        shx = sx / (TCm)nz;
-        shy = sy / (TCm)nz;
-        // refinement sweep: the correction also removes the mean of the current iterate
-        if (target_mean) shx += (TCm)__ldcg(target_mean);
-      } else {
-        swt = 0;
-        for (int k = 0; k < nz; ++k) swt += (TCm)W[k];
-      }
-    }
-    red[0] = shx;
-    red[1] = shy;
-    red[2] = swt;
-    red[3] = sx;
-    red[4] = sy;
-  }
+  if (threadIdx.x == 0)
+    lowk_recurrence<TCm, ADJ>(zx, zy, w, 1, a, c, W, nz, kx, ky, singular, lamx, lamy, scale, target_mean, stats,
+                              red, sq_out);
   __syncthreads();
   const TCm shift_x = red[0], shift_y = red[1], sumw = red[2], sum_x = red[3], sum_y = red[4];
-  if (!ADJ && sq_out && threadIdx.x == 0) {
-    TCm sq = 0;
-    for (int k = 0; k < nz; ++k) {
-      const TCm ox = singular ? zx[k] - shift_x : zx[k], oy = singular ? zy[k] - shift_y : zy[k];
-      sq += ox * ox + oy * oy;
-    }
-    *sq_out = (double)sq;
-  }
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
     TCm ox = zx[k], oy = zy[k];
     if (singular) {
@@ -183,8 +198,6 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
     colp[(long long)k * g.plane] = o;
   }
 }
-
-
 
 // ---------------------------------------------------------------------------
 // Twisted FP32 solve of the columns of one staged tile [nz][TC] (two threads per
