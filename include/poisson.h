@@ -129,7 +129,14 @@ typedef enum {
                                     phi <= 1/2 (||delta_n||/(1 - phi) with the measured phi when that is
                                     above 1/2); if that bound is at most the tolerance the solve returns
                                     p_{n-1} without the sweep's inverse transforms (the two-threads-per-
-                                    column kernel only).  0: every sweep is applied in full */
+                                    column kernel only).  On grids with nx/8 > max(8, sqrt(LOWK_RADIUS2))
+                                    and ny > nx/4 the second sweep first solves only the columns with kx,
+                                    |ky'| <= kcut = nx/8 (after a y-pass of those kx) and bounds the other
+                                    columns of delta_2 by sqrt(W_max/W_min) ||r||/lambda_cut (lambda_cut
+                                    the smallest horizontal eigenvalue outside that set): the norm is an
+                                    upper bound, and when it does not certify p_1 the sweep runs in full.
+                                    2: the verification solves every column (no cheaper first try).
+                                    0: every sweep is applied in full */
 } poisson_option;
 
 /* Field layouts (POISSON_OPT_LAYOUT), C order, outermost index first. */

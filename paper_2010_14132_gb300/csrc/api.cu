@@ -356,7 +356,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
                o_aff = take(nz * 8), o_cff = take(nz * 8), o_lxd = take(pl->nxh * 8),
                o_lyd = take(ny * 8), o_lxf = take(pl->nxh * 4), o_lyf = take(ny * 4), o_twxd = take(n * 16),
                o_twrd = take(pl->nxh * 16), o_twyd = take(ny * 16), o_twxf = take(n * 8), o_twrf = take(pl->nxh * 8),
-               o_twyf = take(ny * 8), o_dz = take(nz * 8), o_rho = take(nz * 8), o_floor = take(8);
+               o_twyf = take(ny * 8), o_dz = take(nz * 8), o_rho = take(nz * 8), o_floor = take(16);
   cudaError_t e = cudaMalloc(&pl->tables, off);
   if (e != cudaSuccess) {
     delete pl;
@@ -511,7 +511,7 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       pl->fused = (int)value;
       return POISSON_OK;
     case POISSON_OPT_VERIFY:
-      if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
+      if (!(value == 0 || value == 1 || value == 2)) return POISSON_ERR_INVALID_ARG;
       pl->verify = (int)value;
       return POISSON_OK;
     case POISSON_OPT_RESIDUAL_PASS:
@@ -606,7 +606,7 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
                                    int adjoint, const int* done, const double* target_mean = nullptr,
                                    const ResidualArgs* R = nullptr, int* res_nblocks = nullptr, int pass = 0,
                                    bool* middle_fused = nullptr, double* sqnorm = nullptr,
-                                   int* sqnorm_blocks = nullptr, bool* res_stored_p = nullptr) {
+                                   int* sqnorm_blocks = nullptr, bool* res_stored_p = nullptr, int kcut = -1) {
   const bool t_double = pl->fp64();
   void* spec = ws + pl->off_spec;
   Stats* stats = (Stats*)(ws + pl->off_stats);
@@ -656,7 +656,9 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
     if (e != cudaSuccess) return e;
     if (try_fused) continue;
     ps = prof_begin(pl, POISSON_PHASE_YFWD, st);
-    e = ypass(pl, gc, -1, spec, done, stats, st);
+    Geom gy = gc;
+    if (kcut >= 0) gy.nxh = kcut + 1;   // only the kx the low-wavenumber column solves need
+    e = ypass(pl, gy, -1, spec, done, stats, st);
     prof_end(pl, ps, st);
     if (e != cudaSuccess) return e;
   }
@@ -676,6 +678,7 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
   A.done = done;
   A.target_mean = target_mean;
   A.col_tile = pl->coltile;
+  A.kcut = kcut;
   if (res_nblocks) *res_nblocks = rparts;
   if (sqnorm_blocks) *sqnorm_blocks = 0;
   if (try_fused) {
@@ -700,6 +703,28 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
   e = launch_thomas(A, pl->g, pl->tb, st);
   prof_end(pl, ps, st);
   return e;
+}
+
+// The low-wavenumber verification of sweep 1's iterate (POISSON_OPT_VERIFY = 1): the columns of the
+// correction delta_2 with kx, |ky'| <= kcut = nx/8 are solved exactly (a y-pass of those kx only, the
+// twisted column kernel restricted to them); every other column is (lambda_h + T)^{-1} of the
+// residual's column with lambda_h >= lambda_cut and T = W^{-1} M similar to a positive semidefinite
+// matrix through W^{1/2}, so its norm is at most sqrt(W_max/W_min)/lambda_cut times the residual
+// column's.  ||delta_2||^2 <= ||delta_low||^2 + (W_max/W_min) ||r||^2/lambda_cut^2 is then an upper
+// bound, and the verification test (verify_decide) takes it in place of the full norm.  -1 where the
+// cut would not save work (small grids) or would leave low-|k| columns outside it.
+static int verify_cut(const poisson_plan* pl, double* inv_lcut2) {
+  *inv_lcut2 = 0.0;
+  if (!pl->mixed() || pl->verify != 1 || pl->fused) return -1;
+  const int kc = pl->nx / 8;
+  int r = 0;
+  while ((r + 1) * (r + 1) <= pl->lowk_r2) ++r;
+  if (kc <= 8 || kc <= r || kc + 1 >= pl->nxh || 2 * kc + 1 >= pl->ny) return -1;
+  const double sx = std::sin(M_PI * (kc + 1) / pl->nx), sy = std::sin(M_PI * (kc + 1) / pl->ny);
+  const double lx = 4.0 / (pl->dx * pl->dx) * sx * sx, ly = 4.0 / (pl->dy * pl->dy) * sy * sy;
+  const double lcut = lx < ly ? lx : ly;
+  *inv_lcut2 = 1.0 / (lcut * lcut);
+  return kc;
 }
 
 // Inverse transform (chunked y-pass then x-pass with the given epilogue);
@@ -845,6 +870,26 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
       // from the second sweep on, the correction's norm (Parseval on the solved spectrum) can already
       // certify the current iterate: then the sweep stops before its inverse transforms.  Sweep 2's
       // residual x-pass stores sweep 1's iterate p0 + q as p on the way, in case it does.
+      double inv_lcut2 = 0.0;
+      const int kcut = sweep == 2 ? verify_cut(pl, &inv_lcut2) : -1;
+      if (kcut >= 0) {
+        // first try: certify p_1 from the low-wavenumber columns of delta_2 and a bound on the rest; the
+        // full sweep below then returns at once on the done flag (or runs, verifying again, if not)
+        double* sqv = (double*)(ws + pl->off_sqn);
+        ResidualArgs Rl = R;
+        Rl.p_out = (double*)p;
+        int nres_l = 0, nsq_l = 0;
+        bool stored_l = false;
+        PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &Rl, &nres_l, sweep, nullptr, sqv,
+                                 &nsq_l, &stored_l, kcut));
+        if (nsq_l > 0) {
+          const int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
+          e = launch_verify(stats, sqv, nsq_l, rpart, nres_l, sweep, pl->tol, pl->tb.floor_d,
+                            (double)pl->nx * pl->ny, stored_l ? 1 : 0, inv_lcut2, st);
+          prof_end(pl, ps, st);
+          PGB_CUDA(e);
+        }
+      }
       double* sqn = (pl->verify && sweep >= 2) ? (double*)(ws + pl->off_sqn) : nullptr;
       R.p_out = (sqn && sweep == 2) ? (double*)p : nullptr;
       bool stored = false;
@@ -853,7 +898,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
       if (sqn && nsq > 0) {
         const int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
         e = launch_verify(stats, sqn, nsq, rpart, nres, sweep, pl->tol, pl->tb.floor_d, (double)pl->nx * pl->ny,
-                          stored ? 1 : 0, st);
+                          stored ? 1 : 0, 0.0, st);
         prof_end(pl, ps, st);
         PGB_CUDA(e);
       }

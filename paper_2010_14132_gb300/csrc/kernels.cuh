@@ -240,6 +240,8 @@ struct ThomasArgs {
   double* sqnorm;             // nullable: per-CTA w-weighted sums of |x|^2 of the solved spectrum (the
                               // two-threads-per-column kernel only); *sqnorm_blocks receives their count
   int* sqnorm_blocks;
+  int kcut;                   // >= 0 (two-threads-per-column kernel): solve only the columns with kx <= kcut
+                              // and |ky'| <= kcut (ky' signed); -1: every column
 };
 cudaError_t launch_thomas(const ThomasArgs& a, const Geom& g, const Tables& tb, cudaStream_t st);
 
@@ -276,8 +278,12 @@ cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, c
 // phi = ||delta_n||/||delta_{n-1}|| when that exceeds 1/2.  When the bound is at most tol the
 // refinement stops on p_{n-1} (done; p still to be written when pass n-1 stored only q).  res_partials:
 // the sweep's residual norms (its forward x-pass).  p_stored: that x-pass also stored p_{n-1} as p.
+// inv_lcut2 > 0: the columns were solved only for the low wavenumbers (kx, |ky'| <= kcut) and the rest
+// of ||delta_n||^2 is bounded by (W_max/W_min) ||r||^2/lambda_cut^2 (inv_lcut2 = 1/lambda_cut^2, the
+// weight ratio from floor[1]); see verify_low_wavenumbers in api.cu.
 cudaError_t launch_verify(Stats* st_dev, const double* sq, int nsq, const double* res_partials, int res_nblocks,
-                          int pass, double tol, const double* floor, double nxny, int p_stored, cudaStream_t st);
+                          int pass, double tol, const double* floor, double nxny, int p_stored, double inv_lcut2,
+                          cudaStream_t st);
 // p = p0 + q (double) when the refinement stopped after a sweep that stored only q (Stats::need_final).
 cudaError_t launch_finalize(const float* p0, const float* q, double* p, long long n, const Stats* stats,
                             cudaStream_t st);
@@ -367,7 +373,8 @@ void batch_persistent_free(BatchPersistent* bp);
 
 // Limiting accuracy F of the mixed refinement from the plan's coefficients (one block; nz <= 512):
 // the relative error that the double-float residual's rounding leaves after any number of sweeps,
-// added to every error bound.  Written to *out.
+// added to every error bound.  Written to out[0]; out[1] = max_k W_k / min_k W_k (the bound on the
+// vertical solve's non-normality that the low-wavenumber verification uses).
 cudaError_t launch_accuracy_floor(const double* a_d, const double* c_d, const double* W_d, int nz, int nx, int ny,
                                   double dx, double dy, int top_dirichlet, double* out, cudaStream_t st);
 cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math*/, const void* g, const void* p, const Geom& g_, const Tables& tb,

@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(kFloorThreads) k_accuracy_floor(const double* 
                                                                    double* __restrict__ out) {
   __shared__ double d[kFloorThreads], e2[kFloorThreads], mu[kFloorThreads];
   __shared__ double g[kFloorGrid];
-  __shared__ double red[4][kFloorThreads];
+  __shared__ double red[6][kFloorThreads];
   const int t = threadIdx.x;
-  double kmax = 0, sw = 0, sw2 = 0, gmax = 0;
+  double kmax = 0, sw = 0, sw2 = 0, gmax = 0, wmax = 0, wmin = 1e300;
   for (int k = t; k < nz; k += blockDim.x) {
     d[k] = a[k] + c[k];
     e2[k] = (k + 1 < nz) ? c[k] * a[k + 1] : 0.0;   // squared off-diagonal of B between k and k+1
@@ -102,6 +102,8 @@ __global__ void __launch_bounds__(kFloorThreads) k_accuracy_floor(const double* 
   __syncthreads();
   for (int k = t; k < nz; k += blockDim.x) {
     kmax = fmax(kmax, d[k]);
+    wmax = fmax(wmax, W[k]);
+    wmin = fmin(wmin, W[k]);
     sw += W[k];
     sw2 += W[k] * W[k];
     const double off = ((k > 0) ? sqrt(e2[k - 1]) : 0.0) + ((k + 1 < nz) ? sqrt(e2[k]) : 0.0);
@@ -111,6 +113,8 @@ __global__ void __launch_bounds__(kFloorThreads) k_accuracy_floor(const double* 
   red[1][t] = sw;
   red[2][t] = sw2;
   red[3][t] = gmax;
+  red[4][t] = wmax;
+  red[5][t] = wmin;
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
     if (t < h) {
@@ -118,9 +122,12 @@ __global__ void __launch_bounds__(kFloorThreads) k_accuracy_floor(const double* 
       red[1][t] += red[1][t + h];
       red[2][t] += red[2][t + h];
       red[3][t] = fmax(red[3][t], red[3][t + h]);
+      red[4][t] = fmax(red[4][t], red[4][t + h]);
+      red[5][t] = fmin(red[5][t], red[5][t + h]);
     }
     __syncthreads();
   }
+  const double wratio = (red[5][0] > 0) ? red[4][0] / red[5][0] : 1.0;
   const double K = red[0][0] + 2.0 / (dx * dx) + 2.0 / (dy * dy);
   const double eta = (red[1][0] > 0) ? nz * red[2][0] / (red[1][0] * red[1][0]) : 1.0;
   const double top = red[3][0] * (1.0 + 1e-12) + 1e-300;
@@ -185,7 +192,8 @@ __global__ void __launch_bounds__(kFloorThreads) k_accuracy_floor(const double* 
   if (t == 0) {
     const double u = 0x1p-48;
     const double npts = (double)nx * ny * nz;
-    *out = u * K * sqrt(eta) * sqrt(red[0][0] / npts);
+    out[0] = u * K * sqrt(eta) * sqrt(red[0][0] / npts);
+    out[1] = wratio;
   }
 }
 
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(256) k_control(Stats* st, const double* __rest
 __global__ void __launch_bounds__(1024) k_verify(Stats* st, const double* __restrict__ sq, int nsq,
                                                  const double* __restrict__ res_partials, int res_nblocks, int pass,
                                                  double tol, const double* __restrict__ floor, double nxny,
-                                                 int p_stored) {
+                                                 int p_stored, double inv_lcut2) {
   __shared__ double sh[3][1024];
   if (st->done) return;   // an earlier pass already ended the refinement
   const int t = threadIdx.x;
@@ -288,12 +296,19 @@ __global__ void __launch_bounds__(1024) k_verify(Stats* st, const double* __rest
     __syncthreads();
   }
   if (t != 0) return;
-  verify_decide(st, nxny * sh[0][0], sh[1][0], sh[2][0], pass, tol, *floor, p_stored);
+  double sd = nxny * sh[0][0];
+  // low wavenumbers only: every other column of the correction is (lambda_h + T)^{-1} of the residual's
+  // column, with T = W^{-1} M similar to a positive semidefinite matrix through W^{1/2}, so its norm is at
+  // most sqrt(W_max/W_min)/lambda_h <= sqrt(W_max/W_min)/lambda_cut times the residual column's (Parseval)
+  if (inv_lcut2 > 0) sd += floor[1] * inv_lcut2 * sh[1][0];
+  verify_decide(st, sd, sh[1][0], sh[2][0], pass, tol, floor[0], p_stored);
 }
 
 cudaError_t launch_verify(Stats* st_dev, const double* sq, int nsq, const double* res_partials, int res_nblocks,
-                          int pass, double tol, const double* floor, double nxny, int p_stored, cudaStream_t st) {
-  k_verify<<<1, 1024, 0, st>>>(st_dev, sq, nsq, res_partials, res_nblocks, pass, tol, floor, nxny, p_stored);
+                          int pass, double tol, const double* floor, double nxny, int p_stored, double inv_lcut2,
+                          cudaStream_t st) {
+  k_verify<<<1, 1024, 0, st>>>(st_dev, sq, nsq, res_partials, res_nblocks, pass, tol, floor, nxny, p_stored,
+                               inv_lcut2);
   return cudaGetLastError();
 }
 

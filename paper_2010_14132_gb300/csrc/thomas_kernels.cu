@@ -274,14 +274,15 @@ __global__ void __launch_bounds__(64) k_thomas_pair(float2* __restrict__ spec, G
 // ---------------------------------------------------------------------------
 // sqn (nullable): CTA b stores sqn[b] = sum over its columns of w_kx sum_k |x_k|^2 (w = 1 for
 // kx = 0 and nx/2, 2 otherwise), so that Parseval gives the norm of the correction this solve
-// computed before the inverse transforms.
+// computed before the inverse transforms.  kcut >= 0: only the columns with kx <= kcut and
+// |ky'| <= kcut are solved; CTAs holding none of them store 0 and return before loading.
 template <typename TCm>
 __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Geom g, const float* __restrict__ a,
                                                   const float* __restrict__ c, const float* __restrict__ lamx,
                                                   const float* __restrict__ lamy, float scale, int lowk_r2,
                                                   const int* __restrict__ done, Stats* stats,
                                                   const __grid_constant__ CUtensorMap tm, int box_rows, LowkArgs L,
-                                                  double* __restrict__ sqn) {
+                                                  double* __restrict__ sqn, int kcut) {
   pdl_trigger();
   pdl_wait();   // the previous kernels of the stream are complete
   if (done && *done) return;
@@ -302,6 +303,16 @@ __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Ge
   float2* xm_s = reinterpret_cast<float2*>(meet + TC);             // [TC]: x_m
   uint64_t* bar = reinterpret_cast<uint64_t*>(xm_s + TC);
   const long long c0 = (long long)(blockIdx.x - L.n) * TC;
+  auto low_row = [&](long long r) { return r <= kcut || r >= g.ny - kcut; };
+  if (kcut >= 0) {
+    // the tile spans rows c0/P .. (c0 + TC - 1)/P (TC <= P): does it hold a low column?
+    const long long r0 = c0 / g.P, r1 = (c0 + TC - 1) / g.P;
+    const bool any = (low_row(r0) && c0 - r0 * g.P <= kcut) || (r1 != r0 && r1 < g.ny && low_row(r1));
+    if (!any) {
+      if (sqn && t == 0) sqn[blockIdx.x] = 0.0;
+      return;
+    }
+  }
   for (int k = t; k < nz; k += blockDim.x) ac[k] = make_float2(a[k], c[k]);
   if (t == 0) {
     mbar_init(bar, 1);
@@ -323,7 +334,8 @@ __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Ge
   const long long col = c0 + col_t;
   const int ky = (int)(col / g.P), kx = (int)(col - (long long)ky * g.P);
   const int kys = signed_ky(ky, g.ny);
-  const bool valid = col < g.plane && kx < g.nxh && (kx * kx + kys * kys > lowk_r2);
+  const bool valid = col < g.plane && kx < g.nxh && (kx * kx + kys * kys > lowk_r2) &&
+                     (kcut < 0 || (kx <= kcut && low_row(ky)));
   const float s = valid ? -(lamx[kx] + lamy[ky]) : 1.f;
   const float sq = tw_solve_tile(tile + col_t, wv + col_t, ac, meet, xm_s, TC, nz, col_t, upper, true, valid, s,
                                  -scale, spec + (valid ? col : 0), g.plane);
@@ -435,7 +447,8 @@ static cudaError_t thomas_tw_launch(const ThomasArgs& A, const Geom& g, const Ta
   *used = true;
   if (A.sqnorm && A.sqnorm_blocks) *A.sqnorm_blocks = (int)(nb + A.n_lowk);
   return pdl_launch(kern, dim3((unsigned)(nb + A.n_lowk)), dim3(2 * tc), smem, st, (float2*)A.spec, g, tb.a_f, tb.c_f,
-                    tb.lamx_f, tb.lamy_f, (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows, L, A.sqnorm);
+                    tb.lamx_f, tb.lamy_f, (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows, L, A.sqnorm,
+                    A.kcut);
 }
 
 template <typename T, typename TCm, bool ADJ>

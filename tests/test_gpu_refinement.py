@@ -166,10 +166,11 @@ def test_residual_pass_equals_fused_residual(shape):
 def test_verification_stops_on_the_certified_iterate():
     """Sweep 2's correction, solved but not transformed back, certifies sweep 1's iterate: the
     solve returns p_1 with the bound 2 ||delta_2||/||p_1|| (contraction <= 1/2), and that bound holds
-    against the oracle.  With verification off the correction is applied (bound ||delta_2||)."""
+    against the oracle.  With verification off the correction is applied (bound ||delta_2||).
+    POISSON_OPT_VERIFY = 2 solves every column of delta_2 for the verification."""
     d = wl.anelastic_noise(384, 256, 64, seed=21)
     ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
-    pv, iv = _solve(d)                       # POISSON_OPT_VERIFY = 1 (default)
+    pv, iv = _solve(d, verify=2)
     pa, ia = _solve(d, verify=0)
     p1, i1 = _solve(d, max_sweeps=1, tolerance=1e-300)
     assert iv["converged"] and iv["sweeps"] == 1, iv
@@ -179,10 +180,50 @@ def test_verification_stops_on_the_certified_iterate():
     assert iv["rel_residual"][1] > 0            # the verification sweep formed p_1's residual
     assert ia["converged"] and ia["sweeps"] == 2, ia
     assert ia["error_estimate"] == pytest.approx(ia["rel_update"][2] + F, rel=1e-12), ia
-    # the returned iterate is p_1 (converted to double by the finishing kernel)
+    # the returned iterate is p_1 (stored as a double by the verification sweep's residual x-pass)
     np.testing.assert_allclose(pv, p1, rtol=2e-14, atol=2e-14 * np.abs(p1).max())
     ev, ea = O.relative_l2(pv, ref), O.relative_l2(pa, ref)
     assert ev <= iv["error_estimate"] <= 1e-10, (ev, iv)
     assert ea <= ia["error_estimate"] <= 1e-10, (ea, ia)
     # the verification correction and sweep 2's applied correction are the same solve
     assert iv["rel_update"][2] == pytest.approx(ia["rel_update"][2], rel=1e-3)
+
+
+@pytest.mark.parametrize("shape,seed", [((384, 256, 64), 21), ((512, 512, 64), 3), ((256, 512, 3), 11)])
+def test_low_wavenumber_verification_bounds_the_full_one(shape, seed):
+    """The default verification (POISSON_OPT_VERIFY = 1) solves only the columns with kx, |ky'| <=
+    nx/8 and bounds the rest of ||delta_2|| by sqrt(W_max/W_min) ||r||/lambda_cut: its norm is at least
+    the full verification's, it returns the same iterate bit for bit, and its bound holds.  On the
+    shallow 256 x 512 x 3 grid sweep 1 leaves 1.7e-10, so neither verification certifies p_1 and both
+    solves apply sweep 2 in full."""
+    nx, ny, nz = shape
+    d = wl.anelastic_noise(nx, ny, nz, seed=seed)
+    ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
+    pl, il = _solve(d)                 # low wavenumbers first
+    pf, if_ = _solve(d, verify=2)      # every column
+    assert il["converged"] and if_["converged"] and il["sweeps"] == if_["sweeps"], (il, if_)
+    np.testing.assert_array_equal(pl, pf)
+    err = O.relative_l2(pl, ref)
+    if if_["sweeps"] == 1:
+        assert il["rel_update"][2] >= if_["rel_update"][2] * (1 - 1e-6), (il, if_)
+        assert il["rel_update"][2] <= 4 * if_["rel_update"][2], (il, if_)   # the bound is not vacuous
+        assert err <= if_["error_estimate"] <= il["error_estimate"] <= 1e-10, (err, il, if_)
+    else:
+        assert il["error_estimate"] == if_["error_estimate"], (il, if_)
+        assert err <= il["error_estimate"] <= 1e-10, (err, il)
+
+
+def test_uncertified_low_wavenumber_bound_falls_back_to_the_full_sweep():
+    """A tolerance between the low-wavenumber bound and the full verification's bound: the first try
+    does not certify p_1, the full sweep 2 runs and its own verification does, so the result is the
+    full verification's (same iterate, same bound)."""
+    d = wl.anelastic_noise(384, 256, 64, seed=21)
+    _, il = _solve(d)
+    pf, if_ = _solve(d, verify=2)
+    lo, hi = if_["error_estimate"], il["error_estimate"]
+    assert hi > lo * 1.001, (il, if_)
+    tol = (lo * hi) ** 0.5
+    pt, it = _solve(d, tolerance=tol)
+    assert it["converged"] and it["sweeps"] == 1, it
+    assert it["error_estimate"] == pytest.approx(lo, rel=1e-12), (it, if_)
+    np.testing.assert_array_equal(pt, pf)

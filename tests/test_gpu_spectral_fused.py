@@ -93,7 +93,7 @@ def test_fused_kernel_is_the_one_that_runs():
     d = wl.anelastic_noise(256, 256, 32, seed=48)
     c = _phases(d, "mixed", max_sweeps=2, tolerance=1e-300, spectral_fused=1)
     assert c["spectral"] == 3 and c["yfwd"] == 0 and c["columns"] == 0 and c["yinv"] == 0, c
-    c0 = _phases(d, "mixed", max_sweeps=2, tolerance=1e-300, spectral_fused=0)
+    c0 = _phases(d, "mixed", max_sweeps=2, tolerance=1e-300, spectral_fused=0, verify=2)
     assert c0["spectral"] == 0 and c0["yfwd"] == 3 and c0["columns"] == 3 and c0["yinv"] == 3, c0
 
 
