@@ -88,6 +88,7 @@ struct poisson_plan {
   double* rho_d = nullptr;
   void* tables = nullptr;
   int2* lowk_d = nullptr;
+  double* lowk_inv_d = nullptr;   // pivot reciprocals of the listed columns [n_lowk][nz] (launch_lowk_pivots)
   int n_lowk = 0;
   std::vector<int> lowk_kx;     // kx of every listed low-|k| column (host copy)
   int* mid_d = nullptr;         // item list of the fused spectral middle (device)
@@ -151,6 +152,12 @@ int build_lowk(poisson_plan* pl) {
   pl->n_lowk = (int)cols.size();
   pl->lowk_kx.clear();
   for (const int2& c : cols) pl->lowk_kx.push_back(c.x);
+  if (pl->lowk_inv_d) cudaFree(pl->lowk_inv_d);
+  pl->lowk_inv_d = nullptr;
+  PGB_CUDA(cudaMalloc(&pl->lowk_inv_d, (size_t)pl->n_lowk * pl->nz * sizeof(double)));
+  PGB_CUDA(launch_lowk_pivots(pl->lowk_d, pl->n_lowk, pl->tb.a_d, pl->tb.c_d, pl->tb.lamx_d, pl->tb.lamy_d, pl->nz,
+                              !pl->top_dirichlet(), pl->lowk_inv_d, 0));
+  PGB_CUDA(cudaStreamSynchronize(0));
   return POISSON_OK;
 }
 
@@ -274,6 +281,7 @@ int poisson_plan_destroy(poisson_plan* pl) {
   for (cudaEvent_t e : pl->prof.pool) cudaEventDestroy(e);
   if (pl->tables) cudaFree(pl->tables);
   if (pl->lowk_d) cudaFree(pl->lowk_d);
+  if (pl->lowk_inv_d) cudaFree(pl->lowk_inv_d);
   if (pl->mid_d) cudaFree(pl->mid_d);
   delete pl;
   return POISSON_OK;
@@ -560,6 +568,8 @@ int poisson_plan_set_rho0(poisson_plan* pl, const double* rho0_dev, void* stream
                                pl->top_dirichlet(), st));
   PGB_CUDA(launch_accuracy_floor(tb.a_d, tb.c_d, tb.W_d, pl->nz, pl->nx, pl->ny, pl->g.dx, pl->g.dy,
                                  pl->top_dirichlet(), (double*)tb.floor_d, st));
+  PGB_CUDA(launch_lowk_pivots(pl->lowk_d, pl->n_lowk, tb.a_d, tb.c_d, tb.lamx_d, tb.lamy_d, pl->nz,
+                              !pl->top_dirichlet(), pl->lowk_inv_d, st));
   return POISSON_OK;
 }
 
@@ -670,6 +680,7 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
   A.lowk_r2 = pl->mixed() ? pl->lowk_r2 : 0;
   A.lowk_double = pl->mixed() || t_double;
   A.lowk_cols = pl->lowk_d;
+  A.lowk_inv = A.lowk_double ? pl->lowk_inv_d : nullptr;
   A.singular00 = !pl->top_dirichlet();
   A.n_lowk = pl->n_lowk;
   A.lowk_z = (double2*)(ws + pl->off_lz);
@@ -878,6 +889,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
         double* sqv = (double*)(ws + pl->off_sqn);
         ResidualArgs Rl = R;
         Rl.p_out = (double*)p;
+        Rl.kmax = kcut;   // the residual's transform is read only up to kx = kcut
         int nres_l = 0, nsq_l = 0;
         bool stored_l = false;
         PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &Rl, &nres_l, sweep, nullptr, sqv,
@@ -1262,6 +1274,7 @@ static std::vector<BatchDomIn> batch_dom_inputs(const poisson_batch* b, const vo
     in.n_lowk = pl->n_lowk;
     in.singular00 = !pl->top_dirichlet();
     in.lowk_cols = pl->lowk_d;
+    in.lowk_inv = pl->lowk_inv_d;
     in.max_sweeps = pl->max_sweeps;
     in.verify = pl->verify;
     in.tol = pl->tol;

@@ -72,6 +72,7 @@ struct BDom {
   double scale_d;
   int lowk_r2, n_lowk, singular00;
   const int2* lowk_cols;
+  const double* lowk_inv;   // the plan's pivot table of the listed columns
   const float2* twx;
   const float2* twr;
   const float2* twy;
@@ -451,7 +452,8 @@ __device__ void item_lowk(const BDom& D, int pass, int sub, unsigned char* sm) {
     const int2 ck = __ldg(&D.lowk_cols[j0 + tid]);
     const bool singular = D.singular00 && ck.x == 0 && ck.y == 0;
     lowk_recurrence<double, false>(zx + tid, zy + tid, w + tid, kBLowk, a, c, W, nz, ck.x, ck.y, singular, D.lamx_d,
-                                   D.lamy_d, D.scale_d, target_mean, D.stats, red + 5 * tid, sq + tid);
+                                   D.lamy_d, D.scale_d, target_mean, D.stats, red + 5 * tid, sq + tid,
+                                   D.lowk_inv ? D.lowk_inv + (size_t)(j0 + tid) * nz : nullptr);
   }
   __syncthreads();
   for (int i = tid; i < nz * kBLowk; i += kBT) {
@@ -825,6 +827,7 @@ int batch_persistent_build(BatchPersistent* bp, const std::vector<BatchDomIn>& d
     D.n_lowk = in.n_lowk;
     D.singular00 = in.singular00;
     D.lowk_cols = in.lowk_cols;
+    D.lowk_inv = in.lowk_inv;
     const Tables& tb = *in.tb;
     D.twx = tb.twx_f;
     D.twr = tb.twr_f;

@@ -29,7 +29,27 @@ struct LowkArgs {
   const double* target_mean;
   double scale;   // 1/(nx ny) in double for the double-precision columns
   int singular00; // zero flux at the top: the (0,0) column is singular
+  const double* inv_tab;   // nullable: [n][nz] pivot reciprocals 1/u_k of the listed columns (double
+                           // columns only), from lowk_pivots; the recurrence then reads them
 };
+
+// One step of the low-|k| pivot recurrence (rounded step by step, so that the table built ahead by
+// k_lowk_pivots and a column solve computing its own pivots agree bit for bit):
+// g_k = s + a_k g_{k-1}/u_{k-1} (g_0 = s), u_k = g_k + c_k, returns 1/u_k (0 for the pinned singular top).
+template <typename TCm> __device__ __forceinline__ TCm rn_mul(TCm x, TCm y);
+template <> __device__ __forceinline__ double rn_mul<double>(double x, double y) { return __dmul_rn(x, y); }
+template <> __device__ __forceinline__ float rn_mul<float>(float x, float y) { return __fmul_rn(x, y); }
+template <typename TCm> __device__ __forceinline__ TCm rn_add(TCm x, TCm y);
+template <> __device__ __forceinline__ double rn_add<double>(double x, double y) { return __dadd_rn(x, y); }
+template <> __device__ __forceinline__ float rn_add<float>(float x, float y) { return __fadd_rn(x, y); }
+template <typename TCm>
+__device__ __forceinline__ TCm lowk_pivot_step(int k, TCm s, TCm ak, TCm ck, TCm& g_prev, TCm inv_prev,
+                                               bool last_singular) {
+  const TCm gk = (k == 0) ? s : rn_add(s, rn_mul(rn_mul(ak, g_prev), inv_prev));
+  const TCm u = rn_add(gk, ck);
+  g_prev = gk;
+  return last_singular ? (TCm)0 : (TCm)1 / u;   // the singular top pivot is pinned
+}
 
 // ---------------------------------------------------------------------------
 // Low-|k| and singular columns: one thread per listed column, compute type TCm
@@ -51,7 +71,8 @@ __device__ __forceinline__ void lowk_recurrence(TCm* zx, TCm* zy, TCm* w, int ld
                                                 const TCm* W, int nz, int kx, int ky, bool singular,
                                                 const double* __restrict__ lamx, const double* __restrict__ lamy,
                                                 double scale, const double* __restrict__ target_mean,
-                                                Stats* stats, TCm* red, double* sq_out) {
+                                                Stats* stats, TCm* red, double* sq_out,
+                                                const double* __restrict__ inv_col = nullptr) {
   TCm mean_x = 0, mean_y = 0;
   if (singular) {
     TCm sw = 0;
@@ -71,10 +92,11 @@ __device__ __forceinline__ void lowk_recurrence(TCm* zx, TCm* zy, TCm* w, int ld
   TCm g_prev = s, inv_prev = 0, yx = 0, yy = 0;
   for (int k = 0; k < nz; ++k) {
     const TCm bx = ms * (zx[k * ld] - mean_x), by = ms * (zy[k * ld] - mean_y);
-    const TCm gk = (k == 0) ? s : s + (TCm)a[k] * g_prev * inv_prev;
-    const TCm u = gk + (TCm)c[k];
-    const bool last_singular = singular && (k == nz - 1);
-    const TCm inv = last_singular ? (TCm)0 : (TCm)1 / u;   // the singular top pivot is pinned
+    // the pivots depend on the column's wavenumbers and the levels only: read from the plan's table
+    // when it has them (no division on the chain), else computed here
+    const TCm inv = inv_col ? (TCm)__ldg(inv_col + k)
+                            : lowk_pivot_step<TCm>(k, s, (TCm)a[k], (TCm)c[k], g_prev, inv_prev,
+                                                   singular && (k == nz - 1));
     if (!ADJ) {
       TCm nx_ = bx, ny_ = by;
       if (k > 0) {
@@ -99,7 +121,6 @@ __device__ __forceinline__ void lowk_recurrence(TCm* zx, TCm* zy, TCm* w, int ld
       zy[k * ld] = yy;
       w[k * ld] = (k + 1 < nz) ? (TCm)a[k + 1] * inv : (TCm)0;
     }
-    g_prev = gk;
     inv_prev = inv;
   }
   TCm xx = zx[(nz - 1) * ld], xy = zy[(nz - 1) * ld];
@@ -150,7 +171,8 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
                                             const double* __restrict__ lamx, const double* __restrict__ lamy,
                                             double scale, int2 colk, Stats* stats,
                                             const double* __restrict__ target_mean, bool singular00,
-                                            double* sq_out = nullptr) {
+                                            double* sq_out = nullptr, const double* inv_tab = nullptr,
+                                            int col_index = 0) {
   using CS = typename CT<TS>::t;
   const int nz = g.nz;
   TCm* zx = reinterpret_cast<TCm*>(smraw);   // right-hand side, then z, then x (real parts)
@@ -176,7 +198,8 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
   __syncthreads();
   if (threadIdx.x == 0)
     lowk_recurrence<TCm, ADJ>(zx, zy, w, 1, a, c, W, nz, kx, ky, singular, lamx, lamy, scale, target_mean, stats,
-                              red, sq_out);
+                              red, sq_out,
+                              (inv_tab && sizeof(TCm) == 8) ? inv_tab + (size_t)col_index * nz : nullptr);
   __syncthreads();
   const TCm shift_x = red[0], shift_y = red[1], sumw = red[2], sum_x = red[3], sum_y = red[4];
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {

@@ -195,6 +195,8 @@ struct ResidualArgs {
   const float2* c_ff;
   float2 cx, cy;
   const float2* mu_ff;
+  int kmax;              // > 0: the static residual x-pass stores only the bins kx <= kmax (nothing reads
+                         // the others); 0: every bin
 };
 
 // ---- launchers (stream-ordered, return cudaError_t of the launch) ----
@@ -240,6 +242,7 @@ struct ThomasArgs {
   double* sqnorm;             // nullable: per-CTA w-weighted sums of |x|^2 of the solved spectrum (the
                               // two-threads-per-column kernel only); *sqnorm_blocks receives their count
   int* sqnorm_blocks;
+  const double* lowk_inv;     // nullable: the plan's pivot table of the listed columns (double columns only)
   int kcut;                   // >= 0 (two-threads-per-column kernel): solve only the columns with kx <= kcut
                               // and |ky'| <= kcut (ky' signed); -1: every column
 };
@@ -340,6 +343,7 @@ struct BatchDomIn {
   float2 cx, cy;            // double-float 1/dx^2, 1/dy^2
   int lowk_r2, n_lowk, singular00;
   const int2* lowk_cols;
+  const double* lowk_inv;   // the plan's pivot table of the listed columns
   int max_sweeps, verify;
   double tol;
   const double* S;
@@ -375,6 +379,11 @@ void batch_persistent_free(BatchPersistent* bp);
 // the relative error that the double-float residual's rounding leaves after any number of sweeps,
 // added to every error bound.  Written to out[0]; out[1] = max_k W_k / min_k W_k (the bound on the
 // vertical solve's non-normality that the low-wavenumber verification uses).
+// Pivot reciprocals 1/u_k of the listed low-|k| columns ([n][nz], double), which depend only on the
+// column's wavenumbers and the levels: built once per plan (and per poisson_plan_set_rho0) so that the
+// double column solves run their recurrences without a division on the dependency chain.
+cudaError_t launch_lowk_pivots(const int2* cols, int n, const double* a_d, const double* c_d, const double* lamx_d,
+                               const double* lamy_d, int nz, int singular00, double* inv_tab, cudaStream_t st);
 cudaError_t launch_accuracy_floor(const double* a_d, const double* c_d, const double* W_d, int nz, int nx, int ny,
                                   double dx, double dy, int top_dirichlet, double* out, cudaStream_t st);
 cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math*/, const void* g, const void* p, const Geom& g_, const Tables& tb,

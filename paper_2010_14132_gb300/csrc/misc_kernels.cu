@@ -1,5 +1,6 @@
 // Refinement control, correction rebuild, coefficient tables, rho0-gradient reductions and
 // the field-layout conversion.
+#include "columns.cuh"
 #include "kernels.cuh"
 #include "residual2.cuh"
 
@@ -201,6 +202,35 @@ cudaError_t launch_accuracy_floor(const double* a_d, const double* c_d, const do
                                   double dx, double dy, int top_dirichlet, double* out, cudaStream_t st) {
   if (nz > kFloorThreads) return cudaErrorInvalidValue;
   k_accuracy_floor<<<1, kFloorThreads, 0, st>>>(a_d, c_d, W_d, nz, nx, ny, dx, dy, top_dirichlet, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Pivot reciprocals of the listed low-|k| columns, one thread per column, with the step the column
+// solves use (lowk_pivot_step), so that reading the table gives the same solution bit for bit.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_lowk_pivots(const int2* __restrict__ cols, int n,
+                                                     const double* __restrict__ a, const double* __restrict__ c,
+                                                     const double* __restrict__ lamx,
+                                                     const double* __restrict__ lamy, int nz, int singular00,
+                                                     double* __restrict__ inv_tab) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int2 ck = cols[j];
+  const bool singular = singular00 && ck.x == 0 && ck.y == 0;
+  const double s = singular ? 0.0 : -(lamx[ck.x] + lamy[ck.y]);
+  double g_prev = s, inv_prev = 0.0;
+  for (int k = 0; k < nz; ++k) {
+    const double inv = lowk_pivot_step<double>(k, s, a[k], c[k], g_prev, inv_prev, singular && (k == nz - 1));
+    inv_tab[(size_t)j * nz + k] = inv;
+    inv_prev = inv;
+  }
+}
+
+cudaError_t launch_lowk_pivots(const int2* cols, int n, const double* a_d, const double* c_d, const double* lamx_d,
+                               const double* lamy_d, int nz, int singular00, double* inv_tab, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_lowk_pivots<<<(n + 127) / 128, 128, 0, st>>>(cols, n, a_d, c_d, lamx_d, lamy_d, nz, singular00, inv_tab);
   return cudaGetLastError();
 }
 

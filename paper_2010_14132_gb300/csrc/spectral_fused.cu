@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(kMidTK * (N / kMidE), 2)
                       A.spec + (valid ? (long long)ky * g.P + kx : 0), g.plane);
       } else {   // MID_L
         lowk_column<float, TCm, false>(buf, A.spec, g, A.L.a_d, A.L.c_d, A.L.W_d, A.L.lamx_d, A.L.lamy_d, A.L.scale,
-                                       A.L.cols[sub], A.stats, A.L.target_mean, A.L.singular00 != 0);
+                                       A.L.cols[sub], A.stats, A.L.target_mean, A.L.singular00 != 0, nullptr,
+                                       A.L.inv_tab, sub);
       }
     }
     // the item's shared-memory accesses precede the next TMA write into the buffer, and its spectrum
@@ -309,7 +310,7 @@ cudaError_t launch_spectral_fused(const ThomasArgs& T, const Geom& g, const FftP
   A.scale = (float)T.scale;
   A.lowk_r2 = T.lowk_r2;
   A.L = LowkArgs{T.lowk_cols, T.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, T.target_mean, T.scale,
-                 T.singular00};
+                 T.singular00, T.lowk_inv};
   A.items = items;
   A.nitems = nitems;
   A.nstrips = (g.nxh + TK - 1) / TK;

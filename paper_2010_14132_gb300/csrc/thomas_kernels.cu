@@ -42,7 +42,8 @@ __global__ void __launch_bounds__(128) k_thomas(typename CT<T>::t* __restrict__ 
   extern __shared__ __align__(128) unsigned char smraw[];
   if ((int)blockIdx.x < L.n) {
     lowk_column<T, TCm, ADJ>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale,
-                             L.cols[blockIdx.x], stats, L.target_mean, L.singular00 != 0);
+                             L.cols[blockIdx.x], stats, L.target_mean, L.singular00 != 0, nullptr, L.inv_tab,
+                             blockIdx.x);
     return;
   }
   const int TC = blockDim.x, t = threadIdx.x, nz = g.nz;
@@ -212,7 +213,8 @@ __global__ void __launch_bounds__(64) k_thomas_pair(float2* __restrict__ spec, G
   extern __shared__ __align__(128) unsigned char smraw[];
   if ((int)blockIdx.x < L.n) {
     lowk_column<float, TCm, ADJ>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale,
-                                 L.cols[blockIdx.x], stats, L.target_mean, L.singular00 != 0);
+                                 L.cols[blockIdx.x], stats, L.target_mean, L.singular00 != 0, nullptr, L.inv_tab,
+                                 blockIdx.x);
     return;
   }
   const int TC = blockDim.x, t = threadIdx.x, nz = g.nz;
@@ -275,7 +277,9 @@ __global__ void __launch_bounds__(64) k_thomas_pair(float2* __restrict__ spec, G
 // sqn (nullable): CTA b stores sqn[b] = sum over its columns of w_kx sum_k |x_k|^2 (w = 1 for
 // kx = 0 and nx/2, 2 otherwise), so that Parseval gives the norm of the correction this solve
 // computed before the inverse transforms.  kcut >= 0: only the columns with kx <= kcut and
-// |ky'| <= kcut are solved; CTAs holding none of them store 0 and return before loading.
+// |ky'| <= kcut are solved; the grid then holds just their tiles, ceil((kcut + 1)/TC) from the start
+// of each of the rows ky = 0..kcut and ny - kcut..ny - 1 (P, a multiple of 16, keeps every tile's
+// first entry 16-byte aligned for the TMA box).
 template <typename TCm>
 __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Geom g, const float* __restrict__ a,
                                                   const float* __restrict__ c, const float* __restrict__ lamx,
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Ge
     double sq = 0.0;
     const int2 ck = L.cols[blockIdx.x];
     lowk_column<float, TCm, false>(smraw, spec, g, L.a_d, L.c_d, L.W_d, L.lamx_d, L.lamy_d, L.scale, ck, stats,
-                                   L.target_mean, L.singular00 != 0, sqn ? &sq : nullptr);
+                                   L.target_mean, L.singular00 != 0, sqn ? &sq : nullptr, L.inv_tab, blockIdx.x);
     if (sqn && threadIdx.x == 0) sqn[blockIdx.x] = (ck.x == 0 || ck.x == g.nxh - 1 ? 1.0 : 2.0) * sq;
     return;
   }
@@ -302,16 +306,12 @@ __global__ void __launch_bounds__(128) k_thomas_tw(float2* __restrict__ spec, Ge
   float4* meet = reinterpret_cast<float4*>(ac + nz + (nz & 1));   // [TC]: lower part's (g-term, z-term re, im, -)
   float2* xm_s = reinterpret_cast<float2*>(meet + TC);             // [TC]: x_m
   uint64_t* bar = reinterpret_cast<uint64_t*>(xm_s + TC);
-  const long long c0 = (long long)(blockIdx.x - L.n) * TC;
+  long long c0 = (long long)(blockIdx.x - L.n) * TC;
   auto low_row = [&](long long r) { return r <= kcut || r >= g.ny - kcut; };
-  if (kcut >= 0) {
-    // the tile spans rows c0/P .. (c0 + TC - 1)/P (TC <= P): does it hold a low column?
-    const long long r0 = c0 / g.P, r1 = (c0 + TC - 1) / g.P;
-    const bool any = (low_row(r0) && c0 - r0 * g.P <= kcut) || (r1 != r0 && r1 < g.ny && low_row(r1));
-    if (!any) {
-      if (sqn && t == 0) sqn[blockIdx.x] = 0.0;
-      return;
-    }
+  if (kcut >= 0) {   // tile jt of low row r
+    const int tpr = (kcut + TC) / TC, tb = (int)blockIdx.x - L.n, r = tb / tpr, jt = tb - r * tpr;
+    const int ky = r <= kcut ? r : g.ny - (2 * kcut + 1 - r);
+    c0 = (long long)ky * g.P + (long long)jt * TC;
   }
   for (int k = t; k < nz; k += blockDim.x) ac[k] = make_float2(a[k], c[k]);
   if (t == 0) {
@@ -409,7 +409,7 @@ static cudaError_t thomas_pair_launch(const ThomasArgs& A, const Geom& g, const 
   const int npairs = g.ny / 2 + 1;
   const long long nb = (long long)npairs * kx_chunks;
   const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale,
-                   A.singular00};
+                   A.singular00, A.lowk_inv};
   kern<<<(unsigned)(nb + A.n_lowk), tc, smem, st>>>((float2*)A.spec, g, tb.a_f, tb.c_f, tb.lamx_f, tb.lamy_f,
                                                     (float)A.scale, A.lowk_r2, A.done, A.stats, tm, box_rows,
                                                     kx_chunks, L);
@@ -441,9 +441,11 @@ static cudaError_t thomas_tw_launch(const ThomasArgs& A, const Geom& g, const Ta
   auto kern = k_thomas_tw<TCm>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long nb = (g.plane + tc - 1) / tc;
+  // every tile of the plane, or (kcut >= 0) the low rows' first ceil((kcut + 1)/tc) tiles
+  const long long nb = A.kcut >= 0 ? (long long)(2 * A.kcut + 1) * ((A.kcut + tc) / tc) : (g.plane + tc - 1) / tc;
+  if (A.kcut >= 0 && (2 * A.kcut + 1 > g.ny || A.kcut + tc > g.P || g.P % 16)) return cudaSuccess;
   const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale,
-                   A.singular00};
+                   A.singular00, A.lowk_inv};
   *used = true;
   if (A.sqnorm && A.sqnorm_blocks) *A.sqnorm_blocks = (int)(nb + A.n_lowk);
   return pdl_launch(kern, dim3((unsigned)(nb + A.n_lowk)), dim3(2 * tc), smem, st, (float2*)A.spec, g, tb.a_f, tb.c_f,
@@ -494,7 +496,7 @@ static cudaError_t thomas_launch(const ThomasArgs& A, const Geom& g, const Table
                           ? 1
                           : 0;
   const LowkArgs L{A.lowk_cols, A.n_lowk, tb.a_d, tb.c_d, tb.W_d, tb.lamx_d, tb.lamy_d, A.target_mean, A.scale,
-                   A.singular00};
+                   A.singular00, A.lowk_inv};
   kern<<<(unsigned)(nb + A.n_lowk), tc, smem, st>>>((C*)A.spec, g, a, c, lx, ly, (T)A.scale, A.lowk_r2, A.done,
                                                    A.stats, tm, use_tma, box_rows, L);
   return cudaGetLastError();

@@ -81,7 +81,7 @@ __device__ __forceinline__ void ring_drain(Ring& rg, uint64_t* bar, int ns) {
 // bins 0..N to dst: each thread takes the bin pairs (k, N - k), k = lane + nl q.
 template <int N, int E>
 __device__ __forceinline__ void r2c_unpack_store(const float2* fin, const float2* twr_s, float2* dst, int lane,
-                                                 bool valid) {
+                                                 bool valid, int kmax = N) {
   using C = float2;
   constexpr int nl = N / E;
   const Swizzled sw{};
@@ -93,9 +93,9 @@ __device__ __forceinline__ void r2c_unpack_store(const float2* fin, const float2
     const C ev = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
     const C dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y - B.y));
     const C wo = cmul(twr_s[k], make_float2(dd.y, -dd.x));   // w^k * (-i dd)
-    if (valid) {
-      dst[k] = cadd(ev, wo);
-      dst[N - k] = cconj(csub(ev, wo));
+    if (valid) {   // bins above kmax are not stored
+      if (k <= kmax) dst[k] = cadd(ev, wo);
+      if (N - k <= kmax) dst[N - k] = cconj(csub(ev, wo));
     }
   }
   if (lane == 0) {   // the self-paired bin k = N/2
@@ -104,7 +104,7 @@ __device__ __forceinline__ void r2c_unpack_store(const float2* fin, const float2
     const C ev = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
     const C dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y - B.y));
     const C wo = cmul(twr_s[N / 2], make_float2(dd.y, -dd.x));
-    if (valid) dst[N / 2] = cadd(ev, wo);
+    if (valid && N / 2 <= kmax) dst[N / 2] = cadd(ev, wo);
   }
 }
 

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xr
     }
     sync();   // the line's threads have read the S row before it is overwritten
     const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
-    r2c_unpack_store<N, E>(fin, twr_s, spec + (valid ? row : 0) * g.P, lane, valid);
+    r2c_unpack_store<N, E>(fin, twr_s, spec + (valid ? row : 0) * g.P, lane, valid, R.kmax > 0 ? R.kmax : N);
     fence_proxy_async_smem();   // generic writes to the staged row come before its refill by TMA
   }
   if (tid == 0) {
