@@ -129,7 +129,22 @@ def recorded_traffic(phase):
     return None
 
 
-def algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3, verified=False):
+def verify_cut(nx, ny, lowk_r2=64):
+    """The wavenumber cut of the library's low-wavenumber verification (POISSON_OPT_VERIFY = 1):
+    kcut = nx/8 where it saves work and keeps every low-|k| column inside it, else None (the
+    verification then solves every column)."""
+    kc = nx // 8
+    r = int(lowk_r2 ** 0.5)
+    while (r + 1) ** 2 <= lowk_r2:
+        r += 1
+    while r * r > lowk_r2:
+        r -= 1
+    if kc <= 8 or kc <= r or kc + 1 >= nx // 2 + 1 or 2 * kc + 1 >= ny:
+        return None
+    return kc
+
+
+def algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3, verified=False, kcut=None):
     """Per-phase bytes of one mixed solve with `sweeps` executed sweeps (of at most max_sweeps),
     and the solve's algorithmic total.
 
@@ -139,11 +154,18 @@ def algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3, verified=False):
     last sweep allowed; a later sweep also reads q and stores p.  A third sweep first rebuilds q
     from p ("residual" phase); the final p = p0 + q after a stop at sweep 1 is the "control" phase.
     verified: one more sweep ran up to its column solves and its correction's norm certified the
-    iterate (its residual x-pass, forward y-pass and columns run; no inverse transforms).
+    iterate (its residual x-pass, forward y-pass and columns run; no inverse transforms); its
+    residual x-pass also stores the certified iterate as p.  kcut: that verification solved only the
+    columns with kx, |ky'| <= kcut, so its residual's transform is stored for kx <= kcut only, its
+    y-pass covers those kx and its column solve the (kcut + 1)(2 kcut + 1) low columns.
     """
     N = nx * ny * nz
     Nc = (nx // 2 + 1) * ny * nz
+    Ncx = (kcut + 1) * ny * nz if kcut is not None else Nc              # low-kx part of the spectrum
+    Ncl = (kcut + 1) * (2 * kcut + 1) * nz if kcut is not None else Nc  # low columns
     q_only = max_sweeps >= 2   # sweep 1 stores q, not p
+    nv = 1 if verified else 0
+    v = sweeps + 1              # the verification sweep's index
 
     def xinv_sweep(s):
         reads = 8 * Nc + 4 * N + (4 * N if s > 1 else 0)
@@ -151,21 +173,21 @@ def algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3, verified=False):
         return reads + writes
 
     b = {
-        "xfwd": 8 * N + 8 * Nc + sum(8 * N + 4 * N + (4 * N if s > 1 else 0) + 8 * Nc
-                                     for s in range(1, sweeps + 1 + (1 if verified else 0))),
-        "yfwd": (1 + sweeps + (1 if verified else 0)) * 16 * Nc,
-        "columns": (1 + sweeps + (1 if verified else 0)) * 16 * Nc,
+        "xfwd": 8 * N + 8 * Nc + sum(8 * N + 4 * N + (4 * N if s > 1 else 0) + 8 * Nc for s in range(1, sweeps + 1))
+                + nv * (8 * N + 4 * N + (4 * N if v > 1 else 0) + 8 * Ncx + 8 * N),
+        "yfwd": (1 + sweeps) * 16 * Nc + nv * 16 * Ncx,
+        "columns": (1 + sweeps) * 16 * Nc + nv * 16 * Ncl,
         "yinv": (1 + sweeps) * 16 * Nc,
         "xinv": (8 * Nc + 4 * N) + sum(xinv_sweep(s) for s in range(1, sweeps + 1)),
         # q rebuilt from p and p0 before a third sweep
         "residual": 16 * N if sweeps >= 3 else 0,
-        # p = p0 + q written after a stop at sweep 1 (or on sweep 1's iterate, verified)
-        "control": 16 * N if (sweeps == 1 and q_only) else 0,
+        # p = p0 + q written after a stop at sweep 1 by the stopping rule (a verification stores p itself)
+        "control": 16 * N if (sweeps == 1 and q_only and not verified) else 0,
     }
     # the solve as a whole: read S, write p once; spectrum written and read once per pass;
     # each applied sweep also reads S and p and updates p; a verification sweep reads S and p and
-    # moves the spectrum once
-    total = 16 * N + 16 * Nc + sweeps * (32 * N + 16 * Nc) + ((16 * N + 16 * Nc) if verified else 0)
+    # moves the part of the spectrum it solves once
+    total = 16 * N + 16 * Nc + sweeps * (32 * N + 16 * Nc) + nv * (16 * N + 16 * Ncx)
     return b, total
 
 
@@ -353,7 +375,9 @@ def main():
     peak, peak_kind = measured_peaks()
     sweeps = int(info["sweeps"])
     verified = sweeps + 1 < 4 and info["rel_update"][sweeps + 1] > 0
-    alg, alg_total = algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3, verified=verified)
+    # the low-wavenumber verification certifies on this workload (POISSON_OPT_VERIFY = 1, sweep 2)
+    kcut = verify_cut(nx, ny) if (verified and sweeps == 1) else None
+    alg, alg_total = algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3, verified=verified, kcut=kcut)
     phases = {}
     for name, (tms, cnt) in prof.items():
         if cnt == 0:

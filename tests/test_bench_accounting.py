@@ -71,4 +71,27 @@ def test_verified_solve_counts_one_sweep_plus_the_verification():
     for name in ("yfwd", "columns"):
         assert per_phase[name] == 3 * 16 * Nc
     assert per_phase["yinv"] == 2 * 16 * Nc
-    assert per_phase["control"] == 16 * N     # p = p0 + q written at the end
+    assert per_phase["control"] == 0          # the verification's residual pass stores p itself
+    # its residual x-pass: S, p0, q in; spectrum and p out
+    assert per_phase["xfwd"] == (8 * N + 8 * Nc) + (12 * N + 8 * Nc) + (16 * N + 8 * Nc + 8 * N)
+
+
+def test_low_wavenumber_verification_moves_its_part_of_the_spectrum():
+    nx, ny, nz = 1024, 1024, 128
+    N, Nc = nx * ny * nz, (nx // 2 + 1) * ny * nz
+    kc = B.verify_cut(nx, ny)
+    assert kc == 128
+    Ncx, Ncl = (kc + 1) * ny * nz, (kc + 1) * (2 * kc + 1) * nz
+    per_phase, total = B.algorithmic_bytes(nx, ny, nz, 1, max_sweeps=3, verified=True, kcut=kc)
+    assert total == 16 * N + 16 * Nc + (32 * N + 16 * Nc) + (16 * N + 16 * Ncx)
+    assert per_phase["yfwd"] == 2 * 16 * Nc + 16 * Ncx
+    assert per_phase["columns"] == 2 * 16 * Nc + 16 * Ncl
+    assert per_phase["xfwd"] == (8 * N + 8 * Nc) + (12 * N + 8 * Nc) + (16 * N + 8 * Ncx + 8 * N)
+
+
+@pytest.mark.parametrize("nx,ny,lowk,expect", [(1024, 1024, 64, 128), (384, 256, 64, 48), (64, 512, 64, None),
+                                               (256, 64, 64, None), (512, 512, 400, 64), (512, 512, 4096, None)])
+def test_verify_cut_rule(nx, ny, lowk, expect):
+    # kcut = nx/8 while it exceeds 8 and the low-|k| radius, stays inside the half spectrum and leaves
+    # high rows in y (2 kcut + 1 < ny)
+    assert B.verify_cut(nx, ny, lowk) == expect
