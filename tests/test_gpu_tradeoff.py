@@ -36,7 +36,9 @@ def test_precision_ladder_orders_accuracy():
     assert m1 < 1e-2 * m0 and m1 <= 1e-10
     # sweeps 2 and 3 sit at the double-float residual's floor (~1e-12 here): no worse than sweep 1
     assert m2 <= m1 + 1e-12 and m3 <= m1 + 1e-12 and max(m2, m3) <= 1e-11
-    assert rows["mixed, stop rule"]["rel_l2_diff"] <= 1e-10
+    for mode in ("mixed, stop rule", "mixed, stop rule, full-spectrum verification",
+                 "mixed, stop rule, no verification"):
+        assert rows[mode]["rel_l2_diff"] <= rows[mode]["error_estimate"] <= 1e-10, (mode, rows[mode])
     # k sweeps exactly, unless an update comes out exactly zero (then the rule stops early)
     assert rows["mixed, 0 sweeps"]["sweeps"] == 0 and rows["mixed, 1 sweep"]["sweeps"] == 1
     assert 1 <= rows["mixed, 2 sweeps"]["sweeps"] <= 2 and 1 <= rows["mixed, 3 sweeps"]["sweeps"] <= 3
