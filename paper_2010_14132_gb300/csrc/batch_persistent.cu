@@ -109,8 +109,8 @@ struct BDom {
   BPh ph[kBMaxPh];
 };
 
-__host__ __device__ constexpr int bx_elems(int N) { return N % 3 == 0 ? 24 : 8; }
-__host__ __device__ constexpr int by_elems(int ny) { return ny % 3 == 0 ? 24 : 16; }
+__host__ __device__ constexpr int bx_elems(int N) { return N % 3 == 0 ? kE3 : 8; }
+__host__ __device__ constexpr int by_elems(int ny) { return ny % 3 == 0 ? kE3 : 16; }
 __host__ __device__ constexpr size_t b_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ---------------------------------------------------------------------------

@@ -17,7 +17,8 @@
 namespace pgb {
 
 // Radix schedule for n = 2^a 3^b and E elements per thread: radix-3 stages,
-// then radix 16 (when E is a multiple of 16) or radix 8, then a final 2, 4 or 8.
+// then radix 16 (when E is a multiple of 16), 8 (a multiple of 8) or 4, then a
+// final 2, 4 or 8.
 constexpr int st_count(int n, int p) {
   int c = 0;
   while (n > 1 && n % p == 0) {
@@ -26,7 +27,10 @@ constexpr int st_count(int n, int p) {
   }
   return c;
 }
-constexpr int st_big_log(int e) { return e % 16 == 0 ? 4 : 3; }   // log2 of the main power-of-two radix
+constexpr int st_big_log(int e) { return e % 16 == 0 ? 4 : (e % 8 == 0 ? 3 : 2); }   // log2 of the main power-of-two radix
+// Elements per thread for lengths with a factor 3: radix 3, then radix 4 (12 values per thread
+// keep a line's data in twice as many threads as the radix-8 schedule's 24, for the same shared memory)
+constexpr int kE3 = 12;
 constexpr int st_nstages(int n, int e) {
   return st_count(n, 3) + st_count(n, 2) / st_big_log(e) + (st_count(n, 2) % st_big_log(e) ? 1 : 0);
 }

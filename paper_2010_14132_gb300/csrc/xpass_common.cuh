@@ -172,15 +172,15 @@ template <typename K> cudaError_t prepare(K kernel, int threads, size_t smem, in
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// Elements per thread of the persistent x-pass for a half length N: 24 when N has
-// a factor 3 (radix 3, then 8), else the plan's 8 or 16.
-inline int xs_elems(int N, int plan_e) { return N % 3 == 0 ? 24 : (plan_e == 16 ? 16 : 8); }
+// Elements per thread of the persistent x-pass for a half length N: kE3 when N has
+// a factor 3 (radix 3, then 4), else the plan's 8 or 16.
+inline int xs_elems(int N, int plan_e) { return N % 3 == 0 ? kE3 : (plan_e == 16 ? 16 : 8); }
 
 // Dispatch to the compile-time (N, E) instance; shapes the engine cannot take are
 // never instantiated (and are not reported supported).
 #define PGB_XS_E_SWITCH(E, ...)                                 \
-  if ((E) == 24) {                                              \
-    constexpr int EE = 24;                                      \
+  if ((E) == kE3) {                                             \
+    constexpr int EE = kE3;                                     \
     __VA_ARGS__;                                                \
   } else if ((E) == 16) {                                       \
     constexpr int EE = 16;                                      \
@@ -189,9 +189,9 @@ inline int xs_elems(int N, int plan_e) { return N % 3 == 0 ? 24 : (plan_e == 16 
     constexpr int EE = 8;                                       \
     __VA_ARGS__;                                                \
   }
-#define PGB_XS_E8_24_SWITCH(E, ...)                             \
-  if ((E) == 24) {                                              \
-    constexpr int EE = 24;                                      \
+#define PGB_XS_E8_E3_SWITCH(E, ...)                             \
+  if ((E) == kE3) {                                             \
+    constexpr int EE = kE3;                                     \
     __VA_ARGS__;                                                \
   } else {                                                      \
     constexpr int EE = 8;                                       \

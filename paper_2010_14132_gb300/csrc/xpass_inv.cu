@@ -15,7 +15,10 @@ namespace {
 #ifndef PGB_XINV_MIN_BLOCKS
 #define PGB_XINV_MIN_BLOCKS 3
 #endif
-constexpr int xinv_min_blocks(int e) { return e >= 24 ? 1 : PGB_XINV_MIN_BLOCKS; }
+#ifndef PGB_XINV_E3_BLOCKS
+#define PGB_XINV_E3_BLOCKS 2
+#endif
+constexpr int xinv_min_blocks(int e) { return e % 3 == 0 ? PGB_XINV_E3_BLOCKS : PGB_XINV_MIN_BLOCKS; }
 template <int N, int E, typename TO, int MODE>
 __global__ void __launch_bounds__(xs_threads(E), xinv_min_blocks(E)) k_xinv_s(const float2* __restrict__ spec, TO* __restrict__ out, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,

@@ -23,7 +23,12 @@ namespace {
 #ifndef PGB_XRES_Q_BLOCKS
 #define PGB_XRES_Q_BLOCKS 2
 #endif
-constexpr int xres_min_blocks(int e, bool has_q) { return e >= 24 ? 2 : (e >= 16 ? 4 : (has_q ? PGB_XRES_Q_BLOCKS : 3)); }
+#ifndef PGB_XRES_E3_BLOCKS
+#define PGB_XRES_E3_BLOCKS 2
+#endif
+constexpr int xres_min_blocks(int e, bool has_q) {
+  return e % 3 == 0 ? PGB_XRES_E3_BLOCKS : (e >= 16 ? 4 : (has_q ? PGB_XRES_Q_BLOCKS : 3));
+}
 template <int N, int E, bool HAS_Q, bool STAGE_P, bool ISO>
 __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
@@ -200,12 +205,12 @@ cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, in
     return cudaSuccess;
   const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
   if (stage_p) {
-    PGB_XS_E8_24_SWITCH(E, PGB_XS_N_SWITCH(N, {
+    PGB_XS_E8_E3_SWITCH(E, PGB_XS_N_SWITCH(N, {
       return xs_launch(k_xres_s<NN, EE, HAS_Q, true, ISO>, NN / EE, RB, c, ngroups, nblocks_out, st, used, R, spec, g,
                        tb.twx_f, tb.twr_f, done, err);
     }));
   } else {
-    PGB_XS_E8_24_SWITCH(E, PGB_XS_N_SWITCH(N, {
+    PGB_XS_E8_E3_SWITCH(E, PGB_XS_N_SWITCH(N, {
       return xs_launch(k_xres_s<NN, EE, HAS_Q, false, ISO>, NN / EE, RB, c, ngroups, nblocks_out, st, used, R, spec, g,
                        tb.twx_f, tb.twr_f, done, err);
     }));
@@ -219,7 +224,7 @@ cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, in
 cudaError_t launch_xres_static_iso(const ResidualArgs& R, void* spec, const Geom& g, const FftPlan& fx,
                                    const Tables& tb, const int* done, unsigned* err, int* nblocks_out,
                                    cudaStream_t st, bool* used) {
-  const int E = fx.n % 3 == 0 ? 24 : 8;
+  const int E = fx.n % 3 == 0 ? kE3 : 8;
   if (R.q) return xres_s<true, true>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
   return xres_s<false, true>(R, (float2*)spec, g, fx.n, E, tb, done, err, nblocks_out, st, used);
 }
@@ -232,7 +237,7 @@ cudaError_t launch_xres_static(const ResidualArgs& R, void* spec, const Geom& g,
                                const int* done, unsigned* err, int* nblocks_out, cudaStream_t st, bool* used) {
   *used = false;
   if (!xpass_static_supported(fx.n)) return cudaSuccess;
-  const int E = fx.n % 3 == 0 ? 24 : 8;   // the residual kernel: 8 elements per thread for powers of two
+  const int E = fx.n % 3 == 0 ? kE3 : 8;   // the residual kernel: 8 elements per thread for powers of two
   // dx == dy: the kernels with the merged horizontal term
   if (R.cx.x == R.cy.x && R.cx.y == R.cy.y)
     return launch_xres_static_iso(R, spec, g, fx, tb, done, err, nblocks_out, st, used);

@@ -37,7 +37,7 @@ size_t ys_smem(int N, int TK, bool inplace) {
   return (inplace ? 2 : 3) * ys_tile_bytes(N, TK) + (size_t)N * sizeof(float2) + 64;
 }
 
-constexpr int ys_max_threads(int E) { return E >= 16 ? 512 : 1024; }
+constexpr int ys_max_threads(int E) { return E >= 16 || E % 3 == 0 ? 512 : 1024; }
 
 template <int N, int E, int SIGN, bool INPLACE>
 __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant__ CUtensorMap tm, Geom g,
@@ -320,8 +320,8 @@ cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPla
   if (!ypass_static_supported(fy.n)) return cudaSuccess;
   int tk = tile > 0 ? tile : 8;   // 64-byte TMA box rows (measured best untuned at 1024^2 and on small domains)
   if (tk % 2) tk += 1;   // 16-byte inner TMA box
-  // 24 elements per thread when ny has a factor 3 (radix 3, then 8)
-  const int E = fy.n % 3 == 0 ? 24 : (fy.E == 16 ? 16 : 8);
+  // kE3 elements per thread when ny has a factor 3 (radix 3, then 4)
+  const int E = fy.n % 3 == 0 ? kE3 : (fy.E == 16 ? 16 : 8);
   if (variant == 2 && E == 16) {   // single-buffered, in place, two CTAs per SM (16 elements per thread)
     int tk1 = tk;
     while (tk1 > 2 && tk1 * (fy.n / E) > ys_max_threads(E)) tk1 >>= 1;
@@ -336,9 +336,9 @@ cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPla
 #define PGB_YS_CALL(EE, SG)                                                                   \
   return inplace ? ys_launch<EE, SG, true>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)    \
                  : ys_launch<EE, SG, false>(sp, g, fy.n, tb.twy_f, tk, done, err, st, used)
-  if (E == 24) {
-    if (sign < 0) PGB_YS_CALL(24, -1);
-    PGB_YS_CALL(24, +1);
+  if (E == kE3) {
+    if (sign < 0) PGB_YS_CALL(kE3, -1);
+    PGB_YS_CALL(kE3, +1);
   }
   if (E == 16) {
     if (sign < 0) PGB_YS_CALL(16, -1);
