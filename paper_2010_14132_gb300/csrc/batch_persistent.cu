@@ -445,6 +445,7 @@ __device__ void item_lowk(const BDom& D, int pass, int sub, unsigned char* sm) {
       const float2 v = __ldcg(D.spec + (long long)k * g.plane + (long long)ck.y * g.P + ck.x);
       zx[i] = (double)v.x;
       zy[i] = (double)v.y;
+      if (D.lowk_inv) w[i] = __ldg(D.lowk_inv + (size_t)(j0 + j) * nz + k);   // the column's pivot table
     }
   }
   __syncthreads();
@@ -453,7 +454,7 @@ __device__ void item_lowk(const BDom& D, int pass, int sub, unsigned char* sm) {
     const bool singular = D.singular00 && ck.x == 0 && ck.y == 0;
     lowk_recurrence<double, false>(zx + tid, zy + tid, w + tid, kBLowk, a, c, W, nz, ck.x, ck.y, singular, D.lamx_d,
                                    D.lamy_d, D.scale_d, target_mean, D.stats, red + 5 * tid, sq + tid,
-                                   D.lowk_inv ? D.lowk_inv + (size_t)(j0 + tid) * nz : nullptr);
+                                   D.lowk_inv != nullptr);
   }
   __syncthreads();
   for (int i = tid; i < nz * kBLowk; i += kBT) {

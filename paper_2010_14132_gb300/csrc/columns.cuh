@@ -66,13 +66,16 @@ __device__ __forceinline__ TCm lowk_pivot_step(int k, TCm s, TCm ak, TCm ck, TCm
 // back-substitution factors in w[k ld], the level tables a, c, W (stride 1).
 // red receives (shift_x, shift_y, sum W, sum x, sum y) for the caller's output
 // pass; sq_out (nullable, forward only) the sum of |x_k|^2 of the output.
+// tab: w[k ld] holds the column's pivot reciprocals 1/u_k on entry (staged by the caller from the
+// plan's table, in parallel): the chain then loads them from shared memory instead of forming
+// pivots, and the back substitution forms its factors from them (the same products as when they are
+// stored by the forward sweep, so both ways give the same bits).
 template <typename TCm, bool ADJ>
 __device__ __forceinline__ void lowk_recurrence(TCm* zx, TCm* zy, TCm* w, int ld, const TCm* a, const TCm* c,
                                                 const TCm* W, int nz, int kx, int ky, bool singular,
                                                 const double* __restrict__ lamx, const double* __restrict__ lamy,
                                                 double scale, const double* __restrict__ target_mean,
-                                                Stats* stats, TCm* red, double* sq_out,
-                                                const double* __restrict__ inv_col = nullptr) {
+                                                Stats* stats, TCm* red, double* sq_out, bool tab = false) {
   TCm mean_x = 0, mean_y = 0;
   if (singular) {
     TCm sw = 0;
@@ -92,11 +95,11 @@ __device__ __forceinline__ void lowk_recurrence(TCm* zx, TCm* zy, TCm* w, int ld
   TCm g_prev = s, inv_prev = 0, yx = 0, yy = 0;
   for (int k = 0; k < nz; ++k) {
     const TCm bx = ms * (zx[k * ld] - mean_x), by = ms * (zy[k * ld] - mean_y);
-    // the pivots depend on the column's wavenumbers and the levels only: read from the plan's table
-    // when it has them (no division on the chain), else computed here
-    const TCm inv = inv_col ? (TCm)__ldg(inv_col + k)
-                            : lowk_pivot_step<TCm>(k, s, (TCm)a[k], (TCm)c[k], g_prev, inv_prev,
-                                                   singular && (k == nz - 1));
+    // the pivots depend on the column's wavenumbers and the levels only: staged from the plan's
+    // table when it has them (no division on the chain), else computed here
+    const TCm inv = tab ? w[k * ld]
+                        : lowk_pivot_step<TCm>(k, s, (TCm)a[k], (TCm)c[k], g_prev, inv_prev,
+                                               singular && (k == nz - 1));
     if (!ADJ) {
       TCm nx_ = bx, ny_ = by;
       if (k > 0) {
@@ -108,7 +111,7 @@ __device__ __forceinline__ void lowk_recurrence(TCm* zx, TCm* zy, TCm* w, int ld
       yy = ny_;
       zx[k * ld] = yx * inv;
       zy[k * ld] = yy * inv;
-      w[k * ld] = (TCm)c[k] * inv;
+      if (!tab) w[k * ld] = (TCm)c[k] * inv;
     } else {
       TCm nx_ = bx, ny_ = by;
       if (k > 0) {
@@ -119,15 +122,16 @@ __device__ __forceinline__ void lowk_recurrence(TCm* zx, TCm* zy, TCm* w, int ld
       yy = ny_ * inv;
       zx[k * ld] = yx;
       zy[k * ld] = yy;
-      w[k * ld] = (k + 1 < nz) ? (TCm)a[k + 1] * inv : (TCm)0;
+      if (!tab) w[k * ld] = (k + 1 < nz) ? (TCm)a[k + 1] * inv : (TCm)0;
     }
     inv_prev = inv;
   }
   TCm xx = zx[(nz - 1) * ld], xy = zy[(nz - 1) * ld];
   TCm sx = xx, sy = xy;
   for (int k = nz - 2; k >= 0; --k) {
-    xx = zx[k * ld] + w[k * ld] * xx;
-    xy = zy[k * ld] + w[k * ld] * xy;
+    const TCm wk = !tab ? w[k * ld] : (ADJ ? (TCm)a[k + 1] * w[k * ld] : (TCm)c[k] * w[k * ld]);
+    xx = zx[k * ld] + wk * xx;
+    xy = zy[k * ld] + wk * xy;
     zx[k * ld] = xx;
     zy[k * ld] = xy;
     sx += xx;
@@ -160,10 +164,171 @@ __device__ __forceinline__ void lowk_recurrence(TCm* zx, TCm* zy, TCm* w, int ld
   }
 }
 
-// One low-|k| or singular column, solved by the whole block: the strided loads
-// and stores of the column and the coefficient tables go through shared memory
-// in parallel; thread 0 runs the sequential recurrence out of shared memory.
-// sq_out (nullable): thread 0 stores the solution's sum of |x_k|^2 over the levels (forward solve).
+// Shared memory (in units of the compute type) of one low-|k| column solved by a block.
+__host__ __device__ constexpr size_t lowk_smem_elems(int nz) { return 6 * (size_t)nz + 96; }
+
+// Fixed-order sum of three values over the block (every thread gets the result): each thread's
+// values, then a shuffle tree in each warp, then the warps in order.  scratch: 3 doubles per warp.
+__device__ __forceinline__ double3 lowk_block_sum3(double v0, double v1, double v2, double* scratch) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, o);
+    v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    v2 += __shfl_down_sync(0xffffffffu, v2, o);
+  }
+  const int wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();   // scratch may still be read from an earlier sum
+  if ((threadIdx.x & 31) == 0) {
+    scratch[3 * wid] = v0;
+    scratch[3 * wid + 1] = v1;
+    scratch[3 * wid + 2] = v2;
+  }
+  __syncthreads();
+  double3 r = make_double3(0.0, 0.0, 0.0);
+  for (int w = 0; w < nw; ++w) {
+    r.x += scratch[3 * w];
+    r.y += scratch[3 * w + 1];
+    r.z += scratch[3 * w + 2];
+  }
+  return r;
+}
+
+// One low-|k| or singular column in double precision from the plan's pivot table (inv_col: 1/u_k,
+// 0 for the pinned singular top), solved by the whole block (at most 1024 threads).  The FP64 units
+// issue a warp's instruction at the same cost however few of its lanes are active, so the serial
+// part is kept to the two recurrences alone: the real parts run on lane 0 and the imaginary parts on
+// lane 1 of the first warp (one double FMA instruction per level and sweep), and everything that
+// does not depend on the previous level (the scaled right-hand side, the elimination and
+// back-substitution factors, the means and sums) runs across the block.
+//   forward  (M x = b):   y_k = b_k + (a_k/u_{k-1}) y_{k-1},  z_k = y_k/u_k,  x_k = z_k + (c_k/u_k) x_{k+1}
+//   adjoint (M^T x = b):  v_k = (b_k + c_{k-1} v_{k-1})/u_k,                  x_k = v_k + (a_{k+1}/u_k) x_{k+1}
+template <typename TS, bool ADJ>
+__device__ __forceinline__ void lowk_column_tab(unsigned char* smraw, typename CT<TS>::t* __restrict__ spec,
+                                                const Geom& g, const double* __restrict__ ag,
+                                                const double* __restrict__ cg, const double* __restrict__ Wg,
+                                                const double* __restrict__ lamx, const double* __restrict__ lamy,
+                                                double scale, int2 colk, Stats* stats,
+                                                const double* __restrict__ target_mean, bool singular00,
+                                                double* sq_out, const double* __restrict__ inv_col) {
+  using CS = typename CT<TS>::t;
+  const int nz = g.nz, t = threadIdx.x, nt = blockDim.x;
+  double* z = reinterpret_cast<double*>(smraw);   // [2][nz]: real parts, imaginary parts
+  double* inv = z + 2 * nz;                        // 1/u_k, then the back-substitution factors
+  double* F = inv + nz;                            // forward factors
+  double* scratch = F + nz;                        // [3 per warp]
+  const int kx = colk.x, ky = colk.y;
+  const bool singular = singular00 && kx == 0 && ky == 0;   // nonsingular with p = 0 on the top face
+  CS* colp = spec + (long long)ky * g.P + kx;
+  // the column is read at L2 (not through L1), so that a persistent kernel that produced it earlier
+  // in the same launch on another SM is seen
+  double mx = 0.0, my = 0.0, sw = 0.0;
+  for (int k = t; k < nz; k += nt) {
+    const CS v = __ldcg(&colp[(long long)k * g.plane]);
+    z[k] = (double)v.x;
+    z[nz + k] = (double)v.y;
+    inv[k] = __ldg(inv_col + k);
+    if (singular) {   // compatibility: the W-weighted (adjoint: plain) mean of the right-hand side
+      const double wk = ADJ ? 1.0 : __ldg(Wg + k);
+      mx += wk * (double)v.x;
+      my += wk * (double)v.y;
+      sw += wk;
+    }
+  }
+  double mean_x = 0.0, mean_y = 0.0;
+  if (singular) {
+    const double3 m = lowk_block_sum3(mx, my, sw, scratch);
+    mean_x = m.x / m.z;
+    mean_y = m.y / m.z;
+    // only the first solve records mu_W (a refinement correction solve has a target mean)
+    if (!ADJ && t == 0 && stats && !target_mean) stats->mu_w = mean_x * scale;
+  }
+  __syncthreads();
+  const double ms = -scale;
+  for (int k = t; k < nz; k += nt) {
+    z[k] = ms * (z[k] - mean_x);
+    z[nz + k] = ms * (z[nz + k] - mean_y);
+    F[k] = k == 0 ? 0.0 : (ADJ ? __ldg(cg + k - 1) : __ldg(ag + k) * inv[k - 1]);
+  }
+  __syncthreads();
+  if (t < 2) {   // forward elimination: lane 0 the real parts, lane 1 the imaginary parts
+    double* zp = z + t * nz;
+    double y = ADJ ? zp[0] * inv[0] : zp[0];
+    zp[0] = y;
+    for (int k = 1; k < nz; ++k) {
+      y = fma(F[k], y, zp[k]);
+      if (ADJ) y *= inv[k];
+      zp[k] = y;
+    }
+  }
+  __syncthreads();
+  for (int k = t; k < nz; k += nt) {
+    const double u = inv[k];
+    if (!ADJ) {
+      z[k] *= u;
+      z[nz + k] *= u;
+      inv[k] = __ldg(cg + k) * u;
+    } else {
+      inv[k] = k + 1 < nz ? __ldg(ag + k + 1) * u : 0.0;
+    }
+  }
+  __syncthreads();
+  if (t < 2) {   // back substitution
+    double* zp = z + t * nz;
+    double x = zp[nz - 1];
+    for (int k = nz - 2; k >= 0; --k) {
+      x = fma(inv[k], x, zp[k]);
+      zp[k] = x;
+    }
+  }
+  __syncthreads();
+  double shx = 0.0, shy = 0.0, fx = 0.0, fy = 0.0;
+  if (singular) {
+    double sx = 0.0, sy = 0.0, swt = 0.0;
+    for (int k = t; k < nz; k += nt) {
+      sx += z[k];
+      sy += z[nz + k];
+      if (ADJ) swt += __ldg(Wg + k);
+    }
+    const double3 r = lowk_block_sum3(sx, sy, swt, scratch);
+    if (!ADJ) {
+      shx = r.x / (double)nz;
+      shy = r.y / (double)nz;
+      // refinement sweep: the correction also removes the mean of the current iterate
+      if (target_mean) shx += __ldcg(target_mean);
+    } else {   // remove the W direction (the null vector of the transposed column)
+      fx = r.x / r.z;
+      fy = r.y / r.z;
+    }
+  }
+  double sq = 0.0;
+  for (int k = t; k < nz; k += nt) {
+    double ox = z[k], oy = z[nz + k];
+    if (singular) {
+      if (!ADJ) {
+        ox -= shx;
+        oy -= shy;
+      } else {
+        const double wk = __ldg(Wg + k);
+        ox -= wk * fx;
+        oy -= wk * fy;
+      }
+    }
+    if (!ADJ && sq_out) sq += ox * ox + oy * oy;
+    CS o;
+    o.x = (TS)ox;
+    o.y = (TS)oy;
+    colp[(long long)k * g.plane] = o;
+  }
+  if (!ADJ && sq_out) {
+    const double3 r = lowk_block_sum3(sq, 0.0, 0.0, scratch);
+    if (t == 0) *sq_out = r.x;
+  }
+}
+
+// One low-|k| or singular column, solved by the whole block.  With the plan's pivot table (double
+// columns) this is lowk_column_tab; otherwise the strided loads and stores of the column and the
+// coefficient tables go through shared memory in parallel and thread 0 runs the sequential
+// recurrence out of shared memory.  sq_out (nullable): the solution's sum of |x_k|^2 over the
+// levels (forward solve), stored by thread 0.  Shared memory: lowk_smem_elems(nz) of TCm.
 template <typename TS, typename TCm, bool ADJ>
 __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS>::t* __restrict__ spec,
                                             const Geom& g, const double* __restrict__ ag,
@@ -185,6 +350,11 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
   const int kx = colk.x, ky = colk.y;
   const bool singular = singular00 && kx == 0 && ky == 0;   // nonsingular with p = 0 on the top face
   CS* colp = spec + (long long)ky * g.P + kx;
+  if (inv_tab && sizeof(TCm) == 8) {   // the plan's pivot table holds double pivots
+    lowk_column_tab<TS, ADJ>(smraw, spec, g, ag, cg, Wg, lamx, lamy, scale, colk, stats, target_mean, singular00,
+                             sq_out, inv_tab + (size_t)col_index * nz);
+    return;
+  }
   // the column and the target mean are read at L2 (not through L1), so a persistent kernel that
   // produced them earlier in the same launch on another SM is seen
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
@@ -198,8 +368,7 @@ __device__ __forceinline__ void lowk_column(unsigned char* smraw, typename CT<TS
   __syncthreads();
   if (threadIdx.x == 0)
     lowk_recurrence<TCm, ADJ>(zx, zy, w, 1, a, c, W, nz, kx, ky, singular, lamx, lamy, scale, target_mean, stats,
-                              red, sq_out,
-                              (inv_tab && sizeof(TCm) == 8) ? inv_tab + (size_t)col_index * nz : nullptr);
+                              red, sq_out);
   __syncthreads();
   const TCm shift_x = red[0], shift_y = red[1], sumw = red[2], sum_x = red[3], sum_y = red[4];
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {

@@ -83,7 +83,7 @@ __host__ __device__ constexpr size_t mid_buf_offset(int N, int nz) {
 __host__ __device__ constexpr size_t mid_buf_bytes(int N, int nz, int TC, size_t lowk_elem) {
   const size_t y = (size_t)N * kMidTK * 8;
   const size_t c = (size_t)nz * TC * 12 + (size_t)TC * 24;
-  const size_t l = (6 * (size_t)nz + 8) * lowk_elem;
+  const size_t l = lowk_smem_elems(nz) * lowk_elem;
   return y > c ? (y > l ? y : l) : (c > l ? c : l);
 }
 

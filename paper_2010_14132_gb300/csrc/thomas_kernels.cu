@@ -389,7 +389,7 @@ static cudaError_t thomas_pair_launch(const ThomasArgs& A, const Geom& g, const 
   }
   size_t smem = 2 * (size_t)g.nz * tc * sizeof(float2) + (((size_t)g.nz * tc * sizeof(float) + 15) & ~(size_t)15) +
                 ((size_t)g.nz + 1) * sizeof(float2) + 16;
-  const size_t lowk_smem = (6 * (size_t)g.nz + 8) * sizeof(TCm);
+  const size_t lowk_smem = lowk_smem_elems(g.nz) * sizeof(TCm);
   if (smem < lowk_smem) smem = lowk_smem;
   int box_rows = 1;
   for (int d = 256; d >= 1; --d)
@@ -424,7 +424,7 @@ static cudaError_t thomas_tw_launch(const ThomasArgs& A, const Geom& g, const Ta
   *used = false;
   size_t smem = (((size_t)g.nz * tc * (sizeof(float2) + sizeof(float)) + 15) & ~(size_t)15) +
                 ((size_t)g.nz + 1) * sizeof(float2) + (size_t)tc * (sizeof(float4) + sizeof(float2)) + 16;
-  const size_t lowk_smem = (6 * (size_t)g.nz + 8) * sizeof(TCm);
+  const size_t lowk_smem = lowk_smem_elems(g.nz) * sizeof(TCm);
   if (smem < lowk_smem) smem = lowk_smem;
   if (smem > 200 * 1024) return cudaSuccess;
   int box_rows = 1;
@@ -474,7 +474,7 @@ static cudaError_t thomas_launch(const ThomasArgs& A, const Geom& g, const Table
   const int tc = thomas_tile(g.nz, sizeof(C) + sizeof(T), A.col_tile);
   if (tc == 0) return cudaErrorInvalidValue;
   size_t smem = (((size_t)g.nz * tc * (sizeof(C) + sizeof(T)) + 15) & ~(size_t)15) + 16;
-  const size_t lowk_smem = (6 * (size_t)g.nz + 8) * sizeof(TCm);
+  const size_t lowk_smem = lowk_smem_elems(g.nz) * sizeof(TCm);
   if (smem < lowk_smem) smem = lowk_smem;
   const long long nb = (g.plane + tc - 1) / tc;
   auto kern = k_thomas<T, TCm, ADJ>;
