@@ -341,8 +341,8 @@ int poisson_batch_workspace_bytes(const poisson_batch* batch, size_t* bytes);
  * domain's solve and refinement (Sections 2.1 and 2.2), per-domain dependency
  * counters with bounded device waits (POISSON_ERR_TIMEOUT when one runs out).
  * Other batches capture the launch sequences of all domains into one CUDA graph
- * of concurrent branches (domains largest first, each to the least-loaded of 8
- * branches).  Either way the first call captures a CUDA graph bound to the given
+ * of concurrent branches (domains largest first, each to the least-loaded branch;
+ * POISSON_BATCH_OPT_BRANCHES).  Either way the first call captures a CUDA graph bound to the given
  * pointers and workspace; later calls with the same pointers, workspace and
  * options replay it with a single graph launch, anything else re-captures.  The
  * persistent kernel ignores the plans' kernel-shape options (it has its own tile
@@ -360,10 +360,11 @@ int poisson_batch_plan(poisson_batch* batch, int i, poisson_plan** plan);
 typedef enum {
   POISSON_BATCH_OPT_PERSISTENT = 0,  /* 1 (default): the persistent kernel where the shapes allow; 0: the
                                         graph of per-domain launches */
-  POISSON_BATCH_OPT_STALL_TEST = 1   /* test hook, -1 (default) off: with the persistent kernel, the first
+  POISSON_BATCH_OPT_STALL_TEST = 1,  /* test hook, -1 (default) off: with the persistent kernel, the first
                                         control item of this domain waits for a work count that never
                                         arrives, so its bounded wait runs out (a few seconds) and the
                                         solve returns POISSON_ERR_TIMEOUT; no fault, no endless wait */
+  POISSON_BATCH_OPT_BRANCHES = 2     /* graph of per-domain launches: concurrent branches, 1..32 (default 24) */
 } poisson_batch_option;
 int poisson_batch_set_option(poisson_batch* batch, int option, double value);
 

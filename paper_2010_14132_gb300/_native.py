@@ -36,6 +36,7 @@ POISSON_OPT_RESIDUAL_PASS = 13
 POISSON_OPT_VERIFY = 14
 POISSON_BATCH_OPT_PERSISTENT = 0
 POISSON_BATCH_OPT_STALL_TEST = 1
+POISSON_BATCH_OPT_BRANCHES = 2
 POISSON_LAYOUT_Z_Y_X = 0
 POISSON_LAYOUT_X_Y_Z = 1
 PHASES = ("xfwd", "yfwd", "columns", "yinv", "xinv", "residual", "control", "spectral")

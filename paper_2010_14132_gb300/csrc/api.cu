@@ -109,15 +109,15 @@ struct poisson_plan {
 };
 
 struct poisson_batch {
-  static constexpr int kBranches = 8;   // concurrent graph branches
+  static constexpr int kMaxBranches = 32;   // concurrent graph branches (POISSON_BATCH_OPT_BRANCHES)
   int n = 0;
   int dtype = 0;
   std::vector<poisson_plan*> plans;
   std::vector<size_t> off;
   size_t ws_bytes = 0;
   cudaStream_t cap = nullptr;
-  cudaStream_t branch[kBranches] = {};
-  cudaEvent_t fork = nullptr, join[kBranches] = {};
+  cudaStream_t branch[kMaxBranches] = {};
+  cudaEvent_t fork = nullptr, join[kMaxBranches] = {};
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> capS;
   std::vector<void*> capP;
@@ -125,6 +125,7 @@ struct poisson_batch {
   void* capW = nullptr;
   int persistent = 1;           // POISSON_BATCH_OPT_PERSISTENT
   int stall_test = -1;          // POISSON_BATCH_OPT_STALL_TEST
+  int branches = 24;            // POISSON_BATCH_OPT_BRANCHES
   BatchPersistent bp;           // descriptors and item list of the persistent kernel (when it is used)
 };
 
@@ -1190,7 +1191,7 @@ int poisson_batch_destroy(poisson_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   batch_persistent_free(&b->bp);
   if (b->cap) cudaStreamDestroy(b->cap);
-  for (int k = 0; k < poisson_batch::kBranches; ++k) {
+  for (int k = 0; k < poisson_batch::kMaxBranches; ++k) {
     if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
     if (b->join[k]) cudaEventDestroy(b->join[k]);
   }
@@ -1226,7 +1227,7 @@ int poisson_batch_create(int n, const int* nx, const int* ny, const int* nz, con
   b->ws_bytes = off;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-  for (int k = 0; k < poisson_batch::kBranches && e == cudaSuccess; ++k) {
+  for (int k = 0; k < poisson_batch::kMaxBranches && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
   }
@@ -1296,6 +1297,10 @@ int poisson_batch_set_option(poisson_batch* b, int option, double value) {
   } else if (option == POISSON_BATCH_OPT_STALL_TEST) {
     if (value != std::floor(value) || value < -1.0 || value >= (double)b->n) return POISSON_ERR_INVALID_ARG;
     b->stall_test = (int)value;
+  } else if (option == POISSON_BATCH_OPT_BRANCHES) {
+    if (value != std::floor(value) || value < 1.0 || value > (double)poisson_batch::kMaxBranches)
+      return POISSON_ERR_INVALID_ARG;
+    b->branches = (int)value;
   } else {
     return POISSON_ERR_INVALID_ARG;
   }
@@ -1364,12 +1369,13 @@ int poisson_batch_solve(poisson_batch* b, const void* const* S, void* const* p, 
   }
   if (!same && !b->exec) {
     batch_persistent_free(&b->bp);
-    // domains largest first, each to the least-loaded of the concurrent branches
+    // domains largest first, each to the least-loaded of the concurrent branches; a domain's load is its
+    // points plus a fixed 2M for the latency-bound part of its launch chain (about 0.1 ms of a branch)
     std::vector<int> order(b->n);
     for (int i = 0; i < b->n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return b->plans[x]->g.N > b->plans[y]->g.N; });
-    const int nbr = b->n < poisson_batch::kBranches ? b->n : poisson_batch::kBranches;
+    const int nbr = b->n < b->branches ? b->n : b->branches;
     std::vector<long long> load(nbr, 0);
     std::vector<int> branch_of(b->n, 0);
     for (int i : order) {
@@ -1377,7 +1383,7 @@ int poisson_batch_solve(poisson_batch* b, const void* const* S, void* const* p, 
       for (int k = 1; k < nbr; ++k)
         if (load[k] < load[best]) best = k;
       branch_of[i] = best;
-      load[best] += b->plans[i]->g.N;
+      load[best] += b->plans[i]->g.N + (1ll << 21);
     }
     PGB_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
     int rc = POISSON_OK;

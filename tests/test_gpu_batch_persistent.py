@@ -10,6 +10,7 @@ a (domain, phase, tile) work list with per-domain dependency counters.
   fields equal to rounding (the two forms share every kernel's arithmetic; only the
   order of the norm sums differs).
 * Replays are bit-identical (fixed-order sums, whatever CTA runs an item).
+* The graph form gives the same bits whatever its number of concurrent branches.
 * Bounded waits: the test hook makes one domain's first control item wait for a
   work count that never arrives; the wait runs out, the solve reports
   POISSON_ERR_TIMEOUT without a fault, and the next solve on the same context is
@@ -92,10 +93,24 @@ def test_timeout_is_reported_and_the_context_stays_usable(mixed_shapes):
         assert O.relative_l2(p.cpu().numpy(), ref) <= 1e-10, d.name
 
 
+def test_branch_count_leaves_the_graph_form_bitwise_unchanged(mixed_shapes):
+    doms, _ = mixed_shapes
+    S = _sources(doms)
+    b = Batch(doms, dtype="mixed", persistent=False)
+    ref = [p.clone() for p in b.solve(S)]
+    for nb in (1, 5, 32):
+        b.set_option(N.POISSON_BATCH_OPT_BRANCHES, nb)
+        outs = b.solve(S)
+        torch.cuda.synchronize()
+        for d, a, r in zip(doms, outs, ref):
+            assert torch.equal(a, r), (nb, d.name)
+
+
 def test_batch_options_are_checked():
     doms = [wl.anelastic_noise(64, 64, 4, seed=1)]
     b = Batch(doms, dtype="mixed")
     for opt, val in ((N.POISSON_BATCH_OPT_PERSISTENT, 2), (N.POISSON_BATCH_OPT_STALL_TEST, 1),
-                     (N.POISSON_BATCH_OPT_STALL_TEST, 0.5), (7, 0)):
+                     (N.POISSON_BATCH_OPT_STALL_TEST, 0.5), (N.POISSON_BATCH_OPT_BRANCHES, 0),
+                     (N.POISSON_BATCH_OPT_BRANCHES, 33), (N.POISSON_BATCH_OPT_BRANCHES, 2.5), (7, 0)):
         with pytest.raises(N.PoissonError):
             b.set_option(opt, val)

@@ -98,3 +98,13 @@ def test_cg_entry_points_reject_null_arguments():
     st = lib.poisson_cg_solve(None, None, None, None, 1e-10, 10, None, None, C.byref(info))
     assert st == N.POISSON_ERR_INVALID_ARG
     assert info.iterations == 0 and info.converged == 0   # cleared before any check
+
+
+def test_header_enum_values_match_the_binding():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    values = dict((k, int(v)) for k, v in re.findall(r"\b(POISSON_[A-Z0-9_]+)\s*=\s*(-?\d+)", text))
+    named = {k: v for k, v in values.items() if hasattr(N, k)}
+    assert len(named) >= 20
+    for k, v in named.items():
+        assert getattr(N, k) == v, k
+    assert N.POISSON_BATCH_OPT_BRANCHES == values["POISSON_BATCH_OPT_BRANCHES"]
