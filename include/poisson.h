@@ -335,14 +335,14 @@ int poisson_batch_create(int n, const int* nx, const int* ny, const int* nz, con
                          int dtype, poisson_batch** out);
 int poisson_batch_workspace_bytes(const poisson_batch* batch, size_t* bytes);
 /* S[b], p[b]: device fields of domain b.  info: nullable array of n structs.
- * Mixed batches whose every domain has nx and ny in {64, 128, 256, 384, 512} and
- * 2 <= nz <= 128 run as ONE persistent kernel (POISSON_BATCH_OPT_PERSISTENT, default
- * on): a work list of (domain, phase, tile) items covering every step of every
- * domain's solve and refinement (Sections 2.1 and 2.2), per-domain dependency
- * counters with bounded device waits (POISSON_ERR_TIMEOUT when one runs out).
- * Other batches capture the launch sequences of all domains into one CUDA graph
+ * By default the launch sequences of all domains are captured into one CUDA graph
  * of concurrent branches (domains largest first, each to the least-loaded branch;
- * POISSON_BATCH_OPT_BRANCHES).  Either way the first call captures a CUDA graph bound to the given
+ * POISSON_BATCH_OPT_BRANCHES).  With POISSON_BATCH_OPT_PERSISTENT = 1, mixed batches
+ * whose every domain has nx and ny in {64, 128, 256, 384, 512} and 2 <= nz <= 128 run
+ * as ONE persistent kernel instead: a work list of (domain, phase, tile) items
+ * covering every step of every domain's solve and refinement (Sections 2.1 and 2.2),
+ * per-domain dependency counters with bounded device waits (POISSON_ERR_TIMEOUT when
+ * one runs out).  Either way the first call captures a CUDA graph bound to the given
  * pointers and workspace; later calls with the same pointers, workspace and
  * options replay it with a single graph launch, anything else re-captures.  The
  * persistent kernel ignores the plans' kernel-shape options (it has its own tile
@@ -358,8 +358,8 @@ int poisson_batch_plan(poisson_batch* batch, int i, poisson_plan** plan);
 /* Batch options (the next solve re-captures; query poisson_batch_workspace_bytes again after a
  * change).  POISSON_ERR_INVALID_ARG for an unknown option or value. */
 typedef enum {
-  POISSON_BATCH_OPT_PERSISTENT = 0,  /* 1 (default): the persistent kernel where the shapes allow; 0: the
-                                        graph of per-domain launches */
+  POISSON_BATCH_OPT_PERSISTENT = 0,  /* 0 (default): the graph of per-domain launches; 1: the persistent
+                                        kernel where the shapes allow */
   POISSON_BATCH_OPT_STALL_TEST = 1,  /* test hook, -1 (default) off: with the persistent kernel, the first
                                         control item of this domain waits for a work count that never
                                         arrives, so its bounded wait runs out (a few seconds) and the

@@ -123,7 +123,7 @@ struct poisson_batch {
   std::vector<void*> capP;
   std::vector<unsigned> capV;   // plan versions at capture
   void* capW = nullptr;
-  int persistent = 1;           // POISSON_BATCH_OPT_PERSISTENT
+  int persistent = 0;           // POISSON_BATCH_OPT_PERSISTENT
   int stall_test = -1;          // POISSON_BATCH_OPT_STALL_TEST
   int branches = 24;            // POISSON_BATCH_OPT_BRANCHES
   BatchPersistent bp;           // descriptors and item list of the persistent kernel (when it is used)

@@ -239,15 +239,15 @@ def poisson_solve(S: torch.Tensor, plan: Plan, rho0: torch.Tensor | None = None)
 class Batch:
     """Many independent domains of uneven sizes, solved by one CUDA-graph launch.
 
-    Mixed batches of supported shapes (nx, ny in {64, 128, 256, 384, 512}, nz <= 128)
-    run as one persistent kernel over a (domain, phase, tile) work list
-    (``persistent=True``, the default); otherwise the graph runs the domains'
-    launch sequences on concurrent branches.  With ``tune=True`` every distinct grid
+    The graph runs the domains' launch sequences on concurrent branches (the
+    default); with ``persistent=True``, mixed batches of supported shapes (nx, ny in
+    {64, 128, 256, 384, 512}, nz <= 128) run as one persistent kernel over a
+    (domain, phase, tile) work list instead.  With ``tune=True`` every distinct grid
     shape gets the autotuner's kernel shapes (measured once per GPU, shape and
     dtype, then cached), applied to the domains' plans (the graph form uses them).
     """
 
-    def __init__(self, domains, dtype="mixed", device=None, tune=False, persistent=True):
+    def __init__(self, domains, dtype="mixed", device=None, tune=False, persistent=False):
         if dtype not in ("fp32", "mixed"):
             raise ValueError("batched solves support dtype 'fp32' or 'mixed'")
         self.dtype = dtype

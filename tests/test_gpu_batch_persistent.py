@@ -46,7 +46,7 @@ def _sources(doms):
 
 def test_every_shape_against_the_oracle(mixed_shapes):
     doms, refs = mixed_shapes
-    b = Batch(doms, dtype="mixed")
+    b = Batch(doms, dtype="mixed", persistent=True)
     outs, infos = b.solve(_sources(doms), info=True)
     torch.cuda.synchronize()
     for d, p, ref, info in zip(doms, outs, refs, infos):
@@ -79,7 +79,7 @@ def test_persistent_equals_graph_of_launches(mixed_shapes):
 def test_timeout_is_reported_and_the_context_stays_usable(mixed_shapes):
     doms, refs = mixed_shapes
     doms, refs = doms[:4], refs[:4]
-    b = Batch(doms, dtype="mixed")
+    b = Batch(doms, dtype="mixed", persistent=True)
     S = _sources(doms)
     b.set_option(N.POISSON_BATCH_OPT_STALL_TEST, 1)
     with pytest.raises(N.PoissonError) as ei:
