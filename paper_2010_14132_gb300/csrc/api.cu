@@ -81,6 +81,9 @@ struct poisson_plan {
   int lowk_r2 = 64, max_sweeps = 3, ytile = 0, ykernel = 4, xkernel = 0, xelems = 8, yelems = 16, lchunk = 0,
       coltile = 0, fused = 0, respass = 0, verify = 1;
   unsigned version = 0;   // bumped by every option change (invalidates captured batch graphs)
+  // Set by a batch while it captures its graph: the stream into which each later refinement sweep is
+  // captured as the body of a graph IF node (run only while the solve is not done); null otherwise.
+  cudaStream_t cond_body = nullptr;
   double tol = 1e-10;
   Geom g{};
   Tables tb{};
@@ -116,6 +119,7 @@ struct poisson_batch {
   std::vector<size_t> off;
   size_t ws_bytes = 0;
   cudaStream_t cap = nullptr;
+  cudaStream_t body = nullptr;   // captures the domains' conditional sweep bodies (one at a time)
   cudaStream_t branch[kMaxBranches] = {};
   cudaEvent_t fork = nullptr, join[kMaxBranches] = {};
   cudaGraphExec_t exec = nullptr;
@@ -817,6 +821,42 @@ static cudaError_t from_solver_layout(const poisson_plan* pl, const void* src, v
   return launch_swap_outer_inner(src, dst, pl->nz, pl->ny, pl->nx, (int)pl->elem(), st);
 }
 
+// Capture of a refinement sweep as the body of a graph IF node (the capturing stream st gets a node
+// that sets the condition from the device's done flag, then the IF node; the body is captured from the
+// body stream until cond_end).  A certified solve then skips the sweep's kernels instead of launching
+// them to return at once.
+static cudaError_t cond_begin(cudaStream_t st, cudaStream_t body, const int* done) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = launch_set_if_not_done(h, done, st);
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, &edges, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, graph, deps, edges, nd, &np);
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(body, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+  return e;
+}
+static cudaError_t cond_end(cudaStream_t body) {
+  cudaGraph_t g = nullptr;   // the IF node's body graph (owned by the node)
+  return cudaStreamEndCapture(body, &g);
+}
+
 // The solve on fields in the solver's layout.
 static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cudaStream_t st) {
   Stats* stats = (Stats*)(ws + pl->off_stats);
@@ -860,12 +900,6 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
     // first rebuilds q from the double iterate of the second.
     double* rpart = (double*)(ws + pl->off_rpart);
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
-      if (sweep > 2) {
-        const int ps = prof_begin(pl, POISSON_PHASE_RESIDUAL, st);
-        const cudaError_t eq = launch_q_rebuild((const double*)p, p0, q, pl->g.N, done, st);
-        prof_end(pl, ps, st);
-        PGB_CUDA(eq);
-      }
       // residual computed inside the forward x-pass (its rows are never stored)
       ResidualArgs R{};
       R.partials = rpart;
@@ -903,37 +937,58 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
           PGB_CUDA(e);
         }
       }
-      double* sqn = (pl->verify && sweep >= 2) ? (double*)(ws + pl->off_sqn) : nullptr;
-      R.p_out = (sqn && sweep == 2) ? (double*)p : nullptr;
-      bool stored = false;
-      PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &R, &nres, sweep, &mid, sqn, &nsq,
-                               &stored));
-      if (sqn && nsq > 0) {
-        const int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-        e = launch_verify(stats, sqn, nsq, rpart, nres, sweep, pl->tol, pl->tb.floor_d, (double)pl->nx * pl->ny,
-                          stored ? 1 : 0, 0.0, st);
-        prof_end(pl, ps, st);
-        PGB_CUDA(e);
-      }
-      const bool last_allowed = sweep == pl->max_sweeps;
-      XinvExtra eu = ex;
-      eu.p0 = p0;
-      eu.q = q;
-      eu.q_valid = sweep > 1;
-      eu.q_out = (sweep == 1 && !last_allowed) ? q : nullptr;
-      eu.p_out = (sweep == 1 && !last_allowed) ? nullptr : (double*)p;
-      eu.done = done;
-      eu.ctl_pass = sweep;
-      eu.res_partials = rpart;
-      eu.res_nblocks = nres;
-      PGB_CUDA(inverse(pl, ws, st, done, 0, XINV_UPDATE, nullptr, eu, &nb, &fused, mid));
-      if (!fused) {
-        int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
-        e = launch_control(stats, ex.partials, nb, rpart, nres, sweep, pl->max_sweeps, pl->tol, pl->tb.floor_d,
-                           pl->g.N,
-                           eu.p_out != nullptr, st);
-        prof_end(pl, ps, st);
-        PGB_CUDA(e);
+      // From sweep 2 on, inside a batch's graph capture, the sweep is the body of an IF node on the done
+      // flag; elsewhere its kernels read the flag and return at once when the solve is already done.
+      const bool cond = sweep >= 2 && pl->cond_body != nullptr;
+      if (cond) PGB_CUDA(cond_begin(st, pl->cond_body, done));
+      cudaStream_t ss = cond ? pl->cond_body : st;
+      auto run_sweep = [&]() -> int {
+        if (sweep > 2) {
+          const int ps = prof_begin(pl, POISSON_PHASE_RESIDUAL, ss);
+          const cudaError_t eq = launch_q_rebuild((const double*)p, p0, q, pl->g.N, done, ss);
+          prof_end(pl, ps, ss);
+          PGB_CUDA(eq);
+        }
+        double* sqn = (pl->verify && sweep >= 2) ? (double*)(ws + pl->off_sqn) : nullptr;
+        R.p_out = (sqn && sweep == 2) ? (double*)p : nullptr;
+        bool stored = false;
+        PGB_CUDA(forward_columns(pl, nullptr, 0, ws, ss, 0, done, &stats->pmean, &R, &nres, sweep, &mid, sqn, &nsq,
+                                 &stored));
+        if (sqn && nsq > 0) {
+          const int ps = prof_begin(pl, POISSON_PHASE_CONTROL, ss);
+          e = launch_verify(stats, sqn, nsq, rpart, nres, sweep, pl->tol, pl->tb.floor_d, (double)pl->nx * pl->ny,
+                            stored ? 1 : 0, 0.0, ss);
+          prof_end(pl, ps, ss);
+          PGB_CUDA(e);
+        }
+        const bool last_allowed = sweep == pl->max_sweeps;
+        XinvExtra eu = ex;
+        eu.p0 = p0;
+        eu.q = q;
+        eu.q_valid = sweep > 1;
+        eu.q_out = (sweep == 1 && !last_allowed) ? q : nullptr;
+        eu.p_out = (sweep == 1 && !last_allowed) ? nullptr : (double*)p;
+        eu.done = done;
+        eu.ctl_pass = sweep;
+        eu.res_partials = rpart;
+        eu.res_nblocks = nres;
+        PGB_CUDA(inverse(pl, ws, ss, done, 0, XINV_UPDATE, nullptr, eu, &nb, &fused, mid));
+        if (!fused) {
+          int ps = prof_begin(pl, POISSON_PHASE_CONTROL, ss);
+          e = launch_control(stats, ex.partials, nb, rpart, nres, sweep, pl->max_sweeps, pl->tol, pl->tb.floor_d,
+                             pl->g.N, eu.p_out != nullptr, ss);
+          prof_end(pl, ps, ss);
+          PGB_CUDA(e);
+        }
+        return POISSON_OK;
+      };
+      const int rc_sweep = run_sweep();
+      if (cond) {   // end the body's capture even after an error, so that the stream is usable again
+        const cudaError_t ce = cond_end(pl->cond_body);
+        if (rc_sweep != POISSON_OK) return rc_sweep;
+        PGB_CUDA(ce);
+      } else if (rc_sweep != POISSON_OK) {
+        return rc_sweep;
       }
     }
     if (pl->max_sweeps >= 2) {
@@ -1191,6 +1246,7 @@ int poisson_batch_destroy(poisson_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   batch_persistent_free(&b->bp);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->body) cudaStreamDestroy(b->body);
   for (int k = 0; k < poisson_batch::kMaxBranches; ++k) {
     if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
     if (b->join[k]) cudaEventDestroy(b->join[k]);
@@ -1226,6 +1282,7 @@ int poisson_batch_create(int n, const int* nx, const int* ny, const int* nz, con
   }
   b->ws_bytes = off;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   for (int k = 0; k < poisson_batch::kMaxBranches && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
@@ -1391,7 +1448,10 @@ int poisson_batch_solve(poisson_batch* b, const void* const* S, void* const* p, 
     for (int k = 0; k < nbr && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
     for (int i : order) {
       if (rc != POISSON_OK || ce != cudaSuccess) break;
+      // a domain's refinement sweeps after the first become IF nodes on its done flag
+      b->plans[i]->cond_body = b->body;
       rc = poisson_solve(b->plans[i], S[i], p[i], (char*)workspace + b->off[i], b->branch[branch_of[i]], nullptr);
+      b->plans[i]->cond_body = nullptr;
     }
     for (int k = 0; k < nbr && ce == cudaSuccess; ++k) {
       ce = cudaEventRecord(b->join[k], b->branch[k]);

@@ -290,6 +290,10 @@ cudaError_t launch_verify(Stats* st_dev, const double* sq, int nsq, const double
 // p = p0 + q (double) when the refinement stopped after a sweep that stored only q (Stats::need_final).
 cudaError_t launch_finalize(const float* p0, const float* q, double* p, long long n, const Stats* stats,
                             cudaStream_t st);
+// Inside a captured CUDA graph: sets conditional handle h to 1 while the refinement is not done
+// (*done == 0), else 0, so that the IF node that follows runs its body (a refinement sweep) only
+// while the solve still needs it.
+cudaError_t launch_set_if_not_done(cudaGraphConditionalHandle h, const int* done, cudaStream_t st);
 // Conjugate gradients for a density varying in x, y and z (cg_kernels.cu).
 enum CgOp { CG_WMEAN = 0, CG_START, CG_APPLY, CG_UPDATE, CG_DOTS, CG_DIR, CG_SUM, CG_SHIFT, CG_FACES };
 struct CgLevel {      // per-level constants, so that no FP64 division runs per point

@@ -400,6 +400,15 @@ cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, c
   return cudaGetLastError();
 }
 
+__global__ void k_set_if_not_done(cudaGraphConditionalHandle h, const int* __restrict__ done) {
+  cudaGraphSetConditional(h, *done ? 0u : 1u);
+}
+
+cudaError_t launch_set_if_not_done(cudaGraphConditionalHandle h, const int* done, cudaStream_t st) {
+  k_set_if_not_done<<<1, 1, 0, st>>>(h, done);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const float* p0, const float* q, double* p, long long n, const Stats* stats,
                             cudaStream_t st) {
   const long long npairs = n / 2;   // nx is even
