@@ -157,7 +157,9 @@ def algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3, verified=False, kcut=Non
     iterate (its residual x-pass, forward y-pass and columns run; no inverse transforms); its
     residual x-pass also stores the certified iterate as p.  kcut: that verification solved only the
     columns with kx, |ky'| <= kcut, so its residual's transform is stored for kx <= kcut only, its
-    y-pass covers those kx and its column solve the (kcut + 1)(2 kcut + 1) low columns.
+    y-pass covers those kx and its column solve the (kcut + 1)(2 kcut + 1) low columns; and it is
+    sweep 2's first try, whose residual is r0 - L q from sweep 1's residual r0 stored in FP32: sweep 1
+    writes r0 (4 B) and the verification reads it in place of S (8 B).
     """
     N = nx * ny * nz
     Nc = (nx // 2 + 1) * ny * nz
@@ -172,9 +174,11 @@ def algorithmic_bytes(nx, ny, nz, sweeps, max_sweeps=3, verified=False, kcut=Non
         writes = 4 * N if (s == 1 and q_only) else 8 * N
         return reads + writes
 
+    kept_r0 = verified and kcut is not None and v == 2
     b = {
         "xfwd": 8 * N + 8 * Nc + sum(8 * N + 4 * N + (4 * N if s > 1 else 0) + 8 * Nc for s in range(1, sweeps + 1))
-                + nv * (8 * N + 4 * N + (4 * N if v > 1 else 0) + 8 * Ncx + 8 * N),
+                + nv * ((4 if kept_r0 else 8) * N + 4 * N + (4 * N if v > 1 else 0) + 8 * Ncx + 8 * N)
+                + (4 * N if kept_r0 else 0),
         "yfwd": (1 + sweeps) * 16 * Nc + nv * 16 * Ncx,
         "columns": (1 + sweeps) * 16 * Nc + nv * 16 * Ncl,
         "yinv": (1 + sweeps) * 16 * Nc,

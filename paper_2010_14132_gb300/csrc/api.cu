@@ -369,7 +369,7 @@ int poisson_plan_create(int nx, int ny, int nz, double dx, double dy, const doub
                o_aff = take(nz * 8), o_cff = take(nz * 8), o_lxd = take(pl->nxh * 8),
                o_lyd = take(ny * 8), o_lxf = take(pl->nxh * 4), o_lyf = take(ny * 4), o_twxd = take(n * 16),
                o_twrd = take(pl->nxh * 16), o_twyd = take(ny * 16), o_twxf = take(n * 8), o_twrf = take(pl->nxh * 8),
-               o_twyf = take(ny * 8), o_dz = take(nz * 8), o_rho = take(nz * 8), o_floor = take(16);
+               o_twyf = take(ny * 8), o_dz = take(nz * 8), o_rho = take(nz * 8), o_floor = take(32);
   cudaError_t e = cudaMalloc(&pl->tables, off);
   if (e != cudaSuccess) {
     delete pl;
@@ -657,6 +657,7 @@ static cudaError_t forward_columns(poisson_plan* pl, const void* in, int in_doub
         e = launch_xres_static(Rc, spec, gc, pl->fx, pl->tb, done, &stats->err, &nb, st, &used);
         stat = used;
       }
+      if (Rc.r0 && !stat) return cudaErrorNotSupported;   // the r0 - L q form exists in the static pass only
       if (res_stored_p && stat && Rc.q && Rc.p_out && lc >= pl->nz) *res_stored_p = true;
       Rc.p_out = nullptr;   // the other residual forms do not store the iterate
       if (e == cudaSuccess && !used) e = launch_xfwd_residual(Rc, spec, gc, pl->fx, pl->tb, done, &nb, st);
@@ -899,6 +900,13 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
     // sweep 1, or sweep 2's correction certifying it), k_finalize forms p = p0 + q.  A third sweep
     // first rebuilds q from the double iterate of the second.
     double* rpart = (double*)(ws + pl->off_rpart);
+    // When sweep 2 starts with the low-wavenumber verification, sweep 1 keeps its residual r0 in FP32 in
+    // the rows of p (row r's first nx floats; p is written in full later on every path) and the
+    // verification forms r0 - L q from it instead of S - mu - L (p0 + q).
+    double icut_unused = 0.0;
+    const bool keep_r0 = pl->max_sweeps >= 2 && verify_cut(pl, &icut_unused) >= 0 && pl->xkernel == 0 &&
+                         !pl->respass && level_chunk(pl) >= pl->nz && xpass_static_supported(pl->fx.n) &&
+                         ((uintptr_t)p & 15) == 0;
     for (int sweep = 1; sweep <= pl->max_sweeps; ++sweep) {
       // residual computed inside the forward x-pass (its rows are never stored)
       ResidualArgs R{};
@@ -912,6 +920,8 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
       R.cx = pl->cx;
       R.cy = pl->cy;
       R.mu_ff = &stats->mu_ff;
+      R.r_ld = 2LL * pl->nx;
+      if (sweep == 1 && keep_r0) R.r_out = (float*)p;
       int nres = 0, nsq = 0;
       // from the second sweep on, the correction's norm (Parseval on the solved spectrum) can already
       // certify the current iterate: then the sweep stops before its inverse transforms.  Sweep 2's
@@ -925,6 +935,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
         ResidualArgs Rl = R;
         Rl.p_out = (double*)p;
         Rl.kmax = kcut;   // the residual's transform is read only up to kx = kcut
+        if (keep_r0) Rl.r0 = (const float*)p;
         int nres_l = 0, nsq_l = 0;
         bool stored_l = false;
         PGB_CUDA(forward_columns(pl, nullptr, 0, ws, st, 0, done, &stats->pmean, &Rl, &nres_l, sweep, nullptr, sqv,
@@ -932,7 +943,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
         if (nsq_l > 0) {
           const int ps = prof_begin(pl, POISSON_PHASE_CONTROL, st);
           e = launch_verify(stats, sqv, nsq_l, rpart, nres_l, sweep, pl->tol, pl->tb.floor_d,
-                            (double)pl->nx * pl->ny, stored_l ? 1 : 0, inv_lcut2, st);
+                            (double)pl->nx * pl->ny, stored_l ? 1 : 0, inv_lcut2, keep_r0 ? 1 : 0, st);
           prof_end(pl, ps, st);
           PGB_CUDA(e);
         }
@@ -957,7 +968,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
         if (sqn && nsq > 0) {
           const int ps = prof_begin(pl, POISSON_PHASE_CONTROL, ss);
           e = launch_verify(stats, sqn, nsq, rpart, nres, sweep, pl->tol, pl->tb.floor_d, (double)pl->nx * pl->ny,
-                            stored ? 1 : 0, 0.0, ss);
+                            stored ? 1 : 0, 0.0, 0, ss);
           prof_end(pl, ps, ss);
           PGB_CUDA(e);
         }

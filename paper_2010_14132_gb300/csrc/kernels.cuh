@@ -197,6 +197,12 @@ struct ResidualArgs {
   const float2* mu_ff;
   int kmax;              // > 0: the static residual x-pass stores only the bins kx <= kmax (nothing reads
                          // the others); 0: every bin
+  // Residual kept between sweep 1 and the verification's first try (static x-pass only): sweep 1 stores
+  // its residual r0 in FP32 at r_out (row r at r_out + r r_ld floats); the first try, given r0 instead,
+  // forms r0 - L q (S and p0's stencil are not read; p0 only for the stored iterate).
+  float* r_out;          // nullable
+  const float* r0;       // nullable
+  long long r_ld;        // row stride of r_out / r0 in floats
 };
 
 // ---- launchers (stream-ordered, return cudaError_t of the launch) ----
@@ -283,10 +289,12 @@ cudaError_t launch_control(Stats* st_dev, const double* partials, int nblocks, c
 // the sweep's residual norms (its forward x-pass).  p_stored: that x-pass also stored p_{n-1} as p.
 // inv_lcut2 > 0: the columns were solved only for the low wavenumbers (kx, |ky'| <= kcut) and the rest
 // of ||delta_n||^2 is bounded by (W_max/W_min) ||r||^2/lambda_cut^2 (inv_lcut2 = 1/lambda_cut^2, the
-// weight ratio from floor[1]); see verify_low_wavenumbers in api.cu.
+// weight ratio from floor[1]); verify_cut in api.cu picks kcut.  from_r0: the sweep's residual was
+// formed as r0 - L q from the previous sweep's FP32 residual r0 (ResidualArgs::r0); the bound then adds
+// 2^-24 ||r0|| G/||p|| for r0's rounding and takes ||S|| from the previous sweep.
 cudaError_t launch_verify(Stats* st_dev, const double* sq, int nsq, const double* res_partials, int res_nblocks,
                           int pass, double tol, const double* floor, double nxny, int p_stored, double inv_lcut2,
-                          cudaStream_t st);
+                          int from_r0, cudaStream_t st);
 // p = p0 + q (double) when the refinement stopped after a sweep that stored only q (Stats::need_final).
 cudaError_t launch_finalize(const float* p0, const float* q, double* p, long long n, const Stats* stats,
                             cudaStream_t st);
@@ -379,15 +387,16 @@ int batch_persistent_build(BatchPersistent* bp, const std::vector<BatchDomIn>& d
 cudaError_t batch_persistent_launch(const BatchPersistent& bp, cudaStream_t st);
 void batch_persistent_free(BatchPersistent* bp);
 
-// Limiting accuracy F of the mixed refinement from the plan's coefficients (one block; nz <= 512):
-// the relative error that the double-float residual's rounding leaves after any number of sweeps,
-// added to every error bound.  Written to out[0]; out[1] = max_k W_k / min_k W_k (the bound on the
-// vertical solve's non-normality that the low-wavenumber verification uses).
 // Pivot reciprocals 1/u_k of the listed low-|k| columns ([n][nz], double), which depend only on the
 // column's wavenumbers and the levels: built once per plan (and per poisson_plan_set_rho0) so that the
 // double column solves run their recurrences without a division on the dependency chain.
 cudaError_t launch_lowk_pivots(const int2* cols, int n, const double* a_d, const double* c_d, const double* lamx_d,
                                const double* lamy_d, int nz, int singular00, double* inv_tab, cudaStream_t st);
+// Limiting accuracy F of the mixed refinement from the plan's coefficients (one block; nz <= 512):
+// the relative error that the double-float residual's rounding leaves after any number of sweeps,
+// added to every error bound.  Written to out[0]; out[1] = max_k W_k / min_k W_k (the bound on the
+// vertical solve's non-normality that the low-wavenumber verification uses); out[2] = G, the factor
+// by which a residual noise of 2-norm e reaches the solution (e G), so that F = u K ||p|| G/||p||.
 cudaError_t launch_accuracy_floor(const double* a_d, const double* c_d, const double* W_d, int nz, int nx, int ny,
                                   double dx, double dy, int top_dirichlet, double* out, cudaStream_t st);
 cudaError_t launch_grho(int kind /*0 double, 1 float, 2 double fields float math*/, const void* g, const void* p, const Geom& g_, const Tables& tb,

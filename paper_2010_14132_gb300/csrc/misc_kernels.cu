@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(kFloorThreads) k_accuracy_floor(const double* 
     const double npts = (double)nx * ny * nz;
     out[0] = u * K * sqrt(eta) * sqrt(red[0][0] / npts);
     out[1] = wratio;
+    out[2] = sqrt(eta) * sqrt(red[0][0] / npts);   // the same amplification for any residual noise
   }
 }
 
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(256) k_control(Stats* st, const double* __rest
 __global__ void __launch_bounds__(1024) k_verify(Stats* st, const double* __restrict__ sq, int nsq,
                                                  const double* __restrict__ res_partials, int res_nblocks, int pass,
                                                  double tol, const double* __restrict__ floor, double nxny,
-                                                 int p_stored, double inv_lcut2) {
+                                                 int p_stored, double inv_lcut2, int from_r0) {
   __shared__ double sh[3][1024];
   if (st->done) return;   // an earlier pass already ended the refinement
   const int t = threadIdx.x;
@@ -331,14 +332,24 @@ __global__ void __launch_bounds__(1024) k_verify(Stats* st, const double* __rest
   // column, with T = W^{-1} M similar to a positive semidefinite matrix through W^{1/2}, so its norm is at
   // most sqrt(W_max/W_min)/lambda_h <= sqrt(W_max/W_min)/lambda_cut times the residual column's (Parseval)
   if (inv_lcut2 > 0) sd += floor[1] * inv_lcut2 * sh[1][0];
-  verify_decide(st, sd, sh[1][0], sh[2][0], pass, tol, floor[0], p_stored);
+  double fl = floor[0], ss = sh[2][0];
+  if (from_r0 && pass >= 2) {
+    // the residual was formed as r0 - L q from the previous sweep's residual r0 stored in FP32: its
+    // rounding (at most 2^-24 ||r0|| in the 2-norm) reaches the correction like the residual's own
+    // rounding does, so it adds 2^-24 ||r0|| G/||p|| to the limiting accuracy (G = floor[2]); the
+    // source norm is the previous sweep's (this pass did not read S)
+    const double sp = st->sq_p[pass - 1];
+    if (sp > 0) fl += 0x1p-24 * sqrt(st->sq_res[pass - 2]) * floor[2] / sqrt(sp);
+    ss = st->sq_src[pass - 2];
+  }
+  verify_decide(st, sd, sh[1][0], ss, pass, tol, fl, p_stored);
 }
 
 cudaError_t launch_verify(Stats* st_dev, const double* sq, int nsq, const double* res_partials, int res_nblocks,
                           int pass, double tol, const double* floor, double nxny, int p_stored, double inv_lcut2,
-                          cudaStream_t st) {
+                          int from_r0, cudaStream_t st) {
   k_verify<<<1, 1024, 0, st>>>(st_dev, sq, nsq, res_partials, res_nblocks, pass, tol, floor, nxny, p_stored,
-                               inv_lcut2);
+                               inv_lcut2, from_r0);
   return cudaGetLastError();
 }
 

@@ -211,4 +211,54 @@ __device__ __forceinline__ float2 residual_value2(float2 pc, float2 pe, float2 p
   return add2(r, add2(er, sub2(add2(et, sub2(Sl, k.mul)), lp_lo)));
 }
 
+// r = r0 - L q at the two points, from sweep 1's residual r0 of the iterate p0 (stored in FP32) and the
+// correction q: the residual of p0 + q, with q's stencil as in residual_value2 (exact neighbour sums and
+// differences, products with the coefficient splits by FMA-based TwoProduct) and one double-float
+// accumulation onto r0.  r0's own FP32 rounding (at most 2^-24 |r0| per point) is the one error added
+// to the residual_value2 form; the verification's bound accounts for it.
+template <bool ISO>
+__device__ __forceinline__ float2 residual_from_r0(float2 r0, float2 qc, float2 qe, float2 qw, float2 qn, float2 qs,
+                                                   float2 qd, float2 qu, const ResCoef& k) {
+  float2 nth, thl;   // -(horizontal part of L q) high, + low
+  if constexpr (ISO) {
+    float2 a1, f1, a2, f2, a3, f3;
+    two_sum2(qe, qw, a1, f1);
+    two_sum2(qn, qs, a2, f2);
+    two_sum2(a1, a2, a3, f3);
+    const float2 h = fma2(qc, make_float2(-4.f, -4.f), a3);   // neighbour sum - 4 qc, rounded once
+    const float2 dl = add2(add2(f1, f2), f3);
+    nth = mul2(k.ncxh, h);
+    thl = fma2(k.cxh, dl, fma2(k.cxl, h, fma2(k.cxh, h, nth)));
+  } else {
+    const float2 m2 = make_float2(-2.f, -2.f);
+    float2 a1, f1, a2, f2;
+    two_sum2(qe, qw, a1, f1);
+    const float2 hx = fma2(qc, m2, a1);
+    const float2 ntx = mul2(k.ncxh, hx);
+    const float2 txl = fma2(k.cxh, f1, fma2(k.cxl, hx, fma2(k.cxh, hx, ntx)));
+    two_sum2(qn, qs, a2, f2);
+    const float2 hy = fma2(qc, m2, a2);
+    const float2 nty = mul2(k.ncyh, hy);
+    const float2 tyl = fma2(k.cyh, f2, fma2(k.cyl, hy, fma2(k.cyh, hy, nty)));
+    float2 ea;
+    two_sum2(ntx, nty, nth, ea);
+    thl = sub2(add2(txl, tyl), ea);
+  }
+  // z: a (qd - qc) + c (qu - qc), the differences exact
+  float2 dd, ed, du, eu;
+  two_diff2(qd, qc, dd, ed);
+  two_diff2(qu, qc, du, eu);
+  const float2 np1 = mul2(k.nah, dd);
+  const float2 l1 = fma2(k.ah, ed, fma2(k.al, dd, fma2(k.ah, dd, np1)));
+  const float2 np2 = mul2(k.nch, du);
+  const float2 l2 = fma2(k.ch, eu, fma2(k.cl, du, fma2(k.ch, du, np2)));
+  float2 b, eb, c, ec;
+  two_sum2(np1, np2, b, eb);
+  two_sum2(nth, b, c, ec);                                     // -Lq high, exact with eb + ec
+  const float2 lq_lo = sub2(add2(thl, add2(l1, l2)), add2(eb, ec));   // Lq low
+  float2 r, er;
+  two_sum2(r0, c, r, er);
+  return add2(r, sub2(er, lq_lo));
+}
+
 }  // namespace pgb

@@ -26,11 +26,14 @@ namespace {
 #ifndef PGB_XRES_E3_BLOCKS
 #define PGB_XRES_E3_BLOCKS 2
 #endif
-constexpr int xres_min_blocks(int e, bool has_q) {
-  return e % 3 == 0 ? PGB_XRES_E3_BLOCKS : (e >= 16 ? 4 : (has_q ? PGB_XRES_Q_BLOCKS : 3));
+// (the r0 - L q form holds no S or p0 stencil values: three CTAs, like the first sweep's)
+constexpr int xres_min_blocks(int e, bool has_q, bool from_r0 = false) {
+  return e % 3 == 0 ? PGB_XRES_E3_BLOCKS : (e >= 16 ? 4 : (has_q && !from_r0 ? PGB_XRES_Q_BLOCKS : 3));
 }
-template <int N, int E, bool HAS_Q, bool STAGE_P, bool ISO>
-__global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
+// FROM_R0 (with HAS_Q): the rows staged are sweep 1's FP32 residual r0 (one bulk copy per row, at the
+// start of the row's slot, whose full width the line buffers need later) and r = r0 - L q.
+template <int N, int E, bool HAS_Q, bool STAGE_P, bool ISO, bool FROM_R0 = false>
+__global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q, FROM_R0)) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
                                                       const int* __restrict__ done, unsigned* __restrict__ err,
                                                       int ns, unsigned stage_bytes) {
@@ -59,10 +62,18 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xr
   __syncthreads();
   pdl_wait();   // the previous kernels of the stream are complete
   if (done && *done) return;
+  static_assert(!FROM_R0 || (HAS_Q && !STAGE_P), "r0 - L q is formed with q, from the staged r0 rows");
   auto issue = [&](long long grp, int s) {
     const long long r0 = row_begin + grp * RB;
     const unsigned nv = (unsigned)(row_end - r0 < RB ? row_end - r0 : RB);
     unsigned char* d = stg + (size_t)s * stage_bytes;
+    if constexpr (FROM_R0) {
+      mbar_arrive_expect_tx(&bar[s], nv * NX * 4u);
+      for (unsigned j = 0; j < nv; ++j)
+        bulk_g2s(d + (size_t)j * NX * 8, R.r0 + (r0 + j) * R.r_ld, NX * 4u, &bar[s]);
+      rg.issued[s]++;
+      return;
+    }
     mbar_arrive_expect_tx(&bar[s], nv * NX * (8u + (STAGE_P ? 4u + (HAS_Q ? 4u : 0u) : 0u)));
     bulk_g2s(d, R.S + r0 * NX, nv * NX * 8u, &bar[s]);
     if constexpr (STAGE_P) {
@@ -121,6 +132,32 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xr
     const float* qrow = STAGE_P ? reinterpret_cast<const float*>(d + s_bytes + p_bytes) + (size_t)ty * NX
                                 : (HAS_Q ? R.q + rc * NX : nullptr);
     C v[E];
+    if constexpr (FROM_R0) {
+      const float2* r0row = reinterpret_cast<const float2*>(d + (size_t)ty * NX * 8);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int e = st_in_index<N, E, 0>(lane, i);
+        const float2 qc = reinterpret_cast<const float2*>(qrow)[e];
+        const float qw = qrow[e == 0 ? NX - 1 : 2 * e - 1];
+        const float qe = qrow[e == N - 1 ? 0 : 2 * e + 2];
+        const float2 qn = reinterpret_cast<const float2*>(R.q + rn * NX)[e];
+        const float2 qs = reinterpret_cast<const float2*>(R.q + rs * NX)[e];
+        const float2 qd = has_dn ? reinterpret_cast<const float2*>(R.q + (rc - g.ny) * NX)[e] : qc;
+        const float2 qu = has_up ? reinterpret_cast<const float2*>(R.q + (rc + g.ny) * NX)[e] : make_float2(0.f, 0.f);
+        // the pair's east neighbours are (qc.y, qe), its west neighbours (qw, qc.x)
+        v[i] = residual_from_r0<ISO>(r0row[e], qc, make_float2(qc.y, qe), make_float2(qw, qc.x), qn, qs, qd, qu, K);
+        if (valid) {
+          racc = fma2(v[i], v[i], racc);
+          if (R.p_out) {   // the iterate p0 + q as the double the inverse x-pass would store
+            const float2 pc = reinterpret_cast<const float2*>(prow)[e];
+            float2 sp, tp;
+            two_sum2(pc, qc, sp, tp);
+            __stcs(reinterpret_cast<double2*>(R.p_out + row * NX) + e,
+                   make_double2(ff2d_fast(sp.x, tp.x), ff2d_fast(sp.y, tp.y)));
+          }
+        }
+      }
+    } else {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int e = st_in_index<N, E, 0>(lane, i);
@@ -150,6 +187,9 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xr
       if (valid) {
         racc = fma2(v[i], v[i], racc);
         sacc = fma2(Sh, Sh, sacc);
+        if constexpr (!HAS_Q) {   // sweep 1's residual, kept for the verification's first try
+          if (R.r_out) __stcs(reinterpret_cast<float2*>(R.r_out + row * R.r_ld) + e, v[i]);
+        }
         if constexpr (HAS_Q) {
           if (R.p_out) {   // the iterate p0 + q as the double the inverse x-pass would store
             float2 sp, tp;
@@ -160,7 +200,8 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q)) k_xr
         }
       }
     }
-    sync();   // the line's threads have read the S row before it is overwritten
+    }
+    sync();   // the line's threads have read the staged row before it is overwritten
     const C* fin = st_fft<N, E, -1, false, float>(v, la, lb, sw, lane, tw_s, sync);
     r2c_unpack_store<N, E>(fin, twr_s, spec + (valid ? row : 0) * g.P, lane, valid, R.kmax > 0 ? R.kmax : N);
     fence_proxy_async_smem();   // generic writes to the staged row come before its refill by TMA
@@ -201,9 +242,22 @@ cudaError_t xres_s(const ResidualArgs& R, float2* spec, const Geom& g, int N, in
   const XsConfig c_all = xs_config(N, E, RB * row_bytes_all, 0, true);
   const bool stage_p = c_all.ns > 0 && c_all.smem <= 75 * 1024 * (size_t)xs_threads(E) / 256;
   const XsConfig c = stage_p ? c_all : xs_config(N, E, RB * row_bytes_s, 0, true);
+  const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
+  if constexpr (HAS_Q) {
+    if (R.r0) {   // the first try's r0 - L q: r0 rows staged in slots of an S row's width
+      const XsConfig c0 = xs_config(N, E, RB * row_bytes_s, 0, true);
+      if (c0.ns == 0 || !aligned16(R.r0) || (R.r_ld * 4) % 16 || !aligned16(R.p0) || !aligned16(R.q) ||
+          (g.nx * 4) % 16)
+        return cudaSuccess;
+      PGB_XS_E8_E3_SWITCH(E, PGB_XS_N_SWITCH(N, {
+        return xs_launch(k_xres_s<NN, EE, true, false, ISO, true>, NN / EE, RB, c0, ngroups, nblocks_out, st, used,
+                         R, spec, g, tb.twx_f, tb.twr_f, done, err);
+      }));
+      return cudaSuccess;
+    }
+  }
   if (c.ns == 0 || !aligned16(R.S) || !aligned16(R.p0) || (HAS_Q && !aligned16(R.q)) || (g.nx * 4) % 16)
     return cudaSuccess;
-  const long long ngroups = ((long long)g.ny * (g.lev1 - g.lev0) + RB - 1) / RB;
   if (stage_p) {
     PGB_XS_E8_E3_SWITCH(E, PGB_XS_N_SWITCH(N, {
       return xs_launch(k_xres_s<NN, EE, HAS_Q, true, ISO>, NN / EE, RB, c, ngroups, nblocks_out, st, used, R, spec, g,

@@ -227,3 +227,27 @@ def test_uncertified_low_wavenumber_bound_falls_back_to_the_full_sweep():
     assert it["converged"] and it["sweeps"] == 1, it
     assert it["error_estimate"] == pytest.approx(lo, rel=1e-12), (it, if_)
     np.testing.assert_array_equal(pt, pf)
+
+
+@pytest.mark.parametrize("shape,seed", [((512, 512, 64), 3), ((384, 256, 64), 21), ((512, 384, 32), 5)])
+def test_first_try_from_the_kept_residual(shape, seed):
+    """Sweep 1 keeps its residual r0 in FP32 (in the rows of p) and the low-wavenumber first try forms
+    r0 - L q from it instead of S - mu - L (p0 + q).  Against the first try formed from S (the separate
+    residual pass keeps nothing): the same iterate; the correction's norm within r0's rounding relative
+    to the residual, 2^-24 ||r0||/||r1||; and a bound that adds r0's rounding term (positive, far below
+    the tolerance) and still holds against the oracle."""
+    nx, ny, nz = shape
+    d = wl.anelastic_noise(nx, ny, nz, seed=seed)
+    pk, ik = _solve(d)                      # r0 kept
+    ps, is_ = _solve(d, residual_pass=1)    # from S
+    assert ik["converged"] and is_["converged"] and ik["sweeps"] == is_["sweeps"] == 1, (ik, is_)
+    np.testing.assert_allclose(pk, ps, rtol=2e-14, atol=2e-14 * np.abs(ps).max())
+    rho = 2.0 ** -24 * ik["rel_residual"][0] / ik["rel_residual"][1]
+    assert ik["rel_update"][2] == pytest.approx(is_["rel_update"][2], rel=max(rho, 1e-6)), (ik, is_, rho)
+    assert ik["rel_residual"][1] == pytest.approx(is_["rel_residual"][1], rel=max(rho, 1e-6))
+    F = ik["accuracy_floor"]
+    extra = ik["error_estimate"] - (2 * ik["rel_update"][2] + F)
+    assert 0 < extra < 1e-11, (extra, ik)
+    assert is_["error_estimate"] == pytest.approx(2 * is_["rel_update"][2] + F, rel=1e-12), is_
+    ref = O.solve(d.S, d.dx, d.dy, d.dz, d.rho0)
+    assert O.relative_l2(pk, ref) <= ik["error_estimate"] <= 1e-10, ik
