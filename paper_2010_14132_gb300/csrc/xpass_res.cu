@@ -30,8 +30,9 @@ namespace {
 constexpr int xres_min_blocks(int e, bool has_q, bool from_r0 = false) {
   return e % 3 == 0 ? PGB_XRES_E3_BLOCKS : (e >= 16 ? 4 : (has_q && !from_r0 ? PGB_XRES_Q_BLOCKS : 3));
 }
-// FROM_R0 (with HAS_Q): the rows staged are sweep 1's FP32 residual r0 (one bulk copy per row, at the
-// start of the row's slot, whose full width the line buffers need later) and r = r0 - L q.
+// FROM_R0 (with HAS_Q): the rows staged are sweep 1's FP32 residual r0 and the correction q (one bulk
+// copy each per row, side by side in the row's slot, whose full width the line buffers need later) and
+// r = r0 - L q.
 template <int N, int E, bool HAS_Q, bool STAGE_P, bool ISO, bool FROM_R0 = false>
 __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q, FROM_R0)) k_xres_s(ResidualArgs R, float2* __restrict__ spec, Geom g,
                                                       const float2* __restrict__ twx, const float2* __restrict__ twr,
@@ -68,9 +69,11 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q, FROM_
     const unsigned nv = (unsigned)(row_end - r0 < RB ? row_end - r0 : RB);
     unsigned char* d = stg + (size_t)s * stage_bytes;
     if constexpr (FROM_R0) {
-      mbar_arrive_expect_tx(&bar[s], nv * NX * 4u);
-      for (unsigned j = 0; j < nv; ++j)
+      mbar_arrive_expect_tx(&bar[s], nv * NX * 8u);
+      for (unsigned j = 0; j < nv; ++j) {
         bulk_g2s(d + (size_t)j * NX * 8, R.r0 + (r0 + j) * R.r_ld, NX * 4u, &bar[s]);
+        bulk_g2s(d + (size_t)j * NX * 8 + NX * 4, R.q + (r0 + j) * NX, NX * 4u, &bar[s]);
+      }
       rg.issued[s]++;
       return;
     }
@@ -134,12 +137,13 @@ __global__ void __launch_bounds__(xs_threads(E), xres_min_blocks(E, HAS_Q, FROM_
     C v[E];
     if constexpr (FROM_R0) {
       const float2* r0row = reinterpret_cast<const float2*>(d + (size_t)ty * NX * 8);
+      const float* qs_row = reinterpret_cast<const float*>(d + (size_t)ty * NX * 8 + NX * 4);   // staged q row
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int e = st_in_index<N, E, 0>(lane, i);
-        const float2 qc = reinterpret_cast<const float2*>(qrow)[e];
-        const float qw = qrow[e == 0 ? NX - 1 : 2 * e - 1];
-        const float qe = qrow[e == N - 1 ? 0 : 2 * e + 2];
+        const float2 qc = reinterpret_cast<const float2*>(qs_row)[e];
+        const float qw = qs_row[e == 0 ? NX - 1 : 2 * e - 1];
+        const float qe = qs_row[e == N - 1 ? 0 : 2 * e + 2];
         const float2 qn = reinterpret_cast<const float2*>(R.q + rn * NX)[e];
         const float2 qs = reinterpret_cast<const float2*>(R.q + rs * NX)[e];
         const float2 qd = has_dn ? reinterpret_cast<const float2*>(R.q + (rc - g.ny) * NX)[e] : qc;
