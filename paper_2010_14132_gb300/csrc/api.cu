@@ -1517,7 +1517,8 @@ struct poisson_pipe {
   int first_status = POISSON_OK;
   // per-step (done, sweeps, converged, err) copied from the device statistics after each solve
   static constexpr int kRing = 1024;
-  int4* status_ring = nullptr;   // page-locked, kRing entries
+  int4* status_ring = nullptr;   // page-locked and mapped, kRing entries
+  int4* status_ring_dev = nullptr;   // the same ring as the device addresses it
 };
 
 int poisson_pipe_destroy(poisson_pipe* pp) {
@@ -1556,7 +1557,8 @@ int poisson_pipe_create(poisson_plan* pl, poisson_pipe** out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pp->ev_comp[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pp->ev_out[k], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaMallocHost(&pp->status_ring, sizeof(int4) * poisson_pipe::kRing);
+  if (e == cudaSuccess) e = cudaHostAlloc(&pp->status_ring, sizeof(int4) * poisson_pipe::kRing, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&pp->status_ring_dev, pp->status_ring, 0);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pp->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pp->s_comp, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pp->s_out, cudaStreamNonBlocking);
@@ -1581,9 +1583,11 @@ int poisson_pipe_submit(poisson_pipe* pp, const void* S_host, void* p_host) {
   const int st = poisson_solve(pp->plan, pp->dS[k], pp->dp[k], pp->ws, pp->s_comp, nullptr);
   if (st != POISSON_OK && pp->first_status == POISSON_OK) pp->first_status = st;
   static_assert(offsetof(Stats, err) == offsetof(Stats, done) + 3 * sizeof(int), "status fields not contiguous");
-  PGB_CUDA(cudaMemcpyAsync(&pp->status_ring[pp->since_wait % poisson_pipe::kRing],
-                           (char*)pp->ws + pp->plan->off_stats + offsetof(Stats, done), sizeof(int4),
-                           cudaMemcpyDeviceToHost, pp->s_comp));
+  // the step's status goes to the host ring by a one-thread kernel (stores into mapped host memory): a
+  // copy here would queue on the copy engine behind the previous step's solution copy and hold the
+  // compute stream, and with it the next solve, until that copy ends
+  PGB_CUDA(launch_copy_status((const int*)((char*)pp->ws + pp->plan->off_stats + offsetof(Stats, done)),
+                              (int*)&pp->status_ring_dev[pp->since_wait % poisson_pipe::kRing], pp->s_comp));
   pp->since_wait++;
   PGB_CUDA(cudaEventRecord(pp->ev_comp[k], pp->s_comp));
   PGB_CUDA(cudaStreamWaitEvent(pp->s_out, pp->ev_comp[k], 0));

@@ -420,6 +420,19 @@ cudaError_t launch_set_if_not_done(cudaGraphConditionalHandle h, const int* done
   return cudaGetLastError();
 }
 
+// four ints (src need not be 16-byte aligned)
+__global__ void k_copy_status(const int* __restrict__ src, int* dst) {
+  dst[0] = src[0];
+  dst[1] = src[1];
+  dst[2] = src[2];
+  dst[3] = src[3];
+}
+
+cudaError_t launch_copy_status(const int* src, int* dst, cudaStream_t st) {
+  k_copy_status<<<1, 1, 0, st>>>(src, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const float* p0, const float* q, double* p, long long n, const Stats* stats,
                             cudaStream_t st) {
   const long long npairs = n / 2;   // nx is even

@@ -53,3 +53,30 @@ def test_pipe_rejects_device_tensors():
     with pytest.raises(ValueError):
         pipe.submit(S, torch.empty(plan.shape, dtype=torch.float64))
     pipe.close()
+
+
+def test_pipe_reports_each_steps_status():
+    """The per-step status (done, sweeps, converged, error bits) reaches the host ring at wait(): a
+    tolerance below the limiting accuracy is never met, so the mixed steps end NOT_CONVERGED; the
+    same sources with the default tolerance converge."""
+    from paper_2010_14132_gb300 import _native as N
+    d = wl.anelastic_noise(128, 96, 24, seed=43)
+    S = torch.from_numpy(np.ascontiguousarray(d.S)).pin_memory()
+    outs = [torch.empty_like(S).pin_memory() for _ in range(3)]
+    strict = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype="mixed", tolerance=1e-300)
+    pipe = Pipe(strict)
+    for p in outs:
+        pipe.submit(S, p)
+    with pytest.raises(N.PoissonError) as ei:
+        pipe.wait()
+    assert ei.value.status == N.POISSON_ERR_NOT_CONVERGED
+    pipe.close()
+    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, d.rho0, dtype="mixed")
+    pipe = Pipe(plan)
+    for p in outs:
+        pipe.submit(S, p)
+    pipe.wait()
+    ref = plan.solve(S.cuda()).cpu()
+    for p in outs:
+        assert torch.equal(p, ref)
+    pipe.close()
