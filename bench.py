@@ -424,20 +424,26 @@ def main():
             ph[1].copy_(p, non_blocking=True)
     torch.cuda.synchronize()
     link_gbs = 3 * 2 * S.numel() * 8 / (time.perf_counter() - t_link) / 1e9
-    torch.cuda.synchronize()
-    barrier()
-    t_e2e = time.perf_counter()
-    for i in range(K2):
-        pipe.submit(Sh[i % 2], ph[i % 2])
-    pipe.wait()
-    t_e2e = time.perf_counter() - t_e2e
-    barrier()
-    ms_e2e = max_over_ranks(t_e2e * 1e3 / K2, dist, "cuda")
+    # three runs of K2 steps, the median reported: the host link is shared with the box's other GPUs
+    runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        barrier()
+        t_e2e = time.perf_counter()
+        for i in range(K2):
+            pipe.submit(Sh[i % 2], ph[i % 2])
+        pipe.wait()
+        t_e2e = time.perf_counter() - t_e2e
+        barrier()
+        runs.append(max_over_ranks(t_e2e * 1e3 / K2, dist, "cuda"))
+    ms_e2e = sorted(runs)[1]
     pipe.close()
     e2e = {"value": world * d.npoints / (ms_e2e * 1e-3) / 1e6, "unit": "Mpoints/s",
            "h2d_bytes_per_step": int(S.numel() * 8), "d2h_bytes_per_step": int(p.numel() * 8),
-           "ms_per_step": ms_e2e, "steps": K2, "host_link_gbs_both_directions": link_gbs,
-           "how": "poisson_pipe: H2D of step i+1 and D2H of step i-1 overlap the solve of step i; host wall clock"}
+           "ms_per_step": ms_e2e, "steps": K2, "runs_ms_per_step": runs,
+           "host_link_gbs_both_directions": link_gbs,
+           "how": "poisson_pipe: H2D of step i+1 and D2H of step i-1 overlap the solve of step i; host wall "
+                  "clock; median of three runs of `steps` steps"}
 
     # ---- plain FP64 GPU solve of the same grid (the comparison the metric names)
     fp64 = None
