@@ -29,6 +29,8 @@
  *   - fields are C-contiguous [nz][ny][nx] arrays, x fastest, in DEVICE memory
  *     (or [nx][ny][nz], z fastest, with POISSON_OPT_LAYOUT = POISSON_LAYOUT_X_Y_Z);
  *   - element type: double for POISSON_FP64 and POISSON_MIXED, float for POISSON_FP32;
+ *   - device fields start on a 16-byte boundary (the kernels move two points per access;
+ *     cudaMalloc and torch allocations always do): POISSON_ERR_INVALID_ARG otherwise;
  *   - the caller owns every field and the workspace; the plan owns only its small
  *     device tables (coefficients, twiddles), allocated by create, freed by destroy;
  *   - every call is asynchronous on the given CUDA stream (a cudaStream_t passed as

@@ -227,6 +227,9 @@ void layout_workspace(poisson_plan* pl) {
   pl->ws_bytes = off;
 }
 
+// Device fields are read and written with 16-byte vector accesses (two points at a time).
+bool field_aligned(const void* f) { return ((uintptr_t)f & 15) == 0; }
+
 bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
   const char* pa = (const char*)a;
   const char* pb = (const char*)b;
@@ -1016,6 +1019,7 @@ static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cuda
 
 int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, void* stream, poisson_info* info) {
   if (!pl || !S || !p) return POISSON_ERR_INVALID_ARG;
+  if (!field_aligned(S) || !field_aligned(p)) return POISSON_ERR_INVALID_ARG;
   int rc = check_ws(pl, workspace);
   if (rc != POISSON_OK) return rc;
   const size_t fbytes = (size_t)pl->g.N * pl->elem();
@@ -1042,6 +1046,7 @@ int poisson_solve_adjoint(poisson_plan* pl, const void* gp, const void* p, void*
                           void* stream) {
   if (!pl || !gp || !gS) return POISSON_ERR_INVALID_ARG;
   if (grho && !p) return POISSON_ERR_INVALID_ARG;
+  if (!field_aligned(gp) || !field_aligned(gS) || (p && !field_aligned(p))) return POISSON_ERR_INVALID_ARG;
   int rc = check_ws(pl, workspace);
   if (rc != POISSON_OK) return rc;
   const size_t fbytes = (size_t)pl->g.N * pl->elem();
@@ -1131,6 +1136,7 @@ int poisson_cg_solve(poisson_plan* pl, const double* rho3, const double* S, doub
                      void* workspace, void* stream, poisson_cg_info* info) {
   if (info) std::memset(info, 0, sizeof(*info));
   if (!pl || !rho3 || !S || !p) return POISSON_ERR_INVALID_ARG;
+  if (!field_aligned(rho3) || !field_aligned(S) || !field_aligned(p)) return POISSON_ERR_INVALID_ARG;
   if (pl->dtype == POISSON_FP32 || pl->layout != POISSON_LAYOUT_Z_Y_X) return POISSON_ERR_UNSUPPORTED;
   if (!(tol > 0) || max_iter < 1) return POISSON_ERR_INVALID_ARG;
   int rc = check_ws(pl, workspace);
@@ -1400,7 +1406,7 @@ int poisson_batch_solve(poisson_batch* b, const void* const* S, void* const* p, 
   if (!b || !S || !p) return POISSON_ERR_INVALID_ARG;
   if (!workspace || ((uintptr_t)workspace & 255)) return POISSON_ERR_WORKSPACE;
   for (int i = 0; i < b->n; ++i)
-    if (!S[i] || !p[i]) return POISSON_ERR_INVALID_ARG;
+    if (!S[i] || !p[i] || !field_aligned(S[i]) || !field_aligned(p[i])) return POISSON_ERR_INVALID_ARG;
   bool same = b->exec && b->capW == workspace;
   if (same)
     for (int i = 0; i < b->n; ++i)
