@@ -229,8 +229,9 @@ def test_uncertified_low_wavenumber_bound_falls_back_to_the_full_sweep():
     np.testing.assert_array_equal(pt, pf)
 
 
-@pytest.mark.parametrize("shape,seed", [((512, 512, 64), 3), ((384, 256, 64), 21), ((512, 384, 32), 5)])
-def test_first_try_from_the_kept_residual(shape, seed):
+@pytest.mark.parametrize("shape,seed,dy", [((512, 512, 64), 3, 50.0), ((384, 256, 64), 21, 50.0),
+                                           ((512, 384, 32), 5, 50.0), ((384, 256, 48), 9, 65.0)])
+def test_first_try_from_the_kept_residual(shape, seed, dy):
     """Sweep 1 keeps its residual r0 in FP32 (in the rows of p) and the low-wavenumber first try forms
     r0 - L q from it instead of S - mu - L (p0 + q).  Against the first try formed from S (the separate
     residual pass keeps nothing): the same iterate; the correction's norm within r0's rounding relative
@@ -238,6 +239,8 @@ def test_first_try_from_the_kept_residual(shape, seed):
     the tolerance) and still holds against the oracle."""
     nx, ny, nz = shape
     d = wl.anelastic_noise(nx, ny, nz, seed=seed)
+    if dy != d.dy:   # dx != dy: the general stencil of r0 - L q (and, at 384, the radix-3 transform)
+        d = wl.Domain(d.nx, d.ny, d.nz, d.dx, dy, d.dz, d.rho0, d.S, name=f"{d.name}_dy{dy:g}")
     pk, ik = _solve(d)                      # r0 kept
     ps, is_ = _solve(d, residual_pass=1)    # from S
     assert ik["converged"] and is_["converged"] and ik["sweeps"] == is_["sweeps"] == 1, (ik, is_)
