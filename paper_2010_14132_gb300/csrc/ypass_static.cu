@@ -38,6 +38,9 @@ size_t ys_smem(int N, int TK, bool inplace) {
 }
 
 constexpr int ys_max_threads(int E) { return E >= 16 || E % 3 == 0 ? 512 : 1024; }
+// the single-buffered kernel runs two CTAs per SM: 256 threads for the 12-element lengths keeps
+// their registers (128) free of spills
+constexpr int ys1_max_threads(int E) { return E % 3 == 0 ? 256 : ys_max_threads(E); }
 
 template <int N, int E, int SIGN, bool INPLACE>
 __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant__ CUtensorMap tm, Geom g,
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(ys_max_threads(E)) k_ys(const __grid_constant_
 // The next tile's load is issued as soon as the transform has finished reading the
 // tile (its outputs are in registers), so it also overlaps this tile's stores.
 template <int N, int E, int SIGN>
-__global__ void __launch_bounds__(ys_max_threads(E), 2) k_ys1(const __grid_constant__ CUtensorMap tm, Geom g,
+__global__ void __launch_bounds__(ys1_max_threads(E), 2) k_ys1(const __grid_constant__ CUtensorMap tm, Geom g,
                                                              const float2* __restrict__ twy,
                                                              float2* __restrict__ spec, int box_rows,
                                                              int tiles_per_level, int ntiles,
@@ -272,7 +275,7 @@ cudaError_t ys1_launch(float2* spec, const Geom& g, int N, const float2* twy, in
                        cudaStream_t st, bool* used) {
   const size_t smem = ys_tile_bytes(N, tk) + (size_t)N * sizeof(float2) + 64;
   const int nthreads = tk * (N / E);
-  if (smem > 110 * 1024 || nthreads > ys_max_threads(E) || nthreads < 32) return cudaSuccess;
+  if (smem > 110 * 1024 || nthreads > ys1_max_threads(E) || nthreads < 32) return cudaSuccess;
   const int box_rows = largest_divisor_upto(N, 256);
   if (((size_t)box_rows * tk * sizeof(float2)) % 128 != 0 && box_rows != N) return cudaSuccess;
   CUtensorMap tm;
@@ -322,12 +325,17 @@ cudaError_t launch_yfft_static(int sign, void* spec, const Geom& g, const FftPla
   if (tk % 2) tk += 1;   // 16-byte inner TMA box
   // kE3 elements per thread when ny has a factor 3 (radix 3, then 4)
   const int E = fy.n % 3 == 0 ? kE3 : (fy.E == 16 ? 16 : 8);
-  if (variant == 2 && E == 16) {   // single-buffered, in place, two CTAs per SM (16 elements per thread)
+  if (variant == 2 && (E == 16 || E == kE3)) {   // single-buffered, in place, two CTAs per SM
     int tk1 = tk;
-    while (tk1 > 2 && tk1 * (fy.n / E) > ys_max_threads(E)) tk1 >>= 1;
+    while (tk1 > 2 && tk1 * (fy.n / E) > ys1_max_threads(E)) tk1 >>= 1;
     float2* sp = (float2*)spec;
-    cudaError_t e = sign < 0 ? ys1_launch<16, -1>(sp, g, fy.n, tb.twy_f, tk1, done, err, st, used)
-                             : ys1_launch<16, +1>(sp, g, fy.n, tb.twy_f, tk1, done, err, st, used);
+    cudaError_t e;
+    if (E == 16)
+      e = sign < 0 ? ys1_launch<16, -1>(sp, g, fy.n, tb.twy_f, tk1, done, err, st, used)
+                   : ys1_launch<16, +1>(sp, g, fy.n, tb.twy_f, tk1, done, err, st, used);
+    else
+      e = sign < 0 ? ys1_launch<kE3, -1>(sp, g, fy.n, tb.twy_f, tk1, done, err, st, used)
+                   : ys1_launch<kE3, +1>(sp, g, fy.n, tb.twy_f, tk1, done, err, st, used);
     if (e != cudaSuccess || *used) return e;
   }
   const bool inplace = variant == 1;
