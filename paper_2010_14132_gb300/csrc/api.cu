@@ -189,7 +189,7 @@ void layout_workspace(poisson_plan* pl) {
   off = align256(off + (size_t)pl->nz * pl->g.plane * pl->csize());
   pl->off_stats = off;
   // the fused middle's scheduling counters (one set per pass of a solve) follow Stats, so one
-  // memset at the start of a solve clears both
+  // zeroing kernel at the start of a solve clears both
   pl->sched_words = spectral_fused_sched_words(pl->nxh);
   pl->off_sched = off + ((sizeof(Stats) + 15) & ~(size_t)15);
   pl->stats_bytes = pl->off_sched - pl->off_stats + 4 * sizeof(unsigned) * (size_t)pl->sched_words;
@@ -864,7 +864,7 @@ static cudaError_t cond_end(cudaStream_t body) {
 // The solve on fields in the solver's layout.
 static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cudaStream_t st) {
   Stats* stats = (Stats*)(ws + pl->off_stats);
-  PGB_CUDA(cudaMemsetAsync(stats, 0, pl->stats_bytes, st));
+  PGB_CUDA(launch_zero_words(stats, pl->stats_bytes, st));
   const bool t_double = pl->fp64();
   XinvExtra ex{};
   ex.partials = (double*)(ws + pl->off_part);
@@ -1055,7 +1055,7 @@ int poisson_solve_adjoint(poisson_plan* pl, const void* gp, const void* p, void*
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   Stats* stats = (Stats*)(ws + pl->off_stats);
-  PGB_CUDA(cudaMemsetAsync(stats, 0, sizeof(Stats), st));
+  PGB_CUDA(launch_zero_words(stats, sizeof(Stats), st));
   const bool t_double = pl->fp64();
   const int io_double = pl->dtype != POISSON_FP32;
   const bool swap = pl->layout != POISSON_LAYOUT_Z_Y_X;

@@ -302,6 +302,8 @@ cudaError_t launch_finalize(const float* p0, const float* q, double* p, long lon
 // (*done == 0), else 0, so that the IF node that follows runs its body (a refinement sweep) only
 // while the solve still needs it.
 cudaError_t launch_set_if_not_done(cudaGraphConditionalHandle h, const int* done, cudaStream_t st);
+// Zeroes `bytes` (a multiple of 4) at p with a kernel on stream st.
+cudaError_t launch_zero_words(void* p, size_t bytes, cudaStream_t st);
 // Four ints from src to dst by a one-thread kernel (dst may be mapped host memory).
 cudaError_t launch_copy_status(const int* src, int* dst, cudaStream_t st);
 // Conjugate gradients for a density varying in x, y and z (cg_kernels.cu).

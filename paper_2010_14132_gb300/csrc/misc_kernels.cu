@@ -420,6 +420,23 @@ cudaError_t launch_set_if_not_done(cudaGraphConditionalHandle h, const int* done
   return cudaGetLastError();
 }
 
+// Zeroes n 32-bit words.  A kernel rather than cudaMemsetAsync: the solve's statistics are cleared on the
+// compute stream, where a memset can be served by a copy engine and wait behind a host copy in flight.
+__global__ void __launch_bounds__(256) k_zero_words(unsigned* __restrict__ p, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = 0u;
+}
+
+cudaError_t launch_zero_words(void* p, size_t bytes, cudaStream_t st) {
+  if (bytes % 4) return cudaErrorInvalidValue;
+  const long long n = (long long)(bytes / 4);
+  if (n == 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 64) blocks = 64;
+  k_zero_words<<<(unsigned)blocks, 256, 0, st>>>((unsigned*)p, n);
+  return cudaGetLastError();
+}
+
 // four ints (src need not be 16-byte aligned)
 __global__ void k_copy_status(const int* __restrict__ src, int* dst) {
   dst[0] = src[0];
