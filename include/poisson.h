@@ -124,7 +124,7 @@ typedef enum {
                                     level chunk): a stencil pass marching up the levels writes r as
                                     float (one more field-sized buffer in the workspace; query the size
                                     after setting it), then the plain R2C x-pass transforms it */
-  POISSON_OPT_VERIFY = 14         /* mixed: 1 (default): from the second sweep on, once a sweep's column
+  POISSON_OPT_VERIFY = 14,        /* mixed: 1 (default): from the second sweep on, once a sweep's column
                                     solves are done, the norm of its correction delta_n (Parseval on the
                                     solved half spectrum) bounds the error of the current iterate,
                                     ||e_{n-1}|| <= ||delta_n||/(1 - phi) <= 2 ||delta_n|| for a contraction
@@ -139,6 +139,12 @@ typedef enum {
                                     upper bound, and when it does not certify p_1 the sweep runs in full.
                                     2: the verification solves every column (no cheaper first try).
                                     0: every sweep is applied in full */
+  POISSON_OPT_GRAPH = 15          /* mixed: 1 (default): a solve called outside any stream capture and
+                                    without profiling is captured once into a CUDA graph per (S, p,
+                                    workspace) triple (the plan keeps the last four) and replayed on the
+                                    caller's stream; the sweeps after the first are graph IF nodes on the
+                                    device's done flag, so a certified solve launches none of their
+                                    kernels.  0: plain stream launches (those kernels return at once) */
 } poisson_option;
 
 /* Field layouts (POISSON_OPT_LAYOUT), C order, outermost index first. */

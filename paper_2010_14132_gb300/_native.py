@@ -34,6 +34,7 @@ POISSON_OPT_LAYOUT = 11
 POISSON_OPT_SPECTRAL_FUSED = 12
 POISSON_OPT_RESIDUAL_PASS = 13
 POISSON_OPT_VERIFY = 14
+POISSON_OPT_GRAPH = 15
 POISSON_BATCH_OPT_PERSISTENT = 0
 POISSON_BATCH_OPT_STALL_TEST = 1
 POISSON_BATCH_OPT_BRANCHES = 2

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -84,6 +85,20 @@ struct poisson_plan {
   // Set by a batch while it captures its graph: the stream into which each later refinement sweep is
   // captured as the body of a graph IF node (run only while the solve is not done); null otherwise.
   cudaStream_t cond_body = nullptr;
+  // POISSON_OPT_GRAPH: the plan's own captured solves, keyed by their field and workspace pointers
+  struct SolveGraph {
+    const void* S;
+    void* p;
+    void* ws;
+    unsigned version;
+    unsigned long long used;
+    cudaGraphExec_t exec;
+  };
+  static constexpr size_t kGraphs = 4;
+  int use_graph = 1;
+  std::vector<SolveGraph> graphs;
+  unsigned long long graph_clock = 0;
+  cudaStream_t gcap = nullptr, gbody = nullptr;
   double tol = 1e-10;
   Geom g{};
   Tables tb{};
@@ -287,6 +302,9 @@ int poisson_plan_destroy(poisson_plan* pl) {
   if (!pl) return POISSON_OK;
   cudaDeviceSynchronize();
   for (cudaEvent_t e : pl->prof.pool) cudaEventDestroy(e);
+  for (auto& gr : pl->graphs) cudaGraphExecDestroy(gr.exec);
+  if (pl->gcap) cudaStreamDestroy(pl->gcap);
+  if (pl->gbody) cudaStreamDestroy(pl->gbody);
   if (pl->tables) cudaFree(pl->tables);
   if (pl->lowk_d) cudaFree(pl->lowk_d);
   if (pl->lowk_inv_d) cudaFree(pl->lowk_inv_d);
@@ -539,6 +557,10 @@ int poisson_plan_set_option(poisson_plan* pl, int option, double value) {
       if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
       pl->prof.on = value != 0;
       pl->prof.used = 0;
+      return POISSON_OK;
+    case POISSON_OPT_GRAPH:
+      if (!(value == 0 || value == 1)) return POISSON_ERR_INVALID_ARG;
+      pl->use_graph = (int)value;
       return POISSON_OK;
     default:
       return POISSON_ERR_INVALID_ARG;
@@ -861,6 +883,55 @@ static cudaError_t cond_end(cudaStream_t body) {
   return cudaStreamEndCapture(body, &g);
 }
 
+// A plan's captured solve for these pointers (captured now if the plan has none that is current, the
+// least recently used one replaced beyond kGraphs), launched on st.  The sweeps after the first are IF
+// nodes on the done flag (cond_body during the capture).
+static int solve_graph(poisson_plan* pl, const void* S, void* p, void* ws, cudaStream_t st,
+                       const std::function<int(cudaStream_t)>& solve_on) {
+  poisson_plan::SolveGraph* hit = nullptr;
+  for (auto& gr : pl->graphs)
+    if (gr.S == S && gr.p == p && gr.ws == ws && gr.version == pl->version) hit = &gr;
+  if (!hit) {
+    if (!pl->gcap) PGB_CUDA(cudaStreamCreateWithFlags(&pl->gcap, cudaStreamNonBlocking));
+    if (!pl->gbody) PGB_CUDA(cudaStreamCreateWithFlags(&pl->gbody, cudaStreamNonBlocking));
+    PGB_CUDA(cudaStreamBeginCapture(pl->gcap, cudaStreamCaptureModeRelaxed));
+    pl->cond_body = pl->gbody;
+    const int rc = solve_on(pl->gcap);
+    pl->cond_body = nullptr;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(pl->gcap, &graph);
+    if (rc != POISSON_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __LINE__);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate", __LINE__);
+    // stale entries (older options) first, then the least recently used
+    for (size_t i = 0; i < pl->graphs.size();)
+      if (pl->graphs[i].version != pl->version) {
+        cudaGraphExecDestroy(pl->graphs[i].exec);
+        pl->graphs.erase(pl->graphs.begin() + i);
+      } else {
+        ++i;
+      }
+    if (pl->graphs.size() >= poisson_plan::kGraphs) {
+      size_t lru = 0;
+      for (size_t i = 1; i < pl->graphs.size(); ++i)
+        if (pl->graphs[i].used < pl->graphs[lru].used) lru = i;
+      cudaGraphExecDestroy(pl->graphs[lru].exec);   // freed once a launch in flight completes
+      pl->graphs.erase(pl->graphs.begin() + lru);
+    }
+    pl->graphs.push_back({S, p, ws, pl->version, 0, exec});
+    hit = &pl->graphs.back();
+  }
+  hit->used = ++pl->graph_clock;
+  PGB_CUDA(cudaGraphLaunch(hit->exec, st));
+  return POISSON_OK;
+}
+
 // The solve on fields in the solver's layout.
 static int solve_fields(poisson_plan* pl, const void* S, void* p, char* ws, cudaStream_t st) {
   Stats* stats = (Stats*)(ws + pl->off_stats);
@@ -1028,14 +1099,21 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
     return POISSON_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
-  if (pl->layout == POISSON_LAYOUT_Z_Y_X) {
-    rc = solve_fields(pl, S, p, ws, st);
-  } else {
+  auto solve_on = [&](cudaStream_t s) -> int {
+    if (pl->layout == POISSON_LAYOUT_Z_Y_X) return solve_fields(pl, S, p, ws, s);
     void* Sa = ws + pl->off_fa;
     void* pb = ws + pl->off_fb;
-    PGB_CUDA(to_solver_layout(pl, S, Sa, st));
-    rc = solve_fields(pl, Sa, pb, ws, st);
-    if (rc == POISSON_OK) PGB_CUDA(from_solver_layout(pl, pb, p, st));
+    PGB_CUDA(to_solver_layout(pl, S, Sa, s));
+    int r = solve_fields(pl, Sa, pb, ws, s);
+    if (r == POISSON_OK) PGB_CUDA(from_solver_layout(pl, pb, p, s));
+    return r;
+  };
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  PGB_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (pl->mixed() && pl->use_graph && !pl->prof.on && pl->max_sweeps >= 2 && cs == cudaStreamCaptureStatusNone) {
+    rc = solve_graph(pl, S, p, workspace, st, solve_on);
+  } else {
+    rc = solve_on(st);
   }
   if (rc != POISSON_OK) return rc;
   if (info) return fill_info(pl, ws, st, info);

@@ -49,7 +49,7 @@ class Plan:
     def __init__(self, nx, ny, nz, dx, dy, dz, rho0, dtype="fp64", device=None, bc="neumann", layout="zyx",
                  lowk_radius2=None, max_sweeps=None, tolerance=None, y_tile=None, y_kernel=None,
                  x_elems=None, y_elems=None, level_chunk=None, x_kernel=None, col_tile=None,
-                 spectral_fused=None, residual_pass=None, verify=None):
+                 spectral_fused=None, residual_pass=None, verify=None, graph=None):
         if dtype not in DTYPES:
             raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
         if bc not in BCS:
@@ -96,6 +96,8 @@ class Plan:
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_RESIDUAL_PASS, residual_pass)
         if verify is not None:
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_VERIFY, verify)
+        if graph is not None:
+            N.poisson_plan_set_option(self._h, N.POISSON_OPT_GRAPH, graph)
         if layout != "zyx":
             N.poisson_plan_set_option(self._h, N.POISSON_OPT_LAYOUT, LAYOUTS[layout])
         self._ws = None
