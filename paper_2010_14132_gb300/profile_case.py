@@ -51,7 +51,9 @@ def main(argv=None) -> int:
     if args.cg is not None:
         rho3 = wl.perturbed_density(d.nx, d.ny, d.rho0, args.cg, seed=8)
         rho0 = rho3.mean(axis=(1, 2))
-    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, rho0, dtype=args.dtype, **opts)
+    # plain stream launches (POISSON_OPT_GRAPH = 0): the same kernels as the captured graph, each one
+    # launched from the host, so that a profiler sees every launch as its own
+    plan = Plan(d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, rho0, dtype=args.dtype, graph=0, **opts)
     S = torch.from_numpy(d.S).cuda().to(plan.field_dtype)
     p = torch.empty_like(S)
     w = torch.randn_like(S) if args.adjoint else None
