@@ -1109,7 +1109,10 @@ int poisson_solve(poisson_plan* pl, const void* S, void* p, void* workspace, voi
     return r;
   };
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  PGB_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {   // e.g. the legacy stream during another capture
+    (void)cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;                  // plain launches then
+  }
   if (pl->mixed() && pl->use_graph && !pl->prof.on && pl->max_sweeps >= 2 && cs == cudaStreamCaptureStatusNone) {
     rc = solve_graph(pl, S, p, workspace, st, solve_on);
   } else {
